@@ -1,0 +1,300 @@
+"""ctypes front end of the VRP-RPD CPU oracle.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg are the only callers.  The product library never
+imports this package.  Every function here forwards to the plain C oracle in
+this directory (see oracle.h for the paper passages each one follows).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_SOURCES = ["evaluate.c", "exact.c", "search.c"]
+_lock = threading.Lock()
+_lib = None
+
+CYCLE, VEH_CAP, POOL, MALFORMED = 1, 2, 4, 8
+LOAD_FULL = 1
+
+
+def build(force=False):
+    """Compile liboracle.so with gcc (no FMA contraction, so its fp64 search
+    arithmetic rounds exactly as written)."""
+    srcs = [os.path.join(_HERE, s) for s in _SOURCES]
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH):
+        newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "oracle.h")])
+        if os.path.getmtime(_LIB_PATH) >= newest:
+            return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
+           "-pthread", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class Inst(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("R", C.c_int32), ("Q", C.c_int32),
+                ("flags", C.c_uint32), ("d", C.POINTER(C.c_int32)), ("p", C.POINTER(C.c_int32))]
+
+
+class AlnsParams(C.Structure):
+    _fields_ = [("T0", C.c_double), ("alpha", C.c_double), ("reheat", C.c_double),
+                ("r", C.c_double), ("stagnation", C.c_int32), ("tau", C.c_int32),
+                ("sigma1", C.c_int32), ("sigma2", C.c_int32), ("sigma3", C.c_int32),
+                ("w_min", C.c_double), ("q_min", C.c_int32), ("q_max", C.c_int32),
+                ("iterations", C.c_int32), ("repair_mask", C.c_int32)]
+
+
+class AlnsStats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("accepted", C.c_int32), ("improved", C.c_int32),
+                ("new_best", C.c_int32), ("reheats", C.c_int32),
+                ("rejected_infeasible", C.c_int32), ("z_init", C.c_int32),
+                ("z_best", C.c_int32), ("z_current", C.c_int32), ("T_final", C.c_double),
+                ("w_destroy", C.c_double * 4), ("w_repair", C.c_double * 4)]
+
+
+class BrkgaParams(C.Structure):
+    _fields_ = [("pop", C.c_int32), ("generations", C.c_int32), ("warm_slots", C.c_int32),
+                ("warm_variants", C.c_int32), ("elite_frac", C.c_float),
+                ("mutant_frac", C.c_float), ("rho", C.c_float), ("eps", C.c_float)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            i32p, u32p, i64p = C.POINTER(C.c_int32), C.POINTER(C.c_uint32), C.POINTER(C.c_int64)
+            f32p = C.POINTER(C.c_float)
+            L.oracle_euc2d.argtypes = [i32p, C.c_int32, i32p]
+            L.oracle_evaluate.argtypes = [C.POINTER(Inst), i32p, i32p, C.c_int, i32p, u32p, i64p]
+            L.oracle_evaluate_batch.argtypes = [C.POINTER(Inst), C.c_int32, i32p, i32p, i32p, u32p,
+                                                C.c_int32]
+            L.oracle_sp_closure.argtypes = [i32p, C.c_int32, i64p]
+            L.oracle_bruteforce.argtypes = [C.POINTER(Inst), i32p, i32p]
+            L.oracle_bruteforce.restype = C.c_int64
+            L.oracle_minmax_vrp.argtypes = [i32p, C.c_int32, C.c_int32]
+            L.oracle_minmax_vrp.restype = C.c_int64
+            L.oracle_held_karp.argtypes = [i32p, C.c_int32]
+            L.oracle_held_karp.restype = C.c_int64
+            L.oracle_splitmix64_next.argtypes = [C.POINTER(C.c_uint64)]
+            L.oracle_splitmix64_next.restype = C.c_uint64
+            L.oracle_rng.argtypes = [C.c_uint64, C.c_uint64]
+            L.oracle_rng.restype = C.c_uint64
+            L.oracle_exp.argtypes = [C.c_double]
+            L.oracle_exp.restype = C.c_double
+            L.oracle_q_range.argtypes = [C.c_int32, i32p, i32p]
+            L.oracle_insertion_matrix.argtypes = [C.POINTER(Inst), i32p, i32p, C.c_int32, i32p, i32p,
+                                                  u32p]
+            L.oracle_initial_solution.argtypes = [C.POINTER(Inst), i32p, i32p, i32p]
+            L.oracle_alns_run.argtypes = [C.POINTER(Inst), i32p, i32p, C.POINTER(AlnsParams),
+                                          C.c_uint64, i32p, i32p, i32p, i32p, C.POINTER(AlnsStats),
+                                          i32p]
+            L.oracle_decode.argtypes = [C.POINTER(Inst), f32p, i32p, i32p, i32p, i32p, i64p]
+            L.oracle_encode.argtypes = [C.POINTER(Inst), i32p, i32p, f32p]
+            L.oracle_brkga_run.argtypes = [C.POINTER(Inst), C.POINTER(BrkgaParams), i32p, i32p,
+                                           C.c_uint64, f32p, i64p, i32p, i32p, i64p]
+            _lib = L
+    return _lib
+
+
+def _p(a, ct=C.c_int32):
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+def euc2d(coords):
+    coords = np.ascontiguousarray(coords, dtype=np.int32)
+    N = coords.shape[0]
+    d = np.empty((N, N), dtype=np.int32)
+    lib().oracle_euc2d(_p(coords), N, _p(d))
+    return d
+
+
+class OracleInstance:
+    """Holds d, p and sizes for the C oracle; keeps the arrays alive."""
+
+    def __init__(self, d, p, m, R, Q, load_full=False):
+        self.d = np.ascontiguousarray(d, dtype=np.int32)
+        self.p = np.ascontiguousarray(p, dtype=np.int32)
+        self.n = int(self.p.shape[0])
+        assert self.d.shape == (self.n + 1, self.n + 1)
+        self.m, self.R, self.Q = int(m), int(R), int(Q)
+        self.flags = LOAD_FULL if load_full else 0
+        self.c = Inst(self.n, self.m, self.R, self.Q, self.flags, _p(self.d), _p(self.p))
+
+    @classmethod
+    def from_workload(cls, inst, load_full=False):
+        return cls(euc2d(inst.coords), inst.p, inst.m, inst.R, inst.Q, load_full)
+
+
+def evaluate(I, ops, off, allow_partial=False, with_times=False):
+    ops = np.ascontiguousarray(ops, dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int32)
+    z = np.zeros(1, np.int32)
+    st = np.zeros(1, np.uint32)
+    times = np.zeros(2 * I.n + 2, np.int64) if with_times else None
+    rc = lib().oracle_evaluate(C.byref(I.c), _p(ops), _p(off), int(allow_partial), _p(z),
+                               _p(st, C.c_uint32), _p(times, C.c_int64) if with_times else None)
+    if rc != 0:
+        raise OverflowError("oracle: a time exceeded int32")
+    if with_times:
+        return int(z[0]), int(st[0]), times
+    return int(z[0]), int(st[0])
+
+
+def evaluate_batch(I, ops, off, threads=1):
+    ops = np.ascontiguousarray(ops, dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int32)
+    count = ops.shape[0]
+    z = np.zeros(count, np.int32)
+    st = np.zeros(count, np.uint32)
+    lib().oracle_evaluate_batch(C.byref(I.c), count, _p(ops), _p(off), _p(z), _p(st, C.c_uint32),
+                                threads)
+    return z, st
+
+
+def sp_closure(d):
+    d = np.ascontiguousarray(d, dtype=np.int32)
+    N = d.shape[0]
+    sp = np.empty((N, N), np.int64)
+    lib().oracle_sp_closure(_p(d), N, _p(sp, C.c_int64))
+    return sp
+
+
+def bruteforce(I):
+    ops = np.zeros(2 * I.n, np.int32)
+    off = np.zeros(I.m + 1, np.int32)
+    best = lib().oracle_bruteforce(C.byref(I.c), _p(ops), _p(off))
+    return int(best), ops, off
+
+
+def minmax_vrp(d, n, m):
+    d = np.ascontiguousarray(d, dtype=np.int32)
+    return int(lib().oracle_minmax_vrp(_p(d), n, m))
+
+
+def held_karp(d, n):
+    d = np.ascontiguousarray(d, dtype=np.int32)
+    return int(lib().oracle_held_karp(_p(d), n))
+
+
+def splitmix64_stream(seed, count):
+    s = C.c_uint64(seed)
+    return [int(lib().oracle_splitmix64_next(C.byref(s))) for _ in range(count)]
+
+
+def rng(key, counter):
+    return int(lib().oracle_rng(C.c_uint64(key), C.c_uint64(counter)))
+
+
+def exp(x):
+    return float(lib().oracle_exp(float(x)))
+
+
+def q_range(n):
+    a = np.zeros(1, np.int32)
+    b = np.zeros(1, np.int32)
+    lib().oracle_q_range(n, _p(a), _p(b))
+    return int(a[0]), int(b[0])
+
+
+def insertion_matrix(I, ops, off, c):
+    ops = np.ascontiguousarray(ops, dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int32)
+    G = int(off[-1]) + I.m
+    out = np.zeros((G, G), np.int32)
+    trav = np.zeros((G, G), np.int32)
+    st = np.zeros((G, G), np.uint32)
+    rc = lib().oracle_insertion_matrix(C.byref(I.c), _p(ops), _p(off), int(c), _p(out), _p(trav),
+                                       _p(st, C.c_uint32))
+    if rc != 0:
+        raise ValueError("oracle_insertion_matrix failed")
+    return out, trav, st
+
+
+def initial_solution(I, coords):
+    coords = np.ascontiguousarray(coords, dtype=np.int32)
+    ops = np.zeros(2 * I.n, np.int32)
+    off = np.zeros(I.m + 1, np.int32)
+    rc = lib().oracle_initial_solution(C.byref(I.c), _p(coords), _p(ops), _p(off))
+    if rc != 0:
+        raise ValueError("oracle_initial_solution failed")
+    return ops, off
+
+
+def alns_params(iterations, q_min=0, q_max=0, repair_mask=3):
+    return AlnsParams(0.30, 0.9998, 0.50, 0.1, 2000, 100, 33, 9, 13, 0.1, q_min, q_max,
+                      iterations, repair_mask)
+
+
+def alns_run(I, init_ops, init_off, params, seed):
+    init_ops = np.ascontiguousarray(init_ops, dtype=np.int32)
+    init_off = np.ascontiguousarray(init_off, dtype=np.int32)
+    bo = np.zeros(2 * I.n, np.int32)
+    bf = np.zeros(I.m + 1, np.int32)
+    co = np.zeros(2 * I.n, np.int32)
+    cf = np.zeros(I.m + 1, np.int32)
+    st = AlnsStats()
+    trace = np.zeros(max(1, params.iterations), np.int32)
+    rc = lib().oracle_alns_run(C.byref(I.c), _p(init_ops), _p(init_off), C.byref(params),
+                               C.c_uint64(seed), _p(bo), _p(bf), _p(co), _p(cf), C.byref(st),
+                               _p(trace))
+    if rc != 0:
+        raise ValueError(f"oracle_alns_run failed rc={rc}")
+    return dict(best_ops=bo, best_off=bf, cur_ops=co, cur_off=cf, stats=st, trace=trace)
+
+
+def decode(I, keys):
+    keys = np.ascontiguousarray(keys, dtype=np.float32)
+    ops = np.zeros(2 * I.n, np.int32)
+    off = np.zeros(I.m + 1, np.int32)
+    z = np.zeros(1, np.int32)
+    un = np.zeros(1, np.int32)
+    fit = np.zeros(1, np.int64)
+    lib().oracle_decode(C.byref(I.c), _p(keys, C.c_float), _p(ops), _p(off), _p(z), _p(un),
+                        _p(fit, C.c_int64))
+    return ops, off, int(z[0]), int(un[0]), int(fit[0])
+
+
+def encode(I, ops, off):
+    ops = np.ascontiguousarray(ops, dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int32)
+    keys = np.zeros(2 * I.n + I.m, np.float32)
+    lib().oracle_encode(C.byref(I.c), _p(ops), _p(off), _p(keys, C.c_float))
+    return keys
+
+
+def brkga_params(pop, generations, elite=0.2, mutant=0.1, rho=0.7, warm_frac=0.15,
+                 warm_variants=20, eps=0.03):
+    import math
+    return BrkgaParams(pop, generations, int(math.ceil(warm_frac * pop - 1e-9)), warm_variants,
+                       elite, mutant, rho, eps)
+
+
+def brkga_run(I, params, warm_ops, warm_off, seed):
+    L = 2 * I.n + I.m
+    keys = np.zeros((params.pop, L), np.float32)
+    trace = np.zeros(max(1, params.generations), np.int64)
+    bo = np.zeros(2 * I.n, np.int32)
+    bf = np.zeros(I.m + 1, np.int32)
+    best = np.zeros(1, np.int64)
+    wo = None if warm_ops is None else np.ascontiguousarray(warm_ops, dtype=np.int32)
+    wf = None if warm_off is None else np.ascontiguousarray(warm_off, dtype=np.int32)
+    rc = lib().oracle_brkga_run(C.byref(I.c), C.byref(params), _p(wo) if wo is not None else None,
+                                _p(wf) if wf is not None else None, C.c_uint64(seed),
+                                _p(keys, C.c_float), _p(trace, C.c_int64), _p(bo), _p(bf),
+                                _p(best, C.c_int64))
+    if rc != 0:
+        raise ValueError(f"oracle_brkga_run failed rc={rc}")
+    return dict(keys=keys, trace=trace, best_ops=bo, best_off=bf, best_fitness=int(best[0]))

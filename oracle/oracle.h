@@ -1,0 +1,117 @@
+/*
+ * VRP-RPD CPU oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain, slow, obviously-correct C written from the paper's problem statement
+ * (Section 3.1, Eqs. 1-22) and algorithms (Algorithm 1, Algorithm 2, Section
+ * 4.2-4.4).  Only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg may load this library; the product library never links or calls it.
+ * It shares no code, header or table with the CUDA library.
+ *
+ * Conventions: customers 1..n, depot 0, op code o = 2c + isPickup.
+ * A candidate is route-major: ops[off[v] .. off[v+1]) is vehicle v's sequence.
+ * Status bits: 1 CYCLE, 2 VEH_CAP, 4 POOL, 8 MALFORMED.
+ */
+#ifndef VRPRPD_ORACLE_H
+#define VRPRPD_ORACLE_H
+#include <stdint.h>
+
+#define OR_CYCLE 1u
+#define OR_VEH_CAP 2u
+#define OR_POOL 4u
+#define OR_MALFORMED 8u
+#define OR_LOAD_FULL 1u
+
+typedef struct {
+    int32_t n, m, R, Q;
+    uint32_t flags;      /* OR_LOAD_FULL or 0 (minimal load, the default) */
+    const int32_t* d;    /* (n+1)*(n+1) travel times, row-major */
+    const int32_t* p;    /* n processing times, p[c-1] for customer c */
+} oracle_inst;
+
+/* EUC_2D (TSPLIB): d(i,j) = nint(sqrt(dx^2+dy^2)), computed in double. */
+void oracle_euc2d(const int32_t* coords, int32_t n_nodes, int32_t* d);
+
+/* Evaluate one candidate.  allow_partial=1 accepts a subset of customers
+ * (each present customer with both ops), total ops = off[m].
+ * Returns 0, or -1 if a time exceeds INT32_MAX (never for valid instances).
+ * times (optional, size 2n+2 indexed by op code) receives each op's
+ * departure time (drop: arrival) or INT64_MIN if unprocessed. */
+int oracle_evaluate(const oracle_inst* I, const int32_t* ops, const int32_t* off,
+                    int allow_partial, int32_t* z, uint32_t* status, int64_t* times);
+
+void oracle_evaluate_batch(const oracle_inst* I, int32_t count, const int32_t* ops,
+                           const int32_t* off, int32_t* z, uint32_t* status, int32_t threads);
+
+/* Shortest-path closure of d (Floyd-Warshall), for lower-bound invariants. */
+void oracle_sp_closure(const int32_t* d, int32_t n_nodes, int64_t* sp);
+
+/* Exhaustive optimum over all candidates (every op order, every split into m
+ * routes); returns the best makespan among status==0 candidates, or -1. */
+int64_t oracle_bruteforce(const oracle_inst* I, int32_t* best_ops, int32_t* best_off);
+
+/* Min-max VRP optimum by enumeration of customer orders and splits (each
+ * customer visited once, route length = travel only). */
+int64_t oracle_minmax_vrp(const int32_t* d, int32_t n, int32_t m);
+
+/* Held-Karp TSP tour length over nodes 0..n. */
+int64_t oracle_held_karp(const int32_t* d, int32_t n);
+
+/* ---- counter-based RNG and exp (independent restatements) ---- */
+uint64_t oracle_splitmix64_next(uint64_t* state);
+uint64_t oracle_rng(uint64_t key, uint64_t counter);
+double oracle_exp(double x);
+
+/* ---- ALNS (Algorithm 1) ---- */
+typedef struct {
+    double T0, alpha, reheat, r;          /* 0.30, 0.9998, 0.50, 0.1 */
+    int32_t stagnation, tau;              /* 2000, 100 */
+    int32_t sigma1, sigma2, sigma3;       /* 33, 9, 13 */
+    double w_min;                         /* 0.1 */
+    int32_t q_min, q_max;                 /* 0 = paper formula */
+    int32_t iterations;
+    int32_t repair_mask;                  /* bit0 greedy, bit1 regret-2 */
+} oracle_alns_params;
+
+typedef struct {
+    int32_t iterations, accepted, improved, new_best, reheats, rejected_infeasible;
+    int32_t z_init, z_best, z_current;
+    double T_final;
+    double w_destroy[4], w_repair[4];
+} oracle_alns_stats;
+
+void oracle_q_range(int32_t n, int32_t* q_min, int32_t* q_max);
+
+/* Insertion-delta matrix for customer c into partial solution (ops, off).
+ * out has (N+m)^2 int32 entries, row = D gap, col = P gap (gaps enumerated
+ * route by route, gap i of route v sits before the v-th route's op i).
+ * Each entry = z(S') - z(S), or INT32_MAX when S' has any status bit.
+ * Also writes the travel delta per entry (travel_out, may be NULL). */
+int oracle_insertion_matrix(const oracle_inst* I, const int32_t* ops, const int32_t* off,
+                            int32_t c, int32_t* out, int32_t* travel_out, uint32_t* status_out);
+
+int oracle_initial_solution(const oracle_inst* I, const int32_t* coords, int32_t* ops, int32_t* off);
+
+int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t* init_off,
+                    const oracle_alns_params* P, uint64_t seed,
+                    int32_t* best_ops, int32_t* best_off, int32_t* cur_ops, int32_t* cur_off,
+                    oracle_alns_stats* st, int32_t* z_trace);
+
+/* ---- BRKGA (Algorithm 2 decoder, Section 4.4) ---- */
+/* keys: 2n priority keys (op index 2(c-1)+isPickup) followed by m vehicle keys. */
+int oracle_decode(const oracle_inst* I, const float* keys, int32_t* ops, int32_t* off,
+                  int32_t* z, int32_t* unscheduled, int64_t* fitness);
+
+void oracle_encode(const oracle_inst* I, const int32_t* ops, const int32_t* off, float* keys);
+
+typedef struct {
+    int32_t pop, generations, warm_slots, warm_variants;
+    float elite_frac, mutant_frac, rho;
+    float eps;                            /* perturbation half-width, 0.03 */
+} oracle_brkga_params;
+
+int oracle_brkga_run(const oracle_inst* I, const oracle_brkga_params* P,
+                     const int32_t* warm_ops, const int32_t* warm_off, uint64_t seed,
+                     float* final_keys, int64_t* best_fitness_trace,
+                     int32_t* best_ops, int32_t* best_off, int64_t* best_fitness);
+
+#endif

@@ -1,0 +1,725 @@
+/*
+ * VRP-RPD oracle: counter-based RNG, exp, ALNS (Algorithm 1) and BRKGA
+ * (Section 4.4, Algorithm 2).  TEST INFRASTRUCTURE ONLY -- see oracle.h.
+ *
+ * Everything here is sequential and re-simulates from scratch: each entry of
+ * an insertion-delta matrix is the evaluator run on the whole modified
+ * solution.  Floating point is IEEE fp64/fp32 with no FMA contraction (the
+ * library is compiled with -ffp-contract=off), so every rounding is the one
+ * written in the source.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "oracle.h"
+
+/* ------------------------------------------------------------------------ */
+/* SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number     */
+/* generators", OOPSLA 2014): state advances by the golden gamma, output is  */
+/* the variant-13 finaliser of the state.  The counter form returns the      */
+/* (counter+1)-th output of a generator seeded with key.                     */
+/* ------------------------------------------------------------------------ */
+static const uint64_t SM_GAMMA = 0x9E3779B97F4A7C15ull;
+
+static uint64_t sm_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+uint64_t oracle_splitmix64_next(uint64_t* state) {
+    *state += SM_GAMMA;
+    return sm_mix(*state);
+}
+
+uint64_t oracle_rng(uint64_t key, uint64_t counter) { return sm_mix(key + (counter + 1) * SM_GAMMA); }
+
+/* Stream keys: stream s of seed is the s-th draw of the seed itself. */
+enum { STREAM_ALNS = 1, STREAM_BRKGA = 2, STREAM_WARM = 3 };
+static uint64_t stream_key(uint64_t seed, uint64_t s) { return oracle_rng(seed, s); }
+
+/* uniform integer in [0,k): high 32 bits scaled by k (multiply-shift) */
+static int32_t rng_below(uint64_t r, int32_t k) { return (int32_t)(((r >> 32) * (uint64_t)k) >> 32); }
+/* uniform double in [0,1) from 53 bits */
+static double rng_unit(uint64_t r) { return (double)(r >> 11) * (1.0 / 9007199254740992.0); }
+/* float key in [0,1) from 24 bits */
+static float rng_key(uint64_t r) { return (float)(r >> 40) * (1.0f / 16777216.0f); }
+
+/* ------------------------------------------------------------------------ */
+/* exp(x) for the acceptance test: Cody-Waite reduction x = k ln2 + r with   */
+/* ln2 split in two parts, |r| <= ln2/2, then the Taylor series of e^r to    */
+/* degree 20 (truncation error below 2^-70 relative), then scaling by 2^k.   */
+/* ------------------------------------------------------------------------ */
+double oracle_exp(double x) {
+    if (x != x) return x;
+    if (x > 709.0) return INFINITY;
+    if (x < -708.0) return 0.0;
+    const double ln2_hi = 0.693147180369123816490;     /* 32 significant bits of ln 2 */
+    const double ln2_lo = 1.90821492927058770002e-10;  /* ln 2 - ln2_hi */
+    const double inv_ln2 = 1.44269504088896338700;
+    double kd = floor(x * inv_ln2 + 0.5);
+    int k = (int)kd;
+    double r = (x - kd * ln2_hi) - kd * ln2_lo;
+    /* Horner from the highest term: sum_{j=0..20} r^j / j! */
+    double s = 1.0;
+    for (int j = 20; j >= 1; j--) s = 1.0 + s * (r / (double)j);
+    /* 2^k for -1022 <= k <= 1023 built from its exponent field */
+    union { uint64_t u; double f; } scale;
+    scale.u = (uint64_t)(k + 1023) << 52;
+    return s * scale.f;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Evaluation core with caller scratch, plus route travel (sum of legs).     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int cap_ops, cap_m;
+    int32_t *ops, *off;      /* candidate build buffer */
+    int32_t *ops2, *off2;
+} scratch_t;
+
+static int64_t Dd(const oracle_inst* I, int a, int b) { return I->d[(int64_t)a * (I->n + 1) + b]; }
+
+static int64_t travel_of(const oracle_inst* I, const int32_t* ops, const int32_t* off) {
+    int64_t t = 0;
+    for (int v = 0; v < I->m; v++) {
+        if (off[v + 1] == off[v]) continue;
+        int loc = 0;
+        for (int k = off[v]; k < off[v + 1]; k++) { t += Dd(I, loc, ops[k] >> 1); loc = ops[k] >> 1; }
+        t += Dd(I, loc, 0);
+    }
+    return t;
+}
+
+/* Build S' = S + D_c at gap i of route a + P_c at gap j of route b. */
+static void build_insert(const oracle_inst* I, const int32_t* ops, const int32_t* off, int c,
+                         int a, int i, int b, int j, int32_t* nops, int32_t* noff) {
+    int w = 0;
+    noff[0] = 0;
+    for (int v = 0; v < I->m; v++) {
+        int L = off[v + 1] - off[v];
+        for (int k = 0; k <= L; k++) {
+            if (v == a && k == i) nops[w++] = 2 * c;
+            if (v == b && k == j) nops[w++] = 2 * c + 1;
+            if (k < L) nops[w++] = ops[off[v] + k];
+        }
+        noff[v + 1] = w;
+    }
+}
+
+/* Capacity of one route (Eqs. 13-18 with the minimal or the full start load). */
+static int route_cap_violated(const oracle_inst* I, const int32_t* ops, const int32_t* off, int v) {
+    int64_t s = 0, smin = 0, smax = 0;
+    for (int k = off[v]; k < off[v + 1]; k++) {
+        s += (ops[k] & 1) ? 1 : -1;
+        if (s < smin) smin = s;
+        if (s > smax) smax = s;
+    }
+    if (I->flags & OR_LOAD_FULL) return smin < -(int64_t)I->Q || smax > 0;
+    return -smin + smax > I->Q;
+}
+
+static int64_t pack_key_less(int64_t dz1, int64_t dt1, int64_t f1, int64_t dz2, int64_t dt2, int64_t f2) {
+    if (dz1 != dz2) return dz1 < dz2;
+    if (dt1 != dt2) return dt1 < dt2;
+    return f1 < f2;
+}
+
+int oracle_insertion_matrix(const oracle_inst* I, const int32_t* ops, const int32_t* off,
+                            int32_t c, int32_t* out, int32_t* travel_out, uint32_t* status_out) {
+    const int m = I->m, N = off[m], G = N + m;
+    int32_t z0;
+    uint32_t st0;
+    oracle_evaluate(I, ops, off, 1, &z0, &st0, NULL);
+    if (st0 & (OR_CYCLE | OR_MALFORMED)) return -1;
+    int64_t t0 = travel_of(I, ops, off);
+    int32_t* nops = (int32_t*)malloc(sizeof(int32_t) * (N + 2));
+    int32_t* noff = (int32_t*)malloc(sizeof(int32_t) * (m + 1));
+    int rowbase = 0;
+    for (int a = 0; a < m; a++) {
+        int La = off[a + 1] - off[a];
+        for (int i = 0; i <= La; i++) {
+            int row = rowbase + i;
+            int colbase = 0;
+            for (int b = 0; b < m; b++) {
+                int Lb = off[b + 1] - off[b];
+                for (int j = 0; j <= Lb; j++) {
+                    int col = colbase + j;
+                    int64_t idx = (int64_t)row * G + col;
+                    int32_t z;
+                    uint32_t st;
+                    if (a == b && j < i) {
+                        /* pickup before its own drop on one route: a precedence cycle */
+                        z = INT32_MAX;
+                        st = OR_CYCLE;
+                        if (travel_out) travel_out[idx] = 0;
+                    } else {
+                        build_insert(I, ops, off, c, a, i, b, j, nops, noff);
+                        oracle_evaluate(I, nops, noff, 1, &z, &st, NULL);
+                        /* vehicle capacity is judged on the two receiving routes only: a
+                         * destroyed partial solution may violate it elsewhere */
+                        st &= ~OR_VEH_CAP;
+                        if (route_cap_violated(I, nops, noff, a) || route_cap_violated(I, nops, noff, b))
+                            st |= OR_VEH_CAP;
+                        if (travel_out) travel_out[idx] = (int32_t)(travel_of(I, nops, noff) - t0);
+                    }
+                    out[idx] = st ? INT32_MAX : (int32_t)(z - z0);
+                    if (status_out) status_out[idx] = st;
+                }
+                colbase += Lb + 1;
+            }
+        }
+        rowbase += La + 1;
+    }
+    free(nops);
+    free(noff);
+    return 0;
+}
+
+void oracle_q_range(int32_t n, int32_t* q_min, int32_t* q_max) {
+    /* Section 4.2.2: q_max = max(4, floor(0.05 n)), q_min = max(4, floor(q_max/2)) */
+    int32_t qm = (int32_t)((int64_t)n * 5 / 100);
+    if (qm < 4) qm = 4;
+    int32_t qn = qm / 2;
+    if (qn < 4) qn = 4;
+    *q_max = qm;
+    *q_min = qn;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initial solution: customers in exact angular order around the depot       */
+/* (ties by customer id), split into m consecutive sectors by workload       */
+/* w_c = 2 d(0,c) + p_c (midpoint rule), then each route serves its sector   */
+/* in blocks of b customers as "D c1..cb, P c1..cb" with b = min(Q, R/m').   */
+/* ------------------------------------------------------------------------ */
+static const int32_t* g_coords;
+static int angle_half(int64_t dx, int64_t dy) { return (dy < 0 || (dy == 0 && dx < 0)) ? 1 : 0; }
+static int angle_cmp(const void* pa, const void* pb) {
+    int a = *(const int*)pa, b = *(const int*)pb;
+    int64_t ax = g_coords[2 * a] - g_coords[0], ay = g_coords[2 * a + 1] - g_coords[1];
+    int64_t bx = g_coords[2 * b] - g_coords[0], by = g_coords[2 * b + 1] - g_coords[1];
+    int ha = angle_half(ax, ay), hb = angle_half(bx, by);
+    if (ha != hb) return ha - hb;
+    int64_t cr = ax * by - ay * bx;
+    if (cr > 0) return -1;
+    if (cr < 0) return 1;
+    return a - b;
+}
+
+int oracle_initial_solution(const oracle_inst* I, const int32_t* coords, int32_t* ops, int32_t* off) {
+    const int n = I->n, m = I->m;
+    if (I->R < 1 || I->Q < 1 || m < 1) return -1;
+    int* order = (int*)malloc(sizeof(int) * (n + 1));
+    for (int k = 0; k < n; k++) order[k] = k + 1;
+    if (coords) {
+        g_coords = coords;
+        qsort(order, (size_t)n, sizeof(int), angle_cmp);
+    }
+    int mact = m < I->R ? m : I->R;
+    int b = I->R / mact;
+    if (b > I->Q) b = I->Q;
+    if (b < 1) b = 1;
+    int64_t W = 0;
+    for (int k = 0; k < n; k++) W += 2 * Dd(I, 0, order[k]) + I->p[order[k] - 1];
+    int* sector = (int*)malloc(sizeof(int) * (n + 1));
+    int64_t cum = 0;
+    for (int k = 0; k < n; k++) {
+        int64_t w = 2 * Dd(I, 0, order[k]) + I->p[order[k] - 1];
+        int64_t s = W > 0 ? ((2 * cum + w) * mact) / (2 * W) : ((int64_t)k * mact) / n;
+        if (s > mact - 1) s = mact - 1;
+        sector[k] = (int)s;
+        cum += w;
+    }
+    int w = 0;
+    off[0] = 0;
+    for (int v = 0; v < m; v++) {
+        int k = 0;
+        while (k < n) {
+            if (sector[k] != v) { k++; continue; }
+            int blk[4096];
+            int cnt = 0;
+            while (k < n && cnt < b) {
+                if (sector[k] == v) blk[cnt++] = order[k];
+                k++;
+            }
+            for (int t = 0; t < cnt; t++) ops[w++] = 2 * blk[t];
+            for (int t = 0; t < cnt; t++) ops[w++] = 2 * blk[t] + 1;
+        }
+        off[v + 1] = w;
+    }
+    free(order);
+    free(sector);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* ALNS (Algorithm 1) with random removal and greedy / regret-2 repair.      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t dz, dt, flat;
+    int row, col, ok;
+} best_t;
+
+static void remove_customers(int m, const int32_t* ops, const int32_t* off, const char* rem,
+                             int32_t* nops, int32_t* noff) {
+    int w = 0;
+    noff[0] = 0;
+    for (int v = 0; v < m; v++) {
+        for (int k = off[v]; k < off[v + 1]; k++)
+            if (!rem[ops[k] >> 1]) nops[w++] = ops[k];
+        noff[v + 1] = w;
+    }
+}
+
+static void gap_of(const int32_t* off, int m, int g, int* route, int* pos) {
+    for (int v = 0; v < m; v++) {
+        int L = off[v + 1] - off[v];
+        if (g <= L) { *route = v; *pos = g; return; }
+        g -= L + 1;
+    }
+    *route = -1;
+    *pos = -1;
+}
+
+/* Scan the matrix of customer c: overall best and per-drop-vehicle best. */
+static void scan_matrix(const oracle_inst* I, const int32_t* ops, const int32_t* off, int c,
+                        best_t* best, best_t* per_vehicle) {
+    const int m = I->m, N = off[m], G = N + m;
+    int32_t* M = (int32_t*)malloc(sizeof(int32_t) * (size_t)G * G);
+    int32_t* T = (int32_t*)malloc(sizeof(int32_t) * (size_t)G * G);
+    oracle_insertion_matrix(I, ops, off, c, M, T, NULL);
+    best->ok = 0;
+    for (int v = 0; v < m; v++) per_vehicle[v].ok = 0;
+    for (int row = 0; row < G; row++) {
+        int a, i;
+        gap_of(off, m, row, &a, &i);
+        for (int col = 0; col < G; col++) {
+            int64_t idx = (int64_t)row * G + col;
+            if (M[idx] == INT32_MAX) continue;
+            int64_t dz = M[idx], dt = T[idx];
+            if (!best->ok || pack_key_less(dz, dt, idx, best->dz, best->dt, best->flat))
+                *best = (best_t){dz, dt, idx, row, col, 1};
+            best_t* pv = &per_vehicle[a];
+            if (!pv->ok || pack_key_less(dz, dt, idx, pv->dz, pv->dt, pv->flat))
+                *pv = (best_t){dz, dt, idx, row, col, 1};
+        }
+    }
+    free(M);
+    free(T);
+}
+
+static void apply_insert(const oracle_inst* I, int32_t* ops, int32_t* off, int c, int row, int col,
+                         int32_t* tmp_ops, int32_t* tmp_off) {
+    int a, i, b, j;
+    gap_of(off, I->m, row, &a, &i);
+    gap_of(off, I->m, col, &b, &j);
+    build_insert(I, ops, off, c, a, i, b, j, tmp_ops, tmp_off);
+    memcpy(ops, tmp_ops, sizeof(int32_t) * tmp_off[I->m]);
+    memcpy(off, tmp_off, sizeof(int32_t) * (I->m + 1));
+}
+
+#define REGRET_INF ((int64_t)1 << 40)
+
+/* Greedy (repair 0) or regret-2 (repair 1) reinsertion of the customers in
+ * rem[] (listed in ascending id order in list[]). */
+static int repair(const oracle_inst* I, int op, int32_t* ops, int32_t* off, int* list, int cnt,
+                  int32_t* tmp_ops, int32_t* tmp_off) {
+    const int m = I->m;
+    best_t* pv = (best_t*)malloc(sizeof(best_t) * m);
+    best_t* bests = (best_t*)malloc(sizeof(best_t) * (cnt + 1));
+    int64_t* regret = (int64_t*)malloc(sizeof(int64_t) * (cnt + 1));
+    while (cnt > 0) {
+        for (int t = 0; t < cnt; t++) {
+            scan_matrix(I, ops, off, list[t], &bests[t], pv);
+            if (!bests[t].ok) { free(pv); free(bests); free(regret); return -1; }
+            int64_t c1 = REGRET_INF, c2 = REGRET_INF;
+            for (int v = 0; v < m; v++) {
+                if (!pv[v].ok) continue;
+                int64_t cv = pv[v].dz;
+                if (cv < c1) { c2 = c1; c1 = cv; }
+                else if (cv < c2) c2 = cv;
+            }
+            regret[t] = c2 - c1;
+        }
+        int pick = 0;
+        for (int t = 1; t < cnt; t++) {
+            if (op == 0) {
+                /* greedy: smallest key; equal keys -> smaller customer id (list is ascending) */
+                if (pack_key_less(bests[t].dz, bests[t].dt, bests[t].flat, bests[pick].dz, bests[pick].dt,
+                                  bests[pick].flat))
+                    pick = t;
+            } else {
+                /* regret-2: largest regret; ties -> smaller customer id */
+                if (regret[t] > regret[pick]) pick = t;
+            }
+        }
+        apply_insert(I, ops, off, list[pick], bests[pick].row, bests[pick].col, tmp_ops, tmp_off);
+        for (int t = pick; t + 1 < cnt; t++) list[t] = list[t + 1];
+        cnt--;
+    }
+    free(pv);
+    free(bests);
+    free(regret);
+    return 0;
+}
+
+static int roulette(const double* w, const int* enabled, int k, double u) {
+    double sum = 0.0;
+    for (int i = 0; i < k; i++)
+        if (enabled[i]) sum += w[i];
+    double target = u * sum, acc = 0.0;
+    int last = -1;
+    for (int i = 0; i < k; i++) {
+        if (!enabled[i]) continue;
+        acc += w[i];
+        last = i;
+        if (target < acc) return i;
+    }
+    return last;
+}
+
+int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t* init_off,
+                    const oracle_alns_params* P, uint64_t seed, int32_t* best_ops, int32_t* best_off,
+                    int32_t* cur_ops_out, int32_t* cur_off_out, oracle_alns_stats* stats,
+                    int32_t* z_trace) {
+    const int n = I->n, m = I->m, two_n = 2 * n;
+    int32_t *S = malloc(sizeof(int32_t) * two_n), *So = malloc(sizeof(int32_t) * (m + 1));
+    int32_t *Sb = malloc(sizeof(int32_t) * two_n), *Sbo = malloc(sizeof(int32_t) * (m + 1));
+    int32_t *W = malloc(sizeof(int32_t) * (two_n + 2)), *Wo = malloc(sizeof(int32_t) * (m + 1));
+    int32_t *tmp = malloc(sizeof(int32_t) * (two_n + 2)), *tmpo = malloc(sizeof(int32_t) * (m + 1));
+    int* perm = malloc(sizeof(int) * (n + 1));
+    int* list = malloc(sizeof(int) * (n + 1));
+    char* rem = calloc((size_t)n + 1, 1);
+    memcpy(S, init_ops, sizeof(int32_t) * two_n);
+    memcpy(So, init_off, sizeof(int32_t) * (m + 1));
+    int32_t z;
+    uint32_t st;
+    oracle_evaluate(I, S, So, 0, &z, &st, NULL);
+    if (st) return -2;                             /* the search starts from a feasible solution */
+    memcpy(Sb, S, sizeof(int32_t) * two_n);
+    memcpy(Sbo, So, sizeof(int32_t) * (m + 1));
+    int32_t zb = z;
+    const uint64_t key = stream_key(seed, STREAM_ALNS);
+    int32_t qmin = P->q_min, qmax = P->q_max;
+    if (qmin <= 0 || qmax <= 0) oracle_q_range(n, &qmin, &qmax);
+    if (qmax > n) qmax = n;
+    if (qmin > qmax) qmin = qmax;
+    /* operators: one destroy operator (random removal), repair 0 greedy, 1 regret-2 */
+    const int ND = 1, NR = 2;
+    double wd[1] = {1.0}, wr[2] = {1.0, 1.0};
+    int sd[1] = {0}, sr[2] = {0, 0}, ad[1] = {0}, ar[2] = {0, 0};
+    int en_d[1] = {1}, en_r[2] = {(P->repair_mask & 1) != 0, (P->repair_mask & 2) != 0};
+    double T = P->T0 * (double)z;                  /* line 3 */
+    const double T_init = T;
+    int stagnation = 0;
+    memset(stats, 0, sizeof(*stats));
+    stats->z_init = z;
+    for (int it = 1; it <= P->iterations; it++) {
+        const uint64_t base = (uint64_t)it << 16;
+        int di = roulette(wd, en_d, ND, rng_unit(oracle_rng(key, base + 0)));   /* line 8 */
+        int rj = roulette(wr, en_r, NR, rng_unit(oracle_rng(key, base + 1)));   /* line 9 */
+        ad[di]++;
+        ar[rj]++;                                                              /* line 10 */
+        int q = qmin + rng_below(oracle_rng(key, base + 2), qmax - qmin + 1);
+        /* random removal: partial Fisher-Yates over customers 1..n */
+        for (int k = 0; k < n; k++) perm[k] = k + 1;
+        for (int k = 0; k < q; k++) {
+            int jj = k + rng_below(oracle_rng(key, base + 16 + (uint64_t)k), n - k);
+            int t = perm[k]; perm[k] = perm[jj]; perm[jj] = t;
+        }
+        memset(rem, 0, (size_t)n + 1);
+        for (int k = 0; k < q; k++) rem[perm[k]] = 1;
+        remove_customers(m, S, So, rem, W, Wo);
+        int cnt = 0;
+        for (int c = 1; c <= n; c++)
+            if (rem[c]) list[cnt++] = c;
+        int32_t zn = INT32_MAX;
+        st = OR_MALFORMED;
+        if (repair(I, rj, W, Wo, list, cnt, tmp, tmpo) == 0)                     /* line 11 */
+            oracle_evaluate(I, W, Wo, 0, &zn, &st, NULL);                        /* line 12 */
+        if (st) {
+            /* repair found no feasible slot, or a route the destroy left over
+             * capacity was never repaired: the candidate is rejected */
+            stats->rejected_infeasible++;
+        } else if (zn < z) {                                                     /* lines 13-21 */
+            memcpy(S, W, sizeof(int32_t) * two_n);
+            memcpy(So, Wo, sizeof(int32_t) * (m + 1));
+            z = zn;
+            sd[di] += P->sigma2;
+            sr[rj] += P->sigma2;
+            stats->improved++;
+            stats->accepted++;
+            if (zn < zb) {
+                memcpy(Sb, W, sizeof(int32_t) * two_n);
+                memcpy(Sbo, Wo, sizeof(int32_t) * (m + 1));
+                zb = zn;
+                sd[di] += P->sigma1 - P->sigma2;
+                sr[rj] += P->sigma1 - P->sigma2;
+                stagnation = 0;
+                stats->new_best++;
+            }
+        } else {
+            double x = -(double)((int64_t)zn - (int64_t)z) / T;
+            double u = rng_unit(oracle_rng(key, base + 3));
+            if (u < oracle_exp(x)) {                                             /* lines 22-25 */
+                memcpy(S, W, sizeof(int32_t) * two_n);
+                memcpy(So, Wo, sizeof(int32_t) * (m + 1));
+                z = zn;
+                sd[di] += P->sigma3;
+                sr[rj] += P->sigma3;
+                stats->accepted++;
+            }
+        }
+        T = P->alpha * T;                                                        /* line 27 */
+        stagnation++;                                                            /* line 28 */
+        if (stagnation >= P->stagnation && T < 0.01 * T_init) {                  /* lines 29-32 + text gate */
+            T = (P->reheat * P->T0) * (double)zb;
+            stagnation = 0;
+            stats->reheats++;
+        }
+        if (it % P->tau == 0) {                                                  /* lines 33-38 */
+            for (int i = 0; i < ND; i++) {
+                double ratio = ad[i] ? (double)sd[i] / (double)ad[i] : 0.0;
+                double w = (1.0 - P->r) * wd[i] + P->r * ratio;
+                wd[i] = w < P->w_min ? P->w_min : w;
+                sd[i] = 0;
+                ad[i] = 0;
+            }
+            for (int i = 0; i < NR; i++) {
+                double ratio = ar[i] ? (double)sr[i] / (double)ar[i] : 0.0;
+                double w = (1.0 - P->r) * wr[i] + P->r * ratio;
+                wr[i] = w < P->w_min ? P->w_min : w;
+                sr[i] = 0;
+                ar[i] = 0;
+            }
+        }
+        if (z_trace) z_trace[it - 1] = z;
+        stats->iterations = it;
+    }
+    memcpy(best_ops, Sb, sizeof(int32_t) * two_n);
+    memcpy(best_off, Sbo, sizeof(int32_t) * (m + 1));
+    if (cur_ops_out) memcpy(cur_ops_out, S, sizeof(int32_t) * two_n);
+    if (cur_off_out) memcpy(cur_off_out, So, sizeof(int32_t) * (m + 1));
+    stats->z_best = zb;
+    stats->z_current = z;
+    stats->T_final = T;
+    stats->w_destroy[0] = wd[0];
+    stats->w_repair[0] = wr[0];
+    stats->w_repair[1] = wr[1];
+    free(S); free(So); free(Sb); free(Sbo); free(W); free(Wo); free(tmp); free(tmpo);
+    free(perm); free(list); free(rem);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* BRKGA decoder (Algorithm 2).  keys[0..2n) are op priorities (op index     */
+/* 2(c-1)+isPickup), keys[2n..2n+m) order the vehicles for tie-breaks.       */
+/* ------------------------------------------------------------------------ */
+static const float* g_keys;
+static int key_cmp(const void* pa, const void* pb) {
+    int a = *(const int*)pa, b = *(const int*)pb;
+    if (g_keys[a] < g_keys[b]) return -1;
+    if (g_keys[a] > g_keys[b]) return 1;
+    return a - b;                                  /* stable: ties by index */
+}
+
+int oracle_decode(const oracle_inst* I, const float* keys, int32_t* ops, int32_t* off, int32_t* z_out,
+                  int32_t* unsched_out, int64_t* fitness_out) {
+    const int n = I->n, m = I->m, two_n = 2 * n;
+    const int full = (I->flags & OR_LOAD_FULL) != 0;
+    int* order = malloc(sizeof(int) * (two_n + 1));
+    int* vorder = malloc(sizeof(int) * (m + 1));
+    int* rank = malloc(sizeof(int) * (m + 1));
+    for (int k = 0; k < two_n; k++) order[k] = k;
+    g_keys = keys;
+    qsort(order, (size_t)two_n, sizeof(int), key_cmp);                           /* line 1 */
+    for (int v = 0; v < m; v++) vorder[v] = v;
+    g_keys = keys + two_n;
+    qsort(vorder, (size_t)m, sizeof(int), key_cmp);
+    for (int r = 0; r < m; r++) rank[vorder[r]] = r;
+    int64_t* t = calloc((size_t)m, sizeof(int64_t));
+    int* loc = calloc((size_t)m, sizeof(int));
+    int* net = calloc((size_t)m, sizeof(int));
+    int* nmin = calloc((size_t)m, sizeof(int));
+    int* nmax = calloc((size_t)m, sizeof(int));
+    int* load = calloc((size_t)m, sizeof(int));
+    int* cnt = calloc((size_t)m, sizeof(int));
+    int* seq = malloc(sizeof(int) * (size_t)m * (two_n + 1));
+    char* sched = calloc((size_t)two_n + 2, 1);
+    int64_t* tdrop = calloc((size_t)n + 1, sizeof(int64_t));
+    int64_t sum_load = 0;
+    int done = 0;
+    for (int pass = 1; pass <= two_n && done < two_n; pass++) {                  /* line 4 */
+        int progress = 0;
+        for (int k = 0; k < two_n; k++) {                                       /* line 5 */
+            int oi = order[k];
+            int o = oi + 2, c = o >> 1, pick = o & 1;
+            if (sched[o]) continue;
+            if (pick && !sched[2 * c]) continue;                                /* line 11: drop first */
+            int best = -1;
+            int64_t best_arr = 0;
+            for (int v = 0; v < m; v++) {
+                int ok;
+                if (!pick) {
+                    if (full) ok = net[v] > -I->Q;                              /* q[v] > 0 */
+                    else {
+                        int nl = load[v] > -(net[v] - 1) ? load[v] : -(net[v] - 1);
+                        int mx = nmax[v] > 0 ? nmax[v] : 0;
+                        ok = nl + mx <= I->Q && sum_load - load[v] + nl <= I->R;
+                    }
+                } else {
+                    if (full) ok = net[v] < 0;                                  /* q[v] < k */
+                    else ok = load[v] + net[v] + 1 <= I->Q;
+                }
+                if (!ok) continue;
+                int64_t arr = t[v] + Dd(I, loc[v], c);                          /* SelectVehicle */
+                if (best < 0 || arr < best_arr || (arr == best_arr && rank[v] < rank[best])) {
+                    best = v;
+                    best_arr = arr;
+                }
+            }
+            if (best < 0) continue;
+            int v = best;
+            if (!pick) {
+                t[v] = best_arr;
+                tdrop[c] = best_arr;
+                net[v]--;
+                if (net[v] < nmin[v]) nmin[v] = net[v];
+                int nl = -nmin[v];
+                sum_load += nl - load[v];
+                load[v] = nl;
+            } else {
+                int64_t ready = tdrop[c] + I->p[c - 1];
+                t[v] = best_arr > ready ? best_arr : ready;
+                net[v]++;
+                if (net[v] > nmax[v]) nmax[v] = net[v];
+            }
+            loc[v] = c;
+            seq[(size_t)v * (two_n + 1) + cnt[v]++] = o;
+            sched[o] = 1;
+            done++;
+            progress = 1;
+        }
+        if (!progress) break;
+    }
+    int64_t z = 0;
+    int w = 0;
+    off[0] = 0;
+    for (int v = 0; v < m; v++) {
+        if (cnt[v] > 0) {
+            int64_t ret = t[v] + Dd(I, loc[v], 0);                              /* line 17 */
+            if (ret > z) z = ret;
+        }
+        for (int k = 0; k < cnt[v]; k++) ops[w++] = seq[(size_t)v * (two_n + 1) + k];
+        off[v + 1] = w;
+    }
+    int uns = two_n - done;
+    *z_out = (int32_t)z;
+    *unsched_out = uns;
+    *fitness_out = z + (int64_t)1000000 * uns;     /* Section 4.4.3 penalty */
+    free(order); free(vorder); free(rank); free(t); free(loc); free(net); free(nmin); free(nmax);
+    free(load); free(cnt); free(seq); free(sched); free(tdrop);
+    return 0;
+}
+
+/* ALNS seed encoding (Section 4.4.5): pi_o = (r-1)/L_v, vehicle key v/m. */
+void oracle_encode(const oracle_inst* I, const int32_t* ops, const int32_t* off, float* keys) {
+    const int n = I->n, m = I->m;
+    for (int k = 0; k < 2 * n; k++) keys[k] = 0.0f;
+    for (int v = 0; v < m; v++) {
+        int L = off[v + 1] - off[v];
+        for (int r = 0; r < L; r++) keys[ops[off[v] + r] - 2] = (float)r / (float)L;
+        keys[2 * n + v] = (float)v / (float)m;
+    }
+}
+
+typedef struct {
+    int64_t f;
+    int idx;
+} fit_t;
+static int fit_cmp(const void* pa, const void* pb) {
+    const fit_t *a = pa, *b = pb;
+    if (a->f != b->f) return a->f < b->f ? -1 : 1;
+    return a->idx - b->idx;
+}
+
+int oracle_brkga_run(const oracle_inst* I, const oracle_brkga_params* P, const int32_t* warm_ops,
+                     const int32_t* warm_off, uint64_t seed, float* final_keys, int64_t* trace,
+                     int32_t* best_ops, int32_t* best_off, int64_t* best_fitness) {
+    const int n = I->n, m = I->m, L = 2 * n + m, pop = P->pop;
+    const uint64_t key = stream_key(seed, STREAM_BRKGA), wkey = stream_key(seed, STREAM_WARM);
+    const uint64_t per = (uint64_t)L + 2;
+    int Ne = (int)floor((double)P->elite_frac * (double)pop);
+    int Nm = (int)floor((double)P->mutant_frac * (double)pop);
+    if (Ne < 1) Ne = 1;
+    if (Ne + Nm > pop) Nm = pop - Ne;
+    int Nc = pop - Ne - Nm;
+    float* cur = malloc(sizeof(float) * (size_t)pop * L);
+    float* nxt = malloc(sizeof(float) * (size_t)pop * L);
+    float* base = malloc(sizeof(float) * L);
+    fit_t* fit = malloc(sizeof(fit_t) * pop);
+    int32_t* dops = malloc(sizeof(int32_t) * 2 * n);
+    int32_t* doff = malloc(sizeof(int32_t) * (m + 1));
+    /* initial population: warm slots then random keys */
+    int warm = warm_ops ? P->warm_slots : 0;
+    if (warm > pop) warm = pop;
+    if (warm_ops) oracle_encode(I, warm_ops, warm_off, base);
+    const float top = 1.0f - 1.0f / 16777216.0f;
+    for (int s = 0; s < pop; s++) {
+        float* kk = cur + (size_t)s * L;
+        if (s < warm) {
+            int var = s % (P->warm_variants > 0 ? P->warm_variants : 1);
+            for (int g = 0; g < L; g++) {
+                if (var == 0) { kk[g] = base[g]; continue; }
+                float u = rng_key(oracle_rng(wkey, (uint64_t)var * L + g));
+                float e = (u * 2.0f - 1.0f) * P->eps;                        /* U(-eps, eps) */
+                float x = base[g] + e;
+                if (x < 0.0f) x = 0.0f;
+                if (x > top) x = top;
+                kk[g] = x;
+            }
+        } else {
+            for (int g = 0; g < L; g++) kk[g] = rng_key(oracle_rng(key, (uint64_t)s * per + 2 + g));
+        }
+    }
+    for (int gen = 0; gen < P->generations; gen++) {
+        for (int s = 0; s < pop; s++) {
+            int32_t z, un;
+            int64_t f;
+            oracle_decode(I, cur + (size_t)s * L, dops, doff, &z, &un, &f);
+            fit[s].f = f;
+            fit[s].idx = s;
+        }
+        qsort(fit, (size_t)pop, sizeof(fit_t), fit_cmp);
+        trace[gen] = fit[0].f;
+        if (gen == P->generations - 1) break;
+        /* elites, then biased-crossover children, then mutants */
+        const uint64_t gbase = (uint64_t)(gen + 1) * (uint64_t)pop;
+        for (int k = 0; k < Ne; k++)
+            memcpy(nxt + (size_t)k * L, cur + (size_t)fit[k].idx * L, sizeof(float) * L);
+        for (int k = 0; k < Nc; k++) {
+            int s = Ne + k;
+            uint64_t cb = (gbase + (uint64_t)s) * per;
+            int e = fit[rng_below(oracle_rng(key, cb + 0), Ne)].idx;
+            int o = fit[Ne + rng_below(oracle_rng(key, cb + 1), pop - Ne)].idx;
+            for (int g = 0; g < L; g++) {
+                float u = rng_key(oracle_rng(key, cb + 2 + g));
+                nxt[(size_t)s * L + g] = u < P->rho ? cur[(size_t)e * L + g] : cur[(size_t)o * L + g];
+            }
+        }
+        for (int k = 0; k < Nm; k++) {
+            int s = Ne + Nc + k;
+            uint64_t cb = (gbase + (uint64_t)s) * per;
+            for (int g = 0; g < L; g++) nxt[(size_t)s * L + g] = rng_key(oracle_rng(key, cb + 2 + g));
+        }
+        float* t = cur; cur = nxt; nxt = t;
+    }
+    int32_t z, un;
+    int64_t f;
+    oracle_decode(I, cur + (size_t)fit[0].idx * L, best_ops, best_off, &z, &un, &f);
+    *best_fitness = f;
+    if (final_keys) memcpy(final_keys, cur, sizeof(float) * (size_t)pop * L);
+    free(cur); free(nxt); free(base); free(fit); free(dops); free(doff);
+    return 0;
+}
