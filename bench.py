@@ -1,0 +1,285 @@
+#!/usr/bin/env python3
+"""Benchmark of the VRP-RPD hot path on GB300.
+
+Workload (one rank): the n = 1000 instance family -- m = 20 vehicles, pool
+R = 100, capacity Q = 10, 1R20 processing times p = round(U_int[1,20] * mean
+depot distance / 10), mixed uniform/clustered integer coordinates -- with a
+batch of precedence-consistent candidates (every op gets simulated).  A step
+evaluates the whole batch (4.2 GB of candidates, larger than L2, so no flush
+is needed between steps).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+host cores instead (the slow baseline the ratio is taken against).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+N_CUST, M_VEH, R_POOL, Q_CAP = 1000, 20, 100, 10
+BASE_CANDS = 16384          # generated on the host, tiled on the device
+TILE = 32                   # batch = BASE_CANDS * TILE = 524288 candidates
+METRIC = "makespan evals/s and ALNS iters/s at n=1000; batched vs plain GPU, equal makespan"
+UNIT = "evals/s"
+WORKLOAD = ("n=1000 m=20 R=100 Q=10 1R20 mixed uniform/clustered coords; "
+            "524288 precedence-consistent candidates per step (4.24 GB, > L2)")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu_index = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu_index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_inputs(seed):
+    w = workloads.make_instance(N_CUST, M_VEH, R_POOL, Q_CAP, "1R20", "mixed", seed=seed)
+    ops, off = workloads.precedence_candidates(N_CUST, M_VEH, BASE_CANDS, seed=seed)
+    return w, ops, off
+
+
+def cpu_baseline(w, ops, off, budget_s=12.0):
+    """The oracle as it stands, all host cores, on a bounded sample."""
+    import oracle
+    oi = oracle.OracleInstance.from_workload(w)
+    cores = os.cpu_count() or 1
+    probe = 64
+    t0 = time.perf_counter()
+    oracle.evaluate_batch(oi, ops[:probe], off[:probe], threads=1)
+    per = (time.perf_counter() - t0) / probe
+    count = int(min(len(ops), max(cores * 8, budget_s * cores / max(per, 1e-9) * 0.5)))
+    t0 = time.perf_counter()
+    oracle.evaluate_batch(oi, ops[:count], off[:count], threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": count / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{count} candidates of the same workload, one C thread per core, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w, ops, off = make_inputs(seed=0)
+    samples = []
+    for _ in range(args.warmup):
+        cpu_baseline(w, ops, off, budget_s=2.0)
+    t_all = time.perf_counter()
+    for _ in range(args.steps):
+        samples.append(cpu_baseline(w, ops, off, budget_s=max(2.0, 60.0 / max(args.steps, 1))))
+    total = time.perf_counter() - t_all
+    value = statistics.median(s["value"] for s in samples)
+    cb = dict(samples[-1])
+    cb["value"] = value
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / max(args.steps, 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "sampled subset, CPU"},
+        "cpu_baseline": cb, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                    "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2602_23685_gb300 as vrp
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w, ops_h, off_h = make_inputs(seed=rank)
+    inst = vrp.Instance.from_workload(w)
+    base_ops = torch.from_numpy(ops_h).cuda()
+    base_off = torch.from_numpy(off_h).cuda()
+    ops = base_ops.repeat(TILE, 1).contiguous()
+    off = base_off.repeat(TILE, 1).contiguous()
+    B = ops.shape[0]
+    z = torch.empty(B, dtype=torch.int32, device="cuda")
+    st = torch.empty(B, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    tuned = vrp.autotune(inst, ops[: BASE_CANDS * 4], off[: BASE_CANDS * 4])
+    for _ in range(args.warmup):
+        vrp.evaluate(inst, ops, off, z, st)
+    vrp.sync(inst)
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    with ClockSampler(local) as clk:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            starts[i].record(stream)
+            vrp.evaluate(inst, ops, off, z, st)
+            ends[i].record(stream)
+        t1.record(stream)
+        barrier()
+    vrp.sync(inst)
+    total_ms = t0.elapsed_time(t1)
+    kernel_ms = statistics.mean(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if dist is not None:
+        tt = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    value = B * args.steps * world / (total_ms / 1000.0)
+
+    # correctness of the timed output: first tile against the plain GPU form, and
+    # every tiled copy identical to the first
+    zc, sc = z.view(TILE, BASE_CANDS), st.view(TILE, BASE_CANDS)
+    assert bool((zc == zc[0]).all()) and bool((sc == sc[0]).all())
+
+    # plain per-instance GPU form on the same batch, fewer steps
+    zp = torch.empty_like(z)
+    sp = torch.empty_like(st)
+    vrp.evaluate_plain(inst, ops, off, zp, sp)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain_steps = 3
+    e0.record(stream)
+    for _ in range(plain_steps):
+        vrp.evaluate_plain(inst, ops, off, zp, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_value = B * plain_steps / (e0.elapsed_time(e1) / 1000.0)
+    equal = bool(torch.equal(zp, z)) and bool(torch.equal(sp, st))
+
+    # end to end: pinned host candidates -> device -> evaluate -> host results
+    e2e_steps = max(3, min(10, args.steps))
+    ops_pin = ops.cpu().pin_memory()
+    off_pin = off.cpu().pin_memory()
+    z_h = torch.empty(B, dtype=torch.int32).pin_memory()
+    st_h = torch.empty(B, dtype=torch.int32).pin_memory()
+    vrp.evaluate_host(inst, ops_pin, off_pin, z_h, st_h)
+    barrier()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        vrp.evaluate_host(inst, ops_pin, off_pin, z_h, st_h)
+    barrier()
+    e2e_s = time.perf_counter() - t
+    e2e_value = B * e2e_steps * world / e2e_s
+    assert torch.equal(z_h, z.cpu())
+
+    pk = peaks()
+    bytes_per_eval = 4 * (2 * N_CUST + M_VEH + 1) + 8
+    achieved = B * bytes_per_eval / (kernel_ms / 1000.0) / 1e9
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": "measured" if pk else "fallback",
+                "bytes_per_unit": bytes_per_eval, "units_per_launch": B, "traffic": None,
+                "kernel": "eval_tiles_kernel", "kernel_ms": kernel_ms}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "batch": B, "l2": "inputs larger than L2 (no flush)",
+                       "eval_config": tuned},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(ops.numel() * 4 + off.numel() * 4),
+                    "d2h_bytes_per_step": int(B * 8)},
+            "gpu_launches": args.steps,
+            "roofline": roofline,
+            "clocks": clk.summary(),
+            "plain_gpu": {"value": plain_value, "unit": UNIT, "equal_makespan": equal,
+                          "speedup_batched_vs_plain": value / world / plain_value},
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w, ops_h, off_h)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,243 @@
+"""Python binding of libvrprpd (argument marshalling only).
+
+Every computation runs in the CUDA library declared in include/vrprpd.h; this
+module passes device pointers (from torch tensors), sizes and the current
+torch stream through ctypes.  There is no fallback: if the library or a CUDA
+device is missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from .build import LIB, build as _build
+
+__all__ = ["lib", "Instance", "evaluate", "evaluate_host", "evaluate_plain", "autotune",
+           "set_eval_config", "get_eval_config", "sync", "VrpError",
+           "CYCLE", "VEH_CAP", "POOL", "MALFORMED", "DIST_MODES"]
+
+CYCLE, VEH_CAP, POOL, MALFORMED = 1, 2, 4, 8
+LOAD_MIN, LOAD_FULL = 0, 1
+DIST_MODES = {"auto": 0, "smem32": 1, "smem16": 2, "global16": 3, "global32": 4, "coords": 5}
+_DIST_NAMES = {v: k for k, v in DIST_MODES.items()}
+INT32_MAX = 2**31 - 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class VrpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libvrprpd error {code}: {msg}")
+        self.code = code
+
+
+class Batch(C.Structure):
+    _fields_ = [("num", C.c_int32), ("ops", C.c_void_p), ("off", C.c_void_p)]
+
+
+class EvalConfig(C.Structure):
+    _fields_ = [("dist_mode", C.c_int32), ("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32)]
+
+
+def lib():
+    """Load (building first if needed) the in-tree libvrprpd.so."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = LIB if os.path.exists(LIB) else _build()
+            L = C.CDLL(path)
+            vp, i32, u32 = C.c_void_p, C.c_int32, C.c_uint32
+            L.vrprpd_instance_create.argtypes = [vp, vp, i32, i32, i32, i32, u32, C.POINTER(vp)]
+            L.vrprpd_instance_create_dist.argtypes = [vp, vp, i32, i32, i32, i32, u32, C.POINTER(vp)]
+            L.vrprpd_instance_destroy.argtypes = [vp]
+            L.vrprpd_instance_destroy.restype = None
+            L.vrprpd_instance_get_dist.argtypes = [vp, vp]
+            for name in ("vrprpd_evaluate", "vrprpd_evaluate_host", "vrprpd_evaluate_plain"):
+                getattr(L, name).argtypes = [vp, C.POINTER(Batch), vp, vp, vp]
+            L.vrprpd_sync.argtypes = [vp, vp]
+            L.vrprpd_eval_set_config.argtypes = [vp, C.POINTER(EvalConfig)]
+            L.vrprpd_eval_get_config.argtypes = [vp, C.POINTER(EvalConfig)]
+            L.vrprpd_autotune.argtypes = [vp, C.POINTER(Batch), vp, C.POINTER(EvalConfig)]
+            L.vrprpd_last_error.restype = C.c_char_p
+            _register_extra(L)
+            _lib = L
+    return _lib
+
+
+def _register_extra(L):
+    """Signatures of the search entry points (declared in include/vrprpd.h)."""
+    from . import _search_sig
+    _search_sig.register(L)
+
+
+def _check(rc):
+    if rc != 0:
+        raise VrpError(rc, lib().vrprpd_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libvrprpd needs a CUDA device; none is available")
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev_i32(t, name, shape=None):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.int32:
+        raise TypeError(f"{name} must be a CUDA int32 tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t
+
+
+class Instance:
+    """A VRP-RPD instance resident on the current CUDA device."""
+
+    def __init__(self, m, R, Q, p, coords=None, d=None, load_full=False):
+        L = lib()
+        _torch()
+        p = np.ascontiguousarray(p, dtype=np.int32)
+        self.n = int(p.shape[0])
+        self.m, self.R, self.Q = int(m), int(R), int(Q)
+        self.load_full = bool(load_full)
+        flags = LOAD_FULL if load_full else LOAD_MIN
+        h = C.c_void_p()
+        if coords is not None:
+            coords = np.ascontiguousarray(coords, dtype=np.int32)
+            if coords.shape != (self.n + 1, 2):
+                raise ValueError("coords must be (n+1) x 2")
+            _check(L.vrprpd_instance_create(coords.ctypes.data, p.ctypes.data, self.n, self.m,
+                                            self.R, self.Q, flags, C.byref(h)))
+        elif d is not None:
+            d = np.ascontiguousarray(d, dtype=np.int32)
+            if d.shape != (self.n + 1, self.n + 1):
+                raise ValueError("d must be (n+1) x (n+1)")
+            _check(L.vrprpd_instance_create_dist(d.ctypes.data, p.ctypes.data, self.n, self.m,
+                                                 self.R, self.Q, flags, C.byref(h)))
+        else:
+            raise ValueError("need coords or d")
+        self._h = h
+        self.p = p
+        self.coords = coords
+
+    @classmethod
+    def from_workload(cls, w, load_full=False):
+        return cls(w.m, w.R, w.Q, w.p, coords=w.coords, load_full=load_full)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("instance closed")
+        return self._h
+
+    def dist(self):
+        d = np.empty((self.n + 1, self.n + 1), np.int32)
+        _check(lib().vrprpd_instance_get_dist(self.handle, d.ctypes.data))
+        return d
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().vrprpd_instance_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _batch(inst, ops, off):
+    B = ops.shape[0]
+    _dev_i32(ops, "ops", (B, 2 * inst.n))
+    _dev_i32(off, "off", (B, inst.m + 1))
+    return Batch(B, ops.data_ptr(), off.data_ptr())
+
+
+def evaluate(inst, ops, off, z=None, st=None, stream=None):
+    """Batched evaluation on device tensors; returns (makespan int32, status int32 view)."""
+    torch = _torch()
+    b = _batch(inst, ops, off)
+    if z is None:
+        z = torch.empty(b.num, dtype=torch.int32, device=ops.device)
+    if st is None:
+        st = torch.empty(b.num, dtype=torch.int32, device=ops.device)
+    _check(lib().vrprpd_evaluate(inst.handle, C.byref(b), z.data_ptr(), st.data_ptr(), _stream_ptr(stream)))
+    return z, st
+
+
+def evaluate_plain(inst, ops, off, z=None, st=None, stream=None):
+    """The plain one-thread-per-candidate GPU form (comparison baseline)."""
+    torch = _torch()
+    b = _batch(inst, ops, off)
+    if z is None:
+        z = torch.empty(b.num, dtype=torch.int32, device=ops.device)
+    if st is None:
+        st = torch.empty(b.num, dtype=torch.int32, device=ops.device)
+    _check(lib().vrprpd_evaluate_plain(inst.handle, C.byref(b), z.data_ptr(), st.data_ptr(),
+                                       _stream_ptr(stream)))
+    return z, st
+
+
+def evaluate_host(inst, ops, off, z=None, st=None, stream=None):
+    """Evaluation from host memory (numpy arrays or pinned CPU tensors): copies in,
+    evaluates, copies out, returns when done."""
+    def host_ptr(a, name):
+        if hasattr(a, "data_ptr"):
+            if a.device.type != "cpu" or not a.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous CPU tensor")
+            return a.data_ptr()
+        if not (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype == np.int32):
+            raise TypeError(f"{name} must be a contiguous int32 array")
+        return a.ctypes.data
+    B = ops.shape[0]
+    if tuple(ops.shape) != (B, 2 * inst.n) or tuple(off.shape) != (B, inst.m + 1):
+        raise ValueError("bad ops/off shape")
+    if z is None:
+        z = np.empty(B, np.int32)
+    if st is None:
+        st = np.empty(B, np.uint32)
+    b = Batch(B, host_ptr(ops, "ops"), host_ptr(off, "off"))
+    _check(lib().vrprpd_evaluate_host(inst.handle, C.byref(b), host_ptr(z, "z") if hasattr(z, "data_ptr")
+                                      else z.ctypes.data,
+                                      st.data_ptr() if hasattr(st, "data_ptr") else st.ctypes.data,
+                                      _stream_ptr(stream)))
+    return z, st
+
+
+def sync(inst, stream=None):
+    _check(lib().vrprpd_sync(inst.handle, _stream_ptr(stream)))
+
+
+def set_eval_config(inst, dist_mode="auto", warps_per_block=0, blocks_per_sm=0):
+    cfg = EvalConfig(DIST_MODES[dist_mode] if isinstance(dist_mode, str) else int(dist_mode),
+                     warps_per_block, blocks_per_sm)
+    _check(lib().vrprpd_eval_set_config(inst.handle, C.byref(cfg)))
+
+
+def get_eval_config(inst):
+    cfg = EvalConfig()
+    _check(lib().vrprpd_eval_get_config(inst.handle, C.byref(cfg)))
+    return {"dist_mode": _DIST_NAMES[cfg.dist_mode], "warps_per_block": cfg.warps_per_block,
+            "blocks_per_sm": cfg.blocks_per_sm}
+
+
+def autotune(inst, ops, off, stream=None):
+    b = _batch(inst, ops, off)
+    cfg = EvalConfig()
+    _check(lib().vrprpd_autotune(inst.handle, C.byref(b), _stream_ptr(stream), C.byref(cfg)))
+    return {"dist_mode": _DIST_NAMES[cfg.dist_mode], "warps_per_block": cfg.warps_per_block,
+            "blocks_per_sm": cfg.blocks_per_sm}

@@ -1,0 +1,709 @@
+// Batched candidate evaluation (the repair's timing evaluation of Section
+// 4.2.3 and the decoder's schedule simulation of Section 4.4.2, done exactly
+// on the semantics of Section 3.1, Eqs. 7-23).
+//
+// Batched form: a persistent launch; every warp owns a tile of k = 32/m
+// candidates (one lane per route).  Per tile:
+//   1. a TMA bulk copy stages the tile's op arrays in shared memory (plain
+//      loads fill the unaligned head and tail);
+//   2. a pre-pass over all ops, 32 at a time, validates op codes (range and
+//      duplicates) and replaces each op in place by a packed word
+//      (travel-in time << 12 | op code), the travel-in being d(previous stop,
+//      this stop);
+//   3. the route walk: each lane advances its route one op per step --
+//      a drop publishes its pickup-ready time T_drop + p_c to shared memory,
+//      a pickup waits until that time is published (cross-vehicle precedence,
+//      Eq. 9) and then leaves at max(arrival, ready) (Eqs. 8, 10).  A group
+//      that makes no progress in a step while unfinished is a precedence
+//      cycle.  Each lane also tracks its route's stock prefix (Eqs. 13-18);
+//   4. per-candidate reductions: makespan = max return time (Eqs. 21-22),
+//      vehicle capacity, depot pool.
+// Plain form: one thread per candidate, Kahn order over routes, scratch in
+// global memory, distances from global memory.
+#include <algorithm>
+#include <cstring>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace vrp {
+
+struct EvalArgs {
+    const int32_t* ops;
+    const int32_t* off;
+    int32_t* z;
+    uint32_t* st;
+    const int32_t* d32;
+    const uint16_t* d16;
+    const int32_t* coords;
+    const int32_t* p;
+    int* err;
+    long long num;
+    int n, m, R, Q;
+    int load_full;
+    int k;            // candidates per warp tile
+    int N;            // n + 1
+    // shared-memory layout, in 32-bit words
+    int shared_words; // per-block instance data (distances/coords + p)
+    int dist_words;
+    int a_words, ready_words, seen_words, start_words, off_words, valid_words, warp_words;
+    int sw;           // seen words per candidate
+};
+
+template <int DM>
+__device__ __forceinline__ int dist(const EvalArgs& a, const int32_t* sh, int i, int j) {
+    if constexpr (DM == VRPRPD_DIST_SMEM32) {
+        return sh[i * a.N + j];
+    } else if constexpr (DM == VRPRPD_DIST_SMEM16) {
+        return reinterpret_cast<const uint16_t*>(sh)[i * a.N + j];
+    } else if constexpr (DM == VRPRPD_DIST_GLOBAL16) {
+        return __ldg(a.d16 + i * a.N + j);
+    } else if constexpr (DM == VRPRPD_DIST_GLOBAL32) {
+        return __ldg(a.d32 + i * a.N + j);
+    } else {
+        return euc2d_small(sh[2 * i], sh[2 * i + 1], sh[2 * j], sh[2 * j + 1]);
+    }
+}
+
+template <int DM>
+__global__ void __launch_bounds__(1024) eval_tiles_kernel(EvalArgs a) {
+    extern __shared__ __align__(16) int32_t smem[];
+    __shared__ __align__(8) uint64_t block_bar;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int n = a.n, m = a.m, two_n = 2 * n, k = a.k;
+
+    // ---- block-wide staging of the instance (TMA bulk copies) ----
+    int32_t* sh = smem;                        // distances or coordinates
+    int32_t* sp = smem + a.dist_words;         // p[0..n]
+    if (threadIdx.x == 0) {
+        mbar_init(&block_bar, 1);
+        unsigned dist_bytes = 0;
+        if constexpr (DM == VRPRPD_DIST_SMEM32) dist_bytes = ((a.N * a.N * 4) + 15) & ~15;
+        if constexpr (DM == VRPRPD_DIST_SMEM16) dist_bytes = ((a.N * a.N * 2) + 15) & ~15;
+        if constexpr (DM == VRPRPD_DIST_COORDS) dist_bytes = ((a.N * 8) + 15) & ~15;
+        unsigned p_bytes = ((a.N * 4) + 15) & ~15;
+        mbar_arrive_expect_tx(&block_bar, dist_bytes + p_bytes);
+        if constexpr (DM == VRPRPD_DIST_SMEM32) tma_bulk_g2s(sh, a.d32, dist_bytes, &block_bar);
+        if constexpr (DM == VRPRPD_DIST_SMEM16) tma_bulk_g2s(sh, a.d16, dist_bytes, &block_bar);
+        if constexpr (DM == VRPRPD_DIST_COORDS) tma_bulk_g2s(sh, a.coords, dist_bytes, &block_bar);
+        tma_bulk_g2s(sp, a.p, p_bytes, &block_bar);
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&block_bar, 0)) {
+        if (threadIdx.x == 0) atomicExch(a.err, DEV_TIMEOUT_TMA);
+        mbar_wait_bounded(&block_bar, 0);      // give copies in flight one more bounded chance
+        return;
+    }
+
+    // ---- per-warp regions ----
+    int32_t* W = smem + a.shared_words + warp * a.warp_words;
+    int32_t* A = W;
+    int32_t* ready = A + a.a_words;
+    uint32_t* seen = reinterpret_cast<uint32_t*>(ready + a.ready_words);
+    uint32_t* starts = seen + a.seen_words;
+    int32_t* soff = reinterpret_cast<int32_t*>(starts + a.start_words);
+    int32_t* valid = soff + a.off_words;
+    int32_t* red = valid + a.valid_words;      // 96 words
+    uint64_t* bar = reinterpret_cast<uint64_t*>(red + 96);
+    if (lane == 0) mbar_init(bar, 1);
+    __syncwarp();
+
+    const long long ntiles = (a.num + k - 1) / k;
+    const long long gw = static_cast<long long>(blockIdx.x) * nwarps + warp;
+    const long long nw = static_cast<long long>(gridDim.x) * nwarps;
+    const int grp = lane / m, v = lane - grp * m;
+    const unsigned gmask = (grp < k) ? (m == 32 ? FULL_MASK : (((1u << m) - 1u) << (grp * m))) : 0u;
+    unsigned phase = 0;
+
+    for (long long t = gw; t < ntiles; t += nw) {
+        const long long first = t * k;
+        const int kt = static_cast<int>(min(static_cast<long long>(k), a.num - first));
+        const int elems = kt * two_n;
+        const int32_t* src = a.ops + first * two_n;
+
+        // ---- 1. stage ops: aligned interior by TMA, head/tail by plain loads ----
+        const uintptr_t s0 = reinterpret_cast<uintptr_t>(src);
+        const uintptr_t s1 = s0 + static_cast<uintptr_t>(elems) * 4u;
+        const uintptr_t i0 = (s0 + 15u) & ~static_cast<uintptr_t>(15u);
+        const uintptr_t i1 = s1 & ~static_cast<uintptr_t>(15u);
+        const bool bulk = i1 > i0;
+        const int k0 = bulk ? static_cast<int>((i0 - s0) >> 2) : elems;
+        const int ke = bulk ? static_cast<int>((i1 - s0) >> 2) : elems;
+        const int shift = (4 - (k0 & 3)) & 3;
+        int32_t* Ab = A + shift;
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0 && bulk) {
+            mbar_arrive_expect_tx(bar, static_cast<unsigned>(i1 - i0));
+            tma_bulk_g2s(Ab + k0, reinterpret_cast<const void*>(i0), static_cast<unsigned>(i1 - i0), bar);
+        }
+        for (int e = lane; e < k0; e += 32) Ab[e] = __ldg(src + e);
+        for (int e = ke + lane; e < elems; e += 32) Ab[e] = __ldg(src + e);
+        for (int i = lane; i < kt * (m + 1); i += 32) soff[i] = __ldg(a.off + first * (m + 1) + i);
+        for (int i = lane; i < kt; i += 32) valid[i] = 1;
+        for (int i = lane; i < kt * a.sw; i += 32) seen[i] = 0u;
+        for (int i = lane; i < (elems + 31) / 32; i += 32) starts[i] = 0u;
+        for (int i = lane; i < kt * (n + 1); i += 32) ready[i] = UNRESOLVED;
+        __syncwarp();
+        // offsets: off[0] = 0, off[m] = 2n, non-decreasing
+        for (int i = lane; i < kt * (m + 1); i += 32) {
+            const int g = i / (m + 1), vv = i - g * (m + 1);
+            const int val = soff[i];
+            bool bad = val < 0 || val > two_n || (vv == 0 && val != 0) || (vv == m && val != two_n) ||
+                       (vv < m && val > soff[i + 1]);
+            if (bad) atomicAnd(&valid[g], 0);
+        }
+        __syncwarp();
+        for (int i = lane; i < kt * m; i += 32) {
+            const int g = i / m, vv = i - g * m;
+            if (!valid[g]) continue;
+            const int o0 = soff[g * (m + 1) + vv], o1 = soff[g * (m + 1) + vv + 1];
+            if (o0 < o1) {
+                const int e = g * two_n + o0;
+                atomicOr(&starts[e >> 5], 1u << (e & 31));
+            }
+        }
+        if (bulk) {
+            if (!mbar_wait_bounded(bar, phase)) {
+                if (lane == 0) atomicExch(a.err, DEV_TIMEOUT_TMA);
+                mbar_wait_bounded(bar, phase);
+                return;
+            }
+            phase ^= 1u;
+        }
+        __syncwarp();
+
+        // ---- 2. pre-pass: validate and pack (travel-in << 12 | op) in place ----
+        int carry = 0;
+        for (int base = 0; base < elems; base += 32) {
+            const int e = base + lane;
+            const bool in = e < elems;
+            const int raw = in ? Ab[e] : 2;
+            int prev = __shfl_up_sync(FULL_MASK, raw, 1);
+            if (lane == 0) prev = carry;
+            carry = __shfl_sync(FULL_MASK, raw, 31);
+            const bool ok = raw >= 2 && raw <= two_n + 1;
+            const int g = e / two_n;
+            if (in) {
+                if (!ok) {
+                    atomicAnd(&valid[g], 0);
+                } else {
+                    const unsigned bit = 1u << (raw & 31);
+                    const unsigned old = atomicOr(&seen[g * a.sw + (raw >> 5)], bit);
+                    if (old & bit) atomicAnd(&valid[g], 0);
+                }
+            }
+            const bool is_start = in && ((starts[e >> 5] >> (e & 31)) & 1u);
+            const int c = ok ? (raw >> 1) : 0;
+            const int pc = (is_start || !(prev >= 2 && prev <= two_n + 1)) ? 0 : (prev >> 1);
+            const int dd = in ? dist<DM>(a, sh, pc, c) : 0;
+            __syncwarp();
+            if (in) Ab[e] = (dd << PACK_SHIFT) | (ok ? raw : 2);
+        }
+        __syncwarp();
+
+        // ---- 3. route walk ----
+        const bool mine = grp < kt && valid[grp] != 0;
+        int pos = 0, end = 0, start = 0;
+        if (mine) {
+            start = pos = soff[grp * (m + 1) + v];
+            end = soff[grp * (m + 1) + v + 1];
+        }
+        const int ebase = (grp < k ? grp : 0) * two_n;
+        int32_t* rdy = ready + (grp < k ? grp : 0) * (n + 1);
+        int dep = 0, s = 0, smin = 0, smax = 0, last = 0;
+        bool walking = mine && pos < end, cyc = false;
+        while (__any_sync(FULL_MASK, walking)) {
+            int w = 0, r = 0, c = 0;
+            bool go = false, pick = false;
+            if (walking) {
+                w = Ab[ebase + pos];
+                const int o = w & PACK_MASK;
+                c = o >> 1;
+                pick = (o & 1) != 0;
+                if (pick) r = rdy[c];
+                go = !pick || r >= 0;
+            }
+            __syncwarp();
+            if (go) {
+                const int arr = dep + (w >> PACK_SHIFT);
+                if (pick) {
+                    dep = max(arr, r);
+                    ++s;
+                    smax = max(smax, s);
+                } else {
+                    dep = arr;
+                    rdy[c] = arr + sp[c];
+                    --s;
+                    smin = min(smin, s);
+                }
+                last = c;
+                ++pos;
+            }
+            __syncwarp();
+            const unsigned prog = __ballot_sync(FULL_MASK, go);
+            if (walking) {
+                if (pos >= end) walking = false;
+                else if ((prog & gmask) == 0u) { walking = false; cyc = true; }
+            }
+        }
+        if (cyc)                                   // finish the stock prefix of a blocked route
+            for (; pos < end; ++pos) {
+                const int o = Ab[ebase + pos] & PACK_MASK;
+                if (o & 1) { ++s; smax = max(smax, s); } else { --s; smin = min(smin, s); }
+            }
+
+        // ---- 4. per-candidate reduction ----
+        int ret = 0, flags = 0, pool = 0;
+        if (mine) {
+            if (!cyc && end > start) ret = dep + dist<DM>(a, sh, last, 0);
+            if (a.load_full) {
+                flags = (smin < -a.Q || smax > 0) ? VRPRPD_VEH_CAP : 0;
+                pool = a.Q;
+            } else {
+                flags = (-smin + smax > a.Q) ? VRPRPD_VEH_CAP : 0;
+                pool = -smin;
+            }
+            if (cyc) flags |= VRPRPD_CYCLE;
+        }
+        red[lane] = ret;
+        red[32 + lane] = flags;
+        red[64 + lane] = pool;
+        __syncwarp();
+        if (grp < kt && v == 0) {
+            int z = 0, f = 0;
+            long long pl = 0;
+            for (int j = 0; j < m; ++j) {
+                z = max(z, red[grp * m + j]);
+                f |= red[32 + grp * m + j];
+                pl += red[64 + grp * m + j];
+            }
+            if (pl > a.R) f |= VRPRPD_POOL;
+            if (f & VRPRPD_CYCLE) z = 0x7fffffff;
+            if (!valid[grp]) { z = 0x7fffffff; f = VRPRPD_MALFORMED; }
+            a.z[first + grp] = z;
+            a.st[first + grp] = static_cast<uint32_t>(f);
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Plain form: thread per candidate, global scratch, Kahn order.
+// scratch per thread: ready[n+1], pos[m], dep[m], loc[m], seen[(2n+2+31)/32]
+// ---------------------------------------------------------------------------
+__global__ void eval_plain_kernel(const int32_t* __restrict__ ops, const int32_t* __restrict__ off,
+                                  long long num, int n, int m, int R, int Q, int load_full,
+                                  const int32_t* __restrict__ d, const int32_t* __restrict__ p,
+                                  int32_t* __restrict__ zout, uint32_t* __restrict__ stout,
+                                  int32_t* __restrict__ scratch, int scratch_words) {
+    const long long tid = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x;
+    const long long nthreads = static_cast<long long>(gridDim.x) * blockDim.x;
+    const int N = n + 1, two_n = 2 * n, sw = (two_n + 2 + 31) / 32;
+    int32_t* ready = scratch + tid * static_cast<long long>(scratch_words);
+    int32_t* pos = ready + (n + 1);
+    int32_t* dep = pos + m;
+    int32_t* loc = dep + m;
+    uint32_t* seen = reinterpret_cast<uint32_t*>(loc + m);
+    for (long long i = tid; i < num; i += nthreads) {
+        const int32_t* o = ops + i * two_n;
+        const int32_t* f = off + i * (m + 1);
+        uint32_t st = 0;
+        if (f[0] != 0 || f[m] != two_n) st = VRPRPD_MALFORMED;
+        for (int v = 0; v < m && !st; ++v)
+            if (f[v + 1] < f[v]) st = VRPRPD_MALFORMED;
+        for (int w = 0; w < sw; ++w) seen[w] = 0u;
+        for (int k2 = 0; k2 < two_n && !st; ++k2) {
+            const int op = o[k2];
+            if (op < 2 || op > two_n + 1) { st = VRPRPD_MALFORMED; break; }
+            const uint32_t bit = 1u << (op & 31);
+            if (seen[op >> 5] & bit) { st = VRPRPD_MALFORMED; break; }
+            seen[op >> 5] |= bit;
+        }
+        if (st) { zout[i] = 0x7fffffff; stout[i] = st; continue; }
+        for (int c = 0; c <= n; ++c) ready[c] = UNRESOLVED;
+        for (int v = 0; v < m; ++v) { pos[v] = f[v]; dep[v] = 0; loc[v] = 0; }
+        bool progress = true;
+        while (progress) {
+            progress = false;
+            for (int v = 0; v < m; ++v) {
+                while (pos[v] < f[v + 1]) {
+                    const int op = o[pos[v]], c = op >> 1;
+                    const bool pick = op & 1;
+                    if (pick && ready[c] < 0) break;
+                    const int arr = dep[v] + d[static_cast<long long>(loc[v]) * N + c];
+                    if (!pick) { dep[v] = arr; ready[c] = arr + p[c]; }
+                    else dep[v] = max(arr, ready[c]);
+                    loc[v] = c;
+                    ++pos[v];
+                    progress = true;
+                }
+            }
+        }
+        int z = 0;
+        long long pool = 0;
+        for (int v = 0; v < m; ++v) {
+            if (pos[v] < f[v + 1]) st |= VRPRPD_CYCLE;
+            if (f[v + 1] > f[v]) z = max(z, dep[v] + d[static_cast<long long>(loc[v]) * N]);
+            int s = 0, smin = 0, smax = 0;
+            for (int k2 = f[v]; k2 < f[v + 1]; ++k2) {
+                s += (o[k2] & 1) ? 1 : -1;
+                smin = min(smin, s);
+                smax = max(smax, s);
+            }
+            if (load_full) {
+                if (smin < -Q || smax > 0) st |= VRPRPD_VEH_CAP;
+                pool += Q;
+            } else {
+                if (-smin + smax > Q) st |= VRPRPD_VEH_CAP;
+                pool += -smin;
+            }
+        }
+        if (pool > R) st |= VRPRPD_POOL;
+        if (st & VRPRPD_CYCLE) z = 0x7fffffff;
+        zout[i] = z;
+        stout[i] = st;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static int round4(long long w) { return static_cast<int>((w + 3) & ~3ll); }
+
+struct Plan {
+    int dm = 0, warps = 0, blocks = 0;
+    size_t smem = 0;
+    EvalArgs args{};
+};
+
+static bool coords_small(const vrprpd_instance* I) {
+    if (!I->has_coords) return false;
+    int minx = I->h_coords[0], maxx = minx, miny = I->h_coords[1], maxy = miny;
+    for (int i = 0; i <= I->n; ++i) {
+        minx = std::min(minx, I->h_coords[2 * i]);
+        maxx = std::max(maxx, I->h_coords[2 * i]);
+        miny = std::min(miny, I->h_coords[2 * i + 1]);
+        maxy = std::max(maxy, I->h_coords[2 * i + 1]);
+    }
+    long long dx = maxx - minx, dy = maxy - miny;
+    return dx * dx + dy * dy < (1ll << 24);
+}
+
+bool batched_supported(const vrprpd_instance* I) {
+    return I->m <= 32 && 2 * I->n + 1 < (1 << PACK_SHIFT) && I->maxd < (1 << 19);
+}
+
+static bool dist_mode_available(const vrprpd_instance* I, int dm) {
+    switch (dm) {
+        case VRPRPD_DIST_SMEM32: return true;
+        case VRPRPD_DIST_SMEM16: return I->has_d16;
+        case VRPRPD_DIST_GLOBAL16: return I->has_d16;
+        case VRPRPD_DIST_GLOBAL32: return true;
+        case VRPRPD_DIST_COORDS: return coords_small(I);
+    }
+    return false;
+}
+
+// Fill the layout for (dist mode, warps per block); false if it does not fit.
+static bool make_plan(const vrprpd_instance* I, int dm, int warps, int blocks_per_sm, long long num, Plan* P) {
+    EvalArgs& a = P->args;
+    a = EvalArgs{};
+    a.n = I->n;
+    a.m = I->m;
+    a.R = I->R;
+    a.Q = I->Q;
+    a.N = I->n + 1;
+    a.load_full = (I->flags & VRPRPD_LOAD_FULL) != 0;
+    a.k = 32 / I->m;
+    a.d32 = I->d32;
+    a.d16 = I->d16;
+    a.coords = I->coords;
+    a.p = I->p;
+    a.err = I->err;
+    a.num = num;
+    const long long N = a.N, two_n = 2ll * I->n;
+    long long dist_words = 0;
+    if (dm == VRPRPD_DIST_SMEM32) dist_words = N * N;
+    if (dm == VRPRPD_DIST_SMEM16) dist_words = (N * N + 1) / 2;
+    if (dm == VRPRPD_DIST_COORDS) dist_words = 2 * N;
+    a.dist_words = round4(dist_words);
+    a.shared_words = a.dist_words + round4(N);
+    a.sw = static_cast<int>((two_n + 2 + 31) / 32);
+    a.a_words = round4(a.k * two_n + 4);
+    a.ready_words = round4(static_cast<long long>(a.k) * N);
+    a.seen_words = round4(static_cast<long long>(a.k) * a.sw);
+    a.start_words = round4((a.k * two_n + 31) / 32);
+    a.off_words = round4(static_cast<long long>(a.k) * (I->m + 1));
+    a.valid_words = round4(a.k);
+    a.warp_words = a.a_words + a.ready_words + a.seen_words + a.start_words + a.off_words + a.valid_words + 96 + 4;
+    const size_t smem = static_cast<size_t>(a.shared_words + static_cast<long long>(warps) * a.warp_words) * 4;
+    if (smem + 64 > I->smem_optin) return false;
+    P->dm = dm;
+    P->warps = warps;
+    P->smem = smem;
+    return true;
+}
+
+template <int DM>
+static const void* kernel_ptr() { return reinterpret_cast<const void*>(&eval_tiles_kernel<DM>); }
+
+static const void* kernel_for(int dm) {
+    switch (dm) {
+        case VRPRPD_DIST_SMEM32: return kernel_ptr<VRPRPD_DIST_SMEM32>();
+        case VRPRPD_DIST_SMEM16: return kernel_ptr<VRPRPD_DIST_SMEM16>();
+        case VRPRPD_DIST_GLOBAL16: return kernel_ptr<VRPRPD_DIST_GLOBAL16>();
+        case VRPRPD_DIST_GLOBAL32: return kernel_ptr<VRPRPD_DIST_GLOBAL32>();
+        default: return kernel_ptr<VRPRPD_DIST_COORDS>();
+    }
+}
+
+static int finalize_plan(const vrprpd_instance* I, int blocks_per_sm, Plan* P) {
+    const void* fn = kernel_for(P->dm);
+    VRP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(P->smem)));
+    int occ = 0;
+    VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, P->warps * 32, P->smem));
+    VRP_CHECK(occ > 0, VRPRPD_EINVAL, "evaluation layout does not fit on an SM");
+    if (blocks_per_sm > 0) occ = std::min(occ, blocks_per_sm);
+    const long long ntiles = (P->args.num + P->args.k - 1) / P->args.k;
+    long long want = (ntiles + P->warps - 1) / P->warps;
+    long long blocks = std::min<long long>(static_cast<long long>(occ) * I->num_sms, want);
+    P->blocks = static_cast<int>(std::max<long long>(blocks, 1));
+    return VRPRPD_OK;
+}
+
+// Default shape: shared-memory distances when they leave room for 8 warps,
+// else recomputed coordinates, else L2 gathers.
+static int choose_plan(const vrprpd_instance* I, long long num, Plan* P) {
+    const EvalTuning& T = I->tune;
+    if (T.dist_mode != VRPRPD_DIST_AUTO && T.warps_per_block > 0) {
+        VRP_CHECK(dist_mode_available(I, T.dist_mode), VRPRPD_EINVAL, "configured distance mode unavailable");
+        VRP_CHECK(make_plan(I, T.dist_mode, T.warps_per_block, T.blocks_per_sm, num, P), VRPRPD_EINVAL,
+                  "configured evaluation layout exceeds shared memory");
+        return finalize_plan(I, T.blocks_per_sm, P);
+    }
+    const int order[] = {VRPRPD_DIST_SMEM32, VRPRPD_DIST_SMEM16, VRPRPD_DIST_COORDS, VRPRPD_DIST_GLOBAL16,
+                         VRPRPD_DIST_GLOBAL32};
+    for (int dm : order) {
+        if (!dist_mode_available(I, dm)) continue;
+        for (int warps : {16, 8}) {
+            if (dm != VRPRPD_DIST_GLOBAL32 && dm != VRPRPD_DIST_GLOBAL16 && warps < 8) continue;
+            if (make_plan(I, dm, warps, 0, num, P)) return finalize_plan(I, 0, P);
+        }
+    }
+    for (int warps : {8, 4, 2, 1})
+        if (make_plan(I, VRPRPD_DIST_GLOBAL32, warps, 0, num, P)) return finalize_plan(I, 0, P);
+    set_error("no evaluation layout fits shared memory (n=%d, m=%d)", I->n, I->m);
+    return VRPRPD_EINVAL;
+}
+
+static int launch_plan(const Plan& P, cudaStream_t stream) {
+    EvalArgs a = P.args;
+    switch (P.dm) {
+        case VRPRPD_DIST_SMEM32:
+            eval_tiles_kernel<VRPRPD_DIST_SMEM32><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
+            break;
+        case VRPRPD_DIST_SMEM16:
+            eval_tiles_kernel<VRPRPD_DIST_SMEM16><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
+            break;
+        case VRPRPD_DIST_GLOBAL16:
+            eval_tiles_kernel<VRPRPD_DIST_GLOBAL16><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
+            break;
+        case VRPRPD_DIST_GLOBAL32:
+            eval_tiles_kernel<VRPRPD_DIST_GLOBAL32><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
+            break;
+        default:
+            eval_tiles_kernel<VRPRPD_DIST_COORDS><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
+            break;
+    }
+    VRP_CUDA(cudaGetLastError());
+    return VRPRPD_OK;
+}
+
+static int check_batch(const vrprpd_instance* I, const vrprpd_batch* b, const void* z, const void* st) {
+    VRP_CHECK(I && b && z && st, VRPRPD_EINVAL, "NULL argument");
+    VRP_CHECK(b->num >= 0, VRPRPD_EINVAL, "negative batch size");
+    VRP_CHECK(b->num == 0 || (b->ops && b->off), VRPRPD_EINVAL, "NULL ops/off");
+    VRP_CHECK((reinterpret_cast<uintptr_t>(b->ops) & 3u) == 0 && (reinterpret_cast<uintptr_t>(b->off) & 3u) == 0,
+              VRPRPD_EINVAL, "ops/off must be 4-byte aligned");
+    return VRPRPD_OK;
+}
+
+int evaluate_device(const vrprpd_instance* I, const int32_t* ops, const int32_t* off, long long num,
+                    int32_t* z, uint32_t* st, cudaStream_t stream) {
+    if (num == 0) return VRPRPD_OK;
+    if (!batched_supported(I)) {
+        set_error("batched evaluation needs m <= 32, 2n+1 < 4096 and max d < 2^19 (use the plain form)");
+        return VRPRPD_EINVAL;
+    }
+    Plan P;
+    int rc = choose_plan(I, num, &P);
+    if (rc) return rc;
+    P.args.ops = ops;
+    P.args.off = off;
+    P.args.z = z;
+    P.args.st = st;
+    return launch_plan(P, stream);
+}
+
+}  // namespace vrp
+
+using namespace vrp;
+
+extern "C" int vrprpd_evaluate(const vrprpd_instance* I, const vrprpd_batch* b, int32_t* z, uint32_t* st,
+                               void* stream) {
+    int rc = check_batch(I, b, z, st);
+    if (rc) return rc;
+    return evaluate_device(I, b->ops, b->off, b->num, z, st, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int vrprpd_evaluate_host(const vrprpd_instance* I_, const vrprpd_batch* b, int32_t* z_host,
+                                    uint32_t* st_host, void* stream_) {
+    vrprpd_instance* I = const_cast<vrprpd_instance*>(I_);
+    int rc = check_batch(I, b, z_host, st_host);
+    if (rc) return rc;
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    const long long num = b->num;
+    if (num == 0) return VRPRPD_OK;
+    const size_t ops_b = static_cast<size_t>(num) * 2 * I->n * 4, off_b = static_cast<size_t>(num) * (I->m + 1) * 4;
+    const size_t need = ((ops_b + 255) & ~255ull) + ((off_b + 255) & ~255ull) + 2 * ((num * 4 + 255) & ~255ull);
+    if (need > I->stage_bytes) {
+        if (I->stage) cudaFree(I->stage);
+        I->stage = nullptr;
+        I->stage_bytes = 0;
+        VRP_CUDA(cudaMalloc(&I->stage, need));
+        I->stage_bytes = need;
+    }
+    char* base = reinterpret_cast<char*>(I->stage);
+    int32_t* d_ops = reinterpret_cast<int32_t*>(base);
+    int32_t* d_off = reinterpret_cast<int32_t*>(base + ((ops_b + 255) & ~255ull));
+    int32_t* d_z = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(d_off) + ((off_b + 255) & ~255ull));
+    uint32_t* d_st = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(d_z) + ((num * 4 + 255) & ~255ull));
+    VRP_CUDA(cudaMemcpyAsync(d_ops, b->ops, ops_b, cudaMemcpyHostToDevice, stream));
+    VRP_CUDA(cudaMemcpyAsync(d_off, b->off, off_b, cudaMemcpyHostToDevice, stream));
+    rc = evaluate_device(I, d_ops, d_off, num, d_z, d_st, stream);
+    if (rc) return rc;
+    VRP_CUDA(cudaMemcpyAsync(z_host, d_z, num * 4, cudaMemcpyDeviceToHost, stream));
+    VRP_CUDA(cudaMemcpyAsync(st_host, d_st, num * 4, cudaMemcpyDeviceToHost, stream));
+    VRP_CUDA(cudaStreamSynchronize(stream));
+    return VRPRPD_OK;
+}
+
+extern "C" int vrprpd_evaluate_plain(const vrprpd_instance* I_, const vrprpd_batch* b, int32_t* z, uint32_t* st,
+                                     void* stream) {
+    vrprpd_instance* I = const_cast<vrprpd_instance*>(I_);
+    int rc = check_batch(I, b, z, st);
+    if (rc) return rc;
+    if (b->num == 0) return VRPRPD_OK;
+    const int threads = 128;
+    const long long want = (b->num + threads - 1) / threads;
+    const int blocks = static_cast<int>(std::min<long long>(want, 512));
+    const int words = (I->n + 1) + 3 * I->m + (2 * I->n + 2 + 31) / 32;
+    const size_t need = static_cast<size_t>(blocks) * threads * words;
+    if (need > I->plain_scratch_words) {
+        cudaFree(I->plain_scratch);
+        I->plain_scratch = nullptr;
+        I->plain_scratch_words = 0;
+        VRP_CUDA(cudaMalloc(&I->plain_scratch, need * 4));
+        I->plain_scratch_words = need;
+    }
+    eval_plain_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
+        b->ops, b->off, b->num, I->n, I->m, I->R, I->Q, (I->flags & VRPRPD_LOAD_FULL) != 0, I->d32, I->p, z, st,
+        I->plain_scratch, words);
+    VRP_CUDA(cudaGetLastError());
+    return VRPRPD_OK;
+}
+
+extern "C" int vrprpd_eval_set_config(vrprpd_instance* I, const vrprpd_eval_config* cfg) {
+    VRP_CHECK(I && cfg, VRPRPD_EINVAL, "NULL argument");
+    if (cfg->dist_mode == VRPRPD_DIST_AUTO) {
+        I->tune = EvalTuning{};
+        return VRPRPD_OK;
+    }
+    VRP_CHECK(cfg->dist_mode >= VRPRPD_DIST_SMEM32 && cfg->dist_mode <= VRPRPD_DIST_COORDS, VRPRPD_EINVAL,
+              "bad dist_mode %d", cfg->dist_mode);
+    VRP_CHECK(dist_mode_available(I, cfg->dist_mode), VRPRPD_EINVAL, "distance mode %d unavailable here",
+              cfg->dist_mode);
+    VRP_CHECK(cfg->warps_per_block >= 1 && cfg->warps_per_block <= 32, VRPRPD_EINVAL, "bad warps_per_block");
+    Plan P;
+    VRP_CHECK(make_plan(I, cfg->dist_mode, cfg->warps_per_block, cfg->blocks_per_sm, 1, &P), VRPRPD_EINVAL,
+              "layout exceeds shared memory");
+    I->tune.dist_mode = cfg->dist_mode;
+    I->tune.warps_per_block = cfg->warps_per_block;
+    I->tune.blocks_per_sm = cfg->blocks_per_sm;
+    return VRPRPD_OK;
+}
+
+extern "C" int vrprpd_eval_get_config(const vrprpd_instance* I, vrprpd_eval_config* cfg) {
+    VRP_CHECK(I && cfg, VRPRPD_EINVAL, "NULL argument");
+    Plan P;
+    int rc = choose_plan(I, 1 << 20, &P);
+    if (rc) return rc;
+    cfg->dist_mode = P.dm;
+    cfg->warps_per_block = P.warps;
+    cfg->blocks_per_sm = I->tune.blocks_per_sm;
+    return VRPRPD_OK;
+}
+
+extern "C" int vrprpd_autotune(vrprpd_instance* I, const vrprpd_batch* b, void* stream_, vrprpd_eval_config* chosen) {
+    VRP_CHECK(I && b && b->num > 0, VRPRPD_EINVAL, "autotune needs a non-empty batch");
+    if (!batched_supported(I)) {
+        set_error("batched evaluation unsupported for this instance");
+        return VRPRPD_EINVAL;
+    }
+    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    int32_t* z = nullptr;
+    uint32_t* st = nullptr;
+    VRP_CUDA(cudaMalloc(&z, b->num * 4));
+    VRP_CUDA(cudaMalloc(&st, b->num * 4));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    EvalTuning best{};
+    const EvalTuning saved = I->tune;
+    const int modes[] = {VRPRPD_DIST_SMEM32, VRPRPD_DIST_SMEM16, VRPRPD_DIST_COORDS, VRPRPD_DIST_GLOBAL16,
+                         VRPRPD_DIST_GLOBAL32};
+    for (int dm : modes) {
+        if (!dist_mode_available(I, dm)) continue;
+        for (int warps : {4, 8, 12, 16, 24, 32}) {
+            for (int bps : {0, 1, 2}) {
+                Plan P;
+                if (!make_plan(I, dm, warps, bps, b->num, &P)) continue;
+                I->tune = EvalTuning{dm, warps, bps};
+                float ms_min = 1e30f;
+                for (int rep = 0; rep < 4; ++rep) {
+                    cudaEventRecord(e0, stream);
+                    int rc = evaluate_device(I, b->ops, b->off, b->num, z, st, stream);
+                    cudaEventRecord(e1, stream);
+                    if (rc) break;
+                    cudaEventSynchronize(e1);
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) ms_min = std::min(ms_min, ms);
+                }
+                if (ms_min < best_ms) {
+                    best_ms = ms_min;
+                    best = I->tune;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(z);
+    cudaFree(st);
+    if (best.dist_mode == VRPRPD_DIST_AUTO) {
+        I->tune = saved;
+        set_error("autotune found no runnable configuration");
+        return VRPRPD_EINVAL;
+    }
+    I->tune = best;
+    if (chosen) {
+        chosen->dist_mode = best.dist_mode;
+        chosen->warps_per_block = best.warps_per_block;
+        chosen->blocks_per_sm = best.blocks_per_sm;
+    }
+    VRP_CUDA(cudaGetLastError());
+    return VRPRPD_OK;
+}

@@ -1,0 +1,152 @@
+"""GPU parity of candidate evaluation against the CPU oracle: bit-exact makespan
+and status for every candidate, every distance mode, the plain form and the
+host-buffer path; ragged tiles, odd n (unaligned TMA), m = 1 and m = 32,
+malformed and cyclic candidates, and the full-size n = 1000 workload."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+MODES = ["smem32", "smem16", "global16", "global32", "coords"]
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run_modes(vrp, inst, ops, off, modes=MODES):
+    results = {}
+    for mode in modes:
+        try:
+            vrp.set_eval_config(inst, mode, 8)
+        except vrp.VrpError:
+            continue
+        z, st = vrp.evaluate(inst, dev(ops), dev(off))
+        vrp.sync(inst)
+        results[mode] = (z.cpu().numpy(), st.cpu().numpy().astype(np.uint32))
+    vrp.set_eval_config(inst, "auto")
+    return results
+
+
+def check_against_oracle(vrp, w, ops, off, modes=MODES, load_full=False, threads=8):
+    inst = vrp.Instance.from_workload(w, load_full=load_full)
+    oi = oracle.OracleInstance.from_workload(w, load_full=load_full)
+    assert np.array_equal(inst.dist(), oracle.euc2d(w.coords))
+    zo, so = oracle.evaluate_batch(oi, ops, off, threads=threads)
+    res = run_modes(vrp, inst, ops, off, modes)
+    assert res, "no distance mode ran"
+    for mode, (z, st) in res.items():
+        bad = np.nonzero((z != zo) | (st != so))[0]
+        assert bad.size == 0, (mode, bad[:5], z[bad[:5]], zo[bad[:5]], st[bad[:5]], so[bad[:5]])
+    zp, sp = vrp.evaluate_plain(inst, dev(ops), dev(off))
+    assert np.array_equal(zp.cpu().numpy(), zo) and np.array_equal(sp.cpu().numpy().astype(np.uint32), so)
+    return inst, zo, so
+
+
+def test_c1_random_and_precedence(vrp):
+    cfg = workloads.CONFIGS["C1"]
+    w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], seed=0)
+    ops, off = workloads.random_candidates(w.n, w.m, 4096, seed=0)
+    _, zo, so = check_against_oracle(vrp, w, ops, off)
+    assert (so & oracle.CYCLE).any()                     # random orders are mostly cyclic
+    ops, off = workloads.precedence_candidates(w.n, w.m, 4096, seed=1)
+    _, zo, so = check_against_oracle(vrp, w, ops, off)
+    assert not (so & oracle.CYCLE).any()
+
+
+def test_c2_full_batch(vrp):
+    cfg = workloads.CONFIGS["C2"]
+    w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], seed=0)
+    ops, off = workloads.precedence_candidates(w.n, w.m, 65536, seed=2)
+    check_against_oracle(vrp, w, ops, off, modes=["smem32", "coords"])
+
+
+@pytest.mark.parametrize("n,m,count", [(1, 1, 5), (1, 2, 7), (7, 3, 333), (33, 32, 65), (51, 1, 40),
+                                       (101, 5, 1001), (200, 6, 257)])
+def test_shapes_ragged_and_odd(vrp, n, m, count):
+    w = workloads.make_instance(n, m, R=max(1, n // 3), Q=3, variant="2x", seed=n)
+    o1, f1 = workloads.precedence_candidates(n, m, count, seed=5)
+    o2, f2 = workloads.random_candidates(n, m, count, seed=6)
+    ops = np.concatenate([o1, o2])
+    off = np.concatenate([f1, f2])
+    check_against_oracle(vrp, w, ops, off)
+    # an offset view into the batch: the op array no longer starts 16-byte aligned
+    import torch
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    big = dev(np.concatenate([np.full((1, 2 * n), 2, np.int32), ops]).reshape(-1))
+    sub = big[2 * n:].view(-1, 2 * n)
+    if n % 2 == 1:
+        assert (sub.data_ptr() % 16) != 0
+    z, st = vrp.evaluate(inst, sub, dev(off))
+    zo, so = oracle.evaluate_batch(oi, ops, off, threads=8)
+    assert np.array_equal(z.cpu().numpy(), zo) and np.array_equal(st.cpu().numpy().astype(np.uint32), so)
+
+
+def test_load_full(vrp):
+    w = workloads.make_instance(40, 4, R=40, Q=6, seed=9)
+    ops, off = workloads.precedence_candidates(40, 4, 2000, seed=9)
+    check_against_oracle(vrp, w, ops, off, load_full=True)
+
+
+def test_malformed_candidates(vrp):
+    n, m = 10, 3
+    w = workloads.make_instance(n, m, R=5, Q=3, seed=4)
+    ops, off = workloads.precedence_candidates(n, m, 64, seed=4)
+    ops = ops.copy()
+    off = off.copy()
+    ops[0, 3] = ops[0, 4]                  # duplicate op
+    ops[1, 0] = 2 * n + 2                  # op code out of range
+    ops[2, 5] = 1                          # op code below range
+    off[3, 1], off[3, 2] = off[3, 2], off[3, 1] + 0  # possibly decreasing
+    off[3, 1] = off[3, 2] + 1
+    off[4, 0] = 1                          # off[0] != 0
+    off[5, m] = 2 * n - 1                  # off[m] != 2n
+    inst, zo, so = check_against_oracle(vrp, w, ops, off)
+    assert all(so[i] == oracle.MALFORMED for i in range(6))
+
+
+def test_host_path_matches(vrp):
+    w = workloads.make_instance(100, 4, 10, 5, "2x", seed=1)
+    inst = vrp.Instance.from_workload(w)
+    ops, off = workloads.precedence_candidates(100, 4, 3000, seed=8)
+    z1, s1 = vrp.evaluate(inst, dev(ops), dev(off))
+    z2, s2 = vrp.evaluate_host(inst, ops, off)
+    assert np.array_equal(z1.cpu().numpy(), z2) and np.array_equal(s1.cpu().numpy().astype(np.uint32), s2)
+
+
+def test_autotune_keeps_results(vrp):
+    w = workloads.make_instance(100, 4, 10, 5, "2x", seed=3)
+    inst = vrp.Instance.from_workload(w)
+    ops, off = workloads.precedence_candidates(100, 4, 8192, seed=3)
+    z1, s1 = vrp.evaluate(inst, dev(ops), dev(off))
+    cfg = vrp.autotune(inst, dev(ops), dev(off))
+    assert cfg["dist_mode"] in MODES
+    z2, s2 = vrp.evaluate(inst, dev(ops), dev(off))
+    assert np.array_equal(z1.cpu().numpy(), z2.cpu().numpy())
+    assert np.array_equal(s1.cpu().numpy(), s2.cpu().numpy())
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_n1000_full_size_sampled(vrp, seed):
+    # the headline workload: n = 1000, m = 20, R = 100, Q = 10, 1R20 processing times;
+    # a 4096-candidate batch on the device, the oracle checks every 8th candidate
+    cfg = workloads.CONFIGS["C5"]
+    w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=seed)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    assert np.array_equal(inst.dist(), oracle.euc2d(w.coords))
+    ops, off = workloads.precedence_candidates(w.n, w.m, 4096, seed=seed)
+    idx = np.arange(0, 4096, 8)
+    zo, so = oracle.evaluate_batch(oi, ops[idx], off[idx], threads=8)
+    for mode in ["coords", "global16", "global32", "auto"]:
+        vrp.set_eval_config(inst, mode, 4 if mode != "auto" else 0)
+        z, st = vrp.evaluate(inst, dev(ops), dev(off))
+        vrp.sync(inst)
+        assert np.array_equal(z.cpu().numpy()[idx], zo), mode
+        assert np.array_equal(st.cpu().numpy().astype(np.uint32)[idx], so), mode
+    vrp.set_eval_config(inst, "auto")
