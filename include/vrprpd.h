@@ -140,6 +140,143 @@ int vrprpd_eval_get_config(const vrprpd_instance* inst, vrprpd_eval_config* cfg)
 int vrprpd_autotune(vrprpd_instance* inst, const vrprpd_batch* batch, void* stream,
                     vrprpd_eval_config* chosen);
 
+/* ======================================================================== */
+/* ALNS (Section 4.2, Algorithm 1) on the device                             */
+/* ======================================================================== */
+
+/* A solution in HOST memory: ops[2n] and off[m+1] (caller-owned). */
+typedef struct {
+    int32_t* ops;
+    int32_t* off;
+    int32_t makespan;
+    uint32_t status;
+} vrprpd_solution;
+
+/* Hyperparameters (Table 2).  vrprpd_alns_params_default() fills the paper's
+ * values: T0 = 0.30, alpha = 0.9998, reheat 0.50, stagnation 2000, tau = 100,
+ * r = 0.1, sigma = (33, 9, 13), minimum weight 0.1, q from Section 4.2.2. */
+typedef struct {
+    double T0, alpha, reheat, r;
+    int32_t stagnation, tau;
+    int32_t sigma1, sigma2, sigma3;
+    double w_min;
+    int32_t q_min, q_max;      /* 0, 0 = q_max = max(4, floor(0.05 n)), q_min = max(4, floor(q_max/2)) */
+    int32_t iterations;
+    int32_t repair_mask;       /* bit 0 greedy insertion, bit 1 regret-2 insertion */
+    int32_t team_blocks;       /* CTAs cooperating on one instance; 0 = chosen from n */
+} vrprpd_alns_params;
+
+typedef struct {
+    int32_t iterations, accepted, improved, new_best, reheats, rejected_infeasible;
+    int32_t z_init, z_best, z_current;
+    double T_final;
+    double w_destroy[4], w_repair[4];
+    double device_ms;          /* wall time of the device run */
+    int64_t matrix_entries;    /* insertion-matrix entries evaluated in O(1) */
+    int64_t fallback_entries;  /* entries re-simulated in full */
+    int32_t team_blocks;       /* CTAs used */
+} vrprpd_alns_stats;
+
+void vrprpd_alns_params_default(vrprpd_alns_params* params);
+
+/* Deterministic feasible start (host): customers in exact angular order
+ * around the depot (by id when the instance has no coordinates), split into
+ * m sectors of balanced workload w_c = 2 d(0,c) + p_c, each route serving its
+ * sector in blocks "D c1..cb, P c1..cb" with b = min(Q, R / min(m, R)).
+ * out->ops / out->off are host buffers of 2n and m+1 int32; needs R, Q >= 1. */
+int vrprpd_initial_solution(const vrprpd_instance* inst, vrprpd_solution* out);
+
+/*
+ * Run Algorithm 1 on the device: roulette selection of operators (random
+ * removal; greedy or regret-2 insertion over the full insertion-delta matrix),
+ * simulated-annealing acceptance with the text's reheat gate, adaptive weights.
+ * Every random draw is SplitMix64 of (seed-derived key, iteration-derived
+ * counter), so a run is reproducible bit for bit.
+ *   init     host solution to start from, or NULL for vrprpd_initial_solution.
+ *            It must be feasible (status 0).
+ *   best     host buffers receive the best solution found (and its makespan).
+ *   current  host buffers for the final current solution, or NULL.
+ *   stats    may be NULL; z_trace (host, params->iterations int32) receives the
+ *            current makespan after each iteration, or NULL.
+ * Needs m <= 32, 2n + m <= 4096 and max d < 2^17.  Blocking: returns when done.
+ */
+int vrprpd_alns_run(const vrprpd_instance* inst, const vrprpd_solution* init,
+                    const vrprpd_alns_params* params, uint64_t seed, vrprpd_solution* best,
+                    vrprpd_solution* current, vrprpd_alns_stats* stats, int32_t* z_trace, void* stream);
+
+/*
+ * The insertion-delta matrix of Section 4.2.3 for one customer c (absent from
+ * the partial solution given in host memory: ops[off[m]], off[m+1]).  Rows are
+ * the dropoff gaps, columns the pickup gaps, gaps enumerated route by route
+ * (route v has off[v+1]-off[v]+1 gaps).  delta_host (G x G, G = off[m] + m)
+ * receives z(S + D_c + P_c) - z(S), or INT32_MAX when that solution has a
+ * precedence cycle, breaks capacity on a receiving vehicle or the pool;
+ * travel_host (G x G, may be NULL) receives the change in total route length.
+ * Computed by the same kernels the ALNS uses.  Blocking.
+ */
+int vrprpd_insertion_matrix(const vrprpd_instance* inst, const int32_t* ops_host,
+                            const int32_t* off_host, int32_t c, int32_t* delta_host,
+                            int32_t* travel_host, void* stream);
+
+/* ======================================================================== */
+/* BRKGA (Section 4.4, Algorithm 2) on the device                            */
+/* ======================================================================== */
+
+/* Chromosome layout: L = 2n + m float32 keys in [0,1).  keys[2(c-1)+isPickup]
+ * is the priority of customer c's dropoff/pickup (lower = scheduled first,
+ * Section 4.4.1); keys[2n+v] orders the vehicles for SelectVehicle's
+ * tie-break (lower key = preferred). */
+typedef struct {
+    int32_t pop, generations;
+    int32_t warm_slots;        /* slots seeded from the warm start (0 without one) */
+    int32_t warm_variants;     /* distinct warm variants cycled over those slots (20) */
+    float elite_frac, mutant_frac, rho;  /* Table 3: 0.15, 0.15, 0.7 */
+    float eps;                 /* warm perturbation half-width (0.03, Section 4.4.5) */
+} vrprpd_brkga_params;
+
+/* Table 3 values: pop 30000, 20000 generations, elite/mutant 0.15, rho 0.7,
+ * warm slots ceil(0.15 pop), 20 variants, eps 0.03. */
+void vrprpd_brkga_params_default(vrprpd_brkga_params* params);
+
+/*
+ * Decode a batch of chromosomes (Algorithm 2): stable argsort of the 2n
+ * priorities (ties by op index), then passes over the ops in that order; a
+ * dropoff is feasible on a vehicle that can load one more resource within Q
+ * and the pool R; a pickup is feasible once its dropoff is scheduled, on a
+ * vehicle with room; SelectVehicle takes the least arrival time t[v] +
+ * d(l[v], c), ties to the lower vehicle key; the pickup leaves at
+ * max(arrival, T_drop + p_c).  Passes stop when everything is scheduled or a
+ * pass schedules nothing.
+ *   keys     device, num x L float32.
+ *   ops/off  device, num x 2n and num x (m+1): the decoded routes (scheduled ops only).
+ *   z        device, num: makespan of the decoded routes.
+ *   unsched  device, num: ops left unscheduled.
+ *   fitness  device, num int64: z + 10^6 * unsched (Section 4.4.3).
+ * Asynchronous on stream.  Needs m <= 32 and 2n + m <= 8192.
+ */
+int vrprpd_brkga_decode(const vrprpd_instance* inst, const float* keys, int32_t num, int32_t* ops,
+                        int32_t* off, int32_t* z, int32_t* unsched, int64_t* fitness, void* stream);
+
+/*
+ * Run the BRKGA: warm-started population (slot 0 = the exact encoding of
+ * `warm`, pi_o = (r-1)/L_v and vehicle key v/m; slots 1..warm_slots-1 cycle
+ * through perturbed variants, key + U(-eps, eps) clamped to [0, 1-2^-24];
+ * the rest uniform random), then per generation: decode, re-evaluate the
+ * decoded routes with the batched evaluator, rank by (fitness, index), copy
+ * the elites, draw mutants, and fill the rest by biased crossover (elite gene
+ * with probability rho).  One generation is a CUDA graph replayed
+ * `generations` times.
+ *   warm          host solution or NULL (random start).
+ *   best          host buffers: routes of the best chromosome of the last generation.
+ *   best_fitness  host, may be NULL.
+ *   trace         host, `generations` int64 (best fitness per generation) or NULL.
+ *   final_keys    device, pop x L float32 (the last population) or NULL.
+ * Needs pop <= 16384, m <= 32 and 2n + m <= 8192.  Blocking.
+ */
+int vrprpd_brkga_run(const vrprpd_instance* inst, const vrprpd_brkga_params* params,
+                     const vrprpd_solution* warm, uint64_t seed, vrprpd_solution* best,
+                     int64_t* best_fitness, int64_t* trace, float* final_keys, void* stream);
+
 const char* vrprpd_last_error(void);
 
 #ifdef __cplusplus

@@ -241,3 +241,109 @@ def autotune(inst, ops, off, stream=None):
     _check(lib().vrprpd_autotune(inst.handle, C.byref(b), _stream_ptr(stream), C.byref(cfg)))
     return {"dist_mode": _DIST_NAMES[cfg.dist_mode], "warps_per_block": cfg.warps_per_block,
             "blocks_per_sm": cfg.blocks_per_sm}
+
+
+# ---------------------------------------------------------------------------
+# ALNS (Section 4.2)
+# ---------------------------------------------------------------------------
+def _sol(inst, ops=None, off=None):
+    from ._search_sig import Solution
+    ops = np.zeros(2 * inst.n, np.int32) if ops is None else np.ascontiguousarray(ops, dtype=np.int32)
+    off = np.zeros(inst.m + 1, np.int32) if off is None else np.ascontiguousarray(off, dtype=np.int32)
+    return Solution(ops.ctypes.data, off.ctypes.data, 0, 0), ops, off
+
+
+def initial_solution(inst):
+    s, ops, off = _sol(inst)
+    _check(lib().vrprpd_initial_solution(inst.handle, C.byref(s)))
+    return ops, off
+
+
+def alns_params(iterations=1000, q_min=0, q_max=0, repair_mask=3, team_blocks=0, **over):
+    from ._search_sig import AlnsParams
+    p = AlnsParams()
+    lib().vrprpd_alns_params_default(C.byref(p))
+    p.iterations, p.q_min, p.q_max = iterations, q_min, q_max
+    p.repair_mask, p.team_blocks = repair_mask, team_blocks
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def alns_run(inst, params, seed=0, init=None, stream=None):
+    """Algorithm 1 on the device.  init = (ops, off) host arrays or None."""
+    from ._search_sig import AlnsStats
+    best, bo, bf = _sol(inst)
+    cur, co, cf = _sol(inst)
+    init_s = None
+    if init is not None:
+        init_s, _io, _if = _sol(inst, *init)
+    st = AlnsStats()
+    trace = np.zeros(max(1, params.iterations), np.int32)
+    _check(lib().vrprpd_alns_run(inst.handle, C.byref(init_s) if init_s is not None else None, C.byref(params),
+                                 C.c_uint64(seed), C.byref(best), C.byref(cur), C.byref(st),
+                                 trace.ctypes.data, _stream_ptr(stream)))
+    return {"best_ops": bo, "best_off": bf, "z_best": best.makespan, "cur_ops": co, "cur_off": cf,
+            "z_current": cur.makespan, "stats": st, "trace": trace[:params.iterations]}
+
+
+def insertion_matrix(inst, ops, off, c, stream=None):
+    """Full insertion-delta matrix of customer c into a host partial solution."""
+    ops = np.ascontiguousarray(ops, dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int32)
+    G = int(off[-1]) + inst.m
+    delta = np.empty((G, G), np.int32)
+    travel = np.empty((G, G), np.int32)
+    opsp = ops if ops.size else np.zeros(1, np.int32)
+    _check(lib().vrprpd_insertion_matrix(inst.handle, opsp.ctypes.data, off.ctypes.data, int(c),
+                                         delta.ctypes.data, travel.ctypes.data, _stream_ptr(stream)))
+    return delta, travel
+
+
+# ---------------------------------------------------------------------------
+# BRKGA (Section 4.4)
+# ---------------------------------------------------------------------------
+def brkga_params(pop, generations, elite=0.2, mutant=0.1, rho=0.7, warm_frac=0.15, warm_variants=20,
+                 eps=0.03):
+    import math
+    from ._search_sig import BrkgaParams
+    return BrkgaParams(pop, generations, int(math.ceil(warm_frac * pop - 1e-9)), warm_variants,
+                       elite, mutant, rho, eps)
+
+
+def brkga_decode(inst, keys, stream=None):
+    """Decode device keys (num x (2n+m) float32) -> routes, makespan, unscheduled, fitness."""
+    torch = _torch()
+    if keys.dtype != torch.float32 or keys.device.type != "cuda" or not keys.is_contiguous():
+        raise TypeError("keys must be a contiguous CUDA float32 tensor")
+    num = keys.shape[0]
+    if tuple(keys.shape) != (num, 2 * inst.n + inst.m):
+        raise ValueError("keys must be num x (2n+m)")
+    dev = keys.device
+    ops = torch.empty((num, 2 * inst.n), dtype=torch.int32, device=dev)
+    off = torch.empty((num, inst.m + 1), dtype=torch.int32, device=dev)
+    z = torch.empty(num, dtype=torch.int32, device=dev)
+    un = torch.empty(num, dtype=torch.int32, device=dev)
+    fit = torch.empty(num, dtype=torch.int64, device=dev)
+    _check(lib().vrprpd_brkga_decode(inst.handle, keys.data_ptr(), num, ops.data_ptr(), off.data_ptr(),
+                                     z.data_ptr(), un.data_ptr(), fit.data_ptr(), _stream_ptr(stream)))
+    return ops, off, z, un, fit
+
+
+def brkga_run(inst, params, seed=0, warm=None, final_keys=False, stream=None):
+    """Warm-started BRKGA on the device; warm = (ops, off) host arrays or None."""
+    torch = _torch()
+    best, bo, bf = _sol(inst)
+    warm_s = None
+    if warm is not None:
+        warm_s, _wo, _wf = _sol(inst, *warm)
+    trace = np.zeros(params.generations, np.int64)
+    fitness = np.zeros(1, np.int64)
+    keys = None
+    if final_keys:
+        keys = torch.empty((params.pop, 2 * inst.n + inst.m), dtype=torch.float32, device="cuda")
+    _check(lib().vrprpd_brkga_run(inst.handle, C.byref(params), C.byref(warm_s) if warm_s is not None else None,
+                                  C.c_uint64(seed), C.byref(best), fitness.ctypes.data, trace.ctypes.data,
+                                  keys.data_ptr() if keys is not None else None, _stream_ptr(stream)))
+    return {"best_ops": bo, "best_off": bf, "z_best": best.makespan, "best_fitness": int(fitness[0]),
+            "trace": trace, "keys": keys}

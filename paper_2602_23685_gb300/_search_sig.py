@@ -1,5 +1,45 @@
-"""ctypes signatures of the search entry points (ALNS, BRKGA, serving)."""
+"""ctypes declarations of the search entry points (include/vrprpd.h)."""
+import ctypes as C
+
+
+class Solution(C.Structure):
+    _fields_ = [("ops", C.c_void_p), ("off", C.c_void_p), ("makespan", C.c_int32), ("status", C.c_uint32)]
+
+
+class AlnsParams(C.Structure):
+    _fields_ = [("T0", C.c_double), ("alpha", C.c_double), ("reheat", C.c_double), ("r", C.c_double),
+                ("stagnation", C.c_int32), ("tau", C.c_int32), ("sigma1", C.c_int32),
+                ("sigma2", C.c_int32), ("sigma3", C.c_int32), ("w_min", C.c_double),
+                ("q_min", C.c_int32), ("q_max", C.c_int32), ("iterations", C.c_int32),
+                ("repair_mask", C.c_int32), ("team_blocks", C.c_int32)]
+
+
+class AlnsStats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("accepted", C.c_int32), ("improved", C.c_int32),
+                ("new_best", C.c_int32), ("reheats", C.c_int32), ("rejected_infeasible", C.c_int32),
+                ("z_init", C.c_int32), ("z_best", C.c_int32), ("z_current", C.c_int32),
+                ("T_final", C.c_double), ("w_destroy", C.c_double * 4), ("w_repair", C.c_double * 4),
+                ("device_ms", C.c_double), ("matrix_entries", C.c_int64),
+                ("fallback_entries", C.c_int64), ("team_blocks", C.c_int32)]
+
+
+class BrkgaParams(C.Structure):
+    _fields_ = [("pop", C.c_int32), ("generations", C.c_int32), ("warm_slots", C.c_int32),
+                ("warm_variants", C.c_int32), ("elite_frac", C.c_float), ("mutant_frac", C.c_float),
+                ("rho", C.c_float), ("eps", C.c_float)]
 
 
 def register(L):
+    vp = C.c_void_p
+    L.vrprpd_alns_params_default.argtypes = [C.POINTER(AlnsParams)]
+    L.vrprpd_alns_params_default.restype = None
+    L.vrprpd_initial_solution.argtypes = [vp, C.POINTER(Solution)]
+    L.vrprpd_alns_run.argtypes = [vp, C.POINTER(Solution), C.POINTER(AlnsParams), C.c_uint64,
+                                  C.POINTER(Solution), C.POINTER(Solution), C.POINTER(AlnsStats), vp, vp]
+    L.vrprpd_insertion_matrix.argtypes = [vp, vp, vp, C.c_int32, vp, vp, vp]
+    L.vrprpd_brkga_params_default.argtypes = [C.POINTER(BrkgaParams)]
+    L.vrprpd_brkga_params_default.restype = None
+    L.vrprpd_brkga_decode.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp, vp, vp]
+    L.vrprpd_brkga_run.argtypes = [vp, C.POINTER(BrkgaParams), C.POINTER(Solution), C.c_uint64,
+                                   C.POINTER(Solution), vp, vp, vp, vp]
     return L

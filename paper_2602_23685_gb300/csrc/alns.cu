@@ -1,0 +1,1495 @@
+// ALNS on the device (Section 4.2, Algorithm 1): random removal, greedy and
+// regret-2 insertion over the full insertion-delta matrix (Section 4.2.3),
+// simulated-annealing acceptance with reheat (Section 4.2.4), adaptive
+// operator weights (Section 4.2.1).
+//
+// One persistent cooperative launch; a team of CTAs runs one ALNS instance
+// and meets at bounded team barriers.  Each insertion step:
+//   prep    each CTA stages the partial solution W in shared memory (op codes
+//           packed with their travel-in times); one warp walks W from the depot
+//           (node times H, makespan, stock prefixes), the other warps walk W
+//           from every op u (row u of the all-pairs longest-path table LP and
+//           the tail T(u) = longest path from u to a depot return); threads
+//           flag "shortcut" gaps, where d(x,c) + d(c,y) < d(x,y) because of
+//           the nint rounding;
+//   gaps    per-gap vectors (H of the stop before, T of the stop after, the
+//           removed leg, stock prefix/suffix extremes) and sparse tables of
+//           the stock prefix for same-route ranges;
+//   matrix  32 x 128 tiles of (dropoff gap, pickup gap) entries for every
+//           customer still to insert.  Without shortcut gaps the new makespan
+//           is exactly max(z, beta, gamma, delta, epsilon): the old makespan,
+//           the longest path through the new drop only, through the new pickup
+//           only, through drop -> pickup by the processing edge, and through
+//           drop -> route -> pickup (the LP table).  Capacity and pool are O(1)
+//           from the prefix/suffix extremes.  Entries touching a shortcut gap
+//           are re-simulated in full by one warp each;
+//   select  per-customer argmin of (delta z, delta travel, flat index), then
+//           greedy or regret-2 choice across customers; the choice is applied
+//           to W.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include <cooperative_groups.h>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace vrp {
+
+constexpr int NEG = -(1 << 30);               // "unreachable" in the longest-path table
+constexpr int UNRES = INT32_MIN;               // ready value not yet published
+constexpr int TR = 32, TC = 128, LPS = 136;    // matrix tile rows, cols, smem row stride
+constexpr int FB_CHUNK = 64;                   // entries per fallback work item
+constexpr int ALNS_THREADS = 256;
+constexpr int ALNS_WARPS = ALNS_THREADS / 32;
+constexpr unsigned long long KEY_NONE = ~0ull;
+constexpr long long REGRET_INF = 1ll << 40;
+
+struct AlnsCtl {
+    int iter, q, nrem, di, rj;
+    int z_cur, z_best, z_work;
+    unsigned st_work;
+    int stagnation, repair_fail, wsel, err;
+    int work_counter, n_short, sum_load;
+    int pick_t, pick_row, pick_col;
+    unsigned bar_count, bar_gen;
+    double T, T_init;
+    double wd[4], wr[4];
+    int sd[4], sr[4], ad[4], ar[4];
+    int accepted, improved, new_best, reheats, rejected;
+    int z_init;
+    unsigned long long entries, fallback_entries;
+};
+
+struct AlnsTeam {
+    // instance
+    int n, m, R, Q, load_full;
+    const int* d32;
+    const int* p;          // p[0..n]
+    // parameters
+    double T0, alpha, reheat, r, w_min;
+    int stagnation_limit, tau, sigma1, sigma2, sigma3, q_min, q_max, iterations, repair_mask;
+    unsigned long long key;  // RNG stream key
+    int mode;                // 0 = search, 1 = one-customer matrix dump
+    int dump_c;
+    // state and scratch (device)
+    AlnsCtl* ctl;
+    int *cur_ops, *cur_off, *best_ops, *best_off;
+    int *W_ops[2], *W_off[2];
+    int *rem, *perm;
+    int *H, *T, *Ms;
+    int *S_, *PMINp, *PMAXp, *SMINs, *SMAXs;
+    int *spmin, *spmax;      // [LOG][2n]
+    int log_levels;
+    int *gx, *gy, *gHx, *gTy, *gw, *gsb, *gpmin, *gpmax, *gsmin, *gsmax, *groute, *gpos;
+    int *rload;              // start load per route
+    unsigned long long* keys;  // [q_max][G]
+    unsigned char* sc;         // [q_max][G]
+    int* slist;                // [q_max * G] entries t * G + g
+    int* trace;
+    int* dump_delta;
+    int* dump_travel;
+};
+
+// ---------------------------------------------------------------------------
+// shared-memory layout of one CTA
+// ---------------------------------------------------------------------------
+struct Smem {
+    int* sW;        // packed W ops [2n + 4]
+    int* sWoff;     // [m + 1]
+    int* sp;        // p[0..n]
+    int* rdy;       // [warps][n + 1]
+    int* lp;        // [TR][LPS]
+    unsigned* reach;// [TC]
+    int* rowv;      // [TR][RV]
+    int* colv;      // [TC][CV]
+    int* misc;      // 64 ints
+    unsigned char* flags;  // [n + 1] removed flags / route-start bits
+};
+constexpr int RV = 16, CV = 12;
+
+__host__ __device__ inline size_t alns_smem_words(int n, int m) {
+    size_t w = 0;
+    w += ((2 * n + 4) + 3) & ~3;
+    w += ((m + 1) + 3) & ~3;
+    w += ((n + 1) + 3) & ~3;
+    w += static_cast<size_t>(ALNS_WARPS) * (((n + 1) + 3) & ~3);
+    w += TR * LPS + TC + TR * RV + TC * CV + 64;
+    w += ((n + 1 + 3) / 4 + 3) & ~3;
+    return w;
+}
+
+__device__ inline Smem carve(int* base, int n, int m) {
+    Smem s;
+    int* q = base;
+    s.sW = q; q += ((2 * n + 4) + 3) & ~3;
+    s.sWoff = q; q += ((m + 1) + 3) & ~3;
+    s.sp = q; q += ((n + 1) + 3) & ~3;
+    s.rdy = q; q += ALNS_WARPS * (((n + 1) + 3) & ~3);
+    s.lp = q; q += TR * LPS;
+    s.reach = reinterpret_cast<unsigned*>(q); q += TC;
+    s.rowv = q; q += TR * RV;
+    s.colv = q; q += TC * CV;
+    s.misc = q; q += 64;
+    s.flags = reinterpret_cast<unsigned char*>(q);
+    return s;
+}
+
+__device__ __forceinline__ int D(const AlnsTeam& t, int a, int b) { return __ldg(t.d32 + a * (t.n + 1) + b); }
+
+// ---------------------------------------------------------------------------
+// team barrier: all CTAs of the team; bounded (about 2 s), sets ctl->err
+// ---------------------------------------------------------------------------
+__device__ bool team_barrier(AlnsCtl* ctl, int team_blocks, unsigned& gen) {
+    __syncthreads();
+    if (team_blocks > 1) {
+        if (threadIdx.x == 0) {
+            volatile unsigned* vgen = &ctl->bar_gen;
+            __threadfence();
+            const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
+            if (arrived == static_cast<unsigned>(team_blocks)) {
+                ctl->bar_count = 0u;
+                __threadfence();
+                atomicExch(&ctl->bar_gen, gen + 1u);
+            } else {
+                const uint64_t t0 = global_ns();
+                while (*vgen == gen) {
+                    if (global_ns() - t0 > 2000000000ull) {
+                        atomicExch(&ctl->err, DEV_TIMEOUT_BARRIER);
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            __threadfence();
+        }
+        gen += 1u;
+        __syncthreads();
+    }
+    return *reinterpret_cast<volatile int*>(&ctl->err) == 0;
+}
+
+// ---------------------------------------------------------------------------
+// stage W into shared memory: packed (travel-in << 12 | op)
+// ---------------------------------------------------------------------------
+__device__ void stage_W(const AlnsTeam& t, const Smem& s) {
+    const AlnsCtl* ctl = t.ctl;
+    const int* W = t.W_ops[ctl->wsel];
+    const int* Wo = t.W_off[ctl->wsel];
+    const int m = t.m;
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) s.sWoff[i] = Wo[i];
+    __syncthreads();
+    const int N = s.sWoff[m];
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        // the op before k on its route: none if k starts a route
+        int lo = 0, hi = m;                    // find route r with off[r] <= k < off[r+1]
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (s.sWoff[mid] <= k) lo = mid; else hi = mid;
+        }
+        const int o = W[k];
+        const int prev = (k == s.sWoff[lo]) ? 0 : (W[k - 1] >> 1);
+        s.sW[k] = (D(t, prev, o >> 1) << PACK_SHIFT) | o;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// walks (one warp; lane r walks route r; m <= 32)
+// ---------------------------------------------------------------------------
+// From the depot: node times H, stock prefixes, makespan, cycle flag.
+__device__ void walk_depot(const AlnsTeam& t, const Smem& s, int* rdy, bool write_arrays, int* z_out,
+                           unsigned* st_out) {
+    const int lane = threadIdx.x & 31, m = t.m, n = t.n;
+    for (int c = lane; c <= n; c += 32) rdy[c] = UNRES;
+    __syncwarp();
+    const bool mine = lane < m;
+    int pos = mine ? s.sWoff[lane] : 0, end = mine ? s.sWoff[lane + 1] : 0;
+    const int start = pos;
+    int dep = 0, last = 0, sv = 0, smin = 0, smax = 0;
+    bool walking = mine && pos < end, cyc = false;
+    while (__any_sync(FULL_MASK, walking)) {
+        int w = 0, rv = 0, c = 0;
+        bool go = false, pick = false;
+        if (walking) {
+            w = s.sW[pos];
+            const int o = w & PACK_MASK;
+            c = o >> 1;
+            pick = o & 1;
+            if (pick) rv = rdy[c];
+            go = !pick || rv != UNRES;
+        }
+        __syncwarp();
+        if (go) {
+            const int arr = dep + (w >> PACK_SHIFT);
+            if (pick) { dep = max(arr, rv); ++sv; smax = max(smax, sv); }
+            else { dep = arr; rdy[c] = arr + s.sp[c]; --sv; smin = min(smin, sv); }
+            if (write_arrays) {
+                t.H[pos] = dep;
+                t.S_[pos] = sv;
+                t.PMINp[pos] = smin;
+                t.PMAXp[pos] = smax;
+            }
+            last = c;
+            ++pos;
+        }
+        __syncwarp();
+        const unsigned prog = __ballot_sync(FULL_MASK, go);
+        if (walking) {
+            if (pos >= end) walking = false;
+            else if (prog == 0u) { walking = false; cyc = true; }
+        }
+    }
+    if (cyc)
+        for (; pos < end; ++pos) {
+            const int o = s.sW[pos] & PACK_MASK;
+            if (o & 1) { ++sv; smax = max(smax, sv); } else { --sv; smin = min(smin, sv); }
+        }
+    // suffix extremes of the stock prefix, route by route
+    if (write_arrays && mine) {
+        int mn = INT32_MAX, mx = INT32_MIN;
+        for (int k = end - 1; k >= start; --k) {
+            mn = min(mn, t.S_[k]);
+            mx = max(mx, t.S_[k]);
+            t.SMINs[k] = mn;
+            t.SMAXs[k] = mx;
+        }
+    }
+    int ret = (mine && !cyc && end > start) ? dep + D(t, last, 0) : 0;
+    int load = 0;
+    bool bad = false;
+    if (mine) {
+        if (t.load_full) { bad = smin < -t.Q || smax > 0; load = t.Q; }
+        else { bad = -smin + smax > t.Q; load = -smin; }
+        if (write_arrays) t.rload[lane] = load;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        ret = max(ret, __shfl_xor_sync(FULL_MASK, ret, o));
+        load += __shfl_xor_sync(FULL_MASK, load, o);
+    }
+    const unsigned anycyc = __ballot_sync(FULL_MASK, cyc), anybad = __ballot_sync(FULL_MASK, bad);
+    unsigned st = (anycyc ? VRPRPD_CYCLE : 0u) | (anybad ? VRPRPD_VEH_CAP : 0u) | (load > t.R ? VRPRPD_POOL : 0u);
+    if (anycyc) ret = 0x7fffffff;
+    *z_out = ret;
+    *st_out = st;
+    if (write_arrays && lane == 0) t.ctl->sum_load = load;
+}
+
+// From op u: row u of LP (NEG where unreachable) and T(u).
+__device__ void walk_source(const AlnsTeam& t, const Smem& s, int* rdy, int u, int N) {
+    const int lane = threadIdx.x & 31, m = t.m, n = t.n;
+    for (int c = lane; c <= n; c += 32) rdy[c] = UNRES;
+    __syncwarp();
+    const bool mine = lane < m;
+    int pos = mine ? s.sWoff[lane] : 0, end = mine ? s.sWoff[lane + 1] : 0;
+    int val = NEG, last = 0;
+    int* row = t.Ms + static_cast<long long>(u) * N;
+    bool walking = mine && pos < end;
+    while (__any_sync(FULL_MASK, walking)) {
+        int w = 0, rv = 0, c = 0;
+        bool go = false, pick = false;
+        if (walking) {
+            w = s.sW[pos];
+            const int o = w & PACK_MASK;
+            c = o >> 1;
+            pick = o & 1;
+            if (pick && pos != u) rv = rdy[c];
+            go = !pick || pos == u || rv != UNRES;
+        }
+        __syncwarp();
+        if (go) {
+            int v = (val == NEG) ? NEG : val + (w >> PACK_SHIFT);
+            if (pick && pos != u) v = max(v, rv);
+            if (pos == u) v = 0;
+            if (!pick) rdy[c] = (v == NEG) ? NEG : v + s.sp[c];
+            row[pos] = v;
+            val = v;
+            last = c;
+            ++pos;
+        }
+        __syncwarp();
+        const unsigned prog = __ballot_sync(FULL_MASK, go);
+        if (walking) {
+            if (pos >= end) walking = false;
+            else if (prog == 0u) { walking = false; atomicExch(&t.ctl->err, DEV_BAD_STATE); }
+        }
+    }
+    int tail = (mine && val != NEG) ? val + D(t, last, 0) : NEG;
+    for (int o = 16; o > 0; o >>= 1) tail = max(tail, __shfl_xor_sync(FULL_MASK, tail, o));
+    if (lane == 0) t.T[u] = tail;
+}
+
+// Full simulation of W + D_c at gap (a,i) + P_c at gap (b,j): makespan or
+// INT32_MAX on a precedence cycle.  Travel legs next to the new stops are read
+// from the distance matrix.
+__device__ int walk_insert(const AlnsTeam& t, const Smem& s, int* rdy, int c, int a, int i, int b, int j) {
+    const int lane = threadIdx.x & 31, m = t.m, n = t.n;
+    for (int q = lane; q <= n; q += 32) rdy[q] = UNRES;
+    __syncwarp();
+    const bool mine = lane < m;
+    const int base = mine ? s.sWoff[lane] : 0;
+    const int L = mine ? s.sWoff[lane + 1] - base : 0;
+    // up to two virtual stops on this route, in route order (drop first at equal gaps)
+    int g1 = -1, o1 = 0, g2 = -1, o2 = 0;
+    if (mine) {
+        if (lane == a) { g1 = i; o1 = 2 * c; }
+        if (lane == b) {
+            if (g1 < 0) { g1 = j; o1 = 2 * c + 1; } else { g2 = j; o2 = 2 * c + 1; }
+        }
+    }
+    int k = 0, dep = 0, loc = 0, nins = 0;
+    bool prev_virtual = false, done1 = g1 < 0, done2 = g2 < 0;
+    bool walking = mine && (L > 0 || !done1);
+    bool any = walking, cyc = false;
+    while (__any_sync(FULL_MASK, walking)) {
+        int o = 0, rv = 0, cc = 0, dd = 0, which = 0;
+        bool go = false, pick = false;
+        if (walking) {
+            if (!done1 && k == g1) { o = o1; which = 1; }
+            else if (!done2 && k == g2) { o = o2; which = 2; }
+            else { o = s.sW[base + k] & PACK_MASK; which = 0; }
+            cc = o >> 1;
+            pick = o & 1;
+            if (pick) rv = rdy[cc];
+            go = !pick || rv != UNRES;
+            if (go) dd = (which != 0 || prev_virtual) ? D(t, loc, cc) : (s.sW[base + k] >> PACK_SHIFT);
+        }
+        __syncwarp();
+        if (go) {
+            const int arr = dep + dd;
+            if (pick) dep = max(arr, rv);
+            else { dep = arr; rdy[cc] = arr + s.sp[cc]; }
+            loc = cc;
+            if (which == 1) done1 = true;
+            else if (which == 2) done2 = true;
+            else ++k;
+            prev_virtual = which != 0;
+            ++nins;
+        }
+        __syncwarp();
+        const unsigned prog = __ballot_sync(FULL_MASK, go);
+        if (walking) {
+            if (k >= L && done1 && done2) walking = false;
+            else if (prog == 0u) { walking = false; cyc = true; }
+        }
+    }
+    int ret = (mine && any && !cyc) ? dep + D(t, loc, 0) : 0;
+    for (int o = 16; o > 0; o >>= 1) ret = max(ret, __shfl_xor_sync(FULL_MASK, ret, o));
+    const unsigned anycyc = __ballot_sync(FULL_MASK, cyc);
+    return anycyc ? 0x7fffffff : ret;
+}
+
+// ---------------------------------------------------------------------------
+// capacity helpers (Eqs. 13-18 with the minimal or the full start load)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool cap_ok(const AlnsTeam& t, int mn, int mx, int& load) {
+    if (t.load_full) { load = t.Q; return mn >= -t.Q && mx <= 0; }
+    mn = min(mn, 0);
+    mx = max(mx, 0);
+    load = -mn;
+    return load + mx <= t.Q;
+}
+
+__device__ __forceinline__ int range_min(const AlnsTeam& t, int lo, int hi, int N) {
+    const int len = hi - lo + 1;
+    const int l = 31 - __clz(len);
+    return min(t.spmin[l * N + lo], t.spmin[l * N + hi - (1 << l) + 1]);
+}
+__device__ __forceinline__ int range_max(const AlnsTeam& t, int lo, int hi, int N) {
+    const int len = hi - lo + 1;
+    const int l = 31 - __clz(len);
+    return max(t.spmax[l * N + lo], t.spmax[l * N + hi - (1 << l) + 1]);
+}
+
+__device__ __forceinline__ unsigned long long pack_key(int dz, int dt, int col) {
+    return (static_cast<unsigned long long>(static_cast<unsigned>(dz) ^ 0x80000000u) << 32) |
+           (static_cast<unsigned long long>(static_cast<unsigned>(dt + (1 << 19)) & 0xFFFFFu) << 12) |
+           static_cast<unsigned long long>(col & 0xFFF);
+}
+
+// Capacity + pool of one entry from the per-gap arrays (global memory).
+// Returns false when infeasible.
+__device__ bool entry_capacity(const AlnsTeam& t, int row, int col, int N) {
+    const int a = t.groute[row], i = t.gpos[row], b = t.groute[col], j = t.gpos[col];
+    int la = 0, lb = 0;
+    const int sumL = t.ctl->sum_load;
+    if (a != b) {
+        const int mnA = min(min(t.gpmin[row], t.gsb[row] - 1), t.gsmin[row] - 1);
+        const int mxA = max(t.gpmax[row], t.gsmax[row] - 1);
+        const int mnB = min(t.gpmin[col], t.gsmin[col] + 1);
+        const int mxB = max(max(t.gpmax[col], t.gsb[col] + 1), t.gsmax[col] + 1);
+        if (!cap_ok(t, mnA, mxA, la) || !cap_ok(t, mnB, mxB, lb)) return false;
+        return sumL - t.rload[a] - t.rload[b] + la + lb <= t.R;
+    }
+    if (j == i) {
+        const int mn = min(min(t.gpmin[row], t.gsb[row] - 1), t.gsmin[row]);
+        const int mx = max(t.gpmax[row], t.gsmax[row]);
+        if (!cap_ok(t, mn, mx, la)) return false;
+        return sumL - t.rload[a] + la <= t.R;
+    }
+    const int lo = t.gy[row], hi = t.gx[col];   // stock prefixes between the two gaps
+    const int mn = min(min(min(t.gpmin[row], t.gsb[row] - 1), range_min(t, lo, hi, N) - 1), t.gsmin[col]);
+    const int mx = max(max(max(t.gpmax[row], range_max(t, lo, hi, N) - 1), t.S_[hi]), t.gsmax[col]);
+    if (!cap_ok(t, mn, mx, la)) return false;
+    return sumL - t.rload[a] + la <= t.R;
+}
+
+__device__ __forceinline__ int travel_delta(const AlnsTeam& t, const Smem& s, int c, int row, int col) {
+    auto locx = [&](int g) { return t.gx[g] >= 0 ? (s.sW[t.gx[g]] & PACK_MASK) >> 1 : 0; };
+    auto locy = [&](int g) { return t.gy[g] >= 0 ? (s.sW[t.gy[g]] & PACK_MASK) >> 1 : 0; };
+    const int xr = locx(row), yr = locy(row);
+    if (t.groute[row] == t.groute[col] && t.gpos[row] == t.gpos[col])
+        return D(t, xr, c) + D(t, c, c) + D(t, c, yr) - t.gw[row];
+    const int xc = locx(col), yc = locy(col);
+    return (D(t, xr, c) + D(t, c, yr) - t.gw[row]) + (D(t, xc, c) + D(t, c, yc) - t.gw[col]);
+}
+
+// ---------------------------------------------------------------------------
+// phases
+// ---------------------------------------------------------------------------
+__device__ void phase_prep(const AlnsTeam& t, const Smem& s, int rank, int team_blocks) {
+    AlnsCtl* ctl = t.ctl;
+    stage_W(t, s);
+    const int N = s.sWoff[t.m], G = N + t.m;
+    const int warp = threadIdx.x >> 5;
+    const int team_warps = team_blocks * ALNS_WARPS;
+    const int gw = rank * ALNS_WARPS + warp;
+    int* rdy = s.rdy + warp * (((t.n + 1) + 3) & ~3);
+    for (int unit = gw; unit <= N; unit += team_warps) {
+        if (unit == 0) {
+            int z;
+            unsigned st;
+            walk_depot(t, s, rdy, true, &z, &st);
+            if ((threadIdx.x & 31) == 0) { ctl->z_work = z; ctl->st_work = st; }
+        } else {
+            walk_source(t, s, rdy, unit - 1, N);
+        }
+    }
+    // shortcut gaps and key reset for every customer still to insert
+    const int nrem = ctl->nrem;
+    const long long total = static_cast<long long>(nrem) * G;
+    const long long tid = static_cast<long long>(rank) * blockDim.x + threadIdx.x;
+    const long long nthr = static_cast<long long>(team_blocks) * blockDim.x;
+    for (long long e = tid; e < total; e += nthr) {
+        const int ti = static_cast<int>(e / G), g = static_cast<int>(e - static_cast<long long>(ti) * G);
+        const int c = t.rem[ti];
+        // gap g -> route r and position
+        int r = 0, base = 0;
+        while (r < t.m && g > base + (s.sWoff[r + 1] - s.sWoff[r])) { base += s.sWoff[r + 1] - s.sWoff[r] + 1; ++r; }
+        const int pos = g - base, L = s.sWoff[r + 1] - s.sWoff[r];
+        const int x = pos > 0 ? (s.sW[s.sWoff[r] + pos - 1] & PACK_MASK) >> 1 : 0;
+        const int y = pos < L ? (s.sW[s.sWoff[r] + pos] & PACK_MASK) >> 1 : 0;
+        const int w = (L == 0) ? 0 : D(t, x, y);
+        const bool shortcut = D(t, x, c) + D(t, c, y) < w;
+        t.keys[static_cast<long long>(ti) * G + g] = KEY_NONE;
+        t.sc[static_cast<long long>(ti) * G + g] = shortcut ? 1 : 0;
+        if (shortcut) {
+            const int slot = atomicAdd(&ctl->n_short, 1);
+            t.slist[slot] = ti * G + g;
+        }
+    }
+}
+
+__device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_blocks) {
+    const int m = t.m, N = s.sWoff[m], G = N + m;
+    const long long tid = static_cast<long long>(rank) * blockDim.x + threadIdx.x;
+    const long long nthr = static_cast<long long>(team_blocks) * blockDim.x;
+    for (long long gg = tid; gg < G; gg += nthr) {
+        const int g = static_cast<int>(gg);
+        int r = 0, base = 0;
+        while (r < m && g > base + (s.sWoff[r + 1] - s.sWoff[r])) { base += s.sWoff[r + 1] - s.sWoff[r] + 1; ++r; }
+        const int pos = g - base, off = s.sWoff[r], L = s.sWoff[r + 1] - off;
+        const int xo = pos > 0 ? off + pos - 1 : -1, yo = pos < L ? off + pos : -1;
+        const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0;
+        const int y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
+        t.gx[g] = xo;
+        t.gy[g] = yo;
+        t.gHx[g] = xo >= 0 ? t.H[xo] : 0;
+        t.gTy[g] = yo >= 0 ? t.T[yo] : 0;
+        t.gw[g] = L == 0 ? 0 : D(t, x, y);
+        t.gsb[g] = xo >= 0 ? t.S_[xo] : 0;
+        t.gpmin[g] = xo >= 0 ? t.PMINp[xo] : 0;
+        t.gpmax[g] = xo >= 0 ? t.PMAXp[xo] : 0;
+        t.gsmin[g] = yo >= 0 ? t.SMINs[yo] : (1 << 28);
+        t.gsmax[g] = yo >= 0 ? t.SMAXs[yo] : -(1 << 28);
+        t.groute[g] = r;
+        t.gpos[g] = pos;
+    }
+    if (rank == 0) {
+        // sparse tables of the stock prefix over op positions (routes are contiguous)
+        for (int k = threadIdx.x; k < N; k += blockDim.x) { t.spmin[k] = t.S_[k]; t.spmax[k] = t.S_[k]; }
+        __syncthreads();
+        for (int l = 1; (1 << l) <= N; ++l) {
+            const int h = 1 << (l - 1);
+            for (int k = threadIdx.x; k + (1 << l) <= N; k += blockDim.x) {
+                t.spmin[l * N + k] = min(t.spmin[(l - 1) * N + k], t.spmin[(l - 1) * N + k + h]);
+                t.spmax[l * N + k] = max(t.spmax[(l - 1) * N + k], t.spmax[(l - 1) * N + k + h]);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) t.ctl->work_counter = 0;
+    }
+}
+
+// One matrix tile (rows rt*TR.., cols ct*TC..) for every customer still to insert.
+__device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, int N, int G) {
+    AlnsCtl* ctl = t.ctl;
+    const int tid = threadIdx.x;
+    const int r0 = rt * TR, c0 = ct * TC;
+    // LP tile: lp[r][c] = LP(stop after row gap -> stop before col gap)
+    for (int e = tid; e < TR * TC; e += blockDim.x) {
+        const int r = e / TC, c = e - r * TC;
+        const int R = r0 + r, Cg = c0 + c;
+        int v = NEG;
+        if (R < G && Cg < G) {
+            const int ya = t.gy[R], xb = t.gx[Cg];
+            if (ya >= 0 && xb >= 0) v = t.Ms[static_cast<long long>(ya) * N + xb];
+        }
+        s.lp[r * LPS + c] = v;
+    }
+    // reach bits: stop after col gap reaches stop before row gap (would close a cycle)
+    {
+        const int warp = tid >> 5, lane = tid & 31;
+        for (int c = warp; c < TC; c += ALNS_WARPS) {
+            const int Cg = c0 + c, R = r0 + lane;
+            bool rb = false;
+            if (Cg < G && R < G) {
+                const int yb = t.gy[Cg], xa = t.gx[R];
+                if (yb >= 0 && xa >= 0) rb = t.Ms[static_cast<long long>(yb) * N + xa] > NEG;
+            }
+            const unsigned bits = __ballot_sync(FULL_MASK, rb);
+            if (lane == 0) s.reach[c] = bits;
+        }
+    }
+    const int z = ctl->z_work, sumL = ctl->sum_load;
+    const bool dump = t.mode == 1;
+    unsigned long long local_entries = 0;
+    for (int ti = 0; ti < ctl->nrem; ++ti) {
+        const int c = t.rem[ti], pc = s.sp[c];
+        const int dcc = D(t, c, c);
+        __syncthreads();
+        // row (dropoff) vectors
+        if (tid < TR) {
+            const int R = r0 + tid;
+            int* v = s.rowv + tid * RV;
+            if (R < G) {
+                const int xo = t.gx[R], yo = t.gy[R];
+                const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0, y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
+                const int dxc = D(t, x, c), dcy = D(t, c, y), Hx = t.gHx[R], Ty = t.gTy[R], w = t.gw[R];
+                const int delta = dxc + dcy;
+                int la = 0, ladj = 0;
+                const bool okA = cap_ok(t, min(min(t.gpmin[R], t.gsb[R] - 1), t.gsmin[R] - 1),
+                                        max(t.gpmax[R], t.gsmax[R] - 1), la);
+                const bool okAdj = cap_ok(t, min(min(t.gpmin[R], t.gsb[R] - 1), t.gsmin[R]),
+                                          max(t.gpmax[R], t.gsmax[R]), ladj);
+                const int ra = t.groute[R];
+                v[0] = Hx + dxc;                        // arrival at the new drop
+                v[1] = Hx + delta + Ty;                 // beta: through the drop only
+                v[2] = Hx + delta;                      // leaving the drop towards y
+                v[3] = Hx + dxc + max(dcc, pc) + dcy + Ty;  // adjacent drop+pickup
+                v[4] = delta - w;                       // travel change, drop
+                v[5] = dxc + dcc + dcy - w;             // travel change, adjacent pair
+                v[6] = okA ? la - t.rload[ra] : 1 << 28;
+                v[7] = okAdj ? ladj - t.rload[ra] : 1 << 28;
+                v[8] = ra;
+                v[9] = t.gpos[R];
+                v[10] = t.sc[static_cast<long long>(ti) * G + R];
+                v[11] = yo;
+                v[12] = t.gpmin[R];
+                v[13] = t.gsb[R];
+                v[14] = t.gpmax[R];
+            } else {
+                v[8] = -1;
+            }
+        }
+        // col (pickup) vectors
+        if (tid < TC) {
+            const int Cg = c0 + tid;
+            int* v = s.colv + tid * CV;
+            if (Cg < G) {
+                const int xo = t.gx[Cg], yo = t.gy[Cg];
+                const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0, y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
+                const int dxc = D(t, x, c), dcy = D(t, c, y), Hx = t.gHx[Cg], Ty = t.gTy[Cg], w = t.gw[Cg];
+                const int delta = dxc + dcy;
+                int lb = 0;
+                const bool okB = cap_ok(t, min(t.gpmin[Cg], t.gsmin[Cg] + 1),
+                                        max(max(t.gpmax[Cg], t.gsb[Cg] + 1), t.gsmax[Cg] + 1), lb);
+                const int rb = t.groute[Cg];
+                v[0] = Hx + delta + Ty;                 // gamma: through the pickup only
+                v[1] = dcy + Ty;                        // leaving the pickup
+                v[2] = delta + Ty;                      // entering the pickup from x
+                v[3] = delta - w;                       // travel change, pickup
+                v[4] = okB ? lb - t.rload[rb] : 1 << 28;
+                v[5] = rb;
+                v[6] = t.gpos[Cg];
+                v[7] = t.sc[static_cast<long long>(ti) * G + Cg];
+                v[8] = xo;
+                v[9] = t.gsmin[Cg];
+                v[10] = t.gsmax[Cg];
+            } else {
+                v[5] = -1;
+            }
+        }
+        __syncthreads();
+        const int r = tid >> 3, cb = tid & 7;
+        const int* rv = s.rowv + r * RV;
+        unsigned long long best = KEY_NONE;
+        if (rv[8] >= 0) {
+            const int R = r0 + r;
+            const int A1 = rv[0], beta = rv[1], E = rv[2], adjv = rv[3], dtD = rv[4], dtAdj = rv[5];
+            const int dLA = rv[6], dLAdj = rv[7], ra = rv[8], ia = rv[9];
+            const bool scR = rv[10] != 0;
+            const unsigned rbit = 1u << r;
+            for (int kk = 0; kk < TC / 8; ++kk) {
+                const int cc = cb + 8 * kk;
+                const int* cv = s.colv + cc * CV;
+                const int rb = cv[5];
+                if (rb < 0) continue;
+                const int Cg = c0 + cc, jb = cv[6];
+                if (scR || cv[7] != 0) continue;          // shortcut gap: re-simulated in full
+                int znew = 0, dt = 0;
+                bool ok;
+                if (ra == rb) {
+                    if (jb < ia) {
+                        ok = false;
+                    } else if (jb == ia) {
+                        ok = dLAdj < (1 << 27) && sumL + dLAdj <= t.R;
+                        znew = max(z, adjv);
+                        dt = dtAdj;
+                    } else {
+                        const int lo = rv[11], hi = cv[8];
+                        const int mn = min(min(min(rv[12], rv[13] - 1), range_min(t, lo, hi, N) - 1), cv[9]);
+                        const int mx = max(max(max(rv[14], range_max(t, lo, hi, N) - 1), t.S_[hi]), cv[10]);
+                        int l2 = 0;
+                        ok = cap_ok(t, mn, mx, l2) && sumL - t.rload[ra] + l2 <= t.R;
+                        const int lpv = s.lp[r * LPS + cc];
+                        znew = max(max(max(z, beta), cv[0]), max(A1 + pc + cv[1], E + lpv + cv[2]));
+                        dt = dtD + cv[3];
+                    }
+                } else {
+                    ok = (s.reach[cc] & rbit) == 0u && dLA < (1 << 27) && cv[4] < (1 << 27) &&
+                         sumL + dLA + cv[4] <= t.R;
+                    const int lpv = s.lp[r * LPS + cc];
+                    znew = max(max(z, beta), max(cv[0], A1 + pc + cv[1]));
+                    if (lpv != NEG) znew = max(znew, E + lpv + cv[2]);
+                    dt = dtD + cv[3];
+                }
+                ++local_entries;
+                if (dump) {
+                    const long long idx = static_cast<long long>(R) * G + Cg;
+                    t.dump_delta[idx] = ok ? znew - z : 0x7fffffff;
+                    t.dump_travel[idx] = ok ? dt : 0;
+                } else if (ok) {
+                    const unsigned long long key = pack_key(znew - z, dt, Cg);
+                    best = key < best ? key : best;
+                }
+            }
+        }
+        // min over the 8 lanes sharing a row
+        for (int o = 4; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(FULL_MASK, best, o);
+            best = other < best ? other : best;
+        }
+        if (!dump && cb == 0 && best != KEY_NONE)
+            atomicMin(&t.keys[static_cast<long long>(ti) * G + r0 + r], best);
+    }
+    atomicAdd(&ctl->entries, local_entries);
+}
+
+// Fallback item: entries of one shortcut gap (as drop row or pickup column), one warp each.
+__device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N, int G) {
+    AlnsCtl* ctl = t.ctl;
+    const int chunks = (G + FB_CHUNK - 1) / FB_CHUNK;
+    const int e = item / (2 * chunks), rest = item - e * 2 * chunks;
+    const int as_col = rest / chunks, chunk = rest - as_col * chunks;
+    const int packed = t.slist[e];
+    const int ti = packed / G, g = packed - ti * G;
+    const int c = t.rem[ti];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int* rdy = s.rdy + warp * (((t.n + 1) + 3) & ~3);
+    const int z = ctl->z_work;
+    unsigned long long cnt = 0;
+    for (int k = chunk * FB_CHUNK + warp; k < min(G, (chunk + 1) * FB_CHUNK); k += ALNS_WARPS) {
+        const int row = as_col ? k : g, col = as_col ? g : k;
+        if (as_col && t.sc[static_cast<long long>(ti) * G + row]) continue;  // that row item covers it
+        const int a = t.groute[row], i = t.gpos[row], b = t.groute[col], j = t.gpos[col];
+        if (a == b && j < i) {
+            if (t.mode == 1 && lane == 0) {
+                t.dump_delta[static_cast<long long>(row) * G + col] = 0x7fffffff;
+                t.dump_travel[static_cast<long long>(row) * G + col] = 0;
+            }
+            continue;
+        }
+        const bool capok = entry_capacity(t, row, col, N);
+        const int zn = walk_insert(t, s, rdy, c, a, i, b, j);
+        ++cnt;
+        const bool ok = capok && zn != 0x7fffffff;
+        if (lane == 0) {
+            const int dt = travel_delta(t, s, c, row, col);
+            if (t.mode == 1) {
+                t.dump_delta[static_cast<long long>(row) * G + col] = ok ? zn - z : 0x7fffffff;
+                t.dump_travel[static_cast<long long>(row) * G + col] = ok ? dt : 0;
+            } else if (ok) {
+                atomicMin(&t.keys[static_cast<long long>(ti) * G + row], pack_key(zn - z, dt, col));
+            }
+        }
+    }
+    if (lane == 0 && cnt) atomicAdd(&ctl->fallback_entries, cnt);
+}
+
+__device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
+    AlnsCtl* ctl = t.ctl;
+    const int N = s.sWoff[t.m], G = N + t.m;
+    const int RT = (G + TR - 1) / TR, CT = (G + TC - 1) / TC;
+    const int tiles = RT * CT;
+    const int chunks = (G + FB_CHUNK - 1) / FB_CHUNK;
+    const int total = tiles + ctl->n_short * 2 * chunks;
+    int* slot = s.misc;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) slot[0] = atomicAdd(&ctl->work_counter, 1);
+        __syncthreads();
+        const int item = slot[0];
+        if (item >= total) break;
+        if (item < tiles) matrix_tile(t, s, item / CT, item - (item / CT) * CT, N, G);
+        else fallback_item(t, s, item - tiles, N, G);
+    }
+}
+
+// Rank 0: per-customer argmin, greedy / regret-2 choice, apply to W.
+__device__ void phase_select(const AlnsTeam& t, const Smem& s) {
+    AlnsCtl* ctl = t.ctl;
+    const int m = t.m, N = s.sWoff[m], G = N + m, nrem = ctl->nrem;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // per-customer results live in the (now free) tile buffer: best at [0, 1024), regret after
+    unsigned long long* bestv = reinterpret_cast<unsigned long long*>(s.lp);        // [nrem]
+    long long* regret = reinterpret_cast<long long*>(s.lp) + 1024;                 // [nrem]
+    for (int ti = warp; ti < nrem; ti += ALNS_WARPS) {
+        const unsigned long long* kr = t.keys + static_cast<long long>(ti) * G;
+        unsigned long long bv = KEY_NONE;
+        for (int g = lane; g < G; g += 32) {
+            const unsigned long long k = kr[g];
+            if (k == KEY_NONE) continue;
+            const unsigned long long v = ((k >> 12) << 12) | static_cast<unsigned long long>(g);
+            bv = v < bv ? v : bv;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(FULL_MASK, bv, o);
+            bv = other < bv ? other : bv;
+        }
+        // per drop-vehicle best makespan delta (regret-2 options)
+        long long c1 = REGRET_INF, c2 = REGRET_INF;
+        int gbase = 0;
+        for (int v = 0; v < m; ++v) {
+            const int Lv = s.sWoff[v + 1] - s.sWoff[v];
+            unsigned long long bvv = KEY_NONE;
+            for (int g = gbase + lane; g <= gbase + Lv; g += 32) {
+                const unsigned long long k = kr[g];
+                const unsigned long long vv = k == KEY_NONE ? KEY_NONE : (((k >> 12) << 12) | static_cast<unsigned long long>(g));
+                bvv = vv < bvv ? vv : bvv;
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(FULL_MASK, bvv, o);
+                bvv = other < bvv ? other : bvv;
+            }
+            if (bvv != KEY_NONE) {
+                const long long cv = static_cast<long long>(static_cast<int>(static_cast<unsigned>(bvv >> 32) ^ 0x80000000u));
+                if (cv < c1) { c2 = c1; c1 = cv; } else if (cv < c2) { c2 = cv; }
+            }
+            gbase += Lv + 1;
+        }
+        if (lane == 0) {
+            bestv[ti] = bv;
+            regret[ti] = c2 - c1;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int pick = -1;
+        bool fail = false;
+        for (int ti = 0; ti < nrem; ++ti) {
+            if (bestv[ti] == KEY_NONE) { fail = true; break; }
+            if (pick < 0) { pick = ti; continue; }
+            if (ctl->rj == 0) {
+                const unsigned long long a = bestv[ti], b = bestv[pick];
+                const int rowa = static_cast<int>(a & 0xFFF), rowb = static_cast<int>(b & 0xFFF);
+                const unsigned long long ka = t.keys[static_cast<long long>(ti) * G + rowa];
+                const unsigned long long kb = t.keys[static_cast<long long>(pick) * G + rowb];
+                // (dz, dt) then flat index row*G + col
+                const unsigned long long pa = a >> 12, pb = b >> 12;
+                if (pa != pb) { if (pa < pb) pick = ti; }
+                else {
+                    const long long fa = static_cast<long long>(rowa) * G + static_cast<long long>(ka & 0xFFF);
+                    const long long fb = static_cast<long long>(rowb) * G + static_cast<long long>(kb & 0xFFF);
+                    if (fa < fb) pick = ti;
+                }
+            } else {
+                if (regret[ti] > regret[pick]) pick = ti;
+            }
+        }
+        if (fail || pick < 0) {
+            ctl->repair_fail = 1;
+        } else {
+            const int row = static_cast<int>(bestv[pick] & 0xFFF);
+            const int col = static_cast<int>(t.keys[static_cast<long long>(pick) * G + row] & 0xFFF);
+            ctl->pick_t = pick;
+            ctl->pick_row = row;
+            ctl->pick_col = col;
+        }
+    }
+    __syncthreads();
+    if (ctl->repair_fail) return;
+    // apply: route-parallel copy into the other W buffer
+    const int pick = ctl->pick_t, row = ctl->pick_row, col = ctl->pick_col;
+    const int c = t.rem[pick];
+    const int a = t.groute[row], i = t.gpos[row], b = t.groute[col], j = t.gpos[col];
+    const int* W = t.W_ops[ctl->wsel];
+    int* Wn = t.W_ops[ctl->wsel ^ 1];
+    int* Won = t.W_off[ctl->wsel ^ 1];
+    if (threadIdx.x < m) {
+        const int v = threadIdx.x;
+        const int before = (a < v ? 1 : 0) + (b < v ? 1 : 0);
+        int w = s.sWoff[v] + before;
+        const int L = s.sWoff[v + 1] - s.sWoff[v];
+        for (int k = 0; k <= L; ++k) {
+            if (v == a && k == i) Wn[w++] = 2 * c;
+            if (v == b && k == j) Wn[w++] = 2 * c + 1;
+            if (k < L) Wn[w++] = W[s.sWoff[v] + k];
+        }
+    }
+    if (threadIdx.x <= m) {
+        const int v = threadIdx.x;
+        Won[v] = s.sWoff[v] + (a < v ? 1 : 0) + (b < v ? 1 : 0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = pick; k + 1 < nrem; ++k) t.rem[k] = t.rem[k + 1];
+        ctl->nrem = nrem - 1;
+        ctl->wsel ^= 1;
+        ctl->n_short = 0;
+    }
+    __syncthreads();
+}
+
+// roulette wheel over enabled operators (fp64, explicit rounding)
+__device__ int roulette(const double* w, const int* en, int k, double u) {
+    double sum = 0.0;
+    for (int i = 0; i < k; ++i)
+        if (en[i]) sum = __dadd_rn(sum, w[i]);
+    const double target = __dmul_rn(u, sum);
+    double acc = 0.0;
+    int last = -1;
+    for (int i = 0; i < k; ++i) {
+        if (!en[i]) continue;
+        acc = __dadd_rn(acc, w[i]);
+        last = i;
+        if (target < acc) return i;
+    }
+    return last;
+}
+
+// Rank 0: operator choice, q, random removal (partial Fisher-Yates), W = cur - removed.
+__device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
+    AlnsCtl* ctl = t.ctl;
+    const int n = t.n, m = t.m;
+    if (threadIdx.x == 0) {
+        const int it = ctl->iter;
+        const unsigned long long base = static_cast<unsigned long long>(it) << 16;
+        const int en_d[1] = {1};
+        const int en_r[2] = {(t.repair_mask & 1) != 0, (t.repair_mask & 2) != 0};
+        ctl->di = roulette(ctl->wd, en_d, 1, draw_unit(draw(t.key, base + 0)));
+        ctl->rj = roulette(ctl->wr, en_r, 2, draw_unit(draw(t.key, base + 1)));
+        ctl->ad[ctl->di] += 1;
+        ctl->ar[ctl->rj] += 1;
+        const int q = t.q_min + draw_below(draw(t.key, base + 2), t.q_max - t.q_min + 1);
+        ctl->q = q;
+        for (int k = 0; k < n; ++k) t.perm[k] = k + 1;
+        for (int k = 0; k < q; ++k) {
+            const int jj = k + draw_below(draw(t.key, base + 16 + static_cast<unsigned long long>(k)), n - k);
+            const int tmp = t.perm[k];
+            t.perm[k] = t.perm[jj];
+            t.perm[jj] = tmp;
+        }
+        ctl->repair_fail = 0;
+        ctl->n_short = 0;
+        ctl->work_counter = 0;
+    }
+    __syncthreads();
+    const int q = ctl->q;
+    for (int c = threadIdx.x; c <= n; c += blockDim.x) s.flags[c] = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < q; k += blockDim.x) s.flags[t.perm[k]] = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int w = 0;
+        for (int c = 1; c <= n; ++c)
+            if (s.flags[c]) t.rem[w++] = c;
+        ctl->nrem = w;
+    }
+    // W = cur without removed customers: one thread per route for the copy
+    int* Wn = t.W_ops[0];
+    int* Won = t.W_off[0];
+    int* cnt = s.misc;
+    if (threadIdx.x < m) {
+        const int v = threadIdx.x;
+        int k2 = 0;
+        for (int k = t.cur_off[v]; k < t.cur_off[v + 1]; ++k)
+            if (!s.flags[t.cur_ops[k] >> 1]) ++k2;
+        cnt[v] = k2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        Won[0] = 0;
+        for (int v = 0; v < m; ++v) Won[v + 1] = Won[v] + cnt[v];
+        ctl->wsel = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        const int v = threadIdx.x;
+        int w = Won[v];
+        for (int k = t.cur_off[v]; k < t.cur_off[v + 1]; ++k)
+            if (!s.flags[t.cur_ops[k] >> 1]) Wn[w++] = t.cur_ops[k];
+    }
+    __syncthreads();
+}
+
+// Rank 0: evaluate the repaired W and apply Algorithm 1's acceptance, cooling,
+// reheat and weight update.  With first = true only records the start.
+__device__ void phase_end(const AlnsTeam& t, const Smem& s, bool first) {
+    AlnsCtl* ctl = t.ctl;
+    const int n = t.n, m = t.m;
+    stage_W(t, s);
+    int* rdy = s.rdy;
+    if ((threadIdx.x >> 5) == 0) {
+        int z;
+        unsigned st;
+        walk_depot(t, s, rdy, false, &z, &st);
+        if ((threadIdx.x & 31) == 0) {
+            if (ctl->repair_fail) { z = 0x7fffffff; st = VRPRPD_MALFORMED; }
+            ctl->z_work = z;
+            ctl->st_work = st;
+        }
+    }
+    __syncthreads();
+    int* decision = s.misc;
+    if (threadIdx.x == 0) {
+        const int zn = ctl->z_work;
+        const unsigned st = ctl->st_work;
+        int accept = 0, newbest = 0;
+        if (first) {
+            accept = 1;
+            newbest = 1;
+            ctl->z_cur = zn;
+            ctl->z_best = zn;
+            ctl->z_init = zn;
+            ctl->T = __dmul_rn(t.T0, static_cast<double>(zn));
+            ctl->T_init = ctl->T;
+            if (st != 0u) atomicExch(&ctl->err, DEV_BAD_STATE);
+        } else {
+            const int it = ctl->iter;
+            const unsigned long long base = static_cast<unsigned long long>(it) << 16;
+            const int di = ctl->di, rj = ctl->rj;
+            if (st != 0u) {
+                ctl->rejected += 1;
+            } else if (zn < ctl->z_cur) {
+                accept = 1;
+                ctl->z_cur = zn;
+                ctl->sd[di] += t.sigma2;
+                ctl->sr[rj] += t.sigma2;
+                ctl->improved += 1;
+                ctl->accepted += 1;
+                if (zn < ctl->z_best) {
+                    newbest = 1;
+                    ctl->z_best = zn;
+                    ctl->sd[di] += t.sigma1 - t.sigma2;
+                    ctl->sr[rj] += t.sigma1 - t.sigma2;
+                    ctl->stagnation = 0;
+                    ctl->new_best += 1;
+                }
+            } else {
+                const double x = -__ddiv_rn(static_cast<double>(static_cast<long long>(zn) - ctl->z_cur), ctl->T);
+                const double u = draw_unit(draw(t.key, base + 3));
+                if (u < exp_sa(x)) {
+                    accept = 1;
+                    ctl->z_cur = zn;
+                    ctl->sd[di] += t.sigma3;
+                    ctl->sr[rj] += t.sigma3;
+                    ctl->accepted += 1;
+                }
+            }
+            ctl->T = __dmul_rn(t.alpha, ctl->T);
+            ctl->stagnation += 1;
+            if (ctl->stagnation >= t.stagnation_limit && ctl->T < __dmul_rn(0.01, ctl->T_init)) {
+                ctl->T = __dmul_rn(__dmul_rn(t.reheat, t.T0), static_cast<double>(ctl->z_best));
+                ctl->stagnation = 0;
+                ctl->reheats += 1;
+            }
+            if (it % t.tau == 0) {
+                for (int i = 0; i < 1; ++i) {
+                    const double ratio = ctl->ad[i] ? __ddiv_rn(static_cast<double>(ctl->sd[i]), static_cast<double>(ctl->ad[i])) : 0.0;
+                    const double w = __dadd_rn(__dmul_rn(__dsub_rn(1.0, t.r), ctl->wd[i]), __dmul_rn(t.r, ratio));
+                    ctl->wd[i] = w < t.w_min ? t.w_min : w;
+                    ctl->sd[i] = 0;
+                    ctl->ad[i] = 0;
+                }
+                for (int i = 0; i < 2; ++i) {
+                    const double ratio = ctl->ar[i] ? __ddiv_rn(static_cast<double>(ctl->sr[i]), static_cast<double>(ctl->ar[i])) : 0.0;
+                    const double w = __dadd_rn(__dmul_rn(__dsub_rn(1.0, t.r), ctl->wr[i]), __dmul_rn(t.r, ratio));
+                    ctl->wr[i] = w < t.w_min ? t.w_min : w;
+                    ctl->sr[i] = 0;
+                    ctl->ar[i] = 0;
+                }
+            }
+            if (t.trace) t.trace[it - 1] = ctl->z_cur;
+        }
+        decision[0] = accept;
+        decision[1] = newbest;
+    }
+    __syncthreads();
+    const int accept = decision[0], newbest = decision[1];
+    const int* W = t.W_ops[ctl->wsel];
+    const int* Wo = t.W_off[ctl->wsel];
+    if (accept && !first) {
+        for (int k = threadIdx.x; k < 2 * n; k += blockDim.x) t.cur_ops[k] = W[k];
+        for (int v = threadIdx.x; v <= m; v += blockDim.x) t.cur_off[v] = Wo[v];
+    }
+    if (newbest) {
+        for (int k = threadIdx.x; k < 2 * n; k += blockDim.x) t.best_ops[k] = W[k];
+        for (int v = threadIdx.x; v <= m; v += blockDim.x) t.best_off[v] = Wo[v];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(ALNS_THREADS) alns_kernel(AlnsTeam* teams, int team_blocks) {
+    extern __shared__ __align__(16) int smem_alns[];
+    __shared__ AlnsTeam team_s;
+    const int team = blockIdx.x / team_blocks, rank = blockIdx.x - team * team_blocks;
+    if (threadIdx.x == 0) team_s = teams[team];
+    __syncthreads();
+    const AlnsTeam& t = team_s;
+    AlnsCtl* ctl = t.ctl;
+    const Smem s = carve(smem_alns, t.n, t.m);
+    for (int c = threadIdx.x; c <= t.n; c += blockDim.x) s.sp[c] = t.p[c];
+    unsigned gen = 0;
+    __syncthreads();
+
+    if (t.mode == 1) {
+        // one-customer matrix dump on the partial solution already in W[0]
+        if (!team_barrier(ctl, team_blocks, gen)) return;
+        phase_prep(t, s, rank, team_blocks);
+        if (!team_barrier(ctl, team_blocks, gen)) return;
+        phase_gaps(t, s, rank, team_blocks);
+        if (!team_barrier(ctl, team_blocks, gen)) return;
+        phase_matrix(t, s);
+        team_barrier(ctl, team_blocks, gen);
+        return;
+    }
+    // start: W = cur, evaluate
+    if (rank == 0) {
+        for (int k = threadIdx.x; k < 2 * t.n; k += blockDim.x) t.W_ops[0][k] = t.cur_ops[k];
+        for (int v = threadIdx.x; v <= t.m; v += blockDim.x) t.W_off[0][v] = t.cur_off[v];
+        if (threadIdx.x == 0) ctl->wsel = 0;
+        __syncthreads();
+        phase_end(t, s, true);
+    }
+    if (!team_barrier(ctl, team_blocks, gen)) return;
+    for (int it = 1; it <= t.iterations; ++it) {
+        if (rank == 0) {
+            if (threadIdx.x == 0) ctl->iter = it;
+            __syncthreads();
+            phase_begin(t, s);
+        }
+        if (!team_barrier(ctl, team_blocks, gen)) return;
+        while (true) {
+            const int nrem = *reinterpret_cast<volatile int*>(&ctl->nrem);
+            const int fail = *reinterpret_cast<volatile int*>(&ctl->repair_fail);
+            if (nrem == 0 || fail) break;
+            phase_prep(t, s, rank, team_blocks);
+            if (!team_barrier(ctl, team_blocks, gen)) return;
+            phase_gaps(t, s, rank, team_blocks);
+            if (!team_barrier(ctl, team_blocks, gen)) return;
+            phase_matrix(t, s);
+            if (!team_barrier(ctl, team_blocks, gen)) return;
+            if (rank == 0) phase_select(t, s);
+            if (!team_barrier(ctl, team_blocks, gen)) return;
+        }
+        if (rank == 0) phase_end(t, s, false);
+        if (!team_barrier(ctl, team_blocks, gen)) return;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    char* base = nullptr;
+    size_t used = 0, cap = 0;
+    template <class T>
+    T* take(size_t count) {
+        size_t bytes = (count * sizeof(T) + 255) & ~static_cast<size_t>(255);
+        T* p = reinterpret_cast<T*>(base + used);
+        used += bytes;
+        return p;
+    }
+};
+
+static size_t team_bytes(int n, int m, int qmax, int iterations, bool dump) {
+    const size_t N = 2ull * n, G = N + m;
+    int levels = 1;
+    while ((1ull << levels) <= N) ++levels;
+    size_t w = 0;
+    auto add = [&](size_t count, size_t sz) { w += (count * sz + 255) & ~static_cast<size_t>(255); };
+    add(1, sizeof(AlnsCtl));
+    add(N, 4); add(m + 1, 4); add(N, 4); add(m + 1, 4);
+    add(N + 2, 4); add(m + 1, 4); add(N + 2, 4); add(m + 1, 4);
+    add(n + 1, 4); add(n + 1, 4);
+    add(N, 4); add(N, 4); add(N * N, 4);
+    for (int i = 0; i < 5; ++i) add(N, 4);
+    add(levels * N, 4); add(levels * N, 4);
+    for (int i = 0; i < 12; ++i) add(G, 4);
+    add(m, 4);
+    add(static_cast<size_t>(qmax) * G, 8);
+    add(static_cast<size_t>(qmax) * G, 1);
+    add(static_cast<size_t>(qmax) * G, 4);
+    add(std::max(iterations, 1), 4);
+    if (dump) { add(G * G, 4); add(G * G, 4); }
+    return w;
+}
+
+static void carve_team(AlnsTeam& t, DevBuf& B, int n, int m, int qmax, int iterations, bool dump) {
+    const size_t N = 2ull * n, G = N + m;
+    int levels = 1;
+    while ((1ull << levels) <= N) ++levels;
+    t.ctl = B.take<AlnsCtl>(1);
+    t.cur_ops = B.take<int>(N); t.cur_off = B.take<int>(m + 1);
+    t.best_ops = B.take<int>(N); t.best_off = B.take<int>(m + 1);
+    t.W_ops[0] = B.take<int>(N + 2); t.W_off[0] = B.take<int>(m + 1);
+    t.W_ops[1] = B.take<int>(N + 2); t.W_off[1] = B.take<int>(m + 1);
+    t.rem = B.take<int>(n + 1); t.perm = B.take<int>(n + 1);
+    t.H = B.take<int>(N); t.T = B.take<int>(N); t.Ms = B.take<int>(N * N);
+    t.S_ = B.take<int>(N); t.PMINp = B.take<int>(N); t.PMAXp = B.take<int>(N);
+    t.SMINs = B.take<int>(N); t.SMAXs = B.take<int>(N);
+    t.spmin = B.take<int>(levels * N); t.spmax = B.take<int>(levels * N);
+    t.log_levels = levels;
+    t.gx = B.take<int>(G); t.gy = B.take<int>(G); t.gHx = B.take<int>(G); t.gTy = B.take<int>(G);
+    t.gw = B.take<int>(G); t.gsb = B.take<int>(G); t.gpmin = B.take<int>(G); t.gpmax = B.take<int>(G);
+    t.gsmin = B.take<int>(G); t.gsmax = B.take<int>(G); t.groute = B.take<int>(G); t.gpos = B.take<int>(G);
+    t.rload = B.take<int>(m);
+    t.keys = B.take<unsigned long long>(static_cast<size_t>(qmax) * G);
+    t.sc = B.take<unsigned char>(static_cast<size_t>(qmax) * G);
+    t.slist = B.take<int>(static_cast<size_t>(qmax) * G);
+    t.trace = B.take<int>(std::max(iterations, 1));
+    t.dump_delta = dump ? B.take<int>(G * G) : nullptr;
+    t.dump_travel = dump ? B.take<int>(G * G) : nullptr;
+}
+
+bool alns_supported(const vrprpd_instance* I, std::string* why) {
+    if (I->m > 32) { *why = "ALNS needs m <= 32"; return false; }
+    if (2 * I->n + I->m > 4096) { *why = "ALNS needs 2n + m <= 4096"; return false; }
+    if (I->maxd >= (1 << 17)) { *why = "ALNS needs max d < 2^17"; return false; }
+    return true;
+}
+
+static int choose_team_blocks(const vrprpd_instance* I, int requested, size_t smem, int* out) {
+    int occ = 0;
+    VRP_CUDA(cudaFuncSetAttribute(alns_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alns_kernel, ALNS_THREADS, smem));
+    VRP_CHECK(occ > 0, VRPRPD_EINVAL, "ALNS block does not fit on an SM (n=%d)", I->n);
+    const int maxb = occ * I->num_sms;
+    int tb = requested;
+    if (tb <= 0) {
+        // about one tile of the first step's matrix per CTA, at least one CTA
+        const long long G = 2ll * I->n + I->m;
+        const long long tiles = ((G + TR - 1) / TR) * ((G + TC - 1) / TC);
+        tb = static_cast<int>(std::min<long long>(tiles, maxb));
+        if (G < 256) tb = 1;
+    }
+    *out = std::max(1, std::min(tb, maxb));
+    return VRPRPD_OK;
+}
+
+static int launch_alns(const vrprpd_instance* I, AlnsTeam* d_teams, int nteams, int team_blocks, size_t smem,
+                       cudaStream_t stream) {
+    void* args[] = {&d_teams, &team_blocks};
+    const int grid = nteams * team_blocks;
+    if (team_blocks > 1) {
+        VRP_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&alns_kernel), dim3(grid),
+                                             dim3(ALNS_THREADS), args, smem, stream));
+    } else {
+        alns_kernel<<<grid, ALNS_THREADS, smem, stream>>>(d_teams, team_blocks);
+        VRP_CUDA(cudaGetLastError());
+    }
+    return VRPRPD_OK;
+}
+
+}  // namespace vrp
+
+using namespace vrp;
+
+extern "C" void vrprpd_alns_params_default(vrprpd_alns_params* P) {
+    if (!P) return;
+    P->T0 = 0.30;
+    P->alpha = 0.9998;
+    P->reheat = 0.50;
+    P->r = 0.1;
+    P->stagnation = 2000;
+    P->tau = 100;
+    P->sigma1 = 33;
+    P->sigma2 = 9;
+    P->sigma3 = 13;
+    P->w_min = 0.1;
+    P->q_min = 0;
+    P->q_max = 0;
+    P->iterations = 1000;
+    P->repair_mask = 3;
+    P->team_blocks = 0;
+}
+
+// exact angular order around the depot: half plane, then cross product, then id
+static bool angle_less(const std::vector<int32_t>& xy, int a, int b) {
+    const long long ax = xy[2 * a] - xy[0], ay = xy[2 * a + 1] - xy[1];
+    const long long bx = xy[2 * b] - xy[0], by = xy[2 * b + 1] - xy[1];
+    const int ha = (ay < 0 || (ay == 0 && ax < 0)) ? 1 : 0, hb = (by < 0 || (by == 0 && bx < 0)) ? 1 : 0;
+    if (ha != hb) return ha < hb;
+    const long long cr = ax * by - ay * bx;
+    if (cr != 0) return cr > 0;
+    return a < b;
+}
+
+extern "C" int vrprpd_initial_solution(const vrprpd_instance* I, vrprpd_solution* out) {
+    VRP_CHECK(I && out && out->ops && out->off, VRPRPD_EINVAL, "NULL argument");
+    VRP_CHECK(I->R >= 1 && I->Q >= 1, VRPRPD_EINVAL, "initial solution needs R >= 1 and Q >= 1");
+    const int n = I->n, m = I->m, N1 = n + 1;
+    std::vector<int> order(n);
+    for (int k = 0; k < n; ++k) order[k] = k + 1;
+    if (I->has_coords)
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return angle_less(I->h_coords, a, b); });
+    const int mact = std::min(m, I->R);
+    const int b = std::max(1, std::min(I->Q, I->R / mact));
+    long long W = 0;
+    for (int k = 0; k < n; ++k) W += 2ll * I->h_d[order[k]] + I->h_p[order[k]];
+    std::vector<int> sector(n);
+    long long cum = 0;
+    for (int k = 0; k < n; ++k) {
+        const long long w = 2ll * I->h_d[order[k]] + I->h_p[order[k]];
+        long long s = W > 0 ? ((2 * cum + w) * mact) / (2 * W) : (static_cast<long long>(k) * mact) / n;
+        sector[k] = static_cast<int>(std::min<long long>(s, mact - 1));
+        cum += w;
+    }
+    (void)N1;
+    int w = 0;
+    out->off[0] = 0;
+    for (int v = 0; v < m; ++v) {
+        std::vector<int> mine;
+        for (int k = 0; k < n; ++k)
+            if (sector[k] == v) mine.push_back(order[k]);
+        for (size_t s = 0; s < mine.size(); s += b) {
+            const size_t e = std::min(mine.size(), s + b);
+            for (size_t q = s; q < e; ++q) out->ops[w++] = 2 * mine[q];
+            for (size_t q = s; q < e; ++q) out->ops[w++] = 2 * mine[q] + 1;
+        }
+        out->off[v + 1] = w;
+    }
+    out->makespan = 0;
+    out->status = 0;
+    return VRPRPD_OK;
+}
+
+static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const vrprpd_alns_params* P,
+                    uint64_t seed, int mode, int dump_c, const int32_t* dump_ops, const int32_t* dump_off,
+                    vrprpd_solution* best, vrprpd_solution* current, vrprpd_alns_stats* stats, int32_t* trace,
+                    int32_t* dump_delta, int32_t* dump_travel, cudaStream_t stream) {
+    std::string why;
+    VRP_CHECK(alns_supported(I, &why), VRPRPD_EINVAL, "%s", why.c_str());
+    const int n = I->n, m = I->m;
+    int qmin = P->q_min, qmax = P->q_max;
+    if (qmin <= 0 || qmax <= 0) {
+        qmax = std::max(4, static_cast<int>(static_cast<long long>(n) * 5 / 100));
+        qmin = std::max(4, qmax / 2);
+    }
+    qmax = std::min(qmax, n);
+    qmin = std::min(qmin, qmax);
+    VRP_CHECK(qmin >= 1 && qmax <= 1024, VRPRPD_EINVAL, "removal size must lie in [1, 1024] (q_min=%d q_max=%d)",
+              qmin, qmax);
+    const int iters = mode == 1 ? 0 : P->iterations;
+    VRP_CHECK(iters >= 0 && iters <= (1 << 24), VRPRPD_EINVAL, "iterations out of range");
+    VRP_CHECK(P->tau >= 1, VRPRPD_EINVAL, "tau must be >= 1");
+    const bool dump = mode == 1;
+    const int qcap = dump ? 1 : qmax;
+    DevBuf B;
+    B.cap = team_bytes(n, m, qcap, iters, dump) + 4096;
+    VRP_CUDA(cudaMalloc(&B.base, B.cap));
+    AlnsTeam t{};
+    t.n = n;
+    t.m = m;
+    t.R = I->R;
+    t.Q = I->Q;
+    t.load_full = (I->flags & VRPRPD_LOAD_FULL) != 0;
+    t.d32 = I->d32;
+    t.p = I->p;
+    t.T0 = P->T0;
+    t.alpha = P->alpha;
+    t.reheat = P->reheat;
+    t.r = P->r;
+    t.w_min = P->w_min;
+    t.stagnation_limit = P->stagnation;
+    t.tau = P->tau;
+    t.sigma1 = P->sigma1;
+    t.sigma2 = P->sigma2;
+    t.sigma3 = P->sigma3;
+    t.q_min = qmin;
+    t.q_max = qmax;
+    t.iterations = iters;
+    t.repair_mask = P->repair_mask & 3;
+    VRP_CHECK(t.repair_mask != 0, VRPRPD_EINVAL, "repair_mask enables no repair operator");
+    t.key = stream_key(seed, RNG_STREAM_ALNS);
+    t.mode = mode;
+    t.dump_c = dump_c;
+    carve_team(t, B, n, m, qcap, iters, dump);
+    auto cleanup = [&]() { cudaFree(B.base); };
+    AlnsCtl ctl{};
+    ctl.wd[0] = 1.0;
+    ctl.wr[0] = ctl.wr[1] = 1.0;
+    if (dump) {
+        ctl.nrem = 1;
+        ctl.wsel = 0;
+    }
+    cudaError_t e = cudaMemcpyAsync(t.ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, stream);
+    std::vector<int32_t> init_ops(2 * n), init_off(m + 1);
+    if (!dump) {
+        if (init) {
+            std::memcpy(init_ops.data(), init->ops, 2 * n * 4);
+            std::memcpy(init_off.data(), init->off, (m + 1) * 4);
+        } else {
+            vrprpd_solution s{init_ops.data(), init_off.data(), 0, 0};
+            int rc = vrprpd_initial_solution(I, &s);
+            if (rc) { cleanup(); return rc; }
+        }
+        if (e == cudaSuccess) e = cudaMemcpyAsync(t.cur_ops, init_ops.data(), 2 * n * 4, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(t.cur_off, init_off.data(), (m + 1) * 4, cudaMemcpyHostToDevice, stream);
+    } else {
+        const int Nops = dump_off[m];
+        if (e == cudaSuccess) e = cudaMemcpyAsync(t.W_ops[0], dump_ops, std::max(Nops, 1) * 4, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(t.W_off[0], dump_off, (m + 1) * 4, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(t.rem, &dump_c, 4, cudaMemcpyHostToDevice, stream);
+        const size_t G = static_cast<size_t>(Nops) + m;
+        if (e == cudaSuccess) e = cudaMemsetAsync(t.dump_delta, 0xff, G * G * 4, stream);
+    }
+    AlnsTeam* d_team = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&d_team, sizeof(AlnsTeam));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_team, &t, sizeof(AlnsTeam), cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) {
+        cleanup();
+        cudaFree(d_team);
+        set_error("alns setup: %s", cudaGetErrorString(e));
+        return VRPRPD_ECUDA;
+    }
+    const size_t smem = alns_smem_words(n, m) * 4;
+    VRP_CHECK(smem <= I->smem_optin, VRPRPD_EINVAL, "ALNS shared memory %zu exceeds the limit", smem);
+    int tb = 1;
+    int rc = choose_team_blocks(I, P->team_blocks, smem, &tb);
+    if (rc) { cleanup(); cudaFree(d_team); return rc; }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0, stream);
+    rc = launch_alns(I, d_team, 1, tb, smem, stream);
+    cudaEventRecord(e1, stream);
+    if (rc) { cleanup(); cudaFree(d_team); return rc; }
+    e = cudaStreamSynchronize(stream);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    AlnsCtl out{};
+    if (e == cudaSuccess) e = cudaMemcpy(&out, t.ctl, sizeof(out), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        cleanup();
+        cudaFree(d_team);
+        set_error("alns run: %s", cudaGetErrorString(e));
+        return VRPRPD_ECUDA;
+    }
+    if (out.err != 0) {
+        cleanup();
+        cudaFree(d_team);
+        set_error("alns device error %d (%s)", out.err,
+                  out.err == DEV_TIMEOUT_BARRIER ? "team barrier timed out" : "inconsistent state");
+        return out.err == DEV_TIMEOUT_BARRIER ? VRPRPD_ETIMEOUT : VRPRPD_ECUDA;
+    }
+    if (dump) {
+        const size_t G = static_cast<size_t>(dump_off[m]) + m;
+        e = cudaMemcpy(dump_delta, t.dump_delta, G * G * 4, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess && dump_travel) e = cudaMemcpy(dump_travel, t.dump_travel, G * G * 4, cudaMemcpyDeviceToHost);
+    } else {
+        if (best) {
+            e = cudaMemcpy(best->ops, t.best_ops, 2 * n * 4, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(best->off, t.best_off, (m + 1) * 4, cudaMemcpyDeviceToHost);
+            best->makespan = out.z_best;
+            best->status = 0;
+        }
+        if (current && e == cudaSuccess) {
+            e = cudaMemcpy(current->ops, t.cur_ops, 2 * n * 4, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(current->off, t.cur_off, (m + 1) * 4, cudaMemcpyDeviceToHost);
+            current->makespan = out.z_cur;
+            current->status = 0;
+        }
+        if (trace && e == cudaSuccess && iters > 0) e = cudaMemcpy(trace, t.trace, iters * 4, cudaMemcpyDeviceToHost);
+    }
+    if (stats) {
+        std::memset(stats, 0, sizeof(*stats));
+        stats->iterations = iters;
+        stats->accepted = out.accepted;
+        stats->improved = out.improved;
+        stats->new_best = out.new_best;
+        stats->reheats = out.reheats;
+        stats->rejected_infeasible = out.rejected;
+        stats->z_init = out.z_init;
+        stats->z_best = out.z_best;
+        stats->z_current = out.z_cur;
+        stats->T_final = out.T;
+        for (int i = 0; i < 4; ++i) { stats->w_destroy[i] = out.wd[i]; stats->w_repair[i] = out.wr[i]; }
+        stats->device_ms = ms;
+        stats->matrix_entries = static_cast<int64_t>(out.entries);
+        stats->fallback_entries = static_cast<int64_t>(out.fallback_entries);
+        stats->team_blocks = tb;
+    }
+    cleanup();
+    cudaFree(d_team);
+    if (e != cudaSuccess) {
+        set_error("alns copy-out: %s", cudaGetErrorString(e));
+        return VRPRPD_ECUDA;
+    }
+    return VRPRPD_OK;
+}
+
+extern "C" int vrprpd_alns_run(const vrprpd_instance* I, const vrprpd_solution* init, const vrprpd_alns_params* P,
+                               uint64_t seed, vrprpd_solution* best, vrprpd_solution* current,
+                               vrprpd_alns_stats* stats, int32_t* z_trace, void* stream) {
+    VRP_CHECK(I && P && best && best->ops && best->off, VRPRPD_EINVAL, "NULL argument");
+    int rc = run_team(I, init, P, seed, 0, 0, nullptr, nullptr, best, current, stats, z_trace, nullptr, nullptr,
+                      static_cast<cudaStream_t>(stream));
+    return rc;
+}
+
+extern "C" int vrprpd_insertion_matrix(const vrprpd_instance* I, const int32_t* ops, const int32_t* off, int32_t c,
+                                       int32_t* delta, int32_t* travel, void* stream) {
+    VRP_CHECK(I && ops && off && delta, VRPRPD_EINVAL, "NULL argument");
+    VRP_CHECK(c >= 1 && c <= I->n, VRPRPD_EINVAL, "customer %d out of range", c);
+    const int m = I->m;
+    VRP_CHECK(off[0] == 0 && off[m] >= 0 && off[m] <= 2 * I->n - 2, VRPRPD_EINVAL, "bad partial offsets");
+    for (int v = 0; v < m; ++v) VRP_CHECK(off[v + 1] >= off[v], VRPRPD_EINVAL, "offsets decrease");
+    std::vector<char> seen(2 * I->n + 2, 0);
+    for (int k = 0; k < off[m]; ++k) {
+        const int o = ops[k];
+        VRP_CHECK(o >= 2 && o <= 2 * I->n + 1 && !seen[o], VRPRPD_EINVAL, "bad or repeated op %d", o);
+        VRP_CHECK((o >> 1) != c, VRPRPD_EINVAL, "customer %d is already in the partial solution", c);
+        seen[o] = 1;
+    }
+    for (int q = 1; q <= I->n; ++q) VRP_CHECK(seen[2 * q] == seen[2 * q + 1], VRPRPD_EINVAL, "customer %d half present", q);
+    vrprpd_alns_params P;
+    vrprpd_alns_params_default(&P);
+    return run_team(I, nullptr, &P, 0, 1, c, ops, off, nullptr, nullptr, nullptr, nullptr, delta, travel,
+                    static_cast<cudaStream_t>(stream));
+}

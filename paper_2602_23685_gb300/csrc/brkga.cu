@@ -1,0 +1,539 @@
+// BRKGA on the device (Section 4.4): random-key chromosomes, the multi-pass
+// decoder of Algorithm 2, elite preservation, mutants, biased crossover and
+// the ALNS warm start (Section 4.4.5).
+//
+// Per generation (captured once as a CUDA graph, replayed):
+//   decode   one warp per chromosome: warp bitonic sort of (key, op index)
+//            pairs in shared memory -- the segmented key sort -- then the
+//            multi-pass decode with one lane per vehicle; SelectVehicle is a
+//            warp argmin of (arrival, vehicle-key rank);
+//   evaluate the decoded routes go through the batched evaluator (same
+//            makespans by construction; disagreements are counted);
+//   rank     one CTA sorts (fitness, index) and records the generation's best;
+//   evolve   elites copied, children by biased crossover, mutants drawn.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace vrp {
+
+int evaluate_device(const vrprpd_instance* I, const int32_t* ops, const int32_t* off, long long num, int32_t* z,
+                    uint32_t* st, cudaStream_t stream);
+bool batched_supported(const vrprpd_instance* I);
+
+constexpr int DEC_WARPS = 4;
+constexpr long long PENALTY = 1000000;
+
+struct BrkgaCtl {
+    int gen;            // generation being built
+    int sel;            // which key buffer is current
+    int mismatches;     // decoder makespan != evaluator makespan (complete decodes)
+    int pad;
+};
+
+struct DecArgs {
+    const float* keys;   // num x L (or two buffers selected by ctl->sel when keys2 != nullptr)
+    const float* keys2;
+    const BrkgaCtl* ctl;
+    int num, n, m, R, Q, load_full, L, P;   // P = power of two >= 2n
+    const int32_t* d32;
+    const int32_t* p;
+    int smem_dist;       // 1 = distance matrix staged in shared memory
+    int32_t* ops;
+    int32_t* off;
+    int32_t* z;
+    int32_t* unsched;
+    long long* fitness;
+};
+
+__host__ __device__ inline int pow2_at_least(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+__host__ __device__ inline size_t dec_warp_words(int n, int P) {
+    // sort buffer (u64) + tdrop + sched bitmap + per-op (vehicle<<16 | seq)
+    return static_cast<size_t>(2 * P) + (((n + 1) + 3) & ~3) + ((((2 * n + 2 + 31) / 32) + 3) & ~3) +
+           (((2 * n) + 3) & ~3);
+}
+
+__global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
+    extern __shared__ __align__(16) int smem_dec[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n = a.n, m = a.m, two_n = 2 * n, N1 = n + 1;
+    int* sd = smem_dec;                                   // staged distances (optional)
+    int* sp = sd + (a.smem_dist ? ((N1 * N1 + 3) & ~3) : 0);
+    for (int i = threadIdx.x; i < N1; i += blockDim.x) sp[i] = a.p[i];
+    if (a.smem_dist)
+        for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) sd[i] = a.d32[i];
+    int* wbase = sp + ((N1 + 3) & ~3) + warp * static_cast<int>(dec_warp_words(n, a.P));
+    unsigned long long* sb = reinterpret_cast<unsigned long long*>(wbase);
+    int* tdrop = wbase + 2 * a.P;
+    unsigned* sched = reinterpret_cast<unsigned*>(tdrop + (((n + 1) + 3) & ~3));
+    int* vs = reinterpret_cast<int*>(sched + ((((two_n + 2 + 31) / 32) + 3) & ~3));
+    __syncthreads();
+    const float* keys = a.keys;
+    if (a.keys2 != nullptr && a.ctl->sel == 1) keys = a.keys2;
+    auto dist = [&](int i, int j) -> int {
+        return a.smem_dist ? sd[i * N1 + j] : __ldg(a.d32 + i * N1 + j);
+    };
+    for (int ch = blockIdx.x * DEC_WARPS + warp; ch < a.num; ch += gridDim.x * DEC_WARPS) {
+        const float* kk = keys + static_cast<long long>(ch) * a.L;
+        // ---- segmented key sort: (key bits << 32 | op index), padding sorts last ----
+        for (int i = lane; i < a.P; i += 32) {
+            unsigned long long v = ~0ull;
+            if (i < two_n) {
+                const float f = __fadd_rn(kk[i], 0.0f);          // -0 -> +0
+                v = (static_cast<unsigned long long>(__float_as_uint(f)) << 32) | static_cast<unsigned>(i);
+            }
+            sb[i] = v;
+        }
+        for (int i = lane; i <= n; i += 32) tdrop[i] = 0;
+        for (int i = lane; i < (two_n + 2 + 31) / 32; i += 32) sched[i] = 0u;
+        for (int i = lane; i < two_n; i += 32) vs[i] = -1;
+        __syncwarp();
+        for (int size = 2; size <= a.P; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = lane; i < a.P / 2; i += 32) {
+                    const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                    const bool asc = (lo & size) == 0;
+                    const unsigned long long x = sb[lo], y = sb[hi];
+                    if ((x > y) == asc) { sb[lo] = y; sb[hi] = x; }
+                }
+                __syncwarp();
+            }
+        }
+        // ---- vehicle ranks: stable argsort of the m vehicle keys ----
+        const float kv = lane < m ? __fadd_rn(kk[two_n + lane], 0.0f) : 0.0f;
+        int rank = 0;
+        for (int u = 0; u < m; ++u) {
+            const float ku = __shfl_sync(FULL_MASK, kv, u);
+            if (lane < m && (ku < kv || (ku == kv && u < lane))) ++rank;
+        }
+        // ---- multi-pass decode (Algorithm 2), lane v = vehicle v ----
+        int tv = 0, locv = 0, net = 0, nmin = 0, nmax = 0, load = 0, cnt = 0;
+        int sum_load = 0, done = 0;
+        for (int pass = 0; pass < two_n && done < two_n; ++pass) {
+            bool progress = false;
+            for (int k = 0; k < two_n; ++k) {
+                const int oi = static_cast<int>(sb[k] & 0xffffffffu);
+                const int o = oi + 2, c = o >> 1;
+                const bool pick = (o & 1) != 0;
+                if ((sched[o >> 5] >> (o & 31)) & 1u) continue;
+                if (pick && !((sched[(2 * c) >> 5] >> ((2 * c) & 31)) & 1u)) continue;
+                bool ok = false;
+                if (lane < m) {
+                    if (!pick) {
+                        if (a.load_full) ok = net > -a.Q;
+                        else {
+                            const int nl = max(load, 1 - net);
+                            ok = nl + nmax <= a.Q && sum_load - load + nl <= a.R;
+                        }
+                    } else {
+                        ok = a.load_full ? (net < 0) : (load + net + 1 <= a.Q);
+                    }
+                }
+                const int arr = ok ? tv + dist(locv, c) : 0;
+                unsigned long long key = ok ? ((static_cast<unsigned long long>(arr) << 10) |
+                                               (static_cast<unsigned>(rank) << 5) | static_cast<unsigned>(lane))
+                                            : ~0ull;
+                for (int off = 16; off > 0; off >>= 1) {
+                    const unsigned long long other = __shfl_xor_sync(FULL_MASK, key, off);
+                    key = other < key ? other : key;
+                }
+                if (key == ~0ull) continue;
+                const int win = static_cast<int>(key & 31u);
+                int dsum = 0;
+                if (lane == win) {
+                    if (!pick) {
+                        tv = arr;
+                        tdrop[c] = arr;
+                        --net;
+                        nmin = min(nmin, net);
+                        dsum = -nmin - load;
+                        load = -nmin;
+                    } else {
+                        tv = max(arr, tdrop[c] + sp[c]);
+                        ++net;
+                        nmax = max(nmax, net);
+                    }
+                    locv = c;
+                    vs[oi] = (lane << 16) | cnt;
+                    ++cnt;
+                    sched[o >> 5] |= 1u << (o & 31);
+                }
+                sum_load += __shfl_sync(FULL_MASK, dsum, win);
+                __syncwarp();
+                progress = true;
+                ++done;
+            }
+            if (!progress) break;
+        }
+        // ---- outputs: routes, makespan, penalty fitness ----
+        int ret = (lane < m && cnt > 0) ? tv + dist(locv, 0) : 0;
+        for (int off = 16; off > 0; off >>= 1) ret = max(ret, __shfl_xor_sync(FULL_MASK, ret, off));
+        int incl = lane < m ? cnt : 0;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(FULL_MASK, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const int excl = incl - (lane < m ? cnt : 0);
+        int32_t* off_out = a.off + static_cast<long long>(ch) * (m + 1);
+        if (lane < m) off_out[lane] = excl;
+        if (lane == 0) off_out[m] = done;
+        int32_t* ops_out = a.ops + static_cast<long long>(ch) * two_n;
+        __syncwarp();
+        for (int oi = lane; oi < two_n; oi += 32) {
+            const int w = vs[oi];
+            if (w < 0) continue;
+            const int v = w >> 16, seq = w & 0xffff;
+            ops_out[off_out[v] + seq] = oi + 2;
+        }
+        if (lane == 0) {
+            const int un = two_n - done;
+            a.z[ch] = ret;
+            a.unsched[ch] = un;
+            a.fitness[ch] = static_cast<long long>(ret) + PENALTY * un;
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------------------
+__global__ void encode_kernel(const int32_t* __restrict__ ops, const int32_t* __restrict__ off, int n, int m,
+                              float* __restrict__ base) {
+    // ALNS seed encoding: pi_o = (r-1)/L_v (here r is 0-based), vehicle key v/m
+    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) base[i] = 0.0f;
+    __syncthreads();
+    for (int v = 0; v < m; ++v) {
+        const int L = off[v + 1] - off[v];
+        for (int r = threadIdx.x; r < L; r += blockDim.x)
+            base[ops[off[v] + r] - 2] = __fdiv_rn(static_cast<float>(r), static_cast<float>(L));
+    }
+    for (int v = threadIdx.x; v < m; v += blockDim.x)
+        base[2 * n + v] = __fdiv_rn(static_cast<float>(v), static_cast<float>(m));
+}
+
+__global__ void init_pop_kernel(float* __restrict__ keys, const float* __restrict__ base, int pop, int L, int warm,
+                                int variants, float eps, unsigned long long key, unsigned long long wkey) {
+    const long long total = static_cast<long long>(pop) * L;
+    const unsigned long long per = static_cast<unsigned long long>(L) + 2ull;
+    const float top = 1.0f - 1.0f / 16777216.0f;
+    for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int s = static_cast<int>(idx / L), g = static_cast<int>(idx - static_cast<long long>(s) * L);
+        float x;
+        if (s < warm) {
+            const int var = s % (variants > 0 ? variants : 1);
+            if (var == 0) {
+                x = base[g];
+            } else {
+                const float u = draw_key(draw(wkey, static_cast<unsigned long long>(var) * L + g));
+                const float e = __fmul_rn(__fsub_rn(__fmul_rn(u, 2.0f), 1.0f), eps);
+                x = __fadd_rn(base[g], e);
+                x = x < 0.0f ? 0.0f : x;
+                x = x > top ? top : x;
+            }
+        } else {
+            x = draw_key(draw(key, static_cast<unsigned long long>(s) * per + 2ull + g));
+        }
+        keys[idx] = x;
+    }
+}
+
+// One CTA: fitness, (fitness, index) sort, generation best.
+__global__ void __launch_bounds__(1024) rank_kernel(const int32_t* __restrict__ zdec, const int32_t* __restrict__ un,
+                                                    const int32_t* __restrict__ zev, const uint32_t* __restrict__ stev,
+                                                    int pop, int P, BrkgaCtl* ctl, int32_t* __restrict__ rank,
+                                                    long long* __restrict__ fit, long long* __restrict__ trace) {
+    extern __shared__ __align__(16) unsigned long long sk[];
+    for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        unsigned long long v = ~0ull;
+        if (i < pop) {
+            long long f;
+            if (un[i] > 0) {
+                f = static_cast<long long>(zdec[i]) + PENALTY * un[i];
+            } else {
+                f = zev[i];
+                if (zev[i] != zdec[i] || stev[i] != 0u) atomicAdd(&ctl->mismatches, 1);
+            }
+            fit[i] = f;
+            v = (static_cast<unsigned long long>(f) << 24) | static_cast<unsigned>(i);
+        }
+        sk[i] = v;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const unsigned long long x = sk[lo], y = sk[hi];
+                if ((x > y) == asc) { sk[lo] = y; sk[hi] = x; }
+            }
+            __syncthreads();
+        }
+    for (int i = threadIdx.x; i < pop; i += blockDim.x) rank[i] = static_cast<int>(sk[i] & 0xffffffu);
+    if (threadIdx.x == 0 && trace) trace[ctl->gen] = static_cast<long long>(sk[0] >> 24);
+}
+
+// Next population: elites, biased-crossover children, mutants.
+__global__ void evolve_kernel(float* __restrict__ buf0, float* __restrict__ buf1, const BrkgaCtl* __restrict__ ctl,
+                              const int32_t* __restrict__ rank, int pop, int L, int Ne, int Nc, float rho,
+                              unsigned long long key) {
+    const float* cur = ctl->sel == 0 ? buf0 : buf1;
+    float* nxt = ctl->sel == 0 ? buf1 : buf0;
+    const unsigned long long per = static_cast<unsigned long long>(L) + 2ull;
+    const unsigned long long gbase = static_cast<unsigned long long>(ctl->gen + 1) * static_cast<unsigned long long>(pop);
+    const long long total = static_cast<long long>(pop) * L;
+    for (long long idx = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; idx < total;
+         idx += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const int s = static_cast<int>(idx / L), g = static_cast<int>(idx - static_cast<long long>(s) * L);
+        float x;
+        if (s < Ne) {
+            x = cur[static_cast<long long>(rank[s]) * L + g];
+        } else {
+            const unsigned long long cb = (gbase + static_cast<unsigned long long>(s)) * per;
+            if (s < Ne + Nc) {
+                const int e = rank[draw_below(draw(key, cb + 0ull), Ne)];
+                const int o = rank[Ne + draw_below(draw(key, cb + 1ull), pop - Ne)];
+                const float u = draw_key(draw(key, cb + 2ull + g));
+                x = u < rho ? cur[static_cast<long long>(e) * L + g] : cur[static_cast<long long>(o) * L + g];
+            } else {
+                x = draw_key(draw(key, cb + 2ull + g));
+            }
+        }
+        nxt[idx] = x;
+    }
+}
+
+__global__ void advance_kernel(BrkgaCtl* ctl) {
+    ctl->sel ^= 1;
+    ctl->gen += 1;
+}
+
+// ---------------------------------------------------------------------------
+struct DecPlan {
+    int blocks = 0, P = 0;
+    size_t smem = 0;
+    int smem_dist = 0;
+};
+
+static int plan_decode(const vrprpd_instance* I, int num, DecPlan* D) {
+    VRP_CHECK(I->m <= 32, VRPRPD_EINVAL, "BRKGA decoding needs m <= 32");
+    VRP_CHECK(2 * I->n + I->m <= 8192, VRPRPD_EINVAL, "BRKGA decoding needs 2n + m <= 8192");
+    const int n = I->n, N1 = n + 1;
+    D->P = pow2_at_least(2 * n);
+    const size_t warp_words = dec_warp_words(n, D->P);
+    const size_t base_words = ((N1 + 3) & ~3) + DEC_WARPS * warp_words;
+    const size_t dist_words = (static_cast<size_t>(N1) * N1 + 3) & ~3;
+    D->smem_dist = (base_words + dist_words) * 4 + 64 <= I->smem_optin && N1 <= 240 ? 1 : 0;
+    D->smem = (base_words + (D->smem_dist ? dist_words : 0)) * 4;
+    VRP_CHECK(D->smem + 64 <= I->smem_optin, VRPRPD_EINVAL, "decode shared memory %zu too large", D->smem);
+    VRP_CUDA(cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(D->smem)));
+    int occ = 0;
+    VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_kernel, DEC_WARPS * 32, D->smem));
+    VRP_CHECK(occ > 0, VRPRPD_EINVAL, "decode block does not fit");
+    D->blocks = std::max(1, std::min((num + DEC_WARPS - 1) / DEC_WARPS, occ * I->num_sms));
+    return VRPRPD_OK;
+}
+
+static DecArgs dec_args(const vrprpd_instance* I, const DecPlan& D, int num) {
+    DecArgs a{};
+    a.num = num;
+    a.n = I->n;
+    a.m = I->m;
+    a.R = I->R;
+    a.Q = I->Q;
+    a.load_full = (I->flags & VRPRPD_LOAD_FULL) != 0;
+    a.L = 2 * I->n + I->m;
+    a.P = D.P;
+    a.d32 = I->d32;
+    a.p = I->p;
+    a.smem_dist = D.smem_dist;
+    return a;
+}
+
+}  // namespace vrp
+
+using namespace vrp;
+
+extern "C" void vrprpd_brkga_params_default(vrprpd_brkga_params* P) {
+    if (!P) return;
+    P->pop = 30000;
+    P->generations = 20000;
+    P->warm_slots = 4500;      // ceil(0.15 * 30000)
+    P->warm_variants = 20;
+    P->elite_frac = 0.15f;
+    P->mutant_frac = 0.15f;
+    P->rho = 0.7f;
+    P->eps = 0.03f;
+}
+
+extern "C" int vrprpd_brkga_decode(const vrprpd_instance* I, const float* keys, int32_t num, int32_t* ops, int32_t* off,
+                                   int32_t* z, int32_t* unsched, int64_t* fitness, void* stream) {
+    VRP_CHECK(I && keys && ops && off && z && unsched && fitness, VRPRPD_EINVAL, "NULL argument");
+    VRP_CHECK(num >= 0, VRPRPD_EINVAL, "negative count");
+    if (num == 0) return VRPRPD_OK;
+    DecPlan D;
+    int rc = plan_decode(I, num, &D);
+    if (rc) return rc;
+    DecArgs a = dec_args(I, D, num);
+    a.keys = keys;
+    a.ops = ops;
+    a.off = off;
+    a.z = z;
+    a.unsched = unsched;
+    a.fitness = reinterpret_cast<long long*>(fitness);
+    decode_kernel<<<D.blocks, DEC_WARPS * 32, D.smem, static_cast<cudaStream_t>(stream)>>>(a);
+    VRP_CUDA(cudaGetLastError());
+    return VRPRPD_OK;
+}
+
+extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_params* P, const vrprpd_solution* warm,
+                                uint64_t seed, vrprpd_solution* best, int64_t* best_fitness, int64_t* trace,
+                                float* final_keys, void* stream_) {
+    VRP_CHECK(I && P && best && best->ops && best->off, VRPRPD_EINVAL, "NULL argument");
+    VRP_CHECK(P->pop >= 2 && P->pop <= 16384, VRPRPD_EINVAL, "pop must lie in [2, 16384]");
+    VRP_CHECK(P->generations >= 1, VRPRPD_EINVAL, "generations must be >= 1");
+    VRP_CHECK(batched_supported(I), VRPRPD_EINVAL, "the batched evaluator does not support this instance");
+    const int n = I->n, m = I->m, pop = P->pop, L = 2 * n + m, G = P->generations;
+    int Ne = static_cast<int>(std::floor(static_cast<double>(P->elite_frac) * pop));
+    int Nm = static_cast<int>(std::floor(static_cast<double>(P->mutant_frac) * pop));
+    if (Ne < 1) Ne = 1;
+    if (Ne + Nm > pop) Nm = pop - Ne;
+    const int Nc = pop - Ne - Nm;
+    const int warm_slots = warm ? std::min(P->warm_slots, pop) : 0;
+    // work already queued on the caller's stream comes first
+    VRP_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream_)));
+    cudaStream_t s;
+    VRP_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    // device buffers
+    const size_t keys_b = static_cast<size_t>(pop) * L * 4;
+    std::vector<void*> allocs;
+    auto dalloc = [&](size_t bytes) -> void* {
+        void* p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+        allocs.push_back(p);
+        return p;
+    };
+    auto cleanup = [&]() {
+        for (void* p : allocs) cudaFree(p);
+        cudaStreamDestroy(s);
+    };
+    float* buf0 = static_cast<float*>(dalloc(keys_b));
+    float* buf1 = static_cast<float*>(dalloc(keys_b));
+    float* base = static_cast<float*>(dalloc(L * 4));
+    int32_t* dops = static_cast<int32_t*>(dalloc(static_cast<size_t>(pop) * 2 * n * 4));
+    int32_t* doff = static_cast<int32_t*>(dalloc(static_cast<size_t>(pop) * (m + 1) * 4));
+    int32_t* zdec = static_cast<int32_t*>(dalloc(pop * 4));
+    int32_t* un = static_cast<int32_t*>(dalloc(pop * 4));
+    long long* fitd = static_cast<long long*>(dalloc(pop * 8));
+    int32_t* zev = static_cast<int32_t*>(dalloc(pop * 4));
+    uint32_t* stev = static_cast<uint32_t*>(dalloc(pop * 4));
+    int32_t* rank = static_cast<int32_t*>(dalloc(pop * 4));
+    long long* fit = static_cast<long long*>(dalloc(pop * 8));
+    long long* dtrace = static_cast<long long*>(dalloc(static_cast<size_t>(G) * 8));
+    BrkgaCtl* ctl = static_cast<BrkgaCtl*>(dalloc(sizeof(BrkgaCtl)));
+    int32_t* wops = static_cast<int32_t*>(dalloc(2 * n * 4));
+    int32_t* woff = static_cast<int32_t*>(dalloc((m + 1) * 4));
+    for (void* p : allocs)
+        if (!p) { cleanup(); set_error("BRKGA: device allocation failed"); return VRPRPD_ENOMEM; }
+    if (allocs.size() != 17) { cleanup(); set_error("BRKGA: device allocation failed"); return VRPRPD_ENOMEM; }
+    const unsigned long long key = stream_key(seed, RNG_STREAM_BRKGA), wkey = stream_key(seed, RNG_STREAM_WARM);
+    BrkgaCtl c0{0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, L * 4, s);
+    if (warm && e == cudaSuccess) {
+        e = cudaMemcpyAsync(wops, warm->ops, 2 * n * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(woff, warm->off, (m + 1) * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) encode_kernel<<<1, 256, 0, s>>>(wops, woff, n, m, base);
+    }
+    if (e == cudaSuccess) {
+        init_pop_kernel<<<std::min<long long>((static_cast<long long>(pop) * L + 255) / 256, 4096), 256, 0, s>>>(
+            buf0, base, pop, L, warm_slots, P->warm_variants, P->eps, key, wkey);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) { cleanup(); set_error("BRKGA init: %s", cudaGetErrorString(e)); return VRPRPD_ECUDA; }
+    DecPlan D;
+    int rc = plan_decode(I, pop, &D);
+    if (rc) { cleanup(); return rc; }
+    DecArgs da = dec_args(I, D, pop);
+    da.keys = buf0;
+    da.keys2 = buf1;
+    da.ctl = ctl;
+    da.ops = dops;
+    da.off = doff;
+    da.z = zdec;
+    da.unsched = un;
+    da.fitness = fitd;
+    const int Prank = pow2_at_least(pop);
+    const size_t rank_smem = static_cast<size_t>(Prank) * 8;
+    VRP_CHECK(rank_smem + 64 <= I->smem_optin, VRPRPD_EINVAL, "population too large for the ranking kernel");
+    VRP_CUDA(cudaFuncSetAttribute(rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(rank_smem)));
+    const int evo_blocks = static_cast<int>(std::min<long long>((static_cast<long long>(pop) * L + 255) / 256, 8192));
+    auto enqueue_eval_rank = [&]() -> int {
+        decode_kernel<<<D.blocks, DEC_WARPS * 32, D.smem, s>>>(da);
+        VRP_CUDA(cudaGetLastError());
+        int r = evaluate_device(I, dops, doff, pop, zev, stev, s);
+        if (r) return r;
+        rank_kernel<<<1, 1024, rank_smem, s>>>(zdec, un, zev, stev, pop, Prank, ctl, rank, fit, dtrace);
+        VRP_CUDA(cudaGetLastError());
+        return VRPRPD_OK;
+    };
+    // warm-up pass outside capture so every kernel attribute is set
+    rc = VRPRPD_OK;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (G > 1) {
+        VRP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_eval_rank();
+        if (rc == VRPRPD_OK) {
+            evolve_kernel<<<evo_blocks, 256, 0, s>>>(buf0, buf1, ctl, rank, pop, L, Ne, Nc, P->rho, key);
+            advance_kernel<<<1, 1, 0, s>>>(ctl);
+        }
+        cudaError_t ce = cudaStreamEndCapture(s, &graph);
+        if (rc == VRPRPD_OK && ce != cudaSuccess) { set_error("graph capture: %s", cudaGetErrorString(ce)); rc = VRPRPD_ECUDA; }
+        if (rc == VRPRPD_OK) {
+            ce = cudaGraphInstantiate(&exec, graph, 0);
+            if (ce != cudaSuccess) { set_error("graph instantiate: %s", cudaGetErrorString(ce)); rc = VRPRPD_ECUDA; }
+        }
+        for (int g = 0; rc == VRPRPD_OK && g < G - 1; ++g) {
+            ce = cudaGraphLaunch(exec, s);
+            if (ce != cudaSuccess) { set_error("graph launch: %s", cudaGetErrorString(ce)); rc = VRPRPD_ECUDA; }
+        }
+    }
+    if (rc == VRPRPD_OK) rc = enqueue_eval_rank();          // last generation: evaluate and rank only
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) { cleanup(); return rc; }
+    e = cudaStreamSynchronize(s);
+    BrkgaCtl cend{};
+    int best_idx = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&cend, ctl, sizeof(cend), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&best_idx, rank, 4, cudaMemcpyDeviceToHost);
+    long long bf = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&bf, fit + best_idx, 8, cudaMemcpyDeviceToHost);
+    int32_t bz = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(best->ops, dops + static_cast<long long>(best_idx) * 2 * n, 2 * n * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(best->off, doff + static_cast<long long>(best_idx) * (m + 1), (m + 1) * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&bz, zdec + best_idx, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && trace) e = cudaMemcpy(trace, dtrace, static_cast<size_t>(G) * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && final_keys)
+        e = cudaMemcpy(final_keys, cend.sel == 0 ? buf0 : buf1, keys_b, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) { cleanup(); set_error("BRKGA copy-out: %s", cudaGetErrorString(e)); return VRPRPD_ECUDA; }
+    best->makespan = bz;
+    best->status = 0;
+    if (best_fitness) *best_fitness = bf;
+    cleanup();
+    if (cend.mismatches != 0) {
+        set_error("BRKGA: %d decoded makespans disagree with the evaluator", cend.mismatches);
+        return VRPRPD_ECUDA;
+    }
+    return VRPRPD_OK;
+}

@@ -174,84 +174,116 @@ __global__ void __launch_bounds__(1024) eval_tiles_kernel(EvalArgs a) {
         __syncwarp();
 
         // ---- 2. pre-pass: validate and pack (travel-in << 12 | op) in place ----
-        int carry = 0;
-        for (int base = 0; base < elems; base += 32) {
-            const int e = base + lane;
-            const bool in = e < elems;
-            const int raw = in ? Ab[e] : 2;
-            int prev = __shfl_up_sync(FULL_MASK, raw, 1);
-            if (lane == 0) prev = carry;
-            carry = __shfl_sync(FULL_MASK, raw, 31);
-            const bool ok = raw >= 2 && raw <= two_n + 1;
-            const int g = e / two_n;
-            if (in) {
-                if (!ok) {
-                    atomicAnd(&valid[g], 0);
-                } else {
-                    const unsigned bit = 1u << (raw & 31);
-                    const unsigned old = atomicOr(&seen[g * a.sw + (raw >> 5)], bit);
-                    if (old & bit) atomicAnd(&valid[g], 0);
+        // Four chunks of 32 ops per round so their distance reads overlap.
+        // Candidate index of element e without a division: the candidate of the
+        // round's first element plus boundary steps (none when k == 1).
+        {
+            int carry = 0, gbase = 0;
+            for (int base = 0; base < elems; base += 128) {
+                int raw[4], prv[4], gg[4], dd[4];
+                bool in[4], ok[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = base + 32 * u + lane;
+                    in[u] = e < elems;
+                    raw[u] = in[u] ? Ab[e] : 2;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    int pv = __shfl_up_sync(FULL_MASK, raw[u], 1);
+                    if (lane == 0) pv = carry;
+                    carry = __shfl_sync(FULL_MASK, raw[u], 31);
+                    prv[u] = pv;
+                }
+                if (k > 1)
+                    while ((gbase + 1) * two_n <= base) ++gbase;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = base + 32 * u + lane;
+                    int g = gbase;
+                    if (k > 1)
+                        while ((g + 1) * two_n <= e) ++g;
+                    gg[u] = g;
+                    ok[u] = raw[u] >= 2 && raw[u] <= two_n + 1;
+                    const bool is_start = in[u] && ((starts[e >> 5] >> (e & 31)) & 1u);
+                    const int pc = (is_start || prv[u] < 2 || prv[u] > two_n + 1) ? 0 : (prv[u] >> 1);
+                    dd[u] = dist<DM>(a, sh, pc, ok[u] ? (raw[u] >> 1) : 0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    bool bad = !ok[u];
+                    if (in[u] && ok[u]) {
+                        const unsigned bit = 1u << (raw[u] & 31);
+                        bad = (atomicOr(&seen[gg[u] * a.sw + (raw[u] >> 5)], bit) & bit) != 0u;
+                    }
+                    if (in[u] && bad) atomicAnd(&valid[gg[u]], 0);
+                }
+                __syncwarp();
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = base + 32 * u + lane;
+                    if (in[u]) Ab[e] = (dd[u] << PACK_SHIFT) | (ok[u] ? raw[u] : 2);
                 }
             }
-            const bool is_start = in && ((starts[e >> 5] >> (e & 31)) & 1u);
-            const int c = ok ? (raw >> 1) : 0;
-            const int pc = (is_start || !(prev >= 2 && prev <= two_n + 1)) ? 0 : (prev >> 1);
-            const int dd = in ? dist<DM>(a, sh, pc, c) : 0;
-            __syncwarp();
-            if (in) Ab[e] = (dd << PACK_SHIFT) | (ok ? raw : 2);
         }
         __syncwarp();
 
-        // ---- 3. route walk ----
+        // ---- 3. route walk (branch-free; up to two ops per lane per step) ----
+        // Ready times have a single writer (the dropping lane) and are read
+        // with volatile loads: a pickup sees either "unresolved" (and retries
+        // next step) or the final value.  The __syncwarp at the end of each
+        // step makes every write of step t visible in step t+1, so a group
+        // with no progress in a step can never progress again (a cycle).
         const bool mine = grp < kt && valid[grp] != 0;
         int pos = 0, end = 0, start = 0;
         if (mine) {
             start = pos = soff[grp * (m + 1) + v];
             end = soff[grp * (m + 1) + v + 1];
         }
-        const int ebase = (grp < k ? grp : 0) * two_n;
-        int32_t* rdy = ready + (grp < k ? grp : 0) * (n + 1);
-        int dep = 0, s = 0, smin = 0, smax = 0, last = 0;
+        const int* wp = Ab + (grp < k ? grp : 0) * two_n;
+        volatile int* rdy = ready + (grp < k ? grp : 0) * (n + 1);
+        int dep = 0, s = 0, smin = 0, smax = 0;
         bool walking = mine && pos < end, cyc = false;
         while (__any_sync(FULL_MASK, walking)) {
-            int w = 0, r = 0, c = 0;
-            bool go = false, pick = false;
-            if (walking) {
-                w = Ab[ebase + pos];
-                const int o = w & PACK_MASK;
-                c = o >> 1;
-                pick = (o & 1) != 0;
-                if (pick) r = rdy[c];
-                go = !pick || r >= 0;
-            }
+            // first op
+            const int w1 = walking ? wp[pos] : 0;
+            const int c1 = (w1 & PACK_MASK) >> 1;
+            const bool p1 = (w1 & 1) != 0;
+            const int r1 = rdy[c1];
+            const bool go1 = walking && (!p1 || r1 >= 0);
+            const int a1 = dep + (w1 >> PACK_SHIFT);
+            if (go1 && !p1) rdy[c1] = a1 + sp[c1];
+            dep = go1 ? max(a1, p1 ? r1 : 0) : dep;
+            s += go1 ? (p1 ? 1 : -1) : 0;
+            smin = min(smin, s);
+            smax = max(smax, s);
+            pos += go1 ? 1 : 0;
+            // second op, only behind a first one that went
+            const bool try2 = go1 && pos < end;
+            const int w2 = try2 ? wp[pos] : 0;
+            const int c2 = (w2 & PACK_MASK) >> 1;
+            const bool p2 = (w2 & 1) != 0;
+            const int r2 = rdy[c2];
+            const bool go2 = try2 && (!p2 || r2 >= 0);
+            const int a2 = dep + (w2 >> PACK_SHIFT);
+            if (go2 && !p2) rdy[c2] = a2 + sp[c2];
+            dep = go2 ? max(a2, p2 ? r2 : 0) : dep;
+            s += go2 ? (p2 ? 1 : -1) : 0;
+            smin = min(smin, s);
+            smax = max(smax, s);
+            pos += go2 ? 1 : 0;
+            const unsigned prog = __ballot_sync(FULL_MASK, go1);
+            const bool more = pos < end;
+            cyc = cyc || (walking && more && (prog & gmask) == 0u);
+            walking = walking && more && !cyc;
             __syncwarp();
-            if (go) {
-                const int arr = dep + (w >> PACK_SHIFT);
-                if (pick) {
-                    dep = max(arr, r);
-                    ++s;
-                    smax = max(smax, s);
-                } else {
-                    dep = arr;
-                    rdy[c] = arr + sp[c];
-                    --s;
-                    smin = min(smin, s);
-                }
-                last = c;
-                ++pos;
-            }
-            __syncwarp();
-            const unsigned prog = __ballot_sync(FULL_MASK, go);
-            if (walking) {
-                if (pos >= end) walking = false;
-                else if ((prog & gmask) == 0u) { walking = false; cyc = true; }
-            }
         }
         if (cyc)                                   // finish the stock prefix of a blocked route
             for (; pos < end; ++pos) {
-                const int o = Ab[ebase + pos] & PACK_MASK;
+                const int o = wp[pos] & PACK_MASK;
                 if (o & 1) { ++s; smax = max(smax, s); } else { --s; smin = min(smin, s); }
             }
+        const int last = (end > start) ? ((wp[end - 1] & PACK_MASK) >> 1) : 0;
 
         // ---- 4. per-candidate reduction ----
         int ret = 0, flags = 0, pool = 0;

@@ -1,0 +1,216 @@
+"""GPU parity of the ALNS path against the CPU oracle: the insertion-delta
+matrix element by element (oracle: full re-simulation of every entry), the
+start solution, and whole ALNS trajectories (same counter-based draws, so the
+per-iteration makespans, the accept/improve counts, temperature and weights
+must agree exactly); every returned solution is re-evaluated by the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+INT32_MAX = 2**31 - 1
+
+
+def destroyed(ops, off, m, remove):
+    rem = set(int(c) for c in remove)
+    routes = [[int(o) for o in ops[off[v]:off[v + 1]] if (int(o) >> 1) not in rem] for v in range(m)]
+    po = np.array(sum(routes, []), np.int32)
+    pf = np.zeros(m + 1, np.int32)
+    pf[1:] = np.cumsum([len(r) for r in routes])
+    return po, pf
+
+
+def matrix_case(vrp, w, seed, n_remove, load_full=False, start="initial"):
+    inst = vrp.Instance.from_workload(w, load_full=load_full)
+    oi = oracle.OracleInstance.from_workload(w, load_full=load_full)
+    rng = np.random.default_rng(seed)
+    if start == "initial":                      # feasible start: the library constructor
+        ops, off = vrp.initial_solution(inst)
+    else:                                       # random acyclic routes, capacity unchecked
+        ops, off = workloads.precedence_candidates(w.n, w.m, 1, seed)
+        ops, off = ops[0], off[0]
+    remove = rng.choice(np.arange(1, w.n + 1), size=n_remove, replace=False)
+    po, pf = destroyed(ops, off, w.m, remove)
+    if oracle.evaluate(oi, po, pf, allow_partial=True)[1] & oracle.CYCLE:
+        pytest.skip("partial solution cyclic")
+    for c in remove[:2]:
+        dg, tg = vrp.insertion_matrix(inst, po, pf, int(c))
+        do, to, so = oracle.insertion_matrix(oi, po, pf, int(c))
+        bad = np.argwhere(dg != do)
+        assert bad.size == 0, (bad[:5], dg[tuple(bad[0])], do[tuple(bad[0])], so[tuple(bad[0])])
+        feas = do != INT32_MAX
+        assert np.array_equal(tg[feas], to[feas])
+        if start == "initial":
+            assert feas.any()
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_matrix_c1(vrp, seed):
+    cfg = workloads.CONFIGS["C1"]
+    w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], seed=seed)
+    matrix_case(vrp, w, seed, 4)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_matrix_medium(vrp, seed):
+    w = workloads.make_instance(40, 4, R=10, Q=5, variant="2x", seed=10 + seed)
+    matrix_case(vrp, w, seed, 6)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_matrix_random_routes(vrp, seed):
+    w = workloads.make_instance(30, 3, R=40, Q=30, variant="5x", seed=20 + seed)
+    matrix_case(vrp, w, seed, 5, start="random")
+
+
+def test_matrix_load_full(vrp):
+    w = workloads.make_instance(20, 3, R=30, Q=6, seed=5)
+    matrix_case(vrp, w, 5, 5, load_full=True)
+
+
+def test_matrix_shortcut_gaps(vrp):
+    # nearly collinear points make nint(|xc|) + nint(|cy|) < nint(|xy|): entries on such
+    # gaps go through the full re-simulation path and must still match
+    coords = np.array([[0, 0], [1, 1], [2, 2], [3, 3], [4, 4], [10, 0], [0, 10], [5, 5], [7, 7]], np.int32)
+    p = np.array([3, 1, 4, 1, 5, 9, 2, 6], np.int32)
+    w = workloads.Instance(coords, p, 2, 4, 3)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    ops = np.array([2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17], np.int32)
+    off = np.array([0, 8, 16], np.int32)
+    for c in (2, 3, 8):
+        po, pf = destroyed(ops, off, 2, [c])
+        dg, tg = vrp.insertion_matrix(inst, po, pf, c)
+        do, to, so = oracle.insertion_matrix(oi, po, pf, c)
+        assert np.array_equal(dg, do)
+        feas = do != INT32_MAX
+        assert np.array_equal(tg[feas], to[feas])
+
+
+def test_initial_solution_matches_oracle(vrp):
+    for (n, m, R, Q) in [(16, 2, 4, 4), (100, 4, 10, 5), (200, 6, 20, 6), (1000, 20, 100, 10), (7, 5, 3, 2)]:
+        w = workloads.make_instance(n, m, R, Q, "2x", "clustered" if n == 200 else "uniform", seed=n)
+        inst = vrp.Instance.from_workload(w)
+        oi = oracle.OracleInstance.from_workload(w)
+        go, gf = vrp.initial_solution(inst)
+        oo, of = oracle.initial_solution(oi, w.coords)
+        assert np.array_equal(go, oo) and np.array_equal(gf, of)
+        assert oracle.evaluate(oi, go, gf)[1] == 0
+
+
+def run_both(vrp, w, iters, seed, q=(0, 0), mask=3, team_blocks=0):
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    init = oracle.initial_solution(oi, w.coords)
+    g = vrp.alns_run(inst, vrp.alns_params(iters, q[0], q[1], mask, team_blocks), seed=seed, init=init)
+    o = oracle.alns_run(oi, init[0], init[1], oracle.alns_params(iters, q[0], q[1], mask), seed)
+    return inst, oi, g, o
+
+
+def assert_same_run(oi, g, o):
+    assert np.array_equal(g["trace"], o["trace"]), np.nonzero(g["trace"] != o["trace"])[0][:5]
+    gs, os_ = g["stats"], o["stats"]
+    for f in ("accepted", "improved", "new_best", "reheats", "rejected_infeasible"):
+        assert getattr(gs, f) == getattr(os_, f), f
+    assert gs.z_best == os_.z_best and g["z_best"] == os_.z_best
+    assert gs.T_final == os_.T_final
+    assert list(gs.w_repair)[:2] == list(os_.w_repair)[:2]
+    assert np.array_equal(g["best_ops"], o["best_ops"]) and np.array_equal(g["best_off"], o["best_off"])
+    assert np.array_equal(g["cur_ops"], o["cur_ops"]) and np.array_equal(g["cur_off"], o["cur_off"])
+    # every returned solution re-evaluated by the oracle
+    assert oracle.evaluate(oi, g["best_ops"], g["best_off"]) == (g["z_best"], 0)
+    assert oracle.evaluate(oi, g["cur_ops"], g["cur_off"]) == (g["z_current"], 0)
+
+
+def test_alns_c1_trajectory(vrp):
+    # configuration 1: n=16, m=2, R=4, Q=4, base p; 200 iterations from seed 0
+    cfg = workloads.CONFIGS["C1"]
+    w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], seed=0)
+    _, oi, g, o = run_both(vrp, w, 200, seed=0)
+    assert_same_run(oi, g, o)
+    assert g["z_best"] <= g["trace"][0]
+
+
+@pytest.mark.parametrize("mask", [1, 2])
+def test_alns_single_repair_operator(vrp, mask):
+    w = workloads.make_instance(24, 3, 6, 4, "5x", seed=3)
+    _, oi, g, o = run_both(vrp, w, 60, seed=7, mask=mask)
+    assert_same_run(oi, g, o)
+
+
+def test_alns_medium_trajectory(vrp):
+    # configuration 2 shape (m=4, R=10, Q=5, 2x, q = 10% of n) at n=40 so the
+    # oracle's full re-simulation stays quick
+    w = workloads.make_instance(40, 4, 10, 5, "2x", seed=2)
+    _, oi, g, o = run_both(vrp, w, 6, seed=1, q=(4, 4))
+    assert_same_run(oi, g, o)
+
+
+def test_alns_team_blocks_agree(vrp):
+    w = workloads.make_instance(100, 4, 10, 5, "2x", seed=0)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    init = oracle.initial_solution(oi, w.coords)
+    runs = [vrp.alns_run(inst, vrp.alns_params(8, 10, 10, 3, tb), seed=3, init=init) for tb in (1, 6)]
+    assert runs[1]["stats"].team_blocks == 6
+    assert np.array_equal(runs[0]["trace"], runs[1]["trace"])
+    assert np.array_equal(runs[0]["best_ops"], runs[1]["best_ops"])
+    assert oracle.evaluate(oi, runs[0]["best_ops"], runs[0]["best_off"]) == (runs[0]["z_best"], 0)
+
+
+def test_alns_n1000_reevaluated(vrp):
+    cfg = workloads.CONFIGS["C5"]
+    w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=0)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    g = vrp.alns_run(inst, vrp.alns_params(3), seed=0)
+    assert oracle.evaluate(oi, g["best_ops"], g["best_off"]) == (g["z_best"], 0)
+    assert oracle.evaluate(oi, g["cur_ops"], g["cur_off"]) == (g["z_current"], 0)
+    assert g["stats"].matrix_entries > 0
+
+
+def test_matrix_n1000_sampled(vrp):
+    cfg = workloads.CONFIGS["C5"]
+    w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=1)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    ops, off = vrp.initial_solution(inst)
+    rng = np.random.default_rng(0)
+    remove = rng.choice(np.arange(1, w.n + 1), size=30, replace=False)
+    po, pf = destroyed(ops, off, w.m, remove)
+    c = int(remove[0])
+    dg, tg = vrp.insertion_matrix(inst, po, pf, c)
+    z0, st0 = oracle.evaluate(oi, po, pf, allow_partial=True)
+    G = dg.shape[0]
+    gaps = [(v, i) for v in range(w.m) for i in range(pf[v + 1] - pf[v] + 1)]
+    idx = rng.choice(G * G, size=300, replace=False)
+    for flat in idx:
+        r, col = divmod(int(flat), G)
+        (a, i), (b, j) = gaps[r], gaps[col]
+        if a == b and j < i:
+            assert dg[r, col] == INT32_MAX
+            continue
+        routes = [list(po[pf[v]:pf[v + 1]]) for v in range(w.m)]
+        if a == b:
+            routes[a] = routes[a][:i] + [2 * c] + routes[a][i:j] + [2 * c + 1] + routes[a][j:]
+        else:
+            routes[a] = routes[a][:i] + [2 * c] + routes[a][i:]
+            routes[b] = routes[b][:j] + [2 * c + 1] + routes[b][j:]
+        so = np.array(sum(routes, []), np.int32)
+        sf = np.zeros(w.m + 1, np.int32)
+        sf[1:] = np.cumsum([len(x) for x in routes])
+        z, st = oracle.evaluate(oi, so, sf, allow_partial=True)
+        cap = any(_route_cap_bad(routes[v], w.Q) for v in {a, b})
+        expect = INT32_MAX if (st & (oracle.CYCLE | oracle.POOL)) or cap else z - z0
+        assert dg[r, col] == expect, (r, col, dg[r, col], expect)
+
+
+def _route_cap_bad(route, Q):
+    s = smin = smax = 0
+    for o in route:
+        s += 1 if o & 1 else -1
+        smin, smax = min(smin, s), max(smax, s)
+    return -smin + smax > Q

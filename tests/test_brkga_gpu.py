@@ -1,0 +1,83 @@
+"""GPU parity of the BRKGA path against the CPU oracle: the decoder (segmented
+key sort + Algorithm 2) chromosome by chromosome, the warm-start encoding, and
+whole BRKGA runs (same counter-based draws: identical per-generation best
+fitness and bit-identical final populations); decoded routes re-evaluated."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def decode_compare(vrp, w, keys, load_full=False):
+    import torch
+    inst = vrp.Instance.from_workload(w, load_full=load_full)
+    oi = oracle.OracleInstance.from_workload(w, load_full=load_full)
+    ops, off, z, un, fit = [t.cpu().numpy() for t in vrp.brkga_decode(inst, torch.from_numpy(keys).cuda())]
+    for i in range(keys.shape[0]):
+        oo, of, oz, oun, ofit = oracle.decode(oi, keys[i])
+        assert (z[i], un[i], fit[i]) == (oz, oun, ofit), i
+        assert np.array_equal(off[i], of), i
+        assert np.array_equal(ops[i][:of[-1]], oo[:of[-1]]), i
+        if oun == 0:
+            # invariant: the decoder's makespan is the evaluator's
+            assert oracle.evaluate(oi, oo, of) == (oz, 0)
+
+
+@pytest.mark.parametrize("n,m,R,Q", [(16, 2, 4, 4), (30, 3, 6, 3), (200, 6, 20, 6), (7, 5, 2, 1)])
+def test_decode_random_keys(vrp, n, m, R, Q):
+    w = workloads.make_instance(n, m, R, Q, "5x", "clustered" if n == 200 else "uniform", seed=n)
+    keys = workloads.random_keys(256 if n < 200 else 96, 2 * n + m, seed=1)
+    keys[0, : 2 * n] = 0.5                       # all priorities tie: order by op index
+    keys[1, 2 * n:] = 0.25                       # all vehicle keys tie: order by vehicle index
+    decode_compare(vrp, w, keys)
+
+
+def test_decode_load_full(vrp):
+    w = workloads.make_instance(24, 3, 18, 6, seed=4)
+    decode_compare(vrp, w, workloads.random_keys(128, 51, seed=2), load_full=True)
+
+
+def test_decode_encoded_alns_solution(vrp):
+    w = workloads.make_instance(40, 4, 10, 5, "2x", seed=6)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    ops, off = vrp.initial_solution(inst)
+    keys = oracle.encode(oi, ops, off)[None, :].astype(np.float32)
+    decode_compare(vrp, w, keys)
+
+
+def run_pair(vrp, w, pop, gens, seed, warm=True, elite=0.2, mutant=0.1):
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    wo, wf = oracle.initial_solution(oi, w.coords) if warm else (None, None)
+    g = vrp.brkga_run(inst, vrp.brkga_params(pop, gens, elite, mutant), seed=seed,
+                      warm=(wo, wf) if warm else None, final_keys=True)
+    o = oracle.brkga_run(oi, oracle.brkga_params(pop, gens, elite, mutant), wo, wf, seed)
+    assert np.array_equal(g["trace"], o["trace"]), (g["trace"][:10], o["trace"][:10])
+    gk = g["keys"].cpu().numpy()
+    assert np.array_equal(gk.view(np.uint32), o["keys"].view(np.uint32))
+    assert g["best_fitness"] == o["best_fitness"]
+    assert np.array_equal(g["best_ops"], o["best_ops"]) and np.array_equal(g["best_off"], o["best_off"])
+    assert oracle.evaluate(oi, g["best_ops"], g["best_off"]) == (g["z_best"], 0)
+    assert all(np.diff(g["trace"]) <= 0)          # elites survive: best never worsens
+    return g, o
+
+
+def test_brkga_small_warm(vrp):
+    w = workloads.make_instance(16, 2, 4, 4, "base", seed=0)
+    run_pair(vrp, w, 64, 25, seed=3)
+
+
+def test_brkga_small_random_start(vrp):
+    w = workloads.make_instance(20, 3, 6, 3, "2x", seed=1)
+    run_pair(vrp, w, 50, 10, seed=9, warm=False, elite=0.15, mutant=0.15)
+
+
+def test_brkga_c3_shape_few_generations(vrp):
+    # configuration 3 shape: n=200 clustered, m=6, R=20, Q=6, 5x; pop 1024, 0.2/0.1/0.7
+    cfg = workloads.CONFIGS["C3"]
+    w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=0)
+    run_pair(vrp, w, 1024, 3, seed=0)
