@@ -170,6 +170,100 @@ def run_profile(args):
                       "evals_per_s": len(ops_h) / (ms / 1000), "config": vrp.get_eval_config(inst)}))
 
 
+def run_searches(vrp, args):
+    """ALNS iterations/s (n=1000 and the n=100 configuration) and BRKGA
+    generations/s (n=200 clustered, pop 1024), each timed on the device."""
+    out = {}
+    w5 = workloads.make_instance(N_CUST, M_VEH, R_POOL, Q_CAP, "1R20", "mixed", seed=0)
+    i5 = vrp.Instance.from_workload(w5)
+    vrp.alns_run(i5, vrp.alns_params(1), seed=1)                       # warm-up
+    r = vrp.alns_run(i5, vrp.alns_params(args.alns_iters), seed=0)
+    st = r["stats"]
+    out["alns_n1000"] = {
+        "value": args.alns_iters / (st.device_ms / 1000.0), "unit": "ALNS iters/s",
+        "config": "n=1000 m=20 R=100 Q=10 1R20, q in [25,50] (Section 4.2.2), greedy+regret-2 over the "
+                  "full insertion-delta matrix", "iterations": args.alns_iters,
+        "matrix_entries_per_s": st.matrix_entries / (st.device_ms / 1000.0),
+        "fallback_entries": st.fallback_entries, "team_blocks": st.team_blocks,
+        "z_init": st.z_init, "z_best": st.z_best, "device_ms": st.device_ms}
+    w2 = workloads.make_instance(100, 4, 10, 5, "2x", "uniform", seed=0)
+    i2 = vrp.Instance.from_workload(w2)
+    r2 = vrp.alns_run(i2, vrp.alns_params(args.alns_iters * 10, 10, 10), seed=0)
+    st2 = r2["stats"]
+    out["alns_n100"] = {
+        "value": args.alns_iters * 10 / (st2.device_ms / 1000.0), "unit": "ALNS iters/s",
+        "config": "n=100 m=4 R=10 Q=5 2x, q=10", "iterations": args.alns_iters * 10,
+        "matrix_entries_per_s": st2.matrix_entries / (st2.device_ms / 1000.0),
+        "team_blocks": st2.team_blocks, "z_init": st2.z_init, "z_best": st2.z_best}
+    w3 = workloads.make_instance(200, 6, 20, 6, "5x", "clustered", seed=0)
+    i3 = vrp.Instance.from_workload(w3)
+    a3 = vrp.alns_run(i3, vrp.alns_params(50), seed=0)
+    warm = (a3["best_ops"], a3["best_off"])
+    vrp.brkga_run(i3, vrp.brkga_params(1024, 2), seed=1, warm=warm)   # warm-up
+    t = time.perf_counter()
+    b = vrp.brkga_run(i3, vrp.brkga_params(1024, args.brkga_gens), seed=0, warm=warm)
+    dt = time.perf_counter() - t
+    out["brkga_n200"] = {
+        "value": args.brkga_gens / dt, "unit": "BRKGA generations/s",
+        "decodes_per_s": args.brkga_gens * 1024 / dt,
+        "config": "n=200 clustered m=6 R=20 Q=6 5x, pop 1024, elite 0.2 mutant 0.1 rho 0.7, warm start "
+                  "from 50 ALNS iterations", "generations": args.brkga_gens,
+        "alns_z": a3["z_best"], "brkga_best": b["best_fitness"]}
+    return out
+
+
+def run_multi(vrp, args):
+    """256 instances, n log-uniform in [17, 500], m = ceil(n/25), R = ceil(n/10),
+    Q = 8, 1R10; 4096 candidates each (512 generated per instance, tiled 8x on
+    the device) in one persistent launch replayed as a CUDA graph, against the
+    plain form launched once per instance."""
+    import torch
+    ws = workloads.uneven_instances(256, 17, 500, 8, "1R10", seed=4)
+    items = []
+    total = 0
+    for i, w in enumerate(ws):
+        o, f = workloads.precedence_candidates(w.n, w.m, 512, seed=i)
+        ops = torch.from_numpy(o).cuda().repeat(8, 1).contiguous()
+        off = torch.from_numpy(f).cuda().repeat(8, 1).contiguous()
+        items.append((vrp.Instance.from_workload(w), ops, off))
+        total += ops.shape[0]
+    mb = vrp.MultiBatch(items)
+    cfg = mb.autotune()
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        mb.evaluate()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(5, args.steps // 5)
+    e0.record(stream)
+    for _ in range(reps):
+        mb.evaluate()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    multi_ms = e0.elapsed_time(e1) / reps
+    zs = [z.clone() for z in mb.z]
+    outs = []
+    for inst, ops, off in items:
+        outs.append(vrp.evaluate_plain(inst, ops, off))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for (inst, ops, off), (zp, sp) in zip(items, outs):
+        vrp.evaluate_plain(inst, ops, off, zp, sp)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = e0.elapsed_time(e1)
+    equal = all(torch.equal(a, b[0]) for a, b in zip(zs, outs))
+    mean_bytes = sum(4 * (2 * w.n + w.m + 1) + 8 for w in ws) / len(ws)
+    return {"batched_multi": {
+        "value": total / (multi_ms / 1000.0), "unit": "evals/s",
+        "config": "256 instances, n log-uniform [17,500], m=ceil(n/25), R=ceil(n/10), Q=8, 1R10; 4096 "
+                  "candidates each, one persistent launch replayed as a CUDA graph",
+        "candidates_per_launch": total, "ms_per_launch": multi_ms, "eval_config": cfg,
+        "achieved_gbs": total * mean_bytes / (multi_ms / 1000.0) / 1e9,
+        "plain_per_instance_evals_per_s": total / (plain_ms / 1000.0),
+        "speedup_vs_plain": plain_ms / multi_ms, "equal_makespan": equal}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -177,6 +271,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-search", action="store_true", help="skip the ALNS / BRKGA legs")
+    ap.add_argument("--alns-iters", type=int, default=20)
+    ap.add_argument("--brkga-gens", type=int, default=100)
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu: 16384 candidates (132 MB), default kernel shape, no tuning")
     args = ap.parse_args()
@@ -278,6 +375,10 @@ def main():
     e2e_value = B * e2e_steps * world / e2e_s
     assert torch.equal(z_h, z.cpu())
 
+    searches = {} if args.no_search else run_searches(vrp, args)
+    if not args.no_search:
+        searches.update(run_multi(vrp, args))
+
     pk = peaks()
     bytes_per_eval = 4 * (2 * N_CUST + M_VEH + 1) + 8
     achieved = B * bytes_per_eval / (kernel_ms / 1000.0) / 1e9
@@ -302,6 +403,7 @@ def main():
             "plain_gpu": {"value": plain_value, "unit": UNIT, "equal_makespan": equal,
                           "speedup_batched_vs_plain": value / world / plain_value},
         }
+        line.update(searches)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, ops_h, off_h)
         print(json.dumps(line), flush=True)

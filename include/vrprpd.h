@@ -140,6 +140,28 @@ int vrprpd_eval_get_config(const vrprpd_instance* inst, vrprpd_eval_config* cfg)
 int vrprpd_autotune(vrprpd_instance* inst, const vrprpd_batch* batch, void* stream,
                     vrprpd_eval_config* chosen);
 
+/* ---- many instances of uneven size in one persistent launch ---- */
+typedef struct vrprpd_multi vrprpd_multi;
+
+/* Plan one persistent launch over n_inst (instance, batch) pairs (Section
+ * 4.2.1's multi-instance parallelism applied to evaluation): the tiles of all
+ * batches form one work list; every warp takes tiles in turn, whatever
+ * instance they belong to.  insts, batches, makespan and status are HOST
+ * arrays of n_inst entries; the batch and output pointers they hold are
+ * DEVICE pointers that must stay valid while the plan is used.  All instances
+ * must live on one device and satisfy the batched evaluator's limits. */
+int vrprpd_multi_create(const vrprpd_instance* const* insts, const vrprpd_batch* batches,
+                        int32_t* const* makespan, uint32_t* const* status, int32_t n_inst,
+                        vrprpd_multi** out);
+/* Evaluate every batch of the plan, asynchronously on stream.  On a non-NULL
+ * stream that is not being captured the first call captures the launch as a
+ * CUDA graph and later calls replay it; inside a caller's capture (or on the
+ * NULL stream) it launches directly.  Results as vrprpd_evaluate. */
+int vrprpd_multi_evaluate(vrprpd_multi* plan, void* stream);
+/* Time warps-per-block and distance modes on the plan's own batches; keep the fastest. */
+int vrprpd_multi_autotune(vrprpd_multi* plan, void* stream, vrprpd_eval_config* chosen);
+void vrprpd_multi_destroy(vrprpd_multi* plan);
+
 /* ======================================================================== */
 /* ALNS (Section 4.2, Algorithm 1) on the device                             */
 /* ======================================================================== */

@@ -347,3 +347,47 @@ def brkga_run(inst, params, seed=0, warm=None, final_keys=False, stream=None):
                                   keys.data_ptr() if keys is not None else None, _stream_ptr(stream)))
     return {"best_ops": bo, "best_off": bf, "z_best": best.makespan, "best_fitness": int(fitness[0]),
             "trace": trace, "keys": keys}
+
+
+# ---------------------------------------------------------------------------
+# many instances in one persistent launch
+# ---------------------------------------------------------------------------
+class MultiBatch:
+    """A plan over (instance, ops, off) triples of uneven size; evaluate() runs
+    them all in one persistent launch (replayed as a CUDA graph)."""
+
+    def __init__(self, items):
+        torch = _torch()
+        L = lib()
+        self.items = list(items)
+        n = len(self.items)
+        self.z = [torch.empty(ops.shape[0], dtype=torch.int32, device=ops.device) for _, ops, _ in self.items]
+        self.st = [torch.empty(ops.shape[0], dtype=torch.int32, device=ops.device) for _, ops, _ in self.items]
+        self._insts = (C.c_void_p * n)(*[inst.handle.value for inst, _, _ in self.items])
+        self._batches = (Batch * n)(*[_batch(inst, ops, off) for inst, ops, off in self.items])
+        self._z = (C.c_void_p * n)(*[t.data_ptr() for t in self.z])
+        self._st = (C.c_void_p * n)(*[t.data_ptr() for t in self.st])
+        h = C.c_void_p()
+        _check(L.vrprpd_multi_create(C.cast(self._insts, C.c_void_p), C.cast(self._batches, C.c_void_p),
+                                     C.cast(self._z, C.c_void_p), C.cast(self._st, C.c_void_p), n, C.byref(h)))
+        self._h = h
+
+    def evaluate(self, stream=None):
+        _check(lib().vrprpd_multi_evaluate(self._h, _stream_ptr(stream)))
+        return self.z, self.st
+
+    def autotune(self, stream=None):
+        cfg = EvalConfig()
+        _check(lib().vrprpd_multi_autotune(self._h, _stream_ptr(stream), C.byref(cfg)))
+        return {"dist_mode": _DIST_NAMES[cfg.dist_mode], "warps_per_block": cfg.warps_per_block}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().vrprpd_multi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -37,6 +37,11 @@ def register(L):
     L.vrprpd_alns_run.argtypes = [vp, C.POINTER(Solution), C.POINTER(AlnsParams), C.c_uint64,
                                   C.POINTER(Solution), C.POINTER(Solution), C.POINTER(AlnsStats), vp, vp]
     L.vrprpd_insertion_matrix.argtypes = [vp, vp, vp, C.c_int32, vp, vp, vp]
+    L.vrprpd_multi_create.argtypes = [vp, vp, vp, vp, C.c_int32, C.POINTER(vp)]
+    L.vrprpd_multi_evaluate.argtypes = [vp, vp]
+    L.vrprpd_multi_autotune.argtypes = [vp, vp, vp]
+    L.vrprpd_multi_destroy.argtypes = [vp]
+    L.vrprpd_multi_destroy.restype = None
     L.vrprpd_brkga_params_default.argtypes = [C.POINTER(BrkgaParams)]
     L.vrprpd_brkga_params_default.restype = None
     L.vrprpd_brkga_decode.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp, vp, vp]

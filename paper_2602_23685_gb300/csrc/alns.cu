@@ -1204,7 +1204,7 @@ static int choose_team_blocks(const vrprpd_instance* I, int requested, size_t sm
         const long long G = 2ll * I->n + I->m;
         const long long tiles = ((G + TR - 1) / TR) * ((G + TC - 1) / TC);
         tb = static_cast<int>(std::min<long long>(tiles, maxb));
-        if (G < 256) tb = 1;
+        if (G < 64) tb = 1;
     }
     *out = std::max(1, std::min(tb, maxb));
     return VRPRPD_OK;
@@ -1320,7 +1320,7 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     const int qcap = dump ? 1 : qmax;
     DevBuf B;
     B.cap = team_bytes(n, m, qcap, iters, dump) + 4096;
-    VRP_CUDA(cudaMalloc(&B.base, B.cap));
+    VRP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&B.base), B.cap, stream));
     AlnsTeam t{};
     t.n = n;
     t.m = m;
@@ -1348,7 +1348,7 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     t.mode = mode;
     t.dump_c = dump_c;
     carve_team(t, B, n, m, qcap, iters, dump);
-    auto cleanup = [&]() { cudaFree(B.base); };
+    auto cleanup = [&]() { cudaFreeAsync(B.base, stream); };
     AlnsCtl ctl{};
     ctl.wd[0] = 1.0;
     ctl.wr[0] = ctl.wr[1] = 1.0;
@@ -1378,11 +1378,11 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
         if (e == cudaSuccess) e = cudaMemsetAsync(t.dump_delta, 0xff, G * G * 4, stream);
     }
     AlnsTeam* d_team = nullptr;
-    if (e == cudaSuccess) e = cudaMalloc(&d_team, sizeof(AlnsTeam));
+    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_team), sizeof(AlnsTeam), stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_team, &t, sizeof(AlnsTeam), cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) {
         cleanup();
-        cudaFree(d_team);
+        cudaFreeAsync(d_team, stream);
         set_error("alns setup: %s", cudaGetErrorString(e));
         return VRPRPD_ECUDA;
     }
@@ -1390,52 +1390,53 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     VRP_CHECK(smem <= I->smem_optin, VRPRPD_EINVAL, "ALNS shared memory %zu exceeds the limit", smem);
     int tb = 1;
     int rc = choose_team_blocks(I, P->team_blocks, smem, &tb);
-    if (rc) { cleanup(); cudaFree(d_team); return rc; }
+    if (rc) { cleanup(); cudaFreeAsync(d_team, stream); return rc; }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, stream);
     rc = launch_alns(I, d_team, 1, tb, smem, stream);
     cudaEventRecord(e1, stream);
-    if (rc) { cleanup(); cudaFree(d_team); return rc; }
+    if (rc) { cleanup(); cudaFreeAsync(d_team, stream); return rc; }
     e = cudaStreamSynchronize(stream);
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     AlnsCtl out{};
-    if (e == cudaSuccess) e = cudaMemcpy(&out, t.ctl, sizeof(out), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&out, t.ctl, sizeof(out), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
         cleanup();
-        cudaFree(d_team);
+        cudaFreeAsync(d_team, stream);
         set_error("alns run: %s", cudaGetErrorString(e));
         return VRPRPD_ECUDA;
     }
     if (out.err != 0) {
         cleanup();
-        cudaFree(d_team);
+        cudaFreeAsync(d_team, stream);
         set_error("alns device error %d (%s)", out.err,
                   out.err == DEV_TIMEOUT_BARRIER ? "team barrier timed out" : "inconsistent state");
         return out.err == DEV_TIMEOUT_BARRIER ? VRPRPD_ETIMEOUT : VRPRPD_ECUDA;
     }
     if (dump) {
         const size_t G = static_cast<size_t>(dump_off[m]) + m;
-        e = cudaMemcpy(dump_delta, t.dump_delta, G * G * 4, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess && dump_travel) e = cudaMemcpy(dump_travel, t.dump_travel, G * G * 4, cudaMemcpyDeviceToHost);
+        e = cudaMemcpyAsync(dump_delta, t.dump_delta, G * G * 4, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess && dump_travel) e = cudaMemcpyAsync(dump_travel, t.dump_travel, G * G * 4, cudaMemcpyDeviceToHost, stream);
     } else {
         if (best) {
-            e = cudaMemcpy(best->ops, t.best_ops, 2 * n * 4, cudaMemcpyDeviceToHost);
-            if (e == cudaSuccess) e = cudaMemcpy(best->off, t.best_off, (m + 1) * 4, cudaMemcpyDeviceToHost);
+            e = cudaMemcpyAsync(best->ops, t.best_ops, 2 * n * 4, cudaMemcpyDeviceToHost, stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(best->off, t.best_off, (m + 1) * 4, cudaMemcpyDeviceToHost, stream);
             best->makespan = out.z_best;
             best->status = 0;
         }
         if (current && e == cudaSuccess) {
-            e = cudaMemcpy(current->ops, t.cur_ops, 2 * n * 4, cudaMemcpyDeviceToHost);
-            if (e == cudaSuccess) e = cudaMemcpy(current->off, t.cur_off, (m + 1) * 4, cudaMemcpyDeviceToHost);
+            e = cudaMemcpyAsync(current->ops, t.cur_ops, 2 * n * 4, cudaMemcpyDeviceToHost, stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(current->off, t.cur_off, (m + 1) * 4, cudaMemcpyDeviceToHost, stream);
             current->makespan = out.z_cur;
             current->status = 0;
         }
-        if (trace && e == cudaSuccess && iters > 0) e = cudaMemcpy(trace, t.trace, iters * 4, cudaMemcpyDeviceToHost);
+        if (trace && e == cudaSuccess && iters > 0) e = cudaMemcpyAsync(trace, t.trace, iters * 4, cudaMemcpyDeviceToHost, stream);
     }
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
@@ -1455,8 +1456,9 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
         stats->fallback_entries = static_cast<int64_t>(out.fallback_entries);
         stats->team_blocks = tb;
     }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     cleanup();
-    cudaFree(d_team);
+    cudaFreeAsync(d_team, stream);
     if (e != cudaSuccess) {
         set_error("alns copy-out: %s", cudaGetErrorString(e));
         return VRPRPD_ECUDA;

@@ -416,14 +416,19 @@ extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_par
     // device buffers
     const size_t keys_b = static_cast<size_t>(pop) * L * 4;
     std::vector<void*> allocs;
+    bool alloc_failed = false;
     auto dalloc = [&](size_t bytes) -> void* {
         void* p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+        if (cudaMallocAsync(&p, std::max<size_t>(bytes, 16), s) != cudaSuccess) {
+            alloc_failed = true;
+            return nullptr;
+        }
         allocs.push_back(p);
         return p;
     };
     auto cleanup = [&]() {
-        for (void* p : allocs) cudaFree(p);
+        for (void* p : allocs) cudaFreeAsync(p, s);
+        cudaStreamSynchronize(s);
         cudaStreamDestroy(s);
     };
     float* buf0 = static_cast<float*>(dalloc(keys_b));
@@ -442,9 +447,7 @@ extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_par
     BrkgaCtl* ctl = static_cast<BrkgaCtl*>(dalloc(sizeof(BrkgaCtl)));
     int32_t* wops = static_cast<int32_t*>(dalloc(2 * n * 4));
     int32_t* woff = static_cast<int32_t*>(dalloc((m + 1) * 4));
-    for (void* p : allocs)
-        if (!p) { cleanup(); set_error("BRKGA: device allocation failed"); return VRPRPD_ENOMEM; }
-    if (allocs.size() != 17) { cleanup(); set_error("BRKGA: device allocation failed"); return VRPRPD_ENOMEM; }
+    if (alloc_failed) { cleanup(); set_error("BRKGA: device allocation failed"); return VRPRPD_ENOMEM; }
     const unsigned long long key = stream_key(seed, RNG_STREAM_BRKGA), wkey = stream_key(seed, RNG_STREAM_WARM);
     BrkgaCtl c0{0, 0, 0, 0};
     cudaError_t e = cudaMemcpyAsync(ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, s);
@@ -515,17 +518,20 @@ extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_par
     e = cudaStreamSynchronize(s);
     BrkgaCtl cend{};
     int best_idx = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&cend, ctl, sizeof(cend), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(&best_idx, rank, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cend, ctl, sizeof(cend), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&best_idx, rank, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     long long bf = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(&bf, fit + best_idx, 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bf, fit + best_idx, 8, cudaMemcpyDeviceToHost, s);
     int32_t bz = 0;
-    if (e == cudaSuccess) e = cudaMemcpy(best->ops, dops + static_cast<long long>(best_idx) * 2 * n, 2 * n * 4, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(best->off, doff + static_cast<long long>(best_idx) * (m + 1), (m + 1) * 4, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess) e = cudaMemcpy(&bz, zdec + best_idx, 4, cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && trace) e = cudaMemcpy(trace, dtrace, static_cast<size_t>(G) * 8, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(best->ops, dops + static_cast<long long>(best_idx) * 2 * n, 2 * n * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(best->off, doff + static_cast<long long>(best_idx) * (m + 1), (m + 1) * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bz, zdec + best_idx, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && trace) e = cudaMemcpyAsync(trace, dtrace, static_cast<size_t>(G) * 8, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && final_keys)
-        e = cudaMemcpy(final_keys, cend.sel == 0 ? buf0 : buf1, keys_b, cudaMemcpyDeviceToDevice);
+        e = cudaMemcpyAsync(final_keys, cend.sel == 0 ? buf0 : buf1, keys_b, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { cleanup(); set_error("BRKGA copy-out: %s", cudaGetErrorString(e)); return VRPRPD_ECUDA; }
     best->makespan = bz;
     best->status = 0;

@@ -22,6 +22,7 @@
 // global memory, distances from global memory.
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -65,12 +66,233 @@ __device__ __forceinline__ int dist(const EvalArgs& a, const int32_t* sh, int i,
     }
 }
 
+// One tile of k candidates of one instance, processed by one warp.
+// W is the warp's shared-memory region (layout from a), sh/sp the block's
+// staged distances or coordinates and p.  Returns false if a bounded TMA
+// wait gave up (the caller must stop).
+template <int DM>
+__device__ __forceinline__ bool eval_tile(const EvalArgs& a, const int32_t* sh, const int32_t* sp, int32_t* W,
+                                          uint64_t* bar, unsigned& phase, long long t) {
+    const int lane = threadIdx.x & 31;
+    const int n = a.n, m = a.m, two_n = 2 * n, k = a.k;
+    int32_t* A = W;
+    int32_t* ready = A + a.a_words;
+    uint32_t* seen = reinterpret_cast<uint32_t*>(ready + a.ready_words);
+    uint32_t* starts = seen + a.seen_words;
+    int32_t* soff = reinterpret_cast<int32_t*>(starts + a.start_words);
+    int32_t* valid = soff + a.off_words;
+    int32_t* red = valid + a.valid_words;      // 96 words
+    const int grp = lane / m, v = lane - grp * m;
+    const unsigned gmask = (grp < k) ? (m == 32 ? FULL_MASK : (((1u << m) - 1u) << (grp * m))) : 0u;
+    const long long first = t * k;
+    const int kt = static_cast<int>(min(static_cast<long long>(k), a.num - first));
+    const int elems = kt * two_n;
+    const int32_t* src = a.ops + first * two_n;
+
+    // ---- 1. stage ops: aligned interior by TMA, head/tail by plain loads ----
+    const uintptr_t s0 = reinterpret_cast<uintptr_t>(src);
+    const uintptr_t s1 = s0 + static_cast<uintptr_t>(elems) * 4u;
+    const uintptr_t i0 = (s0 + 15u) & ~static_cast<uintptr_t>(15u);
+    const uintptr_t i1 = s1 & ~static_cast<uintptr_t>(15u);
+    const bool bulk = i1 > i0;
+    const int k0 = bulk ? static_cast<int>((i0 - s0) >> 2) : elems;
+    const int ke = bulk ? static_cast<int>((i1 - s0) >> 2) : elems;
+    const int shift = (4 - (k0 & 3)) & 3;
+    int32_t* Ab = A + shift;
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0 && bulk) {
+        mbar_arrive_expect_tx(bar, static_cast<unsigned>(i1 - i0));
+        tma_bulk_g2s(Ab + k0, reinterpret_cast<const void*>(i0), static_cast<unsigned>(i1 - i0), bar);
+    }
+    for (int e = lane; e < k0; e += 32) Ab[e] = __ldg(src + e);
+    for (int e = ke + lane; e < elems; e += 32) Ab[e] = __ldg(src + e);
+    for (int i = lane; i < kt * (m + 1); i += 32) soff[i] = __ldg(a.off + first * (m + 1) + i);
+    for (int i = lane; i < kt; i += 32) valid[i] = 1;
+    for (int i = lane; i < kt * a.sw; i += 32) seen[i] = 0u;
+    for (int i = lane; i < (elems + 31) / 32; i += 32) starts[i] = 0u;
+    for (int i = lane; i < kt * (n + 1); i += 32) ready[i] = UNRESOLVED;
+    __syncwarp();
+    // offsets: off[0] = 0, off[m] = 2n, non-decreasing
+    for (int i = lane; i < kt * (m + 1); i += 32) {
+        const int g = i / (m + 1), vv = i - g * (m + 1);
+        const int val = soff[i];
+        bool bad = val < 0 || val > two_n || (vv == 0 && val != 0) || (vv == m && val != two_n) ||
+                   (vv < m && val > soff[i + 1]);
+        if (bad) atomicAnd(&valid[g], 0);
+    }
+    __syncwarp();
+    for (int i = lane; i < kt * m; i += 32) {
+        const int g = i / m, vv = i - g * m;
+        if (!valid[g]) continue;
+        const int o0 = soff[g * (m + 1) + vv], o1 = soff[g * (m + 1) + vv + 1];
+        if (o0 < o1) {
+            const int e = g * two_n + o0;
+            atomicOr(&starts[e >> 5], 1u << (e & 31));
+        }
+    }
+    if (bulk) {
+        if (!mbar_wait_bounded(bar, phase)) {
+            if (lane == 0) atomicExch(a.err, DEV_TIMEOUT_TMA);
+            mbar_wait_bounded(bar, phase);
+            return false;
+        }
+        phase ^= 1u;
+    }
+    __syncwarp();
+
+    // ---- 2. pre-pass: validate and pack (travel-in << 12 | op) in place ----
+    // Four chunks of 32 ops per round so their distance reads overlap.
+    // Candidate index of element e without a division: the candidate of the
+    // round's first element plus boundary steps (none when k == 1).
+    {
+        int carry = 0, gbase = 0;
+        for (int base = 0; base < elems; base += 128) {
+            int raw[4], prv[4], gg[4], dd[4];
+            bool in[4], ok[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = base + 32 * u + lane;
+                in[u] = e < elems;
+                raw[u] = in[u] ? Ab[e] : 2;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int pv = __shfl_up_sync(FULL_MASK, raw[u], 1);
+                if (lane == 0) pv = carry;
+                carry = __shfl_sync(FULL_MASK, raw[u], 31);
+                prv[u] = pv;
+            }
+            if (k > 1)
+                while ((gbase + 1) * two_n <= base) ++gbase;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = base + 32 * u + lane;
+                int g = gbase;
+                if (k > 1)
+                    while ((g + 1) * two_n <= e) ++g;
+                gg[u] = g;
+                ok[u] = raw[u] >= 2 && raw[u] <= two_n + 1;
+                const bool is_start = in[u] && ((starts[e >> 5] >> (e & 31)) & 1u);
+                const int pc = (is_start || prv[u] < 2 || prv[u] > two_n + 1) ? 0 : (prv[u] >> 1);
+                dd[u] = dist<DM>(a, sh, pc, ok[u] ? (raw[u] >> 1) : 0);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                bool bad = !ok[u];
+                if (in[u] && ok[u]) {
+                    const unsigned bit = 1u << (raw[u] & 31);
+                    bad = (atomicOr(&seen[gg[u] * a.sw + (raw[u] >> 5)], bit) & bit) != 0u;
+                }
+                if (in[u] && bad) atomicAnd(&valid[gg[u]], 0);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = base + 32 * u + lane;
+                if (in[u]) Ab[e] = (dd[u] << PACK_SHIFT) | (ok[u] ? raw[u] : 2);
+            }
+        }
+    }
+    __syncwarp();
+
+    // ---- 3. route walk (branch-free; up to two ops per lane per step) ----
+    // Ready times have a single writer (the dropping lane) and are read
+    // with volatile loads: a pickup sees either "unresolved" (and retries
+    // next step) or the final value.  The __syncwarp at the end of each
+    // step makes every write of step t visible in step t+1, so a group
+    // with no progress in a step can never progress again (a cycle).
+    const bool mine = grp < kt && valid[grp] != 0;
+    int pos = 0, end = 0, start = 0;
+    if (mine) {
+        start = pos = soff[grp * (m + 1) + v];
+        end = soff[grp * (m + 1) + v + 1];
+    }
+    const int* wp = Ab + (grp < k ? grp : 0) * two_n;
+    volatile int* rdy = ready + (grp < k ? grp : 0) * (n + 1);
+    int dep = 0, s = 0, smin = 0, smax = 0;
+    bool walking = mine && pos < end, cyc = false;
+    while (__any_sync(FULL_MASK, walking)) {
+        // first op
+        const int w1 = walking ? wp[pos] : 0;
+        const int c1 = (w1 & PACK_MASK) >> 1;
+        const bool p1 = (w1 & 1) != 0;
+        const int r1 = rdy[c1];
+        const bool go1 = walking && (!p1 || r1 >= 0);
+        const int a1 = dep + (w1 >> PACK_SHIFT);
+        if (go1 && !p1) rdy[c1] = a1 + sp[c1];
+        dep = go1 ? max(a1, p1 ? r1 : 0) : dep;
+        s += go1 ? (p1 ? 1 : -1) : 0;
+        smin = min(smin, s);
+        smax = max(smax, s);
+        pos += go1 ? 1 : 0;
+        // second op, only behind a first one that went
+        const bool try2 = go1 && pos < end;
+        const int w2 = try2 ? wp[pos] : 0;
+        const int c2 = (w2 & PACK_MASK) >> 1;
+        const bool p2 = (w2 & 1) != 0;
+        const int r2 = rdy[c2];
+        const bool go2 = try2 && (!p2 || r2 >= 0);
+        const int a2 = dep + (w2 >> PACK_SHIFT);
+        if (go2 && !p2) rdy[c2] = a2 + sp[c2];
+        dep = go2 ? max(a2, p2 ? r2 : 0) : dep;
+        s += go2 ? (p2 ? 1 : -1) : 0;
+        smin = min(smin, s);
+        smax = max(smax, s);
+        pos += go2 ? 1 : 0;
+        const unsigned prog = __ballot_sync(FULL_MASK, go1);
+        const bool more = pos < end;
+        cyc = cyc || (walking && more && (prog & gmask) == 0u);
+        walking = walking && more && !cyc;
+        __syncwarp();
+    }
+    if (cyc)                                   // finish the stock prefix of a blocked route
+        for (; pos < end; ++pos) {
+            const int o = wp[pos] & PACK_MASK;
+            if (o & 1) { ++s; smax = max(smax, s); } else { --s; smin = min(smin, s); }
+        }
+    const int last = (end > start) ? ((wp[end - 1] & PACK_MASK) >> 1) : 0;
+
+    // ---- 4. per-candidate reduction ----
+    int ret = 0, flags = 0, pool = 0;
+    if (mine) {
+        if (!cyc && end > start) ret = dep + dist<DM>(a, sh, last, 0);
+        if (a.load_full) {
+            flags = (smin < -a.Q || smax > 0) ? VRPRPD_VEH_CAP : 0;
+            pool = a.Q;
+        } else {
+            flags = (-smin + smax > a.Q) ? VRPRPD_VEH_CAP : 0;
+            pool = -smin;
+        }
+        if (cyc) flags |= VRPRPD_CYCLE;
+    }
+    red[lane] = ret;
+    red[32 + lane] = flags;
+    red[64 + lane] = pool;
+    __syncwarp();
+    if (grp < kt && v == 0) {
+        int z = 0, f = 0;
+        long long pl = 0;
+        for (int j = 0; j < m; ++j) {
+            z = max(z, red[grp * m + j]);
+            f |= red[32 + grp * m + j];
+            pl += red[64 + grp * m + j];
+        }
+        if (pl > a.R) f |= VRPRPD_POOL;
+        if (f & VRPRPD_CYCLE) z = 0x7fffffff;
+        if (!valid[grp]) { z = 0x7fffffff; f = VRPRPD_MALFORMED; }
+        a.z[first + grp] = z;
+        a.st[first + grp] = static_cast<uint32_t>(f);
+    }
+    __syncwarp();
+    return true;
+}
+
 template <int DM>
 __global__ void __launch_bounds__(1024) eval_tiles_kernel(EvalArgs a) {
     extern __shared__ __align__(16) int32_t smem[];
     __shared__ __align__(8) uint64_t block_bar;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int n = a.n, m = a.m, two_n = 2 * n, k = a.k;
 
     // ---- block-wide staging of the instance (TMA bulk copies) ----
     int32_t* sh = smem;                        // distances or coordinates
@@ -94,231 +316,47 @@ __global__ void __launch_bounds__(1024) eval_tiles_kernel(EvalArgs a) {
         mbar_wait_bounded(&block_bar, 0);      // give copies in flight one more bounded chance
         return;
     }
-
-    // ---- per-warp regions ----
     int32_t* W = smem + a.shared_words + warp * a.warp_words;
-    int32_t* A = W;
-    int32_t* ready = A + a.a_words;
-    uint32_t* seen = reinterpret_cast<uint32_t*>(ready + a.ready_words);
-    uint32_t* starts = seen + a.seen_words;
-    int32_t* soff = reinterpret_cast<int32_t*>(starts + a.start_words);
-    int32_t* valid = soff + a.off_words;
-    int32_t* red = valid + a.valid_words;      // 96 words
-    uint64_t* bar = reinterpret_cast<uint64_t*>(red + 96);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(W + a.warp_words - 4);
     if (lane == 0) mbar_init(bar, 1);
     __syncwarp();
-
-    const long long ntiles = (a.num + k - 1) / k;
+    const long long ntiles = (a.num + a.k - 1) / a.k;
     const long long gw = static_cast<long long>(blockIdx.x) * nwarps + warp;
     const long long nw = static_cast<long long>(gridDim.x) * nwarps;
-    const int grp = lane / m, v = lane - grp * m;
-    const unsigned gmask = (grp < k) ? (m == 32 ? FULL_MASK : (((1u << m) - 1u) << (grp * m))) : 0u;
     unsigned phase = 0;
+    for (long long t = gw; t < ntiles; t += nw)
+        if (!eval_tile<DM>(a, sh, sp, W, bar, phase, t)) return;
+}
 
-    for (long long t = gw; t < ntiles; t += nw) {
-        const long long first = t * k;
-        const int kt = static_cast<int>(min(static_cast<long long>(k), a.num - first));
-        const int elems = kt * two_n;
-        const int32_t* src = a.ops + first * two_n;
-
-        // ---- 1. stage ops: aligned interior by TMA, head/tail by plain loads ----
-        const uintptr_t s0 = reinterpret_cast<uintptr_t>(src);
-        const uintptr_t s1 = s0 + static_cast<uintptr_t>(elems) * 4u;
-        const uintptr_t i0 = (s0 + 15u) & ~static_cast<uintptr_t>(15u);
-        const uintptr_t i1 = s1 & ~static_cast<uintptr_t>(15u);
-        const bool bulk = i1 > i0;
-        const int k0 = bulk ? static_cast<int>((i0 - s0) >> 2) : elems;
-        const int ke = bulk ? static_cast<int>((i1 - s0) >> 2) : elems;
-        const int shift = (4 - (k0 & 3)) & 3;
-        int32_t* Ab = A + shift;
-        fence_proxy_async_smem();
-        __syncwarp();
-        if (lane == 0 && bulk) {
-            mbar_arrive_expect_tx(bar, static_cast<unsigned>(i1 - i0));
-            tma_bulk_g2s(Ab + k0, reinterpret_cast<const void*>(i0), static_cast<unsigned>(i1 - i0), bar);
+// Many instances of uneven size in one persistent launch: tile t of the
+// whole job belongs to the instance whose tile prefix brackets it.  Distances
+// come from each instance's matrix in global memory (L2-resident); p is read
+// through the cache.  Every warp region is sized for the largest instance.
+template <int DM>
+__global__ void __launch_bounds__(1024) eval_multi_kernel(const EvalArgs* __restrict__ insts,
+                                                          const long long* __restrict__ tile_prefix, int n_inst,
+                                                          int warp_words) {
+    extern __shared__ __align__(16) int32_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int32_t* W = smem + warp * warp_words;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(W + warp_words - 4);
+    if (lane == 0) mbar_init(bar, 1);
+    __syncwarp();
+    const long long total = tile_prefix[n_inst];
+    const long long gw = static_cast<long long>(blockIdx.x) * nwarps + warp;
+    const long long nw = static_cast<long long>(gridDim.x) * nwarps;
+    unsigned phase = 0;
+    for (long long t = gw; t < total; t += nw) {
+        int lo = 0, hi = n_inst;                // prefix[lo] <= t < prefix[lo+1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(tile_prefix + mid) <= t) lo = mid; else hi = mid;
         }
-        for (int e = lane; e < k0; e += 32) Ab[e] = __ldg(src + e);
-        for (int e = ke + lane; e < elems; e += 32) Ab[e] = __ldg(src + e);
-        for (int i = lane; i < kt * (m + 1); i += 32) soff[i] = __ldg(a.off + first * (m + 1) + i);
-        for (int i = lane; i < kt; i += 32) valid[i] = 1;
-        for (int i = lane; i < kt * a.sw; i += 32) seen[i] = 0u;
-        for (int i = lane; i < (elems + 31) / 32; i += 32) starts[i] = 0u;
-        for (int i = lane; i < kt * (n + 1); i += 32) ready[i] = UNRESOLVED;
-        __syncwarp();
-        // offsets: off[0] = 0, off[m] = 2n, non-decreasing
-        for (int i = lane; i < kt * (m + 1); i += 32) {
-            const int g = i / (m + 1), vv = i - g * (m + 1);
-            const int val = soff[i];
-            bool bad = val < 0 || val > two_n || (vv == 0 && val != 0) || (vv == m && val != two_n) ||
-                       (vv < m && val > soff[i + 1]);
-            if (bad) atomicAnd(&valid[g], 0);
-        }
-        __syncwarp();
-        for (int i = lane; i < kt * m; i += 32) {
-            const int g = i / m, vv = i - g * m;
-            if (!valid[g]) continue;
-            const int o0 = soff[g * (m + 1) + vv], o1 = soff[g * (m + 1) + vv + 1];
-            if (o0 < o1) {
-                const int e = g * two_n + o0;
-                atomicOr(&starts[e >> 5], 1u << (e & 31));
-            }
-        }
-        if (bulk) {
-            if (!mbar_wait_bounded(bar, phase)) {
-                if (lane == 0) atomicExch(a.err, DEV_TIMEOUT_TMA);
-                mbar_wait_bounded(bar, phase);
-                return;
-            }
-            phase ^= 1u;
-        }
-        __syncwarp();
-
-        // ---- 2. pre-pass: validate and pack (travel-in << 12 | op) in place ----
-        // Four chunks of 32 ops per round so their distance reads overlap.
-        // Candidate index of element e without a division: the candidate of the
-        // round's first element plus boundary steps (none when k == 1).
-        {
-            int carry = 0, gbase = 0;
-            for (int base = 0; base < elems; base += 128) {
-                int raw[4], prv[4], gg[4], dd[4];
-                bool in[4], ok[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int e = base + 32 * u + lane;
-                    in[u] = e < elems;
-                    raw[u] = in[u] ? Ab[e] : 2;
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    int pv = __shfl_up_sync(FULL_MASK, raw[u], 1);
-                    if (lane == 0) pv = carry;
-                    carry = __shfl_sync(FULL_MASK, raw[u], 31);
-                    prv[u] = pv;
-                }
-                if (k > 1)
-                    while ((gbase + 1) * two_n <= base) ++gbase;
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int e = base + 32 * u + lane;
-                    int g = gbase;
-                    if (k > 1)
-                        while ((g + 1) * two_n <= e) ++g;
-                    gg[u] = g;
-                    ok[u] = raw[u] >= 2 && raw[u] <= two_n + 1;
-                    const bool is_start = in[u] && ((starts[e >> 5] >> (e & 31)) & 1u);
-                    const int pc = (is_start || prv[u] < 2 || prv[u] > two_n + 1) ? 0 : (prv[u] >> 1);
-                    dd[u] = dist<DM>(a, sh, pc, ok[u] ? (raw[u] >> 1) : 0);
-                }
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    bool bad = !ok[u];
-                    if (in[u] && ok[u]) {
-                        const unsigned bit = 1u << (raw[u] & 31);
-                        bad = (atomicOr(&seen[gg[u] * a.sw + (raw[u] >> 5)], bit) & bit) != 0u;
-                    }
-                    if (in[u] && bad) atomicAnd(&valid[gg[u]], 0);
-                }
-                __syncwarp();
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int e = base + 32 * u + lane;
-                    if (in[u]) Ab[e] = (dd[u] << PACK_SHIFT) | (ok[u] ? raw[u] : 2);
-                }
-            }
-        }
-        __syncwarp();
-
-        // ---- 3. route walk (branch-free; up to two ops per lane per step) ----
-        // Ready times have a single writer (the dropping lane) and are read
-        // with volatile loads: a pickup sees either "unresolved" (and retries
-        // next step) or the final value.  The __syncwarp at the end of each
-        // step makes every write of step t visible in step t+1, so a group
-        // with no progress in a step can never progress again (a cycle).
-        const bool mine = grp < kt && valid[grp] != 0;
-        int pos = 0, end = 0, start = 0;
-        if (mine) {
-            start = pos = soff[grp * (m + 1) + v];
-            end = soff[grp * (m + 1) + v + 1];
-        }
-        const int* wp = Ab + (grp < k ? grp : 0) * two_n;
-        volatile int* rdy = ready + (grp < k ? grp : 0) * (n + 1);
-        int dep = 0, s = 0, smin = 0, smax = 0;
-        bool walking = mine && pos < end, cyc = false;
-        while (__any_sync(FULL_MASK, walking)) {
-            // first op
-            const int w1 = walking ? wp[pos] : 0;
-            const int c1 = (w1 & PACK_MASK) >> 1;
-            const bool p1 = (w1 & 1) != 0;
-            const int r1 = rdy[c1];
-            const bool go1 = walking && (!p1 || r1 >= 0);
-            const int a1 = dep + (w1 >> PACK_SHIFT);
-            if (go1 && !p1) rdy[c1] = a1 + sp[c1];
-            dep = go1 ? max(a1, p1 ? r1 : 0) : dep;
-            s += go1 ? (p1 ? 1 : -1) : 0;
-            smin = min(smin, s);
-            smax = max(smax, s);
-            pos += go1 ? 1 : 0;
-            // second op, only behind a first one that went
-            const bool try2 = go1 && pos < end;
-            const int w2 = try2 ? wp[pos] : 0;
-            const int c2 = (w2 & PACK_MASK) >> 1;
-            const bool p2 = (w2 & 1) != 0;
-            const int r2 = rdy[c2];
-            const bool go2 = try2 && (!p2 || r2 >= 0);
-            const int a2 = dep + (w2 >> PACK_SHIFT);
-            if (go2 && !p2) rdy[c2] = a2 + sp[c2];
-            dep = go2 ? max(a2, p2 ? r2 : 0) : dep;
-            s += go2 ? (p2 ? 1 : -1) : 0;
-            smin = min(smin, s);
-            smax = max(smax, s);
-            pos += go2 ? 1 : 0;
-            const unsigned prog = __ballot_sync(FULL_MASK, go1);
-            const bool more = pos < end;
-            cyc = cyc || (walking && more && (prog & gmask) == 0u);
-            walking = walking && more && !cyc;
-            __syncwarp();
-        }
-        if (cyc)                                   // finish the stock prefix of a blocked route
-            for (; pos < end; ++pos) {
-                const int o = wp[pos] & PACK_MASK;
-                if (o & 1) { ++s; smax = max(smax, s); } else { --s; smin = min(smin, s); }
-            }
-        const int last = (end > start) ? ((wp[end - 1] & PACK_MASK) >> 1) : 0;
-
-        // ---- 4. per-candidate reduction ----
-        int ret = 0, flags = 0, pool = 0;
-        if (mine) {
-            if (!cyc && end > start) ret = dep + dist<DM>(a, sh, last, 0);
-            if (a.load_full) {
-                flags = (smin < -a.Q || smax > 0) ? VRPRPD_VEH_CAP : 0;
-                pool = a.Q;
-            } else {
-                flags = (-smin + smax > a.Q) ? VRPRPD_VEH_CAP : 0;
-                pool = -smin;
-            }
-            if (cyc) flags |= VRPRPD_CYCLE;
-        }
-        red[lane] = ret;
-        red[32 + lane] = flags;
-        red[64 + lane] = pool;
-        __syncwarp();
-        if (grp < kt && v == 0) {
-            int z = 0, f = 0;
-            long long pl = 0;
-            for (int j = 0; j < m; ++j) {
-                z = max(z, red[grp * m + j]);
-                f |= red[32 + grp * m + j];
-                pl += red[64 + grp * m + j];
-            }
-            if (pl > a.R) f |= VRPRPD_POOL;
-            if (f & VRPRPD_CYCLE) z = 0x7fffffff;
-            if (!valid[grp]) { z = 0x7fffffff; f = VRPRPD_MALFORMED; }
-            a.z[first + grp] = z;
-            a.st[first + grp] = static_cast<uint32_t>(f);
-        }
-        __syncwarp();
+        const EvalArgs a = insts[lo];
+        if (!eval_tile<DM>(a, nullptr, a.p, W, bar, phase, t - __ldg(tile_prefix + lo))) return;
     }
 }
+
 
 // ---------------------------------------------------------------------------
 // Plain form: thread per candidate, global scratch, Kahn order.
@@ -739,3 +777,190 @@ extern "C" int vrprpd_autotune(vrprpd_instance* I, const vrprpd_batch* b, void* 
     VRP_CUDA(cudaGetLastError());
     return VRPRPD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// many instances, one persistent launch
+// ---------------------------------------------------------------------------
+struct vrprpd_multi {
+    int n_inst = 0, device = 0, num_sms = 0;
+    size_t smem_optin = 0;
+    std::vector<EvalArgs> args;
+    std::vector<long long> prefix;
+    EvalArgs* d_args = nullptr;
+    long long* d_prefix = nullptr;
+    int dm = VRPRPD_DIST_GLOBAL16, warps = 8, blocks = 0, warp_words = 0;
+    size_t smem = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t graph_stream = nullptr;
+};
+
+namespace vrp {
+
+static int multi_layout(vrprpd_multi* M, int dm, int warps) {
+    int ww = 0;
+    for (auto& a : M->args) ww = std::max(ww, a.warp_words);
+    const size_t smem = static_cast<size_t>(warps) * ww * 4;
+    if (smem + 64 > M->smem_optin) return VRPRPD_EINVAL;
+    const void* fn = dm == VRPRPD_DIST_GLOBAL16 ? reinterpret_cast<const void*>(&eval_multi_kernel<VRPRPD_DIST_GLOBAL16>)
+                                                : reinterpret_cast<const void*>(&eval_multi_kernel<VRPRPD_DIST_GLOBAL32>);
+    VRP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    int occ = 0;
+    VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, warps * 32, smem));
+    if (occ <= 0) return VRPRPD_EINVAL;
+    const long long total = M->prefix.back();
+    M->blocks = static_cast<int>(std::max<long long>(1, std::min<long long>(static_cast<long long>(occ) * M->num_sms,
+                                                                         (total + warps - 1) / warps)));
+    M->dm = dm;
+    M->warps = warps;
+    M->warp_words = ww;
+    M->smem = smem;
+    if (M->exec) { cudaGraphExecDestroy(M->exec); M->exec = nullptr; }
+    if (M->graph) { cudaGraphDestroy(M->graph); M->graph = nullptr; }
+    return VRPRPD_OK;
+}
+
+static int multi_launch(vrprpd_multi* M, cudaStream_t s) {
+    if (M->dm == VRPRPD_DIST_GLOBAL16)
+        eval_multi_kernel<VRPRPD_DIST_GLOBAL16><<<M->blocks, M->warps * 32, M->smem, s>>>(M->d_args, M->d_prefix,
+                                                                                         M->n_inst, M->warp_words);
+    else
+        eval_multi_kernel<VRPRPD_DIST_GLOBAL32><<<M->blocks, M->warps * 32, M->smem, s>>>(M->d_args, M->d_prefix,
+                                                                                         M->n_inst, M->warp_words);
+    VRP_CUDA(cudaGetLastError());
+    return VRPRPD_OK;
+}
+
+}  // namespace vrp
+
+extern "C" int vrprpd_multi_create(const vrprpd_instance* const* insts, const vrprpd_batch* batches,
+                                   int32_t* const* makespan, uint32_t* const* status, int32_t n_inst,
+                                   vrprpd_multi** out) {
+    VRP_CHECK(insts && batches && makespan && status && out && n_inst >= 1, VRPRPD_EINVAL, "bad arguments");
+    *out = nullptr;
+    vrprpd_multi* M = new vrprpd_multi();
+    M->n_inst = n_inst;
+    M->prefix.assign(1, 0);
+    bool all16 = true;
+    for (int i = 0; i < n_inst; ++i) {
+        const vrprpd_instance* I = insts[i];
+        int rc = check_batch(I, &batches[i], makespan[i], status[i]);
+        if (rc) { delete M; return rc; }
+        if (!batched_supported(I)) {
+            delete M;
+            set_error("instance %d: batched evaluation needs m <= 32, 2n+1 < 4096, max d < 2^19", i);
+            return VRPRPD_EINVAL;
+        }
+        if (i == 0) {
+            M->device = I->device;
+            M->num_sms = I->num_sms;
+            M->smem_optin = I->smem_optin;
+        } else if (I->device != M->device) {
+            delete M;
+            set_error("instances live on different devices");
+            return VRPRPD_EINVAL;
+        }
+        all16 = all16 && I->has_d16;
+        Plan P;
+        make_plan(I, VRPRPD_DIST_GLOBAL32, 1, 0, batches[i].num, &P);
+        EvalArgs a = P.args;
+        a.shared_words = 0;
+        a.dist_words = 0;
+        a.ops = batches[i].ops;
+        a.off = batches[i].off;
+        a.z = makespan[i];
+        a.st = status[i];
+        M->args.push_back(a);
+        M->prefix.push_back(M->prefix.back() + (a.num + a.k - 1) / a.k);
+    }
+    cudaError_t e = cudaMalloc(&M->d_args, sizeof(EvalArgs) * n_inst);
+    if (e == cudaSuccess) e = cudaMalloc(&M->d_prefix, sizeof(long long) * (n_inst + 1));
+    if (e == cudaSuccess) e = cudaMemcpy(M->d_args, M->args.data(), sizeof(EvalArgs) * n_inst, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(M->d_prefix, M->prefix.data(), sizeof(long long) * (n_inst + 1), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        set_error("multi_create: %s", cudaGetErrorString(e));
+        vrprpd_multi_destroy(M);
+        return VRPRPD_ECUDA;
+    }
+    int rc = VRPRPD_EINVAL;
+    for (int warps : {8, 4, 2, 1}) {
+        rc = multi_layout(M, all16 ? VRPRPD_DIST_GLOBAL16 : VRPRPD_DIST_GLOBAL32, warps);
+        if (rc == VRPRPD_OK) break;
+    }
+    if (rc) {
+        set_error("multi_create: no layout fits shared memory");
+        vrprpd_multi_destroy(M);
+        return rc;
+    }
+    *out = M;
+    return VRPRPD_OK;
+}
+
+extern "C" int vrprpd_multi_evaluate(vrprpd_multi* M, void* stream_) {
+    VRP_CHECK(M, VRPRPD_EINVAL, "NULL plan");
+    cudaStream_t s = static_cast<cudaStream_t>(stream_);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (s != nullptr) VRP_CUDA(cudaStreamIsCapturing(s, &cs));
+    if (s == nullptr || cs != cudaStreamCaptureStatusNone) return multi_launch(M, s);
+    if (!M->exec || M->graph_stream != s) {
+        if (M->exec) { cudaGraphExecDestroy(M->exec); M->exec = nullptr; }
+        if (M->graph) { cudaGraphDestroy(M->graph); M->graph = nullptr; }
+        VRP_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int rc = multi_launch(M, s);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+        VRP_CHECK(e == cudaSuccess, VRPRPD_ECUDA, "capture failed: %s", cudaGetErrorString(e));
+        M->graph = g;
+        VRP_CUDA(cudaGraphInstantiate(&M->exec, g, 0));
+        M->graph_stream = s;
+    }
+    VRP_CUDA(cudaGraphLaunch(M->exec, s));
+    return VRPRPD_OK;
+}
+
+extern "C" int vrprpd_multi_autotune(vrprpd_multi* M, void* stream_, vrprpd_eval_config* chosen) {
+    VRP_CHECK(M, VRPRPD_EINVAL, "NULL plan");
+    cudaStream_t s = static_cast<cudaStream_t>(stream_);
+    bool all16 = true;
+    for (auto& a : M->args) all16 = all16 && a.d16 != nullptr;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int bdm = M->dm, bw = M->warps;
+    for (int dm : {VRPRPD_DIST_GLOBAL16, VRPRPD_DIST_GLOBAL32}) {
+        if (dm == VRPRPD_DIST_GLOBAL16 && !all16) continue;
+        for (int warps : {4, 8, 12, 16, 24, 32}) {
+            if (multi_layout(M, dm, warps) != VRPRPD_OK) continue;
+            float ms_min = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                cudaEventRecord(e0, s);
+                multi_launch(M, s);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) ms_min = std::min(ms_min, ms);
+            }
+            if (ms_min < best) { best = ms_min; bdm = dm; bw = warps; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int rc = multi_layout(M, bdm, bw);
+    if (rc) return rc;
+    if (chosen) { chosen->dist_mode = bdm; chosen->warps_per_block = bw; chosen->blocks_per_sm = 0; }
+    VRP_CUDA(cudaGetLastError());
+    return VRPRPD_OK;
+}
+
+extern "C" void vrprpd_multi_destroy(vrprpd_multi* M) {
+    if (!M) return;
+    if (M->exec) cudaGraphExecDestroy(M->exec);
+    if (M->graph) cudaGraphDestroy(M->graph);
+    cudaFree(M->d_args);
+    cudaFree(M->d_prefix);
+    delete M;
+}
+

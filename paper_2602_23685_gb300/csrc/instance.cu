@@ -60,7 +60,7 @@ static int finish_create(vrprpd_instance* I, vrprpd_instance** out) {
     }
     VRP_CUDA(cudaMalloc(&I->err, 16));
     VRP_CUDA(cudaMemset(I->err, 0, 16));
-    VRP_CUDA(cudaDeviceSynchronize());
+    VRP_CUDA(cudaStreamSynchronize(nullptr));   // this creation's own work only
     *out = I;
     return VRPRPD_OK;
 }

@@ -169,3 +169,16 @@ CONFIGS = {
                per_instance=4096),
     "C5": dict(n=1000, m=20, R=100, Q=10, variant="1R20", layout="mixed"),
 }
+
+
+def uneven_instances(count, n_lo, n_hi, Q, variant, seed, per_instance_seed=1000):
+    """Configuration-4 style set: n log-uniform in [n_lo, n_hi], m = ceil(n/25),
+    R = ceil(n/10), Q fixed, uniform coordinates."""
+    sizes = loguniform_sizes(count, n_lo, n_hi, seed)
+    out = []
+    for i, n in enumerate(sizes):
+        n = int(n)
+        m = -(-n // 25)
+        R = -(-n // 10)
+        out.append(make_instance(n, m, R, Q, variant, "uniform", seed=per_instance_seed + i))
+    return out
