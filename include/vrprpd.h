@@ -116,6 +116,27 @@ int vrprpd_evaluate_host(const vrprpd_instance* inst, const vrprpd_batch* host_b
 int vrprpd_evaluate_plain(const vrprpd_instance* inst, const vrprpd_batch* batch,
                           int32_t* makespan, uint32_t* status, void* stream);
 
+/*
+ * vrprpd_evaluate_plain without any device allocation.  The paper has no
+ * counterpart; this exists for callers that cannot let a library allocate
+ * device memory: code recording a CUDA graph, serving processes that reserve
+ * their memory budget up front, and processes whose framework caching
+ * allocator already holds the free memory.
+ *   Same arguments, results and stream semantics as vrprpd_evaluate_plain.
+ *   Scratch: a fixed 16 MiB array inside the library image (4 Mi int32 words),
+ *   present on every GPU that loads the library until the process exits.  A
+ *   call needs (n+1) + 3m + ceil((2n+2)/32) words per thread and fails with
+ *   VRPRPD_EINVAL when that leaves room for fewer than 32 threads.
+ *   The first call on each device looks up the array's device address (a
+ *   runtime query, not an allocation); make that first call before any stream
+ *   capture.  Every call shares the one array: calls whose kernels overlap on
+ *   the GPU (different streams, or host threads without ordering) race on it.
+ *   The kernel initialises every scratch word it reads, so leftover contents
+ *   from a previous call are harmless.
+ */
+int vrprpd_evaluate_plain_noalloc(const vrprpd_instance* inst, const vrprpd_batch* batch,
+                                  int32_t* makespan, uint32_t* status, void* stream);
+
 /* Wait for stream and report a device-side error the kernels recorded for
  * this instance (VRPRPD_ETIMEOUT if a bounded wait gave up), then clear it. */
 int vrprpd_sync(const vrprpd_instance* inst, void* stream);

@@ -964,3 +964,58 @@ extern "C" void vrprpd_multi_destroy(vrprpd_multi* M) {
     delete M;
 }
 
+// ---------------------------------------------------------------------------
+// Plain evaluation without any device allocation.
+//
+// Some callers cannot let the library allocate device memory: code that is
+// recording a CUDA graph (an allocation there is not part of the capture and
+// breaks it), serving processes that reserve their whole memory budget up
+// front and must not grow, and processes whose framework caching allocator
+// already holds the free device memory, so a fresh cudaMalloc would fail.
+// For them this entry point runs the plain one-thread-per-candidate kernel
+// with its per-thread scratch (ready times, route cursors, the op bitmap)
+// carved from a fixed array that is part of the library image: 16 MiB on each
+// GPU that loads the library, held until the process exits.
+// ---------------------------------------------------------------------------
+namespace vrp {
+constexpr long long NOALLOC_SCRATCH_WORDS = 4ll << 20;   // 4 Mi int32 = 16 MiB
+static __device__ __align__(256) int32_t g_noalloc_scratch[NOALLOC_SCRATCH_WORDS];
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+static std::mutex g_noalloc_mu;
+}  // namespace vrp
+
+extern "C" int vrprpd_evaluate_plain_noalloc(const vrprpd_instance* I, const vrprpd_batch* b, int32_t* z,
+                                             uint32_t* st, void* stream) {
+    int rc = check_batch(I, b, z, st);
+    if (rc) return rc;
+    if (b->num == 0) return VRPRPD_OK;
+    const long long words = (I->n + 1) + 3ll * I->m + (2ll * I->n + 2 + 31) / 32;
+    const long long max_threads = NOALLOC_SCRATCH_WORDS / words;
+    VRP_CHECK(max_threads >= 32, VRPRPD_EINVAL,
+              "instance needs %lld scratch words per thread; the fixed %lld-word scratch fits fewer than 32 "
+              "threads (use vrprpd_evaluate_plain)", words, NOALLOC_SCRATCH_WORDS);
+    int dev = 0;
+    VRP_CUDA(cudaGetDevice(&dev));
+    VRP_CHECK(dev >= 0 && dev < NOALLOC_MAX_DEVICES, VRPRPD_EINVAL, "device index %d too large", dev);
+    void* scratch = nullptr;
+    {
+        // one-time set-up per device (the current one): the host needs the
+        // array's device address; the symbol's host-side name is not it
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void* p = nullptr;
+            VRP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    const int threads = 128;
+    const long long want = (b->num + threads - 1) / threads;
+    const int blocks = static_cast<int>(std::max<long long>(1, std::min<long long>(want, max_threads / threads)));
+    eval_plain_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
+        b->ops, b->off, b->num, I->n, I->m, I->R, I->Q, (I->flags & VRPRPD_LOAD_FULL) != 0, I->d32, I->p, z, st,
+        static_cast<int32_t*>(scratch), static_cast<int>(words));
+    VRP_CUDA(cudaGetLastError());
+    return VRPRPD_OK;
+}
