@@ -218,6 +218,7 @@ typedef struct {
     int64_t matrix_entries;    /* insertion-matrix entries evaluated in O(1) */
     int64_t fallback_entries;  /* entries re-simulated in full */
     int32_t team_blocks;       /* CTAs used */
+    double phase_ms[6];        /* wall time per phase: begin, prep, gaps, matrix, select, end */
 } vrprpd_alns_stats;
 
 void vrprpd_alns_params_default(vrprpd_alns_params* params);
@@ -319,6 +320,59 @@ int vrprpd_brkga_decode(const vrprpd_instance* inst, const float* keys, int32_t 
 int vrprpd_brkga_run(const vrprpd_instance* inst, const vrprpd_brkga_params* params,
                      const vrprpd_solution* warm, uint64_t seed, vrprpd_solution* best,
                      int64_t* best_fitness, int64_t* trace, float* final_keys, void* stream);
+
+/* ======================================================================== */
+/* Serving: continuous batching of solve requests                            */
+/* ======================================================================== */
+
+/* A solve request: the instance (host arrays, copied at submit) and the
+ * pipeline's budgets.  The server runs ALNS from the deterministic start
+ * solution, then BRKGA warm-started from the ALNS incumbent (Section 4,
+ * "sequential two-stage pipeline"), and answers with the better of the two. */
+typedef struct {
+    const int32_t* coords;     /* host, (n+1) x 2 */
+    const int32_t* p;          /* host, n */
+    int32_t n, m, R, Q;
+    uint32_t flags;
+    vrprpd_alns_params alns;   /* iterations >= 1; team_blocks is set by the server */
+    vrprpd_brkga_params brkga; /* generations = 0 skips BRKGA */
+    uint64_t seed;
+} vrprpd_request;
+
+typedef struct {
+    int64_t id;
+    int32_t status;            /* VRPRPD_OK or the error the request hit */
+    int32_t z_alns, z_brkga, z_best;
+    double t_submit_ms, t_start_ms, t_end_ms;   /* server clock */
+    double device_ms;
+    int32_t n, m;
+    char message[160];         /* error text when status != VRPRPD_OK */
+} vrprpd_result;
+
+typedef struct {
+    int32_t submitted, completed, pending, active, peak_active;
+    size_t bytes_in_use, peak_bytes;
+    double p50_ms, p99_ms;     /* submit-to-finish latency of completed requests */
+} vrprpd_server_stats;
+
+typedef struct vrprpd_server vrprpd_server;
+
+/* Start a server on the current device with max_active worker slots.  A
+ * request is admitted (FIFO) when a slot is free, its estimated device memory
+ * fits what mem_budget leaves, and its ALNS team fits the resident-CTA share;
+ * admitted requests run concurrently on their own streams.  Results do not
+ * depend on what else runs: every draw is counter-based. */
+int vrprpd_server_create(size_t mem_budget, int32_t max_active, vrprpd_server** out);
+/* Queue a request; VRPRPD_EBUSY if it alone exceeds the memory budget. */
+int vrprpd_server_submit(vrprpd_server* server, const vrprpd_request* req, int64_t* id);
+/* VRPRPD_ENOTREADY until the request finished; then fills *out and, when the
+ * host buffers are given, the best routes (ops[2n], off[m+1]). */
+int vrprpd_server_poll(vrprpd_server* server, int64_t id, vrprpd_result* out, int32_t* ops, int32_t* off);
+/* Blocking form of poll. */
+int vrprpd_server_wait(vrprpd_server* server, int64_t id, vrprpd_result* out, int32_t* ops, int32_t* off);
+int vrprpd_server_get_stats(vrprpd_server* server, vrprpd_server_stats* out);
+/* Finish everything queued, stop the workers, free the server. */
+void vrprpd_server_destroy(vrprpd_server* server);
 
 const char* vrprpd_last_error(void);
 

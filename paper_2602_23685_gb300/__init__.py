@@ -391,3 +391,69 @@ class MultiBatch:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+class Server:
+    """Continuous-batching solve server (vrprpd_server_*): requests are admitted
+    by memory budget and worker slots and run concurrently on the device."""
+
+    def __init__(self, mem_budget_bytes, max_active=4):
+        L = lib()
+        _torch()
+        h = C.c_void_p()
+        _check(L.vrprpd_server_create(C.c_size_t(int(mem_budget_bytes)), int(max_active), C.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, w, alns_iterations, brkga_pop=0, brkga_generations=0, seed=0, q_min=0, q_max=0):
+        from ._search_sig import Request
+        coords = np.ascontiguousarray(w.coords, dtype=np.int32)
+        p = np.ascontiguousarray(w.p, dtype=np.int32)
+        req = Request(coords.ctypes.data, p.ctypes.data, w.n, w.m, w.R, w.Q, 0,
+                      alns_params(alns_iterations, q_min, q_max),
+                      brkga_params(max(brkga_pop, 2), brkga_generations), C.c_uint64(seed))
+        rid = C.c_int64()
+        _check(lib().vrprpd_server_submit(self._h, C.byref(req), C.byref(rid)))
+        self._keep[rid.value] = (w.n, w.m)
+        return rid.value
+
+    def _result(self, fn, rid):
+        from ._search_sig import Result
+        n, m = self._keep[rid]
+        res = Result()
+        ops = np.zeros(2 * n, np.int32)
+        off = np.zeros(m + 1, np.int32)
+        rc = fn(self._h, C.c_int64(rid), C.byref(res), ops.ctypes.data, off.ctypes.data)
+        if rc == -6:
+            return None
+        _check(rc)
+        return {"id": res.id, "status": res.status, "z_alns": res.z_alns, "z_brkga": res.z_brkga,
+                "z_best": res.z_best, "ops": ops, "off": off, "t_submit_ms": res.t_submit_ms,
+                "t_start_ms": res.t_start_ms, "t_end_ms": res.t_end_ms, "device_ms": res.device_ms,
+                "message": res.message.decode(errors="replace")}
+
+    def poll(self, rid):
+        return self._result(lib().vrprpd_server_poll, rid)
+
+    def wait(self, rid):
+        return self._result(lib().vrprpd_server_wait, rid)
+
+    def stats(self):
+        from ._search_sig import ServerStats
+        st = ServerStats()
+        _check(lib().vrprpd_server_get_stats(self._h, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lib().vrprpd_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -20,13 +20,32 @@ class AlnsStats(C.Structure):
                 ("z_init", C.c_int32), ("z_best", C.c_int32), ("z_current", C.c_int32),
                 ("T_final", C.c_double), ("w_destroy", C.c_double * 4), ("w_repair", C.c_double * 4),
                 ("device_ms", C.c_double), ("matrix_entries", C.c_int64),
-                ("fallback_entries", C.c_int64), ("team_blocks", C.c_int32)]
+                ("fallback_entries", C.c_int64), ("team_blocks", C.c_int32), ("phase_ms", C.c_double * 6)]
 
 
 class BrkgaParams(C.Structure):
     _fields_ = [("pop", C.c_int32), ("generations", C.c_int32), ("warm_slots", C.c_int32),
                 ("warm_variants", C.c_int32), ("elite_frac", C.c_float), ("mutant_frac", C.c_float),
                 ("rho", C.c_float), ("eps", C.c_float)]
+
+
+class Request(C.Structure):
+    _fields_ = [("coords", C.c_void_p), ("p", C.c_void_p), ("n", C.c_int32), ("m", C.c_int32),
+                ("R", C.c_int32), ("Q", C.c_int32), ("flags", C.c_uint32), ("alns", AlnsParams),
+                ("brkga", BrkgaParams), ("seed", C.c_uint64)]
+
+
+class Result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("z_alns", C.c_int32), ("z_brkga", C.c_int32),
+                ("z_best", C.c_int32), ("t_submit_ms", C.c_double), ("t_start_ms", C.c_double),
+                ("t_end_ms", C.c_double), ("device_ms", C.c_double), ("n", C.c_int32), ("m", C.c_int32),
+                ("message", C.c_char * 160)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int32), ("completed", C.c_int32), ("pending", C.c_int32),
+                ("active", C.c_int32), ("peak_active", C.c_int32), ("bytes_in_use", C.c_size_t),
+                ("peak_bytes", C.c_size_t), ("p50_ms", C.c_double), ("p99_ms", C.c_double)]
 
 
 def register(L):
@@ -47,4 +66,11 @@ def register(L):
     L.vrprpd_brkga_decode.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp, vp, vp]
     L.vrprpd_brkga_run.argtypes = [vp, C.POINTER(BrkgaParams), C.POINTER(Solution), C.c_uint64,
                                    C.POINTER(Solution), vp, vp, vp, vp]
+    L.vrprpd_server_create.argtypes = [C.c_size_t, C.c_int32, C.POINTER(vp)]
+    L.vrprpd_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(C.c_int64)]
+    L.vrprpd_server_poll.argtypes = [vp, C.c_int64, C.POINTER(Result), vp, vp]
+    L.vrprpd_server_wait.argtypes = [vp, C.c_int64, C.POINTER(Result), vp, vp]
+    L.vrprpd_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+    L.vrprpd_server_destroy.argtypes = [vp]
+    L.vrprpd_server_destroy.restype = None
     return L

@@ -335,7 +335,7 @@ static int plan_decode(const vrprpd_instance* I, int num, DecPlan* D) {
     D->smem_dist = (base_words + dist_words) * 4 + 64 <= I->smem_optin && N1 <= 240 ? 1 : 0;
     D->smem = (base_words + (D->smem_dist ? dist_words : 0)) * 4;
     VRP_CHECK(D->smem + 64 <= I->smem_optin, VRPRPD_EINVAL, "decode shared memory %zu too large", D->smem);
-    VRP_CUDA(cudaFuncSetAttribute(decode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(D->smem)));
+    { int rc_ = ensure_smem_limit(reinterpret_cast<const void*>(&decode_kernel)); if (rc_) return rc_; }
     int occ = 0;
     VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_kernel, DEC_WARPS * 32, D->smem));
     VRP_CHECK(occ > 0, VRPRPD_EINVAL, "decode block does not fit");
@@ -478,7 +478,7 @@ extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_par
     const int Prank = pow2_at_least(pop);
     const size_t rank_smem = static_cast<size_t>(Prank) * 8;
     VRP_CHECK(rank_smem + 64 <= I->smem_optin, VRPRPD_EINVAL, "population too large for the ranking kernel");
-    VRP_CUDA(cudaFuncSetAttribute(rank_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(rank_smem)));
+    { int rc_ = ensure_smem_limit(reinterpret_cast<const void*>(&rank_kernel)); if (rc_) { cleanup(); return rc_; } }
     const int evo_blocks = static_cast<int>(std::min<long long>((static_cast<long long>(pop) * L + 255) / 256, 8192));
     auto enqueue_eval_rank = [&]() -> int {
         decode_kernel<<<D.blocks, DEC_WARPS * 32, D.smem, s>>>(da);

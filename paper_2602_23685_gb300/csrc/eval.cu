@@ -460,6 +460,8 @@ static bool coords_small(const vrprpd_instance* I) {
     return dx * dx + dy * dy < (1ll << 24);
 }
 
+bool coords_exact_small(const vrprpd_instance* I) { return coords_small(I); }
+
 bool batched_supported(const vrprpd_instance* I) {
     return I->m <= 32 && 2 * I->n + 1 < (1 << PACK_SHIFT) && I->maxd < (1 << 19);
 }
@@ -530,7 +532,7 @@ static const void* kernel_for(int dm) {
 
 static int finalize_plan(const vrprpd_instance* I, int blocks_per_sm, Plan* P) {
     const void* fn = kernel_for(P->dm);
-    VRP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(P->smem)));
+    { int rc_ = ensure_smem_limit(fn); if (rc_) return rc_; }
     int occ = 0;
     VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, P->warps * 32, P->smem));
     VRP_CHECK(occ > 0, VRPRPD_EINVAL, "evaluation layout does not fit on an SM");
@@ -804,7 +806,7 @@ static int multi_layout(vrprpd_multi* M, int dm, int warps) {
     if (smem + 64 > M->smem_optin) return VRPRPD_EINVAL;
     const void* fn = dm == VRPRPD_DIST_GLOBAL16 ? reinterpret_cast<const void*>(&eval_multi_kernel<VRPRPD_DIST_GLOBAL16>)
                                                 : reinterpret_cast<const void*>(&eval_multi_kernel<VRPRPD_DIST_GLOBAL32>);
-    VRP_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    { int rc_ = ensure_smem_limit(fn); if (rc_) return rc_; }
     int occ = 0;
     VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, warps * 32, smem));
     if (occ <= 0) return VRPRPD_EINVAL;

@@ -3,6 +3,9 @@
 #include <cstdarg>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -38,6 +41,23 @@ __global__ void narrow16_kernel(const int32_t* __restrict__ d32, uint16_t* __res
     for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
          i += static_cast<long long>(gridDim.x) * blockDim.x)
         d16[i] = static_cast<uint16_t>(d32[i]);
+}
+
+int ensure_smem_limit(const void* kernel) {
+    static std::mutex mu;
+    static std::set<std::pair<const void*, int>> done;
+    int dev = 0;
+    VRP_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({kernel, dev})) return VRPRPD_OK;
+    cudaFuncAttributes fa{};
+    VRP_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    int optin = 0;
+    VRP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    VRP_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin - static_cast<int>(fa.sharedSizeBytes)));
+    done.insert({kernel, dev});
+    return VRPRPD_OK;
 }
 
 static size_t pad16(size_t bytes) { return (bytes + 15) & ~static_cast<size_t>(15); }

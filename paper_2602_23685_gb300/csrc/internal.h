@@ -13,6 +13,12 @@ namespace vrp {
 
 void set_error(const char* fmt, ...);
 
+// Raise a kernel's dynamic shared-memory limit to everything the device
+// allows, once per (kernel, device).  The limit is per-function global state,
+// so setting it per launch would race between host threads that launch the
+// same kernel with different sizes; the size a launch uses is its own.
+int ensure_smem_limit(const void* kernel);
+
 #define VRP_CUDA(call)                                                                   \
     do {                                                                                 \
         cudaError_t e_ = (call);                                                         \
