@@ -61,6 +61,7 @@ struct AlnsCtl {
     int accepted, improved, new_best, reheats, rejected;
     int z_init;
     unsigned long long entries, fallback_entries;
+    unsigned long long phase_ns[6];   // begin, prep, gaps, matrix, select, end (rank 0 wall time)
 };
 
 struct AlnsTeam {
@@ -74,6 +75,7 @@ struct AlnsTeam {
     unsigned long long key;  // RNG stream key
     int mode;                // 0 = search, 1 = one-customer matrix dump
     int dump_c;
+    const int* coords;       // device (n+1) x 2 when distances can be recomputed exactly, else null
     // state and scratch (device)
     AlnsCtl* ctl;
     int *cur_ops, *cur_off, *best_ops, *best_off;
@@ -85,7 +87,8 @@ struct AlnsTeam {
     int log_levels;
     int *gx, *gy, *gHx, *gTy, *gw, *gsb, *gpmin, *gpmax, *gsmin, *gsmax, *groute, *gpos;
     int *rload;              // start load per route
-    unsigned long long* keys;  // [q_max][G]
+    unsigned long long* keys;  // [q_max][G]: per drop gap, best (dz, dt, col)
+    unsigned long long* rkeys; // [q_max][32]: per drop vehicle, best (dz, dt, row)
     unsigned char* sc;         // [q_max][G]
     int* slist;                // [q_max * G] entries t * G + g
     int* trace;
@@ -107,17 +110,27 @@ struct Smem {
     int* colv;      // [TC][CV]
     int* misc;      // 64 ints
     unsigned char* flags;  // [n + 1] removed flags / route-start bits
+    int* xy;        // coordinates [n + 1][2] (when staged)
 };
-constexpr int RV = 16, CV = 12;
+constexpr int RV = 16, CV = 12;   // row / col vector widths (ints)
+constexpr int CB = 4, RPC = 7, CPC = 5;  // customers per matrix batch; per-customer row / col vector widths
 
-__host__ __device__ inline size_t alns_smem_words(int n, int m) {
+// walk buffers (one ready array per warp), also holding a matrix batch's vectors
+__host__ __device__ inline size_t rdy_words(int n) {
+    const size_t walks = static_cast<size_t>(ALNS_WARPS) * (((n + 1) + 3) & ~3);
+    const size_t batch = static_cast<size_t>(CB) * (TR * RPC + TC * CPC);
+    return walks > batch ? walks : batch;
+}
+
+__host__ __device__ inline size_t alns_smem_words(int n, int m, bool with_coords) {
     size_t w = 0;
     w += ((2 * n + 4) + 3) & ~3;
     w += ((m + 1) + 3) & ~3;
     w += ((n + 1) + 3) & ~3;
-    w += static_cast<size_t>(ALNS_WARPS) * (((n + 1) + 3) & ~3);
+    w += rdy_words(n);
     w += TR * LPS + TC + TR * RV + TC * CV + 64;
     w += ((n + 1 + 3) / 4 + 3) & ~3;
+    if (with_coords) w += ((2 * (n + 1)) + 3) & ~3;   // coordinates
     return w;
 }
 
@@ -127,17 +140,26 @@ __device__ inline Smem carve(int* base, int n, int m) {
     s.sW = q; q += ((2 * n + 4) + 3) & ~3;
     s.sWoff = q; q += ((m + 1) + 3) & ~3;
     s.sp = q; q += ((n + 1) + 3) & ~3;
-    s.rdy = q; q += ALNS_WARPS * (((n + 1) + 3) & ~3);
+    s.rdy = q; q += rdy_words(n);
     s.lp = q; q += TR * LPS;
     s.reach = reinterpret_cast<unsigned*>(q); q += TC;
     s.rowv = q; q += TR * RV;
     s.colv = q; q += TC * CV;
     s.misc = q; q += 64;
     s.flags = reinterpret_cast<unsigned char*>(q);
+    q += ((n + 1 + 3) / 4 + 3) & ~3;
+    s.xy = q;
     return s;
 }
 
 __device__ __forceinline__ int D(const AlnsTeam& t, int a, int b) { return __ldg(t.d32 + a * (t.n + 1) + b); }
+
+// Same value as D: recomputed exactly (EUC_2D) from shared-memory coordinates
+// when the instance has small ones, so no L2 round trip sits on the path.
+__device__ __forceinline__ int Dx(const AlnsTeam& t, const Smem& s, int a, int b) {
+    if (t.coords) return euc2d_small(s.xy[2 * a], s.xy[2 * a + 1], s.xy[2 * b], s.xy[2 * b + 1]);
+    return __ldg(t.d32 + a * (t.n + 1) + b);
+}
 
 // ---------------------------------------------------------------------------
 // team barrier: all CTAs of the team; bounded (about 2 s), sets ctl->err
@@ -191,7 +213,7 @@ __device__ void stage_W(const AlnsTeam& t, const Smem& s) {
         }
         const int o = W[k];
         const int prev = (k == s.sWoff[lo]) ? 0 : (W[k - 1] >> 1);
-        s.sW[k] = (D(t, prev, o >> 1) << PACK_SHIFT) | o;
+        s.sW[k] = (Dx(t, s, prev, o >> 1) << PACK_SHIFT) | o;
     }
     __syncthreads();
 }
@@ -257,7 +279,7 @@ __device__ void walk_depot(const AlnsTeam& t, const Smem& s, int* rdy, bool writ
             t.SMAXs[k] = mx;
         }
     }
-    int ret = (mine && !cyc && end > start) ? dep + D(t, last, 0) : 0;
+    int ret = (mine && !cyc && end > start) ? dep + Dx(t, s, last, 0) : 0;
     int load = 0;
     bool bad = false;
     if (mine) {
@@ -316,7 +338,7 @@ __device__ void walk_source(const AlnsTeam& t, const Smem& s, int* rdy, int u, i
             else if (prog == 0u) { walking = false; atomicExch(&t.ctl->err, DEV_BAD_STATE); }
         }
     }
-    int tail = (mine && val != NEG) ? val + D(t, last, 0) : NEG;
+    int tail = (mine && val != NEG) ? val + Dx(t, s, last, 0) : NEG;
     for (int o = 16; o > 0; o >>= 1) tail = max(tail, __shfl_xor_sync(FULL_MASK, tail, o));
     if (lane == 0) t.T[u] = tail;
 }
@@ -354,7 +376,7 @@ __device__ int walk_insert(const AlnsTeam& t, const Smem& s, int* rdy, int c, in
             pick = o & 1;
             if (pick) rv = rdy[cc];
             go = !pick || rv != UNRES;
-            if (go) dd = (which != 0 || prev_virtual) ? D(t, loc, cc) : (s.sW[base + k] >> PACK_SHIFT);
+            if (go) dd = (which != 0 || prev_virtual) ? Dx(t, s, loc, cc) : (s.sW[base + k] >> PACK_SHIFT);
         }
         __syncwarp();
         if (go) {
@@ -375,7 +397,7 @@ __device__ int walk_insert(const AlnsTeam& t, const Smem& s, int* rdy, int c, in
             else if (prog == 0u) { walking = false; cyc = true; }
         }
     }
-    int ret = (mine && any && !cyc) ? dep + D(t, loc, 0) : 0;
+    int ret = (mine && any && !cyc) ? dep + Dx(t, s, loc, 0) : 0;
     for (int o = 16; o > 0; o >>= 1) ret = max(ret, __shfl_xor_sync(FULL_MASK, ret, o));
     const unsigned anycyc = __ballot_sync(FULL_MASK, cyc);
     return anycyc ? 0x7fffffff : ret;
@@ -441,9 +463,9 @@ __device__ __forceinline__ int travel_delta(const AlnsTeam& t, const Smem& s, in
     auto locy = [&](int g) { return t.gy[g] >= 0 ? (s.sW[t.gy[g]] & PACK_MASK) >> 1 : 0; };
     const int xr = locx(row), yr = locy(row);
     if (t.groute[row] == t.groute[col] && t.gpos[row] == t.gpos[col])
-        return D(t, xr, c) + D(t, c, c) + D(t, c, yr) - t.gw[row];
+        return Dx(t, s, xr, c) + Dx(t, s, c, c) + Dx(t, s, c, yr) - t.gw[row];
     const int xc = locx(col), yc = locy(col);
-    return (D(t, xr, c) + D(t, c, yr) - t.gw[row]) + (D(t, xc, c) + D(t, c, yc) - t.gw[col]);
+    return (Dx(t, s, xr, c) + Dx(t, s, c, yr) - t.gw[row]) + (Dx(t, s, xc, c) + Dx(t, s, c, yc) - t.gw[col]);
 }
 
 // ---------------------------------------------------------------------------
@@ -475,15 +497,19 @@ __device__ void phase_prep(const AlnsTeam& t, const Smem& s, int rank, int team_
     for (long long e = tid; e < total; e += nthr) {
         const int ti = static_cast<int>(e / G), g = static_cast<int>(e - static_cast<long long>(ti) * G);
         const int c = t.rem[ti];
-        // gap g -> route r and position
-        int r = 0, base = 0;
-        while (r < t.m && g > base + (s.sWoff[r + 1] - s.sWoff[r])) { base += s.sWoff[r + 1] - s.sWoff[r] + 1; ++r; }
-        const int pos = g - base, L = s.sWoff[r + 1] - s.sWoff[r];
+        // gap g -> route r (gaps of route r start at off[r] + r) and position
+        int lo = 0, hi = t.m;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s.sWoff[mid] + mid <= g) lo = mid; else hi = mid;
+        }
+        const int r = lo, pos = g - (s.sWoff[r] + r), L = s.sWoff[r + 1] - s.sWoff[r];
         const int x = pos > 0 ? (s.sW[s.sWoff[r] + pos - 1] & PACK_MASK) >> 1 : 0;
         const int y = pos < L ? (s.sW[s.sWoff[r] + pos] & PACK_MASK) >> 1 : 0;
-        const int w = (L == 0) ? 0 : D(t, x, y);
-        const bool shortcut = D(t, x, c) + D(t, c, y) < w;
+        const int w = (L == 0) ? 0 : Dx(t, s, x, y);
+        const bool shortcut = Dx(t, s, x, c) + Dx(t, s, c, y) < w;
         t.keys[static_cast<long long>(ti) * G + g] = KEY_NONE;
+        if (g < 32) t.rkeys[ti * 32 + g] = KEY_NONE;
         t.sc[static_cast<long long>(ti) * G + g] = shortcut ? 1 : 0;
         if (shortcut) {
             const int slot = atomicAdd(&ctl->n_short, 1);
@@ -498,9 +524,12 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
     const long long nthr = static_cast<long long>(team_blocks) * blockDim.x;
     for (long long gg = tid; gg < G; gg += nthr) {
         const int g = static_cast<int>(gg);
-        int r = 0, base = 0;
-        while (r < m && g > base + (s.sWoff[r + 1] - s.sWoff[r])) { base += s.sWoff[r + 1] - s.sWoff[r] + 1; ++r; }
-        const int pos = g - base, off = s.sWoff[r], L = s.sWoff[r + 1] - off;
+        int lo = 0, hi = m;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s.sWoff[mid] + mid <= g) lo = mid; else hi = mid;
+        }
+        const int r = lo, pos = g - (s.sWoff[r] + r), off = s.sWoff[r], L = s.sWoff[r + 1] - off;
         const int xo = pos > 0 ? off + pos - 1 : -1, yo = pos < L ? off + pos : -1;
         const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0;
         const int y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
@@ -508,7 +537,7 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
         t.gy[g] = yo;
         t.gHx[g] = xo >= 0 ? t.H[xo] : 0;
         t.gTy[g] = yo >= 0 ? t.T[yo] : 0;
-        t.gw[g] = L == 0 ? 0 : D(t, x, y);
+        t.gw[g] = L == 0 ? 0 : Dx(t, s, x, y);
         t.gsb[g] = xo >= 0 ? t.S_[xo] : 0;
         t.gpmin[g] = xo >= 0 ? t.PMINp[xo] : 0;
         t.gpmax[g] = xo >= 0 ? t.PMAXp[xo] : 0;
@@ -534,10 +563,16 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
 }
 
 // One matrix tile (rows rt*TR.., cols ct*TC..) for every customer still to insert.
+// Everything that depends only on the gaps (head/tail times, the removed leg,
+// stock extremes and the capacity of inserting a lone drop or pickup) is
+// loaded once per tile; per customer only d(x,c) and d(c,y) are read, and the
+// next customer's reads are in flight while the current one's entries run.
 __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, int N, int G) {
     AlnsCtl* ctl = t.ctl;
     const int tid = threadIdx.x;
     const int r0 = rt * TR, c0 = ct * TC;
+    int* rowc = s.rowv;                        // [TR][RV] tile constants of the drop gaps
+    int* colc = s.colv;                        // [TC][CV] tile constants of the pickup gaps
     // LP tile: lp[r][c] = LP(stop after row gap -> stop before col gap)
     for (int e = tid; e < TR * TC; e += blockDim.x) {
         const int r = e / TC, c = e - r * TC;
@@ -563,92 +598,129 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
             if (lane == 0) s.reach[c] = bits;
         }
     }
+    // tile constants
+    const bool is_col = tid < TC;
+    const bool is_row = tid >= TC && tid < TC + TR;
+    const int myg = is_col ? c0 + tid : (is_row ? r0 + tid - TC : G);
+    if (is_row) {
+        int* v = rowc + (tid - TC) * RV;
+        const int R = myg;
+        if (R < G) {
+            const int yo = t.gy[R];
+            int la = 0, ladj = 0;
+            const bool okA = cap_ok(t, min(min(t.gpmin[R], t.gsb[R] - 1), t.gsmin[R] - 1),
+                                    max(t.gpmax[R], t.gsmax[R] - 1), la);
+            const bool okAdj = cap_ok(t, min(min(t.gpmin[R], t.gsb[R] - 1), t.gsmin[R]), max(t.gpmax[R], t.gsmax[R]),
+                                      ladj);
+            const int ra = t.groute[R];
+            v[0] = t.gHx[R];
+            v[1] = t.gTy[R];
+            v[2] = t.gw[R];
+            v[6] = okA ? la - t.rload[ra] : 1 << 28;
+            v[7] = okAdj ? ladj - t.rload[ra] : 1 << 28;
+            v[8] = ra;
+            v[9] = t.gpos[R];
+            v[11] = yo;
+            v[12] = t.gpmin[R];
+            v[13] = t.gsb[R];
+            v[14] = t.gpmax[R];
+        } else {
+            v[8] = -1;
+        }
+    }
+    if (is_col) {
+        int* v = colc + tid * CV;
+        const int Cg = myg;
+        if (Cg < G) {
+            const int xo = t.gx[Cg];
+            int lb = 0;
+            const bool okB = cap_ok(t, min(t.gpmin[Cg], t.gsmin[Cg] + 1),
+                                    max(max(t.gpmax[Cg], t.gsb[Cg] + 1), t.gsmax[Cg] + 1), lb);
+            v[4] = okB ? lb - t.rload[t.groute[Cg]] : 1 << 28;
+            v[5] = t.groute[Cg];
+            v[6] = t.gpos[Cg];
+            v[8] = xo;
+            v[9] = t.gsmin[Cg];
+            v[10] = t.gsmax[Cg];
+            v[11] = t.gHx[Cg] + t.gTy[Cg];          // H(x) + T(y)
+        } else {
+            v[5] = -1;
+        }
+    }
+    // Customers go in batches of CB: every thread builds per-customer vector
+    // entries for (customer, gap) pairs of the batch, then every thread runs
+    // its 16 entries for each customer of the batch; two block barriers per
+    // batch.  Per-customer vectors: rows {A1, beta, E, adj, dtD, dtAdj, sc},
+    // cols {gamma, B1, F, dtP, sc}.
+    // The batch vectors live in the per-warp walk buffers, which tiles do not use.
+    int* rvec = s.rdy;                         // [CB][TR][RPC]
+    int* cvec = s.rdy + CB * TR * RPC;         // [CB][TC][CPC]
+    const int nrem = ctl->nrem;
     const int z = ctl->z_work, sumL = ctl->sum_load;
     const bool dump = t.mode == 1;
     unsigned long long local_entries = 0;
-    for (int ti = 0; ti < ctl->nrem; ++ti) {
-        const int c = t.rem[ti], pc = s.sp[c];
-        const int dcc = D(t, c, c);
-        __syncthreads();
-        // row (dropoff) vectors
-        if (tid < TR) {
-            const int R = r0 + tid;
-            int* v = s.rowv + tid * RV;
-            if (R < G) {
-                const int xo = t.gx[R], yo = t.gy[R];
-                const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0, y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
-                const int dxc = D(t, x, c), dcy = D(t, c, y), Hx = t.gHx[R], Ty = t.gTy[R], w = t.gw[R];
-                const int delta = dxc + dcy;
-                int la = 0, ladj = 0;
-                const bool okA = cap_ok(t, min(min(t.gpmin[R], t.gsb[R] - 1), t.gsmin[R] - 1),
-                                        max(t.gpmax[R], t.gsmax[R] - 1), la);
-                const bool okAdj = cap_ok(t, min(min(t.gpmin[R], t.gsb[R] - 1), t.gsmin[R]),
-                                          max(t.gpmax[R], t.gsmax[R]), ladj);
-                const int ra = t.groute[R];
-                v[0] = Hx + dxc;                        // arrival at the new drop
-                v[1] = Hx + delta + Ty;                 // beta: through the drop only
-                v[2] = Hx + delta;                      // leaving the drop towards y
-                v[3] = Hx + dxc + max(dcc, pc) + dcy + Ty;  // adjacent drop+pickup
-                v[4] = delta - w;                       // travel change, drop
-                v[5] = dxc + dcc + dcy - w;             // travel change, adjacent pair
-                v[6] = okA ? la - t.rload[ra] : 1 << 28;
-                v[7] = okAdj ? ladj - t.rload[ra] : 1 << 28;
-                v[8] = ra;
-                v[9] = t.gpos[R];
-                v[10] = t.sc[static_cast<long long>(ti) * G + R];
-                v[11] = yo;
-                v[12] = t.gpmin[R];
-                v[13] = t.gsb[R];
-                v[14] = t.gpmax[R];
+    for (int tb = 0; tb < nrem; tb += CB) {
+        const int nb = min(CB, nrem - tb);
+        __syncthreads();                       // previous batch's entries are done with the vectors
+        for (int it = tid; it < nb * (TR + TC); it += blockDim.x) {
+            const int k = it / (TR + TC), slot = it - k * (TR + TC);
+            const int ti = tb + k, c = t.rem[ti];
+            const int pc = s.sp[c];
+            if (slot < TR) {
+                const int R = r0 + slot;
+                int* v = rvec + (k * TR + slot) * RPC;
+                if (R < G && rowc[slot * RV + 8] >= 0) {
+                    const int xo = t.gx[R], yo = t.gy[R];
+                    const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0, y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
+                    const int dxc = Dx(t, s, x, c), dcy = Dx(t, s, c, y), dcc = Dx(t, s, c, c);
+                    const int Hx = rowc[slot * RV + 0], Ty = rowc[slot * RV + 1], w = rowc[slot * RV + 2];
+                    const int delta = dxc + dcy;
+                    v[0] = Hx + dxc;                               // arrival at the new drop
+                    v[2] = Hx + delta;                             // leaving the drop towards y
+                    v[1] = v[2] + Ty;                              // beta: through the drop only
+                    v[3] = Hx + dxc + max(dcc, pc) + dcy + Ty;     // adjacent drop+pickup
+                    v[4] = delta - w;                              // travel change, drop
+                    v[5] = dxc + dcc + dcy - w;                    // travel change, adjacent pair
+                    v[6] = delta < w ? 1 : 0;                      // shortcut gap (flagged in prep too)
+                }
             } else {
-                v[8] = -1;
-            }
-        }
-        // col (pickup) vectors
-        if (tid < TC) {
-            const int Cg = c0 + tid;
-            int* v = s.colv + tid * CV;
-            if (Cg < G) {
-                const int xo = t.gx[Cg], yo = t.gy[Cg];
-                const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0, y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
-                const int dxc = D(t, x, c), dcy = D(t, c, y), Hx = t.gHx[Cg], Ty = t.gTy[Cg], w = t.gw[Cg];
-                const int delta = dxc + dcy;
-                int lb = 0;
-                const bool okB = cap_ok(t, min(t.gpmin[Cg], t.gsmin[Cg] + 1),
-                                        max(max(t.gpmax[Cg], t.gsb[Cg] + 1), t.gsmax[Cg] + 1), lb);
-                const int rb = t.groute[Cg];
-                v[0] = Hx + delta + Ty;                 // gamma: through the pickup only
-                v[1] = dcy + Ty;                        // leaving the pickup
-                v[2] = delta + Ty;                      // entering the pickup from x
-                v[3] = delta - w;                       // travel change, pickup
-                v[4] = okB ? lb - t.rload[rb] : 1 << 28;
-                v[5] = rb;
-                v[6] = t.gpos[Cg];
-                v[7] = t.sc[static_cast<long long>(ti) * G + Cg];
-                v[8] = xo;
-                v[9] = t.gsmin[Cg];
-                v[10] = t.gsmax[Cg];
-            } else {
-                v[5] = -1;
+                const int cc = slot - TR, Cg = c0 + cc;
+                int* v = cvec + (k * TC + cc) * CPC;
+                if (Cg < G && colc[cc * CV + 5] >= 0) {
+                    const int xo = t.gx[Cg], yo = t.gy[Cg];
+                    const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0, y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
+                    const int dxc = Dx(t, s, x, c), dcy = Dx(t, s, c, y);
+                    const int Ty = t.gTy[Cg], w = t.gw[Cg];
+                    const int delta = dxc + dcy;
+                    v[0] = colc[cc * CV + 11] + delta;             // gamma: through the pickup only
+                    v[1] = dcy + Ty;                               // leaving the pickup
+                    v[2] = delta + Ty;                             // entering the pickup from x
+                    v[3] = delta - w;                              // travel change, pickup
+                    v[4] = delta < w ? 1 : 0;
+                }
             }
         }
         __syncthreads();
         const int r = tid >> 3, cb = tid & 7;
-        const int* rv = s.rowv + r * RV;
-        unsigned long long best = KEY_NONE;
-        if (rv[8] >= 0) {
-            const int R = r0 + r;
+        const int* rk = rowc + r * RV;
+        const bool row_ok = rk[8] >= 0;        // all 8 lanes of a row agree; no early exit (shuffles below)
+        const int R = r0 + r;
+        const int dLA = rk[6], dLAdj = rk[7], ra = rk[8], ia = rk[9];
+        const unsigned rbit = 1u << r;
+        for (int k = 0; k < nb; ++k) {
+            const int ti = tb + k, c = t.rem[ti], pc = s.sp[c];
+            const int* rv = rvec + (k * TR + r) * RPC;
             const int A1 = rv[0], beta = rv[1], E = rv[2], adjv = rv[3], dtD = rv[4], dtAdj = rv[5];
-            const int dLA = rv[6], dLAdj = rv[7], ra = rv[8], ia = rv[9];
-            const bool scR = rv[10] != 0;
-            const unsigned rbit = 1u << r;
-            for (int kk = 0; kk < TC / 8; ++kk) {
+            const bool scR = rv[6] != 0;
+            unsigned long long best = KEY_NONE;
+            for (int kk = 0; row_ok && kk < TC / 8; ++kk) {
                 const int cc = cb + 8 * kk;
-                const int* cv = s.colv + cc * CV;
-                const int rb = cv[5];
+                const int* ck = colc + cc * CV;
+                const int rb = ck[5];
                 if (rb < 0) continue;
-                const int Cg = c0 + cc, jb = cv[6];
-                if (scR || cv[7] != 0) continue;          // shortcut gap: re-simulated in full
+                const int* cv = cvec + (k * TC + cc) * CPC;
+                const int Cg = c0 + cc, jb = ck[6];
+                if (scR || cv[4] != 0) continue;          // shortcut gap: re-simulated in full
                 int znew = 0, dt = 0;
                 bool ok;
                 if (ra == rb) {
@@ -659,9 +731,9 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
                         znew = max(z, adjv);
                         dt = dtAdj;
                     } else {
-                        const int lo = rv[11], hi = cv[8];
-                        const int mn = min(min(min(rv[12], rv[13] - 1), range_min(t, lo, hi, N) - 1), cv[9]);
-                        const int mx = max(max(max(rv[14], range_max(t, lo, hi, N) - 1), t.S_[hi]), cv[10]);
+                        const int lo = rk[11], hi = ck[8];
+                        const int mn = min(min(min(rk[12], rk[13] - 1), range_min(t, lo, hi, N) - 1), ck[9]);
+                        const int mx = max(max(max(rk[14], range_max(t, lo, hi, N) - 1), t.S_[hi]), ck[10]);
                         int l2 = 0;
                         ok = cap_ok(t, mn, mx, l2) && sumL - t.rload[ra] + l2 <= t.R;
                         const int lpv = s.lp[r * LPS + cc];
@@ -669,8 +741,8 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
                         dt = dtD + cv[3];
                     }
                 } else {
-                    ok = (s.reach[cc] & rbit) == 0u && dLA < (1 << 27) && cv[4] < (1 << 27) &&
-                         sumL + dLA + cv[4] <= t.R;
+                    ok = (s.reach[cc] & rbit) == 0u && dLA < (1 << 27) && ck[4] < (1 << 27) &&
+                         sumL + dLA + ck[4] <= t.R;
                     const int lpv = s.lp[r * LPS + cc];
                     znew = max(max(z, beta), max(cv[0], A1 + pc + cv[1]));
                     if (lpv != NEG) znew = max(znew, E + lpv + cv[2]);
@@ -686,14 +758,16 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
                     best = key < best ? key : best;
                 }
             }
+            // min over the 8 lanes sharing a row
+            for (int o = 4; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+                best = other < best ? other : best;
+            }
+            if (!dump && cb == 0 && best != KEY_NONE) {
+                atomicMin(&t.keys[static_cast<long long>(ti) * G + R], best);
+                atomicMin(&t.rkeys[ti * 32 + ra], ((best >> 12) << 12) | static_cast<unsigned long long>(R));
+            }
         }
-        // min over the 8 lanes sharing a row
-        for (int o = 4; o > 0; o >>= 1) {
-            const unsigned long long other = __shfl_xor_sync(FULL_MASK, best, o);
-            best = other < best ? other : best;
-        }
-        if (!dump && cb == 0 && best != KEY_NONE)
-            atomicMin(&t.keys[static_cast<long long>(ti) * G + r0 + r], best);
     }
     atomicAdd(&ctl->entries, local_entries);
 }
@@ -732,7 +806,9 @@ __device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N,
                 t.dump_delta[static_cast<long long>(row) * G + col] = ok ? zn - z : 0x7fffffff;
                 t.dump_travel[static_cast<long long>(row) * G + col] = ok ? dt : 0;
             } else if (ok) {
-                atomicMin(&t.keys[static_cast<long long>(ti) * G + row], pack_key(zn - z, dt, col));
+                const unsigned long long key = pack_key(zn - z, dt, col);
+                atomicMin(&t.keys[static_cast<long long>(ti) * G + row], key);
+                atomicMin(&t.rkeys[ti * 32 + a], ((key >> 12) << 12) | static_cast<unsigned long long>(row));
             }
         }
     }
@@ -763,46 +839,30 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
     AlnsCtl* ctl = t.ctl;
     const int m = t.m, N = s.sWoff[m], G = N + m, nrem = ctl->nrem;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // per-customer results live in the (now free) tile buffer: best at [0, 1024), regret after
-    unsigned long long* bestv = reinterpret_cast<unsigned long long*>(s.lp);        // [nrem]
+    // per-customer results in the (now free) tile buffer
+    unsigned long long* bestv = reinterpret_cast<unsigned long long*>(s.lp);        // [nrem] (dz,dt)<<12 | row
     long long* regret = reinterpret_cast<long long*>(s.lp) + 1024;                 // [nrem]
+    int* bestcol = s.lp + 2 * 2048 + 64;                                           // [nrem]
     for (int ti = warp; ti < nrem; ti += ALNS_WARPS) {
         const unsigned long long* kr = t.keys + static_cast<long long>(ti) * G;
-        unsigned long long bv = KEY_NONE;
-        for (int g = lane; g < G; g += 32) {
-            const unsigned long long k = kr[g];
-            if (k == KEY_NONE) continue;
-            const unsigned long long v = ((k >> 12) << 12) | static_cast<unsigned long long>(g);
-            bv = v < bv ? v : bv;
-        }
+        // best per drop vehicle (the regret-2 options) and overall, from the route keys
+        const unsigned long long rk = lane < m ? t.rkeys[ti * 32 + lane] : KEY_NONE;
+        unsigned long long bv = rk;
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long other = __shfl_xor_sync(FULL_MASK, bv, o);
             bv = other < bv ? other : bv;
         }
-        // per drop-vehicle best makespan delta (regret-2 options)
         long long c1 = REGRET_INF, c2 = REGRET_INF;
-        int gbase = 0;
         for (int v = 0; v < m; ++v) {
-            const int Lv = s.sWoff[v + 1] - s.sWoff[v];
-            unsigned long long bvv = KEY_NONE;
-            for (int g = gbase + lane; g <= gbase + Lv; g += 32) {
-                const unsigned long long k = kr[g];
-                const unsigned long long vv = k == KEY_NONE ? KEY_NONE : (((k >> 12) << 12) | static_cast<unsigned long long>(g));
-                bvv = vv < bvv ? vv : bvv;
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long other = __shfl_xor_sync(FULL_MASK, bvv, o);
-                bvv = other < bvv ? other : bvv;
-            }
-            if (bvv != KEY_NONE) {
-                const long long cv = static_cast<long long>(static_cast<int>(static_cast<unsigned>(bvv >> 32) ^ 0x80000000u));
-                if (cv < c1) { c2 = c1; c1 = cv; } else if (cv < c2) { c2 = cv; }
-            }
-            gbase += Lv + 1;
+            const unsigned long long bvv = __shfl_sync(FULL_MASK, rk, v);
+            if (bvv == KEY_NONE) continue;
+            const long long cv = static_cast<long long>(static_cast<int>(static_cast<unsigned>(bvv >> 32) ^ 0x80000000u));
+            if (cv < c1) { c2 = c1; c1 = cv; } else if (cv < c2) { c2 = cv; }
         }
         if (lane == 0) {
             bestv[ti] = bv;
             regret[ti] = c2 - c1;
+            bestcol[ti] = bv == KEY_NONE ? 0 : static_cast<int>(kr[bv & 0xFFF] & 0xFFF);
         }
     }
     __syncthreads();
@@ -813,16 +873,12 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
             if (bestv[ti] == KEY_NONE) { fail = true; break; }
             if (pick < 0) { pick = ti; continue; }
             if (ctl->rj == 0) {
-                const unsigned long long a = bestv[ti], b = bestv[pick];
-                const int rowa = static_cast<int>(a & 0xFFF), rowb = static_cast<int>(b & 0xFFF);
-                const unsigned long long ka = t.keys[static_cast<long long>(ti) * G + rowa];
-                const unsigned long long kb = t.keys[static_cast<long long>(pick) * G + rowb];
-                // (dz, dt) then flat index row*G + col
-                const unsigned long long pa = a >> 12, pb = b >> 12;
+                // greedy: (dz, dt), then flat index row*G + col; ties to the smaller customer id
+                const unsigned long long pa = bestv[ti] >> 12, pb = bestv[pick] >> 12;
                 if (pa != pb) { if (pa < pb) pick = ti; }
                 else {
-                    const long long fa = static_cast<long long>(rowa) * G + static_cast<long long>(ka & 0xFFF);
-                    const long long fb = static_cast<long long>(rowb) * G + static_cast<long long>(kb & 0xFFF);
+                    const long long fa = static_cast<long long>(bestv[ti] & 0xFFF) * G + bestcol[ti];
+                    const long long fb = static_cast<long long>(bestv[pick] & 0xFFF) * G + bestcol[pick];
                     if (fa < fb) pick = ti;
                 }
             } else {
@@ -832,32 +888,35 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
         if (fail || pick < 0) {
             ctl->repair_fail = 1;
         } else {
-            const int row = static_cast<int>(bestv[pick] & 0xFFF);
-            const int col = static_cast<int>(t.keys[static_cast<long long>(pick) * G + row] & 0xFFF);
             ctl->pick_t = pick;
-            ctl->pick_row = row;
-            ctl->pick_col = col;
+            ctl->pick_row = static_cast<int>(bestv[pick] & 0xFFF);
+            ctl->pick_col = bestcol[pick];
         }
     }
     __syncthreads();
     if (ctl->repair_fail) return;
-    // apply: route-parallel copy into the other W buffer
+    // apply, element-parallel from the staged copy of W: old op i of route v
+    // moves right by the insertions that precede it
     const int pick = ctl->pick_t, row = ctl->pick_row, col = ctl->pick_col;
     const int c = t.rem[pick];
-    const int a = t.groute[row], i = t.gpos[row], b = t.groute[col], j = t.gpos[col];
-    const int* W = t.W_ops[ctl->wsel];
+    const int a = t.groute[row], ia = t.gpos[row], b = t.groute[col], jb = t.gpos[col];
     int* Wn = t.W_ops[ctl->wsel ^ 1];
     int* Won = t.W_off[ctl->wsel ^ 1];
-    if (threadIdx.x < m) {
-        const int v = threadIdx.x;
-        const int before = (a < v ? 1 : 0) + (b < v ? 1 : 0);
-        int w = s.sWoff[v] + before;
-        const int L = s.sWoff[v + 1] - s.sWoff[v];
-        for (int k = 0; k <= L; ++k) {
-            if (v == a && k == i) Wn[w++] = 2 * c;
-            if (v == b && k == j) Wn[w++] = 2 * c + 1;
-            if (k < L) Wn[w++] = W[s.sWoff[v] + k];
+    for (int p = threadIdx.x; p < N; p += blockDim.x) {
+        int lo = 0, hi = m;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s.sWoff[mid] <= p) lo = mid; else hi = mid;
         }
+        const int v = lo, i = p - s.sWoff[v];
+        const int shift = (a < v ? 1 : 0) + (b < v ? 1 : 0) + (v == a && i >= ia ? 1 : 0) + (v == b && i >= jb ? 1 : 0);
+        Wn[p + shift] = s.sW[p] & PACK_MASK;
+    }
+    if (threadIdx.x == 0) {
+        const int base_a = s.sWoff[a] + (b < a ? 1 : 0);
+        Wn[base_a + ia] = 2 * c;
+        const int base_b = s.sWoff[b] + (a < b ? 1 : 0);
+        Wn[base_b + jb + (a == b ? 1 : 0)] = 2 * c + 1;
     }
     if (threadIdx.x <= m) {
         const int v = threadIdx.x;
@@ -893,7 +952,11 @@ __device__ int roulette(const double* w, const int* en, int k, double u) {
 // Rank 0: operator choice, q, random removal (partial Fisher-Yates), W = cur - removed.
 __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
     AlnsCtl* ctl = t.ctl;
-    const int n = t.n, m = t.m;
+    const int n = t.n, m = t.m, two_n = 2 * n;
+    int* perm = s.lp;                          // [n], shared memory
+    for (int k = threadIdx.x; k < n; k += blockDim.x) perm[k] = k + 1;
+    for (int c = threadIdx.x; c <= n; c += blockDim.x) s.flags[c] = 0;
+    __syncthreads();
     if (threadIdx.x == 0) {
         const int it = ctl->iter;
         const unsigned long long base = static_cast<unsigned long long>(it) << 16;
@@ -905,52 +968,66 @@ __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
         ctl->ar[ctl->rj] += 1;
         const int q = t.q_min + draw_below(draw(t.key, base + 2), t.q_max - t.q_min + 1);
         ctl->q = q;
-        for (int k = 0; k < n; ++k) t.perm[k] = k + 1;
         for (int k = 0; k < q; ++k) {
             const int jj = k + draw_below(draw(t.key, base + 16 + static_cast<unsigned long long>(k)), n - k);
-            const int tmp = t.perm[k];
-            t.perm[k] = t.perm[jj];
-            t.perm[jj] = tmp;
+            const int tmp = perm[k];
+            perm[k] = perm[jj];
+            perm[jj] = tmp;
+            s.flags[perm[k]] = 1;
         }
         ctl->repair_fail = 0;
         ctl->n_short = 0;
         ctl->work_counter = 0;
-    }
-    __syncthreads();
-    const int q = ctl->q;
-    for (int c = threadIdx.x; c <= n; c += blockDim.x) s.flags[c] = 0;
-    __syncthreads();
-    for (int k = threadIdx.x; k < q; k += blockDim.x) s.flags[t.perm[k]] = 1;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int w = 0;
-        for (int c = 1; c <= n; ++c)
-            if (s.flags[c]) t.rem[w++] = c;
-        ctl->nrem = w;
-    }
-    // W = cur without removed customers: one thread per route for the copy
-    int* Wn = t.W_ops[0];
-    int* Won = t.W_off[0];
-    int* cnt = s.misc;
-    if (threadIdx.x < m) {
-        const int v = threadIdx.x;
-        int k2 = 0;
-        for (int k = t.cur_off[v]; k < t.cur_off[v + 1]; ++k)
-            if (!s.flags[t.cur_ops[k] >> 1]) ++k2;
-        cnt[v] = k2;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        Won[0] = 0;
-        for (int v = 0; v < m; ++v) Won[v + 1] = Won[v] + cnt[v];
         ctl->wsel = 0;
     }
     __syncthreads();
-    if (threadIdx.x < m) {
-        const int v = threadIdx.x;
-        int w = Won[v];
-        for (int k = t.cur_off[v]; k < t.cur_off[v + 1]; ++k)
-            if (!s.flags[t.cur_ops[k] >> 1]) Wn[w++] = t.cur_ops[k];
+    // removed customers in ascending id order (ballot compaction by warp 0)
+    if ((threadIdx.x >> 5) == 0) {
+        const int lane = threadIdx.x & 31;
+        int w = 0;
+        for (int c0 = 1; c0 <= n; c0 += 32) {
+            const int c = c0 + lane;
+            const bool r = c <= n && s.flags[c];
+            const unsigned bal = __ballot_sync(FULL_MASK, r);
+            if (r) t.rem[w + __popc(bal & ((1u << lane) - 1u))] = c;
+            w += __popc(bal);
+        }
+        if (lane == 0) ctl->nrem = w;
+    }
+    // W = cur without the removed customers: block-wide scan of the kept flags
+    const int per = (two_n + blockDim.x - 1) / blockDim.x;
+    const int k0 = threadIdx.x * per, k1 = min(two_n, k0 + per);
+    int cnt = 0;
+    for (int k = k0; k < k1; ++k) cnt += s.flags[t.cur_ops[k] >> 1] ? 0 : 1;
+    int* wsum = s.misc;                        // [ALNS_WARPS]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    const int base_pos = before + incl - cnt;
+    int pos = base_pos;
+    int* Wn = t.W_ops[0];
+    for (int k = k0; k < k1; ++k) {
+        const int o = t.cur_ops[k];
+        if (!s.flags[o >> 1]) Wn[pos++] = o;
+    }
+    // route offsets: the kept-op count before each route start, taken from the
+    // scan by the thread whose range holds that start
+    for (int v = 0; v <= m; ++v) {
+        const int ov = t.cur_off[v];
+        if (ov >= k0 && ov < k1) {
+            int kept = base_pos;
+            for (int k = k0; k < ov; ++k) kept += s.flags[t.cur_ops[k] >> 1] ? 0 : 1;
+            t.W_off[0][v] = kept;
+        } else if (ov == two_n && threadIdx.x == 0) {
+            t.W_off[0][v] = two_n - 2 * ctl->q;
+        }
     }
     __syncthreads();
 }
@@ -1070,8 +1147,10 @@ __global__ void __launch_bounds__(ALNS_THREADS) alns_kernel(AlnsTeam* teams, int
     __syncthreads();
     const AlnsTeam& t = team_s;
     AlnsCtl* ctl = t.ctl;
-    const Smem s = carve(smem_alns, t.n, t.m);
+    const Smem s = carve(smem_alns, t.n, t.m);   // coordinates follow the flags when staged
     for (int c = threadIdx.x; c <= t.n; c += blockDim.x) s.sp[c] = t.p[c];
+    if (t.coords)
+        for (int i = threadIdx.x; i < 2 * (t.n + 1); i += blockDim.x) s.xy[i] = t.coords[i];
     unsigned gen = 0;
     __syncthreads();
 
@@ -1095,6 +1174,15 @@ __global__ void __launch_bounds__(ALNS_THREADS) alns_kernel(AlnsTeam* teams, int
         phase_end(t, s, true);
     }
     if (!team_barrier(ctl, team_blocks, gen)) return;
+    // wall time per phase, read by rank 0 at each barrier exit
+    uint64_t tmark = global_ns();
+    auto mark = [&](int ph) {
+        if (rank == 0 && threadIdx.x == 0) {
+            const uint64_t now = global_ns();
+            ctl->phase_ns[ph] += now - tmark;
+            tmark = now;
+        }
+    };
     for (int it = 1; it <= t.iterations; ++it) {
         if (rank == 0) {
             if (threadIdx.x == 0) ctl->iter = it;
@@ -1102,21 +1190,27 @@ __global__ void __launch_bounds__(ALNS_THREADS) alns_kernel(AlnsTeam* teams, int
             phase_begin(t, s);
         }
         if (!team_barrier(ctl, team_blocks, gen)) return;
+        mark(0);
         while (true) {
             const int nrem = *reinterpret_cast<volatile int*>(&ctl->nrem);
             const int fail = *reinterpret_cast<volatile int*>(&ctl->repair_fail);
             if (nrem == 0 || fail) break;
             phase_prep(t, s, rank, team_blocks);
             if (!team_barrier(ctl, team_blocks, gen)) return;
+            mark(1);
             phase_gaps(t, s, rank, team_blocks);
             if (!team_barrier(ctl, team_blocks, gen)) return;
+            mark(2);
             phase_matrix(t, s);
             if (!team_barrier(ctl, team_blocks, gen)) return;
+            mark(3);
             if (rank == 0) phase_select(t, s);
             if (!team_barrier(ctl, team_blocks, gen)) return;
+            mark(4);
         }
         if (rank == 0) phase_end(t, s, false);
         if (!team_barrier(ctl, team_blocks, gen)) return;
+        mark(5);
     }
 }
 
@@ -1151,6 +1245,7 @@ static size_t team_bytes(int n, int m, int qmax, int iterations, bool dump) {
     for (int i = 0; i < 12; ++i) add(G, 4);
     add(m, 4);
     add(static_cast<size_t>(qmax) * G, 8);
+    add(static_cast<size_t>(qmax) * 32, 8);
     add(static_cast<size_t>(qmax) * G, 1);
     add(static_cast<size_t>(qmax) * G, 4);
     add(std::max(iterations, 1), 4);
@@ -1178,11 +1273,18 @@ static void carve_team(AlnsTeam& t, DevBuf& B, int n, int m, int qmax, int itera
     t.gsmin = B.take<int>(G); t.gsmax = B.take<int>(G); t.groute = B.take<int>(G); t.gpos = B.take<int>(G);
     t.rload = B.take<int>(m);
     t.keys = B.take<unsigned long long>(static_cast<size_t>(qmax) * G);
+    t.rkeys = B.take<unsigned long long>(static_cast<size_t>(qmax) * 32);
     t.sc = B.take<unsigned char>(static_cast<size_t>(qmax) * G);
     t.slist = B.take<int>(static_cast<size_t>(qmax) * G);
     t.trace = B.take<int>(std::max(iterations, 1));
     t.dump_delta = dump ? B.take<int>(G * G) : nullptr;
     t.dump_travel = dump ? B.take<int>(G * G) : nullptr;
+}
+
+bool coords_exact_small(const vrprpd_instance* I);
+
+size_t alns_device_bytes(int n, int m, int qmax, int iterations) {
+    return team_bytes(n, m, qmax, iterations, false) + sizeof(AlnsTeam) + 8192;
 }
 
 bool alns_supported(const vrprpd_instance* I, std::string* why) {
@@ -1194,7 +1296,7 @@ bool alns_supported(const vrprpd_instance* I, std::string* why) {
 
 static int choose_team_blocks(const vrprpd_instance* I, int requested, size_t smem, int* out) {
     int occ = 0;
-    VRP_CUDA(cudaFuncSetAttribute(alns_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)));
+    { int rc_ = ensure_smem_limit(reinterpret_cast<const void*>(&alns_kernel)); if (rc_) return rc_; }
     VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alns_kernel, ALNS_THREADS, smem));
     VRP_CHECK(occ > 0, VRPRPD_EINVAL, "ALNS block does not fit on an SM (n=%d)", I->n);
     const int maxb = occ * I->num_sms;
@@ -1329,6 +1431,7 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     t.load_full = (I->flags & VRPRPD_LOAD_FULL) != 0;
     t.d32 = I->d32;
     t.p = I->p;
+    t.coords = coords_exact_small(I) ? I->coords : nullptr;
     t.T0 = P->T0;
     t.alpha = P->alpha;
     t.reheat = P->reheat;
@@ -1386,7 +1489,18 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
         set_error("alns setup: %s", cudaGetErrorString(e));
         return VRPRPD_ECUDA;
     }
-    const size_t smem = alns_smem_words(n, m) * 4;
+    // recompute distances from staged coordinates only when that costs no resident CTAs
+    size_t smem = alns_smem_words(n, m, false) * 4;
+    if (t.coords) {
+        const size_t smem_c = alns_smem_words(n, m, true) * 4;
+        int occ0 = 0, occ1 = 0;
+        ensure_smem_limit(reinterpret_cast<const void*>(&alns_kernel));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, alns_kernel, ALNS_THREADS, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, alns_kernel, ALNS_THREADS, smem_c);
+        if (occ1 >= occ0 && smem_c <= I->smem_optin) smem = smem_c;
+        else t.coords = nullptr;
+        cudaMemcpyAsync(d_team, &t, sizeof(AlnsTeam), cudaMemcpyHostToDevice, stream);
+    }
     VRP_CHECK(smem <= I->smem_optin, VRPRPD_EINVAL, "ALNS shared memory %zu exceeds the limit", smem);
     int tb = 1;
     int rc = choose_team_blocks(I, P->team_blocks, smem, &tb);
@@ -1455,6 +1569,7 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
         stats->matrix_entries = static_cast<int64_t>(out.entries);
         stats->fallback_entries = static_cast<int64_t>(out.fallback_entries);
         stats->team_blocks = tb;
+        for (int i = 0; i < 6; ++i) stats->phase_ms[i] = static_cast<double>(out.phase_ns[i]) * 1e-6;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     cleanup();
