@@ -185,7 +185,8 @@ def run_searches(vrp, args):
                   "full insertion-delta matrix", "iterations": args.alns_iters,
         "matrix_entries_per_s": st.matrix_entries / (st.device_ms / 1000.0),
         "fallback_entries": st.fallback_entries, "team_blocks": st.team_blocks,
-        "z_init": st.z_init, "z_best": st.z_best, "device_ms": st.device_ms}
+        "z_init": st.z_init, "z_best": st.z_best, "device_ms": st.device_ms,
+        "phase_ms": dict(zip(["begin", "prep", "gaps", "matrix", "select", "end"], list(st.phase_ms)))}
     w2 = workloads.make_instance(100, 4, 10, 5, "2x", "uniform", seed=0)
     i2 = vrp.Instance.from_workload(w2)
     r2 = vrp.alns_run(i2, vrp.alns_params(args.alns_iters * 10, 10, 10), seed=0)
@@ -264,6 +265,62 @@ def run_multi(vrp, args):
         "speedup_vs_plain": plain_ms / multi_ms, "equal_makespan": equal}}
 
 
+def run_serving(vrp, args):
+    """Continuous batching: a Poisson stream of solve requests (n uniform in
+    [50, 400], m = ceil(n/25), R = ceil(n/10), Q = 10, 1R20, mixed coords),
+    each running 50 ALNS iterations then 20 BRKGA generations of 256, admitted
+    by a device-memory budget onto 4 concurrent slots.  Capacity is measured
+    first with all requests queued at once; the stream then arrives at 0.8 of
+    that rate and p50/p99 submit-to-finish latency is reported."""
+    import numpy as np
+    rng = np.random.default_rng(7)
+    reqs = []
+    for i in range(args.serve_requests):
+        n = int(rng.integers(50, 401))
+        reqs.append(workloads.make_instance(n, -(-n // 25), -(-n // 10), 10, "1R20", "mixed", seed=100 + i))
+    budget = 16 << 30
+
+    def run(rate):
+        srv = vrp.Server(budget, max_active=4)
+        t0 = time.perf_counter()
+        ids = []
+        for i, w in enumerate(reqs):
+            if rate is not None and i:
+                time.sleep(float(rng.exponential(1.0 / rate)))
+            ids.append(srv.submit(w, alns_iterations=50, brkga_pop=256, brkga_generations=20, seed=i))
+        res = [srv.wait(r) for r in ids]
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        return res, wall, st
+
+    _, wall0, _ = run(None)
+    capacity = len(reqs) / wall0
+    res, wall, st = run(0.8 * capacity)
+    ok = all(r["status"] == 0 for r in res)
+    return {"serving": {
+        "value": len(reqs) / wall, "unit": "requests/s", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+        "capacity_requests_per_s": capacity, "arrival_rate": 0.8 * capacity, "requests": len(reqs),
+        "peak_active": st["peak_active"], "peak_bytes": st["peak_bytes"], "all_ok": ok,
+        "config": "Poisson arrivals at 0.8x measured capacity; n ~ U[50,400], m=ceil(n/25), R=ceil(n/10), "
+                  "Q=10, 1R20; 50 ALNS iterations + 20 BRKGA generations of 256 per request; 4 slots, 16 GiB"}}
+
+
+def run_profile_alns(args):
+    """One warm-up ALNS launch and one measured one (n=200 clustered, m=6,
+    R=20, Q=6, 5x; 10 iterations, q from Section 4.2.2)."""
+    import paper_2602_23685_gb300 as vrp
+    w = workloads.make_instance(200, 6, 20, 6, "5x", "clustered", seed=0)
+    inst = vrp.Instance.from_workload(w)
+    vrp.alns_run(inst, vrp.alns_params(10), seed=1)
+    r = vrp.alns_run(inst, vrp.alns_params(10), seed=0)
+    st = r["stats"]
+    print(json.dumps({"profile_case": "ALNS n=200 m=6, 10 iterations", "device_ms": st.device_ms,
+                      "phase_ms": list(st.phase_ms),
+                      "iters_per_s": 10 / (st.device_ms / 1000), "team_blocks": st.team_blocks,
+                      "matrix_entries": st.matrix_entries, "fallback_entries": st.fallback_entries}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,6 +331,9 @@ def main():
     ap.add_argument("--no-search", action="store_true", help="skip the ALNS / BRKGA legs")
     ap.add_argument("--alns-iters", type=int, default=20)
     ap.add_argument("--brkga-gens", type=int, default=100)
+    ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--profile-alns", action="store_true",
+                    help="small ALNS case for ncu: n=200, 10 iterations per launch, one warm-up launch")
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu: 16384 candidates (132 MB), default kernel shape, no tuning")
     args = ap.parse_args()
@@ -283,6 +343,8 @@ def main():
         return run_reference(args)
     if args.profile:
         return run_profile(args)
+    if args.profile_alns:
+        return run_profile_alns(args)
 
     import torch
     import paper_2602_23685_gb300 as vrp
@@ -378,6 +440,7 @@ def main():
     searches = {} if args.no_search else run_searches(vrp, args)
     if not args.no_search:
         searches.update(run_multi(vrp, args))
+        searches.update(run_serving(vrp, args))
 
     pk = peaks()
     bytes_per_eval = 4 * (2 * N_CUST + M_VEH + 1) + 8
