@@ -307,17 +307,23 @@ def run_serving(vrp, args):
 
 
 def run_profile_alns(args):
-    """One warm-up ALNS launch and one measured one (n=200 clustered, m=6,
-    R=20, Q=6, 5x; 10 iterations, q from Section 4.2.2)."""
+    """One warm-up ALNS launch and one measured one: n=200 clustered, m=6,
+    R=20, Q=6, 5x, 10 iterations; or (--profile-alns-n1000) the n=1000
+    workload of the ALNS leg, 2 iterations.  q follows Section 4.2.2."""
     import paper_2602_23685_gb300 as vrp
-    w = workloads.make_instance(200, 6, 20, 6, "5x", "clustered", seed=0)
+    if args.profile_alns_n1000:
+        w = workloads.make_instance(N_CUST, M_VEH, R_POOL, Q_CAP, "1R20", "mixed", seed=0)
+        iters, name = 2, "ALNS n=1000 m=20, 2 iterations"
+    else:
+        w = workloads.make_instance(200, 6, 20, 6, "5x", "clustered", seed=0)
+        iters, name = 10, "ALNS n=200 m=6, 10 iterations"
     inst = vrp.Instance.from_workload(w)
-    vrp.alns_run(inst, vrp.alns_params(10), seed=1)
-    r = vrp.alns_run(inst, vrp.alns_params(10), seed=0)
+    vrp.alns_run(inst, vrp.alns_params(iters), seed=1)
+    r = vrp.alns_run(inst, vrp.alns_params(iters), seed=0)
     st = r["stats"]
-    print(json.dumps({"profile_case": "ALNS n=200 m=6, 10 iterations", "device_ms": st.device_ms,
+    print(json.dumps({"profile_case": name, "device_ms": st.device_ms,
                       "phase_ms": list(st.phase_ms),
-                      "iters_per_s": 10 / (st.device_ms / 1000), "team_blocks": st.team_blocks,
+                      "iters_per_s": iters / (st.device_ms / 1000), "team_blocks": st.team_blocks,
                       "matrix_entries": st.matrix_entries, "fallback_entries": st.fallback_entries}))
 
 
@@ -334,6 +340,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--profile-alns", action="store_true",
                     help="small ALNS case for ncu: n=200, 10 iterations per launch, one warm-up launch")
+    ap.add_argument("--profile-alns-n1000", action="store_true",
+                    help="small ALNS case for ncu on the n=1000 workload: 2 iterations per launch")
     ap.add_argument("--profile", action="store_true",
                     help="small case for ncu: 16384 candidates (132 MB), default kernel shape, no tuning")
     args = ap.parse_args()
@@ -343,7 +351,7 @@ def main():
         return run_reference(args)
     if args.profile:
         return run_profile(args)
-    if args.profile_alns:
+    if args.profile_alns or args.profile_alns_n1000:
         return run_profile_alns(args)
 
     import torch

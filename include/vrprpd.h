@@ -242,7 +242,8 @@ int vrprpd_initial_solution(const vrprpd_instance* inst, vrprpd_solution* out);
  *   current  host buffers for the final current solution, or NULL.
  *   stats    may be NULL; z_trace (host, params->iterations int32) receives the
  *            current makespan after each iteration, or NULL.
- * Needs m <= 32, 2n + m <= 4096 and max d < 2^17.  Blocking: returns when done.
+ * Needs m <= 32, 2n + m <= 4096, max d < 2^17 and (2n+1)*max(d) + n*max(p) < 2^27
+ * (VRPRPD_EINVAL otherwise).  Blocking: returns when done.
  */
 int vrprpd_alns_run(const vrprpd_instance* inst, const vrprpd_solution* init,
                     const vrprpd_alns_params* params, uint64_t seed, vrprpd_solution* best,

@@ -40,8 +40,7 @@ namespace vrp {
 
 constexpr int NEG = -(1 << 30);               // "unreachable" in the longest-path table
 constexpr int UNRES = INT32_MIN;               // ready value not yet published
-constexpr int TR = 32, TC = 128, LPS = 136;    // matrix tile rows, cols, smem row stride
-constexpr int FB_CHUNK = 64;                   // entries per fallback work item
+constexpr int TR = 32, TC = 128;               // matrix tile rows, cols
 constexpr int ALNS_THREADS = 256;
 constexpr int ALNS_WARPS = ALNS_THREADS / 32;
 constexpr unsigned long long KEY_NONE = ~0ull;
@@ -103,9 +102,7 @@ struct Smem {
     int* sW;        // packed W ops [2n + 4]
     int* sWoff;     // [m + 1]
     int* sp;        // p[0..n]
-    int* rdy;       // [warps][n + 1]
-    int* lp;        // [TR][LPS]
-    unsigned* reach;// [TC]
+    int* rdy;       // [warps][n + 1] walk buffers; also the matrix batch vectors and select / begin scratch
     int* rowv;      // [TR][RV]
     int* colv;      // [TC][CV]
     int* misc;      // 64 ints
@@ -113,13 +110,25 @@ struct Smem {
     int* xy;        // coordinates [n + 1][2] (when staged)
 };
 constexpr int RV = 16, CV = 12;   // row / col vector widths (ints)
-constexpr int CB = 4, RPC = 7, CPC = 5;  // customers per matrix batch; per-customer row / col vector widths
+constexpr int CB = 8;             // customers per matrix batch
 
-// walk buffers (one ready array per warp), also holding a matrix batch's vectors
+// Walk buffers (one ready array per warp).  The same words hold a matrix
+// batch's vectors (int4 per column and row, int2 per row), a shortcut item's
+// two walk buffers with its departure and tail arrays, the selection's
+// per-customer results (5 words per removed customer) and the removal
+// permutation (n words); no phase needs two of these at once.
 __host__ __device__ inline size_t rdy_words(int n) {
-    const size_t walks = static_cast<size_t>(ALNS_WARPS) * (((n + 1) + 3) & ~3);
-    const size_t batch = static_cast<size_t>(CB) * (TR * RPC + TC * CPC);
-    return walks > batch ? walks : batch;
+    const size_t rw = static_cast<size_t>(((n + 1) + 3) & ~3);
+    const size_t walks = static_cast<size_t>(ALNS_WARPS) * rw;
+    const size_t fb = 2 * rw + 2 * ((static_cast<size_t>(2 * n) + 3) & ~static_cast<size_t>(3));
+    const size_t batch = static_cast<size_t>(CB) * (4 * TC + 6 * TR);
+    const size_t q = static_cast<size_t>(n < 1024 ? n : 1024);
+    const size_t sel = 5 * q + 8;
+    size_t w = walks > batch ? walks : batch;
+    w = w > fb ? w : fb;
+    w = w > sel ? w : sel;
+    w = w > static_cast<size_t>(n) + 4 ? w : static_cast<size_t>(n) + 4;
+    return (w + 3) & ~static_cast<size_t>(3);
 }
 
 __host__ __device__ inline size_t alns_smem_words(int n, int m, bool with_coords) {
@@ -128,7 +137,7 @@ __host__ __device__ inline size_t alns_smem_words(int n, int m, bool with_coords
     w += ((m + 1) + 3) & ~3;
     w += ((n + 1) + 3) & ~3;
     w += rdy_words(n);
-    w += TR * LPS + TC + TR * RV + TC * CV + 64;
+    w += TR * RV + TC * CV + 64;
     w += ((n + 1 + 3) / 4 + 3) & ~3;
     if (with_coords) w += ((2 * (n + 1)) + 3) & ~3;   // coordinates
     return w;
@@ -141,8 +150,6 @@ __device__ inline Smem carve(int* base, int n, int m) {
     s.sWoff = q; q += ((m + 1) + 3) & ~3;
     s.sp = q; q += ((n + 1) + 3) & ~3;
     s.rdy = q; q += rdy_words(n);
-    s.lp = q; q += TR * LPS;
-    s.reach = reinterpret_cast<unsigned*>(q); q += TC;
     s.rowv = q; q += TR * RV;
     s.colv = q; q += TC * CV;
     s.misc = q; q += 64;
@@ -403,6 +410,116 @@ __device__ int walk_insert(const AlnsTeam& t, const Smem& s, int* rdy, int c, in
     return anycyc ? 0x7fffffff : ret;
 }
 
+// W plus one stop V (op code ov) at gap (a, i), forward: the departure time of
+// every W position into Hb[pos] and of V into *hv; returns the makespan
+// (INT32_MAX on a precedence cycle).  A pickup V without its drop leaves at
+// arrival: the drop's edge comes with the second stop, not here.
+__device__ int walk_fwd1(const AlnsTeam& t, const Smem& s, int* rdy, int ov, int a, int i, int* Hb, int* hv) {
+    const int lane = threadIdx.x & 31, m = t.m, n = t.n;
+    for (int q = lane; q <= n; q += 32) rdy[q] = UNRES;
+    __syncwarp();
+    const bool mine = lane < m;
+    const int base = mine ? s.sWoff[lane] : 0;
+    const int L = mine ? s.sWoff[lane + 1] - base : 0;
+    const int gv = (mine && lane == a) ? i : -1;
+    int k = 0, dep = 0, loc = 0;
+    bool prev_virtual = false, vdone = gv < 0;
+    bool walking = mine && (L > 0 || !vdone);
+    const bool any = walking;
+    bool cyc = false;
+    while (__any_sync(FULL_MASK, walking)) {
+        int o = 0, rv = 0, cc = 0, dd = 0;
+        bool go = false, pick = false, virt = false;
+        if (walking) {
+            virt = !vdone && k == gv;
+            o = virt ? ov : (s.sW[base + k] & PACK_MASK);
+            cc = o >> 1;
+            pick = (o & 1) && !virt;
+            if (pick) rv = rdy[cc];
+            go = !pick || rv != UNRES;
+            if (go) dd = (virt || prev_virtual) ? Dx(t, s, loc, cc) : (s.sW[base + k] >> PACK_SHIFT);
+        }
+        __syncwarp();
+        if (go) {
+            const int arr = dep + dd;
+            if (pick) dep = max(arr, rv);
+            else {
+                dep = arr;
+                if (!virt) rdy[cc] = arr + s.sp[cc];
+            }
+            loc = cc;
+            if (virt) { vdone = true; *hv = dep; }
+            else { Hb[base + k] = dep; ++k; }
+            prev_virtual = virt;
+        }
+        __syncwarp();
+        const unsigned prog = __ballot_sync(FULL_MASK, go);
+        if (walking) {
+            if (k >= L && vdone) walking = false;
+            else if (prog == 0u) { walking = false; cyc = true; }
+        }
+    }
+    int ret = (mine && any && !cyc) ? dep + Dx(t, s, loc, 0) : 0;
+    for (int o = 16; o > 0; o >>= 1) ret = max(ret, __shfl_xor_sync(FULL_MASK, ret, o));
+    const unsigned anycyc = __ballot_sync(FULL_MASK, cyc);
+    return anycyc ? 0x7fffffff : ret;
+}
+
+// The same graph backward: the tail of every W position (longest path from its
+// departure to the end of the schedule, return leg included) into Tb[pos] and
+// V's into *tv.  A drop's tail also takes p plus its pickup's tail; V has no
+// partner in this graph.  tp: per-customer pickup tails (n + 1 words).
+__device__ void walk_bwd1(const AlnsTeam& t, const Smem& s, int* tp, int ov, int a, int i, int* Tb, int* tv) {
+    const int lane = threadIdx.x & 31, m = t.m, n = t.n;
+    for (int q = lane; q <= n; q += 32) tp[q] = UNRES;
+    __syncwarp();
+    const bool mine = lane < m;
+    const int base = mine ? s.sWoff[lane] : 0;
+    const int L = mine ? s.sWoff[lane + 1] - base : 0;
+    const int gv = (mine && lane == a) ? i : -1;
+    // k: W position still to do (counting down); V sits between positions gv-1 and gv
+    int k = L - 1, acc = 0, nloc = 0;
+    bool next_virtual = false, vdone = gv < 0, next_depot = true;
+    bool walking = mine && (L > 0 || !vdone);
+    while (__any_sync(FULL_MASK, walking)) {
+        int o = 0, rv = 0, cc = 0, dd = 0, w = 0;
+        bool go = false, drop = false, virt = false;
+        if (walking) {
+            virt = !vdone && k == gv - 1;
+            if (!virt) w = s.sW[base + k];
+            o = virt ? ov : (w & PACK_MASK);
+            cc = o >> 1;
+            drop = !(o & 1) && !virt;
+            if (drop) rv = tp[cc];
+            go = !drop || rv != UNRES;
+            if (go) {
+                // travel to the next stop: packed in W when both are W stops
+                if (next_depot) dd = Dx(t, s, cc, 0);
+                else if (virt || next_virtual) dd = Dx(t, s, cc, nloc);
+                else dd = s.sW[base + k + 1] >> PACK_SHIFT;
+            }
+        }
+        __syncwarp();
+        if (go) {
+            int val = dd + acc;
+            if (drop) val = max(val, s.sp[cc] + rv);
+            else if (!virt) tp[cc] = val;
+            if (virt) { vdone = true; *tv = val; }
+            else { Tb[base + k] = val; --k; }
+            acc = val;
+            nloc = cc;
+            next_virtual = virt;
+            next_depot = false;
+        }
+        __syncwarp();
+        const unsigned prog = __ballot_sync(FULL_MASK, go);
+        if (walking) {
+            if (k < 0 && vdone) walking = false;
+            else if (prog == 0u) { walking = false; atomicExch(&t.ctl->err, DEV_BAD_STATE); }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // capacity helpers (Eqs. 13-18 with the minimal or the full start load)
 // ---------------------------------------------------------------------------
@@ -563,50 +680,37 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
 }
 
 // One matrix tile (rows rt*TR.., cols ct*TC..) for every customer still to insert.
-// Everything that depends only on the gaps (head/tail times, the removed leg,
-// stock extremes and the capacity of inserting a lone drop or pickup) is
-// loaded once per tile; per customer only d(x,c) and d(c,y) are read, and the
-// next customer's reads are in flight while the current one's entries run.
+//
+// Whether a (drop gap, pickup gap) pair can take a customer at all does not
+// depend on the customer: every customer moves one unit of the resource, and
+// the cycle test and the longest path between the two gaps are properties of
+// W.  So each thread first settles its 16 pairs (row tid/8, columns
+// tid%8 + 8k) into one register each: the longest-path value LP, or the
+// sentinel SKIPV when the pair is excluded (capacity, pool, a cycle, a pickup
+// gap before the drop gap on one route).  Per customer an entry is then
+//     z' = max(max(z, beta), gamma, A1 + p_c + B1, E + LP + F)
+// with the row terms in registers and the column terms one 16-byte shared
+// load; excluded pairs and shortcut gaps come out at or above SKIPV and never
+// win.  The pair in which both gaps coincide (drop and pickup back to back)
+// is the adjacent case, handled once per row.
+constexpr int SKIPV = 1 << 28;   // schedule times stay below 2^27 (alns_supported)
+
 __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, int N, int G) {
     AlnsCtl* ctl = t.ctl;
     const int tid = threadIdx.x;
     const int r0 = rt * TR, c0 = ct * TC;
     int* rowc = s.rowv;                        // [TR][RV] tile constants of the drop gaps
     int* colc = s.colv;                        // [TC][CV] tile constants of the pickup gaps
-    // LP tile: lp[r][c] = LP(stop after row gap -> stop before col gap)
-    for (int e = tid; e < TR * TC; e += blockDim.x) {
-        const int r = e / TC, c = e - r * TC;
-        const int R = r0 + r, Cg = c0 + c;
-        int v = NEG;
-        if (R < G && Cg < G) {
-            const int ya = t.gy[R], xb = t.gx[Cg];
-            if (ya >= 0 && xb >= 0) v = t.Ms[static_cast<long long>(ya) * N + xb];
-        }
-        s.lp[r * LPS + c] = v;
-    }
-    // reach bits: stop after col gap reaches stop before row gap (would close a cycle)
-    {
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int c = warp; c < TC; c += ALNS_WARPS) {
-            const int Cg = c0 + c, R = r0 + lane;
-            bool rb = false;
-            if (Cg < G && R < G) {
-                const int yb = t.gy[Cg], xa = t.gx[R];
-                if (yb >= 0 && xa >= 0) rb = t.Ms[static_cast<long long>(yb) * N + xa] > NEG;
-            }
-            const unsigned bits = __ballot_sync(FULL_MASK, rb);
-            if (lane == 0) s.reach[c] = bits;
-        }
-    }
+    const int sumL = ctl->sum_load;
     // tile constants
     const bool is_col = tid < TC;
     const bool is_row = tid >= TC && tid < TC + TR;
     const int myg = is_col ? c0 + tid : (is_row ? r0 + tid - TC : G);
+    __syncthreads();                           // previous tile is done with rowc / colc
     if (is_row) {
         int* v = rowc + (tid - TC) * RV;
         const int R = myg;
         if (R < G) {
-            const int yo = t.gy[R];
             int la = 0, ladj = 0;
             const bool okA = cap_ok(t, min(min(t.gpmin[R], t.gsb[R] - 1), t.gsmin[R] - 1),
                                     max(t.gpmax[R], t.gsmax[R] - 1), la);
@@ -616,11 +720,12 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
             v[0] = t.gHx[R];
             v[1] = t.gTy[R];
             v[2] = t.gw[R];
+            v[3] = okAdj && sumL + ladj - t.rload[ra] <= t.R ? 1 : 0;   // adjacent pair fits
             v[6] = okA ? la - t.rload[ra] : 1 << 28;
-            v[7] = okAdj ? ladj - t.rload[ra] : 1 << 28;
             v[8] = ra;
             v[9] = t.gpos[R];
-            v[11] = yo;
+            v[10] = t.gx[R];
+            v[11] = t.gy[R];
             v[12] = t.gpmin[R];
             v[13] = t.gsb[R];
             v[14] = t.gpmax[R];
@@ -632,14 +737,14 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
         int* v = colc + tid * CV;
         const int Cg = myg;
         if (Cg < G) {
-            const int xo = t.gx[Cg];
             int lb = 0;
             const bool okB = cap_ok(t, min(t.gpmin[Cg], t.gsmin[Cg] + 1),
                                     max(max(t.gpmax[Cg], t.gsb[Cg] + 1), t.gsmax[Cg] + 1), lb);
             v[4] = okB ? lb - t.rload[t.groute[Cg]] : 1 << 28;
             v[5] = t.groute[Cg];
             v[6] = t.gpos[Cg];
-            v[8] = xo;
+            v[7] = t.gy[Cg];
+            v[8] = t.gx[Cg];
             v[9] = t.gsmin[Cg];
             v[10] = t.gsmax[Cg];
             v[11] = t.gHx[Cg] + t.gTy[Cg];          // H(x) + T(y)
@@ -647,115 +752,152 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
             v[5] = -1;
         }
     }
-    // Customers go in batches of CB: every thread builds per-customer vector
-    // entries for (customer, gap) pairs of the batch, then every thread runs
-    // its 16 entries for each customer of the batch; two block barriers per
-    // batch.  Per-customer vectors: rows {A1, beta, E, adj, dtD, dtAdj, sc},
-    // cols {gamma, B1, F, dtP, sc}.
-    // The batch vectors live in the per-warp walk buffers, which tiles do not use.
-    int* rvec = s.rdy;                         // [CB][TR][RPC]
-    int* cvec = s.rdy + CB * TR * RPC;         // [CB][TC][CPC]
+    __syncthreads();
+    // this thread's pairs
+    const int r = tid >> 3, cb = tid & 7;
+    const int* rk = rowc + r * RV;
+    const int ra = rk[8];
+    const bool row_ok = ra >= 0;               // all 8 lanes of a row agree; no early exit (shuffles below)
+    const int R = r0 + r;
+    int lpv[TC / 8];
+    int diag = -1;                             // column slot of the coinciding gap, if in this thread's set
+#pragma unroll
+    for (int kk = 0; kk < TC / 8; ++kk) {
+        const int cc = cb + 8 * kk;
+        const int* ck = colc + cc * CV;
+        int v = SKIPV;
+        const int rb = ck[5];
+        if (row_ok && rb >= 0) {
+            if (ra == rb) {
+                const int ia = rk[9], jb = ck[6];
+                if (jb == ia) {
+                    diag = cc;
+                } else if (jb > ia) {
+                    const int lo = rk[11], hi = ck[8];
+                    const int mn = min(min(min(rk[12], rk[13] - 1), range_min(t, lo, hi, N) - 1), ck[9]);
+                    const int mx = max(max(max(rk[14], range_max(t, lo, hi, N) - 1), t.S_[hi]), ck[10]);
+                    int l2 = 0;
+                    if (cap_ok(t, mn, mx, l2) && sumL - t.rload[ra] + l2 <= t.R)
+                        v = t.Ms[static_cast<long long>(lo) * N + hi];
+                }
+            } else {
+                const int dLA = rk[6], dLB = ck[4];
+                const int yb = ck[7], xa = rk[10];
+                const bool cyc = yb >= 0 && xa >= 0 && t.Ms[static_cast<long long>(yb) * N + xa] > NEG;
+                if (!cyc && dLA < (1 << 27) && dLB < (1 << 27) && sumL + dLA + dLB <= t.R) {
+                    const int ya = rk[11], xb = ck[8];
+                    v = (ya >= 0 && xb >= 0) ? t.Ms[static_cast<long long>(ya) * N + xb] : NEG;
+                }
+            }
+        }
+        lpv[kk] = v;
+    }
+    const bool adj_ok = rk[3] != 0;
+    // Customers go in batches of CB: every thread builds per-customer vectors
+    // for (customer, gap) pairs of the batch, then runs its 16 entries for each
+    // customer of the batch; two block barriers per batch.  The vectors live
+    // in the per-warp walk buffers, which tiles do not use:
+    //   cols [CB][TC] {gamma (SKIPV on a shortcut gap), B1, F, (dtP << 12) + col}
+    //   rows [CB][TR] {max(z, beta) (SKIPV on a shortcut gap), A1 + p_c, E, (dtD + 2^19) << 12}
+    //   adj  [CB][TR] {max(z, adjacent) (SKIPV on a shortcut gap), ((dtAdj + 2^19) << 12) + row}
+    int4* cvec = reinterpret_cast<int4*>(s.rdy);
+    int4* rvec = cvec + CB * TC;
+    int2* avec = reinterpret_cast<int2*>(rvec + CB * TR);
     const int nrem = ctl->nrem;
-    const int z = ctl->z_work, sumL = ctl->sum_load;
+    const int z = ctl->z_work;
     const bool dump = t.mode == 1;
-    unsigned long long local_entries = 0;
+    unsigned local_entries = 0;
+    const unsigned ncols = static_cast<unsigned>(max(0, min(TC / 8, (G - c0 - cb + 7) / 8)));  // this thread's columns < G
     for (int tb = 0; tb < nrem; tb += CB) {
         const int nb = min(CB, nrem - tb);
         __syncthreads();                       // previous batch's entries are done with the vectors
         for (int it = tid; it < nb * (TR + TC); it += blockDim.x) {
             const int k = it / (TR + TC), slot = it - k * (TR + TC);
-            const int ti = tb + k, c = t.rem[ti];
+            const int c = t.rem[tb + k];
             const int pc = s.sp[c];
             if (slot < TR) {
-                const int R = r0 + slot;
-                int* v = rvec + (k * TR + slot) * RPC;
-                if (R < G && rowc[slot * RV + 8] >= 0) {
-                    const int xo = t.gx[R], yo = t.gy[R];
+                const int Rr = r0 + slot;
+                const int* v = rowc + slot * RV;
+                int4 o = make_int4(SKIPV, 0, 0, 0);
+                int2 a = make_int2(SKIPV, 0);
+                if (Rr < G && v[8] >= 0) {
+                    const int xo = v[10], yo = v[11];
                     const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0, y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
                     const int dxc = Dx(t, s, x, c), dcy = Dx(t, s, c, y), dcc = Dx(t, s, c, c);
-                    const int Hx = rowc[slot * RV + 0], Ty = rowc[slot * RV + 1], w = rowc[slot * RV + 2];
+                    const int Hx = v[0], Ty = v[1], w = v[2];
                     const int delta = dxc + dcy;
-                    v[0] = Hx + dxc;                               // arrival at the new drop
-                    v[2] = Hx + delta;                             // leaving the drop towards y
-                    v[1] = v[2] + Ty;                              // beta: through the drop only
-                    v[3] = Hx + dxc + max(dcc, pc) + dcy + Ty;     // adjacent drop+pickup
-                    v[4] = delta - w;                              // travel change, drop
-                    v[5] = dxc + dcc + dcy - w;                    // travel change, adjacent pair
-                    v[6] = delta < w ? 1 : 0;                      // shortcut gap (flagged in prep too)
+                    const bool sc = delta < w;                     // shortcut gap: re-simulated in full
+                    o.x = sc ? SKIPV : max(z, Hx + delta + Ty);    // beta: through the drop only
+                    o.y = Hx + dxc + pc;                           // arrival at the drop + processing
+                    o.z = Hx + delta;                              // leaving the drop towards y
+                    o.w = static_cast<int>(static_cast<unsigned>(delta - w + (1 << 19)) << 12);
+                    a.x = sc ? SKIPV : max(z, Hx + dxc + max(dcc, pc) + dcy + Ty);
+                    a.y = static_cast<int>((static_cast<unsigned>(dxc + dcc + dcy - w + (1 << 19)) << 12) |
+                                           static_cast<unsigned>(Rr));
                 }
+                rvec[k * TR + slot] = o;
+                avec[k * TR + slot] = a;
             } else {
                 const int cc = slot - TR, Cg = c0 + cc;
-                int* v = cvec + (k * TC + cc) * CPC;
-                if (Cg < G && colc[cc * CV + 5] >= 0) {
-                    const int xo = t.gx[Cg], yo = t.gy[Cg];
+                const int* v = colc + cc * CV;
+                int4 o = make_int4(SKIPV, 0, 0, Cg);
+                if (Cg < G && v[5] >= 0) {
+                    const int xo = v[8], yo = v[7];
                     const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0, y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
                     const int dxc = Dx(t, s, x, c), dcy = Dx(t, s, c, y);
                     const int Ty = t.gTy[Cg], w = t.gw[Cg];
                     const int delta = dxc + dcy;
-                    v[0] = colc[cc * CV + 11] + delta;             // gamma: through the pickup only
-                    v[1] = dcy + Ty;                               // leaving the pickup
-                    v[2] = delta + Ty;                             // entering the pickup from x
-                    v[3] = delta - w;                              // travel change, pickup
-                    v[4] = delta < w ? 1 : 0;
+                    o.x = delta < w ? SKIPV : v[11] + delta;       // gamma: through the pickup only
+                    o.y = dcy + Ty;                                // leaving the pickup
+                    o.z = delta + Ty;                              // entering the pickup from x
+                    o.w = static_cast<int>((static_cast<unsigned>(delta - w) << 12) + static_cast<unsigned>(Cg));
                 }
+                cvec[k * TC + cc] = o;
             }
         }
         __syncthreads();
-        const int r = tid >> 3, cb = tid & 7;
-        const int* rk = rowc + r * RV;
-        const bool row_ok = rk[8] >= 0;        // all 8 lanes of a row agree; no early exit (shuffles below)
-        const int R = r0 + r;
-        const int dLA = rk[6], dLAdj = rk[7], ra = rk[8], ia = rk[9];
-        const unsigned rbit = 1u << r;
         for (int k = 0; k < nb; ++k) {
-            const int ti = tb + k, c = t.rem[ti], pc = s.sp[c];
-            const int* rv = rvec + (k * TR + r) * RPC;
-            const int A1 = rv[0], beta = rv[1], E = rv[2], adjv = rv[3], dtD = rv[4], dtAdj = rv[5];
-            const bool scR = rv[6] != 0;
+            const int ti = tb + k;
+            const int4 rv = rvec[k * TR + r];
             unsigned long long best = KEY_NONE;
-            for (int kk = 0; row_ok && kk < TC / 8; ++kk) {
-                const int cc = cb + 8 * kk;
-                const int* ck = colc + cc * CV;
-                const int rb = ck[5];
-                if (rb < 0) continue;
-                const int* cv = cvec + (k * TC + cc) * CPC;
-                const int Cg = c0 + cc, jb = ck[6];
-                if (scR || cv[4] != 0) continue;          // shortcut gap: re-simulated in full
-                int znew = 0, dt = 0;
-                bool ok;
-                if (ra == rb) {
-                    if (jb < ia) {
-                        ok = false;
-                    } else if (jb == ia) {
-                        ok = dLAdj < (1 << 27) && sumL + dLAdj <= t.R;
-                        znew = max(z, adjv);
-                        dt = dtAdj;
-                    } else {
-                        const int lo = rk[11], hi = ck[8];
-                        const int mn = min(min(min(rk[12], rk[13] - 1), range_min(t, lo, hi, N) - 1), ck[9]);
-                        const int mx = max(max(max(rk[14], range_max(t, lo, hi, N) - 1), t.S_[hi]), ck[10]);
-                        int l2 = 0;
-                        ok = cap_ok(t, mn, mx, l2) && sumL - t.rload[ra] + l2 <= t.R;
-                        const int lpv = s.lp[r * LPS + cc];
-                        znew = max(max(max(z, beta), cv[0]), max(A1 + pc + cv[1], E + lpv + cv[2]));
-                        dt = dtD + cv[3];
-                    }
-                } else {
-                    ok = (s.reach[cc] & rbit) == 0u && dLA < (1 << 27) && ck[4] < (1 << 27) &&
-                         sumL + dLA + ck[4] <= t.R;
-                    const int lpv = s.lp[r * LPS + cc];
-                    znew = max(max(z, beta), max(cv[0], A1 + pc + cv[1]));
-                    if (lpv != NEG) znew = max(znew, E + lpv + cv[2]);
-                    dt = dtD + cv[3];
-                }
-                ++local_entries;
-                if (dump) {
-                    const long long idx = static_cast<long long>(R) * G + Cg;
-                    t.dump_delta[idx] = ok ? znew - z : 0x7fffffff;
-                    t.dump_travel[idx] = ok ? dt : 0;
-                } else if (ok) {
-                    const unsigned long long key = pack_key(znew - z, dt, Cg);
+            if (row_ok && !dump) {
+#pragma unroll
+                for (int kk = 0; kk < TC / 8; ++kk) {
+                    const int4 g = cvec[k * TC + cb + 8 * kk];
+                    const int zz = max(max(rv.x, g.x), max(rv.y + g.y, rv.z + lpv[kk] + g.z));
+                    const unsigned lo = static_cast<unsigned>(rv.w) + static_cast<unsigned>(g.w);
+                    const unsigned long long key =
+                        (static_cast<unsigned long long>(static_cast<unsigned>(zz)) << 32) | lo;
                     best = key < best ? key : best;
+                }
+                local_entries += ncols;
+                if (diag >= 0 && adj_ok) {
+                    const int2 a = avec[k * TR + r];
+                    const unsigned long long key =
+                        (static_cast<unsigned long long>(static_cast<unsigned>(a.x)) << 32) | static_cast<unsigned>(a.y);
+                    best = key < best ? key : best;
+                }
+            } else if (row_ok) {
+                // every entry written out (parity runs): shortcut entries are left
+                // to the fallback items, excluded pairs read "infeasible"
+                const bool scR = rv.x >= SKIPV;
+#pragma unroll
+                for (int kk = 0; kk < TC / 8; ++kk) {
+                    const int cc = cb + 8 * kk, Cg = c0 + cc;
+                    const int4 g = cvec[k * TC + cc];
+                    if (Cg >= G || scR || g.x >= SKIPV) continue;
+                    const long long idx = static_cast<long long>(R) * G + Cg;
+                    if (cc == diag) {
+                        const int2 a = avec[k * TR + r];
+                        t.dump_delta[idx] = adj_ok ? a.x - z : 0x7fffffff;
+                        t.dump_travel[idx] = adj_ok ? static_cast<int>(static_cast<unsigned>(a.y) >> 12) - (1 << 19) : 0;
+                        continue;
+                    }
+                    const int zz = max(max(rv.x, g.x), max(rv.y + g.y, rv.z + lpv[kk] + g.z));
+                    const unsigned lo = static_cast<unsigned>(rv.w) + static_cast<unsigned>(g.w);
+                    const bool ok = lpv[kk] != SKIPV;
+                    t.dump_delta[idx] = ok ? zz - z : 0x7fffffff;
+                    t.dump_travel[idx] = ok ? static_cast<int>(lo >> 12) - (1 << 19) : 0;
                 }
             }
             // min over the 8 lanes sharing a row
@@ -763,56 +905,136 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
                 const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
                 best = other < best ? other : best;
             }
-            if (!dump && cb == 0 && best != KEY_NONE) {
-                atomicMin(&t.keys[static_cast<long long>(ti) * G + R], best);
-                atomicMin(&t.rkeys[ti * 32 + ra], ((best >> 12) << 12) | static_cast<unsigned long long>(R));
+            const int bz = static_cast<int>(best >> 32);
+            if (!dump && cb == 0 && best != KEY_NONE && bz < SKIPV) {
+                const unsigned long long key =
+                    (static_cast<unsigned long long>(static_cast<unsigned>(bz - z) ^ 0x80000000u) << 32) |
+                    (best & 0xFFFFFFFFull);
+                atomicMin(&t.keys[static_cast<long long>(ti) * G + R], key);
+                atomicMin(&t.rkeys[ti * 32 + ra], ((key >> 12) << 12) | static_cast<unsigned long long>(R));
             }
         }
     }
-    atomicAdd(&ctl->entries, local_entries);
+    const unsigned warp_entries = __reduce_add_sync(0xffffffffu, local_entries);
+    if ((tid & 31) == 0 && warp_entries) atomicAdd(&ctl->entries, static_cast<unsigned long long>(warp_entries));
 }
 
-// Fallback item: entries of one shortcut gap (as drop row or pickup column), one warp each.
+// Shortcut item: every entry with one shortcut gap g for customer c (the
+// rounded legs x->c->y shorter than x->y, so the old paths through (x,y) do not
+// all survive and the tile formula's max(z, ...) is not exact).  As a drop gap
+// (as_col = 0) the graph W + D_c at g is simulated once, forward (departures
+// H1, makespan z1, D_c's time h_d) and backward (tails T1), by two warps at
+// once; then every pickup gap (x_b, y_b) that is not a shortcut for c is exact
+// in O(1):
+//     z' = max(z1, max(H1(x_b) + d(x_b,c), h_d + p_c) + d(c,y_b) + T1(y_b))
+// because each path of W + D_c either survives or gains length.  As a pickup
+// gap (as_col = 1) the graph is W + P_c with P_c leaving at arrival; for a
+// drop gap (x_a, y_a) with drop time t_d = H2(x_a) + d(x_a,c),
+//     z' = max(z2, t_d + d(c,y_a) + T2(y_a), t_d + p_c + T2(P_c)).
+// Cycles, the pickup-before-drop order and capacity are the tile's tests.
+// Entries whose two gaps are both shortcuts for c (the diagonal of g among
+// them) are re-simulated in full, in the item of their drop gap.
 __device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N, int G) {
     AlnsCtl* ctl = t.ctl;
-    const int chunks = (G + FB_CHUNK - 1) / FB_CHUNK;
-    const int e = item / (2 * chunks), rest = item - e * 2 * chunks;
-    const int as_col = rest / chunks, chunk = rest - as_col * chunks;
+    const int e = item >> 1, as_col = item & 1;
     const int packed = t.slist[e];
     const int ti = packed / G, g = packed - ti * G;
     const int c = t.rem[ti];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int* rdy = s.rdy + warp * (((t.n + 1) + 3) & ~3);
-    const int z = ctl->z_work;
-    unsigned long long cnt = 0;
-    for (int k = chunk * FB_CHUNK + warp; k < min(G, (chunk + 1) * FB_CHUNK); k += ALNS_WARPS) {
+    const int n = t.n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rw = ((n + 1) + 3) & ~3;
+    int* Hb = s.rdy + 2 * rw;                  // [N] departures in W + V
+    int* Tb = Hb + ((N + 3) & ~3);             // [N] tails in W + V
+    int* sh = s.misc + 8;                      // z1, h_v, t_v
+    const int ga = t.groute[g], gi = t.gpos[g];
+    const int ov = 2 * c + as_col;
+    if (warp == 0) {
+        int hv = 0;
+        const int z1 = walk_fwd1(t, s, s.rdy, ov, ga, gi, Hb, &hv);
+        if (lane == ga) sh[1] = hv;
+        if (lane == 0) sh[0] = z1;
+    } else if (warp == 1) {
+        int tv = 0;
+        walk_bwd1(t, s, s.rdy + rw, ov, ga, gi, Tb, &tv);
+        if (lane == ga) sh[2] = tv;
+    }
+    __syncthreads();
+    const int z1 = sh[0], hv = sh[1], tv = sh[2];
+    const int z = ctl->z_work, pc = s.sp[c];
+    const long long scrow = static_cast<long long>(ti) * G;
+    const bool dump = t.mode == 1;
+    unsigned cnt = 0;
+    auto loc = [&](int pos) { return pos >= 0 ? (s.sW[pos] & PACK_MASK) >> 1 : 0; };
+    for (int k = tid; k < G && z1 != 0x7fffffff; k += blockDim.x) {
+        if (k == g || t.sc[scrow + k]) continue;              // both gaps shortcuts: below / elsewhere
         const int row = as_col ? k : g, col = as_col ? g : k;
-        if (as_col && t.sc[static_cast<long long>(ti) * G + row]) continue;  // that row item covers it
         const int a = t.groute[row], i = t.gpos[row], b = t.groute[col], j = t.gpos[col];
+        const long long idx = static_cast<long long>(row) * G + col;
         if (a == b && j < i) {
-            if (t.mode == 1 && lane == 0) {
-                t.dump_delta[static_cast<long long>(row) * G + col] = 0x7fffffff;
-                t.dump_travel[static_cast<long long>(row) * G + col] = 0;
-            }
+            if (dump) { t.dump_delta[idx] = 0x7fffffff; t.dump_travel[idx] = 0; }
             continue;
         }
-        const bool capok = entry_capacity(t, row, col, N);
-        const int zn = walk_insert(t, s, rdy, c, a, i, b, j);
+        const int xa = t.gx[row], yb = t.gy[col];
+        const bool cyc = xa >= 0 && yb >= 0 && t.Ms[static_cast<long long>(yb) * N + xa] > NEG;
+        const bool ok = !cyc && entry_capacity(t, row, col, N);
+        int zn;
+        if (!as_col) {
+            const int xb = t.gx[col];
+            const int arr = (xb >= 0 ? Hb[xb] : 0) + Dx(t, s, loc(xb), c);
+            const int dep = max(arr, hv + pc);
+            zn = max(z1, dep + Dx(t, s, c, loc(yb)) + (yb >= 0 ? Tb[yb] : 0));
+        } else {
+            const int ya = t.gy[row];
+            const int td = (xa >= 0 ? Hb[xa] : 0) + Dx(t, s, loc(xa), c);
+            zn = max(z1, max(td + Dx(t, s, c, loc(ya)) + (ya >= 0 ? Tb[ya] : 0), td + pc + tv));
+        }
         ++cnt;
-        const bool ok = capok && zn != 0x7fffffff;
-        if (lane == 0) {
-            const int dt = travel_delta(t, s, c, row, col);
-            if (t.mode == 1) {
-                t.dump_delta[static_cast<long long>(row) * G + col] = ok ? zn - z : 0x7fffffff;
-                t.dump_travel[static_cast<long long>(row) * G + col] = ok ? dt : 0;
-            } else if (ok) {
-                const unsigned long long key = pack_key(zn - z, dt, col);
-                atomicMin(&t.keys[static_cast<long long>(ti) * G + row], key);
-                atomicMin(&t.rkeys[ti * 32 + a], ((key >> 12) << 12) | static_cast<unsigned long long>(row));
+        const int dt = travel_delta(t, s, c, row, col);
+        if (dump) {
+            t.dump_delta[idx] = ok ? zn - z : 0x7fffffff;
+            t.dump_travel[idx] = ok ? dt : 0;
+        } else if (ok) {
+            const unsigned long long key = pack_key(zn - z, dt, col);
+            atomicMin(&t.keys[scrow + row], key);
+            atomicMin(&t.rkeys[ti * 32 + a], ((key >> 12) << 12) | static_cast<unsigned long long>(row));
+        }
+    }
+    // both gaps shortcuts, from the drop gap's item: full re-simulation, one warp each
+    if (!as_col) {
+        __syncthreads();                       // Hb / Tb done; walk buffers back to one per warp
+        int* rdy = s.rdy + warp * rw;
+        for (int k0 = warp * 32; k0 < G; k0 += ALNS_WARPS * 32) {
+            const int kl = k0 + lane;
+            const bool both = kl < G && (kl == g || t.sc[scrow + kl]);
+            unsigned todo = __ballot_sync(FULL_MASK, both);
+            while (todo) {
+                const int col = k0 + __ffs(todo) - 1;
+                todo &= todo - 1;
+                const int a = ga, i = gi, b = t.groute[col], j = t.gpos[col];
+                const long long idx = static_cast<long long>(g) * G + col;
+                if (a == b && j < i) {
+                    if (dump && lane == 0) { t.dump_delta[idx] = 0x7fffffff; t.dump_travel[idx] = 0; }
+                    continue;
+                }
+                const bool capok = entry_capacity(t, g, col, N);
+                const int zn = walk_insert(t, s, rdy, c, a, i, b, j);
+                const bool ok = capok && zn != 0x7fffffff;
+                if (lane == 0) {
+                    ++cnt;
+                    const int dt = travel_delta(t, s, c, g, col);
+                    if (dump) {
+                        t.dump_delta[idx] = ok ? zn - z : 0x7fffffff;
+                        t.dump_travel[idx] = ok ? dt : 0;
+                    } else if (ok) {
+                        const unsigned long long key = pack_key(zn - z, dt, col);
+                        atomicMin(&t.keys[scrow + g], key);
+                        atomicMin(&t.rkeys[ti * 32 + a], ((key >> 12) << 12) | static_cast<unsigned long long>(g));
+                    }
+                }
             }
         }
     }
-    if (lane == 0 && cnt) atomicAdd(&ctl->fallback_entries, cnt);
+    const unsigned wc = __reduce_add_sync(FULL_MASK, cnt);
+    if (lane == 0 && wc) atomicAdd(&ctl->fallback_entries, static_cast<unsigned long long>(wc));
 }
 
 __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
@@ -820,8 +1042,8 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
     const int N = s.sWoff[t.m], G = N + t.m;
     const int RT = (G + TR - 1) / TR, CT = (G + TC - 1) / TC;
     const int tiles = RT * CT;
-    const int chunks = (G + FB_CHUNK - 1) / FB_CHUNK;
-    const int total = tiles + ctl->n_short * 2 * chunks;
+    const int nfb = 2 * ctl->n_short;          // shortcut items first: each holds two walks
+    const int total = nfb + tiles;
     int* slot = s.misc;
     for (;;) {
         __syncthreads();
@@ -829,8 +1051,12 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
         __syncthreads();
         const int item = slot[0];
         if (item >= total) break;
-        if (item < tiles) matrix_tile(t, s, item / CT, item - (item / CT) * CT, N, G);
-        else fallback_item(t, s, item - tiles, N, G);
+        if (item < nfb) {
+            fallback_item(t, s, item, N, G);
+        } else {
+            const int tile = item - nfb;
+            matrix_tile(t, s, tile / CT, tile - (tile / CT) * CT, N, G);
+        }
     }
 }
 
@@ -839,10 +1065,10 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
     AlnsCtl* ctl = t.ctl;
     const int m = t.m, N = s.sWoff[m], G = N + m, nrem = ctl->nrem;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // per-customer results in the (now free) tile buffer
-    unsigned long long* bestv = reinterpret_cast<unsigned long long*>(s.lp);        // [nrem] (dz,dt)<<12 | row
-    long long* regret = reinterpret_cast<long long*>(s.lp) + 1024;                 // [nrem]
-    int* bestcol = s.lp + 2 * 2048 + 64;                                           // [nrem]
+    // per-customer results in the (now free) walk buffers
+    unsigned long long* bestv = reinterpret_cast<unsigned long long*>(s.rdy);       // [nrem] (dz,dt)<<12 | row
+    long long* regret = reinterpret_cast<long long*>(s.rdy) + nrem;                // [nrem]
+    int* bestcol = s.rdy + 4 * nrem;                                               // [nrem]
     for (int ti = warp; ti < nrem; ti += ALNS_WARPS) {
         const unsigned long long* kr = t.keys + static_cast<long long>(ti) * G;
         // best per drop vehicle (the regret-2 options) and overall, from the route keys
@@ -953,7 +1179,7 @@ __device__ int roulette(const double* w, const int* en, int k, double u) {
 __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
     AlnsCtl* ctl = t.ctl;
     const int n = t.n, m = t.m, two_n = 2 * n;
-    int* perm = s.lp;                          // [n], shared memory
+    int* perm = s.rdy;                         // [n], shared memory
     for (int k = threadIdx.x; k < n; k += blockDim.x) perm[k] = k + 1;
     for (int c = threadIdx.x; c <= n; c += blockDim.x) s.flags[c] = 0;
     __syncthreads();
@@ -1139,7 +1365,7 @@ __device__ void phase_end(const AlnsTeam& t, const Smem& s, bool first) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(ALNS_THREADS) alns_kernel(AlnsTeam* teams, int team_blocks) {
+__global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, int team_blocks) {
     extern __shared__ __align__(16) int smem_alns[];
     __shared__ AlnsTeam team_s;
     const int team = blockIdx.x / team_blocks, rank = blockIdx.x - team * team_blocks;
@@ -1291,6 +1517,10 @@ bool alns_supported(const vrprpd_instance* I, std::string* why) {
     if (I->m > 32) { *why = "ALNS needs m <= 32"; return false; }
     if (2 * I->n + I->m > 4096) { *why = "ALNS needs 2n + m <= 4096"; return false; }
     if (I->maxd >= (1 << 17)) { *why = "ALNS needs max d < 2^17"; return false; }
+    // every schedule time of every insertion the matrix scores stays below
+    // 2^27, so sums of three of them next to the exclusion sentinel fit int32
+    const long long bound = (2ll * I->n + 1) * I->maxd + static_cast<long long>(I->n) * I->maxp;
+    if (bound >= (1ll << 27)) { *why = "ALNS needs (2n+1)*max(d) + n*max(p) < 2^27"; return false; }
     return true;
 }
 
