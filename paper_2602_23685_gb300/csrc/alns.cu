@@ -59,6 +59,13 @@ struct AlnsCtl {
     int sd[4], sr[4], ad[4], ar[4];
     int accepted, improved, new_best, reheats, rejected;
     int z_init;
+    // set by the selection when the insertion it applied used no shortcut gap:
+    // the next step updates the longest-path table in place of re-walking W.
+    // upd: c, x_a, y_a, x_b, y_b (old positions, -1 = depot), adjacent, new
+    // positions of D_c and P_c, old length, d(x_a,c), d(c,y_a), d(x_b,c),
+    // d(c,y_b), d(c,c), p_c
+    int incr;
+    int upd[16];
     unsigned long long entries, fallback_entries;
     unsigned long long phase_ns[6];   // begin, prep, gaps, matrix, select, end (rank 0 wall time)
 };
@@ -81,6 +88,7 @@ struct AlnsTeam {
     int *W_ops[2], *W_off[2];
     int *rem, *perm;
     int *H, *T, *Ms;
+    int *H2, *T2, *Ms2;      // the other copy of each: written by the incremental update, then swapped
     int *S_, *PMINp, *PMAXp, *SMINs, *SMAXs;
     int *spmin, *spmax;      // [LOG][2n]
     int log_levels;
@@ -588,7 +596,171 @@ __device__ __forceinline__ int travel_delta(const AlnsTeam& t, const Smem& s, in
 // ---------------------------------------------------------------------------
 // phases
 // ---------------------------------------------------------------------------
-__device__ void phase_prep(const AlnsTeam& t, const Smem& s, int rank, int team_blocks) {
+// Stock prefix arrays of route r from the staged W (one warp): what the walk
+// from the depot writes, S_ (stock after each op), its running min / max with
+// the start at 0, and the suffix min / max of S_ within the route; the route's
+// start load goes to rload[r] and is added to sum_load.
+__device__ void scan_route_stock(const AlnsTeam& t, const Smem& s, int r) {
+    const int lane = threadIdx.x & 31;
+    const int st = s.sWoff[r], en = s.sWoff[r + 1];
+    int carry = 0, cmin = 0, cmax = 0;
+    for (int base = st; base < en; base += 32) {
+        const int k = base + lane;
+        const bool in = k < en;
+        int v = in ? (((s.sW[k] & PACK_MASK) & 1) ? 1 : -1) : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL_MASK, v, o);
+            if (lane >= o) v += y;
+        }
+        const int sv = carry + v;
+        int mn = in ? sv : INT32_MAX, mx = in ? sv : INT32_MIN;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y1 = __shfl_up_sync(FULL_MASK, mn, o), y2 = __shfl_up_sync(FULL_MASK, mx, o);
+            if (lane >= o) { mn = min(mn, y1); mx = max(mx, y2); }
+        }
+        mn = min(mn, cmin);
+        mx = max(mx, cmax);
+        if (in) { t.S_[k] = sv; t.PMINp[k] = mn; t.PMAXp[k] = mx; }
+        carry = __shfl_sync(FULL_MASK, sv, 31);
+        cmin = __shfl_sync(FULL_MASK, mn, 31);
+        cmax = __shfl_sync(FULL_MASK, mx, 31);
+    }
+    __syncwarp();
+    int smn = INT32_MAX, smx = INT32_MIN;
+    for (int top = en - 1; top >= st; top -= 32) {
+        const int k = top - lane;
+        const bool in = k >= st;
+        const int sv = in ? t.S_[k] : 0;
+        int mn = in ? sv : INT32_MAX, mx = in ? sv : INT32_MIN;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y1 = __shfl_up_sync(FULL_MASK, mn, o), y2 = __shfl_up_sync(FULL_MASK, mx, o);
+            if (lane >= o) { mn = min(mn, y1); mx = max(mx, y2); }
+        }
+        mn = min(mn, smn);
+        mx = max(mx, smx);
+        if (in) { t.SMINs[k] = mn; t.SMAXs[k] = mx; }
+        smn = __shfl_sync(FULL_MASK, mn, 31);
+        smx = __shfl_sync(FULL_MASK, mx, 31);
+    }
+    if (lane == 0) {
+        const int load = t.load_full ? t.Q : -cmin;
+        t.rload[r] = load;
+        atomicAdd(&t.ctl->sum_load, load);
+    }
+}
+
+// After inserting D_c into gap (x_a, y_a) and P_c into gap (x_b, y_b), neither
+// a shortcut for c, every path of the old graph survives with at least its old
+// length, and a new path meets D_c, or P_c, or both.  With LP the old table,
+//     A(u) = LP(u,x_a) + d(x_a,c)                    (reaching D_c)
+//     E(u) = max(LP(u,x_b), A(u) + d(c,y_a) + LP(y_a,x_b)) + d(x_b,c)
+//     B(v) = d(c,y_b) + LP(y_b,v)                    (leaving P_c)
+//     D(v) = max(d(c,y_a) + max(LP(y_a,v), LP(y_a,x_b) + d(x_b,c) + B(v)), p_c + B(v))
+//     LP'(u,v) = max(LP(u,v), A(u) + D(v), E(u) + B(v)),
+// and the same with the depot's start as u (heads H) and its end as v (tails
+// T).  When both stops share one gap, D_c is P_c's only predecessor:
+// D(v) = max(d(c,c), p_c) + B(v) and the E term drops.  Unreachable is NEG;
+// sums stay clear of overflow by clamping NEG to -2^28 first and mapping every
+// negative result back to NEG.  Old positions move right by the new stops
+// before them; the new table has stride N + 2 and goes to the second buffers.
+constexpr int NEGC = -(1 << 28);
+
+__device__ void phase_update(const AlnsTeam& t, const Smem& s, int rank, int team_blocks) {
+    AlnsCtl* ctl = t.ctl;
+    const int* up = ctl->upd;
+    const int xa = up[2], ya = up[3], xb = up[4], yb = up[5], adj = up[6], Pd = up[7], Pp = up[8];
+    const int No = up[9], Nn = No + 2;
+    const int dxa = up[10], dya = up[11], dxb = up[12], dyb = up[13], dcc = up[14], pc = up[15];
+    const int* Mo = t.Ms;
+    int* Mn = t.Ms2;
+    auto cl = [](int x) { return x == NEG ? NEGC : x; };
+    auto fix = [](int x) { return x < 0 ? NEG : x; };
+    const int mcp = max(dcc, pc);
+    const int Lyx = (!adj && ya >= 0 && xb >= 0) ? cl(Mo[static_cast<long long>(ya) * No + xb]) : NEGC;
+    const int hA = (xa >= 0 ? t.H[xa] : 0) + dxa;
+    const int hE = adj ? NEGC : max(xb >= 0 ? t.H[xb] : 0, hA + dya + Lyx) + dxb;
+    const int tB = dyb + (yb >= 0 ? t.T[yb] : 0);
+    const int tD = adj ? mcp + tB : max(dya + (ya >= 0 ? max(t.T[ya], Lyx + dxb + tB) : 0), pc + tB);
+    const int LPdp = adj ? mcp : max(pc, Lyx + dya + dxb);
+    if (rank == 0 && threadIdx.x == 0) {
+        const int z = ctl->z_work;
+        ctl->z_work = max(max(z, hA + tD), hE + tB);
+    }
+    // new position -> 0 (old op, index in *old), 1 (D_c), 2 (P_c)
+    auto kind_of = [&](int k, int* old) {
+        if (k == Pd) return 1;
+        if (k == Pp) return 2;
+        *old = k - (k > Pd ? 1 : 0) - (k > Pp ? 1 : 0);
+        return 0;
+    };
+    constexpr int UR = 16;                     // rows per tile; columns = threads
+    int* rowA = s.rowv;                        // [UR] A, E, kind, old index
+    int* rowE = rowA + UR;
+    int* rowK = rowE + UR;
+    int* rowO = rowK + UR;
+    const int ntr = (Nn + UR - 1) / UR, ntc = (Nn + ALNS_THREADS - 1) / ALNS_THREADS;
+    for (int tile = rank; tile < ntr * ntc; tile += team_blocks) {
+        const int r0 = (tile / ntc) * UR, c0 = (tile % ntc) * ALNS_THREADS;
+        __syncthreads();                       // the previous tile is done with the row values
+        if (threadIdx.x < UR) {
+            const int k = r0 + threadIdx.x;
+            int kind = 3, u = 0, A = NEGC, E = NEGC;
+            if (k < Nn) {
+                kind = kind_of(k, &u);
+                if (kind == 0) {
+                    const long long ro = static_cast<long long>(u) * No;
+                    A = xa >= 0 ? cl(Mo[ro + xa]) + dxa : NEGC;
+                    E = (adj || xb < 0) ? NEGC : max(cl(Mo[ro + xb]), A + dya + Lyx) + dxb;
+                }
+                if (c0 == 0)
+                    t.T2[k] = kind == 0 ? max(t.T[u], max(A + tD, E + tB)) : (kind == 1 ? tD : tB);
+            }
+            rowA[threadIdx.x] = A;
+            rowE[threadIdx.x] = E;
+            rowK[threadIdx.x] = kind;
+            rowO[threadIdx.x] = u;
+        }
+        __syncthreads();
+        const int k = c0 + threadIdx.x;
+        if (k >= Nn) continue;
+        int v = 0;
+        const int ck = kind_of(k, &v);
+        int B = NEGC, D = NEGC;
+        if (ck == 0) {
+            B = yb >= 0 ? dyb + cl(Mo[static_cast<long long>(yb) * No + v]) : NEGC;
+            D = adj ? mcp + B
+                    : max(ya >= 0 ? dya + max(cl(Mo[static_cast<long long>(ya) * No + v]), Lyx + dxb + B) : NEGC,
+                          pc + B);
+        }
+        if (r0 == 0)
+            t.H2[k] = ck == 0 ? max(t.H[v], max(hA + D, hE + B)) : (ck == 1 ? hA : (adj ? hA + mcp : max(hE, hA + pc)));
+        // all old values of this column first: the stores below may not be
+        // ordered ahead of these loads
+        int old[UR];
+#pragma unroll
+        for (int rr = 0; rr < UR; ++rr)
+            old[rr] = (ck == 0 && rowK[rr] == 0) ? Mo[static_cast<long long>(rowO[rr]) * No + v] : NEG;
+#pragma unroll
+        for (int rr = 0; rr < UR; ++rr) {
+            const int rk = rowK[rr];
+            if (rk == 3) break;
+            const int A = rowA[rr], E = rowE[rr];
+            int val;
+            if (rk == 0) {
+                if (ck == 0) val = fix(max(old[rr], max(A + D, E + B)));
+                else if (ck == 1) val = fix(A);
+                else val = fix(adj ? A + mcp : max(E, A + pc));
+            } else if (rk == 1) {
+                val = ck == 0 ? fix(D) : (ck == 1 ? 0 : LPdp);
+            } else {
+                val = ck == 0 ? fix(B) : (ck == 1 ? NEG : 0);
+            }
+            Mn[static_cast<long long>(r0 + rr) * Nn + k] = val;
+        }
+    }
+}
+
+__device__ void phase_prep(const AlnsTeam& t, const Smem& s, int rank, int team_blocks, bool incr) {
     AlnsCtl* ctl = t.ctl;
     stage_W(t, s);
     const int N = s.sWoff[t.m], G = N + t.m;
@@ -596,7 +768,11 @@ __device__ void phase_prep(const AlnsTeam& t, const Smem& s, int rank, int team_
     const int team_warps = team_blocks * ALNS_WARPS;
     const int gw = rank * ALNS_WARPS + warp;
     int* rdy = s.rdy + warp * (((t.n + 1) + 3) & ~3);
-    for (int unit = gw; unit <= N; unit += team_warps) {
+    if (incr) {
+        phase_update(t, s, rank, team_blocks);
+        for (int r = gw; r < t.m; r += team_warps) scan_route_stock(t, s, r);
+    }
+    for (int unit = gw; !incr && unit <= N; unit += team_warps) {
         if (unit == 0) {
             int z;
             unsigned st;
@@ -663,20 +839,44 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
         t.groute[g] = r;
         t.gpos[g] = pos;
     }
-    if (rank == 0) {
-        // sparse tables of the stock prefix over op positions (routes are contiguous)
-        for (int k = threadIdx.x; k < N; k += blockDim.x) { t.spmin[k] = t.S_[k]; t.spmax[k] = t.S_[k]; }
-        __syncthreads();
-        for (int l = 1; (1 << l) <= N; ++l) {
-            const int h = 1 << (l - 1);
-            for (int k = threadIdx.x; k + (1 << l) <= N; k += blockDim.x) {
-                t.spmin[l * N + k] = min(t.spmin[(l - 1) * N + k], t.spmin[(l - 1) * N + k + h]);
-                t.spmax[l * N + k] = max(t.spmax[(l - 1) * N + k], t.spmax[(l - 1) * N + k + h]);
+    // sparse tables of the stock prefix over op positions.  Every range query
+    // lies inside one route, so levels stop at the longest route; each CTA
+    // builds a segment of SPB positions from a window reaching 2^top further,
+    // all levels in shared memory, min then max.
+    constexpr int SPB = 256;
+    int lmax = 1;
+    for (int r = 0; r < m; ++r) lmax = max(lmax, s.sWoff[r + 1] - s.sWoff[r]);
+    int top = 0;
+    while ((2 << top) <= lmax) ++top;
+    const int nseg = (N + SPB - 1) / SPB;
+    int* bufA = s.rdy;
+    int* bufB = s.rdy + SPB + (1 << top);
+    for (int seg = rank; seg < nseg; seg += team_blocks) {
+        const int k0 = seg * SPB;
+        const int wn = min(SPB + (1 << top), N - k0);
+        for (int pass = 0; pass < 2; ++pass) {
+            int* spx = pass ? t.spmax : t.spmin;
+            __syncthreads();                   // the buffers are free
+            for (int k = threadIdx.x; k < wn; k += blockDim.x) {
+                const int v = t.S_[k0 + k];
+                bufA[k] = v;
+                if (k < SPB) spx[k0 + k] = v;
             }
             __syncthreads();
+            int* src = bufA;
+            int* dst = bufB;
+            for (int l = 1; l <= top; ++l) {
+                const int h = 1 << (l - 1);
+                const int valid = wn - (1 << l) + 1;
+                for (int k = threadIdx.x; k < valid; k += blockDim.x)
+                    dst[k] = pass ? max(src[k], src[k + h]) : min(src[k], src[k + h]);
+                __syncthreads();
+                for (int k = threadIdx.x; k < min(SPB, valid); k += blockDim.x) spx[l * N + k0 + k] = dst[k];
+                int* q = src; src = dst; dst = q;
+            }
         }
-        if (threadIdx.x == 0) t.ctl->work_counter = 0;
     }
+    if (rank == 0 && threadIdx.x == 0) t.ctl->work_counter = 0;
 }
 
 // One matrix tile (rows rt*TR.., cols ct*TC..) for every customer still to insert.
@@ -1148,6 +1348,30 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
         const int v = threadIdx.x;
         Won[v] = s.sWoff[v] + (a < v ? 1 : 0) + (b < v ? 1 : 0);
     }
+    if (threadIdx.x == 0) {
+        // the next step updates the longest-path table incrementally unless a
+        // gap of this insertion was a shortcut for c
+        const long long scb = static_cast<long long>(pick) * G;
+        const bool shortcut = t.sc[scb + row] != 0 || t.sc[scb + col] != 0;
+        int* up = ctl->upd;
+        const int xa = t.gx[row], ya = t.gy[row], xb = t.gx[col], yb = t.gy[col];
+        auto loc = [&](int pos) { return pos >= 0 ? (s.sW[pos] & PACK_MASK) >> 1 : 0; };
+        up[0] = 1;
+        up[1] = c;
+        up[2] = xa; up[3] = ya; up[4] = xb; up[5] = yb;
+        up[6] = (a == b && ia == jb) ? 1 : 0;
+        up[7] = s.sWoff[a] + ia + (b < a ? 1 : 0);
+        up[8] = s.sWoff[b] + jb + (a <= b ? 1 : 0);
+        up[9] = N;
+        up[10] = Dx(t, s, loc(xa), c);
+        up[11] = Dx(t, s, c, loc(ya));
+        up[12] = Dx(t, s, loc(xb), c);
+        up[13] = Dx(t, s, c, loc(yb));
+        up[14] = Dx(t, s, c, c);
+        up[15] = s.sp[c];
+        ctl->incr = shortcut ? 0 : 1;
+        if (!shortcut) ctl->sum_load = 0;      // the route scans of the update add it back up
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         for (int k = pick; k + 1 < nrem; ++k) t.rem[k] = t.rem[k + 1];
@@ -1205,6 +1429,7 @@ __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
         ctl->n_short = 0;
         ctl->work_counter = 0;
         ctl->wsel = 0;
+        ctl->incr = 0;                         // W lost customers: the next step walks it in full
     }
     __syncthreads();
     // removed customers in ascending id order (ballot compaction by warp 0)
@@ -1383,7 +1608,7 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
     if (t.mode == 1) {
         // one-customer matrix dump on the partial solution already in W[0]
         if (!team_barrier(ctl, team_blocks, gen)) return;
-        phase_prep(t, s, rank, team_blocks);
+        phase_prep(t, s, rank, team_blocks, false);
         if (!team_barrier(ctl, team_blocks, gen)) return;
         phase_gaps(t, s, rank, team_blocks);
         if (!team_barrier(ctl, team_blocks, gen)) return;
@@ -1421,7 +1646,18 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
             const int nrem = *reinterpret_cast<volatile int*>(&ctl->nrem);
             const int fail = *reinterpret_cast<volatile int*>(&ctl->repair_fail);
             if (nrem == 0 || fail) break;
-            phase_prep(t, s, rank, team_blocks);
+            const bool incr = *reinterpret_cast<volatile int*>(&ctl->incr) != 0;
+            phase_prep(t, s, rank, team_blocks, incr);
+            if (incr) {
+                // every CTA swaps its own copy of the pointers: the update wrote the second buffers
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int* q = team_s.H; team_s.H = team_s.H2; team_s.H2 = q;
+                    q = team_s.T; team_s.T = team_s.T2; team_s.T2 = q;
+                    q = team_s.Ms; team_s.Ms = team_s.Ms2; team_s.Ms2 = q;
+                }
+                __syncthreads();
+            }
             if (!team_barrier(ctl, team_blocks, gen)) return;
             mark(1);
             phase_gaps(t, s, rank, team_blocks);
@@ -1466,6 +1702,7 @@ static size_t team_bytes(int n, int m, int qmax, int iterations, bool dump) {
     add(N + 2, 4); add(m + 1, 4); add(N + 2, 4); add(m + 1, 4);
     add(n + 1, 4); add(n + 1, 4);
     add(N, 4); add(N, 4); add(N * N, 4);
+    add(N, 4); add(N, 4); add(N * N, 4);
     for (int i = 0; i < 5; ++i) add(N, 4);
     add(levels * N, 4); add(levels * N, 4);
     for (int i = 0; i < 12; ++i) add(G, 4);
@@ -1490,6 +1727,7 @@ static void carve_team(AlnsTeam& t, DevBuf& B, int n, int m, int qmax, int itera
     t.W_ops[1] = B.take<int>(N + 2); t.W_off[1] = B.take<int>(m + 1);
     t.rem = B.take<int>(n + 1); t.perm = B.take<int>(n + 1);
     t.H = B.take<int>(N); t.T = B.take<int>(N); t.Ms = B.take<int>(N * N);
+    t.H2 = B.take<int>(N); t.T2 = B.take<int>(N); t.Ms2 = B.take<int>(N * N);
     t.S_ = B.take<int>(N); t.PMINp = B.take<int>(N); t.PMAXp = B.take<int>(N);
     t.SMINs = B.take<int>(N); t.SMAXs = B.take<int>(N);
     t.spmin = B.take<int>(levels * N); t.spmax = B.take<int>(levels * N);
