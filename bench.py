@@ -186,7 +186,8 @@ def run_searches(vrp, args):
         "matrix_entries_per_s": st.matrix_entries / (st.device_ms / 1000.0),
         "fallback_entries": st.fallback_entries, "team_blocks": st.team_blocks,
         "z_init": st.z_init, "z_best": st.z_best, "device_ms": st.device_ms,
-        "phase_ms": dict(zip(["begin", "prep", "gaps", "matrix", "select", "end"], list(st.phase_ms)))}
+        "phase_ms": dict(zip(["begin", "prep", "gaps", "matrix", "select", "end"], list(st.phase_ms))),
+        "incremental_steps": st.incremental_steps, "full_steps": st.full_steps}
     w2 = workloads.make_instance(100, 4, 10, 5, "2x", "uniform", seed=0)
     i2 = vrp.Instance.from_workload(w2)
     r2 = vrp.alns_run(i2, vrp.alns_params(args.alns_iters * 10, 10, 10), seed=0)
@@ -322,7 +323,8 @@ def run_profile_alns(args):
     r = vrp.alns_run(inst, vrp.alns_params(iters), seed=0)
     st = r["stats"]
     print(json.dumps({"profile_case": name, "device_ms": st.device_ms,
-                      "phase_ms": list(st.phase_ms),
+                      "phase_ms": list(st.phase_ms), "incremental_steps": st.incremental_steps,
+                      "full_steps": st.full_steps,
                       "iters_per_s": iters / (st.device_ms / 1000), "team_blocks": st.team_blocks,
                       "matrix_entries": st.matrix_entries, "fallback_entries": st.fallback_entries}))
 

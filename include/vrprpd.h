@@ -215,10 +215,14 @@ typedef struct {
     double T_final;
     double w_destroy[4], w_repair[4];
     double device_ms;          /* wall time of the device run */
-    int64_t matrix_entries;    /* insertion-matrix entries evaluated in O(1) */
-    int64_t fallback_entries;  /* entries re-simulated in full */
+    int64_t matrix_entries;    /* insertion-matrix entries scored by the O(1) tile formula */
+    int64_t fallback_entries;  /* entries with a shortcut gap: exact from simulations with one stop
+                                  (both gaps shortcuts: both stops) instead of the tile formula */
     int32_t team_blocks;       /* CTAs used */
     double phase_ms[6];        /* wall time per phase: begin, prep, gaps, matrix, select, end */
+    int64_t incremental_steps; /* greedy steps whose longest-path table was updated in O(N^2) */
+    int64_t full_steps;        /* greedy steps that re-walked W from every op (after a removal or a
+                                  shortcut insertion) */
 } vrprpd_alns_stats;
 
 void vrprpd_alns_params_default(vrprpd_alns_params* params);

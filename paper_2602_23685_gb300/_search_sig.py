@@ -20,7 +20,8 @@ class AlnsStats(C.Structure):
                 ("z_init", C.c_int32), ("z_best", C.c_int32), ("z_current", C.c_int32),
                 ("T_final", C.c_double), ("w_destroy", C.c_double * 4), ("w_repair", C.c_double * 4),
                 ("device_ms", C.c_double), ("matrix_entries", C.c_int64),
-                ("fallback_entries", C.c_int64), ("team_blocks", C.c_int32), ("phase_ms", C.c_double * 6)]
+                ("fallback_entries", C.c_int64), ("team_blocks", C.c_int32), ("phase_ms", C.c_double * 6),
+                ("incremental_steps", C.c_int64), ("full_steps", C.c_int64)]
 
 
 class BrkgaParams(C.Structure):

@@ -40,7 +40,13 @@ namespace vrp {
 
 constexpr int NEG = -(1 << 30);               // "unreachable" in the longest-path table
 constexpr int UNRES = INT32_MIN;               // ready value not yet published
-constexpr int TR = 32, TC = 128;               // matrix tile rows, cols
+constexpr int SKIPV = 1 << 28;                 // excluded matrix entry; schedule times stay below 2^27
+// Shortcut gaps per greedy step whose simulations run ahead, in the gap phase
+// (more than this, rare, are simulated inside the matrix phase instead).
+// Per shortcut gap: departures and tails with the drop alone (H1, T1) and with
+// the pickup alone (H2, T2), N words each, then z1, h_v1, t_v1, z2, h_v2, t_v2.
+constexpr int SC_CAP = 64;
+constexpr int TR = 32, TC = 64;                // matrix tile rows, cols
 constexpr int ALNS_THREADS = 256;
 constexpr int ALNS_WARPS = ALNS_THREADS / 32;
 constexpr unsigned long long KEY_NONE = ~0ull;
@@ -66,6 +72,7 @@ struct AlnsCtl {
     // d(c,y_b), d(c,c), p_c
     int incr;
     int upd[16];
+    unsigned long long steps_incr, steps_full;
     unsigned long long entries, fallback_entries;
     unsigned long long phase_ns[6];   // begin, prep, gaps, matrix, select, end (rank 0 wall time)
 };
@@ -94,10 +101,17 @@ struct AlnsTeam {
     int log_levels;
     int *gx, *gy, *gHx, *gTy, *gw, *gsb, *gpmin, *gpmax, *gsmin, *gsmax, *groute, *gpos;
     int *rload;              // start load per route
+    int *growc, *gcolc;      // [G][RV], [G][CV]: per-gap constants of the matrix tiles
+    int4 *vrow, *vcol;       // [q_max][G]: per (customer, gap) row / column vectors of the matrix
+    int2 *vadj;              // [q_max][G]: per (customer, gap) adjacent-pair vector
     unsigned long long* keys;  // [q_max][G]: per drop gap, best (dz, dt, col)
     unsigned long long* rkeys; // [q_max][32]: per drop vehicle, best (dz, dt, row)
     unsigned char* sc;         // [q_max][G]
     int* slist;                // [q_max * G] entries t * G + g
+    int* scix;                 // [q_max][G]: index in slist of a shortcut (customer, gap)
+    int* scw;                  // [SC_CAP][scw_stride]: walks of the first SC_CAP shortcut gaps (below)
+    int scw_stride;
+    int* scpair;               // [SC_CAP][SC_CAP]: makespan with both stops in two shortcut gaps of one customer
     int* trace;
     int* dump_delta;
     int* dump_travel;
@@ -121,7 +135,7 @@ constexpr int RV = 16, CV = 12;   // row / col vector widths (ints)
 constexpr int CB = 8;             // customers per matrix batch
 
 // Walk buffers (one ready array per warp).  The same words hold a matrix
-// batch's vectors (int4 per column and row, int2 per row), a shortcut item's
+// tile's batch vectors, row minima and pair list, a shortcut item's
 // two walk buffers with its departure and tail arrays, the selection's
 // per-customer results (5 words per removed customer) and the removal
 // permutation (n words); no phase needs two of these at once.
@@ -129,7 +143,9 @@ __host__ __device__ inline size_t rdy_words(int n) {
     const size_t rw = static_cast<size_t>(((n + 1) + 3) & ~3);
     const size_t walks = static_cast<size_t>(ALNS_WARPS) * rw;
     const size_t fb = 2 * rw + 2 * ((static_cast<size_t>(2 * n) + 3) & ~static_cast<size_t>(3));
-    const size_t batch = static_cast<size_t>(CB) * (4 * TC + 6 * TR);
+    // tile: column and row vectors, adjacent-pair vectors and row minima per
+    // customer of a batch, then the compacted pair list (int2 per pair)
+    const size_t batch = static_cast<size_t>(CB) * (4 * TC + 8 * TR) + 2 * static_cast<size_t>(TR) * TC;
     const size_t q = static_cast<size_t>(n < 1024 ? n : 1024);
     const size_t sel = 5 * q + 8;
     size_t w = walks > batch ? walks : batch;
@@ -237,9 +253,14 @@ __device__ void stage_W(const AlnsTeam& t, const Smem& s) {
 // walks (one warp; lane r walks route r; m <= 32)
 // ---------------------------------------------------------------------------
 // From the depot: node times H, stock prefixes, makespan, cycle flag.
-__device__ void walk_depot(const AlnsTeam& t, const Smem& s, int* rdy, bool write_arrays, int* z_out,
+__device__ void walk_depot(const AlnsTeam& t, const Smem& s, int* rdy_, bool write_arrays, int* z_out,
                            unsigned* st_out) {
+    const int* __restrict__ sW = s.sW;
+    const int* __restrict__ spp = s.sp;
+    int* const Hh = t.H;
+
     const int lane = threadIdx.x & 31, m = t.m, n = t.n;
+    volatile int* rdy = rdy_;
     for (int c = lane; c <= n; c += 32) rdy[c] = UNRES;
     __syncwarp();
     const bool mine = lane < m;
@@ -247,60 +268,58 @@ __device__ void walk_depot(const AlnsTeam& t, const Smem& s, int* rdy, bool writ
     const int start = pos;
     int dep = 0, last = 0, sv = 0, smin = 0, smax = 0;
     bool walking = mine && pos < end, cyc = false;
-    while (__any_sync(FULL_MASK, walking)) {
-        int w = 0, rv = 0, c = 0;
-        bool go = false, pick = false;
-        if (walking) {
-            w = s.sW[pos];
-            const int o = w & PACK_MASK;
-            c = o >> 1;
-            pick = o & 1;
-            if (pick) rv = rdy[c];
-            go = !pick || rv != UNRES;
+    // up to two ops per lane per step, both reads up front (see walk_source)
+    bool alive = __any_sync(FULL_MASK, walking);
+    while (alive) {
+        const bool can1 = walking, can2 = walking && pos + 1 < end;
+        const int w1 = can1 ? sW[pos] : 0, w2 = can2 ? sW[pos + 1] : 0;
+        const int c1 = (w1 & PACK_MASK) >> 1, c2 = (w2 & PACK_MASK) >> 1;
+        const bool k1 = (w1 & 1) != 0, k2 = (w2 & 1) != 0;
+        const int r1 = (can1 && k1) ? rdy[c1] : 0;
+        const int r2 = (can2 && k2) ? rdy[c2] : 0;
+        const bool go1 = can1 && (!k1 || r1 != UNRES);
+        const bool go2 = go1 && can2 && (!k2 || r2 != UNRES);
+        const int a1 = dep + (w1 >> PACK_SHIFT);
+        const int d1 = k1 ? max(a1, r1) : a1;
+        const int a2 = d1 + (w2 >> PACK_SHIFT);
+        const int d2 = k2 ? max(a2, r2) : a2;
+        if (go1) {
+            if (!k1) rdy[c1] = a1 + spp[c1];
+            if (write_arrays) Hh[pos] = d1;
+            sv += k1 ? 1 : -1;
+            smin = min(smin, sv);
+            smax = max(smax, sv);
+            dep = d1;
+            last = c1;
         }
+        if (go2) {
+            if (!k2) rdy[c2] = a2 + spp[c2];
+            if (write_arrays) Hh[pos + 1] = d2;
+            sv += k2 ? 1 : -1;
+            smin = min(smin, sv);
+            smax = max(smax, sv);
+            dep = d2;
+            last = c2;
+        }
+        pos += (go1 ? 1 : 0) + (go2 ? 1 : 0);
+        const bool more = pos < end;
+        const unsigned prog = __ballot_sync(FULL_MASK, go1);
+        if (walking && more && prog == 0u) cyc = true;
+        walking = walking && more && prog != 0u;
         __syncwarp();
-        if (go) {
-            const int arr = dep + (w >> PACK_SHIFT);
-            if (pick) { dep = max(arr, rv); ++sv; smax = max(smax, sv); }
-            else { dep = arr; rdy[c] = arr + s.sp[c]; --sv; smin = min(smin, sv); }
-            if (write_arrays) {
-                t.H[pos] = dep;
-                t.S_[pos] = sv;
-                t.PMINp[pos] = smin;
-                t.PMAXp[pos] = smax;
-            }
-            last = c;
-            ++pos;
-        }
-        __syncwarp();
-        const unsigned prog = __ballot_sync(FULL_MASK, go);
-        if (walking) {
-            if (pos >= end) walking = false;
-            else if (prog == 0u) { walking = false; cyc = true; }
-        }
+        alive = prog != 0u && __any_sync(FULL_MASK, walking);
     }
     if (cyc)
         for (; pos < end; ++pos) {
-            const int o = s.sW[pos] & PACK_MASK;
+            const int o = sW[pos] & PACK_MASK;
             if (o & 1) { ++sv; smax = max(smax, sv); } else { --sv; smin = min(smin, sv); }
         }
-    // suffix extremes of the stock prefix, route by route
-    if (write_arrays && mine) {
-        int mn = INT32_MAX, mx = INT32_MIN;
-        for (int k = end - 1; k >= start; --k) {
-            mn = min(mn, t.S_[k]);
-            mx = max(mx, t.S_[k]);
-            t.SMINs[k] = mn;
-            t.SMAXs[k] = mx;
-        }
-    }
     int ret = (mine && !cyc && end > start) ? dep + Dx(t, s, last, 0) : 0;
     int load = 0;
     bool bad = false;
     if (mine) {
         if (t.load_full) { bad = smin < -t.Q || smax > 0; load = t.Q; }
         else { bad = -smin + smax > t.Q; load = -smin; }
-        if (write_arrays) t.rload[lane] = load;
     }
     for (int o = 16; o > 0; o >>= 1) {
         ret = max(ret, __shfl_xor_sync(FULL_MASK, ret, o));
@@ -311,220 +330,292 @@ __device__ void walk_depot(const AlnsTeam& t, const Smem& s, int* rdy, bool writ
     if (anycyc) ret = 0x7fffffff;
     *z_out = ret;
     *st_out = st;
-    if (write_arrays && lane == 0) t.ctl->sum_load = load;
 }
 
-// From op u: row u of LP (NEG where unreachable) and T(u).
-__device__ void walk_source(const AlnsTeam& t, const Smem& s, int* rdy, int u, int N) {
+// From op u: row u of LP (NEG where unreachable) and T(u).  Up to two ops per
+// lane per step; ready times have one writer (the dropping lane) and are read
+// volatile, so a pickup sees "unresolved" (and retries) or the final value,
+// and the __syncwarp closing each step makes every write of a step visible in
+// the next: a step in which no lane moves means a precedence cycle.
+__device__ void walk_source(const AlnsTeam& t, const Smem& s, int* rdy_, int u, int N) {
+    const int* __restrict__ sW = s.sW;
+    const int* __restrict__ spp = s.sp;
+
     const int lane = threadIdx.x & 31, m = t.m, n = t.n;
+    volatile int* rdy = rdy_;
     for (int c = lane; c <= n; c += 32) rdy[c] = UNRES;
     __syncwarp();
     const bool mine = lane < m;
-    int pos = mine ? s.sWoff[lane] : 0, end = mine ? s.sWoff[lane + 1] : 0;
+    int pos = mine ? s.sWoff[lane] : 0;
+    const int end = mine ? s.sWoff[lane + 1] : 0;
     int val = NEG, last = 0;
     int* row = t.Ms + static_cast<long long>(u) * N;
     bool walking = mine && pos < end;
-    while (__any_sync(FULL_MASK, walking)) {
-        int w = 0, rv = 0, c = 0;
-        bool go = false, pick = false;
-        if (walking) {
-            w = s.sW[pos];
-            const int o = w & PACK_MASK;
-            c = o >> 1;
-            pick = o & 1;
-            if (pick && pos != u) rv = rdy[c];
-            go = !pick || pos == u || rv != UNRES;
+    // each step reads both candidate stops and both ready times first; a
+    // pickup right behind its own drop waits one step
+    bool alive = __any_sync(FULL_MASK, walking);
+    while (alive) {
+        const bool can1 = walking, can2 = walking && pos + 1 < end;
+        const int w1 = can1 ? sW[pos] : 0, w2 = can2 ? sW[pos + 1] : 0;
+        const int c1 = (w1 & PACK_MASK) >> 1, c2 = (w2 & PACK_MASK) >> 1;
+        const bool k1 = (w1 & 1) != 0, k2 = (w2 & 1) != 0;
+        const bool at1 = pos == u, at2 = pos + 1 == u;
+        const int r1 = (can1 && k1 && !at1) ? rdy[c1] : 0;
+        const int r2 = (can2 && k2 && !at2) ? rdy[c2] : 0;
+        const bool go1 = can1 && (!k1 || at1 || r1 != UNRES);
+        const bool go2 = go1 && can2 && (!k2 || at2 || r2 != UNRES);
+        int v1 = (val == NEG) ? NEG : val + (w1 >> PACK_SHIFT);
+        if (k1 && !at1) v1 = max(v1, r1);
+        if (at1) v1 = 0;
+        int v2 = (v1 == NEG) ? NEG : v1 + (w2 >> PACK_SHIFT);
+        if (k2 && !at2) v2 = max(v2, r2);
+        if (at2) v2 = 0;
+        if (go1) {
+            if (!k1) rdy[c1] = (v1 == NEG) ? NEG : v1 + spp[c1];
+            row[pos] = v1;
+            val = v1;
+            last = c1;
         }
+        if (go2) {
+            if (!k2) rdy[c2] = (v2 == NEG) ? NEG : v2 + spp[c2];
+            row[pos + 1] = v2;
+            val = v2;
+            last = c2;
+        }
+        pos += (go1 ? 1 : 0) + (go2 ? 1 : 0);
+        const bool more = pos < end;
+        const unsigned prog = __ballot_sync(FULL_MASK, go1);
+        if (walking && more && prog == 0u) atomicExch(&t.ctl->err, DEV_BAD_STATE);
+        walking = walking && more && prog != 0u;
         __syncwarp();
-        if (go) {
-            int v = (val == NEG) ? NEG : val + (w >> PACK_SHIFT);
-            if (pick && pos != u) v = max(v, rv);
-            if (pos == u) v = 0;
-            if (!pick) rdy[c] = (v == NEG) ? NEG : v + s.sp[c];
-            row[pos] = v;
-            val = v;
-            last = c;
-            ++pos;
-        }
-        __syncwarp();
-        const unsigned prog = __ballot_sync(FULL_MASK, go);
-        if (walking) {
-            if (pos >= end) walking = false;
-            else if (prog == 0u) { walking = false; atomicExch(&t.ctl->err, DEV_BAD_STATE); }
-        }
+        alive = prog != 0u && __any_sync(FULL_MASK, walking);
     }
     int tail = (mine && val != NEG) ? val + Dx(t, s, last, 0) : NEG;
     for (int o = 16; o > 0; o >>= 1) tail = max(tail, __shfl_xor_sync(FULL_MASK, tail, o));
     if (lane == 0) t.T[u] = tail;
 }
 
-// Full simulation of W + D_c at gap (a,i) + P_c at gap (b,j): makespan or
-// INT32_MAX on a precedence cycle.  Travel legs next to the new stops are read
-// from the distance matrix.
-__device__ int walk_insert(const AlnsTeam& t, const Smem& s, int* rdy, int c, int a, int i, int b, int j) {
-    const int lane = threadIdx.x & 31, m = t.m, n = t.n;
-    for (int q = lane; q <= n; q += 32) rdy[q] = UNRES;
-    __syncwarp();
+// Forward simulation of W plus up to two stops, V1 (op code o1) at gap (a, i)
+// and V2 (op code o2) at gap (b, j); a < 0 or b < 0 leaves one out, and V1
+// goes first when both share a gap.  Returns the makespan (INT32_MAX on a
+// precedence cycle); with Hb non-null the departure of every W position goes
+// to Hb[pos] and V1's to *hv.  Up to two stops per lane per step (see
+// walk_source); the legs next to the new stops are read before the walk.
+__device__ int walk_fwd(const AlnsTeam& t, const Smem& s, int* rdy_, int a, int i, int o1, int b, int j, int o2,
+                        int* Hb, int* hv) {
+    const int* __restrict__ sW = s.sW;
+    const int* __restrict__ spp = s.sp;
+
+    const int lane = threadIdx.x & 31, m = t.m;
+    volatile int* rdy = rdy_;
     const bool mine = lane < m;
     const int base = mine ? s.sWoff[lane] : 0;
     const int L = mine ? s.sWoff[lane + 1] - base : 0;
-    // up to two virtual stops on this route, in route order (drop first at equal gaps)
-    int g1 = -1, o1 = 0, g2 = -1, o2 = 0;
+    // this lane's stops in route order: (gap g0, op v0, leg in tv0, leg after ta0), then (g1, v1, tv1, ta1)
+    int nv = 0, g0 = -1, v0 = 0, g1 = -1, v1 = 0, f0 = 0;
     if (mine) {
-        if (lane == a) { g1 = i; o1 = 2 * c; }
+        if (lane == a) { g0 = i; v0 = o1; f0 = 1; nv = 1; }
         if (lane == b) {
-            if (g1 < 0) { g1 = j; o1 = 2 * c + 1; } else { g2 = j; o2 = 2 * c + 1; }
+            if (nv == 0) { g0 = j; v0 = o2; nv = 1; }
+            else { g1 = j; v1 = o2; nv = 2; }
         }
     }
-    int k = 0, dep = 0, loc = 0, nins = 0;
-    bool prev_virtual = false, done1 = g1 < 0, done2 = g2 < 0;
-    bool walking = mine && (L > 0 || !done1);
-    bool any = walking, cyc = false;
-    while (__any_sync(FULL_MASK, walking)) {
-        int o = 0, rv = 0, cc = 0, dd = 0, which = 0;
-        bool go = false, pick = false;
-        if (walking) {
-            if (!done1 && k == g1) { o = o1; which = 1; }
-            else if (!done2 && k == g2) { o = o2; which = 2; }
-            else { o = s.sW[base + k] & PACK_MASK; which = 0; }
-            cc = o >> 1;
-            pick = o & 1;
-            if (pick) rv = rdy[cc];
-            go = !pick || rv != UNRES;
-            if (go) dd = (which != 0 || prev_virtual) ? Dx(t, s, loc, cc) : (s.sW[base + k] >> PACK_SHIFT);
+    auto cust = [&](int k) { return (sW[base + k] & PACK_MASK) >> 1; };
+    int tv0 = 0, ta0 = 0, tv1 = 0, ta1 = 0;
+    if (nv >= 1) {
+        tv0 = Dx(t, s, g0 > 0 ? cust(g0 - 1) : 0, v0 >> 1);
+        if (nv == 2 && g1 == g0) {
+            tv1 = Dx(t, s, v0 >> 1, v1 >> 1);
+            ta1 = g1 < L ? Dx(t, s, v1 >> 1, cust(g1)) : 0;
+        } else {
+            ta0 = g0 < L ? Dx(t, s, v0 >> 1, cust(g0)) : 0;
+            if (nv == 2) {
+                tv1 = Dx(t, s, cust(g1 - 1), v1 >> 1);
+                ta1 = g1 < L ? Dx(t, s, v1 >> 1, cust(g1)) : 0;
+            }
         }
+    }
+    int k = 0, vi = 0, dep = 0, loc = 0;
+    bool pv = false;                           // the previous stop was a new one
+    bool walking = mine && (L > 0 || nv > 0);
+    const bool any = walking;
+    bool cyc = false;
+    // the stop at state (W position kk, new stops done vv), its op and the leg into it
+    auto peek = [&](int kk, int vv, bool ppv, bool can, bool& virt, bool& real, int& w, int& op, int& leg) {
+        virt = can && vv < nv && kk == (vv == 0 ? g0 : g1);
+        real = can && !virt && kk < L;                     // never past the route
+        w = real ? sW[base + kk] : 0;
+        op = virt ? (vv == 0 ? v0 : v1) : (w & PACK_MASK);
+        leg = virt ? (vv == 0 ? tv0 : tv1) : (ppv ? (vv == 1 ? ta0 : ta1) : (w >> PACK_SHIFT));
+    };
+    // two stops per step: both located and both ready times read first
+    bool alive = __any_sync(FULL_MASK, walking);
+    while (alive) {
+        bool vr1, rl1, vr2, rl2;
+        int w1, op1, lg1, w2, op2, lg2;
+        peek(k, vi, pv, walking, vr1, rl1, w1, op1, lg1);
+        const bool can1 = vr1 || rl1;
+        const int kb = k + (rl1 ? 1 : 0), vb = vi + (vr1 ? 1 : 0);
+        peek(kb, vb, vr1, can1, vr2, rl2, w2, op2, lg2);
+        const bool can2 = vr2 || rl2;
+        const int c1 = op1 >> 1, c2 = op2 >> 1;
+        const bool p1 = (op1 & 1) != 0, p2 = (op2 & 1) != 0;
+        const int r1 = (can1 && p1) ? rdy[c1] : 0;
+        const int r2 = (can2 && p2) ? rdy[c2] : 0;
+        const bool go1 = can1 && (!p1 || r1 != UNRES);
+        const bool go2 = go1 && can2 && (!p2 || r2 != UNRES);
+        const int a1 = dep + lg1;
+        const int d1 = p1 ? max(a1, r1) : a1;
+        const int a2 = d1 + lg2;
+        const int d2 = p2 ? max(a2, r2) : a2;
+        if (go1) {
+            if (!p1) rdy[c1] = a1 + spp[c1];
+            if (Hb != nullptr) {
+                if (vr1) { if (vi == 0 && f0) *hv = d1; }
+                else Hb[base + k] = d1;
+            }
+            dep = d1;
+            loc = c1;
+        }
+        if (go2) {
+            if (!p2) rdy[c2] = a2 + spp[c2];
+            if (Hb != nullptr) {
+                if (vr2) { if (vb == 0 && f0) *hv = d2; }
+                else Hb[base + kb] = d2;
+            }
+            dep = d2;
+            loc = c2;
+            k = kb + (rl2 ? 1 : 0);
+            vi = vb + (vr2 ? 1 : 0);
+            pv = vr2;
+        } else if (go1) {
+            k = kb;
+            vi = vb;
+            pv = vr1;
+        }
+        const bool more = k < L || vi < nv;
+        const unsigned prog = __ballot_sync(FULL_MASK, go1);
+        if (walking && more && prog == 0u) cyc = true;
+        walking = walking && more && prog != 0u;
         __syncwarp();
-        if (go) {
-            const int arr = dep + dd;
-            if (pick) dep = max(arr, rv);
-            else { dep = arr; rdy[cc] = arr + s.sp[cc]; }
-            loc = cc;
-            if (which == 1) done1 = true;
-            else if (which == 2) done2 = true;
-            else ++k;
-            prev_virtual = which != 0;
-            ++nins;
-        }
-        __syncwarp();
-        const unsigned prog = __ballot_sync(FULL_MASK, go);
-        if (walking) {
-            if (k >= L && done1 && done2) walking = false;
-            else if (prog == 0u) { walking = false; cyc = true; }
-        }
+        alive = prog != 0u && __any_sync(FULL_MASK, walking);
     }
     int ret = (mine && any && !cyc) ? dep + Dx(t, s, loc, 0) : 0;
     for (int o = 16; o > 0; o >>= 1) ret = max(ret, __shfl_xor_sync(FULL_MASK, ret, o));
     const unsigned anycyc = __ballot_sync(FULL_MASK, cyc);
     return anycyc ? 0x7fffffff : ret;
+}
+
+// Full simulation of W + D_c at gap (a,i) + P_c at gap (b,j): makespan or
+// INT32_MAX on a precedence cycle.
+__device__ int walk_insert(const AlnsTeam& t, const Smem& s, int* rdy, int c, int a, int i, int b, int j) {
+    const int lane = threadIdx.x & 31, n = t.n;
+    for (int q = lane; q <= n; q += 32) rdy[q] = UNRES;
+    __syncwarp();
+    return walk_fwd(t, s, rdy, a, i, 2 * c, b, j, 2 * c + 1, nullptr, nullptr);
 }
 
 // W plus one stop V (op code ov) at gap (a, i), forward: the departure time of
 // every W position into Hb[pos] and of V into *hv; returns the makespan
 // (INT32_MAX on a precedence cycle).  A pickup V without its drop leaves at
-// arrival: the drop's edge comes with the second stop, not here.
+// arrival (its ready time is set to 0): the drop's edge comes with the second
+// stop, not here.
 __device__ int walk_fwd1(const AlnsTeam& t, const Smem& s, int* rdy, int ov, int a, int i, int* Hb, int* hv) {
-    const int lane = threadIdx.x & 31, m = t.m, n = t.n;
+    const int lane = threadIdx.x & 31, n = t.n;
     for (int q = lane; q <= n; q += 32) rdy[q] = UNRES;
     __syncwarp();
-    const bool mine = lane < m;
-    const int base = mine ? s.sWoff[lane] : 0;
-    const int L = mine ? s.sWoff[lane + 1] - base : 0;
-    const int gv = (mine && lane == a) ? i : -1;
-    int k = 0, dep = 0, loc = 0;
-    bool prev_virtual = false, vdone = gv < 0;
-    bool walking = mine && (L > 0 || !vdone);
-    const bool any = walking;
-    bool cyc = false;
-    while (__any_sync(FULL_MASK, walking)) {
-        int o = 0, rv = 0, cc = 0, dd = 0;
-        bool go = false, pick = false, virt = false;
-        if (walking) {
-            virt = !vdone && k == gv;
-            o = virt ? ov : (s.sW[base + k] & PACK_MASK);
-            cc = o >> 1;
-            pick = (o & 1) && !virt;
-            if (pick) rv = rdy[cc];
-            go = !pick || rv != UNRES;
-            if (go) dd = (virt || prev_virtual) ? Dx(t, s, loc, cc) : (s.sW[base + k] >> PACK_SHIFT);
-        }
-        __syncwarp();
-        if (go) {
-            const int arr = dep + dd;
-            if (pick) dep = max(arr, rv);
-            else {
-                dep = arr;
-                if (!virt) rdy[cc] = arr + s.sp[cc];
-            }
-            loc = cc;
-            if (virt) { vdone = true; *hv = dep; }
-            else { Hb[base + k] = dep; ++k; }
-            prev_virtual = virt;
-        }
-        __syncwarp();
-        const unsigned prog = __ballot_sync(FULL_MASK, go);
-        if (walking) {
-            if (k >= L && vdone) walking = false;
-            else if (prog == 0u) { walking = false; cyc = true; }
-        }
-    }
-    int ret = (mine && any && !cyc) ? dep + Dx(t, s, loc, 0) : 0;
-    for (int o = 16; o > 0; o >>= 1) ret = max(ret, __shfl_xor_sync(FULL_MASK, ret, o));
-    const unsigned anycyc = __ballot_sync(FULL_MASK, cyc);
-    return anycyc ? 0x7fffffff : ret;
+    if (lane == 0 && (ov & 1)) rdy[ov >> 1] = 0;
+    __syncwarp();
+    return walk_fwd(t, s, rdy, a, i, ov, -1, 0, 0, Hb, hv);
 }
 
 // The same graph backward: the tail of every W position (longest path from its
 // departure to the end of the schedule, return leg included) into Tb[pos] and
 // V's into *tv.  A drop's tail also takes p plus its pickup's tail; V has no
-// partner in this graph.  tp: per-customer pickup tails (n + 1 words).
-__device__ void walk_bwd1(const AlnsTeam& t, const Smem& s, int* tp, int ov, int a, int i, int* Tb, int* tv) {
+// partner in this graph.  tp: per-customer pickup tails (n + 1 words).  Up to
+// two stops per lane per step, as in the forward walks.
+__device__ void walk_bwd1(const AlnsTeam& t, const Smem& s, int* tp_, int ov, int a, int i, int* Tb, int* tv) {
+    const int* __restrict__ sW = s.sW;
+    const int* __restrict__ spp = s.sp;
+
     const int lane = threadIdx.x & 31, m = t.m, n = t.n;
+    volatile int* tp = tp_;
     for (int q = lane; q <= n; q += 32) tp[q] = UNRES;
     __syncwarp();
     const bool mine = lane < m;
     const int base = mine ? s.sWoff[lane] : 0;
     const int L = mine ? s.sWoff[lane + 1] - base : 0;
     const int gv = (mine && lane == a) ? i : -1;
+    const int vc = ov >> 1;
+    // legs next to V, read before the walk: V -> the stop after it, the stop before V -> V
+    int lv = 0, lb = 0;
+    if (gv >= 0) {
+        lv = Dx(t, s, vc, gv < L ? (sW[base + gv] & PACK_MASK) >> 1 : 0);
+        if (gv > 0) lb = Dx(t, s, (sW[base + gv - 1] & PACK_MASK) >> 1, vc);
+    }
+    const int lastleg = L > 0 ? Dx(t, s, (sW[base + L - 1] & PACK_MASK) >> 1, 0) : 0;
+    const int vret = gv >= 0 ? Dx(t, s, vc, 0) : 0;
     // k: W position still to do (counting down); V sits between positions gv-1 and gv
-    int k = L - 1, acc = 0, nloc = 0;
-    bool next_virtual = false, vdone = gv < 0, next_depot = true;
+    int k = L - 1, acc = 0;
+    bool vdone = gv < 0, nvn = false, first = true;
     bool walking = mine && (L > 0 || !vdone);
-    while (__any_sync(FULL_MASK, walking)) {
-        int o = 0, rv = 0, cc = 0, dd = 0, w = 0;
-        bool go = false, drop = false, virt = false;
-        if (walking) {
-            virt = !vdone && k == gv - 1;
-            if (!virt) w = s.sW[base + k];
-            o = virt ? ov : (w & PACK_MASK);
-            cc = o >> 1;
-            drop = !(o & 1) && !virt;
-            if (drop) rv = tp[cc];
-            go = !drop || rv != UNRES;
-            if (go) {
-                // travel to the next stop: packed in W when both are W stops
-                if (next_depot) dd = Dx(t, s, cc, 0);
-                else if (virt || next_virtual) dd = Dx(t, s, cc, nloc);
-                else dd = s.sW[base + k + 1] >> PACK_SHIFT;
-            }
+    // the stop at state (kk, done), with "the next stop is V" / "no next stop" flags
+    auto peek = [&](int kk, bool done, bool nx, bool fst, bool can, bool& virt, bool& real, int& w, int& c, int& leg) {
+        virt = can && !done && kk == gv - 1;
+        real = can && !virt && kk >= 0;
+        w = real ? sW[base + kk] : 0;
+        c = virt ? vc : (w & PACK_MASK) >> 1;
+        if (virt) leg = fst ? vret : lv;
+        else if (fst) leg = lastleg;
+        else if (nx) leg = lb;
+        else leg = real ? (sW[base + kk + 1] >> PACK_SHIFT) : 0;
+    };
+    bool alive = __any_sync(FULL_MASK, walking);
+    while (alive) {
+        bool vr1, rl1, vr2, rl2;
+        int w1, c1, lg1, w2, c2, lg2;
+        peek(k, vdone, nvn, first, walking, vr1, rl1, w1, c1, lg1);
+        const bool can1 = vr1 || rl1;
+        const int kb = k - (rl1 ? 1 : 0);
+        const bool db = vdone || vr1;
+        peek(kb, db, vr1, false, can1, vr2, rl2, w2, c2, lg2);
+        const bool can2 = vr2 || rl2;
+        const bool dr1 = rl1 && !(w1 & 1), dr2 = rl2 && !(w2 & 1);
+        const int r1 = dr1 ? tp[c1] : 0;
+        const int r2 = dr2 ? tp[c2] : 0;
+        const bool go1 = can1 && (!dr1 || r1 != UNRES);
+        const bool go2 = go1 && can2 && (!dr2 || r2 != UNRES);
+        int t1 = lg1 + acc;
+        if (dr1) t1 = max(t1, spp[c1] + r1);
+        int t2 = lg2 + t1;
+        if (dr2) t2 = max(t2, spp[c2] + r2);
+        if (go1) {
+            if (rl1 && !dr1) tp[c1] = t1;
+            if (vr1) *tv = t1;
+            else Tb[base + k] = t1;
+            acc = t1;
         }
+        if (go2) {
+            if (rl2 && !dr2) tp[c2] = t2;
+            if (vr2) *tv = t2;
+            else Tb[base + kb] = t2;
+            acc = t2;
+            k = kb - (rl2 ? 1 : 0);
+            vdone = db || vr2;
+            nvn = vr2;
+            first = false;
+        } else if (go1) {
+            k = kb;
+            vdone = db;
+            nvn = vr1;
+            first = false;
+        }
+        const bool more = k >= 0 || !vdone;
+        const unsigned prog = __ballot_sync(FULL_MASK, go1);
+        if (walking && more && prog == 0u) atomicExch(&t.ctl->err, DEV_BAD_STATE);
+        walking = walking && more && prog != 0u;
         __syncwarp();
-        if (go) {
-            int val = dd + acc;
-            if (drop) val = max(val, s.sp[cc] + rv);
-            else if (!virt) tp[cc] = val;
-            if (virt) { vdone = true; *tv = val; }
-            else { Tb[base + k] = val; --k; }
-            acc = val;
-            nloc = cc;
-            next_virtual = virt;
-            next_depot = false;
-        }
-        __syncwarp();
-        const unsigned prog = __ballot_sync(FULL_MASK, go);
-        if (walking) {
-            if (k < 0 && vdone) walking = false;
-            else if (prog == 0u) { walking = false; atomicExch(&t.ctl->err, DEV_BAD_STATE); }
-        }
+        alive = prog != 0u && __any_sync(FULL_MASK, walking);
     }
 }
 
@@ -763,15 +854,14 @@ __device__ void phase_update(const AlnsTeam& t, const Smem& s, int rank, int tea
 __device__ void phase_prep(const AlnsTeam& t, const Smem& s, int rank, int team_blocks, bool incr) {
     AlnsCtl* ctl = t.ctl;
     stage_W(t, s);
-    const int N = s.sWoff[t.m], G = N + t.m;
+    const int N = s.sWoff[t.m];
     const int warp = threadIdx.x >> 5;
     const int team_warps = team_blocks * ALNS_WARPS;
     const int gw = rank * ALNS_WARPS + warp;
     int* rdy = s.rdy + warp * (((t.n + 1) + 3) & ~3);
-    if (incr) {
-        phase_update(t, s, rank, team_blocks);
-        for (int r = gw; r < t.m; r += team_warps) scan_route_stock(t, s, r);
-    }
+    if (incr) phase_update(t, s, rank, team_blocks);
+    // stock arrays and start loads, route by route (the route loads add up into sum_load)
+    for (int r = team_warps - 1 - gw; r < t.m; r += team_warps) scan_route_stock(t, s, r);
     for (int unit = gw; !incr && unit <= N; unit += team_warps) {
         if (unit == 0) {
             int z;
@@ -782,15 +872,15 @@ __device__ void phase_prep(const AlnsTeam& t, const Smem& s, int rank, int team_
             walk_source(t, s, rdy, unit - 1, N);
         }
     }
-    // shortcut gaps and key reset for every customer still to insert
-    const int nrem = ctl->nrem;
+    // shortcut gaps (the rounded legs x->c->y shorter than x->y) and key reset
+    // for every customer still to insert; W alone decides them
+    const int G = N + t.m, nrem = ctl->nrem;
     const long long total = static_cast<long long>(nrem) * G;
     const long long tid = static_cast<long long>(rank) * blockDim.x + threadIdx.x;
     const long long nthr = static_cast<long long>(team_blocks) * blockDim.x;
     for (long long e = tid; e < total; e += nthr) {
         const int ti = static_cast<int>(e / G), g = static_cast<int>(e - static_cast<long long>(ti) * G);
         const int c = t.rem[ti];
-        // gap g -> route r (gaps of route r start at off[r] + r) and position
         int lo = 0, hi = t.m;
         while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
@@ -801,12 +891,13 @@ __device__ void phase_prep(const AlnsTeam& t, const Smem& s, int rank, int team_
         const int y = pos < L ? (s.sW[s.sWoff[r] + pos] & PACK_MASK) >> 1 : 0;
         const int w = (L == 0) ? 0 : Dx(t, s, x, y);
         const bool shortcut = Dx(t, s, x, c) + Dx(t, s, c, y) < w;
-        t.keys[static_cast<long long>(ti) * G + g] = KEY_NONE;
+        t.keys[e] = KEY_NONE;
         if (g < 32) t.rkeys[ti * 32 + g] = KEY_NONE;
-        t.sc[static_cast<long long>(ti) * G + g] = shortcut ? 1 : 0;
+        t.sc[e] = shortcut ? 1 : 0;
         if (shortcut) {
             const int slot = atomicAdd(&ctl->n_short, 1);
             t.slist[slot] = ti * G + g;
+            t.scix[e] = slot;
         }
     }
 }
@@ -838,6 +929,58 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
         t.gsmax[g] = yo >= 0 ? t.SMAXs[yo] : -(1 << 28);
         t.groute[g] = r;
         t.gpos[g] = pos;
+        // constants of gap g in the matrix tiles: as a drop gap (row) and as a pickup gap (column)
+        const int Hx = xo >= 0 ? t.H[xo] : 0, Ty = yo >= 0 ? t.T[yo] : 0;
+        const int sb = xo >= 0 ? t.S_[xo] : 0, pmn = xo >= 0 ? t.PMINp[xo] : 0, pmx = xo >= 0 ? t.PMAXp[xo] : 0;
+        const int smn = yo >= 0 ? t.SMINs[yo] : (1 << 28), smx = yo >= 0 ? t.SMAXs[yo] : -(1 << 28);
+        const int sumL = t.ctl->sum_load, rl = t.rload[r];
+        int la = 0, ladj = 0, lb = 0;
+        const bool okA = cap_ok(t, min(min(pmn, sb - 1), smn - 1), max(pmx, smx - 1), la);
+        const bool okAdj = cap_ok(t, min(min(pmn, sb - 1), smn), max(pmx, smx), ladj);
+        const bool okB = cap_ok(t, min(pmn, smn + 1), max(max(pmx, sb + 1), smx + 1), lb);
+        int4* rw4 = reinterpret_cast<int4*>(t.growc + static_cast<long long>(g) * RV);
+        rw4[0] = make_int4(Hx, Ty, t.gw[g], okAdj && sumL + ladj - rl <= t.R ? 1 : 0);
+        rw4[1] = make_int4(0, 0, okA ? la - rl : 1 << 28, 0);
+        rw4[2] = make_int4(r, pos, xo, yo);
+        rw4[3] = make_int4(pmn, sb, pmx, 0);
+        int4* cw4 = reinterpret_cast<int4*>(t.gcolc + static_cast<long long>(g) * CV);
+        cw4[0] = make_int4(0, 0, 0, 0);
+        cw4[1] = make_int4(okB ? lb - rl : 1 << 28, r, pos, yo);
+        cw4[2] = make_int4(xo, smn, smx, Hx + Ty);
+    }
+    // per (customer, gap): the matrix vectors
+    //   row {max(z, beta) (SKIPV on a shortcut gap), A1 + p_c, E, (dtD + 2^19) << 12}
+    //   adj {max(z, adjacent) (SKIPV on a shortcut gap), ((dtAdj + 2^19) << 12) + gap}
+    //   col {gamma (SKIPV on a shortcut gap), B1, F, (dtP << 12) + gap}
+    {
+        AlnsCtl* ctl = t.ctl;
+        const int nrem = ctl->nrem, z = ctl->z_work;
+        const long long total = static_cast<long long>(nrem) * G;
+        for (long long e = tid; e < total; e += nthr) {
+            const int ti = static_cast<int>(e / G), g = static_cast<int>(e - static_cast<long long>(ti) * G);
+            const int c = t.rem[ti], pc = s.sp[c];
+            int lo = 0, hi = m;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s.sWoff[mid] + mid <= g) lo = mid; else hi = mid;
+            }
+            const int r = lo, pos = g - (s.sWoff[r] + r), off = s.sWoff[r], L = s.sWoff[r + 1] - off;
+            const int xo = pos > 0 ? off + pos - 1 : -1, yo = pos < L ? off + pos : -1;
+            const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0;
+            const int y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
+            const int Hx = xo >= 0 ? t.H[xo] : 0, Ty = yo >= 0 ? t.T[yo] : 0;
+            const int w = (L == 0) ? 0 : Dx(t, s, x, y);
+            const int dxc = Dx(t, s, x, c), dcy = Dx(t, s, c, y), dcc = Dx(t, s, c, c);
+            const int delta = dxc + dcy;
+            const bool shortcut = delta < w;
+            t.vrow[e] = make_int4(shortcut ? SKIPV : max(z, Hx + delta + Ty), Hx + dxc + pc, Hx + delta,
+                                  static_cast<int>(static_cast<unsigned>(delta - w + (1 << 19)) << 12));
+            t.vadj[e] = make_int2(shortcut ? SKIPV : max(z, Hx + dxc + max(dcc, pc) + dcy + Ty),
+                                  static_cast<int>((static_cast<unsigned>(dxc + dcc + dcy - w + (1 << 19)) << 12) |
+                                                   static_cast<unsigned>(g)));
+            t.vcol[e] = make_int4(shortcut ? SKIPV : Hx + Ty + delta, dcy + Ty, delta + Ty,
+                                  static_cast<int>((static_cast<unsigned>(delta - w) << 12) + static_cast<unsigned>(g)));
+        }
     }
     // sparse tables of the stock prefix over op positions.  Every range query
     // lies inside one route, so levels stop at the longest route; each CTA
@@ -876,6 +1019,65 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
             }
         }
     }
+    // Simulations of the shortcut gaps, ahead of the matrix phase: per shortcut
+    // gap g of customer c the graph with D_c alone at g (forward, backward) and
+    // with P_c alone at g (forward, backward); per pair of shortcut gaps of one
+    // customer (g itself twice: the adjacent pair) W with both stops.  One warp
+    // per simulation, handed out from the last CTA down (the first CTAs build
+    // the sparse tables).
+    {
+        AlnsCtl* ctl = t.ctl;
+        const int ns = min(ctl->n_short, SC_CAP);
+        const int nmax = (t.scw_stride - 8) / 4;
+        const int nitems = 4 * ns + ns * ns;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        const int team_warps = team_blocks * ALNS_WARPS;
+        const int gw = (team_blocks - 1 - rank) * ALNS_WARPS + warp;
+        int* rdy = s.rdy + warp * (((t.n + 1) + 3) & ~3);
+        auto route_of = [&](int g, int* pos) {
+            int lo = 0, hi = m;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s.sWoff[mid] + mid <= g) lo = mid; else hi = mid;
+            }
+            *pos = g - (s.sWoff[lo] + lo);
+            return lo;
+        };
+        __syncthreads();                       // the sparse-table buffers are free
+        for (int item = gw; item < nitems; item += team_warps) {
+            if (item < 4 * ns) {
+                const int e = item >> 2, kind = item & 3;
+                const int packed = t.slist[e], ti = packed / G, g = packed - ti * G;
+                const int c = t.rem[ti];
+                int pos = 0;
+                const int r = route_of(g, &pos);
+                int* base = t.scw + static_cast<long long>(e) * t.scw_stride;
+                int* Hb = base + (kind >> 1) * 2 * nmax;
+                int* scal = base + 4 * nmax + (kind >> 1) * 3;
+                const int ov = 2 * c + (kind >> 1);
+                if ((kind & 1) == 0) {
+                    int hv = 0;
+                    const int z1 = walk_fwd1(t, s, rdy, ov, r, pos, Hb, &hv);
+                    if (lane == r) scal[1] = hv;
+                    if (lane == 0) scal[0] = z1;
+                } else {
+                    int tv = 0;
+                    walk_bwd1(t, s, rdy, ov, r, pos, Hb + nmax, &tv);
+                    if (lane == r) scal[2] = tv;
+                }
+            } else {
+                const int q = item - 4 * ns, e1 = q / ns, e2 = q - e1 * ns;
+                const int p1 = t.slist[e1], p2 = t.slist[e2];
+                const int ti = p1 / G;
+                if (p2 / G != ti) continue;
+                int i1 = 0, i2 = 0;
+                const int r1 = route_of(p1 - ti * G, &i1), r2 = route_of(p2 - ti * G, &i2);
+                if (r1 == r2 && i2 < i1) continue;   // the pickup before the drop: never feasible
+                const int zn = walk_insert(t, s, rdy, t.rem[ti], r1, i1, r2, i2);
+                if (lane == 0) t.scpair[e1 * SC_CAP + e2] = zn;
+            }
+        }
+    }
     if (rank == 0 && threadIdx.x == 0) t.ctl->work_counter = 0;
 }
 
@@ -893,66 +1095,55 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
 // load; excluded pairs and shortcut gaps come out at or above SKIPV and never
 // win.  The pair in which both gaps coincide (drop and pickup back to back)
 // is the adjacent case, handled once per row.
-constexpr int SKIPV = 1 << 28;   // schedule times stay below 2^27 (alns_supported)
 
 __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, int N, int G) {
     AlnsCtl* ctl = t.ctl;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5;
     const int r0 = rt * TR, c0 = ct * TC;
-    int* rowc = s.rowv;                        // [TR][RV] tile constants of the drop gaps
-    int* colc = s.colv;                        // [TC][CV] tile constants of the pickup gaps
+    int* rowc = s.rowv;                        // [TR][RV] constants of the drop gaps
+    int* colc = s.colv;                        // [TC][CV] constants of the pickup gaps
     const int sumL = ctl->sum_load;
-    // tile constants
-    const bool is_col = tid < TC;
-    const bool is_row = tid >= TC && tid < TC + TR;
-    const int myg = is_col ? c0 + tid : (is_row ? r0 + tid - TC : G);
-    __syncthreads();                           // previous tile is done with rowc / colc
-    if (is_row) {
-        int* v = rowc + (tid - TC) * RV;
-        const int R = myg;
-        if (R < G) {
-            int la = 0, ladj = 0;
-            const bool okA = cap_ok(t, min(min(t.gpmin[R], t.gsb[R] - 1), t.gsmin[R] - 1),
-                                    max(t.gpmax[R], t.gsmax[R] - 1), la);
-            const bool okAdj = cap_ok(t, min(min(t.gpmin[R], t.gsb[R] - 1), t.gsmin[R]), max(t.gpmax[R], t.gsmax[R]),
-                                      ladj);
-            const int ra = t.groute[R];
-            v[0] = t.gHx[R];
-            v[1] = t.gTy[R];
-            v[2] = t.gw[R];
-            v[3] = okAdj && sumL + ladj - t.rload[ra] <= t.R ? 1 : 0;   // adjacent pair fits
-            v[6] = okA ? la - t.rload[ra] : 1 << 28;
-            v[8] = ra;
-            v[9] = t.gpos[R];
-            v[10] = t.gx[R];
-            v[11] = t.gy[R];
-            v[12] = t.gpmin[R];
-            v[13] = t.gsb[R];
-            v[14] = t.gpmax[R];
+    __syncthreads();                           // the previous tile is done with rowc / colc and the vectors
+    for (int e = tid; e < TR * (RV / 4) + TC * (CV / 4); e += blockDim.x) {
+        if (e < TR * (RV / 4)) {
+            const int rr = e / (RV / 4), q = e - rr * (RV / 4);
+            int4 v = make_int4(0, 0, 0, 0);
+            if (r0 + rr < G) v = reinterpret_cast<const int4*>(t.growc)[static_cast<long long>(r0 + rr) * (RV / 4) + q];
+            else if (q == 2) v.x = -1;         // no such gap: route -1
+            reinterpret_cast<int4*>(rowc)[e] = v;
         } else {
-            v[8] = -1;
-        }
-    }
-    if (is_col) {
-        int* v = colc + tid * CV;
-        const int Cg = myg;
-        if (Cg < G) {
-            int lb = 0;
-            const bool okB = cap_ok(t, min(t.gpmin[Cg], t.gsmin[Cg] + 1),
-                                    max(max(t.gpmax[Cg], t.gsb[Cg] + 1), t.gsmax[Cg] + 1), lb);
-            v[4] = okB ? lb - t.rload[t.groute[Cg]] : 1 << 28;
-            v[5] = t.groute[Cg];
-            v[6] = t.gpos[Cg];
-            v[7] = t.gy[Cg];
-            v[8] = t.gx[Cg];
-            v[9] = t.gsmin[Cg];
-            v[10] = t.gsmax[Cg];
-            v[11] = t.gHx[Cg] + t.gTy[Cg];          // H(x) + T(y)
-        } else {
-            v[5] = -1;
+            const int e2 = e - TR * (RV / 4);
+            const int cc = e2 / (CV / 4), q = e2 - cc * (CV / 4);
+            int4 v = make_int4(0, 0, 0, 0);
+            if (c0 + cc < G) v = reinterpret_cast<const int4*>(t.gcolc)[static_cast<long long>(c0 + cc) * (CV / 4) + q];
+            else if (q == 1) v.y = -1;
+            reinterpret_cast<int4*>(colc)[e2] = v;
         }
     }
     __syncthreads();
+    // Per customer the vectors of the tile's gaps come from the per-step arrays, CB
+    // customers per pair of block barriers, into the walk buffers (unused by tiles):
+    //   cols [CB][TC] int4, rows [CB][TR] int4, adj [CB][TR] int2.
+    int4* cvec = reinterpret_cast<int4*>(s.rdy);
+    int4* rvec = cvec + CB * TC;
+    int2* avec = reinterpret_cast<int2*>(rvec + CB * TR);
+    auto load_batch = [&](int tb, int nb) {
+        for (int it = tid; it < nb * (TR + TC); it += blockDim.x) {
+            const int k = it / (TR + TC), slot = it - k * (TR + TC);
+            const long long vb = static_cast<long long>(tb + k) * G;
+            if (slot < TR) {
+                const int Rr = r0 + slot;
+                const bool in = Rr < G;
+                rvec[k * TR + slot] = in ? t.vrow[vb + Rr] : make_int4(SKIPV, 0, 0, 0);
+                avec[k * TR + slot] = in ? t.vadj[vb + Rr] : make_int2(SKIPV, 0);
+            } else {
+                const int cc = slot - TR, Cg = c0 + cc;
+                cvec[k * TC + cc] = Cg < G ? t.vcol[vb + Cg] : make_int4(SKIPV, 0, 0, Cg);
+            }
+        }
+    };
+    // the first batch's vectors load while the pair values below are read
+    load_batch(0, min(CB, ctl->nrem));
     // this thread's pairs
     const int r = tid >> 3, cb = tid & 7;
     const int* rk = rowc + r * RV;
@@ -961,6 +1152,22 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
     const int R = r0 + r;
     int lpv[TC / 8];
     int diag = -1;                             // column slot of the coinciding gap, if in this thread's set
+    // both table reads of every pair first, as predicated loads all in flight
+    // together: LP(y_a -> x_b) and the cycle test LP(y_b -> x_a) > NEG
+    int lpl[TC / 8], rcl[TC / 8];
+    {
+        const int xa = rk[10], ya = rk[11];
+#pragma unroll
+        for (int kk = 0; kk < TC / 8; ++kk) {
+            const int* ck = colc + (cb + 8 * kk) * CV;
+            const int rb = ck[5], yb = ck[7], xb = ck[8];
+            const bool use = row_ok && rb >= 0;
+            const bool okl = use && ya >= 0 && xb >= 0;
+            const bool okr = use && ra != rb && yb >= 0 && xa >= 0;
+            lpl[kk] = okl ? t.Ms[static_cast<long long>(ya) * N + xb] : NEG;
+            rcl[kk] = okr ? t.Ms[static_cast<long long>(yb) * N + xa] : NEG;
+        }
+    }
 #pragma unroll
     for (int kk = 0; kk < TC / 8; ++kk) {
         const int cc = cb + 8 * kk;
@@ -977,109 +1184,32 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
                     const int mn = min(min(min(rk[12], rk[13] - 1), range_min(t, lo, hi, N) - 1), ck[9]);
                     const int mx = max(max(max(rk[14], range_max(t, lo, hi, N) - 1), t.S_[hi]), ck[10]);
                     int l2 = 0;
-                    if (cap_ok(t, mn, mx, l2) && sumL - t.rload[ra] + l2 <= t.R)
-                        v = t.Ms[static_cast<long long>(lo) * N + hi];
+                    if (cap_ok(t, mn, mx, l2) && sumL - t.rload[ra] + l2 <= t.R) v = lpl[kk];
                 }
             } else {
                 const int dLA = rk[6], dLB = ck[4];
-                const int yb = ck[7], xa = rk[10];
-                const bool cyc = yb >= 0 && xa >= 0 && t.Ms[static_cast<long long>(yb) * N + xa] > NEG;
-                if (!cyc && dLA < (1 << 27) && dLB < (1 << 27) && sumL + dLA + dLB <= t.R) {
-                    const int ya = rk[11], xb = ck[8];
-                    v = (ya >= 0 && xb >= 0) ? t.Ms[static_cast<long long>(ya) * N + xb] : NEG;
-                }
+                if (rcl[kk] == NEG && dLA < (1 << 27) && dLB < (1 << 27) && sumL + dLA + dLB <= t.R) v = lpl[kk];
             }
         }
         lpv[kk] = v;
     }
     const bool adj_ok = rk[3] != 0;
-    // Customers go in batches of CB: every thread builds per-customer vectors
-    // for (customer, gap) pairs of the batch, then runs its 16 entries for each
-    // customer of the batch; two block barriers per batch.  The vectors live
-    // in the per-warp walk buffers, which tiles do not use:
-    //   cols [CB][TC] {gamma (SKIPV on a shortcut gap), B1, F, (dtP << 12) + col}
-    //   rows [CB][TR] {max(z, beta) (SKIPV on a shortcut gap), A1 + p_c, E, (dtD + 2^19) << 12}
-    //   adj  [CB][TR] {max(z, adjacent) (SKIPV on a shortcut gap), ((dtAdj + 2^19) << 12) + row}
-    int4* cvec = reinterpret_cast<int4*>(s.rdy);
-    int4* rvec = cvec + CB * TC;
-    int2* avec = reinterpret_cast<int2*>(rvec + CB * TR);
+    const bool dump = t.mode == 1;
     const int nrem = ctl->nrem;
     const int z = ctl->z_work;
-    const bool dump = t.mode == 1;
     unsigned local_entries = 0;
     const unsigned ncols = static_cast<unsigned>(max(0, min(TC / 8, (G - c0 - cb + 7) / 8)));  // this thread's columns < G
-    for (int tb = 0; tb < nrem; tb += CB) {
-        const int nb = min(CB, nrem - tb);
-        __syncthreads();                       // previous batch's entries are done with the vectors
-        for (int it = tid; it < nb * (TR + TC); it += blockDim.x) {
-            const int k = it / (TR + TC), slot = it - k * (TR + TC);
-            const int c = t.rem[tb + k];
-            const int pc = s.sp[c];
-            if (slot < TR) {
-                const int Rr = r0 + slot;
-                const int* v = rowc + slot * RV;
-                int4 o = make_int4(SKIPV, 0, 0, 0);
-                int2 a = make_int2(SKIPV, 0);
-                if (Rr < G && v[8] >= 0) {
-                    const int xo = v[10], yo = v[11];
-                    const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0, y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
-                    const int dxc = Dx(t, s, x, c), dcy = Dx(t, s, c, y), dcc = Dx(t, s, c, c);
-                    const int Hx = v[0], Ty = v[1], w = v[2];
-                    const int delta = dxc + dcy;
-                    const bool sc = delta < w;                     // shortcut gap: re-simulated in full
-                    o.x = sc ? SKIPV : max(z, Hx + delta + Ty);    // beta: through the drop only
-                    o.y = Hx + dxc + pc;                           // arrival at the drop + processing
-                    o.z = Hx + delta;                              // leaving the drop towards y
-                    o.w = static_cast<int>(static_cast<unsigned>(delta - w + (1 << 19)) << 12);
-                    a.x = sc ? SKIPV : max(z, Hx + dxc + max(dcc, pc) + dcy + Ty);
-                    a.y = static_cast<int>((static_cast<unsigned>(dxc + dcc + dcy - w + (1 << 19)) << 12) |
-                                           static_cast<unsigned>(Rr));
-                }
-                rvec[k * TR + slot] = o;
-                avec[k * TR + slot] = a;
-            } else {
-                const int cc = slot - TR, Cg = c0 + cc;
-                const int* v = colc + cc * CV;
-                int4 o = make_int4(SKIPV, 0, 0, Cg);
-                if (Cg < G && v[5] >= 0) {
-                    const int xo = v[8], yo = v[7];
-                    const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0, y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
-                    const int dxc = Dx(t, s, x, c), dcy = Dx(t, s, c, y);
-                    const int Ty = t.gTy[Cg], w = t.gw[Cg];
-                    const int delta = dxc + dcy;
-                    o.x = delta < w ? SKIPV : v[11] + delta;       // gamma: through the pickup only
-                    o.y = dcy + Ty;                                // leaving the pickup
-                    o.z = delta + Ty;                              // entering the pickup from x
-                    o.w = static_cast<int>((static_cast<unsigned>(delta - w) << 12) + static_cast<unsigned>(Cg));
-                }
-                cvec[k * TC + cc] = o;
-            }
-        }
-        __syncthreads();
-        for (int k = 0; k < nb; ++k) {
-            const int ti = tb + k;
-            const int4 rv = rvec[k * TR + r];
-            unsigned long long best = KEY_NONE;
-            if (row_ok && !dump) {
-#pragma unroll
-                for (int kk = 0; kk < TC / 8; ++kk) {
-                    const int4 g = cvec[k * TC + cb + 8 * kk];
-                    const int zz = max(max(rv.x, g.x), max(rv.y + g.y, rv.z + lpv[kk] + g.z));
-                    const unsigned lo = static_cast<unsigned>(rv.w) + static_cast<unsigned>(g.w);
-                    const unsigned long long key =
-                        (static_cast<unsigned long long>(static_cast<unsigned>(zz)) << 32) | lo;
-                    best = key < best ? key : best;
-                }
-                local_entries += ncols;
-                if (diag >= 0 && adj_ok) {
-                    const int2 a = avec[k * TR + r];
-                    const unsigned long long key =
-                        (static_cast<unsigned long long>(static_cast<unsigned>(a.x)) << 32) | static_cast<unsigned>(a.y);
-                    best = key < best ? key : best;
-                }
-            } else if (row_ok) {
-                // every entry written out (parity runs): shortcut entries are left
-                // to the fallback items, excluded pairs read "infeasible"
+    if (dump) {
+        // every entry written out (parity runs): shortcut entries are left to
+        // the shortcut items, excluded pairs read "infeasible"
+        for (int tb = 0; tb < nrem; tb += CB) {
+            const int nb = min(CB, nrem - tb);
+            __syncthreads();
+            if (tb > 0) load_batch(tb, nb);
+            __syncthreads();
+            for (int k = 0; k < nb; ++k) {
+                const int4 rv = rvec[k * TR + r];
+                if (!row_ok) continue;
                 const bool scR = rv.x >= SKIPV;
 #pragma unroll
                 for (int kk = 0; kk < TC / 8; ++kk) {
@@ -1100,22 +1230,115 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
                     t.dump_travel[idx] = ok ? static_cast<int>(lo >> 12) - (1 << 19) : 0;
                 }
             }
-            // min over the 8 lanes sharing a row
-            for (int o = 4; o > 0; o >>= 1) {
-                const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
-                best = other < best ? other : best;
+        }
+        return;
+    }
+    // Only part of the pairs survive (a sixth to a third at n = 1000), scattered
+    // over the tile.  They are compacted into one row-major list for the whole
+    // CTA and every thread takes an equal contiguous share of it per customer,
+    // keeping a running minimum per row that it folds into the row's slot in
+    // shared memory when its row changes; once per batch the row minima go to
+    // the global keys.
+    unsigned long long* rowbest = reinterpret_cast<unsigned long long*>(avec + CB * TR);   // [CB][TR]
+    int2* list = reinterpret_cast<int2*>(rowbest + CB * TR);                                // [TR * TC]
+    unsigned fm = 0;
+#pragma unroll
+    for (int kk = 0; kk < TC / 8; ++kk) fm |= (lpv[kk] != SKIPV ? 1u : 0u) << kk;
+    const int cnt = __popc(fm);
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL_MASK, incl, o);
+        if ((tid & 31) >= o) incl += y;
+    }
+    int* wsum = s.misc + 16;                   // [ALNS_WARPS] per-warp totals
+    if ((tid & 31) == 31) wsum[warp] = incl;
+    __syncthreads();
+    int woff = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < ALNS_WARPS; ++w) {
+        const int v = wsum[w];
+        woff += w < warp ? v : 0;
+        total += v;
+    }
+    {
+        int at = woff + incl - cnt;
+#pragma unroll
+        for (int kk = 0; kk < TC / 8; ++kk)
+            if ((fm >> kk) & 1u) list[at++] = make_int2(lpv[kk], (r << 8) | (cb + 8 * kk));
+    }
+    for (int q = tid; q < CB * TR; q += blockDim.x) rowbest[q] = KEY_NONE;
+    const int beg = static_cast<int>((static_cast<long long>(tid) * total) / blockDim.x);
+    const int end = static_cast<int>((static_cast<long long>(tid + 1) * total) / blockDim.x);
+    for (int tb = 0; tb < nrem; tb += CB) {
+        const int nb = min(CB, nrem - tb);
+        __syncthreads();                       // the list and the row slots are ready; the previous batch is flushed
+        if (tb > 0) load_batch(tb, nb);
+        __syncthreads();
+        // IL customers per pass over the share: the list entry and the row
+        // change are shared, the minimum chains run side by side
+        constexpr int IL = 4;
+        const unsigned long long lim = static_cast<unsigned long long>(SKIPV) << 32;
+        for (int k = 0; k < nb; k += IL) {
+            int kx[IL];
+#pragma unroll
+            for (int u = 0; u < IL; ++u) kx[u] = min(k + u, nb - 1);
+            int cur = -1;
+            int4 rv[IL];
+            unsigned long long best[IL];
+#pragma unroll
+            for (int u = 0; u < IL; ++u) { rv[u] = make_int4(0, 0, 0, 0); best[u] = KEY_NONE; }
+            for (int q = beg; q < end; ++q) {
+                const int2 le = list[q];
+                const int rr = le.y >> 8;
+                if (rr != cur) {
+#pragma unroll
+                    for (int u = 0; u < IL; ++u) {
+                        if (best[u] < lim && k + u < nb) atomicMin(&rowbest[kx[u] * TR + cur], best[u]);
+                        rv[u] = rvec[kx[u] * TR + rr];
+                        best[u] = KEY_NONE;
+                    }
+                    cur = rr;
+                }
+                const int cc = le.y & 0xFF;
+#pragma unroll
+                for (int u = 0; u < IL; ++u) {
+                    const int4 g = cvec[kx[u] * TC + cc];
+                    const int zz = max(max(rv[u].x, g.x), max(rv[u].y + g.y, rv[u].z + le.x + g.z));
+                    const unsigned lo = static_cast<unsigned>(rv[u].w) + static_cast<unsigned>(g.w);
+                    const unsigned long long key = (static_cast<unsigned long long>(static_cast<unsigned>(zz)) << 32) | lo;
+                    best[u] = key < best[u] ? key : best[u];
+                }
             }
-            const int bz = static_cast<int>(best >> 32);
-            if (!dump && cb == 0 && best != KEY_NONE && bz < SKIPV) {
+#pragma unroll
+            for (int u = 0; u < IL; ++u)
+                if (best[u] < lim && k + u < nb) atomicMin(&rowbest[kx[u] * TR + cur], best[u]);
+            if (diag >= 0 && adj_ok) {
+                for (int u = 0; u < IL && k + u < nb; ++u) {
+                    const int2 a = avec[(k + u) * TR + r];
+                    const unsigned long long key =
+                        (static_cast<unsigned long long>(static_cast<unsigned>(a.x)) << 32) | static_cast<unsigned>(a.y);
+                    if (key < lim) atomicMin(&rowbest[(k + u) * TR + r], key);
+                }
+            }
+        }
+        if (row_ok) local_entries += static_cast<unsigned>(nb) * ncols;
+        __syncthreads();
+        // row minima of the batch to the global keys, slots back to empty
+        for (int q = tid; q < nb * TR; q += blockDim.x) {
+            const unsigned long long b = rowbest[q];
+            if (b != KEY_NONE) {
+                const int k = q / TR, rr = q - k * TR;
+                const int ti = tb + k, Rr = r0 + rr, rra = rowc[rr * RV + 8];
                 const unsigned long long key =
-                    (static_cast<unsigned long long>(static_cast<unsigned>(bz - z) ^ 0x80000000u) << 32) |
-                    (best & 0xFFFFFFFFull);
-                atomicMin(&t.keys[static_cast<long long>(ti) * G + R], key);
-                atomicMin(&t.rkeys[ti * 32 + ra], ((key >> 12) << 12) | static_cast<unsigned long long>(R));
+                    (static_cast<unsigned long long>(static_cast<unsigned>(static_cast<int>(b >> 32) - z) ^ 0x80000000u) << 32) |
+                    (b & 0xFFFFFFFFull);
+                atomicMin(&t.keys[static_cast<long long>(ti) * G + Rr], key);
+                atomicMin(&t.rkeys[ti * 32 + rra], ((key >> 12) << 12) | static_cast<unsigned long long>(Rr));
+                rowbest[q] = KEY_NONE;
             }
         }
     }
-    const unsigned warp_entries = __reduce_add_sync(0xffffffffu, local_entries);
+    const unsigned warp_entries = __reduce_add_sync(FULL_MASK, local_entries);
     if ((tid & 31) == 0 && warp_entries) atomicAdd(&ctl->entries, static_cast<unsigned long long>(warp_entries));
 }
 
@@ -1142,23 +1365,30 @@ __device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N,
     const int c = t.rem[ti];
     const int n = t.n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int rw = ((n + 1) + 3) & ~3;
-    int* Hb = s.rdy + 2 * rw;                  // [N] departures in W + V
-    int* Tb = Hb + ((N + 3) & ~3);             // [N] tails in W + V
+    // the first SC_CAP shortcut gaps were simulated in the gap phase
+    const bool pre = e < SC_CAP;
+    const int nmax = (t.scw_stride - 8) / 4;
+    const int* pbase = t.scw + static_cast<long long>(pre ? e : 0) * t.scw_stride + as_col * 2 * nmax;
+    int* Hs = s.rdy + 2 * rw;                  // [N] departures in W + V (simulated here)
+    int* Ts = Hs + ((N + 3) & ~3);             // [N] tails in W + V
     int* sh = s.misc + 8;                      // z1, h_v, t_v
     const int ga = t.groute[g], gi = t.gpos[g];
     const int ov = 2 * c + as_col;
-    if (warp == 0) {
+    if (!pre && warp == 0) {
         int hv = 0;
-        const int z1 = walk_fwd1(t, s, s.rdy, ov, ga, gi, Hb, &hv);
+        const int z1 = walk_fwd1(t, s, s.rdy, ov, ga, gi, Hs, &hv);
         if (lane == ga) sh[1] = hv;
         if (lane == 0) sh[0] = z1;
-    } else if (warp == 1) {
+    } else if (!pre && warp == 1) {
         int tv = 0;
-        walk_bwd1(t, s, s.rdy + rw, ov, ga, gi, Tb, &tv);
+        walk_bwd1(t, s, s.rdy + rw, ov, ga, gi, Ts, &tv);
         if (lane == ga) sh[2] = tv;
     }
     __syncthreads();
-    const int z1 = sh[0], hv = sh[1], tv = sh[2];
+    const int* Hb = pre ? pbase : Hs;
+    const int* Tb = pre ? pbase + nmax : Ts;
+    const int* scal = pre ? t.scw + static_cast<long long>(e) * t.scw_stride + 4 * nmax + as_col * 3 : sh;
+    const int z1 = scal[0], hv = scal[1], tv = scal[2];
     const int z = ctl->z_work, pc = s.sp[c];
     const long long scrow = static_cast<long long>(ti) * G;
     const bool dump = t.mode == 1;
@@ -1216,7 +1446,8 @@ __device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N,
                     continue;
                 }
                 const bool capok = entry_capacity(t, g, col, N);
-                const int zn = walk_insert(t, s, rdy, c, a, i, b, j);
+                const int e2 = t.scix[scrow + col];
+                const int zn = (pre && e2 < SC_CAP) ? t.scpair[e * SC_CAP + e2] : walk_insert(t, s, rdy, c, a, i, b, j);
                 const bool ok = capok && zn != 0x7fffffff;
                 if (lane == 0) {
                     ++cnt;
@@ -1268,9 +1499,12 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
     // per-customer results in the (now free) walk buffers
     unsigned long long* bestv = reinterpret_cast<unsigned long long*>(s.rdy);       // [nrem] (dz,dt)<<12 | row
     long long* regret = reinterpret_cast<long long*>(s.rdy) + nrem;                // [nrem]
-    int* bestcol = s.rdy + 4 * nrem;                                               // [nrem]
+    // the column of a customer's best entry, read from its row key (needed on
+    // ties of (dz, dt) between customers and for the one picked)
+    auto colof = [&](int ti) {
+        return static_cast<int>(t.keys[static_cast<long long>(ti) * G + (bestv[ti] & 0xFFF)] & 0xFFF);
+    };
     for (int ti = warp; ti < nrem; ti += ALNS_WARPS) {
-        const unsigned long long* kr = t.keys + static_cast<long long>(ti) * G;
         // best per drop vehicle (the regret-2 options) and overall, from the route keys
         const unsigned long long rk = lane < m ? t.rkeys[ti * 32 + lane] : KEY_NONE;
         unsigned long long bv = rk;
@@ -1288,7 +1522,6 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
         if (lane == 0) {
             bestv[ti] = bv;
             regret[ti] = c2 - c1;
-            bestcol[ti] = bv == KEY_NONE ? 0 : static_cast<int>(kr[bv & 0xFFF] & 0xFFF);
         }
     }
     __syncthreads();
@@ -1303,8 +1536,8 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
                 const unsigned long long pa = bestv[ti] >> 12, pb = bestv[pick] >> 12;
                 if (pa != pb) { if (pa < pb) pick = ti; }
                 else {
-                    const long long fa = static_cast<long long>(bestv[ti] & 0xFFF) * G + bestcol[ti];
-                    const long long fb = static_cast<long long>(bestv[pick] & 0xFFF) * G + bestcol[pick];
+                    const long long fa = static_cast<long long>(bestv[ti] & 0xFFF) * G + colof(ti);
+                    const long long fb = static_cast<long long>(bestv[pick] & 0xFFF) * G + colof(pick);
                     if (fa < fb) pick = ti;
                 }
             } else {
@@ -1316,7 +1549,7 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
         } else {
             ctl->pick_t = pick;
             ctl->pick_row = static_cast<int>(bestv[pick] & 0xFFF);
-            ctl->pick_col = bestcol[pick];
+            ctl->pick_col = colof(pick);
         }
     }
     __syncthreads();
@@ -1370,11 +1603,15 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
         up[14] = Dx(t, s, c, c);
         up[15] = s.sp[c];
         ctl->incr = shortcut ? 0 : 1;
-        if (!shortcut) ctl->sum_load = 0;      // the route scans of the update add it back up
+        ctl->sum_load = 0;                     // the route scans of the next step add it back up
     }
     __syncthreads();
+    // drop the inserted customer from the ones still to insert, order kept
+    int* tmp = s.rdy;
+    for (int k = threadIdx.x; k + 1 < nrem; k += blockDim.x) tmp[k] = t.rem[k + (k >= pick ? 1 : 0)];
+    __syncthreads();
+    for (int k = threadIdx.x; k + 1 < nrem; k += blockDim.x) t.rem[k] = tmp[k];
     if (threadIdx.x == 0) {
-        for (int k = pick; k + 1 < nrem; ++k) t.rem[k] = t.rem[k + 1];
         ctl->nrem = nrem - 1;
         ctl->wsel ^= 1;
         ctl->n_short = 0;
@@ -1430,6 +1667,7 @@ __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
         ctl->work_counter = 0;
         ctl->wsel = 0;
         ctl->incr = 0;                         // W lost customers: the next step walks it in full
+        ctl->sum_load = 0;
     }
     __syncthreads();
     // removed customers in ascending id order (ballot compaction by warp 0)
@@ -1647,6 +1885,9 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
             const int fail = *reinterpret_cast<volatile int*>(&ctl->repair_fail);
             if (nrem == 0 || fail) break;
             const bool incr = *reinterpret_cast<volatile int*>(&ctl->incr) != 0;
+            if (rank == 0 && threadIdx.x == 0) {
+                if (incr) ctl->steps_incr += 1; else ctl->steps_full += 1;
+            }
             phase_prep(t, s, rank, team_blocks, incr);
             if (incr) {
                 // every CTA swaps its own copy of the pointers: the update wrote the second buffers
@@ -1707,10 +1948,16 @@ static size_t team_bytes(int n, int m, int qmax, int iterations, bool dump) {
     add(levels * N, 4); add(levels * N, 4);
     for (int i = 0; i < 12; ++i) add(G, 4);
     add(m, 4);
+    add(G * 16, 4); add(G * 12, 4);
+    add(static_cast<size_t>(qmax) * G, 16); add(static_cast<size_t>(qmax) * G, 16);
+    add(static_cast<size_t>(qmax) * G, 8);
     add(static_cast<size_t>(qmax) * G, 8);
     add(static_cast<size_t>(qmax) * 32, 8);
     add(static_cast<size_t>(qmax) * G, 1);
     add(static_cast<size_t>(qmax) * G, 4);
+    add(static_cast<size_t>(qmax) * G, 4);
+    add(static_cast<size_t>(SC_CAP) * (4 * N + 8), 4);
+    add(static_cast<size_t>(SC_CAP) * SC_CAP, 4);
     add(std::max(iterations, 1), 4);
     if (dump) { add(G * G, 4); add(G * G, 4); }
     return w;
@@ -1736,10 +1983,17 @@ static void carve_team(AlnsTeam& t, DevBuf& B, int n, int m, int qmax, int itera
     t.gw = B.take<int>(G); t.gsb = B.take<int>(G); t.gpmin = B.take<int>(G); t.gpmax = B.take<int>(G);
     t.gsmin = B.take<int>(G); t.gsmax = B.take<int>(G); t.groute = B.take<int>(G); t.gpos = B.take<int>(G);
     t.rload = B.take<int>(m);
+    t.growc = B.take<int>(G * 16); t.gcolc = B.take<int>(G * 12);
+    t.vrow = B.take<int4>(static_cast<size_t>(qmax) * G); t.vcol = B.take<int4>(static_cast<size_t>(qmax) * G);
+    t.vadj = B.take<int2>(static_cast<size_t>(qmax) * G);
     t.keys = B.take<unsigned long long>(static_cast<size_t>(qmax) * G);
     t.rkeys = B.take<unsigned long long>(static_cast<size_t>(qmax) * 32);
     t.sc = B.take<unsigned char>(static_cast<size_t>(qmax) * G);
     t.slist = B.take<int>(static_cast<size_t>(qmax) * G);
+    t.scix = B.take<int>(static_cast<size_t>(qmax) * G);
+    t.scw_stride = static_cast<int>(4 * N + 8);
+    t.scw = B.take<int>(static_cast<size_t>(SC_CAP) * (4 * N + 8));
+    t.scpair = B.take<int>(static_cast<size_t>(SC_CAP) * SC_CAP);
     t.trace = B.take<int>(std::max(iterations, 1));
     t.dump_delta = dump ? B.take<int>(G * G) : nullptr;
     t.dump_travel = dump ? B.take<int>(G * G) : nullptr;
@@ -2038,6 +2292,8 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
         stats->fallback_entries = static_cast<int64_t>(out.fallback_entries);
         stats->team_blocks = tb;
         for (int i = 0; i < 6; ++i) stats->phase_ms[i] = static_cast<double>(out.phase_ns[i]) * 1e-6;
+        stats->incremental_steps = static_cast<int64_t>(out.steps_incr);
+        stats->full_steps = static_cast<int64_t>(out.steps_full);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     cleanup();
