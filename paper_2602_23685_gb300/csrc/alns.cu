@@ -58,6 +58,7 @@ struct AlnsCtl {
     unsigned st_work;
     int stagnation, repair_fail, wsel, err;
     int work_counter, n_short, sum_load;
+    int walks_done;                   // shortcut simulations finished in this greedy step
     int pick_t, pick_row, pick_col;
     unsigned bar_count, bar_gen;
     double T, T_init;
@@ -215,6 +216,42 @@ __device__ bool team_barrier(AlnsCtl* ctl, int team_blocks, unsigned& gen) {
                     }
                     __nanosleep(64);
                 }
+            }
+            __threadfence();
+        }
+        gen += 1u;
+        __syncthreads();
+    }
+    return *reinterpret_cast<volatile int*>(&ctl->err) == 0;
+}
+
+// The same barrier in two halves, so a CTA can do work that no one waits on
+// at the barrier (the shortcut simulations) between arriving and waiting.
+__device__ void team_arrive(AlnsCtl* ctl, int team_blocks, unsigned gen) {
+    __syncthreads();
+    if (team_blocks > 1 && threadIdx.x == 0) {
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
+        if (arrived == static_cast<unsigned>(team_blocks)) {
+            ctl->bar_count = 0u;
+            __threadfence();
+            atomicExch(&ctl->bar_gen, gen + 1u);
+        }
+    }
+}
+
+__device__ bool team_wait(AlnsCtl* ctl, int team_blocks, unsigned& gen) {
+    __syncthreads();
+    if (team_blocks > 1) {
+        if (threadIdx.x == 0) {
+            volatile unsigned* vgen = &ctl->bar_gen;
+            const uint64_t t0 = global_ns();
+            while (*vgen == gen) {
+                if (global_ns() - t0 > 2000000000ull) {
+                    atomicExch(&ctl->err, DEV_TIMEOUT_BARRIER);
+                    break;
+                }
+                __nanosleep(64);
             }
             __threadfence();
         }
@@ -1019,12 +1056,24 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
             }
         }
     }
-    // Simulations of the shortcut gaps, ahead of the matrix phase: per shortcut
-    // gap g of customer c the graph with D_c alone at g (forward, backward) and
-    // with P_c alone at g (forward, backward); per pair of shortcut gaps of one
-    // customer (g itself twice: the adjacent pair) W with both stops.  One warp
-    // per simulation, handed out from the last CTA down (the first CTAs build
-    // the sparse tables).
+    if (rank == 0 && threadIdx.x == 0) t.ctl->work_counter = 0;
+}
+
+// Simulations of the shortcut gaps for the matrix phase: per shortcut gap g of
+// customer c the graph with D_c alone at g (forward, backward) and with P_c
+// alone at g (forward, backward); per pair of shortcut gaps of one customer (g
+// itself twice: the adjacent pair) W with both stops.  One warp per
+// simulation, handed out from the last CTA down.  They run between arriving
+// at the barrier before the matrix phase and waiting at it, so the tiles of
+// the other CTAs proceed meanwhile; every finished simulation is counted in
+// walks_done, which the shortcut items wait for.
+__device__ int gap_walk_items(const AlnsTeam& t) {
+    const int ns = min(t.ctl->n_short, SC_CAP);
+    return 4 * ns + ns * ns;
+}
+
+__device__ void gap_walks(const AlnsTeam& t, const Smem& s, int rank, int team_blocks) {
+    const int m = t.m, N = s.sWoff[m], G = N + m;
     {
         AlnsCtl* ctl = t.ctl;
         const int ns = min(ctl->n_short, SC_CAP);
@@ -1043,7 +1092,6 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
             *pos = g - (s.sWoff[lo] + lo);
             return lo;
         };
-        __syncthreads();                       // the sparse-table buffers are free
         for (int item = gw; item < nitems; item += team_warps) {
             if (item < 4 * ns) {
                 const int e = item >> 2, kind = item & 3;
@@ -1069,17 +1117,24 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
                 const int q = item - 4 * ns, e1 = q / ns, e2 = q - e1 * ns;
                 const int p1 = t.slist[e1], p2 = t.slist[e2];
                 const int ti = p1 / G;
-                if (p2 / G != ti) continue;
+                if (p2 / G != ti) { if (lane == 0) atomicAdd(&ctl->walks_done, 1); continue; }
                 int i1 = 0, i2 = 0;
                 const int r1 = route_of(p1 - ti * G, &i1), r2 = route_of(p2 - ti * G, &i2);
-                if (r1 == r2 && i2 < i1) continue;   // the pickup before the drop: never feasible
+                if (r1 == r2 && i2 < i1) {           // the pickup before the drop: never feasible
+                    if (lane == 0) atomicAdd(&ctl->walks_done, 1);
+                    continue;
+                }
                 const int zn = walk_insert(t, s, rdy, t.rem[ti], r1, i1, r2, i2);
                 if (lane == 0) t.scpair[e1 * SC_CAP + e2] = zn;
             }
+            // results visible device-wide, then counted
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) atomicAdd(&ctl->walks_done, 1);
         }
     }
-    if (rank == 0 && threadIdx.x == 0) t.ctl->work_counter = 0;
 }
+
 
 // One matrix tile (rows rt*TR.., cols ct*TC..) for every customer still to insert.
 //
@@ -1473,8 +1528,10 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
     const int N = s.sWoff[t.m], G = N + t.m;
     const int RT = (G + TR - 1) / TR, CT = (G + TC - 1) / TC;
     const int tiles = RT * CT;
-    const int nfb = 2 * ctl->n_short;          // shortcut items first: each holds two walks
-    const int total = nfb + tiles;
+    const int nfb = 2 * ctl->n_short;          // shortcut items after the tiles: they wait for the walks
+    const int total = tiles + nfb;
+    const int nwalks = gap_walk_items(t);
+    bool walks_seen = false;
     int* slot = s.misc;
     for (;;) {
         __syncthreads();
@@ -1482,11 +1539,27 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
         __syncthreads();
         const int item = slot[0];
         if (item >= total) break;
-        if (item < nfb) {
-            fallback_item(t, s, item, N, G);
+        if (item < tiles) {
+            matrix_tile(t, s, item / CT, item - (item / CT) * CT, N, G);
         } else {
-            const int tile = item - nfb;
-            matrix_tile(t, s, tile / CT, tile - (tile / CT) * CT, N, G);
+            if (!walks_seen) {
+                // the shortcut simulations, still running in other CTAs, must be done (bounded wait)
+                if (threadIdx.x == 0) {
+                    volatile int* wd = &ctl->walks_done;
+                    const uint64_t t0 = global_ns();
+                    while (*wd < nwalks) {
+                        if (global_ns() - t0 > 2000000000ull) {
+                            atomicExch(&ctl->err, DEV_TIMEOUT_BARRIER);
+                            break;
+                        }
+                        __nanosleep(256);
+                    }
+                    __threadfence();
+                }
+                __syncthreads();
+                walks_seen = true;
+            }
+            fallback_item(t, s, item - tiles, N, G);
         }
     }
 }
@@ -1604,6 +1677,7 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
         up[15] = s.sp[c];
         ctl->incr = shortcut ? 0 : 1;
         ctl->sum_load = 0;                     // the route scans of the next step add it back up
+        ctl->walks_done = 0;
     }
     __syncthreads();
     // drop the inserted customer from the ones still to insert, order kept
@@ -1668,6 +1742,7 @@ __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
         ctl->wsel = 0;
         ctl->incr = 0;                         // W lost customers: the next step walks it in full
         ctl->sum_load = 0;
+        ctl->walks_done = 0;
     }
     __syncthreads();
     // removed customers in ascending id order (ballot compaction by warp 0)
@@ -1849,7 +1924,9 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
         phase_prep(t, s, rank, team_blocks, false);
         if (!team_barrier(ctl, team_blocks, gen)) return;
         phase_gaps(t, s, rank, team_blocks);
-        if (!team_barrier(ctl, team_blocks, gen)) return;
+        team_arrive(ctl, team_blocks, gen);
+        gap_walks(t, s, rank, team_blocks);
+        if (!team_wait(ctl, team_blocks, gen)) return;
         phase_matrix(t, s);
         team_barrier(ctl, team_blocks, gen);
         return;
@@ -1902,7 +1979,9 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
             if (!team_barrier(ctl, team_blocks, gen)) return;
             mark(1);
             phase_gaps(t, s, rank, team_blocks);
-            if (!team_barrier(ctl, team_blocks, gen)) return;
+            team_arrive(ctl, team_blocks, gen);
+            gap_walks(t, s, rank, team_blocks);
+            if (!team_wait(ctl, team_blocks, gen)) return;
             mark(2);
             phase_matrix(t, s);
             if (!team_barrier(ctl, team_blocks, gen)) return;
