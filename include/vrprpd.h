@@ -271,20 +271,29 @@ int vrprpd_insertion_matrix(const vrprpd_instance* inst, const int32_t* ops_host
 /* BRKGA (Section 4.4, Algorithm 2) on the device                            */
 /* ======================================================================== */
 
-/* Chromosome layout: L = 2n + m float32 keys in [0,1).  keys[2(c-1)+isPickup]
- * is the priority of customer c's dropoff/pickup (lower = scheduled first,
- * Section 4.4.1); keys[2n+v] orders the vehicles for SelectVehicle's
- * tie-break (lower key = preferred). */
+/* Chromosome layouts, float32 keys in [0,1).  Both start with the 2n op
+ * priorities: keys[2(c-1)+isPickup] for customer c's dropoff/pickup (lower =
+ * scheduled first, Section 4.4.1).
+ *   VRPRPD_LAYOUT_VKEYS (L = 2n + m): keys[2n+v] orders the vehicles for
+ *     SelectVehicle's tie-break (lower key = preferred).
+ *   VRPRPD_LAYOUT_HINTS (L = 4n, the paper's (pi, alpha)): keys[2n + o-2] is
+ *     op o's assignment hint alpha_o; among the vehicles at the least arrival
+ *     op o goes to h = floor(m * alpha_o) (fp64, capped at m-1), else to the
+ *     next one in cyclic order h+1, h+2, ... (mod m). */
+#define VRPRPD_LAYOUT_VKEYS 0
+#define VRPRPD_LAYOUT_HINTS 1
+
 typedef struct {
     int32_t pop, generations;
     int32_t warm_slots;        /* slots seeded from the warm start (0 without one) */
     int32_t warm_variants;     /* distinct warm variants cycled over those slots (20) */
     float elite_frac, mutant_frac, rho;  /* Table 3: 0.15, 0.15, 0.7 */
     float eps;                 /* warm perturbation half-width (0.03, Section 4.4.5) */
+    int32_t layout;            /* VRPRPD_LAYOUT_VKEYS (default) or VRPRPD_LAYOUT_HINTS */
 } vrprpd_brkga_params;
 
 /* Table 3 values: pop 30000, 20000 generations, elite/mutant 0.15, rho 0.7,
- * warm slots ceil(0.15 pop), 20 variants, eps 0.03. */
+ * warm slots ceil(0.15 pop), 20 variants, eps 0.03; layout VRPRPD_LAYOUT_VKEYS. */
 void vrprpd_brkga_params_default(vrprpd_brkga_params* params);
 
 /*
@@ -293,22 +302,25 @@ void vrprpd_brkga_params_default(vrprpd_brkga_params* params);
  * dropoff is feasible on a vehicle that can load one more resource within Q
  * and the pool R; a pickup is feasible once its dropoff is scheduled, on a
  * vehicle with room; SelectVehicle takes the least arrival time t[v] +
- * d(l[v], c), ties to the lower vehicle key; the pickup leaves at
- * max(arrival, T_drop + p_c).  Passes stop when everything is scheduled or a
- * pass schedules nothing.
- *   keys     device, num x L float32.
+ * d(l[v], c), ties by the layout's rule (vehicle keys or the op's hint); the
+ * pickup leaves at max(arrival, T_drop + p_c).  Passes stop when everything
+ * is scheduled or a pass schedules nothing.
+ *   keys     device, num x L float32 (L by layout: 2n + m or 4n).
+ *   layout   VRPRPD_LAYOUT_VKEYS or VRPRPD_LAYOUT_HINTS (else VRPRPD_EINVAL).
  *   ops/off  device, num x 2n and num x (m+1): the decoded routes (scheduled ops only).
  *   z        device, num: makespan of the decoded routes.
  *   unsched  device, num: ops left unscheduled.
  *   fitness  device, num int64: z + 10^6 * unsched (Section 4.4.3).
  * Asynchronous on stream.  Needs m <= 32 and 2n + m <= 8192.
  */
-int vrprpd_brkga_decode(const vrprpd_instance* inst, const float* keys, int32_t num, int32_t* ops,
-                        int32_t* off, int32_t* z, int32_t* unsched, int64_t* fitness, void* stream);
+int vrprpd_brkga_decode(const vrprpd_instance* inst, const float* keys, int32_t num, int32_t layout,
+                        int32_t* ops, int32_t* off, int32_t* z, int32_t* unsched, int64_t* fitness,
+                        void* stream);
 
 /*
  * Run the BRKGA: warm-started population (slot 0 = the exact encoding of
- * `warm`, pi_o = (r-1)/L_v and vehicle key v/m; slots 1..warm_slots-1 cycle
+ * `warm`, pi_o = (r-1)/L_v and vehicle key v/m, or every op's hint v/m rounded
+ * up so that floor(m * alpha) = v under VRPRPD_LAYOUT_HINTS; slots 1..warm_slots-1 cycle
  * through perturbed variants, key + U(-eps, eps) clamped to [0, 1-2^-24];
  * the rest uniform random), then per generation: decode, re-evaluate the
  * decoded routes with the batched evaluator, rank by (fitness, index), copy

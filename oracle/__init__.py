@@ -66,7 +66,16 @@ class AlnsStats(C.Structure):
 class BrkgaParams(C.Structure):
     _fields_ = [("pop", C.c_int32), ("generations", C.c_int32), ("warm_slots", C.c_int32),
                 ("warm_variants", C.c_int32), ("elite_frac", C.c_float),
-                ("mutant_frac", C.c_float), ("rho", C.c_float), ("eps", C.c_float)]
+                ("mutant_frac", C.c_float), ("rho", C.c_float), ("eps", C.c_float),
+                ("layout", C.c_int32)]
+
+
+LAYOUT_VKEYS = 0   # 2n priority keys + m vehicle keys
+LAYOUT_HINTS = 1   # 2n priority keys + 2n assignment hints (Section 4.4.1)
+
+
+def key_length(I, layout):
+    return 4 * I.n if layout == LAYOUT_HINTS else 2 * I.n + I.m
 
 
 def lib():
@@ -103,6 +112,8 @@ def lib():
                                           i32p]
             L.oracle_decode.argtypes = [C.POINTER(Inst), f32p, i32p, i32p, i32p, i32p, i64p]
             L.oracle_encode.argtypes = [C.POINTER(Inst), i32p, i32p, f32p]
+            L.oracle_decode_l.argtypes = [C.POINTER(Inst), f32p, C.c_int32, i32p, i32p, i32p, i32p, i64p]
+            L.oracle_encode_l.argtypes = [C.POINTER(Inst), i32p, i32p, C.c_int32, f32p]
             L.oracle_brkga_run.argtypes = [C.POINTER(Inst), C.POINTER(BrkgaParams), i32p, i32p,
                                            C.c_uint64, f32p, i64p, i32p, i32p, i64p]
             _lib = L
@@ -255,35 +266,36 @@ def alns_run(I, init_ops, init_off, params, seed):
     return dict(best_ops=bo, best_off=bf, cur_ops=co, cur_off=cf, stats=st, trace=trace)
 
 
-def decode(I, keys):
+def decode(I, keys, layout=LAYOUT_VKEYS):
     keys = np.ascontiguousarray(keys, dtype=np.float32)
+    assert keys.shape[-1] == key_length(I, layout)
     ops = np.zeros(2 * I.n, np.int32)
     off = np.zeros(I.m + 1, np.int32)
     z = np.zeros(1, np.int32)
     un = np.zeros(1, np.int32)
     fit = np.zeros(1, np.int64)
-    lib().oracle_decode(C.byref(I.c), _p(keys, C.c_float), _p(ops), _p(off), _p(z), _p(un),
-                        _p(fit, C.c_int64))
+    lib().oracle_decode_l(C.byref(I.c), _p(keys, C.c_float), layout, _p(ops), _p(off), _p(z), _p(un),
+                          _p(fit, C.c_int64))
     return ops, off, int(z[0]), int(un[0]), int(fit[0])
 
 
-def encode(I, ops, off):
+def encode(I, ops, off, layout=LAYOUT_VKEYS):
     ops = np.ascontiguousarray(ops, dtype=np.int32)
     off = np.ascontiguousarray(off, dtype=np.int32)
-    keys = np.zeros(2 * I.n + I.m, np.float32)
-    lib().oracle_encode(C.byref(I.c), _p(ops), _p(off), _p(keys, C.c_float))
+    keys = np.zeros(key_length(I, layout), np.float32)
+    lib().oracle_encode_l(C.byref(I.c), _p(ops), _p(off), layout, _p(keys, C.c_float))
     return keys
 
 
 def brkga_params(pop, generations, elite=0.2, mutant=0.1, rho=0.7, warm_frac=0.15,
-                 warm_variants=20, eps=0.03):
+                 warm_variants=20, eps=0.03, layout=LAYOUT_VKEYS):
     import math
     return BrkgaParams(pop, generations, int(math.ceil(warm_frac * pop - 1e-9)), warm_variants,
-                       elite, mutant, rho, eps)
+                       elite, mutant, rho, eps, layout)
 
 
 def brkga_run(I, params, warm_ops, warm_off, seed):
-    L = 2 * I.n + I.m
+    L = key_length(I, params.layout)
     keys = np.zeros((params.pop, L), np.float32)
     trace = np.zeros(max(1, params.generations), np.int64)
     bo = np.zeros(2 * I.n, np.int32)

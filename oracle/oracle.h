@@ -97,16 +97,30 @@ int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t
                     oracle_alns_stats* st, int32_t* z_trace);
 
 /* ---- BRKGA (Algorithm 2 decoder, Section 4.4) ---- */
-/* keys: 2n priority keys (op index 2(c-1)+isPickup) followed by m vehicle keys. */
+/* Chromosome layouts.  Both start with 2n priority keys (op index
+ * 2(c-1)+isPickup).  Layout 0 (2n+m keys): then m vehicle keys; SelectVehicle
+ * ties go to the lower vehicle key.  Layout 1 (4n keys, Section 4.4.1): then
+ * 2n assignment hints alpha_o; op o's ties go to the hinted vehicle
+ * h = floor(m * alpha_o) (computed in fp64, at most m-1), then by increasing
+ * cyclic distance (v - h) mod m. */
+#define OR_LAYOUT_VKEYS 0
+#define OR_LAYOUT_HINTS 1
 int oracle_decode(const oracle_inst* I, const float* keys, int32_t* ops, int32_t* off,
                   int32_t* z, int32_t* unscheduled, int64_t* fitness);
+int oracle_decode_l(const oracle_inst* I, const float* keys, int32_t layout, int32_t* ops, int32_t* off,
+                    int32_t* z, int32_t* unscheduled, int64_t* fitness);
 
+/* ALNS seed encoding (Section 4.4.5): pi_o = (r-1)/L_v; layout 0 vehicle
+ * key v/m; layout 1 hint alpha_o = v/m for every op on vehicle v, rounded up
+ * to the smallest float with m * alpha_o >= v, so that floor(m * alpha_o) = v. */
 void oracle_encode(const oracle_inst* I, const int32_t* ops, const int32_t* off, float* keys);
+void oracle_encode_l(const oracle_inst* I, const int32_t* ops, const int32_t* off, int32_t layout, float* keys);
 
 typedef struct {
     int32_t pop, generations, warm_slots, warm_variants;
     float elite_frac, mutant_frac, rho;
     float eps;                            /* perturbation half-width, 0.03 */
+    int32_t layout;                       /* OR_LAYOUT_VKEYS or OR_LAYOUT_HINTS */
 } oracle_brkga_params;
 
 int oracle_brkga_run(const oracle_inst* I, const oracle_brkga_params* P,

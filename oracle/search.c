@@ -514,8 +514,17 @@ int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t
 
 /* ------------------------------------------------------------------------ */
 /* BRKGA decoder (Algorithm 2).  keys[0..2n) are op priorities (op index     */
-/* 2(c-1)+isPickup), keys[2n..2n+m) order the vehicles for tie-breaks.       */
+/* 2(c-1)+isPickup); then either m vehicle keys ordering the vehicles for    */
+/* tie-breaks (layout 0) or 2n per-op assignment hints (layout 1).           */
 /* ------------------------------------------------------------------------ */
+/* the vehicle an assignment hint names: floor(m * alpha) in fp64, capped */
+static int hint_vehicle(float alpha, int m) {
+    double x = (double)alpha * (double)m;
+    int h = (int)floor(x);
+    if (h > m - 1) h = m - 1;
+    if (h < 0) h = 0;
+    return h;
+}
 static const float* g_keys;
 static int key_cmp(const void* pa, const void* pb) {
     int a = *(const int*)pa, b = *(const int*)pb;
@@ -526,6 +535,11 @@ static int key_cmp(const void* pa, const void* pb) {
 
 int oracle_decode(const oracle_inst* I, const float* keys, int32_t* ops, int32_t* off, int32_t* z_out,
                   int32_t* unsched_out, int64_t* fitness_out) {
+    return oracle_decode_l(I, keys, OR_LAYOUT_VKEYS, ops, off, z_out, unsched_out, fitness_out);
+}
+
+int oracle_decode_l(const oracle_inst* I, const float* keys, int32_t layout, int32_t* ops, int32_t* off,
+                    int32_t* z_out, int32_t* unsched_out, int64_t* fitness_out) {
     const int n = I->n, m = I->m, two_n = 2 * n;
     const int full = (I->flags & OR_LOAD_FULL) != 0;
     int* order = malloc(sizeof(int) * (two_n + 1));
@@ -535,8 +549,10 @@ int oracle_decode(const oracle_inst* I, const float* keys, int32_t* ops, int32_t
     g_keys = keys;
     qsort(order, (size_t)two_n, sizeof(int), key_cmp);                           /* line 1 */
     for (int v = 0; v < m; v++) vorder[v] = v;
-    g_keys = keys + two_n;
-    qsort(vorder, (size_t)m, sizeof(int), key_cmp);
+    if (layout == OR_LAYOUT_VKEYS) {
+        g_keys = keys + two_n;
+        qsort(vorder, (size_t)m, sizeof(int), key_cmp);
+    }
     for (int r = 0; r < m; r++) rank[vorder[r]] = r;
     int64_t* t = calloc((size_t)m, sizeof(int64_t));
     int* loc = calloc((size_t)m, sizeof(int));
@@ -580,6 +596,28 @@ int oracle_decode(const oracle_inst* I, const float* keys, int32_t* ops, int32_t
                 }
             }
             if (best < 0) continue;
+            if (layout == OR_LAYOUT_HINTS) {
+                /* among the vehicles at the least arrival: the hinted one, then cyclic order */
+                const int h = hint_vehicle(keys[two_n + oi], m);
+                int bd = m;
+                for (int v = 0; v < m; v++) {
+                    int ok;
+                    if (!pick) {
+                        if (full) ok = net[v] > -I->Q;
+                        else {
+                            int nl = load[v] > -(net[v] - 1) ? load[v] : -(net[v] - 1);
+                            int mx = nmax[v] > 0 ? nmax[v] : 0;
+                            ok = nl + mx <= I->Q && sum_load - load[v] + nl <= I->R;
+                        }
+                    } else {
+                        if (full) ok = net[v] < 0;
+                        else ok = load[v] + net[v] + 1 <= I->Q;
+                    }
+                    if (!ok || t[v] + Dd(I, loc[v], c) != best_arr) continue;
+                    const int dv = ((v - h) % m + m) % m;
+                    if (dv < bd) { bd = dv; best = v; }
+                }
+            }
             int v = best;
             if (!pick) {
                 t[v] = best_arr;
@@ -623,14 +661,30 @@ int oracle_decode(const oracle_inst* I, const float* keys, int32_t* ops, int32_t
     return 0;
 }
 
-/* ALNS seed encoding (Section 4.4.5): pi_o = (r-1)/L_v, vehicle key v/m. */
+/* ALNS seed encoding (Section 4.4.5): pi_o = (r-1)/L_v; vehicle key v/m
+ * (layout 0) or the hint v/m of every op on vehicle v (layout 1), the latter
+ * rounded up to the smallest float with m * alpha >= v so that the decoder's
+ * floor(m * alpha) names v again. */
+static float hint_of(int v, int m) {
+    float a = (float)v / (float)m;
+    while ((double)a * (double)m < (double)v) a = nextafterf(a, 2.0f);
+    return a;
+}
+
 void oracle_encode(const oracle_inst* I, const int32_t* ops, const int32_t* off, float* keys) {
+    oracle_encode_l(I, ops, off, OR_LAYOUT_VKEYS, keys);
+}
+
+void oracle_encode_l(const oracle_inst* I, const int32_t* ops, const int32_t* off, int32_t layout, float* keys) {
     const int n = I->n, m = I->m;
-    for (int k = 0; k < 2 * n; k++) keys[k] = 0.0f;
+    for (int k = 0; k < (layout == OR_LAYOUT_HINTS ? 4 * n : 2 * n); k++) keys[k] = 0.0f;
     for (int v = 0; v < m; v++) {
         int L = off[v + 1] - off[v];
-        for (int r = 0; r < L; r++) keys[ops[off[v] + r] - 2] = (float)r / (float)L;
-        keys[2 * n + v] = (float)v / (float)m;
+        for (int r = 0; r < L; r++) {
+            keys[ops[off[v] + r] - 2] = (float)r / (float)L;
+            if (layout == OR_LAYOUT_HINTS) keys[2 * n + ops[off[v] + r] - 2] = hint_of(v, m);
+        }
+        if (layout == OR_LAYOUT_VKEYS) keys[2 * n + v] = (float)v / (float)m;
     }
 }
 
@@ -647,7 +701,7 @@ static int fit_cmp(const void* pa, const void* pb) {
 int oracle_brkga_run(const oracle_inst* I, const oracle_brkga_params* P, const int32_t* warm_ops,
                      const int32_t* warm_off, uint64_t seed, float* final_keys, int64_t* trace,
                      int32_t* best_ops, int32_t* best_off, int64_t* best_fitness) {
-    const int n = I->n, m = I->m, L = 2 * n + m, pop = P->pop;
+    const int n = I->n, m = I->m, L = P->layout == OR_LAYOUT_HINTS ? 4 * n : 2 * n + m, pop = P->pop;
     const uint64_t key = stream_key(seed, STREAM_BRKGA), wkey = stream_key(seed, STREAM_WARM);
     const uint64_t per = (uint64_t)L + 2;
     int Ne = (int)floor((double)P->elite_frac * (double)pop);
@@ -664,7 +718,7 @@ int oracle_brkga_run(const oracle_inst* I, const oracle_brkga_params* P, const i
     /* initial population: warm slots then random keys */
     int warm = warm_ops ? P->warm_slots : 0;
     if (warm > pop) warm = pop;
-    if (warm_ops) oracle_encode(I, warm_ops, warm_off, base);
+    if (warm_ops) oracle_encode_l(I, warm_ops, warm_off, P->layout, base);
     const float top = 1.0f - 1.0f / 16777216.0f;
     for (int s = 0; s < pop; s++) {
         float* kk = cur + (size_t)s * L;
@@ -687,7 +741,7 @@ int oracle_brkga_run(const oracle_inst* I, const oracle_brkga_params* P, const i
         for (int s = 0; s < pop; s++) {
             int32_t z, un;
             int64_t f;
-            oracle_decode(I, cur + (size_t)s * L, dops, doff, &z, &un, &f);
+            oracle_decode_l(I, cur + (size_t)s * L, P->layout, dops, doff, &z, &un, &f);
             fit[s].f = f;
             fit[s].idx = s;
         }
@@ -717,7 +771,7 @@ int oracle_brkga_run(const oracle_inst* I, const oracle_brkga_params* P, const i
     }
     int32_t z, un;
     int64_t f;
-    oracle_decode(I, cur + (size_t)fit[0].idx * L, best_ops, best_off, &z, &un, &f);
+    oracle_decode_l(I, cur + (size_t)fit[0].idx * L, P->layout, best_ops, best_off, &z, &un, &f);
     *best_fitness = f;
     if (final_keys) memcpy(final_keys, cur, sizeof(float) * (size_t)pop * L);
     free(cur); free(nxt); free(base); free(fit); free(dops); free(doff);

@@ -303,29 +303,37 @@ def insertion_matrix(inst, ops, off, c, stream=None):
 # ---------------------------------------------------------------------------
 # BRKGA (Section 4.4)
 # ---------------------------------------------------------------------------
+LAYOUT_VKEYS = 0   # 2n op priorities + m vehicle keys
+LAYOUT_HINTS = 1   # 2n op priorities + 2n assignment hints (the paper's 4n chromosome)
+
+
+def key_length(inst, layout=LAYOUT_VKEYS):
+    return 4 * inst.n if layout == LAYOUT_HINTS else 2 * inst.n + inst.m
+
+
 def brkga_params(pop, generations, elite=0.2, mutant=0.1, rho=0.7, warm_frac=0.15, warm_variants=20,
-                 eps=0.03):
+                 eps=0.03, layout=LAYOUT_VKEYS):
     import math
     from ._search_sig import BrkgaParams
     return BrkgaParams(pop, generations, int(math.ceil(warm_frac * pop - 1e-9)), warm_variants,
-                       elite, mutant, rho, eps)
+                       elite, mutant, rho, eps, layout)
 
 
-def brkga_decode(inst, keys, stream=None):
-    """Decode device keys (num x (2n+m) float32) -> routes, makespan, unscheduled, fitness."""
+def brkga_decode(inst, keys, layout=LAYOUT_VKEYS, stream=None):
+    """Decode device keys (num x L float32, L by layout) -> routes, makespan, unscheduled, fitness."""
     torch = _torch()
     if keys.dtype != torch.float32 or keys.device.type != "cuda" or not keys.is_contiguous():
         raise TypeError("keys must be a contiguous CUDA float32 tensor")
     num = keys.shape[0]
-    if tuple(keys.shape) != (num, 2 * inst.n + inst.m):
-        raise ValueError("keys must be num x (2n+m)")
+    if tuple(keys.shape) != (num, key_length(inst, layout)):
+        raise ValueError(f"keys must be num x {key_length(inst, layout)}")
     dev = keys.device
     ops = torch.empty((num, 2 * inst.n), dtype=torch.int32, device=dev)
     off = torch.empty((num, inst.m + 1), dtype=torch.int32, device=dev)
     z = torch.empty(num, dtype=torch.int32, device=dev)
     un = torch.empty(num, dtype=torch.int32, device=dev)
     fit = torch.empty(num, dtype=torch.int64, device=dev)
-    _check(lib().vrprpd_brkga_decode(inst.handle, keys.data_ptr(), num, ops.data_ptr(), off.data_ptr(),
+    _check(lib().vrprpd_brkga_decode(inst.handle, keys.data_ptr(), num, layout, ops.data_ptr(), off.data_ptr(),
                                      z.data_ptr(), un.data_ptr(), fit.data_ptr(), _stream_ptr(stream)))
     return ops, off, z, un, fit
 
@@ -341,7 +349,7 @@ def brkga_run(inst, params, seed=0, warm=None, final_keys=False, stream=None):
     fitness = np.zeros(1, np.int64)
     keys = None
     if final_keys:
-        keys = torch.empty((params.pop, 2 * inst.n + inst.m), dtype=torch.float32, device="cuda")
+        keys = torch.empty((params.pop, key_length(inst, params.layout)), dtype=torch.float32, device="cuda")
     _check(lib().vrprpd_brkga_run(inst.handle, C.byref(params), C.byref(warm_s) if warm_s is not None else None,
                                   C.c_uint64(seed), C.byref(best), fitness.ctypes.data, trace.ctypes.data,
                                   keys.data_ptr() if keys is not None else None, _stream_ptr(stream)))

@@ -27,7 +27,7 @@ class AlnsStats(C.Structure):
 class BrkgaParams(C.Structure):
     _fields_ = [("pop", C.c_int32), ("generations", C.c_int32), ("warm_slots", C.c_int32),
                 ("warm_variants", C.c_int32), ("elite_frac", C.c_float), ("mutant_frac", C.c_float),
-                ("rho", C.c_float), ("eps", C.c_float)]
+                ("rho", C.c_float), ("eps", C.c_float), ("layout", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -64,7 +64,7 @@ def register(L):
     L.vrprpd_multi_destroy.restype = None
     L.vrprpd_brkga_params_default.argtypes = [C.POINTER(BrkgaParams)]
     L.vrprpd_brkga_params_default.restype = None
-    L.vrprpd_brkga_decode.argtypes = [vp, vp, C.c_int32, vp, vp, vp, vp, vp, vp]
+    L.vrprpd_brkga_decode.argtypes = [vp, vp, C.c_int32, C.c_int32, vp, vp, vp, vp, vp, vp]
     L.vrprpd_brkga_run.argtypes = [vp, C.POINTER(BrkgaParams), C.POINTER(Solution), C.c_uint64,
                                    C.POINTER(Solution), vp, vp, vp, vp]
     L.vrprpd_server_create.argtypes = [C.c_size_t, C.c_int32, C.POINTER(vp)]

@@ -40,6 +40,7 @@ struct DecArgs {
     const float* keys2;
     const BrkgaCtl* ctl;
     int num, n, m, R, Q, load_full, L, P;   // P = power of two >= 2n
+    int layout;          // VRPRPD_LAYOUT_VKEYS (2n+m keys) or VRPRPD_LAYOUT_HINTS (4n keys)
     const int32_t* d32;
     const int32_t* p;
     int smem_dist;       // 1 = distance matrix staged in shared memory
@@ -60,6 +61,15 @@ __host__ __device__ inline size_t dec_warp_words(int n, int P) {
     // sort buffer (u64) + tdrop + sched bitmap + per-op (vehicle<<16 | seq)
     return static_cast<size_t>(2 * P) + (((n + 1) + 3) & ~3) + ((((2 * n + 2 + 31) / 32) + 3) & ~3) +
            (((2 * n) + 3) & ~3);
+}
+
+// The vehicle an assignment hint names: floor(m * alpha) in fp64 (exact for a
+// float alpha and m <= 32), capped at m - 1.
+__host__ __device__ inline int hint_vehicle(float alpha, int m) {
+    const double x = static_cast<double>(alpha) * static_cast<double>(m);
+    int h = static_cast<int>(floor(x));
+    h = h > m - 1 ? m - 1 : h;
+    return h < 0 ? 0 : h;
 }
 
 __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
@@ -108,10 +118,12 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
                 __syncwarp();
             }
         }
-        // ---- vehicle ranks: stable argsort of the m vehicle keys ----
-        const float kv = lane < m ? __fadd_rn(kk[two_n + lane], 0.0f) : 0.0f;
+        // ---- tie-break order: vehicle ranks (stable argsort of the m vehicle
+        // keys) or, per op, cyclic distance from the hinted vehicle ----
+        const bool hints = a.layout == VRPRPD_LAYOUT_HINTS;
+        const float kv = (!hints && lane < m) ? __fadd_rn(kk[two_n + lane], 0.0f) : 0.0f;
         int rank = 0;
-        for (int u = 0; u < m; ++u) {
+        for (int u = 0; !hints && u < m; ++u) {
             const float ku = __shfl_sync(FULL_MASK, kv, u);
             if (lane < m && (ku < kv || (ku == kv && u < lane))) ++rank;
         }
@@ -139,8 +151,9 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
                     }
                 }
                 const int arr = ok ? tv + dist(locv, c) : 0;
+                const int tie = hints ? (lane - hint_vehicle(kk[two_n + oi], m) + m) % m : rank;
                 unsigned long long key = ok ? ((static_cast<unsigned long long>(arr) << 10) |
-                                               (static_cast<unsigned>(rank) << 5) | static_cast<unsigned>(lane))
+                                               (static_cast<unsigned>(tie) << 5) | static_cast<unsigned>(lane))
                                             : ~0ull;
                 for (int off = 16; off > 0; off >>= 1) {
                     const unsigned long long other = __shfl_xor_sync(FULL_MASK, key, off);
@@ -205,18 +218,33 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// v/m rounded up to the smallest float with m * alpha >= v: the hint that
+// hint_vehicle maps back to v
+__device__ inline float hint_of(int v, int m) {
+    float x = __fdiv_rn(static_cast<float>(v), static_cast<float>(m));
+    for (int it = 0; it < 4 && __dmul_rn(static_cast<double>(x), static_cast<double>(m)) < static_cast<double>(v); ++it)
+        x = __int_as_float(__float_as_int(x) + 1);
+    return x;
+}
+
 __global__ void encode_kernel(const int32_t* __restrict__ ops, const int32_t* __restrict__ off, int n, int m,
-                              float* __restrict__ base) {
-    // ALNS seed encoding: pi_o = (r-1)/L_v (here r is 0-based), vehicle key v/m
-    for (int i = threadIdx.x; i < 2 * n; i += blockDim.x) base[i] = 0.0f;
+                              int layout, float* __restrict__ base) {
+    // ALNS seed encoding: pi_o = (r-1)/L_v (here r is 0-based); vehicle key
+    // v/m, or the hint of vehicle v for each of its ops
+    const bool hints = layout == VRPRPD_LAYOUT_HINTS;
+    for (int i = threadIdx.x; i < (hints ? 4 * n : 2 * n); i += blockDim.x) base[i] = 0.0f;
     __syncthreads();
     for (int v = 0; v < m; ++v) {
         const int L = off[v + 1] - off[v];
-        for (int r = threadIdx.x; r < L; r += blockDim.x)
-            base[ops[off[v] + r] - 2] = __fdiv_rn(static_cast<float>(r), static_cast<float>(L));
+        for (int r = threadIdx.x; r < L; r += blockDim.x) {
+            const int oi = ops[off[v] + r] - 2;
+            base[oi] = __fdiv_rn(static_cast<float>(r), static_cast<float>(L));
+            if (hints) base[2 * n + oi] = hint_of(v, m);
+        }
     }
-    for (int v = threadIdx.x; v < m; v += blockDim.x)
-        base[2 * n + v] = __fdiv_rn(static_cast<float>(v), static_cast<float>(m));
+    if (!hints)
+        for (int v = threadIdx.x; v < m; v += blockDim.x)
+            base[2 * n + v] = __fdiv_rn(static_cast<float>(v), static_cast<float>(m));
 }
 
 __global__ void init_pop_kernel(float* __restrict__ keys, const float* __restrict__ base, int pop, int L, int warm,
@@ -343,7 +371,7 @@ static int plan_decode(const vrprpd_instance* I, int num, DecPlan* D) {
     return VRPRPD_OK;
 }
 
-static DecArgs dec_args(const vrprpd_instance* I, const DecPlan& D, int num) {
+static DecArgs dec_args(const vrprpd_instance* I, const DecPlan& D, int num, int layout) {
     DecArgs a{};
     a.num = num;
     a.n = I->n;
@@ -351,7 +379,8 @@ static DecArgs dec_args(const vrprpd_instance* I, const DecPlan& D, int num) {
     a.R = I->R;
     a.Q = I->Q;
     a.load_full = (I->flags & VRPRPD_LOAD_FULL) != 0;
-    a.L = 2 * I->n + I->m;
+    a.layout = layout;
+    a.L = layout == VRPRPD_LAYOUT_HINTS ? 4 * I->n : 2 * I->n + I->m;
     a.P = D.P;
     a.d32 = I->d32;
     a.p = I->p;
@@ -373,17 +402,21 @@ extern "C" void vrprpd_brkga_params_default(vrprpd_brkga_params* P) {
     P->mutant_frac = 0.15f;
     P->rho = 0.7f;
     P->eps = 0.03f;
+    P->layout = VRPRPD_LAYOUT_VKEYS;
 }
 
-extern "C" int vrprpd_brkga_decode(const vrprpd_instance* I, const float* keys, int32_t num, int32_t* ops, int32_t* off,
-                                   int32_t* z, int32_t* unsched, int64_t* fitness, void* stream) {
+extern "C" int vrprpd_brkga_decode(const vrprpd_instance* I, const float* keys, int32_t num, int32_t layout,
+                                   int32_t* ops, int32_t* off, int32_t* z, int32_t* unsched, int64_t* fitness,
+                                   void* stream) {
     VRP_CHECK(I && keys && ops && off && z && unsched && fitness, VRPRPD_EINVAL, "NULL argument");
     VRP_CHECK(num >= 0, VRPRPD_EINVAL, "negative count");
+    VRP_CHECK(layout == VRPRPD_LAYOUT_VKEYS || layout == VRPRPD_LAYOUT_HINTS, VRPRPD_EINVAL, "unknown key layout %d",
+              layout);
     if (num == 0) return VRPRPD_OK;
     DecPlan D;
     int rc = plan_decode(I, num, &D);
     if (rc) return rc;
-    DecArgs a = dec_args(I, D, num);
+    DecArgs a = dec_args(I, D, num, layout);
     a.keys = keys;
     a.ops = ops;
     a.off = off;
@@ -402,7 +435,10 @@ extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_par
     VRP_CHECK(P->pop >= 2 && P->pop <= 16384, VRPRPD_EINVAL, "pop must lie in [2, 16384]");
     VRP_CHECK(P->generations >= 1, VRPRPD_EINVAL, "generations must be >= 1");
     VRP_CHECK(batched_supported(I), VRPRPD_EINVAL, "the batched evaluator does not support this instance");
-    const int n = I->n, m = I->m, pop = P->pop, L = 2 * n + m, G = P->generations;
+    VRP_CHECK(P->layout == VRPRPD_LAYOUT_VKEYS || P->layout == VRPRPD_LAYOUT_HINTS, VRPRPD_EINVAL,
+              "unknown key layout %d", P->layout);
+    const int n = I->n, m = I->m, pop = P->pop, G = P->generations;
+    const int L = P->layout == VRPRPD_LAYOUT_HINTS ? 4 * n : 2 * n + m;
     int Ne = static_cast<int>(std::floor(static_cast<double>(P->elite_frac) * pop));
     int Nm = static_cast<int>(std::floor(static_cast<double>(P->mutant_frac) * pop));
     if (Ne < 1) Ne = 1;
@@ -455,7 +491,7 @@ extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_par
     if (warm && e == cudaSuccess) {
         e = cudaMemcpyAsync(wops, warm->ops, 2 * n * 4, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(woff, warm->off, (m + 1) * 4, cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) encode_kernel<<<1, 256, 0, s>>>(wops, woff, n, m, base);
+        if (e == cudaSuccess) encode_kernel<<<1, 256, 0, s>>>(wops, woff, n, m, P->layout, base);
     }
     if (e == cudaSuccess) {
         init_pop_kernel<<<std::min<long long>((static_cast<long long>(pop) * L + 255) / 256, 4096), 256, 0, s>>>(
@@ -466,7 +502,7 @@ extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_par
     DecPlan D;
     int rc = plan_decode(I, pop, &D);
     if (rc) { cleanup(); return rc; }
-    DecArgs da = dec_args(I, D, pop);
+    DecArgs da = dec_args(I, D, pop, P->layout);
     da.keys = buf0;
     da.keys2 = buf1;
     da.ctl = ctl;
