@@ -205,7 +205,10 @@ typedef struct {
     double w_min;
     int32_t q_min, q_max;      /* 0, 0 = q_max = max(4, floor(0.05 n)), q_min = max(4, floor(q_max/2)) */
     int32_t iterations;
-    int32_t repair_mask;       /* bit 0 greedy insertion, bit 1 regret-2 insertion */
+    int32_t repair_mask;       /* bit 0 greedy, bit 1 regret-2, bit 2 regret-3, bit 3 regret-m insertion
+                                  (Section 4.2.3; default 3).  Regret-k: options are the best insertion
+                                  per dropoff vehicle; regret = sum over the k best of (c_i - c_1),
+                                  a missing option counting 2^40 */
     int32_t team_blocks;       /* CTAs cooperating on one instance; 0 = chosen from n */
 } vrprpd_alns_params;
 

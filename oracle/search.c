@@ -333,14 +333,18 @@ static int repair(const oracle_inst* I, int op, int32_t* ops, int32_t* off, int*
         for (int t = 0; t < cnt; t++) {
             scan_matrix(I, ops, off, list[t], &bests[t], pv);
             if (!bests[t].ok) { free(pv); free(bests); free(regret); return -1; }
-            int64_t c1 = REGRET_INF, c2 = REGRET_INF;
-            for (int v = 0; v < m; v++) {
-                if (!pv[v].ok) continue;
-                int64_t cv = pv[v].dz;
-                if (cv < c1) { c2 = c1; c1 = cv; }
-                else if (cv < c2) c2 = cv;
-            }
-            regret[t] = c2 - c1;
+            /* regret-k (Section 4.2.3): the options are the best insertion per
+             * dropoff vehicle (REGRET_INF where a vehicle has none); regret =
+             * sum over the k best of (c_i - c_1), options past the m there are
+             * counting as REGRET_INF.  k = 2, 3 or m for operators 1, 2, 3. */
+            int64_t cs[64];
+            for (int v = 0; v < m; v++) cs[v] = pv[v].ok ? pv[v].dz : REGRET_INF;
+            for (int i = 1; i < m; i++)                                     /* insertion sort */
+                for (int j = i; j > 0 && cs[j] < cs[j - 1]; j--) { int64_t x = cs[j]; cs[j] = cs[j - 1]; cs[j - 1] = x; }
+            const int k = op == 1 ? 2 : (op == 2 ? 3 : m);
+            int64_t r = 0;
+            for (int i = 0; i < k; i++) r += (i < m ? cs[i] : REGRET_INF) - cs[0];
+            regret[t] = r;
         }
         int pick = 0;
         for (int t = 1; t < cnt; t++) {
@@ -350,7 +354,7 @@ static int repair(const oracle_inst* I, int op, int32_t* ops, int32_t* off, int*
                                   bests[pick].flat))
                     pick = t;
             } else {
-                /* regret-2: largest regret; ties -> smaller customer id */
+                /* regret-k: largest regret; ties -> smaller customer id */
                 if (regret[t] > regret[pick]) pick = t;
             }
         }
@@ -405,11 +409,13 @@ int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t
     if (qmin <= 0 || qmax <= 0) oracle_q_range(n, &qmin, &qmax);
     if (qmax > n) qmax = n;
     if (qmin > qmax) qmin = qmax;
-    /* operators: one destroy operator (random removal), repair 0 greedy, 1 regret-2 */
-    const int ND = 1, NR = 2;
-    double wd[1] = {1.0}, wr[2] = {1.0, 1.0};
-    int sd[1] = {0}, sr[2] = {0, 0}, ad[1] = {0}, ar[2] = {0, 0};
-    int en_d[1] = {1}, en_r[2] = {(P->repair_mask & 1) != 0, (P->repair_mask & 2) != 0};
+    /* operators: one destroy operator (random removal); repair 0 greedy,
+     * 1 regret-2, 2 regret-3, 3 regret-m, enabled by repair_mask bits */
+    const int ND = 1, NR = 4;
+    double wd[1] = {1.0}, wr[4] = {1.0, 1.0, 1.0, 1.0};
+    int sd[1] = {0}, sr[4] = {0, 0, 0, 0}, ad[1] = {0}, ar[4] = {0, 0, 0, 0};
+    int en_d[1] = {1}, en_r[4];
+    for (int i = 0; i < NR; i++) en_r[i] = (P->repair_mask >> i) & 1;
     double T = P->T0 * (double)z;                  /* line 3 */
     const double T_init = T;
     int stagnation = 0;
@@ -505,8 +511,7 @@ int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t
     stats->z_current = z;
     stats->T_final = T;
     stats->w_destroy[0] = wd[0];
-    stats->w_repair[0] = wr[0];
-    stats->w_repair[1] = wr[1];
+    for (int i = 0; i < NR; i++) stats->w_repair[i] = wr[i];
     free(S); free(So); free(Sb); free(Sbo); free(W); free(Wo); free(tmp); free(tmpo);
     free(perm); free(list); free(rem);
     return 0;

@@ -1592,9 +1592,24 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
             const long long cv = static_cast<long long>(static_cast<int>(static_cast<unsigned>(bvv >> 32) ^ 0x80000000u));
             if (cv < c1) { c2 = c1; c1 = cv; } else if (cv < c2) { c2 = cv; }
         }
+        // regret-k over the per-vehicle options: the sum over the k best of
+        // (c_i - c_1), options past the m there are counting as REGRET_INF;
+        // k = 2, 3 or m for repair operators 1, 2, 3
+        const int kreg = ctl->rj == 1 ? 2 : (ctl->rj == 2 ? 3 : m);
+        const long long cvl = (lane < m && rk != KEY_NONE)
+                                  ? static_cast<long long>(static_cast<int>(static_cast<unsigned>(rk >> 32) ^ 0x80000000u))
+                                  : REGRET_INF;
+        int rnk = 0;
+        for (int u = 0; u < m; ++u) {
+            const long long cu = __shfl_sync(FULL_MASK, cvl, u);
+            if (cu < cvl || (cu == cvl && u < lane)) ++rnk;
+        }
+        long long term = (lane < m && rnk < kreg) ? cvl - c1 : 0;
+        for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(FULL_MASK, term, o);
+        if (kreg > m) term += static_cast<long long>(kreg - m) * (REGRET_INF - c1);
         if (lane == 0) {
             bestv[ti] = bv;
-            regret[ti] = c2 - c1;
+            regret[ti] = ctl->rj == 1 ? c2 - c1 : term;
         }
     }
     __syncthreads();
@@ -1722,9 +1737,10 @@ __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
         const int it = ctl->iter;
         const unsigned long long base = static_cast<unsigned long long>(it) << 16;
         const int en_d[1] = {1};
-        const int en_r[2] = {(t.repair_mask & 1) != 0, (t.repair_mask & 2) != 0};
+        const int en_r[4] = {(t.repair_mask & 1) != 0, (t.repair_mask & 2) != 0, (t.repair_mask & 4) != 0,
+                             (t.repair_mask & 8) != 0};
         ctl->di = roulette(ctl->wd, en_d, 1, draw_unit(draw(t.key, base + 0)));
-        ctl->rj = roulette(ctl->wr, en_r, 2, draw_unit(draw(t.key, base + 1)));
+        ctl->rj = roulette(ctl->wr, en_r, 4, draw_unit(draw(t.key, base + 1)));
         ctl->ad[ctl->di] += 1;
         ctl->ar[ctl->rj] += 1;
         const int q = t.q_min + draw_below(draw(t.key, base + 2), t.q_max - t.q_min + 1);
@@ -1875,7 +1891,7 @@ __device__ void phase_end(const AlnsTeam& t, const Smem& s, bool first) {
                     ctl->sd[i] = 0;
                     ctl->ad[i] = 0;
                 }
-                for (int i = 0; i < 2; ++i) {
+                for (int i = 0; i < 4; ++i) {
                     const double ratio = ctl->ar[i] ? __ddiv_rn(static_cast<double>(ctl->sr[i]), static_cast<double>(ctl->ar[i])) : 0.0;
                     const double w = __dadd_rn(__dmul_rn(__dsub_rn(1.0, t.r), ctl->wr[i]), __dmul_rn(t.r, ratio));
                     ctl->wr[i] = w < t.w_min ? t.w_min : w;
@@ -2246,7 +2262,7 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     t.q_min = qmin;
     t.q_max = qmax;
     t.iterations = iters;
-    t.repair_mask = P->repair_mask & 3;
+    t.repair_mask = P->repair_mask & 15;
     VRP_CHECK(t.repair_mask != 0, VRPRPD_EINVAL, "repair_mask enables no repair operator");
     t.key = stream_key(seed, RNG_STREAM_ALNS);
     t.mode = mode;
@@ -2255,7 +2271,7 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     auto cleanup = [&]() { cudaFreeAsync(B.base, stream); };
     AlnsCtl ctl{};
     ctl.wd[0] = 1.0;
-    ctl.wr[0] = ctl.wr[1] = 1.0;
+    ctl.wr[0] = ctl.wr[1] = ctl.wr[2] = ctl.wr[3] = 1.0;
     if (dump) {
         ctl.nrem = 1;
         ctl.wsel = 0;
