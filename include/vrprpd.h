@@ -210,13 +210,28 @@ typedef struct {
                                   per dropoff vehicle; regret = sum over the k best of (c_i - c_1),
                                   a missing option counting 2^40 */
     int32_t team_blocks;       /* CTAs cooperating on one instance; 0 = chosen from n */
+    int32_t destroy_mask;      /* Section 4.2.2 destroy operators (default 1):
+                                  bit 0 random: q customers by partial Fisher-Yates;
+                                  bit 1 worst: removal gains z(S) - z(S - c), ranked largest first, q
+                                    roulette draws with weight r^-6 on the r-th remaining;
+                                  bit 2 Shaw: a random seed and the q-1 customers most related to it,
+                                    i.e. smallest 18 d + 6 |T_drop diff| + 5 [drop vehicles differ] +
+                                    5 [pickup vehicles differ] (2R with phi 9, chi 3, omega 5);
+                                  bit 3 cluster: a random centre and its q-1 nearest by travel time;
+                                  bit 4 route: a random non-empty route's customers, topped up to q_min
+                                    by the least travel time from a removed customer (with this bit on,
+                                    up to n customers await reinsertion, so the run's per-customer
+                                    device buffers take n rows instead of q_max);
+                                  bit 5 critical path: q random customers of the latest-returning route
+                                    (all if fewer), topped up to q_min by the latest pickup completion.
+                                  Ties go to the smaller customer id. */
 } vrprpd_alns_params;
 
 typedef struct {
     int32_t iterations, accepted, improved, new_best, reheats, rejected_infeasible;
     int32_t z_init, z_best, z_current;
     double T_final;
-    double w_destroy[4], w_repair[4];
+    double w_destroy[8], w_repair[4];  /* final operator weights (destroy 0-5 used) */
     double device_ms;          /* wall time of the device run */
     int64_t matrix_entries;    /* insertion-matrix entries scored by the O(1) tile formula */
     int64_t fallback_entries;  /* entries with a shortcut gap: exact from simulations with one stop

@@ -52,7 +52,7 @@ class AlnsParams(C.Structure):
                 ("r", C.c_double), ("stagnation", C.c_int32), ("tau", C.c_int32),
                 ("sigma1", C.c_int32), ("sigma2", C.c_int32), ("sigma3", C.c_int32),
                 ("w_min", C.c_double), ("q_min", C.c_int32), ("q_max", C.c_int32),
-                ("iterations", C.c_int32), ("repair_mask", C.c_int32)]
+                ("iterations", C.c_int32), ("repair_mask", C.c_int32), ("destroy_mask", C.c_int32)]
 
 
 class AlnsStats(C.Structure):
@@ -60,7 +60,7 @@ class AlnsStats(C.Structure):
                 ("new_best", C.c_int32), ("reheats", C.c_int32),
                 ("rejected_infeasible", C.c_int32), ("z_init", C.c_int32),
                 ("z_best", C.c_int32), ("z_current", C.c_int32), ("T_final", C.c_double),
-                ("w_destroy", C.c_double * 4), ("w_repair", C.c_double * 4)]
+                ("w_destroy", C.c_double * 8), ("w_repair", C.c_double * 4)]
 
 
 class BrkgaParams(C.Structure):
@@ -112,6 +112,8 @@ def lib():
                                           i32p]
             L.oracle_decode.argtypes = [C.POINTER(Inst), f32p, i32p, i32p, i32p, i32p, i64p]
             L.oracle_encode.argtypes = [C.POINTER(Inst), i32p, i32p, f32p]
+            L.oracle_destroy.argtypes = [C.POINTER(Inst), C.c_int32, i32p, i32p, C.c_int32, C.c_int32,
+                                         C.c_uint64, C.c_uint64, C.c_char_p]
             L.oracle_decode_l.argtypes = [C.POINTER(Inst), f32p, C.c_int32, i32p, i32p, i32p, i32p, i64p]
             L.oracle_encode_l.argtypes = [C.POINTER(Inst), i32p, i32p, C.c_int32, f32p]
             L.oracle_brkga_run.argtypes = [C.POINTER(Inst), C.POINTER(BrkgaParams), i32p, i32p,
@@ -244,9 +246,9 @@ def initial_solution(I, coords):
     return ops, off
 
 
-def alns_params(iterations, q_min=0, q_max=0, repair_mask=3):
+def alns_params(iterations, q_min=0, q_max=0, repair_mask=3, destroy_mask=1):
     return AlnsParams(0.30, 0.9998, 0.50, 0.1, 2000, 100, 33, 9, 13, 0.1, q_min, q_max,
-                      iterations, repair_mask)
+                      iterations, repair_mask, destroy_mask)
 
 
 def alns_run(I, init_ops, init_off, params, seed):
@@ -310,3 +312,18 @@ def brkga_run(I, params, warm_ops, warm_off, seed):
     if rc != 0:
         raise ValueError(f"oracle_brkga_run failed rc={rc}")
     return dict(keys=keys, trace=trace, best_ops=bo, best_off=bf, best_fitness=int(best[0]))
+
+
+DESTROY = {"random": 0, "worst": 1, "shaw": 2, "cluster": 3, "route": 4, "critical": 5}
+
+
+def destroy(I, op, ops, off, q, qmin, key, base):
+    """One destroy step on (ops, off); returns the boolean removal mask over customers 0..n."""
+    ops = np.ascontiguousarray(ops, dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int32)
+    rem = C.create_string_buffer(I.n + 1)
+    cnt = lib().oracle_destroy(C.byref(I.c), DESTROY.get(op, op), _p(ops), _p(off), q, qmin,
+                               C.c_uint64(key), C.c_uint64(base), rem)
+    mask = np.frombuffer(rem.raw, dtype=np.uint8).astype(bool)
+    assert int(mask.sum()) == cnt
+    return mask

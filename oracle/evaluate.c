@@ -46,6 +46,7 @@ int oracle_evaluate(const oracle_inst* I, const int32_t* ops, const int32_t* off
     if (off[0] != 0 || nops < 0 || nops > 2 * n || (!allow_partial && nops != 2 * n)) st |= OR_MALFORMED;
     for (int v = 0; v < m && !st; v++)
         if (off[v + 1] < off[v]) st |= OR_MALFORMED;
+    if (n < 0) return -1;
     char* seen = (char*)calloc((size_t)(2 * n + 2), 1);
     if (!st) {
         for (int k = 0; k < nops; k++) {

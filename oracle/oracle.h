@@ -69,14 +69,15 @@ typedef struct {
     double w_min;                         /* 0.1 */
     int32_t q_min, q_max;                 /* 0 = paper formula */
     int32_t iterations;
-    int32_t repair_mask;                  /* bit0 greedy, bit1 regret-2 */
+    int32_t repair_mask;                  /* bit0 greedy, bit1 regret-2, bit2 regret-3, bit3 regret-m */
+    int32_t destroy_mask;                 /* bit0 random, 1 worst, 2 Shaw, 3 cluster, 4 route, 5 critical path */
 } oracle_alns_params;
 
 typedef struct {
     int32_t iterations, accepted, improved, new_best, reheats, rejected_infeasible;
     int32_t z_init, z_best, z_current;
     double T_final;
-    double w_destroy[4], w_repair[4];
+    double w_destroy[8], w_repair[4];
 } oracle_alns_stats;
 
 void oracle_q_range(int32_t n, int32_t* q_min, int32_t* q_max);
@@ -90,6 +91,13 @@ int oracle_insertion_matrix(const oracle_inst* I, const int32_t* ops, const int3
                             int32_t c, int32_t* out, int32_t* travel_out, uint32_t* status_out);
 
 int oracle_initial_solution(const oracle_inst* I, const int32_t* coords, int32_t* ops, int32_t* off);
+
+/* One destroy step (Section 4.2.2) on solution (S, So): operator di (0 random,
+ * 1 worst, 2 Shaw, 3 cluster, 4 route, 5 critical path), removal size q,
+ * top-up bound qmin, draws from (key, base + ...).  Marks rem[1..n]; returns
+ * how many customers it removed. */
+int oracle_destroy(const oracle_inst* I, int32_t di, const int32_t* S, const int32_t* So, int32_t q,
+                   int32_t qmin, uint64_t key, uint64_t base, char* rem);
 
 int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t* init_off,
                     const oracle_alns_params* P, uint64_t seed,

@@ -383,6 +383,187 @@ static int roulette(const double* w, const int* enabled, int k, double u) {
     return last;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Destroy operators (Section 4.2.2).  Each marks the customers to remove in   */
+/* rem[] and returns how many.  Draws: operator-specific picks at counter      */
+/* base + 4, sequential draws k at base + 16 + k.                              */
+/* ------------------------------------------------------------------------ */
+enum { D_RANDOM = 0, D_WORST = 1, D_SHAW = 2, D_CLUSTER = 3, D_ROUTE = 4, D_CRITICAL = 5, ND_OPS = 6 };
+
+typedef struct {
+    int64_t key;
+    int c;
+} rank_t;
+static int rank_cmp(const void* pa, const void* pb) {
+    const rank_t *a = pa, *b = pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->c - b->c;                             /* ties: the smaller customer id first */
+}
+
+/* facts of the current solution: departure per op code (drop: arrival), the
+ * vehicles of each customer's dropoff and pickup, and each route's return time */
+static void solution_facts(const oracle_inst* I, const int32_t* S, const int32_t* So, int64_t* times,
+                           int* vd, int* vp, int64_t* ret) {
+    int32_t z;
+    uint32_t st;
+    oracle_evaluate(I, S, So, 0, &z, &st, times);
+    for (int v = 0; v < I->m; v++) {
+        ret[v] = 0;
+        for (int k = So[v]; k < So[v + 1]; k++) {
+            int o = S[k];
+            if (o & 1) vp[o >> 1] = v; else vd[o >> 1] = v;
+        }
+        if (So[v + 1] > So[v]) {
+            int o = S[So[v + 1] - 1];
+            ret[v] = times[o] + Dd(I, o >> 1, 0);
+        }
+    }
+}
+
+int oracle_destroy(const oracle_inst* I, int32_t di, const int32_t* S, const int32_t* So, int32_t q,
+                   int32_t qmin, uint64_t key, uint64_t base, char* rem) {
+    const int n = I->n, m = I->m, two_n = 2 * n;
+    memset(rem, 0, (size_t)n + 1);
+    int cnt = 0;
+    if (di == D_RANDOM) {
+        /* partial Fisher-Yates over customers 1..n */
+        int* perm = malloc(sizeof(int) * (n + 1));
+        for (int k = 0; k < n; k++) perm[k] = k + 1;
+        for (int k = 0; k < q; k++) {
+            int jj = k + rng_below(oracle_rng(key, base + 16 + (uint64_t)k), n - k);
+            int t = perm[k]; perm[k] = perm[jj]; perm[jj] = t;
+            rem[perm[k]] = 1;
+        }
+        free(perm);
+        return q;
+    }
+    int64_t* times = malloc(sizeof(int64_t) * (two_n + 2));
+    int* vd = calloc((size_t)n + 1, sizeof(int));
+    int* vp = calloc((size_t)n + 1, sizeof(int));
+    int64_t* ret = calloc((size_t)m, sizeof(int64_t));
+    rank_t* rk = malloc(sizeof(rank_t) * (n + 1));
+    solution_facts(I, S, So, times, vd, vp, ret);
+    if (di == D_WORST) {
+        /* removal gain z(S) - z(S - c); customers ranked by gain, largest
+         * first; q roulette draws over the remaining ranked list with weight
+         * r^-6 for the r-th remaining customer (power p = 6) */
+        int32_t z, zc;
+        uint32_t st;
+        oracle_evaluate(I, S, So, 0, &z, &st, NULL);
+        int32_t* T = malloc(sizeof(int32_t) * (two_n + 2));
+        int32_t* To = malloc(sizeof(int32_t) * (m + 1));
+        char* one = calloc((size_t)n + 1, 1);
+        for (int c = 1; c <= n; c++) {
+            one[c] = 1;
+            remove_customers(m, S, So, one, T, To);
+            one[c] = 0;
+            oracle_evaluate(I, T, To, 1, &zc, &st, NULL);
+            rk[c - 1].key = -((int64_t)z - (int64_t)zc);
+            rk[c - 1].c = c;
+        }
+        free(T); free(To); free(one);
+        qsort(rk, (size_t)n, sizeof(rank_t), rank_cmp);
+        double* P = malloc(sizeof(double) * (n + 1));
+        double acc = 0.0;
+        for (int r = 1; r <= n; r++) {
+            double x = (double)r, x2 = x * x;
+            acc += 1.0 / (x2 * x2 * x2);
+            P[r] = acc;
+        }
+        for (int k = 0; k < q; k++) {
+            const int R = n - k;
+            const double target = rng_unit(oracle_rng(key, base + 16 + (uint64_t)k)) * P[R];
+            int r = 1;
+            while (r < R && !(P[r] > target)) r++;
+            /* the r-th customer of the ranked list not removed yet */
+            int seen = 0;
+            for (int i = 0; i < n; i++) {
+                if (rem[rk[i].c]) continue;
+                if (++seen == r) { rem[rk[i].c] = 1; break; }
+            }
+        }
+        free(P);
+        cnt = q;
+    } else if (di == D_SHAW || di == D_CLUSTER) {
+        /* a random seed customer and the q - 1 customers closest to it: by
+         * 2R = 18 d + 6 |T_drop diff| + 5 [dropoff vehicles differ] + 5 [pickup
+         * vehicles differ] (Shaw, phi 9, chi 3, omega 5), or by travel time
+         * alone (cluster); ties to the smaller customer id */
+        const int sd = 1 + rng_below(oracle_rng(key, base + 4), n);
+        int w = 0;
+        for (int c = 1; c <= n; c++) {
+            if (c == sd) continue;
+            int64_t k2 = Dd(I, sd, c);
+            if (di == D_SHAW) {
+                int64_t dt = times[2 * sd] - times[2 * c];
+                if (dt < 0) dt = -dt;
+                k2 = 18 * k2 + 6 * dt + 5 * (vd[sd] != vd[c]) + 5 * (vp[sd] != vp[c]);
+            }
+            rk[w].key = k2;
+            rk[w].c = c;
+            w++;
+        }
+        qsort(rk, (size_t)w, sizeof(rank_t), rank_cmp);
+        rem[sd] = 1;
+        for (int k = 0; k + 1 < q && k < w; k++) rem[rk[k].c] = 1;
+        cnt = q < n ? q : n;
+    } else if (di == D_ROUTE || di == D_CRITICAL) {
+        int vsel = 0;
+        if (di == D_ROUTE) {
+            /* the k-th non-empty route */
+            int K = 0;
+            for (int v = 0; v < m; v++) K += So[v + 1] > So[v];
+            int kk = rng_below(oracle_rng(key, base + 4), K);
+            for (int v = 0; v < m; v++)
+                if (So[v + 1] > So[v] && kk-- == 0) { vsel = v; break; }
+            for (int k = So[vsel]; k < So[vsel + 1]; k++)
+                if (!rem[S[k] >> 1]) { rem[S[k] >> 1] = 1; cnt++; }
+        } else {
+            /* the bottleneck route (latest return, the lower index on ties):
+             * q of its customers, or all if fewer, by partial Fisher-Yates in
+             * customer order */
+            for (int v = 1; v < m; v++)
+                if (ret[v] > ret[vsel]) vsel = v;
+            int* L = malloc(sizeof(int) * (n + 1));
+            int nl = 0;
+            for (int c = 1; c <= n; c++)
+                if (vd[c] == vsel || vp[c] == vsel) L[nl++] = c;
+            int take = q < nl ? q : nl;
+            for (int k = 0; k < take; k++) {
+                int jj = k + rng_below(oracle_rng(key, base + 16 + (uint64_t)k), nl - k);
+                int t = L[k]; L[k] = L[jj]; L[jj] = t;
+                rem[L[k]] = 1;
+            }
+            cnt = take;
+            free(L);
+        }
+        if (cnt < qmin) {
+            /* top up from the other routes: route removal by the least travel
+             * time from a removed customer, critical path by the latest pickup
+             * completion; ties to the smaller customer id */
+            int w = 0;
+            for (int c = 1; c <= n; c++) {
+                if (rem[c]) continue;
+                int64_t k2;
+                if (di == D_ROUTE) {
+                    k2 = INT64_MAX;
+                    for (int r = 1; r <= n; r++)
+                        if (rem[r] && Dd(I, r, c) < k2) k2 = Dd(I, r, c);
+                } else {
+                    k2 = -times[2 * c + 1];
+                }
+                rk[w].key = k2;
+                rk[w].c = c;
+                w++;
+            }
+            qsort(rk, (size_t)w, sizeof(rank_t), rank_cmp);
+            for (int k = 0; k < w && cnt < qmin; k++) { rem[rk[k].c] = 1; cnt++; }
+        }
+    }
+    free(times); free(vd); free(vp); free(ret); free(rk);
+    return cnt;
+}
+
 int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t* init_off,
                     const oracle_alns_params* P, uint64_t seed, int32_t* best_ops, int32_t* best_off,
                     int32_t* cur_ops_out, int32_t* cur_off_out, oracle_alns_stats* stats,
@@ -409,12 +590,14 @@ int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t
     if (qmin <= 0 || qmax <= 0) oracle_q_range(n, &qmin, &qmax);
     if (qmax > n) qmax = n;
     if (qmin > qmax) qmin = qmax;
-    /* operators: one destroy operator (random removal); repair 0 greedy,
-     * 1 regret-2, 2 regret-3, 3 regret-m, enabled by repair_mask bits */
-    const int ND = 1, NR = 4;
-    double wd[1] = {1.0}, wr[4] = {1.0, 1.0, 1.0, 1.0};
-    int sd[1] = {0}, sr[4] = {0, 0, 0, 0}, ad[1] = {0}, ar[4] = {0, 0, 0, 0};
-    int en_d[1] = {1}, en_r[4];
+    /* operators: destroy 0 random, 1 worst, 2 Shaw, 3 cluster, 4 route, 5
+     * critical path (destroy_mask bits); repair 0 greedy, 1 regret-2, 2
+     * regret-3, 3 regret-m (repair_mask bits) */
+    const int ND = ND_OPS, NR = 4;
+    double wd[ND_OPS], wr[4] = {1.0, 1.0, 1.0, 1.0};
+    int sd[ND_OPS], sr[4] = {0, 0, 0, 0}, ad[ND_OPS], ar[4] = {0, 0, 0, 0};
+    int en_d[ND_OPS], en_r[4];
+    for (int i = 0; i < ND; i++) { wd[i] = 1.0; sd[i] = 0; ad[i] = 0; en_d[i] = (P->destroy_mask >> i) & 1; }
     for (int i = 0; i < NR; i++) en_r[i] = (P->repair_mask >> i) & 1;
     double T = P->T0 * (double)z;                  /* line 3 */
     const double T_init = T;
@@ -428,14 +611,7 @@ int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t
         ad[di]++;
         ar[rj]++;                                                              /* line 10 */
         int q = qmin + rng_below(oracle_rng(key, base + 2), qmax - qmin + 1);
-        /* random removal: partial Fisher-Yates over customers 1..n */
-        for (int k = 0; k < n; k++) perm[k] = k + 1;
-        for (int k = 0; k < q; k++) {
-            int jj = k + rng_below(oracle_rng(key, base + 16 + (uint64_t)k), n - k);
-            int t = perm[k]; perm[k] = perm[jj]; perm[jj] = t;
-        }
-        memset(rem, 0, (size_t)n + 1);
-        for (int k = 0; k < q; k++) rem[perm[k]] = 1;
+        oracle_destroy(I, di, S, So, q, qmin, key, base, rem);                   /* line 11 */
         remove_customers(m, S, So, rem, W, Wo);
         int cnt = 0;
         for (int c = 1; c <= n; c++)
@@ -510,7 +686,7 @@ int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t
     stats->z_best = zb;
     stats->z_current = z;
     stats->T_final = T;
-    stats->w_destroy[0] = wd[0];
+    for (int i = 0; i < ND; i++) stats->w_destroy[i] = wd[i];
     for (int i = 0; i < NR; i++) stats->w_repair[i] = wr[i];
     free(S); free(So); free(Sb); free(Sbo); free(W); free(Wo); free(tmp); free(tmpo);
     free(perm); free(list); free(rem);

@@ -11,14 +11,15 @@ class AlnsParams(C.Structure):
                 ("stagnation", C.c_int32), ("tau", C.c_int32), ("sigma1", C.c_int32),
                 ("sigma2", C.c_int32), ("sigma3", C.c_int32), ("w_min", C.c_double),
                 ("q_min", C.c_int32), ("q_max", C.c_int32), ("iterations", C.c_int32),
-                ("repair_mask", C.c_int32), ("team_blocks", C.c_int32)]
+                ("repair_mask", C.c_int32), ("team_blocks", C.c_int32),
+                ("destroy_mask", C.c_int32)]
 
 
 class AlnsStats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("accepted", C.c_int32), ("improved", C.c_int32),
                 ("new_best", C.c_int32), ("reheats", C.c_int32), ("rejected_infeasible", C.c_int32),
                 ("z_init", C.c_int32), ("z_best", C.c_int32), ("z_current", C.c_int32),
-                ("T_final", C.c_double), ("w_destroy", C.c_double * 4), ("w_repair", C.c_double * 4),
+                ("T_final", C.c_double), ("w_destroy", C.c_double * 8), ("w_repair", C.c_double * 4),
                 ("device_ms", C.c_double), ("matrix_entries", C.c_int64),
                 ("fallback_entries", C.c_int64), ("team_blocks", C.c_int32), ("phase_ms", C.c_double * 6),
                 ("incremental_steps", C.c_int64), ("full_steps", C.c_int64)]

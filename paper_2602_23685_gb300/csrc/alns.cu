@@ -62,8 +62,8 @@ struct AlnsCtl {
     int pick_t, pick_row, pick_col;
     unsigned bar_count, bar_gen;
     double T, T_init;
-    double wd[4], wr[4];
-    int sd[4], sr[4], ad[4], ar[4];
+    double wd[8], wr[4];
+    int sd[8], sr[4], ad[8], ar[4];
     int accepted, improved, new_best, reheats, rejected;
     int z_init;
     // set by the selection when the insertion it applied used no shortcut gap:
@@ -86,6 +86,7 @@ struct AlnsTeam {
     // parameters
     double T0, alpha, reheat, r, w_min;
     int stagnation_limit, tau, sigma1, sigma2, sigma3, q_min, q_max, iterations, repair_mask;
+    int destroy_mask;        // bit 0 random, 1 worst, 2 Shaw, 3 cluster, 4 route, 5 critical path
     unsigned long long key;  // RNG stream key
     int mode;                // 0 = search, 1 = one-customer matrix dump
     int dump_c;
@@ -114,6 +115,7 @@ struct AlnsTeam {
     int scw_stride;
     int* scpair;               // [SC_CAP][SC_CAP]: makespan with both stops in two shortcut gaps of one customer
     int* trace;
+    int* gains;                // [n+1]: removal gain z(cur) - z(cur - c), worst removal
     int* dump_delta;
     int* dump_travel;
 };
@@ -139,7 +141,8 @@ constexpr int CB = 8;             // customers per matrix batch
 // tile's batch vectors, row minima and pair list, a shortcut item's
 // two walk buffers with its departure and tail arrays, the selection's
 // per-customer results (5 words per removed customer) and the removal
-// permutation (n words); no phase needs two of these at once.
+// permutation (n words) or a structured destroy's sort keys and per-customer
+// facts; no phase needs two of these at once.
 __host__ __device__ inline size_t rdy_words(int n) {
     const size_t rw = static_cast<size_t>(((n + 1) + 3) & ~3);
     const size_t walks = static_cast<size_t>(ALNS_WARPS) * rw;
@@ -147,12 +150,16 @@ __host__ __device__ inline size_t rdy_words(int n) {
     // tile: column and row vectors, adjacent-pair vectors and row minima per
     // customer of a batch, then the compacted pair list (int2 per pair)
     const size_t batch = static_cast<size_t>(CB) * (4 * TC + 8 * TR) + 2 * static_cast<size_t>(TR) * TC;
-    const size_t q = static_cast<size_t>(n < 1024 ? n : 1024);
-    const size_t sel = 5 * q + 8;
+    const size_t sel = 5 * static_cast<size_t>(n) + 8;
     size_t w = walks > batch ? walks : batch;
     w = w > fb ? w : fb;
     w = w > sel ? w : sel;
     w = w > static_cast<size_t>(n) + 4 ? w : static_cast<size_t>(n) + 4;
+    // structured destroy: u64 sort keys (a power of two >= n) and five
+    // per-customer arrays
+    size_t P = 1;
+    while (P < static_cast<size_t>(n)) P <<= 1;
+    w = w > 2 * P + 5 * rw ? w : 2 * P + 5 * rw;
     return (w + 3) & ~static_cast<size_t>(3);
 }
 
@@ -264,10 +271,7 @@ __device__ bool team_wait(AlnsCtl* ctl, int team_blocks, unsigned& gen) {
 // ---------------------------------------------------------------------------
 // stage W into shared memory: packed (travel-in << 12 | op)
 // ---------------------------------------------------------------------------
-__device__ void stage_W(const AlnsTeam& t, const Smem& s) {
-    const AlnsCtl* ctl = t.ctl;
-    const int* W = t.W_ops[ctl->wsel];
-    const int* Wo = t.W_off[ctl->wsel];
+__device__ void stage_ops(const AlnsTeam& t, const Smem& s, const int* W, const int* Wo) {
     const int m = t.m;
     for (int i = threadIdx.x; i <= m; i += blockDim.x) s.sWoff[i] = Wo[i];
     __syncthreads();
@@ -284,6 +288,10 @@ __device__ void stage_W(const AlnsTeam& t, const Smem& s) {
         s.sW[k] = (Dx(t, s, prev, o >> 1) << PACK_SHIFT) | o;
     }
     __syncthreads();
+}
+
+__device__ void stage_W(const AlnsTeam& t, const Smem& s) {
+    stage_ops(t, s, t.W_ops[t.ctl->wsel], t.W_off[t.ctl->wsel]);
 }
 
 // ---------------------------------------------------------------------------
@@ -885,6 +893,65 @@ __device__ void phase_update(const AlnsTeam& t, const Smem& s, int rank, int tea
             }
             Mn[static_cast<long long>(r0 + rr) * Nn + k] = val;
         }
+    }
+}
+
+// The staged solution without customer cx: makespan (INT32_MAX on a cycle).
+// The stop after a skipped one is reached from the last kept stop (or the
+// depot); a route left empty returns at 0.  One stop per lane per step.
+__device__ int walk_skip(const AlnsTeam& t, const Smem& s, int* rdy_, int cx) {
+    const int lane = threadIdx.x & 31, m = t.m, n = t.n;
+    const int* __restrict__ sW = s.sW;
+    const int* __restrict__ spp = s.sp;
+    volatile int* rdy = rdy_;
+    for (int c = lane; c <= n; c += 32) rdy[c] = UNRES;
+    __syncwarp();
+    const bool mine = lane < m;
+    int pos = mine ? s.sWoff[lane] : 0;
+    const int end = mine ? s.sWoff[lane + 1] : 0;
+    int dep = 0, loc = 0;
+    bool skipped = false, any = false, cyc = false;
+    bool walking = mine && pos < end;
+    bool alive = __any_sync(FULL_MASK, walking);
+    while (alive) {
+        const int w = walking ? sW[pos] : 0;
+        const int c = (w & PACK_MASK) >> 1;
+        const bool pick = (w & 1) != 0, skip = walking && c == cx;
+        const int rv = (walking && pick && !skip) ? rdy[c] : 0;
+        const bool go = walking && (skip || !pick || rv != UNRES);
+        if (go && !skip) {
+            const int arr = dep + (skipped ? Dx(t, s, loc, c) : (w >> PACK_SHIFT));
+            if (pick) dep = max(arr, rv);
+            else { dep = arr; rdy[c] = arr + spp[c]; }
+            loc = c;
+            any = true;
+        }
+        if (go) { skipped = skip; ++pos; }
+        const bool more = pos < end;
+        const unsigned prog = __ballot_sync(FULL_MASK, go);
+        if (walking && more && prog == 0u) cyc = true;
+        walking = walking && more && prog != 0u;
+        __syncwarp();
+        alive = prog != 0u && __any_sync(FULL_MASK, walking);
+    }
+    int ret = (mine && any && !cyc) ? dep + Dx(t, s, loc, 0) : 0;
+    for (int o = 16; o > 0; o >>= 1) ret = max(ret, __shfl_xor_sync(FULL_MASK, ret, o));
+    const unsigned anycyc = __ballot_sync(FULL_MASK, cyc);
+    return anycyc ? 0x7fffffff : ret;
+}
+
+// Worst removal's gains (Section 4.2.2): every CTA stages the current
+// solution, then one warp per customer c walks it without c; gains[c] =
+// z(cur) - z(cur - c).
+__device__ void phase_gains(const AlnsTeam& t, const Smem& s, int rank, int team_blocks) {
+    stage_ops(t, s, t.cur_ops, t.cur_off);
+    const int warp = threadIdx.x >> 5;
+    const int team_warps = team_blocks * ALNS_WARPS;
+    int* rdy = s.rdy + warp * (((t.n + 1) + 3) & ~3);
+    const int z = t.ctl->z_cur;
+    for (int c = 1 + rank * ALNS_WARPS + warp; c <= t.n; c += team_warps) {
+        const int zc = walk_skip(t, s, rdy, c);
+        if ((threadIdx.x & 31) == 0) t.gains[c] = z - zc;
     }
 }
 
@@ -1725,7 +1792,234 @@ __device__ int roulette(const double* w, const int* en, int k, double u) {
     return last;
 }
 
-// Rank 0: operator choice, q, random removal (partial Fisher-Yates), W = cur - removed.
+// Operator choice and removal size for iteration it (Algorithm 1, roulette
+// wheels over the enabled operators); thread 0 of rank 0, right after the
+// weight update of the previous iteration.
+enum { D_RANDOM = 0, D_WORST = 1, D_SHAW = 2, D_CLUSTER = 3, D_ROUTE = 4, D_CRITICAL = 5, ND_OPS = 6 };
+
+__device__ void pick_operators(const AlnsTeam& t, int it) {
+    AlnsCtl* ctl = t.ctl;
+    const unsigned long long base = static_cast<unsigned long long>(it) << 16;
+    int en_d[ND_OPS];
+    for (int i = 0; i < ND_OPS; ++i) en_d[i] = (t.destroy_mask >> i) & 1;
+    const int en_r[4] = {(t.repair_mask & 1) != 0, (t.repair_mask & 2) != 0, (t.repair_mask & 4) != 0,
+                         (t.repair_mask & 8) != 0};
+    ctl->di = roulette(ctl->wd, en_d, ND_OPS, draw_unit(draw(t.key, base + 0)));
+    ctl->rj = roulette(ctl->wr, en_r, 4, draw_unit(draw(t.key, base + 1)));
+    ctl->ad[ctl->di] += 1;
+    ctl->ar[ctl->rj] += 1;
+    ctl->q = t.q_min + draw_below(draw(t.key, base + 2), t.q_max - t.q_min + 1);
+}
+
+// Ascending block-wide bitonic sort of P (a power of two) keys in shared memory.
+__device__ void block_sort(unsigned long long* a, int P) {
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const unsigned long long x = a[lo], y = a[hi];
+                if ((x > y) == asc) { a[lo] = y; a[hi] = x; }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// The structured destroy operators (Section 4.2.2), rank 0's block: marks
+// s.flags[c] and leaves the count in ctl->q.  Rankings sort (key << 12 | c),
+// so ties go to the smaller customer id.  Draws: the operator's pick at
+// counter base + 4, sequential draws k at base + 16 + k.
+__device__ void select_structured(const AlnsTeam& t, const Smem& s) {
+    AlnsCtl* ctl = t.ctl;
+    const int n = t.n, m = t.m, di = ctl->di, q = ctl->q, qmin = t.q_min;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const unsigned long long base = static_cast<unsigned long long>(ctl->iter) << 16;
+    int P = 1;
+    while (P < n) P <<= 1;
+    const int rw = ((n + 1) + 3) & ~3;
+    unsigned long long* keys = reinterpret_cast<unsigned long long*>(s.rdy);      // [P]
+    int* vd = s.rdy + 2 * P;                   // [n+1] vehicle of the dropoff
+    int* vp = vd + rw;                         // [n+1] vehicle of the pickup
+    int* tdr = vp + rw;                        // [n+1] dropoff time
+    int* tpk = tdr + rw;                       // [n+1] pickup completion
+    int* lst = tpk + rw;                       // [n+1] customer list
+    int* sh = s.misc + 32;                     // scalars
+    // facts of the current solution
+    stage_ops(t, s, t.cur_ops, t.cur_off);
+    const bool timed = di == D_SHAW || di == D_CRITICAL;
+    if (timed && warp == 0) {
+        int z;
+        unsigned st;
+        walk_depot(t, s, s.rdy, true, &z, &st);
+    }
+    __syncthreads();
+    const int N = s.sWoff[m];
+    for (int k = tid; k < N; k += blockDim.x) {
+        int lo = 0, hi = m;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s.sWoff[mid] <= k) lo = mid; else hi = mid;
+        }
+        const int o = s.sW[k] & PACK_MASK, c = o >> 1;
+        if (o & 1) { vp[c] = lo; if (timed) tpk[c] = t.H[k]; }
+        else { vd[c] = lo; if (timed) tdr[c] = t.H[k]; }
+    }
+    __syncthreads();
+    auto count_flags = [&]() {
+        // every thread gets the number of marked customers
+        __syncthreads();
+        if (warp == 0) {
+            int w = 0;
+            for (int c0 = 1; c0 <= n; c0 += 32) w += __popc(__ballot_sync(FULL_MASK, c0 + lane <= n && s.flags[c0 + lane]));
+            if (lane == 0) sh[1] = w;
+        }
+        __syncthreads();
+        return sh[1];
+    };
+    auto take_sorted = [&](int need) {
+        // mark the first `need` customers of the sorted keys (unmarked ones only carry keys)
+        for (int i = tid; i < P && i < need; i += blockDim.x)
+            if (keys[i] != KEY_NONE) s.flags[static_cast<int>(keys[i] & 0xFFF)] = 1;
+    };
+    if (di == D_WORST) {
+        // removal gains from the team phase, largest first; q roulette draws
+        // over the remaining ranked list with weight r^-6 on the r-th
+        double* pw = reinterpret_cast<double*>(keys + P);                         // [n+1] prefix weights
+        for (int i = tid; i < P; i += blockDim.x)
+            keys[i] = i < n ? ((static_cast<unsigned long long>((1ll << 30) - t.gains[i + 1]) << 12) |
+                               static_cast<unsigned long long>(i + 1))
+                            : KEY_NONE;
+        block_sort(keys, P);
+        if (tid == 0) {
+            double acc = 0.0;
+            for (int r = 1; r <= n; ++r) {
+                const double x = static_cast<double>(r), x2 = __dmul_rn(x, x);
+                acc = __dadd_rn(acc, __ddiv_rn(1.0, __dmul_rn(__dmul_rn(x2, x2), x2)));
+                pw[r] = acc;
+            }
+            for (int k = 0; k < q; ++k) {
+                const int R = n - k;
+                const double target = __dmul_rn(draw_unit(draw(t.key, base + 16 + static_cast<unsigned long long>(k))), pw[R]);
+                int r = 1;
+                while (r < R && !(pw[r] > target)) ++r;
+                int seen = 0;
+                for (int i = 0; i < n; ++i) {
+                    const int c = static_cast<int>(keys[i] & 0xFFF);
+                    if (s.flags[c]) continue;
+                    if (++seen == r) { s.flags[c] = 1; break; }
+                }
+            }
+        }
+    } else if (di == D_SHAW || di == D_CLUSTER) {
+        // a random seed and the q-1 customers nearest to it (Shaw: by the
+        // relatedness measure, doubled to stay integral)
+        if (tid == 0) sh[0] = 1 + draw_below(draw(t.key, base + 4), n);
+        __syncthreads();
+        const int sd = sh[0];
+        for (int i = tid; i < P; i += blockDim.x) {
+            const int c = i + 1;
+            unsigned long long kk = KEY_NONE;
+            if (c <= n && c != sd) {
+                long long k2 = Dx(t, s, sd, c);
+                if (di == D_SHAW) {
+                    long long dt = static_cast<long long>(tdr[sd]) - tdr[c];
+                    dt = dt < 0 ? -dt : dt;
+                    k2 = 18 * k2 + 6 * dt + 5 * (vd[sd] != vd[c]) + 5 * (vp[sd] != vp[c]);
+                }
+                kk = (static_cast<unsigned long long>(k2) << 12) | static_cast<unsigned long long>(c);
+            }
+            keys[i] = kk;
+        }
+        block_sort(keys, P);
+        if (tid == 0) s.flags[sd] = 1;
+        take_sorted(q - 1);
+    } else {
+        // a random non-empty route, or the bottleneck route's customers
+        if (tid == 0) {
+            if (di == D_ROUTE) {
+                int K = 0;
+                for (int v = 0; v < m; ++v) K += s.sWoff[v + 1] > s.sWoff[v] ? 1 : 0;
+                int kk = draw_below(draw(t.key, base + 4), K);
+                int vsel = 0;
+                for (int v = 0; v < m; ++v)
+                    if (s.sWoff[v + 1] > s.sWoff[v] && kk-- == 0) { vsel = v; break; }
+                sh[0] = vsel;
+            } else {
+                // latest return, the lower index on ties; q of its customers by
+                // partial Fisher-Yates in customer order (all if fewer)
+                long long best = -1;
+                int vb = 0;
+                for (int v = 0; v < m; ++v) {
+                    long long rv = 0;
+                    if (s.sWoff[v + 1] > s.sWoff[v]) {
+                        const int last = s.sWoff[v + 1] - 1;
+                        rv = static_cast<long long>(t.H[last]) + Dx(t, s, (s.sW[last] & PACK_MASK) >> 1, 0);
+                    }
+                    if (rv > best) { best = rv; vb = v; }
+                }
+                int nl = 0;
+                for (int c = 1; c <= n; ++c)
+                    if (vd[c] == vb || vp[c] == vb) lst[nl++] = c;
+                const int take = q < nl ? q : nl;
+                for (int k = 0; k < take; ++k) {
+                    const int jj = k + draw_below(draw(t.key, base + 16 + static_cast<unsigned long long>(k)), nl - k);
+                    const int tmp = lst[k];
+                    lst[k] = lst[jj];
+                    lst[jj] = tmp;
+                    s.flags[lst[k]] = 1;
+                }
+                sh[0] = -1;
+            }
+        }
+        __syncthreads();
+        if (di == D_ROUTE) {
+            const int vsel = sh[0];
+            for (int k = s.sWoff[vsel] + tid; k < s.sWoff[vsel + 1]; k += blockDim.x)
+                s.flags[(s.sW[k] & PACK_MASK) >> 1] = 1;
+        }
+        const int cnt = count_flags();
+        if (cnt < qmin) {
+            // top up: route removal by the least travel time from a removed
+            // customer, critical path by the latest pickup completion
+            if (di == D_ROUTE && warp == 0) {
+                int w = 0;
+                for (int c0 = 1; c0 <= n; c0 += 32) {
+                    const int c = c0 + lane;
+                    const bool r = c <= n && s.flags[c];
+                    const unsigned bal = __ballot_sync(FULL_MASK, r);
+                    if (r) lst[w + __popc(bal & ((1u << lane) - 1u))] = c;
+                    w += __popc(bal);
+                }
+            }
+            __syncthreads();
+            for (int i = tid; i < P; i += blockDim.x) {
+                const int c = i + 1;
+                unsigned long long kk = KEY_NONE;
+                if (c <= n && !s.flags[c]) {
+                    long long k2;
+                    if (di == D_ROUTE) {
+                        k2 = 0x7fffffffll;
+                        for (int j = 0; j < cnt; ++j) k2 = min(k2, static_cast<long long>(Dx(t, s, lst[j], c)));
+                    } else {
+                        k2 = (1ll << 30) - tpk[c];
+                    }
+                    kk = (static_cast<unsigned long long>(k2) << 12) | static_cast<unsigned long long>(c);
+                }
+                keys[i] = kk;
+            }
+            block_sort(keys, P);
+            take_sorted(qmin - cnt);
+        }
+    }
+    const int total = count_flags();
+    if (tid == 0) ctl->q = total;
+    __syncthreads();
+}
+
+// Rank 0: the destroy step (operator and q drawn at the end of the previous
+// iteration), W = cur - removed.
 __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
     AlnsCtl* ctl = t.ctl;
     const int n = t.n, m = t.m, two_n = 2 * n;
@@ -1733,18 +2027,10 @@ __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
     for (int k = threadIdx.x; k < n; k += blockDim.x) perm[k] = k + 1;
     for (int c = threadIdx.x; c <= n; c += blockDim.x) s.flags[c] = 0;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && ctl->di == D_RANDOM) {
         const int it = ctl->iter;
         const unsigned long long base = static_cast<unsigned long long>(it) << 16;
-        const int en_d[1] = {1};
-        const int en_r[4] = {(t.repair_mask & 1) != 0, (t.repair_mask & 2) != 0, (t.repair_mask & 4) != 0,
-                             (t.repair_mask & 8) != 0};
-        ctl->di = roulette(ctl->wd, en_d, 1, draw_unit(draw(t.key, base + 0)));
-        ctl->rj = roulette(ctl->wr, en_r, 4, draw_unit(draw(t.key, base + 1)));
-        ctl->ad[ctl->di] += 1;
-        ctl->ar[ctl->rj] += 1;
-        const int q = t.q_min + draw_below(draw(t.key, base + 2), t.q_max - t.q_min + 1);
-        ctl->q = q;
+        const int q = ctl->q;
         for (int k = 0; k < q; ++k) {
             const int jj = k + draw_below(draw(t.key, base + 16 + static_cast<unsigned long long>(k)), n - k);
             const int tmp = perm[k];
@@ -1752,6 +2038,10 @@ __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
             perm[jj] = tmp;
             s.flags[perm[k]] = 1;
         }
+    }
+    __syncthreads();
+    if (ctl->di != D_RANDOM) select_structured(t, s);
+    if (threadIdx.x == 0) {
         ctl->repair_fail = 0;
         ctl->n_short = 0;
         ctl->work_counter = 0;
@@ -1884,7 +2174,7 @@ __device__ void phase_end(const AlnsTeam& t, const Smem& s, bool first) {
                 ctl->reheats += 1;
             }
             if (it % t.tau == 0) {
-                for (int i = 0; i < 1; ++i) {
+                for (int i = 0; i < ND_OPS; ++i) {
                     const double ratio = ctl->ad[i] ? __ddiv_rn(static_cast<double>(ctl->sd[i]), static_cast<double>(ctl->ad[i])) : 0.0;
                     const double w = __dadd_rn(__dmul_rn(__dsub_rn(1.0, t.r), ctl->wd[i]), __dmul_rn(t.r, ratio));
                     ctl->wd[i] = w < t.w_min ? t.w_min : w;
@@ -1903,6 +2193,8 @@ __device__ void phase_end(const AlnsTeam& t, const Smem& s, bool first) {
         }
         decision[0] = accept;
         decision[1] = newbest;
+        const int next = first ? 1 : ctl->iter + 1;
+        if (next <= t.iterations) pick_operators(t, next);
     }
     __syncthreads();
     const int accept = decision[0], newbest = decision[1];
@@ -1966,6 +2258,11 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
         }
     };
     for (int it = 1; it <= t.iterations; ++it) {
+        if (*reinterpret_cast<volatile int*>(&ctl->di) == D_WORST) {
+            // worst removal needs every customer's removal gain: a team phase
+            phase_gains(t, s, rank, team_blocks);
+            if (!team_barrier(ctl, team_blocks, gen)) return;
+        }
         if (rank == 0) {
             if (threadIdx.x == 0) ctl->iter = it;
             __syncthreads();
@@ -2054,6 +2351,7 @@ static size_t team_bytes(int n, int m, int qmax, int iterations, bool dump) {
     add(static_cast<size_t>(SC_CAP) * (4 * N + 8), 4);
     add(static_cast<size_t>(SC_CAP) * SC_CAP, 4);
     add(std::max(iterations, 1), 4);
+    add(n + 1, 4);
     if (dump) { add(G * G, 4); add(G * G, 4); }
     return w;
 }
@@ -2090,14 +2388,21 @@ static void carve_team(AlnsTeam& t, DevBuf& B, int n, int m, int qmax, int itera
     t.scw = B.take<int>(static_cast<size_t>(SC_CAP) * (4 * N + 8));
     t.scpair = B.take<int>(static_cast<size_t>(SC_CAP) * SC_CAP);
     t.trace = B.take<int>(std::max(iterations, 1));
+    t.gains = B.take<int>(n + 1);
     t.dump_delta = dump ? B.take<int>(G * G) : nullptr;
     t.dump_travel = dump ? B.take<int>(G * G) : nullptr;
 }
 
 bool coords_exact_small(const vrprpd_instance* I);
 
-size_t alns_device_bytes(int n, int m, int qmax, int iterations) {
-    return team_bytes(n, m, qmax, iterations, false) + sizeof(AlnsTeam) + 8192;
+// Rows of the per-customer buffers: a route removal takes a whole route, so
+// with that operator on, up to n customers wait for reinsertion at once.
+int alns_removal_cap(int n, int qmax, int destroy_mask) {
+    return (destroy_mask & (1 << D_ROUTE)) ? n : qmax;
+}
+
+size_t alns_device_bytes(int n, int m, int qmax, int destroy_mask, int iterations) {
+    return team_bytes(n, m, alns_removal_cap(n, qmax, destroy_mask), iterations, false) + sizeof(AlnsTeam) + 8192;
 }
 
 bool alns_supported(const vrprpd_instance* I, std::string* why) {
@@ -2164,6 +2469,7 @@ extern "C" void vrprpd_alns_params_default(vrprpd_alns_params* P) {
     P->iterations = 1000;
     P->repair_mask = 3;
     P->team_blocks = 0;
+    P->destroy_mask = 1;
 }
 
 // exact angular order around the depot: half plane, then cross product, then id
@@ -2236,7 +2542,7 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     VRP_CHECK(iters >= 0 && iters <= (1 << 24), VRPRPD_EINVAL, "iterations out of range");
     VRP_CHECK(P->tau >= 1, VRPRPD_EINVAL, "tau must be >= 1");
     const bool dump = mode == 1;
-    const int qcap = dump ? 1 : qmax;
+    const int qcap = dump ? 1 : alns_removal_cap(n, qmax, P->destroy_mask & 63);
     DevBuf B;
     B.cap = team_bytes(n, m, qcap, iters, dump) + 4096;
     VRP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&B.base), B.cap, stream));
@@ -2263,6 +2569,8 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     t.q_max = qmax;
     t.iterations = iters;
     t.repair_mask = P->repair_mask & 15;
+    t.destroy_mask = P->destroy_mask & 63;
+    VRP_CHECK(t.destroy_mask != 0, VRPRPD_EINVAL, "destroy_mask enables no destroy operator");
     VRP_CHECK(t.repair_mask != 0, VRPRPD_EINVAL, "repair_mask enables no repair operator");
     t.key = stream_key(seed, RNG_STREAM_ALNS);
     t.mode = mode;
@@ -2270,7 +2578,7 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     carve_team(t, B, n, m, qcap, iters, dump);
     auto cleanup = [&]() { cudaFreeAsync(B.base, stream); };
     AlnsCtl ctl{};
-    ctl.wd[0] = 1.0;
+    for (int i = 0; i < 8; ++i) ctl.wd[i] = 1.0;
     ctl.wr[0] = ctl.wr[1] = ctl.wr[2] = ctl.wr[3] = 1.0;
     if (dump) {
         ctl.nrem = 1;
@@ -2381,7 +2689,8 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
         stats->z_best = out.z_best;
         stats->z_current = out.z_cur;
         stats->T_final = out.T;
-        for (int i = 0; i < 4; ++i) { stats->w_destroy[i] = out.wd[i]; stats->w_repair[i] = out.wr[i]; }
+        for (int i = 0; i < 8; ++i) stats->w_destroy[i] = i < ND_OPS ? out.wd[i] : 0.0;
+        for (int i = 0; i < 4; ++i) stats->w_repair[i] = out.wr[i];
         stats->device_ms = ms;
         stats->matrix_entries = static_cast<int64_t>(out.entries);
         stats->fallback_entries = static_cast<int64_t>(out.fallback_entries);

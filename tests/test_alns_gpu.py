@@ -101,12 +101,14 @@ def test_initial_solution_matches_oracle(vrp):
         assert oracle.evaluate(oi, go, gf)[1] == 0
 
 
-def run_both(vrp, w, iters, seed, q=(0, 0), mask=3, team_blocks=0):
+def run_both(vrp, w, iters, seed, q=(0, 0), mask=3, team_blocks=0, dmask=1):
     inst = vrp.Instance.from_workload(w)
     oi = oracle.OracleInstance.from_workload(w)
     init = oracle.initial_solution(oi, w.coords)
-    g = vrp.alns_run(inst, vrp.alns_params(iters, q[0], q[1], mask, team_blocks), seed=seed, init=init)
-    o = oracle.alns_run(oi, init[0], init[1], oracle.alns_params(iters, q[0], q[1], mask), seed)
+    g = vrp.alns_run(inst, vrp.alns_params(iters, q[0], q[1], mask, team_blocks, destroy_mask=dmask),
+                     seed=seed, init=init)
+    o = oracle.alns_run(oi, init[0], init[1], oracle.alns_params(iters, q[0], q[1], mask, destroy_mask=dmask),
+                        seed)
     return inst, oi, g, o
 
 
@@ -118,6 +120,7 @@ def assert_same_run(oi, g, o):
     assert gs.z_best == os_.z_best and g["z_best"] == os_.z_best
     assert gs.T_final == os_.T_final
     assert list(gs.w_repair) == list(os_.w_repair)
+    assert list(gs.w_destroy) == list(os_.w_destroy)
     assert np.array_equal(g["best_ops"], o["best_ops"]) and np.array_equal(g["best_off"], o["best_off"])
     assert np.array_equal(g["cur_ops"], o["cur_ops"]) and np.array_equal(g["cur_off"], o["cur_off"])
     # every returned solution re-evaluated by the oracle
@@ -221,3 +224,34 @@ def test_alns_all_repair_operators_medium(vrp):
     w = workloads.make_instance(40, 5, 10, 5, "2x", seed=5)
     _, oi, g, o = run_both(vrp, w, 8, seed=2, q=(4, 4), mask=15)
     assert_same_run(oi, g, o)
+
+
+@pytest.mark.parametrize("dmask", [1, 2, 4, 8, 16, 32, 63])
+def test_alns_destroy_operators(vrp, dmask):
+    # random, worst, Shaw, cluster, route and critical-path removal alone,
+    # then all six under the roulette (Section 4.2.2)
+    w = workloads.make_instance(24, 3, 6, 4, "5x", seed=4)
+    _, oi, g, o = run_both(vrp, w, 60, seed=11, dmask=dmask)
+    assert_same_run(oi, g, o)
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_alns_all_operators_medium(vrp, seed):
+    # every destroy and repair operator, a removal range wide enough for the
+    # route and critical-path top-ups, clustered coordinates
+    w = workloads.make_instance(40, 5, 10, 5, "2x", "clustered", seed=8 + seed)
+    _, oi, g, o = run_both(vrp, w, 24, seed=seed, q=(3, 8), mask=15, dmask=63)
+    assert_same_run(oi, g, o)
+
+
+def test_alns_all_operators_team_blocks_agree(vrp):
+    w = workloads.make_instance(100, 4, 10, 5, "2x", seed=1)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    init = oracle.initial_solution(oi, w.coords)
+    runs = [vrp.alns_run(inst, vrp.alns_params(12, 5, 15, 15, tb, destroy_mask=63), seed=5, init=init)
+            for tb in (1, 7)]
+    assert np.array_equal(runs[0]["trace"], runs[1]["trace"])
+    assert np.array_equal(runs[0]["best_ops"], runs[1]["best_ops"])
+    assert list(runs[0]["stats"].w_destroy) == list(runs[1]["stats"].w_destroy)
+    assert oracle.evaluate(oi, runs[0]["best_ops"], runs[0]["best_off"]) == (runs[0]["z_best"], 0)
