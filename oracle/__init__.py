@@ -91,6 +91,8 @@ def lib():
             L.oracle_evaluate_batch.argtypes = [C.POINTER(Inst), C.c_int32, i32p, i32p, i32p, u32p,
                                                 C.c_int32]
             L.oracle_sp_closure.argtypes = [i32p, C.c_int32, i64p]
+            L.oracle_coordination.argtypes = [C.POINTER(Inst), i32p, i32p, i32p, i32p]
+            L.oracle_coordination.restype = C.c_uint32
             L.oracle_bruteforce.argtypes = [C.POINTER(Inst), i32p, i32p]
             L.oracle_bruteforce.restype = C.c_int64
             L.oracle_minmax_vrp.argtypes = [i32p, C.c_int32, C.c_int32]
@@ -315,6 +317,17 @@ def brkga_run(I, params, warm_ops, warm_off, seed):
 
 
 DESTROY = {"random": 0, "worst": 1, "shaw": 2, "cluster": 3, "route": 4, "critical": 5}
+
+
+def coordination(I, ops, off):
+    """Section 5.2 counts of one complete solution: (cross, interleaved, status);
+    -1 where a count is undefined (malformed; interleaved on a cycle)."""
+    ops = np.ascontiguousarray(ops, dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int32)
+    cr = np.zeros(1, np.int32)
+    il = np.zeros(1, np.int32)
+    st = lib().oracle_coordination(C.byref(I.c), _p(ops), _p(off), _p(cr), _p(il))
+    return int(cr[0]), int(il[0]), int(st)
 
 
 def destroy(I, op, ops, off, q, qmin, key, base):

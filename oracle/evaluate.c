@@ -172,3 +172,44 @@ void oracle_sp_closure(const int32_t* d, int32_t N, int64_t* sp) {
                 if (via < sp[(int64_t)i * N + j]) sp[(int64_t)i * N + j] = via;
             }
 }
+
+/* Coordination metrics (Section 5.2, "Key Metrics") as counts over the n
+ * customers; the percentages are 100 * count / n.
+ *   cross: the dropoff and the pickup are on different vehicles.
+ *   interleaved: the dropoff vehicle does something else between the
+ *     customer's dropoff and its pickup.  On one vehicle: at least one op lies
+ *     between the two in the route.  On two vehicles: the dropoff vehicle's
+ *     next op exists and is reached (departure after the dropoff plus travel)
+ *     before the pickup completes.
+ * Returns the evaluator's status.  Counts are -1 where they are undefined:
+ * both on a malformed solution, interleaved on a precedence cycle. */
+uint32_t oracle_coordination(const oracle_inst* I, const int32_t* ops, const int32_t* off, int32_t* cross,
+                             int32_t* interleaved) {
+    const int n = I->n, m = I->m;
+    int32_t z;
+    uint32_t st;
+    int64_t* times = (int64_t*)malloc(sizeof(int64_t) * (2 * (size_t)n + 2));
+    oracle_evaluate(I, ops, off, 0, &z, &st, times);
+    *cross = -1;
+    *interleaved = -1;
+    if (st & OR_MALFORMED) { free(times); return st; }
+    int* veh = (int*)malloc(sizeof(int) * (2 * (size_t)n + 2));
+    int* pos = (int*)malloc(sizeof(int) * (2 * (size_t)n + 2));
+    for (int v = 0; v < m; v++)
+        for (int k = off[v]; k < off[v + 1]; k++) { veh[ops[k]] = v; pos[ops[k]] = k; }
+    int nc = 0, ni = 0;
+    for (int c = 1; c <= n; c++) {
+        const int vd = veh[2 * c], vp = veh[2 * c + 1];
+        if (vd != vp) {
+            nc++;
+            const int nx = pos[2 * c] + 1;
+            if (nx < off[vd + 1] && times[2 * c] + D(I, c, ops[nx] >> 1) < times[2 * c + 1]) ni++;
+        } else if (pos[2 * c + 1] > pos[2 * c] + 1) {
+            ni++;
+        }
+    }
+    *cross = nc;
+    if (!(st & OR_CYCLE)) *interleaved = ni;
+    free(veh); free(pos); free(times);
+    return st;
+}

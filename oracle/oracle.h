@@ -39,6 +39,10 @@ void oracle_euc2d(const int32_t* coords, int32_t n_nodes, int32_t* d);
 int oracle_evaluate(const oracle_inst* I, const int32_t* ops, const int32_t* off,
                     int allow_partial, int32_t* z, uint32_t* status, int64_t* times);
 
+/* Section 5.2 coordination counts (cross-agent, interleaved) of one complete
+ * solution; -1 where undefined.  Returns the evaluator's status bits. */
+uint32_t oracle_coordination(const oracle_inst* I, const int32_t* ops, const int32_t* off, int32_t* cross,
+                             int32_t* interleaved);
 void oracle_evaluate_batch(const oracle_inst* I, int32_t count, const int32_t* ops,
                            const int32_t* off, int32_t* z, uint32_t* status, int32_t threads);
 
