@@ -137,6 +137,25 @@ int vrprpd_evaluate_plain(const vrprpd_instance* inst, const vrprpd_batch* batch
 int vrprpd_evaluate_plain_noalloc(const vrprpd_instance* inst, const vrprpd_batch* batch,
                                   int32_t* makespan, uint32_t* status, void* stream);
 
+/*
+ * Coordination counts of Section 5.2 ("Key Metrics"; the paper reports them
+ * as percentages of n) for a batch of complete solutions:
+ *   cross        num int32: customers whose dropoff and pickup are made by
+ *                different vehicles (Cross-Agent);
+ *   interleaved  num int32: customers whose dropoff vehicle does something
+ *                else between their dropoff and pickup (Interleaved).  On one
+ *                vehicle: the pickup does not directly follow the dropoff in
+ *                the route.  On two vehicles: the dropoff vehicle has a next
+ *                op and reaches it (dropoff time plus travel) strictly before
+ *                the pickup completes (max(arrival, T_drop + p), Eqs. 8-10).
+ * -1 marks an undefined count: both for a malformed candidate (an op code out
+ * of range or repeated, offsets not 0 <= ... <= 2n), interleaved for a
+ * precedence cycle.  Needs m <= 32 and (2n+1) max d + n max p < 2^31
+ * (VRPRPD_EINVAL otherwise).  Device pointers; asynchronous on stream.
+ */
+int vrprpd_coordination(const vrprpd_instance* inst, const vrprpd_batch* batch, int32_t* cross,
+                        int32_t* interleaved, void* stream);
+
 /* Wait for stream and report a device-side error the kernels recorded for
  * this instance (VRPRPD_ETIMEOUT if a bounded wait gave up), then clear it. */
 int vrprpd_sync(const vrprpd_instance* inst, void* stream);

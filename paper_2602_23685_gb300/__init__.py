@@ -56,7 +56,7 @@ def lib():
             L.vrprpd_instance_destroy.argtypes = [vp]
             L.vrprpd_instance_destroy.restype = None
             L.vrprpd_instance_get_dist.argtypes = [vp, vp]
-            for name in ("vrprpd_evaluate", "vrprpd_evaluate_host", "vrprpd_evaluate_plain"):
+            for name in ("vrprpd_evaluate", "vrprpd_evaluate_host", "vrprpd_evaluate_plain", "vrprpd_coordination"):
                 getattr(L, name).argtypes = [vp, C.POINTER(Batch), vp, vp, vp]
             L.vrprpd_sync.argtypes = [vp, vp]
             L.vrprpd_eval_set_config.argtypes = [vp, C.POINTER(EvalConfig)]
@@ -190,6 +190,18 @@ def evaluate_plain(inst, ops, off, z=None, st=None, stream=None):
     _check(lib().vrprpd_evaluate_plain(inst.handle, C.byref(b), z.data_ptr(), st.data_ptr(),
                                        _stream_ptr(stream)))
     return z, st
+
+
+def coordination(inst, ops, off, stream=None):
+    """Section 5.2 counts of complete solutions on device tensors: (cross,
+    interleaved) int32 per candidate, -1 where undefined."""
+    torch = _torch()
+    b = _batch(inst, ops, off)
+    cross = torch.empty(b.num, dtype=torch.int32, device=ops.device)
+    inter = torch.empty(b.num, dtype=torch.int32, device=ops.device)
+    _check(lib().vrprpd_coordination(inst.handle, C.byref(b), cross.data_ptr(), inter.data_ptr(),
+                                     _stream_ptr(stream)))
+    return cross, inter
 
 
 def evaluate_host(inst, ops, off, z=None, st=None, stream=None):
