@@ -458,7 +458,29 @@ def main():
     e2e_value = B * e2e_steps * world / e2e_s
     assert torch.equal(z_h, z.cpu())
 
+    # Section 5.2 coordination counts over the first quarter of the batch:
+    # same candidate bytes read, a lock-step walk per candidate like the
+    # evaluator's; every tiled copy must give the first copy's counts
+    Bc = B // 4
+    cr, il = vrp.coordination(inst, ops[:Bc], off[:Bc])
+    torch.cuda.synchronize()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    co_steps = 3
+    c0.record(stream)
+    for _ in range(co_steps):
+        cr, il = vrp.coordination(inst, ops[:Bc], off[:Bc])
+    c1.record(stream)
+    torch.cuda.synchronize()
+    co_ms = c0.elapsed_time(c1) / co_steps
+    crv, ilv = cr.view(-1, BASE_CANDS), il.view(-1, BASE_CANDS)
+    coordination = {"coordination_counts": {
+        "value": Bc / (co_ms / 1000.0), "unit": "candidates/s", "candidates": Bc, "ms": co_ms,
+        "kernel": "coordination_kernel", "tiles_agree": bool((crv == crv[0]).all()) and bool((ilv == ilv[0]).all()),
+        "mean_cross_pct": float(cr.double().mean()) * 100.0 / N_CUST,
+        "mean_interleaved_pct": float(il.double().mean()) * 100.0 / N_CUST}}
+
     searches = {} if args.no_search else run_searches(vrp, args)
+    searches.update(coordination)
     if not args.no_search:
         searches.update(run_multi(vrp, args))
         searches.update(run_serving(vrp, args))

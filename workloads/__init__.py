@@ -28,7 +28,8 @@ import numpy as np
 __all__ = [
     "Instance", "uniform_coords", "clustered_coords", "processing_times",
     "make_instance", "random_candidates", "precedence_candidates",
-    "random_keys", "loguniform_sizes", "CONFIGS",
+    "random_keys", "loguniform_sizes", "CONFIGS", "paper_fleet", "paper_processing_times",
+    "make_paper_instance",
 ]
 
 
@@ -95,6 +96,50 @@ def make_instance(n, m, R, Q, variant="base", layout="uniform", seed=0):
         raise ValueError(layout)
     p = processing_times(coords, variant, seed)
     return Instance(coords, p, m, R, Q, name=f"{layout}-n{n}-{variant}-s{seed}")
+
+
+def paper_fleet(n):
+    """Section 5.1 fleet: m = 3 vehicles of capacity 5 below 24 customers,
+    m = 6 of capacity 4 from 24 on.  The paper has no depot pool, so R = mQ
+    (every vehicle may leave full, the LOAD_FULL reading)."""
+    m, Q = (3, 5) if n < 24 else (6, 4)
+    return m, Q, m * Q
+
+
+def paper_processing_times(coords, variant, seed):
+    """Section 5.1 processing-time variants: base = U_int[d_min, d_max] over
+    the instance's edge weights (distinct nodes); 2x and 5x scale it;
+    1R10 / 1R20 multiply each base time by U_int[1, 10] / U_int[1, 20].  The
+    base draws do not depend on the variant, so the variants of one seed pair
+    up as in the paper.  Rounding to the nearest integer is monotone, so the
+    extreme edge weights are the rounded extreme distances."""
+    n = coords.shape[0] - 1
+    if n < 1:
+        return np.zeros(0, np.int32)
+    xy = coords.astype(np.float64)
+    diff = xy[:, None, :] - xy[None, :, :]
+    dist = np.sqrt((diff * diff).sum(-1))
+    off_diag = dist[~np.eye(n + 1, dtype=bool)]
+    dmin = int(np.floor(off_diag.min() + 0.5)) if off_diag.size else 0
+    dmax = int(np.floor(off_diag.max() + 0.5)) if off_diag.size else 0
+    base = _rng(seed, 5).integers(dmin, dmax + 1, size=n, dtype=np.int64)
+    mult = {"base": 1, "2x": 2, "5x": 5}
+    if variant in mult:
+        return (base * mult[variant]).astype(np.int32)
+    hi = {"1R10": 10, "1R20": 20}.get(variant)
+    if hi is None:
+        raise ValueError(f"unknown processing-time variant {variant!r}")
+    k = _rng(seed, 6).integers(1, hi + 1, size=n, dtype=np.int64)
+    return (base * k).astype(np.int32)
+
+
+def make_paper_instance(n, variant="base", layout="uniform", seed=0):
+    """An instance under the paper's own rules (Section 5.1): its fleet and its
+    processing-time variants; evaluate it with the LOAD_FULL flag."""
+    coords = uniform_coords(n, seed) if layout == "uniform" else clustered_coords(n, seed)
+    m, Q, R = paper_fleet(n)
+    p = paper_processing_times(coords, variant, seed)
+    return Instance(coords, p, m, R, Q, name=f"paper-{layout}-n{n}-{variant}-s{seed}")
 
 
 def _cuts(g, total, m, count):
