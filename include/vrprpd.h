@@ -325,7 +325,7 @@ typedef struct {
     int32_t warm_slots;        /* slots seeded from the warm start (0 without one) */
     int32_t warm_variants;     /* distinct warm variants cycled over those slots (20) */
     float elite_frac, mutant_frac, rho;  /* Table 3: 0.15, 0.15, 0.7 */
-    float eps;                 /* warm perturbation half-width (0.03, Section 4.4.5) */
+    float eps;                 /* warm perturbation half-width (0.03, Section 4.4.4) */
     int32_t layout;            /* VRPRPD_LAYOUT_VKEYS (default) or VRPRPD_LAYOUT_HINTS */
 } vrprpd_brkga_params;
 
@@ -347,7 +347,7 @@ void vrprpd_brkga_params_default(vrprpd_brkga_params* params);
  *   ops/off  device, num x 2n and num x (m+1): the decoded routes (scheduled ops only).
  *   z        device, num: makespan of the decoded routes.
  *   unsched  device, num: ops left unscheduled.
- *   fitness  device, num int64: z + 10^6 * unsched (Section 4.4.3).
+ *   fitness  device, num int64: z + 10^6 * unsched (Section 4.4.2, infeasibility handling).
  * Asynchronous on stream.  Needs m <= 32 and 2n + m <= 8192.
  */
 int vrprpd_brkga_decode(const vrprpd_instance* inst, const float* keys, int32_t num, int32_t layout,

@@ -122,7 +122,7 @@ int oracle_decode(const oracle_inst* I, const float* keys, int32_t* ops, int32_t
 int oracle_decode_l(const oracle_inst* I, const float* keys, int32_t layout, int32_t* ops, int32_t* off,
                     int32_t* z, int32_t* unscheduled, int64_t* fitness);
 
-/* ALNS seed encoding (Section 4.4.5): pi_o = (r-1)/L_v; layout 0 vehicle
+/* ALNS seed encoding (Section 4.4.4): pi_o = (r-1)/L_v; layout 0 vehicle
  * key v/m; layout 1 hint alpha_o = v/m for every op on vehicle v, rounded up
  * to the smallest float with m * alpha_o >= v, so that floor(m * alpha_o) = v. */
 void oracle_encode(const oracle_inst* I, const int32_t* ops, const int32_t* off, float* keys);

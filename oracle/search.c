@@ -836,13 +836,13 @@ int oracle_decode_l(const oracle_inst* I, const float* keys, int32_t layout, int
     int uns = two_n - done;
     *z_out = (int32_t)z;
     *unsched_out = uns;
-    *fitness_out = z + (int64_t)1000000 * uns;     /* Section 4.4.3 penalty */
+    *fitness_out = z + (int64_t)1000000 * uns;     /* Section 4.4.2, infeasibility handling */
     free(order); free(vorder); free(rank); free(t); free(loc); free(net); free(nmin); free(nmax);
     free(load); free(cnt); free(seq); free(sched); free(tdrop);
     return 0;
 }
 
-/* ALNS seed encoding (Section 4.4.5): pi_o = (r-1)/L_v; vehicle key v/m
+/* ALNS seed encoding (Section 4.4.4): pi_o = (r-1)/L_v; vehicle key v/m
  * (layout 0) or the hint v/m of every op on vehicle v (layout 1), the latter
  * rounded up to the smallest float with m * alpha >= v so that the decoder's
  * floor(m * alpha) names v again. */

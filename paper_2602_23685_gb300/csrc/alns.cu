@@ -1,31 +1,44 @@
-// ALNS on the device (Section 4.2, Algorithm 1): random removal, greedy and
-// regret-2 insertion over the full insertion-delta matrix (Section 4.2.3),
-// simulated-annealing acceptance with reheat (Section 4.2.4), adaptive
-// operator weights (Section 4.2.1).
+// ALNS on the device (Section 4.2, Algorithm 1): the six destroy operators
+// of Section 4.2.2 (random, worst, Shaw, cluster, route, critical path), the
+// four repair operators of Section 4.2.3 (greedy, regret-2, regret-3,
+// regret-m) over the full insertion-delta matrix, simulated-annealing
+// acceptance with gated reheat (Section 4.2.4) and adaptive roulette weights
+// (Section 4.2.1).
 //
 // One persistent cooperative launch; a team of CTAs runs one ALNS instance
-// and meets at bounded team barriers.  Each insertion step:
-//   prep    each CTA stages the partial solution W in shared memory (op codes
-//           packed with their travel-in times); one warp walks W from the depot
-//           (node times H, makespan, stock prefixes), the other warps walk W
-//           from every op u (row u of the all-pairs longest-path table LP and
-//           the tail T(u) = longest path from u to a depot return); threads
-//           flag "shortcut" gaps, where d(x,c) + d(c,y) < d(x,y) because of
-//           the nint rounding;
+// and meets at bounded team barriers.  Per iteration:
+//   gains   (worst removal only) one skip-walk per customer across the team:
+//           the makespan without that customer;
+//   begin   rank 0 marks the removed customers (Fisher-Yates, or a block
+//           bitonic sort of (key, customer) for the structured operators) and
+//           builds W = current solution without them.
+// Then one insertion step per removed customer:
+//   prep    each CTA stages W in shared memory (op codes packed with their
+//           travel-in times).  After a full step, warps walk W from the depot
+//           (node times H, makespan) and from every op u (row u of the
+//           all-pairs longest-path table LP, and the tail T(u)); after a plain
+//           insertion the table is updated in place from the inserted pair
+//           instead.  Threads flag "shortcut" gaps, where d(x,c) + d(c,y) <
+//           d(x,y) because of the nint rounding;
 //   gaps    per-gap vectors (H of the stop before, T of the stop after, the
-//           removed leg, stock prefix/suffix extremes) and sparse tables of
-//           the stock prefix for same-route ranges;
-//   matrix  32 x 128 tiles of (dropoff gap, pickup gap) entries for every
+//           removed leg, stock prefix/suffix extremes), per-(customer, gap)
+//           row and column vectors, and sparse tables of the stock prefix;
+//           the team then starts the shortcut simulations (schedules with the
+//           single shortcut stop added) without waiting for them;
+//   matrix  32 x 64 tiles of (dropoff gap, pickup gap) entries for every
 //           customer still to insert.  Without shortcut gaps the new makespan
 //           is exactly max(z, beta, gamma, delta, epsilon): the old makespan,
 //           the longest path through the new drop only, through the new pickup
 //           only, through drop -> pickup by the processing edge, and through
 //           drop -> route -> pickup (the LP table).  Capacity and pool are O(1)
-//           from the prefix/suffix extremes.  Entries touching a shortcut gap
-//           are re-simulated in full by one warp each;
+//           from the prefix/suffix extremes.  Feasible pairs are compacted per
+//           CTA and reduced to per-row minima with shared 64-bit atomics.
+//           Entries on shortcut gaps come last, from the simulations;
 //   select  per-customer argmin of (delta z, delta travel, flat index), then
-//           greedy or regret-2 choice across customers; the choice is applied
-//           to W.
+//           the repair operator's choice across customers; the choice is
+//           applied to W.
+// Rank 0 ends the iteration: the repaired W is walked and accepted or not,
+// the temperature and weights are updated and the next operators are drawn.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -1,6 +1,6 @@
 // BRKGA on the device (Section 4.4): random-key chromosomes, the multi-pass
 // decoder of Algorithm 2, elite preservation, mutants, biased crossover and
-// the ALNS warm start (Section 4.4.5).
+// the ALNS warm start (Section 4.4.4).
 //
 // Per generation (captured once as a CUDA graph, replayed):
 //   decode   one warp per chromosome: warp bitonic sort of (key, op index)
