@@ -52,7 +52,8 @@ class AlnsParams(C.Structure):
                 ("r", C.c_double), ("stagnation", C.c_int32), ("tau", C.c_int32),
                 ("sigma1", C.c_int32), ("sigma2", C.c_int32), ("sigma3", C.c_int32),
                 ("w_min", C.c_double), ("q_min", C.c_int32), ("q_max", C.c_int32),
-                ("iterations", C.c_int32), ("repair_mask", C.c_int32), ("destroy_mask", C.c_int32)]
+                ("iterations", C.c_int32), ("repair_mask", C.c_int32), ("destroy_mask", C.c_int32),
+                ("ls_pickup_every", C.c_int32), ("ls_relocate_every", C.c_int32)]
 
 
 class AlnsStats(C.Structure):
@@ -60,7 +61,8 @@ class AlnsStats(C.Structure):
                 ("new_best", C.c_int32), ("reheats", C.c_int32),
                 ("rejected_infeasible", C.c_int32), ("z_init", C.c_int32),
                 ("z_best", C.c_int32), ("z_current", C.c_int32), ("T_final", C.c_double),
-                ("w_destroy", C.c_double * 8), ("w_repair", C.c_double * 4)]
+                ("w_destroy", C.c_double * 8), ("w_repair", C.c_double * 4),
+                ("ls_moves", C.c_int32), ("ls_new_best", C.c_int32)]
 
 
 class BrkgaParams(C.Structure):
@@ -93,6 +95,7 @@ def lib():
             L.oracle_sp_closure.argtypes = [i32p, C.c_int32, i64p]
             L.oracle_coordination.argtypes = [C.POINTER(Inst), i32p, i32p, i32p, i32p]
             L.oracle_coordination.restype = C.c_uint32
+            L.oracle_local_search.argtypes = [C.POINTER(Inst), C.c_int32, C.c_int32, i32p, i32p, i32p]
             L.oracle_bruteforce.argtypes = [C.POINTER(Inst), i32p, i32p]
             L.oracle_bruteforce.restype = C.c_int64
             L.oracle_minmax_vrp.argtypes = [i32p, C.c_int32, C.c_int32]
@@ -248,9 +251,10 @@ def initial_solution(I, coords):
     return ops, off
 
 
-def alns_params(iterations, q_min=0, q_max=0, repair_mask=3, destroy_mask=1):
+def alns_params(iterations, q_min=0, q_max=0, repair_mask=3, destroy_mask=1, ls_pickup_every=200,
+                ls_relocate_every=500):
     return AlnsParams(0.30, 0.9998, 0.50, 0.1, 2000, 100, 33, 9, 13, 0.1, q_min, q_max,
-                      iterations, repair_mask, destroy_mask)
+                      iterations, repair_mask, destroy_mask, ls_pickup_every, ls_relocate_every)
 
 
 def alns_run(I, init_ops, init_off, params, seed):
@@ -328,6 +332,20 @@ def coordination(I, ops, off):
     il = np.zeros(1, np.int32)
     st = lib().oracle_coordination(C.byref(I.c), _p(ops), _p(off), _p(cr), _p(il))
     return int(cr[0]), int(il[0]), int(st)
+
+
+LS_PICKUP, LS_RELOCATE = 1, 2
+
+
+def local_search(I, mode, ops, off, passes=3):
+    """Section 4.2.6 local search on a copy of (ops, off): (moves, z, ops, off)."""
+    ops = np.array(ops, dtype=np.int32)
+    off = np.array(off, dtype=np.int32)
+    z = np.zeros(1, np.int32)
+    mv = lib().oracle_local_search(C.byref(I.c), mode, passes, _p(ops), _p(off), _p(z))
+    if mv < 0:
+        raise ValueError("local search needs a feasible complete solution and mode 1 or 2")
+    return mv, int(z[0]), ops, off
 
 
 def destroy(I, op, ops, off, q, qmin, key, base):

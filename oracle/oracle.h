@@ -75,6 +75,8 @@ typedef struct {
     int32_t iterations;
     int32_t repair_mask;                  /* bit0 greedy, bit1 regret-2, bit2 regret-3, bit3 regret-m */
     int32_t destroy_mask;                 /* bit0 random, 1 worst, 2 Shaw, 3 cluster, 4 route, 5 critical path */
+    int32_t ls_pickup_every;              /* pickup repositioning period (200; 0 = off) */
+    int32_t ls_relocate_every;            /* cross-agent relocation period (500; 0 = off) */
 } oracle_alns_params;
 
 typedef struct {
@@ -82,6 +84,7 @@ typedef struct {
     int32_t z_init, z_best, z_current;
     double T_final;
     double w_destroy[8], w_repair[4];
+    int32_t ls_moves, ls_new_best;        /* local-search moves applied; best solutions it found */
 } oracle_alns_stats;
 
 void oracle_q_range(int32_t n, int32_t* q_min, int32_t* q_max);
@@ -102,6 +105,13 @@ int oracle_initial_solution(const oracle_inst* I, const int32_t* coords, int32_t
  * how many customers it removed. */
 int oracle_destroy(const oracle_inst* I, int32_t di, const int32_t* S, const int32_t* So, int32_t q,
                    int32_t qmin, uint64_t key, uint64_t base, char* rem);
+
+/* Periodic local search (Section 4.2.6) on a feasible complete solution, in
+ * place: mode 1 pickup repositioning, mode 2 cross-agent relocation, up to
+ * `passes` passes.  Returns the moves applied (z = the new makespan), or -1
+ * on an infeasible input or a bad mode. */
+int oracle_local_search(const oracle_inst* I, int32_t mode, int32_t passes, int32_t* ops, int32_t* off,
+                        int32_t* z);
 
 int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t* init_off,
                     const oracle_alns_params* P, uint64_t seed,

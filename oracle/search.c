@@ -564,6 +564,110 @@ int oracle_destroy(const oracle_inst* I, int32_t di, const int32_t* S, const int
     return cnt;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Periodic local search (Section 4.2.6) on the current solution.            */
+/*   LS_PICKUP:   pickup repositioning.  Candidates: customers whose pickup   */
+/*                sits on a vehicle returning at 95% of the makespan or later */
+/*                (20 ret >= 19 z).  Move: the pickup to any position of any  */
+/*                vehicle, the dropoff left where it is.                      */
+/*   LS_RELOCATE: cross-agent relocation.  Candidates: customers with an op   */
+/*                on the bottleneck vehicle (latest return, lower index on   */
+/*                ties).  Move: dropoff and pickup together onto one other    */
+/*                vehicle, at any positions in that order.                    */
+/* A pass scores every move of every candidate by the resulting solution:    */
+/* (makespan, total travel, customer, flat gap index row*G + col, gaps of    */
+/* the solution without the customer), feasible only with no status bit.    */
+/* It applies the least if its makespan is below the current one; up to      */
+/* three passes, candidates re-derived each time.  Returns the moves made.   */
+/* ------------------------------------------------------------------------ */
+enum { LS_PICKUP = 1, LS_RELOCATE = 2 };
+
+static int local_search(const oracle_inst* I, int mode, int32_t* S, int32_t* So, int32_t* z, int passes) {
+    const int n = I->n, m = I->m, two_n = 2 * n;
+    int64_t* times = malloc(sizeof(int64_t) * (two_n + 2));
+    int* vd = calloc((size_t)n + 1, sizeof(int));
+    int* vp = calloc((size_t)n + 1, sizeof(int));
+    int* pd = calloc((size_t)n + 1, sizeof(int));
+    int64_t* ret = calloc((size_t)m, sizeof(int64_t));
+    int32_t *W = malloc(sizeof(int32_t) * (two_n + 2)), *Wo = malloc(sizeof(int32_t) * (m + 1));
+    int32_t *X = malloc(sizeof(int32_t) * (two_n + 2)), *Xo = malloc(sizeof(int32_t) * (m + 1));
+    char* rem = calloc((size_t)n + 1, 1);
+    int moves = 0;
+    for (int pass = 0; pass < passes; pass++) {
+        solution_facts(I, S, So, times, vd, vp, ret);
+        for (int v = 0; v < m; v++)
+            for (int k = So[v]; k < So[v + 1]; k++)
+                if (!(S[k] & 1)) pd[S[k] >> 1] = k - So[v];
+        const int64_t zc = *z;
+        int bott = 0;
+        for (int v = 1; v < m; v++)
+            if (ret[v] > ret[bott]) bott = v;
+        int have = 0, bc = 0, ba = 0, bi = 0, bb = 0, bj = 0;
+        int64_t bz = 0, bt = 0, bf = 0;
+        const int G = (two_n - 2) + m;
+        for (int c = 1; c <= n; c++) {
+            if (mode == LS_PICKUP ? !(20 * ret[vp[c]] >= 19 * zc) : (vd[c] != bott && vp[c] != bott)) continue;
+            rem[c] = 1;
+            remove_customers(m, S, So, rem, W, Wo);
+            rem[c] = 0;
+            for (int a = 0; a < m; a++) {
+                if (mode == LS_PICKUP && a != vd[c]) continue;
+                if (mode == LS_RELOCATE && a == bott) continue;
+                const int La = Wo[a + 1] - Wo[a];
+                for (int i = 0; i <= La; i++) {
+                    if (mode == LS_PICKUP && i != pd[c]) continue;
+                    for (int b = 0; b < m; b++) {
+                        if (mode == LS_RELOCATE && b != a) continue;
+                        const int Lb = Wo[b + 1] - Wo[b];
+                        for (int j = (b == a ? i : 0); j <= Lb; j++) {
+                            build_insert(I, W, Wo, c, a, i, b, j, X, Xo);
+                            int32_t zn;
+                            uint32_t st;
+                            oracle_evaluate(I, X, Xo, 0, &zn, &st, NULL);
+                            if (st) continue;
+                            const int64_t tn = travel_of(I, X, Xo);
+                            const int64_t flat = (int64_t)(Wo[a] + a + i) * G + (Wo[b] + b + j);
+                            int better = !have;
+                            if (!better) {
+                                if (zn != bz) better = zn < bz;
+                                else if (tn != bt) better = tn < bt;
+                                else if (c != bc) better = c < bc;
+                                else better = flat < bf;
+                            }
+                            if (better) {
+                                have = 1;
+                                bz = zn; bt = tn; bc = c; bf = flat;
+                                ba = a; bi = i; bb = b; bj = j;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (!have || bz >= zc) break;
+        rem[bc] = 1;
+        remove_customers(m, S, So, rem, W, Wo);
+        rem[bc] = 0;
+        build_insert(I, W, Wo, bc, ba, bi, bb, bj, X, Xo);
+        memcpy(S, X, sizeof(int32_t) * two_n);
+        memcpy(So, Xo, sizeof(int32_t) * (m + 1));
+        *z = (int32_t)bz;
+        moves++;
+    }
+    free(times); free(vd); free(vp); free(pd); free(ret); free(W); free(Wo); free(X); free(Xo); free(rem);
+    return moves;
+}
+
+int oracle_local_search(const oracle_inst* I, int32_t mode, int32_t passes, int32_t* ops, int32_t* off,
+                        int32_t* z) {
+    int32_t z0;
+    uint32_t st;
+    oracle_evaluate(I, ops, off, 0, &z0, &st, NULL);
+    if (st || (mode != LS_PICKUP && mode != LS_RELOCATE)) return -1;
+    *z = z0;
+    return local_search(I, mode, ops, off, z, passes);
+}
+
 int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t* init_off,
                     const oracle_alns_params* P, uint64_t seed, int32_t* best_ops, int32_t* best_off,
                     int32_t* cur_ops_out, int32_t* cur_off_out, oracle_alns_stats* stats,
@@ -675,6 +779,19 @@ int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t
                 sr[i] = 0;
                 ar[i] = 0;
             }
+        }
+        /* periodic local search on the current solution (Section 4.2.6):
+         * pickup repositioning first when both fall due */
+        if (P->ls_pickup_every > 0 && it % P->ls_pickup_every == 0)
+            stats->ls_moves += local_search(I, LS_PICKUP, S, So, &z, 3);
+        if (P->ls_relocate_every > 0 && it % P->ls_relocate_every == 0)
+            stats->ls_moves += local_search(I, LS_RELOCATE, S, So, &z, 3);
+        if (z < zb) {
+            memcpy(Sb, S, sizeof(int32_t) * two_n);
+            memcpy(Sbo, So, sizeof(int32_t) * (m + 1));
+            zb = z;
+            stagnation = 0;
+            stats->ls_new_best++;
         }
         if (z_trace) z_trace[it - 1] = z;
         stats->iterations = it;
