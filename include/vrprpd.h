@@ -244,6 +244,17 @@ typedef struct {
                                   bit 5 critical path: q random customers of the latest-returning route
                                     (all if fewer), topped up to q_min by the latest pickup completion.
                                   Ties go to the smaller customer id. */
+    int32_t ls_pickup_every;   /* Section 4.2.6 periodic local search on the current solution, after the
+                                  acceptance step of every k-th iteration (0 = off).  Pickup
+                                  repositioning (default 200): customers whose pickup is on a vehicle
+                                  returning at 95% of the makespan or later may move that pickup to any
+                                  position of any vehicle.  Cross-agent relocation (ls_relocate_every,
+                                  default 500): customers with an op on the bottleneck vehicle (latest
+                                  return, lower index on ties) may move both ops onto one other vehicle.
+                                  Each pass applies the move with the least (makespan, travel, customer,
+                                  flat gap index) if it lowers the makespan; up to three passes;
+                                  pickup repositioning first when both fall due. */
+    int32_t ls_relocate_every;
 } vrprpd_alns_params;
 
 typedef struct {
@@ -260,6 +271,9 @@ typedef struct {
     int64_t incremental_steps; /* greedy steps whose longest-path table was updated in O(N^2) */
     int64_t full_steps;        /* greedy steps that re-walked W from every op (after a removal or a
                                   shortcut insertion) */
+    int32_t ls_moves;          /* local-search moves applied */
+    int32_t ls_new_best;       /* iterations whose local search gave a new best solution */
+    double ls_ms;              /* wall time spent in the local search */
 } vrprpd_alns_stats;
 
 void vrprpd_alns_params_default(vrprpd_alns_params* params);

@@ -88,7 +88,15 @@ struct AlnsCtl {
     int upd[16];
     unsigned long long steps_incr, steps_full;
     unsigned long long entries, fallback_entries;
-    unsigned long long phase_ns[6];   // begin, prep, gaps, matrix, select, end (rank 0 wall time)
+    unsigned long long phase_ns[7];   // begin, prep, gaps, matrix, select, end, local search (rank 0 wall time)
+    // periodic local search: its mode while a candidate's matrix runs (0
+    // otherwise), the pass's candidates, the best move so far (customer,
+    // makespan, travel, flat gap index, drop route/position, pickup
+    // route/position in the solution without the customer)
+    int ls, ls_ncand, ls_moved, ls_have, ls_bott, ls_rt;
+    int ls_c, ls_bz, ls_a, ls_ia, ls_b, ls_jb;
+    int ls_moves, ls_new_best;
+    long long ls_travel, ls_bt, ls_bflat;
 };
 
 struct AlnsTeam {
@@ -100,6 +108,7 @@ struct AlnsTeam {
     double T0, alpha, reheat, r, w_min;
     int stagnation_limit, tau, sigma1, sigma2, sigma3, q_min, q_max, iterations, repair_mask;
     int destroy_mask;        // bit 0 random, 1 worst, 2 Shaw, 3 cluster, 4 route, 5 critical path
+    int ls_pickup, ls_relocate;  // local-search periods in iterations (0 = off)
     unsigned long long key;  // RNG stream key
     int mode;                // 0 = search, 1 = one-customer matrix dump
     int dump_c;
@@ -129,6 +138,8 @@ struct AlnsTeam {
     int* scpair;               // [SC_CAP][SC_CAP]: makespan with both stops in two shortcut gaps of one customer
     int* trace;
     int* gains;                // [n+1]: removal gain z(cur) - z(cur - c), worst removal
+    int* lscand;               // [n+1]: local-search candidates of the current pass
+    int4* lsmask;              // [slots]: allowed drop routes, pickup routes, fixed drop gap (-1 any)
     int* dump_delta;
     int* dump_travel;
 };
@@ -1071,7 +1082,7 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
     //   col {gamma (SKIPV on a shortcut gap), B1, F, (dtP << 12) + gap}
     {
         AlnsCtl* ctl = t.ctl;
-        const int nrem = ctl->nrem, z = ctl->z_work;
+        const int nrem = ctl->nrem, z = ctl->z_work, lsm = ctl->ls;
         const long long total = static_cast<long long>(nrem) * G;
         for (long long e = tid; e < total; e += nthr) {
             const int ti = static_cast<int>(e / G), g = static_cast<int>(e - static_cast<long long>(ti) * G);
@@ -1090,12 +1101,20 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
             const int dxc = Dx(t, s, x, c), dcy = Dx(t, s, c, y), dcc = Dx(t, s, c, c);
             const int delta = dxc + dcy;
             const bool shortcut = delta < w;
-            t.vrow[e] = make_int4(shortcut ? SKIPV : max(z, Hx + delta + Ty), Hx + dxc + pc, Hx + delta,
+            // a local-search slot allows some drop gaps (rows) and pickup gaps
+            // (columns) only; the others read as excluded
+            bool rok = true, cok = true;
+            if (lsm) {
+                const int4 mk = t.lsmask[ti];
+                rok = ((static_cast<unsigned>(mk.x) >> r) & 1u) != 0 && (mk.z < 0 || mk.z == g);
+                cok = ((static_cast<unsigned>(mk.y) >> r) & 1u) != 0;
+            }
+            t.vrow[e] = make_int4(shortcut || !rok ? SKIPV : max(z, Hx + delta + Ty), Hx + dxc + pc, Hx + delta,
                                   static_cast<int>(static_cast<unsigned>(delta - w + (1 << 19)) << 12));
-            t.vadj[e] = make_int2(shortcut ? SKIPV : max(z, Hx + dxc + max(dcc, pc) + dcy + Ty),
+            t.vadj[e] = make_int2(shortcut || !(rok && cok) ? SKIPV : max(z, Hx + dxc + max(dcc, pc) + dcy + Ty),
                                   static_cast<int>((static_cast<unsigned>(dxc + dcc + dcy - w + (1 << 19)) << 12) |
                                                    static_cast<unsigned>(g)));
-            t.vcol[e] = make_int4(shortcut ? SKIPV : Hx + Ty + delta, dcy + Ty, delta + Ty,
+            t.vcol[e] = make_int4(shortcut || !cok ? SKIPV : Hx + Ty + delta, dcy + Ty, delta + Ty,
                                   static_cast<int>((static_cast<unsigned>(delta - w) << 12) + static_cast<unsigned>(g)));
         }
     }
@@ -1529,9 +1548,17 @@ __device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N,
     const bool dump = t.mode == 1;
     unsigned cnt = 0;
     auto loc = [&](int pos) { return pos >= 0 ? (s.sW[pos] & PACK_MASK) >> 1 : 0; };
+    // a local-search slot's mask (see the gap phase)
+    const int lsm = ctl->ls;
+    const int4 mk = lsm ? t.lsmask[ti] : make_int4(-1, -1, -1, 0);
+    auto allowed = [&](int row, int col) {
+        return ((static_cast<unsigned>(mk.x) >> t.groute[row]) & 1u) != 0 && (mk.z < 0 || mk.z == row) &&
+               ((static_cast<unsigned>(mk.y) >> t.groute[col]) & 1u) != 0;
+    };
     for (int k = tid; k < G && z1 != 0x7fffffff; k += blockDim.x) {
         if (k == g || t.sc[scrow + k]) continue;              // both gaps shortcuts: below / elsewhere
         const int row = as_col ? k : g, col = as_col ? g : k;
+        if (lsm && !allowed(row, col)) continue;
         const int a = t.groute[row], i = t.gpos[row], b = t.groute[col], j = t.gpos[col];
         const long long idx = static_cast<long long>(row) * G + col;
         if (a == b && j < i) {
@@ -1574,6 +1601,7 @@ __device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N,
             while (todo) {
                 const int col = k0 + __ffs(todo) - 1;
                 todo &= todo - 1;
+                if (lsm && !allowed(g, col)) continue;
                 const int a = ga, i = gi, b = t.groute[col], j = t.gpos[col];
                 const long long idx = static_cast<long long>(g) * G + col;
                 if (a == b && j < i) {
@@ -1613,6 +1641,18 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
     const int nwalks = gap_walk_items(t);
     bool walks_seen = false;
     int* slot = s.misc;
+    // local search: tiles that hold no allowed entry are skipped (pickup
+    // repositioning: one row of tiles; relocation: tiles whose rows and
+    // columns share no route)
+    const int lsm = ctl->ls, ls_rt = ctl->ls_rt;
+    auto ls_skip = [&](int rt, int ct) {
+        if (lsm == 1) return rt != ls_rt;
+        if (lsm == 2) {
+            const int r0 = rt * TR, r1 = min(G, r0 + TR) - 1, c0 = ct * TC, c1 = min(G, c0 + TC) - 1;
+            return t.groute[r1] < t.groute[c0] || t.groute[c1] < t.groute[r0];
+        }
+        return false;
+    };
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) slot[0] = atomicAdd(&ctl->work_counter, 1);
@@ -1620,7 +1660,8 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
         const int item = slot[0];
         if (item >= total) break;
         if (item < tiles) {
-            matrix_tile(t, s, item / CT, item - (item / CT) * CT, N, G);
+            const int rt = item / CT, ct = item - rt * CT;
+            if (!ls_skip(rt, ct)) matrix_tile(t, s, rt, ct, N, G);
         } else {
             if (!walks_seen) {
                 // the shortcut simulations, still running in other CTAs, must be done (bounded wait)
@@ -1644,7 +1685,37 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
     }
 }
 
-// Rank 0: per-customer argmin, greedy / regret-2 choice, apply to W.
+// Insert customer c into the staged solution (s.sW, s.sWoff): its drop at
+// position ia of route a, its pickup at position jb of route b (positions in
+// the staged solution; on one route jb >= ia and the pickup follows the drop).
+// Writes Wn / Won; all threads of the block, element-parallel: old op i of
+// route v moves right by the insertions that precede it.
+__device__ void insert_staged(const AlnsTeam& t, const Smem& s, int c, int a, int ia, int b, int jb, int* Wn,
+                              int* Won) {
+    const int m = t.m, N = s.sWoff[m];
+    for (int p = threadIdx.x; p < N; p += blockDim.x) {
+        int lo = 0, hi = m;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s.sWoff[mid] <= p) lo = mid; else hi = mid;
+        }
+        const int v = lo, i = p - s.sWoff[v];
+        const int shift = (a < v ? 1 : 0) + (b < v ? 1 : 0) + (v == a && i >= ia ? 1 : 0) + (v == b && i >= jb ? 1 : 0);
+        Wn[p + shift] = s.sW[p] & PACK_MASK;
+    }
+    if (threadIdx.x == 0) {
+        const int base_a = s.sWoff[a] + (b < a ? 1 : 0);
+        Wn[base_a + ia] = 2 * c;
+        const int base_b = s.sWoff[b] + (a < b ? 1 : 0);
+        Wn[base_b + jb + (a == b ? 1 : 0)] = 2 * c + 1;
+    }
+    if (threadIdx.x <= m) {
+        const int v = threadIdx.x;
+        Won[v] = s.sWoff[v] + (a < v ? 1 : 0) + (b < v ? 1 : 0);
+    }
+}
+
+// Rank 0: per-customer argmin, greedy / regret-k choice, apply to W.
 __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
     AlnsCtl* ctl = t.ctl;
     const int m = t.m, N = s.sWoff[m], G = N + m, nrem = ctl->nrem;
@@ -1722,33 +1793,11 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
     }
     __syncthreads();
     if (ctl->repair_fail) return;
-    // apply, element-parallel from the staged copy of W: old op i of route v
-    // moves right by the insertions that precede it
+    // apply to the other W buffer
     const int pick = ctl->pick_t, row = ctl->pick_row, col = ctl->pick_col;
     const int c = t.rem[pick];
     const int a = t.groute[row], ia = t.gpos[row], b = t.groute[col], jb = t.gpos[col];
-    int* Wn = t.W_ops[ctl->wsel ^ 1];
-    int* Won = t.W_off[ctl->wsel ^ 1];
-    for (int p = threadIdx.x; p < N; p += blockDim.x) {
-        int lo = 0, hi = m;
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s.sWoff[mid] <= p) lo = mid; else hi = mid;
-        }
-        const int v = lo, i = p - s.sWoff[v];
-        const int shift = (a < v ? 1 : 0) + (b < v ? 1 : 0) + (v == a && i >= ia ? 1 : 0) + (v == b && i >= jb ? 1 : 0);
-        Wn[p + shift] = s.sW[p] & PACK_MASK;
-    }
-    if (threadIdx.x == 0) {
-        const int base_a = s.sWoff[a] + (b < a ? 1 : 0);
-        Wn[base_a + ia] = 2 * c;
-        const int base_b = s.sWoff[b] + (a < b ? 1 : 0);
-        Wn[base_b + jb + (a == b ? 1 : 0)] = 2 * c + 1;
-    }
-    if (threadIdx.x <= m) {
-        const int v = threadIdx.x;
-        Won[v] = s.sWoff[v] + (a < v ? 1 : 0) + (b < v ? 1 : 0);
-    }
+    insert_staged(t, s, c, a, ia, b, jb, t.W_ops[ctl->wsel ^ 1], t.W_off[ctl->wsel ^ 1]);
     if (threadIdx.x == 0) {
         // the next step updates the longest-path table incrementally unless a
         // gap of this insertion was a shortcut for c
@@ -2033,9 +2082,54 @@ __device__ void select_structured(const AlnsTeam& t, const Smem& s) {
 
 // Rank 0: the destroy step (operator and q drawn at the end of the previous
 // iteration), W = cur - removed.
+// W[0] = the current solution without the customers flagged in s.flags:
+// block-wide scan of the kept ops.  All threads of the block.
+__device__ void build_W_from_cur(const AlnsTeam& t, const Smem& s) {
+    const int m = t.m, two_n = 2 * t.n;
+    const int per = (two_n + blockDim.x - 1) / blockDim.x;
+    const int k0 = threadIdx.x * per, k1 = min(two_n, k0 + per);
+    int cnt = 0;
+    for (int k = k0; k < k1; ++k) cnt += s.flags[t.cur_ops[k] >> 1] ? 0 : 1;
+    int* wsum = s.misc;                        // [ALNS_WARPS]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL_MASK, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncthreads();                           // wsum is free
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int before = 0, kept_total = 0;
+    for (int w = 0; w < ALNS_WARPS; ++w) {
+        before += w < warp ? wsum[w] : 0;
+        kept_total += wsum[w];
+    }
+    const int base_pos = before + incl - cnt;
+    int pos = base_pos;
+    int* Wn = t.W_ops[0];
+    for (int k = k0; k < k1; ++k) {
+        const int o = t.cur_ops[k];
+        if (!s.flags[o >> 1]) Wn[pos++] = o;
+    }
+    // route offsets: the kept-op count before each route start, taken from the
+    // scan by the thread whose range holds that start
+    for (int v = 0; v <= m; ++v) {
+        const int ov = t.cur_off[v];
+        if (ov >= k0 && ov < k1) {
+            int kept = base_pos;
+            for (int k = k0; k < ov; ++k) kept += s.flags[t.cur_ops[k] >> 1] ? 0 : 1;
+            t.W_off[0][v] = kept;
+        } else if (ov == two_n && threadIdx.x == 0) {
+            t.W_off[0][v] = kept_total;
+        }
+    }
+    __syncthreads();
+}
+
 __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
     AlnsCtl* ctl = t.ctl;
-    const int n = t.n, m = t.m, two_n = 2 * n;
+    const int n = t.n;
     int* perm = s.rdy;                         // [n], shared memory
     for (int k = threadIdx.x; k < n; k += blockDim.x) perm[k] = k + 1;
     for (int c = threadIdx.x; c <= n; c += blockDim.x) s.flags[c] = 0;
@@ -2077,42 +2171,7 @@ __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
         }
         if (lane == 0) ctl->nrem = w;
     }
-    // W = cur without the removed customers: block-wide scan of the kept flags
-    const int per = (two_n + blockDim.x - 1) / blockDim.x;
-    const int k0 = threadIdx.x * per, k1 = min(two_n, k0 + per);
-    int cnt = 0;
-    for (int k = k0; k < k1; ++k) cnt += s.flags[t.cur_ops[k] >> 1] ? 0 : 1;
-    int* wsum = s.misc;                        // [ALNS_WARPS]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int incl = cnt;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL_MASK, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    int before = 0;
-    for (int w = 0; w < warp; ++w) before += wsum[w];
-    const int base_pos = before + incl - cnt;
-    int pos = base_pos;
-    int* Wn = t.W_ops[0];
-    for (int k = k0; k < k1; ++k) {
-        const int o = t.cur_ops[k];
-        if (!s.flags[o >> 1]) Wn[pos++] = o;
-    }
-    // route offsets: the kept-op count before each route start, taken from the
-    // scan by the thread whose range holds that start
-    for (int v = 0; v <= m; ++v) {
-        const int ov = t.cur_off[v];
-        if (ov >= k0 && ov < k1) {
-            int kept = base_pos;
-            for (int k = k0; k < ov; ++k) kept += s.flags[t.cur_ops[k] >> 1] ? 0 : 1;
-            t.W_off[0][v] = kept;
-        } else if (ov == two_n && threadIdx.x == 0) {
-            t.W_off[0][v] = two_n - 2 * ctl->q;
-        }
-    }
-    __syncthreads();
+    build_W_from_cur(t, s);
 }
 
 // Rank 0: evaluate the repaired W and apply Algorithm 1's acceptance, cooling,
@@ -2224,6 +2283,264 @@ __device__ void phase_end(const AlnsTeam& t, const Smem& s, bool first) {
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// periodic local search (Section 4.2.6), on the current solution
+// ---------------------------------------------------------------------------
+// Each candidate customer c runs one team step (prep, gaps, shortcut walks,
+// matrix) on W = cur - c with one or more masked slots for c: pickup
+// repositioning has one slot whose only drop gap is c's own dropoff place;
+// relocation has one slot per vehicle v other than the bottleneck, with both
+// gaps on v.  Taking c out can leave one of its old routes over capacity; the
+// matrix judges the receiving routes only, so a slot is kept only if every
+// such route is one it writes to.  The pass's best move is
+// the least (makespan, travel, customer, flat gap index) over all slots; it
+// is applied if it lowers the makespan.
+enum { LS_PICKUP = 1, LS_RELOCATE = 2 };
+
+// Rank 0: the candidates of one pass, in ascending id.  Pickup repositioning:
+// customers whose pickup is on a vehicle returning at 95% of the makespan or
+// later (20 ret >= 19 z); relocation: customers with an op on the bottleneck
+// vehicle (latest return, lower index on ties).
+__device__ __noinline__ void ls_candidates(const AlnsTeam& t, const Smem& s, int mode) {
+    AlnsCtl* ctl = t.ctl;
+    const int n = t.n, m = t.m, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    stage_ops(t, s, t.cur_ops, t.cur_off);
+    int* ret = s.misc + 32;                    // [32] return time per route
+    for (int c = tid; c <= n; c += blockDim.x) s.flags[c] = 0;
+    if (warp == 0) {
+        int z;
+        unsigned st;
+        walk_depot(t, s, s.rdy, true, &z, &st);
+        __syncwarp();
+        int rv = 0;
+        if (lane < m && s.sWoff[lane + 1] > s.sWoff[lane]) {
+            const int last = s.sWoff[lane + 1] - 1;
+            rv = t.H[last] + Dx(t, s, (s.sW[last] & PACK_MASK) >> 1, 0);
+        }
+        ret[lane] = rv;
+        __syncwarp();
+        if (lane == 0) {
+            int b = 0;
+            for (int v = 1; v < m; ++v)
+                if (ret[v] > ret[b]) b = v;
+            ctl->ls_bott = b;
+            ctl->ls_have = 0;
+        }
+    }
+    __syncthreads();
+    const long long z = ctl->z_cur;
+    const int bott = ctl->ls_bott, N = s.sWoff[m];
+    for (int k = tid; k < N; k += blockDim.x) {
+        int lo = 0, hi = m;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s.sWoff[mid] <= k) lo = mid; else hi = mid;
+        }
+        const int o = s.sW[k] & PACK_MASK;
+        const bool cand = mode == LS_PICKUP ? ((o & 1) && 20ll * ret[lo] >= 19ll * z) : lo == bott;
+        if (cand) s.flags[o >> 1] = 1;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int w = 0;
+        for (int c0 = 1; c0 <= n; c0 += 32) {
+            const int c = c0 + lane;
+            const bool r = c <= n && s.flags[c];
+            const unsigned bal = __ballot_sync(FULL_MASK, r);
+            if (r) t.lscand[w + __popc(bal & ((1u << lane) - 1u))] = c;
+            w += __popc(bal);
+        }
+        if (lane == 0) ctl->ls_ncand = w;
+    }
+    __syncthreads();
+}
+
+// Rank 0: W = cur - c for candidate k, the routes of W over capacity, its
+// travel, and the slots with their masks.
+__device__ __noinline__ void ls_setup(const AlnsTeam& t, const Smem& s, int mode, int k) {
+    AlnsCtl* ctl = t.ctl;
+    const int n = t.n, m = t.m, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c = t.lscand[k];
+    int* sh = s.misc + 32;                     // [0] drop position of c in cur, [1] bad-route mask
+    unsigned long long* travel = reinterpret_cast<unsigned long long*>(s.misc + 40);
+    for (int x = tid; x <= n; x += blockDim.x) s.flags[x] = x == c ? 1 : 0;
+    for (int q = tid; q < 2 * n; q += blockDim.x)
+        if (t.cur_ops[q] == 2 * c) sh[0] = q;
+    if (tid == 0) {
+        sh[1] = 0;
+        *travel = 0ull;
+        ctl->wsel = 0;
+    }
+    __syncthreads();
+    const int pdrop = sh[0];
+    build_W_from_cur(t, s);
+    stage_W(t, s);
+    __syncthreads();
+    // per route: stock range of W (the minimal or the full start load) and travel
+    for (int r = warp; r < m; r += ALNS_WARPS) {
+        const int st = s.sWoff[r], en = s.sWoff[r + 1];
+        int carry = 0, mn = 0, mx = 0;
+        long long tr = 0;
+        for (int base = st; base < en; base += 32) {
+            const int q = base + lane;
+            const bool in = q < en;
+            const int w = in ? s.sW[q] : 0;
+            int v = in ? (((w & PACK_MASK) & 1) ? 1 : -1) : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL_MASK, v, o);
+                if (lane >= o) v += y;
+            }
+            if (in) {
+                mn = min(mn, carry + v);
+                mx = max(mx, carry + v);
+                tr += w >> PACK_SHIFT;
+            }
+            carry += __shfl_sync(FULL_MASK, v, 31);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            mn = min(mn, __shfl_xor_sync(FULL_MASK, mn, o));
+            mx = max(mx, __shfl_xor_sync(FULL_MASK, mx, o));
+            tr += __shfl_xor_sync(FULL_MASK, tr, o);
+        }
+        if (lane == 0) {
+            int load = 0;
+            if (!cap_ok(t, mn, mx, load)) atomicOr(&sh[1], 1 << r);
+            if (en > st) tr += Dx(t, s, (s.sW[en - 1] & PACK_MASK) >> 1, 0);
+            atomicAdd(travel, static_cast<unsigned long long>(tr));
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned bad = static_cast<unsigned>(sh[1]);
+        const unsigned all = m == 32 ? 0xffffffffu : (1u << m) - 1u;
+        int ns = 0;
+        if (mode == LS_PICKUP) {
+            int a = 0;
+            for (int v = 0; v < m; ++v)
+                if (t.cur_off[v] <= pdrop) a = v;
+            const int ia = pdrop - t.cur_off[a];
+            const int g1 = s.sWoff[a] + a + ia;
+            const unsigned rest = bad & ~(1u << a);
+            if (__popc(rest) <= 1) {
+                t.lsmask[0] = make_int4(static_cast<int>(1u << a), static_cast<int>(rest ? rest : all), g1, 0);
+                t.rem[0] = c;
+                ns = 1;
+            }
+            ctl->ls_rt = g1 / TR;
+        } else {
+            for (int v = 0; v < m; ++v) {
+                if (v == ctl->ls_bott || (bad & ~(1u << v)) != 0u) continue;
+                t.lsmask[ns] = make_int4(static_cast<int>(1u << v), static_cast<int>(1u << v), -1, 0);
+                t.rem[ns] = c;
+                ++ns;
+            }
+            ctl->ls_rt = -1;
+        }
+        ctl->nrem = ns;
+        ctl->ls = mode;
+        ctl->ls_travel = static_cast<long long>(*travel);
+        ctl->repair_fail = 0;
+        ctl->n_short = 0;
+        ctl->work_counter = 0;
+        ctl->incr = 0;
+        ctl->sum_load = 0;
+        ctl->walks_done = 0;
+    }
+    __syncthreads();
+}
+
+// Rank 0 after a candidate's matrix: its best entry over the slots against
+// the pass's best move so far.
+__device__ __noinline__ void ls_collect(const AlnsTeam& t, const Smem& s) {
+    AlnsCtl* ctl = t.ctl;
+    const int m = t.m, N = s.sWoff[m], G = N + m, ns = ctl->nrem, lane = threadIdx.x & 31;
+    if ((threadIdx.x >> 5) == 0) {
+        for (int ti = 0; ti < ns; ++ti) {
+            unsigned long long bv = lane < m ? t.rkeys[ti * 32 + lane] : KEY_NONE;
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(FULL_MASK, bv, o);
+                bv = other < bv ? other : bv;
+            }
+            if (lane == 0 && bv != KEY_NONE) {
+                const int row = static_cast<int>(bv & 0xFFF);
+                const int col = static_cast<int>(t.keys[static_cast<long long>(ti) * G + row] & 0xFFF);
+                const int dz = static_cast<int>(static_cast<unsigned>(bv >> 32) ^ 0x80000000u);
+                const int dt = static_cast<int>((bv >> 12) & 0xFFFFFull) - (1 << 19);
+                const int zn = ctl->z_work + dz;
+                const long long tn = ctl->ls_travel + dt;
+                const long long flat = static_cast<long long>(row) * G + col;
+                const int c = t.rem[ti];
+                bool better = !ctl->ls_have;
+                if (!better) {
+                    if (zn != ctl->ls_bz) better = zn < ctl->ls_bz;
+                    else if (tn != ctl->ls_bt) better = tn < ctl->ls_bt;
+                    else if (c != ctl->ls_c) better = c < ctl->ls_c;
+                    else better = flat < ctl->ls_bflat;
+                }
+                if (better) {
+                    ctl->ls_have = 1;
+                    ctl->ls_c = c;
+                    ctl->ls_bz = zn;
+                    ctl->ls_bt = tn;
+                    ctl->ls_bflat = flat;
+                    ctl->ls_a = t.groute[row];
+                    ctl->ls_ia = t.gpos[row];
+                    ctl->ls_b = t.groute[col];
+                    ctl->ls_jb = t.gpos[col];
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Rank 0 at the end of a pass: apply the best move if it lowers the makespan.
+__device__ __noinline__ void ls_apply(const AlnsTeam& t, const Smem& s) {
+    AlnsCtl* ctl = t.ctl;
+    const bool go = ctl->ls_have && ctl->ls_bz < ctl->z_cur;
+    if (go) {
+        const int c = ctl->ls_c;
+        for (int x = threadIdx.x; x <= t.n; x += blockDim.x) s.flags[x] = x == c ? 1 : 0;
+        if (threadIdx.x == 0) ctl->wsel = 0;
+        __syncthreads();
+        build_W_from_cur(t, s);
+        stage_W(t, s);
+        __syncthreads();
+        insert_staged(t, s, c, ctl->ls_a, ctl->ls_ia, ctl->ls_b, ctl->ls_jb, t.cur_ops, t.cur_off);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ctl->ls_moved = go ? 1 : 0;
+        ctl->ls = 0;
+        if (go) {
+            ctl->z_cur = ctl->ls_bz;
+            ctl->ls_moves += 1;
+        }
+    }
+    __syncthreads();
+}
+
+// Rank 0 after the local search of iteration it: the trace and the best solution.
+__device__ __noinline__ void ls_finish(const AlnsTeam& t, const Smem& s, int it) {
+    AlnsCtl* ctl = t.ctl;
+    int* flag = s.misc;
+    if (threadIdx.x == 0) {
+        flag[0] = ctl->z_cur < ctl->z_best ? 1 : 0;
+        if (flag[0]) {
+            ctl->z_best = ctl->z_cur;
+            ctl->stagnation = 0;
+            ctl->ls_new_best += 1;
+        }
+        if (t.trace) t.trace[it - 1] = ctl->z_cur;
+    }
+    __syncthreads();
+    if (flag[0]) {
+        for (int k = threadIdx.x; k < 2 * t.n; k += blockDim.x) t.best_ops[k] = t.cur_ops[k];
+        for (int v = threadIdx.x; v <= t.m; v += blockDim.x) t.best_off[v] = t.cur_off[v];
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, int team_blocks) {
     extern __shared__ __align__(16) int smem_alns[];
     __shared__ AlnsTeam team_s;
@@ -2319,6 +2636,38 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
         if (rank == 0) phase_end(t, s, false);
         if (!team_barrier(ctl, team_blocks, gen)) return;
         mark(5);
+        const int lsm = (t.ls_pickup > 0 && it % t.ls_pickup == 0 ? LS_PICKUP : 0) |
+                        (t.ls_relocate > 0 && it % t.ls_relocate == 0 ? LS_RELOCATE : 0);
+        if (lsm) {
+            for (int mode = LS_PICKUP; mode <= LS_RELOCATE; ++mode) {
+                if (!(lsm & mode)) continue;
+                for (int pass = 0; pass < 3; ++pass) {
+                    if (rank == 0) ls_candidates(t, s, mode);
+                    if (!team_barrier(ctl, team_blocks, gen)) return;
+                    const int ncand = *reinterpret_cast<volatile int*>(&ctl->ls_ncand);
+                    for (int k = 0; k < ncand; ++k) {
+                        if (rank == 0) ls_setup(t, s, mode, k);
+                        if (!team_barrier(ctl, team_blocks, gen)) return;
+                        if (*reinterpret_cast<volatile int*>(&ctl->nrem) == 0) continue;
+                        phase_prep(t, s, rank, team_blocks, false);
+                        if (!team_barrier(ctl, team_blocks, gen)) return;
+                        phase_gaps(t, s, rank, team_blocks);
+                        team_arrive(ctl, team_blocks, gen);
+                        gap_walks(t, s, rank, team_blocks);
+                        if (!team_wait(ctl, team_blocks, gen)) return;
+                        phase_matrix(t, s);
+                        if (!team_barrier(ctl, team_blocks, gen)) return;
+                        if (rank == 0) ls_collect(t, s);
+                    }
+                    if (rank == 0) ls_apply(t, s);
+                    if (!team_barrier(ctl, team_blocks, gen)) return;
+                    if (!*reinterpret_cast<volatile int*>(&ctl->ls_moved)) break;
+                }
+            }
+            if (rank == 0) ls_finish(t, s, it);
+            if (!team_barrier(ctl, team_blocks, gen)) return;
+            mark(6);
+        }
     }
 }
 
@@ -2346,7 +2695,7 @@ static size_t team_bytes(int n, int m, int qmax, int iterations, bool dump) {
     add(1, sizeof(AlnsCtl));
     add(N, 4); add(m + 1, 4); add(N, 4); add(m + 1, 4);
     add(N + 2, 4); add(m + 1, 4); add(N + 2, 4); add(m + 1, 4);
-    add(n + 1, 4); add(n + 1, 4);
+    add(std::max<size_t>(n + 1, qmax), 4); add(n + 1, 4);
     add(N, 4); add(N, 4); add(N * N, 4);
     add(N, 4); add(N, 4); add(N * N, 4);
     for (int i = 0; i < 5; ++i) add(N, 4);
@@ -2365,6 +2714,7 @@ static size_t team_bytes(int n, int m, int qmax, int iterations, bool dump) {
     add(static_cast<size_t>(SC_CAP) * SC_CAP, 4);
     add(std::max(iterations, 1), 4);
     add(n + 1, 4);
+    add(n + 1, 4); add(static_cast<size_t>(qmax), 16);
     if (dump) { add(G * G, 4); add(G * G, 4); }
     return w;
 }
@@ -2378,7 +2728,7 @@ static void carve_team(AlnsTeam& t, DevBuf& B, int n, int m, int qmax, int itera
     t.best_ops = B.take<int>(N); t.best_off = B.take<int>(m + 1);
     t.W_ops[0] = B.take<int>(N + 2); t.W_off[0] = B.take<int>(m + 1);
     t.W_ops[1] = B.take<int>(N + 2); t.W_off[1] = B.take<int>(m + 1);
-    t.rem = B.take<int>(n + 1); t.perm = B.take<int>(n + 1);
+    t.rem = B.take<int>(std::max(n + 1, qmax)); t.perm = B.take<int>(n + 1);
     t.H = B.take<int>(N); t.T = B.take<int>(N); t.Ms = B.take<int>(N * N);
     t.H2 = B.take<int>(N); t.T2 = B.take<int>(N); t.Ms2 = B.take<int>(N * N);
     t.S_ = B.take<int>(N); t.PMINp = B.take<int>(N); t.PMAXp = B.take<int>(N);
@@ -2402,6 +2752,8 @@ static void carve_team(AlnsTeam& t, DevBuf& B, int n, int m, int qmax, int itera
     t.scpair = B.take<int>(static_cast<size_t>(SC_CAP) * SC_CAP);
     t.trace = B.take<int>(std::max(iterations, 1));
     t.gains = B.take<int>(n + 1);
+    t.lscand = B.take<int>(n + 1);
+    t.lsmask = B.take<int4>(static_cast<size_t>(qmax));
     t.dump_delta = dump ? B.take<int>(G * G) : nullptr;
     t.dump_travel = dump ? B.take<int>(G * G) : nullptr;
 }
@@ -2409,13 +2761,16 @@ static void carve_team(AlnsTeam& t, DevBuf& B, int n, int m, int qmax, int itera
 bool coords_exact_small(const vrprpd_instance* I);
 
 // Rows of the per-customer buffers: a route removal takes a whole route, so
-// with that operator on, up to n customers wait for reinsertion at once.
-int alns_removal_cap(int n, int qmax, int destroy_mask) {
-    return (destroy_mask & (1 << D_ROUTE)) ? n : qmax;
+// with that operator on, up to n customers wait for reinsertion at once; the
+// relocation local search runs up to m - 1 slots for one customer.
+int alns_row_cap(int n, int m, int qmax, const vrprpd_alns_params* P) {
+    int cap = (P->destroy_mask & (1 << D_ROUTE)) ? n : qmax;
+    if (P->ls_relocate_every > 0) cap = std::max(cap, m);
+    return std::max(cap, 1);
 }
 
-size_t alns_device_bytes(int n, int m, int qmax, int destroy_mask, int iterations) {
-    return team_bytes(n, m, alns_removal_cap(n, qmax, destroy_mask), iterations, false) + sizeof(AlnsTeam) + 8192;
+size_t alns_device_bytes(int n, int m, int qmax, const vrprpd_alns_params* P, int iterations) {
+    return team_bytes(n, m, alns_row_cap(n, m, qmax, P), iterations, false) + sizeof(AlnsTeam) + 8192;
 }
 
 bool alns_supported(const vrprpd_instance* I, std::string* why) {
@@ -2483,6 +2838,8 @@ extern "C" void vrprpd_alns_params_default(vrprpd_alns_params* P) {
     P->repair_mask = 3;
     P->team_blocks = 0;
     P->destroy_mask = 1;
+    P->ls_pickup_every = 200;
+    P->ls_relocate_every = 500;
 }
 
 // exact angular order around the depot: half plane, then cross product, then id
@@ -2555,7 +2912,7 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     VRP_CHECK(iters >= 0 && iters <= (1 << 24), VRPRPD_EINVAL, "iterations out of range");
     VRP_CHECK(P->tau >= 1, VRPRPD_EINVAL, "tau must be >= 1");
     const bool dump = mode == 1;
-    const int qcap = dump ? 1 : alns_removal_cap(n, qmax, P->destroy_mask & 63);
+    const int qcap = dump ? 1 : alns_row_cap(n, m, qmax, P);
     DevBuf B;
     B.cap = team_bytes(n, m, qcap, iters, dump) + 4096;
     VRP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&B.base), B.cap, stream));
@@ -2583,6 +2940,10 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     t.iterations = iters;
     t.repair_mask = P->repair_mask & 15;
     t.destroy_mask = P->destroy_mask & 63;
+    VRP_CHECK(P->ls_pickup_every >= 0 && P->ls_relocate_every >= 0, VRPRPD_EINVAL,
+              "local-search periods must be >= 0 (0 = off)");
+    t.ls_pickup = dump ? 0 : P->ls_pickup_every;
+    t.ls_relocate = dump ? 0 : P->ls_relocate_every;
     VRP_CHECK(t.destroy_mask != 0, VRPRPD_EINVAL, "destroy_mask enables no destroy operator");
     VRP_CHECK(t.repair_mask != 0, VRPRPD_EINVAL, "repair_mask enables no repair operator");
     t.key = stream_key(seed, RNG_STREAM_ALNS);
@@ -2711,6 +3072,9 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
         for (int i = 0; i < 6; ++i) stats->phase_ms[i] = static_cast<double>(out.phase_ns[i]) * 1e-6;
         stats->incremental_steps = static_cast<int64_t>(out.steps_incr);
         stats->full_steps = static_cast<int64_t>(out.steps_full);
+        stats->ls_moves = out.ls_moves;
+        stats->ls_new_best = out.ls_new_best;
+        stats->ls_ms = static_cast<double>(out.phase_ns[6]) * 1e-6;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     cleanup();

@@ -20,7 +20,7 @@
 #include "internal.h"
 
 namespace vrp {
-size_t alns_device_bytes(int n, int m, int qmax, int destroy_mask, int iterations);
+size_t alns_device_bytes(int n, int m, int qmax, const vrprpd_alns_params* P, int iterations);
 }  // namespace vrp
 
 struct vrprpd_server {
@@ -64,7 +64,7 @@ static size_t request_bytes(const vrprpd_request& r) {
     int qmax = std::max(4, static_cast<int>(static_cast<long long>(r.n) * 5 / 100));
     if (r.alns.q_max > 0) qmax = r.alns.q_max;
     qmax = std::min(qmax, r.n);
-    const size_t alns = r.alns.iterations > 0 ? alns_device_bytes(r.n, r.m, qmax, r.alns.destroy_mask, r.alns.iterations) : 0;
+    const size_t alns = r.alns.iterations > 0 ? alns_device_bytes(r.n, r.m, qmax, &r.alns, r.alns.iterations) : 0;
     const size_t L = r.brkga.layout == VRPRPD_LAYOUT_HINTS ? 4ull * r.n : 2ull * r.n + r.m;
     const size_t pop = static_cast<size_t>(std::max(r.brkga.pop, 0));
     const size_t brkga = r.brkga.generations > 0

@@ -101,21 +101,23 @@ def test_initial_solution_matches_oracle(vrp):
         assert oracle.evaluate(oi, go, gf)[1] == 0
 
 
-def run_both(vrp, w, iters, seed, q=(0, 0), mask=3, team_blocks=0, dmask=1):
-    inst = vrp.Instance.from_workload(w)
-    oi = oracle.OracleInstance.from_workload(w)
+def run_both(vrp, w, iters, seed, q=(0, 0), mask=3, team_blocks=0, dmask=1, ls=(200, 500), load_full=False):
+    inst = vrp.Instance.from_workload(w, load_full=load_full)
+    oi = oracle.OracleInstance.from_workload(w, load_full=load_full)
     init = oracle.initial_solution(oi, w.coords)
-    g = vrp.alns_run(inst, vrp.alns_params(iters, q[0], q[1], mask, team_blocks, destroy_mask=dmask),
+    g = vrp.alns_run(inst, vrp.alns_params(iters, q[0], q[1], mask, team_blocks, destroy_mask=dmask,
+                                           ls_pickup_every=ls[0], ls_relocate_every=ls[1]),
                      seed=seed, init=init)
-    o = oracle.alns_run(oi, init[0], init[1], oracle.alns_params(iters, q[0], q[1], mask, destroy_mask=dmask),
-                        seed)
+    o = oracle.alns_run(oi, init[0], init[1], oracle.alns_params(iters, q[0], q[1], mask, destroy_mask=dmask,
+                                                                 ls_pickup_every=ls[0],
+                                                                 ls_relocate_every=ls[1]), seed)
     return inst, oi, g, o
 
 
 def assert_same_run(oi, g, o):
     assert np.array_equal(g["trace"], o["trace"]), np.nonzero(g["trace"] != o["trace"])[0][:5]
     gs, os_ = g["stats"], o["stats"]
-    for f in ("accepted", "improved", "new_best", "reheats", "rejected_infeasible"):
+    for f in ("accepted", "improved", "new_best", "reheats", "rejected_infeasible", "ls_moves", "ls_new_best"):
         assert getattr(gs, f) == getattr(os_, f), f
     assert gs.z_best == os_.z_best and g["z_best"] == os_.z_best
     assert gs.T_final == os_.T_final
@@ -254,4 +256,42 @@ def test_alns_all_operators_team_blocks_agree(vrp):
     assert np.array_equal(runs[0]["trace"], runs[1]["trace"])
     assert np.array_equal(runs[0]["best_ops"], runs[1]["best_ops"])
     assert list(runs[0]["stats"].w_destroy) == list(runs[1]["stats"].w_destroy)
+    assert oracle.evaluate(oi, runs[0]["best_ops"], runs[0]["best_off"]) == (runs[0]["z_best"], 0)
+
+
+@pytest.mark.parametrize("ls", [(3, 0), (0, 4), (3, 5)])
+def test_alns_local_search(vrp, ls):
+    # pickup repositioning and cross-agent relocation (Section 4.2.6) at short
+    # periods so that they run many times
+    w = workloads.make_instance(24, 3, 6, 4, "5x", seed=6)
+    _, oi, g, o = run_both(vrp, w, 45, seed=3, ls=ls)
+    assert_same_run(oi, g, o)
+    assert g["stats"].ls_moves > 0
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_alns_local_search_all_operators_medium(vrp, seed):
+    w = workloads.make_instance(40, 5, 10, 5, "2x", "clustered", seed=20 + seed)
+    _, oi, g, o = run_both(vrp, w, 20, seed=seed, q=(3, 8), mask=15, dmask=63, ls=(4, 6))
+    assert_same_run(oi, g, o)
+
+
+def test_alns_local_search_load_full_tight(vrp):
+    # the paper's fleet with every vehicle leaving full: capacity binds, so
+    # removing a customer can leave its old route infeasible
+    w = workloads.make_paper_instance(30, "1R20", seed=4)
+    _, oi, g, o = run_both(vrp, w, 30, seed=1, q=(3, 6), dmask=63, ls=(2, 3), load_full=True)
+    assert_same_run(oi, g, o)
+
+
+def test_alns_local_search_team_blocks_agree(vrp):
+    w = workloads.make_instance(100, 4, 10, 5, "2x", seed=2)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    init = oracle.initial_solution(oi, w.coords)
+    runs = [vrp.alns_run(inst, vrp.alns_params(10, 5, 10, 3, tb, ls_pickup_every=3, ls_relocate_every=5),
+                         seed=4, init=init) for tb in (1, 9)]
+    assert np.array_equal(runs[0]["trace"], runs[1]["trace"])
+    assert np.array_equal(runs[0]["best_ops"], runs[1]["best_ops"])
+    assert runs[0]["stats"].ls_moves == runs[1]["stats"].ls_moves
     assert oracle.evaluate(oi, runs[0]["best_ops"], runs[0]["best_off"]) == (runs[0]["z_best"], 0)
