@@ -95,6 +95,7 @@ def lib():
             L.oracle_sp_closure.argtypes = [i32p, C.c_int32, i64p]
             L.oracle_coordination.argtypes = [C.POINTER(Inst), i32p, i32p, i32p, i32p]
             L.oracle_coordination.restype = C.c_uint32
+            L.oracle_seed_chromosome.argtypes = [C.POINTER(Inst), C.c_int32, C.c_int32, f32p]
             L.oracle_local_search.argtypes = [C.POINTER(Inst), C.c_int32, C.c_int32, i32p, i32p, i32p]
             L.oracle_bruteforce.argtypes = [C.POINTER(Inst), i32p, i32p]
             L.oracle_bruteforce.restype = C.c_int64
@@ -346,6 +347,16 @@ def local_search(I, mode, ops, off, passes=3):
     if mv < 0:
         raise ValueError("local search needs a feasible complete solution and mode 1 or 2")
     return mv, int(z[0]), ops, off
+
+
+SEED_NN, SEED_LB, SEED_SPT = 0, 1, 2
+
+
+def seed_chromosome(I, h, layout=LAYOUT_VKEYS):
+    """Construction seed h of the BRKGA warm start (Section 4.4.4)."""
+    keys = np.zeros(key_length(I, layout), np.float32)
+    lib().oracle_seed_chromosome(C.byref(I.c), h, layout, _p(keys, C.c_float))
+    return keys
 
 
 def destroy(I, op, ops, off, q, qmin, key, base):

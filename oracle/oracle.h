@@ -138,6 +138,10 @@ int oracle_decode_l(const oracle_inst* I, const float* keys, int32_t layout, int
 void oracle_encode(const oracle_inst* I, const int32_t* ops, const int32_t* off, float* keys);
 void oracle_encode_l(const oracle_inst* I, const int32_t* ops, const int32_t* off, int32_t layout, float* keys);
 
+/* Construction seed h (0 nearest neighbour, 1 load-balanced, 2 shortest
+ * processing time) of the BRKGA warm start as a chromosome (Section 4.4.4). */
+void oracle_seed_chromosome(const oracle_inst* I, int32_t h, int32_t layout, float* keys);
+
 typedef struct {
     int32_t pop, generations, warm_slots, warm_variants;
     float elite_frac, mutant_frac, rho;

@@ -986,6 +986,81 @@ void oracle_encode_l(const oracle_inst* I, const int32_t* ops, const int32_t* of
     }
 }
 
+/* Construction seeds of the warm start (Section 4.4.4) as decoder
+ * chromosomes: every drop before every pickup, both in one customer order;
+ * the r-th customer (from 0) gets priority r/(2n) on its drop and (n+r)/(2n)
+ * on its pickup, and the decoder builds the schedule.
+ *   h = 0 nearest neighbour: the order of the nearest-neighbour tour from the
+ *         depot (ties to the smaller id);
+ *   h = 1 load-balanced: customers by workload w_c = 2 d(0,c) + p_c (the
+ *         workload of Section 4.2.5), largest first; in the hint layout both
+ *         ops of c are hinted at the vehicle a greedy least-loaded
+ *         assignment in that order gives c (ties to the lower index);
+ *   h = 2 shortest processing time: customers by p ascending.
+ * Ties go to the smaller id.  The vehicle part is the keys v/m (layout 0) or,
+ * for h = 0 and 2, hints naming vehicle 0 (layout 1). */
+typedef struct {
+    int64_t key;
+    int c;
+} seed_rank_t;
+static int seed_rank_cmp(const void* pa, const void* pb) {
+    const seed_rank_t *a = pa, *b = pb;
+    if (a->key != b->key) return a->key < b->key ? -1 : 1;
+    return a->c - b->c;
+}
+
+void oracle_seed_chromosome(const oracle_inst* I, int32_t h, int32_t layout, float* keys) {
+    const int n = I->n, m = I->m;
+    int* order = malloc(sizeof(int) * (n + 1));
+    int* hv = calloc((size_t)n + 1, sizeof(int));
+    if (h == 0) {
+        char* vis = calloc((size_t)n + 1, 1);
+        int cur = 0;
+        for (int r = 0; r < n; r++) {
+            int best = -1;
+            for (int c = 1; c <= n; c++)
+                if (!vis[c] && (best < 0 || Dd(I, cur, c) < Dd(I, cur, best))) best = c;
+            vis[best] = 1;
+            order[r] = best;
+            cur = best;
+        }
+        free(vis);
+    } else {
+        seed_rank_t* rk = malloc(sizeof(seed_rank_t) * n);
+        for (int c = 1; c <= n; c++) {
+            rk[c - 1].c = c;
+            rk[c - 1].key = h == 1 ? -(2 * Dd(I, 0, c) + I->p[c - 1]) : (int64_t)I->p[c - 1];
+        }
+        qsort(rk, (size_t)n, sizeof(seed_rank_t), seed_rank_cmp);
+        for (int r = 0; r < n; r++) order[r] = rk[r].c;
+        free(rk);
+        if (h == 1) {
+            int64_t* load = calloc((size_t)m, sizeof(int64_t));
+            for (int r = 0; r < n; r++) {
+                int v = 0;
+                for (int u = 1; u < m; u++)
+                    if (load[u] < load[v]) v = u;
+                hv[order[r]] = v;
+                load[v] += 2 * Dd(I, 0, order[r]) + I->p[order[r] - 1];
+            }
+            free(load);
+        }
+    }
+    for (int r = 0; r < n; r++) {
+        const int c = order[r];
+        keys[2 * (c - 1)] = (float)r / (float)(2 * n);
+        keys[2 * (c - 1) + 1] = (float)(n + r) / (float)(2 * n);
+        if (layout == OR_LAYOUT_HINTS) {
+            keys[2 * n + 2 * (c - 1)] = hint_of(hv[c], m);
+            keys[2 * n + 2 * (c - 1) + 1] = hint_of(hv[c], m);
+        }
+    }
+    if (layout == OR_LAYOUT_VKEYS)
+        for (int v = 0; v < m; v++) keys[2 * n + v] = (float)v / (float)m;
+    free(order);
+    free(hv);
+}
+
 typedef struct {
     int64_t f;
     int idx;
@@ -1009,24 +1084,32 @@ int oracle_brkga_run(const oracle_inst* I, const oracle_brkga_params* P, const i
     int Nc = pop - Ne - Nm;
     float* cur = malloc(sizeof(float) * (size_t)pop * L);
     float* nxt = malloc(sizeof(float) * (size_t)pop * L);
-    float* base = malloc(sizeof(float) * L);
+    float* base = malloc(sizeof(float) * 4 * L);   /* ALNS encoding, then the three construction seeds */
     fit_t* fit = malloc(sizeof(fit_t) * pop);
     int32_t* dops = malloc(sizeof(int32_t) * 2 * n);
     int32_t* doff = malloc(sizeof(int32_t) * (m + 1));
     /* initial population: warm slots then random keys */
     int warm = warm_ops ? P->warm_slots : 0;
     if (warm > pop) warm = pop;
-    if (warm_ops) oracle_encode_l(I, warm_ops, warm_off, P->layout, base);
+    if (warm_ops) {
+        oracle_encode_l(I, warm_ops, warm_off, P->layout, base);
+        for (int h = 0; h < 3; h++) oracle_seed_chromosome(I, h, P->layout, base + (size_t)(h + 1) * L);
+    }
     const float top = 1.0f - 1.0f / 16777216.0f;
+    const int nvar = P->warm_variants > 0 ? P->warm_variants : 1;
     for (int s = 0; s < pop; s++) {
         float* kk = cur + (size_t)s * L;
         if (s < warm) {
-            int var = s % (P->warm_variants > 0 ? P->warm_variants : 1);
+            /* variant 0 is the ALNS encoding itself; with four or more
+             * variants the last three perturb the NN, load-balanced and SPT
+             * seeds, the others the ALNS encoding */
+            int var = s % nvar;
+            const float* bs = base + (size_t)(nvar >= 4 && var >= nvar - 3 ? var - (nvar - 3) + 1 : 0) * L;
             for (int g = 0; g < L; g++) {
-                if (var == 0) { kk[g] = base[g]; continue; }
+                if (var == 0) { kk[g] = bs[g]; continue; }
                 float u = rng_key(oracle_rng(wkey, (uint64_t)var * L + g));
                 float e = (u * 2.0f - 1.0f) * P->eps;                        /* U(-eps, eps) */
-                float x = base[g] + e;
+                float x = bs[g] + e;
                 if (x < 0.0f) x = 0.0f;
                 if (x > top) x = top;
                 kk[g] = x;
