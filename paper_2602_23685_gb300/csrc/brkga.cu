@@ -247,6 +247,117 @@ __global__ void encode_kernel(const int32_t* __restrict__ ops, const int32_t* __
             base[2 * n + v] = __fdiv_rn(static_cast<float>(v), static_cast<float>(m));
 }
 
+// Ascending bitonic sort of P (a power of two) keys in shared memory; all
+// threads of the block.
+static __device__ void seed_sort(unsigned long long* a, int P) {
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < P / 2; i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1)), hi = lo + stride;
+                const bool asc = (lo & size) == 0;
+                const unsigned long long x = a[lo], y = a[hi];
+                if ((x > y) == asc) { a[lo] = y; a[hi] = x; }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Construction seeds of the warm start (Section 4.4.4), block h = 0, 1, 2:
+// nearest neighbour, load-balanced, shortest processing time.  A customer
+// order (the nearest-neighbour tour from the depot; workload 2 d(0,c) + p_c
+// descending; p ascending; ties to the smaller id), then every drop before
+// every pickup in that order: priority r/(2n) on the r-th drop and (n+r)/(2n)
+// on its pickup.  Vehicle part: keys v/m, or hints naming vehicle 0 except
+// for the load-balanced seed, whose hints follow a least-loaded assignment in
+// its order (ties to the lower index).  out holds 3 chromosomes of L keys.
+__global__ void __launch_bounds__(256) seed_kernel(const int32_t* __restrict__ d, const int32_t* __restrict__ p, int n,
+                                                   int m, int layout, int L, float* __restrict__ out) {
+    extern __shared__ __align__(16) unsigned long long sq[];
+    __shared__ unsigned long long wmin[8];
+    __shared__ int curc;
+    const int h = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int N1 = n + 1;
+    int P = 1;
+    while (P < n) P <<= 1;
+    unsigned char* vis = reinterpret_cast<unsigned char*>(sq + P);
+    float* o = out + static_cast<size_t>(h) * L;
+    if (h == 0) {
+        for (int c = tid; c <= n; c += blockDim.x) vis[c] = 0;
+        if (tid == 0) curc = 0;
+        __syncthreads();
+        for (int r = 0; r < n; ++r) {
+            const int cur = curc;
+            unsigned long long best = ~0ull;
+            for (int c = 1 + tid; c <= n; c += blockDim.x)
+                if (!vis[c]) {
+                    const unsigned long long k =
+                        (static_cast<unsigned long long>(static_cast<unsigned>(__ldg(d + cur * N1 + c))) << 16) |
+                        static_cast<unsigned long long>(c);
+                    best = k < best ? k : best;
+                }
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long x = __shfl_xor_sync(0xffffffffu, best, off);
+                best = x < best ? x : best;
+            }
+            if (lane == 0) wmin[warp] = best;
+            __syncthreads();
+            if (tid == 0) {
+                unsigned long long b = wmin[0];
+                for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) b = wmin[w] < b ? wmin[w] : b;
+                const int c = static_cast<int>(b & 0xFFFF);
+                vis[c] = 1;
+                sq[r] = static_cast<unsigned long long>(c);
+                curc = c;
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int i = tid; i < P; i += blockDim.x) {
+            unsigned long long k = ~0ull;
+            if (i < n) {
+                const int c = i + 1;
+                const long long pc = __ldg(p + c);
+                const long long v = h == 1 ? (1ll << 46) - (2ll * __ldg(d + c) + pc) : pc;
+                k = (static_cast<unsigned long long>(v) << 16) | static_cast<unsigned long long>(c);
+            }
+            sq[i] = k;
+        }
+        seed_sort(sq, P);
+    }
+    __syncthreads();
+    const float two_n = static_cast<float>(2 * n);
+    for (int r = tid; r < n; r += blockDim.x) {
+        const int c = static_cast<int>(sq[r] & 0xFFFF);
+        o[2 * (c - 1)] = __fdiv_rn(static_cast<float>(r), two_n);
+        o[2 * (c - 1) + 1] = __fdiv_rn(static_cast<float>(n + r), two_n);
+    }
+    if (layout != VRPRPD_LAYOUT_HINTS) {
+        for (int v = tid; v < m; v += blockDim.x) o[2 * n + v] = __fdiv_rn(static_cast<float>(v), static_cast<float>(m));
+    } else if (h != 1) {
+        for (int i = tid; i < 2 * n; i += blockDim.x) o[2 * n + i] = hint_of(0, m);
+    } else if (warp == 0) {
+        long long load = lane < m ? 0 : 0x7fffffffffffffffll;
+        for (int r = 0; r < n; ++r) {
+            const int c = static_cast<int>(sq[r] & 0xFFFF);
+            long long bl = load;
+            int bv = lane;
+            for (int off = 16; off > 0; off >>= 1) {
+                const long long ol = __shfl_xor_sync(0xffffffffu, bl, off);
+                const int ov = __shfl_xor_sync(0xffffffffu, bv, off);
+                if (ol < bl || (ol == bl && ov < bv)) { bl = ol; bv = ov; }
+            }
+            if (lane == bv) load += 2ll * __ldg(d + c) + __ldg(p + c);
+            if (lane == 0) {
+                const float a = hint_of(bv, m);
+                o[2 * n + 2 * (c - 1)] = a;
+                o[2 * n + 2 * (c - 1) + 1] = a;
+            }
+        }
+    }
+}
+
 __global__ void init_pop_kernel(float* __restrict__ keys, const float* __restrict__ base, int pop, int L, int warm,
                                 int variants, float eps, unsigned long long key, unsigned long long wkey) {
     const long long total = static_cast<long long>(pop) * L;
@@ -257,13 +368,18 @@ __global__ void init_pop_kernel(float* __restrict__ keys, const float* __restric
         const int s = static_cast<int>(idx / L), g = static_cast<int>(idx - static_cast<long long>(s) * L);
         float x;
         if (s < warm) {
-            const int var = s % (variants > 0 ? variants : 1);
+            // variant 0 is the ALNS encoding itself; with four or more variants
+            // the last three perturb the three construction seeds (base + L,
+            // + 2L, + 3L), the others the ALNS encoding
+            const int nv = variants > 0 ? variants : 1;
+            const int var = s % nv;
+            const float* bs = base + static_cast<size_t>(nv >= 4 && var >= nv - 3 ? var - (nv - 3) + 1 : 0) * L;
             if (var == 0) {
-                x = base[g];
+                x = bs[g];
             } else {
                 const float u = draw_key(draw(wkey, static_cast<unsigned long long>(var) * L + g));
                 const float e = __fmul_rn(__fsub_rn(__fmul_rn(u, 2.0f), 1.0f), eps);
-                x = __fadd_rn(base[g], e);
+                x = __fadd_rn(bs[g], e);
                 x = x < 0.0f ? 0.0f : x;
                 x = x > top ? top : x;
             }
@@ -469,7 +585,7 @@ extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_par
     };
     float* buf0 = static_cast<float*>(dalloc(keys_b));
     float* buf1 = static_cast<float*>(dalloc(keys_b));
-    float* base = static_cast<float*>(dalloc(L * 4));
+    float* base = static_cast<float*>(dalloc(static_cast<size_t>(4) * L * 4));   // ALNS encoding + 3 seeds
     int32_t* dops = static_cast<int32_t*>(dalloc(static_cast<size_t>(pop) * 2 * n * 4));
     int32_t* doff = static_cast<int32_t*>(dalloc(static_cast<size_t>(pop) * (m + 1) * 4));
     int32_t* zdec = static_cast<int32_t*>(dalloc(pop * 4));
@@ -487,11 +603,18 @@ extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_par
     const unsigned long long key = stream_key(seed, RNG_STREAM_BRKGA), wkey = stream_key(seed, RNG_STREAM_WARM);
     BrkgaCtl c0{0, 0, 0, 0};
     cudaError_t e = cudaMemcpyAsync(ctl, &c0, sizeof(c0), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, L * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base, 0, static_cast<size_t>(4) * L * 4, s);
     if (warm && e == cudaSuccess) {
         e = cudaMemcpyAsync(wops, warm->ops, 2 * n * 4, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(woff, warm->off, (m + 1) * 4, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) encode_kernel<<<1, 256, 0, s>>>(wops, woff, n, m, P->layout, base);
+        if (e == cudaSuccess) {
+            int Ps = 1;
+            while (Ps < n) Ps <<= 1;
+            seed_kernel<<<3, 256, static_cast<size_t>(Ps) * 8 + n + 16, s>>>(I->d32, I->p, n, m, P->layout, L,
+                                                                          base + L);
+            e = cudaGetLastError();
+        }
     }
     if (e == cudaSuccess) {
         init_pop_kernel<<<std::min<long long>((static_cast<long long>(pop) * L + 255) / 256, 4096), 256, 0, s>>>(

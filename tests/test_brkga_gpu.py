@@ -120,3 +120,23 @@ def test_brkga_hint_layout_c3_shape_few_generations(vrp):
     cfg = workloads.CONFIGS["C3"]
     w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=0)
     run_pair(vrp, w, 1024, 3, seed=0, layout=1)
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_warm_population_with_construction_seeds(vrp, layout):
+    # one generation leaves the initial population in place: 24 warm slots
+    # cycle through the 20 variants, whose last three perturb the nearest-
+    # neighbour, load-balanced and SPT seeds (Section 4.4.4)
+    w = workloads.make_instance(37, 4, 10, 5, "5x", "clustered", seed=2)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    wo, wf = oracle.initial_solution(oi, w.coords)
+    g = vrp.brkga_run(inst, vrp.brkga_params(160, 1, layout=layout), seed=3, warm=(wo, wf), final_keys=True)
+    o = oracle.brkga_run(oi, oracle.brkga_params(160, 1, layout=layout), wo, wf, 3)
+    gk = g["keys"].cpu().numpy().reshape(160, -1)
+    ok = o["keys"].reshape(160, -1)
+    assert np.array_equal(gk.view(np.uint32), ok.view(np.uint32))
+    for h in range(3):
+        base = oracle.seed_chromosome(oi, h, layout)
+        assert np.abs(ok[17 + h] - base).max() <= 0.03 + 1e-6
+    assert np.array_equal(g["trace"], o["trace"])
