@@ -95,6 +95,9 @@ def lib():
             L.oracle_sp_closure.argtypes = [i32p, C.c_int32, i64p]
             L.oracle_coordination.argtypes = [C.POINTER(Inst), i32p, i32p, i32p, i32p]
             L.oracle_coordination.restype = C.c_uint32
+            L.oracle_alns_run_replicas.argtypes = [C.POINTER(Inst), i32p, i32p, C.POINTER(AlnsParams), C.c_uint64,
+                                                   C.c_int32, C.c_int32, i32p, i32p, i32p,
+                                                   C.POINTER(AlnsStats), i32p, i32p]
             L.oracle_seed_chromosome.argtypes = [C.POINTER(Inst), C.c_int32, C.c_int32, f32p]
             L.oracle_local_search.argtypes = [C.POINTER(Inst), C.c_int32, C.c_int32, i32p, i32p, i32p]
             L.oracle_bruteforce.argtypes = [C.POINTER(Inst), i32p, i32p]
@@ -333,6 +336,26 @@ def coordination(I, ops, off):
     il = np.zeros(1, np.int32)
     st = lib().oracle_coordination(C.byref(I.c), _p(ops), _p(off), _p(cr), _p(il))
     return int(cr[0]), int(il[0]), int(st)
+
+
+def alns_run_replicas(I, init_ops, init_off, params, seed, replicas, sync_every=1000):
+    """R replicas of Algorithm 1 with the best-of-all import every sync_every
+    iterations (Section 4.2.1)."""
+    init_ops = np.ascontiguousarray(init_ops, dtype=np.int32)
+    init_off = np.ascontiguousarray(init_off, dtype=np.int32)
+    bo = np.zeros(2 * I.n, np.int32)
+    bf = np.zeros(I.m + 1, np.int32)
+    br = np.zeros(1, np.int32)
+    imp = np.zeros(1, np.int32)
+    stats = (AlnsStats * replicas)()
+    traces = np.zeros((replicas, max(1, params.iterations)), np.int32)
+    rc = lib().oracle_alns_run_replicas(C.byref(I.c), _p(init_ops), _p(init_off), C.byref(params),
+                                        C.c_uint64(seed), replicas, sync_every, _p(bo), _p(bf), _p(br),
+                                        stats, _p(traces), _p(imp))
+    if rc != 0:
+        raise ValueError(f"oracle_alns_run_replicas failed rc={rc}")
+    return dict(best_ops=bo, best_off=bf, best_replica=int(br[0]), stats=list(stats),
+                traces=traces[:, :params.iterations], imports=int(imp[0]))
 
 
 LS_PICKUP, LS_RELOCATE = 1, 2

@@ -118,6 +118,17 @@ int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t
                     int32_t* best_ops, int32_t* best_off, int32_t* cur_ops, int32_t* cur_off,
                     oracle_alns_stats* st, int32_t* z_trace);
 
+/* R independent replicas of Algorithm 1 (Section 4.2.1, multi-instance
+ * parallelism), replica r on its own draw stream (r = 0: the single-run
+ * stream), all from the same start.  After every sync_every-th iteration each
+ * replica whose best is worse than the best of all replicas (lowest index on
+ * ties) takes it as its current and best solution.  stats and z_traces hold R
+ * entries / R x iterations; best_* is the best of all. */
+int oracle_alns_run_replicas(const oracle_inst* I, const int32_t* init_ops, const int32_t* init_off,
+                             const oracle_alns_params* P, uint64_t seed, int32_t replicas, int32_t sync_every,
+                             int32_t* best_ops, int32_t* best_off, int32_t* best_replica,
+                             oracle_alns_stats* stats, int32_t* z_traces, int32_t* imports);
+
 /* ---- BRKGA (Algorithm 2 decoder, Section 4.4) ---- */
 /* Chromosome layouts.  Both start with 2n priority keys (op index
  * 2(c-1)+isPickup).  Layout 0 (2n+m keys): then m vehicle keys; SelectVehicle

@@ -668,146 +668,241 @@ int oracle_local_search(const oracle_inst* I, int32_t mode, int32_t passes, int3
     return local_search(I, mode, ops, off, z, passes);
 }
 
+/* One ALNS instance (Algorithm 1) as resumable state: its solutions, the
+ * temperature, the operator weights and scores, and its draw stream. */
+typedef struct {
+    const oracle_inst* I;
+    const oracle_alns_params* P;
+    int32_t *S, *So, *Sb, *Sbo, *W, *Wo, *tmp, *tmpo;
+    int* list;
+    char* rem;
+    int32_t z, zb, qmin, qmax;
+    uint64_t key;
+    double wd[ND_OPS], wr[4], T, T_init;
+    int sd[ND_OPS], sr[4], ad[ND_OPS], ar[4], en_d[ND_OPS], en_r[4];
+    int stagnation;
+    oracle_alns_stats* stats;
+    int32_t* z_trace;
+} alns_t;
+
+static int alns_init(alns_t* A, const oracle_inst* I, const int32_t* init_ops, const int32_t* init_off,
+                     const oracle_alns_params* P, uint64_t key, oracle_alns_stats* stats, int32_t* z_trace) {
+    const int n = I->n, m = I->m, two_n = 2 * n;
+    memset(A, 0, sizeof(*A));
+    A->I = I;
+    A->P = P;
+    A->S = malloc(sizeof(int32_t) * two_n); A->So = malloc(sizeof(int32_t) * (m + 1));
+    A->Sb = malloc(sizeof(int32_t) * two_n); A->Sbo = malloc(sizeof(int32_t) * (m + 1));
+    A->W = malloc(sizeof(int32_t) * (two_n + 2)); A->Wo = malloc(sizeof(int32_t) * (m + 1));
+    A->tmp = malloc(sizeof(int32_t) * (two_n + 2)); A->tmpo = malloc(sizeof(int32_t) * (m + 1));
+    A->list = malloc(sizeof(int) * (n + 1));
+    A->rem = calloc((size_t)n + 1, 1);
+    memcpy(A->S, init_ops, sizeof(int32_t) * two_n);
+    memcpy(A->So, init_off, sizeof(int32_t) * (m + 1));
+    uint32_t st;
+    oracle_evaluate(I, A->S, A->So, 0, &A->z, &st, NULL);
+    if (st) return -2;                             /* the search starts from a feasible solution */
+    memcpy(A->Sb, A->S, sizeof(int32_t) * two_n);
+    memcpy(A->Sbo, A->So, sizeof(int32_t) * (m + 1));
+    A->zb = A->z;
+    A->key = key;
+    A->qmin = P->q_min;
+    A->qmax = P->q_max;
+    if (A->qmin <= 0 || A->qmax <= 0) oracle_q_range(n, &A->qmin, &A->qmax);
+    if (A->qmax > n) A->qmax = n;
+    if (A->qmin > A->qmax) A->qmin = A->qmax;
+    /* operators: destroy 0 random, 1 worst, 2 Shaw, 3 cluster, 4 route, 5
+     * critical path (destroy_mask bits); repair 0 greedy, 1 regret-2, 2
+     * regret-3, 3 regret-m (repair_mask bits) */
+    for (int i = 0; i < ND_OPS; i++) { A->wd[i] = 1.0; A->en_d[i] = (P->destroy_mask >> i) & 1; }
+    for (int i = 0; i < 4; i++) { A->wr[i] = 1.0; A->en_r[i] = (P->repair_mask >> i) & 1; }
+    A->T = P->T0 * (double)A->z;                   /* line 3 */
+    A->T_init = A->T;
+    A->stats = stats;
+    A->z_trace = z_trace;
+    memset(stats, 0, sizeof(*stats));
+    stats->z_init = A->z;
+    return 0;
+}
+
+/* Iteration it of Algorithm 1, then the periodic local search. */
+static void alns_iteration(alns_t* A, int it) {
+    const oracle_inst* I = A->I;
+    const oracle_alns_params* P = A->P;
+    const int n = I->n, m = I->m, two_n = 2 * n, ND = ND_OPS, NR = 4;
+    oracle_alns_stats* stats = A->stats;
+    const uint64_t base = (uint64_t)it << 16, key = A->key;
+    int di = roulette(A->wd, A->en_d, ND, rng_unit(oracle_rng(key, base + 0)));   /* line 8 */
+    int rj = roulette(A->wr, A->en_r, NR, rng_unit(oracle_rng(key, base + 1)));   /* line 9 */
+    A->ad[di]++;
+    A->ar[rj]++;                                                                 /* line 10 */
+    int q = A->qmin + rng_below(oracle_rng(key, base + 2), A->qmax - A->qmin + 1);
+    oracle_destroy(I, di, A->S, A->So, q, A->qmin, key, base, A->rem);           /* line 11 */
+    remove_customers(m, A->S, A->So, A->rem, A->W, A->Wo);
+    int cnt = 0;
+    for (int c = 1; c <= n; c++)
+        if (A->rem[c]) A->list[cnt++] = c;
+    int32_t zn = INT32_MAX;
+    uint32_t st = OR_MALFORMED;
+    if (repair(I, rj, A->W, A->Wo, A->list, cnt, A->tmp, A->tmpo) == 0)          /* line 11 */
+        oracle_evaluate(I, A->W, A->Wo, 0, &zn, &st, NULL);                      /* line 12 */
+    if (st) {
+        /* repair found no feasible slot, or a route the destroy left over
+         * capacity was never repaired: the candidate is rejected */
+        stats->rejected_infeasible++;
+    } else if (zn < A->z) {                                                      /* lines 13-21 */
+        memcpy(A->S, A->W, sizeof(int32_t) * two_n);
+        memcpy(A->So, A->Wo, sizeof(int32_t) * (m + 1));
+        A->z = zn;
+        A->sd[di] += P->sigma2;
+        A->sr[rj] += P->sigma2;
+        stats->improved++;
+        stats->accepted++;
+        if (zn < A->zb) {
+            memcpy(A->Sb, A->W, sizeof(int32_t) * two_n);
+            memcpy(A->Sbo, A->Wo, sizeof(int32_t) * (m + 1));
+            A->zb = zn;
+            A->sd[di] += P->sigma1 - P->sigma2;
+            A->sr[rj] += P->sigma1 - P->sigma2;
+            A->stagnation = 0;
+            stats->new_best++;
+        }
+    } else {
+        double x = -(double)((int64_t)zn - (int64_t)A->z) / A->T;
+        double u = rng_unit(oracle_rng(key, base + 3));
+        if (u < oracle_exp(x)) {                                                 /* lines 22-25 */
+            memcpy(A->S, A->W, sizeof(int32_t) * two_n);
+            memcpy(A->So, A->Wo, sizeof(int32_t) * (m + 1));
+            A->z = zn;
+            A->sd[di] += P->sigma3;
+            A->sr[rj] += P->sigma3;
+            stats->accepted++;
+        }
+    }
+    A->T = P->alpha * A->T;                                                      /* line 27 */
+    A->stagnation++;                                                             /* line 28 */
+    if (A->stagnation >= P->stagnation && A->T < 0.01 * A->T_init) {             /* lines 29-32 + text gate */
+        A->T = (P->reheat * P->T0) * (double)A->zb;
+        A->stagnation = 0;
+        stats->reheats++;
+    }
+    if (it % P->tau == 0) {                                                      /* lines 33-38 */
+        for (int i = 0; i < ND; i++) {
+            double ratio = A->ad[i] ? (double)A->sd[i] / (double)A->ad[i] : 0.0;
+            double w = (1.0 - P->r) * A->wd[i] + P->r * ratio;
+            A->wd[i] = w < P->w_min ? P->w_min : w;
+            A->sd[i] = 0;
+            A->ad[i] = 0;
+        }
+        for (int i = 0; i < NR; i++) {
+            double ratio = A->ar[i] ? (double)A->sr[i] / (double)A->ar[i] : 0.0;
+            double w = (1.0 - P->r) * A->wr[i] + P->r * ratio;
+            A->wr[i] = w < P->w_min ? P->w_min : w;
+            A->sr[i] = 0;
+            A->ar[i] = 0;
+        }
+    }
+    /* periodic local search on the current solution (Section 4.2.6):
+     * pickup repositioning first when both fall due */
+    if (P->ls_pickup_every > 0 && it % P->ls_pickup_every == 0)
+        stats->ls_moves += local_search(I, LS_PICKUP, A->S, A->So, &A->z, 3);
+    if (P->ls_relocate_every > 0 && it % P->ls_relocate_every == 0)
+        stats->ls_moves += local_search(I, LS_RELOCATE, A->S, A->So, &A->z, 3);
+    if (A->z < A->zb) {
+        memcpy(A->Sb, A->S, sizeof(int32_t) * two_n);
+        memcpy(A->Sbo, A->So, sizeof(int32_t) * (m + 1));
+        A->zb = A->z;
+        A->stagnation = 0;
+        stats->ls_new_best++;
+    }
+    if (A->z_trace) A->z_trace[it - 1] = A->z;
+    stats->iterations = it;
+}
+
+static void alns_finish(alns_t* A, int32_t* cur_ops_out, int32_t* cur_off_out) {
+    const int two_n = 2 * A->I->n, m = A->I->m;
+    if (cur_ops_out) memcpy(cur_ops_out, A->S, sizeof(int32_t) * two_n);
+    if (cur_off_out) memcpy(cur_off_out, A->So, sizeof(int32_t) * (m + 1));
+    A->stats->z_best = A->zb;
+    A->stats->z_current = A->z;
+    A->stats->T_final = A->T;
+    for (int i = 0; i < ND_OPS; i++) A->stats->w_destroy[i] = A->wd[i];
+    for (int i = 0; i < 4; i++) A->stats->w_repair[i] = A->wr[i];
+}
+
+static void alns_free(alns_t* A) {
+    free(A->S); free(A->So); free(A->Sb); free(A->Sbo); free(A->W); free(A->Wo); free(A->tmp); free(A->tmpo);
+    free(A->list); free(A->rem);
+}
+
 int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t* init_off,
                     const oracle_alns_params* P, uint64_t seed, int32_t* best_ops, int32_t* best_off,
                     int32_t* cur_ops_out, int32_t* cur_off_out, oracle_alns_stats* stats,
                     int32_t* z_trace) {
-    const int n = I->n, m = I->m, two_n = 2 * n;
-    int32_t *S = malloc(sizeof(int32_t) * two_n), *So = malloc(sizeof(int32_t) * (m + 1));
-    int32_t *Sb = malloc(sizeof(int32_t) * two_n), *Sbo = malloc(sizeof(int32_t) * (m + 1));
-    int32_t *W = malloc(sizeof(int32_t) * (two_n + 2)), *Wo = malloc(sizeof(int32_t) * (m + 1));
-    int32_t *tmp = malloc(sizeof(int32_t) * (two_n + 2)), *tmpo = malloc(sizeof(int32_t) * (m + 1));
-    int* perm = malloc(sizeof(int) * (n + 1));
-    int* list = malloc(sizeof(int) * (n + 1));
-    char* rem = calloc((size_t)n + 1, 1);
-    memcpy(S, init_ops, sizeof(int32_t) * two_n);
-    memcpy(So, init_off, sizeof(int32_t) * (m + 1));
-    int32_t z;
-    uint32_t st;
-    oracle_evaluate(I, S, So, 0, &z, &st, NULL);
-    if (st) return -2;                             /* the search starts from a feasible solution */
-    memcpy(Sb, S, sizeof(int32_t) * two_n);
-    memcpy(Sbo, So, sizeof(int32_t) * (m + 1));
-    int32_t zb = z;
-    const uint64_t key = stream_key(seed, STREAM_ALNS);
-    int32_t qmin = P->q_min, qmax = P->q_max;
-    if (qmin <= 0 || qmax <= 0) oracle_q_range(n, &qmin, &qmax);
-    if (qmax > n) qmax = n;
-    if (qmin > qmax) qmin = qmax;
-    /* operators: destroy 0 random, 1 worst, 2 Shaw, 3 cluster, 4 route, 5
-     * critical path (destroy_mask bits); repair 0 greedy, 1 regret-2, 2
-     * regret-3, 3 regret-m (repair_mask bits) */
-    const int ND = ND_OPS, NR = 4;
-    double wd[ND_OPS], wr[4] = {1.0, 1.0, 1.0, 1.0};
-    int sd[ND_OPS], sr[4] = {0, 0, 0, 0}, ad[ND_OPS], ar[4] = {0, 0, 0, 0};
-    int en_d[ND_OPS], en_r[4];
-    for (int i = 0; i < ND; i++) { wd[i] = 1.0; sd[i] = 0; ad[i] = 0; en_d[i] = (P->destroy_mask >> i) & 1; }
-    for (int i = 0; i < NR; i++) en_r[i] = (P->repair_mask >> i) & 1;
-    double T = P->T0 * (double)z;                  /* line 3 */
-    const double T_init = T;
-    int stagnation = 0;
-    memset(stats, 0, sizeof(*stats));
-    stats->z_init = z;
-    for (int it = 1; it <= P->iterations; it++) {
-        const uint64_t base = (uint64_t)it << 16;
-        int di = roulette(wd, en_d, ND, rng_unit(oracle_rng(key, base + 0)));   /* line 8 */
-        int rj = roulette(wr, en_r, NR, rng_unit(oracle_rng(key, base + 1)));   /* line 9 */
-        ad[di]++;
-        ar[rj]++;                                                              /* line 10 */
-        int q = qmin + rng_below(oracle_rng(key, base + 2), qmax - qmin + 1);
-        oracle_destroy(I, di, S, So, q, qmin, key, base, rem);                   /* line 11 */
-        remove_customers(m, S, So, rem, W, Wo);
-        int cnt = 0;
-        for (int c = 1; c <= n; c++)
-            if (rem[c]) list[cnt++] = c;
-        int32_t zn = INT32_MAX;
-        st = OR_MALFORMED;
-        if (repair(I, rj, W, Wo, list, cnt, tmp, tmpo) == 0)                     /* line 11 */
-            oracle_evaluate(I, W, Wo, 0, &zn, &st, NULL);                        /* line 12 */
-        if (st) {
-            /* repair found no feasible slot, or a route the destroy left over
-             * capacity was never repaired: the candidate is rejected */
-            stats->rejected_infeasible++;
-        } else if (zn < z) {                                                     /* lines 13-21 */
-            memcpy(S, W, sizeof(int32_t) * two_n);
-            memcpy(So, Wo, sizeof(int32_t) * (m + 1));
-            z = zn;
-            sd[di] += P->sigma2;
-            sr[rj] += P->sigma2;
-            stats->improved++;
-            stats->accepted++;
-            if (zn < zb) {
-                memcpy(Sb, W, sizeof(int32_t) * two_n);
-                memcpy(Sbo, Wo, sizeof(int32_t) * (m + 1));
-                zb = zn;
-                sd[di] += P->sigma1 - P->sigma2;
-                sr[rj] += P->sigma1 - P->sigma2;
-                stagnation = 0;
-                stats->new_best++;
-            }
-        } else {
-            double x = -(double)((int64_t)zn - (int64_t)z) / T;
-            double u = rng_unit(oracle_rng(key, base + 3));
-            if (u < oracle_exp(x)) {                                             /* lines 22-25 */
-                memcpy(S, W, sizeof(int32_t) * two_n);
-                memcpy(So, Wo, sizeof(int32_t) * (m + 1));
-                z = zn;
-                sd[di] += P->sigma3;
-                sr[rj] += P->sigma3;
-                stats->accepted++;
-            }
-        }
-        T = P->alpha * T;                                                        /* line 27 */
-        stagnation++;                                                            /* line 28 */
-        if (stagnation >= P->stagnation && T < 0.01 * T_init) {                  /* lines 29-32 + text gate */
-            T = (P->reheat * P->T0) * (double)zb;
-            stagnation = 0;
-            stats->reheats++;
-        }
-        if (it % P->tau == 0) {                                                  /* lines 33-38 */
-            for (int i = 0; i < ND; i++) {
-                double ratio = ad[i] ? (double)sd[i] / (double)ad[i] : 0.0;
-                double w = (1.0 - P->r) * wd[i] + P->r * ratio;
-                wd[i] = w < P->w_min ? P->w_min : w;
-                sd[i] = 0;
-                ad[i] = 0;
-            }
-            for (int i = 0; i < NR; i++) {
-                double ratio = ar[i] ? (double)sr[i] / (double)ar[i] : 0.0;
-                double w = (1.0 - P->r) * wr[i] + P->r * ratio;
-                wr[i] = w < P->w_min ? P->w_min : w;
-                sr[i] = 0;
-                ar[i] = 0;
-            }
-        }
-        /* periodic local search on the current solution (Section 4.2.6):
-         * pickup repositioning first when both fall due */
-        if (P->ls_pickup_every > 0 && it % P->ls_pickup_every == 0)
-            stats->ls_moves += local_search(I, LS_PICKUP, S, So, &z, 3);
-        if (P->ls_relocate_every > 0 && it % P->ls_relocate_every == 0)
-            stats->ls_moves += local_search(I, LS_RELOCATE, S, So, &z, 3);
-        if (z < zb) {
-            memcpy(Sb, S, sizeof(int32_t) * two_n);
-            memcpy(Sbo, So, sizeof(int32_t) * (m + 1));
-            zb = z;
-            stagnation = 0;
-            stats->ls_new_best++;
-        }
-        if (z_trace) z_trace[it - 1] = z;
-        stats->iterations = it;
+    alns_t A;
+    if (alns_init(&A, I, init_ops, init_off, P, stream_key(seed, STREAM_ALNS), stats, z_trace)) {
+        alns_free(&A);
+        return -2;
     }
-    memcpy(best_ops, Sb, sizeof(int32_t) * two_n);
-    memcpy(best_off, Sbo, sizeof(int32_t) * (m + 1));
-    if (cur_ops_out) memcpy(cur_ops_out, S, sizeof(int32_t) * two_n);
-    if (cur_off_out) memcpy(cur_off_out, So, sizeof(int32_t) * (m + 1));
-    stats->z_best = zb;
-    stats->z_current = z;
-    stats->T_final = T;
-    for (int i = 0; i < ND; i++) stats->w_destroy[i] = wd[i];
-    for (int i = 0; i < NR; i++) stats->w_repair[i] = wr[i];
-    free(S); free(So); free(Sb); free(Sbo); free(W); free(Wo); free(tmp); free(tmpo);
-    free(perm); free(list); free(rem);
+    for (int it = 1; it <= P->iterations; it++) alns_iteration(&A, it);
+    alns_finish(&A, cur_ops_out, cur_off_out);
+    memcpy(best_ops, A.Sb, sizeof(int32_t) * 2 * I->n);
+    memcpy(best_off, A.Sbo, sizeof(int32_t) * (I->m + 1));
+    alns_free(&A);
     return 0;
+}
+
+/* The draw stream of replica r: the ALNS stream itself for r = 0, else a
+ * draw of it far past any iteration's counters. */
+static uint64_t replica_key(uint64_t key0, int r) {
+    return r == 0 ? key0 : oracle_rng(key0, (0xFFFFFFFFull << 32) + (uint64_t)r);
+}
+
+int oracle_alns_run_replicas(const oracle_inst* I, const int32_t* init_ops, const int32_t* init_off,
+                             const oracle_alns_params* P, uint64_t seed, int32_t replicas, int32_t sync_every,
+                             int32_t* best_ops, int32_t* best_off, int32_t* best_replica,
+                             oracle_alns_stats* stats, int32_t* z_traces, int32_t* imports) {
+    const int n = I->n, m = I->m;
+    alns_t* A = calloc((size_t)replicas, sizeof(alns_t));
+    const uint64_t key0 = stream_key(seed, STREAM_ALNS);
+    int rc = 0;
+    for (int r = 0; r < replicas && !rc; r++)
+        rc = alns_init(&A[r], I, init_ops, init_off, P, replica_key(key0, r), &stats[r],
+                       z_traces ? z_traces + (size_t)r * P->iterations : NULL);
+    *imports = 0;
+    for (int it = 1; it <= P->iterations && !rc; it++) {
+        for (int r = 0; r < replicas; r++) alns_iteration(&A[r], it);
+        if (replicas > 1 && sync_every > 0 && it % sync_every == 0) {
+            /* every replica takes the best of all when its own is worse (the
+             * lowest index among equal bests) */
+            int g = 0;
+            for (int r = 1; r < replicas; r++)
+                if (A[r].zb < A[g].zb) g = r;
+            for (int r = 0; r < replicas; r++) {
+                if (A[r].zb <= A[g].zb) continue;
+                memcpy(A[r].S, A[g].Sb, sizeof(int32_t) * 2 * n);
+                memcpy(A[r].So, A[g].Sbo, sizeof(int32_t) * (m + 1));
+                memcpy(A[r].Sb, A[g].Sb, sizeof(int32_t) * 2 * n);
+                memcpy(A[r].Sbo, A[g].Sbo, sizeof(int32_t) * (m + 1));
+                A[r].z = A[r].zb = A[g].zb;
+                A[r].stagnation = 0;
+                (*imports)++;
+            }
+        }
+    }
+    if (!rc) {
+        int g = 0;
+        for (int r = 0; r < replicas; r++) {
+            alns_finish(&A[r], NULL, NULL);
+            if (A[r].zb < A[g].zb) g = r;
+        }
+        memcpy(best_ops, A[g].Sb, sizeof(int32_t) * 2 * n);
+        memcpy(best_off, A[g].Sbo, sizeof(int32_t) * (m + 1));
+        *best_replica = g;
+    }
+    for (int r = 0; r < replicas; r++) alns_free(&A[r]);
+    free(A);
+    return rc ? -2 : 0;
 }
 
 /* ------------------------------------------------------------------------ */
