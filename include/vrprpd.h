@@ -255,6 +255,17 @@ typedef struct {
                                   flat gap index) if it lowers the makespan; up to three passes;
                                   pickup repositioning first when both fall due. */
     int32_t ls_relocate_every;
+    int32_t replicas;          /* Section 4.2.1 multi-instance parallelism: independent ALNS instances of
+                                  this one problem in one launch (default 1, 0 reads as 1; the paper
+                                  runs 32 per GPU),
+                                  each a team of CTAs with its own solution, temperature, weights and
+                                  draw stream (replica 0 draws like a single run).  The resident CTAs
+                                  of the GPU are shared among them. */
+    int32_t sync_every;        /* every sync_every-th iteration (default 1000; 0 = never) all replicas
+                                  meet, and each whose best is worse than the best of all (lowest
+                                  index among equal bests) takes that solution as its current and best.
+                                  The paper's replicas poll without meeting; meeting makes runs
+                                  reproducible. */
 } vrprpd_alns_params;
 
 typedef struct {
@@ -274,6 +285,10 @@ typedef struct {
     int32_t ls_moves;          /* local-search moves applied */
     int32_t ls_new_best;       /* iterations whose local search gave a new best solution */
     double ls_ms;              /* wall time spent in the local search */
+    int32_t replicas;          /* replicas run; the counters above are summed over them, z_current,
+                                  T_final, the weights and phase times are replica 0's */
+    int32_t imports;           /* best-of-all solutions taken at checkpoints, over all replicas */
+    int32_t best_replica;      /* the replica whose best solution is returned */
 } vrprpd_alns_stats;
 
 void vrprpd_alns_params_default(vrprpd_alns_params* params);
@@ -286,17 +301,21 @@ void vrprpd_alns_params_default(vrprpd_alns_params* params);
 int vrprpd_initial_solution(const vrprpd_instance* inst, vrprpd_solution* out);
 
 /*
- * Run Algorithm 1 on the device: roulette selection of operators (random
- * removal; greedy or regret-2 insertion over the full insertion-delta matrix),
- * simulated-annealing acceptance with the text's reheat gate, adaptive weights.
- * Every random draw is SplitMix64 of (seed-derived key, iteration-derived
- * counter), so a run is reproducible bit for bit.
+ * Run Algorithm 1 on the device: roulette selection of the enabled destroy
+ * and repair operators (Sections 4.2.2-4.2.3) over the full insertion-delta
+ * matrix, simulated-annealing acceptance with the text's reheat gate, adaptive
+ * weights, the periodic local search (Section 4.2.6) and, with several
+ * replicas, the multi-instance checkpoints (Section 4.2.1).  Every random draw
+ * is SplitMix64 of (seed-derived key, iteration-derived counter), so a run is
+ * reproducible bit for bit.
  *   init     host solution to start from, or NULL for vrprpd_initial_solution.
  *            It must be feasible (status 0).
- *   best     host buffers receive the best solution found (and its makespan).
- *   current  host buffers for the final current solution, or NULL.
- *   stats    may be NULL; z_trace (host, params->iterations int32) receives the
- *            current makespan after each iteration, or NULL.
+ *   best     host buffers receive the best solution found (and its makespan),
+ *            over all replicas.
+ *   current  host buffers for replica 0's final current solution, or NULL.
+ *   stats    may be NULL; z_trace (host, replicas x params->iterations int32,
+ *            replica-major) receives each replica's current makespan after
+ *            each iteration, or NULL.
  * Needs m <= 32, 2n + m <= 4096, max d < 2^17 and (2n+1)*max(d) + n*max(p) < 2^27
  * (VRPRPD_EINVAL otherwise).  Blocking: returns when done.
  */

@@ -291,12 +291,14 @@ def alns_run(inst, params, seed=0, init=None, stream=None):
     if init is not None:
         init_s, _io, _if = _sol(inst, *init)
     st = AlnsStats()
-    trace = np.zeros(max(1, params.iterations), np.int32)
+    R = max(1, params.replicas)
+    traces = np.zeros((R, max(1, params.iterations)), np.int32)
     _check(lib().vrprpd_alns_run(inst.handle, C.byref(init_s) if init_s is not None else None, C.byref(params),
                                  C.c_uint64(seed), C.byref(best), C.byref(cur), C.byref(st),
-                                 trace.ctypes.data, _stream_ptr(stream)))
+                                 traces.ctypes.data, _stream_ptr(stream)))
     return {"best_ops": bo, "best_off": bf, "z_best": best.makespan, "cur_ops": co, "cur_off": cf,
-            "z_current": cur.makespan, "stats": st, "trace": trace[:params.iterations]}
+            "z_current": cur.makespan, "stats": st, "trace": traces[0, :params.iterations],
+            "traces": traces[:, :params.iterations]}
 
 
 def insertion_matrix(inst, ops, off, c, stream=None):

@@ -12,7 +12,8 @@ class AlnsParams(C.Structure):
                 ("sigma2", C.c_int32), ("sigma3", C.c_int32), ("w_min", C.c_double),
                 ("q_min", C.c_int32), ("q_max", C.c_int32), ("iterations", C.c_int32),
                 ("repair_mask", C.c_int32), ("team_blocks", C.c_int32),
-                ("destroy_mask", C.c_int32), ("ls_pickup_every", C.c_int32), ("ls_relocate_every", C.c_int32)]
+                ("destroy_mask", C.c_int32), ("ls_pickup_every", C.c_int32), ("ls_relocate_every", C.c_int32),
+                ("replicas", C.c_int32), ("sync_every", C.c_int32)]
 
 
 class AlnsStats(C.Structure):
@@ -23,7 +24,8 @@ class AlnsStats(C.Structure):
                 ("device_ms", C.c_double), ("matrix_entries", C.c_int64),
                 ("fallback_entries", C.c_int64), ("team_blocks", C.c_int32), ("phase_ms", C.c_double * 6),
                 ("incremental_steps", C.c_int64), ("full_steps", C.c_int64), ("ls_moves", C.c_int32),
-                ("ls_new_best", C.c_int32), ("ls_ms", C.c_double)]
+                ("ls_new_best", C.c_int32), ("ls_ms", C.c_double), ("replicas", C.c_int32),
+                ("imports", C.c_int32), ("best_replica", C.c_int32)]
 
 
 class BrkgaParams(C.Structure):

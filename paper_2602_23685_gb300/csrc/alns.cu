@@ -97,6 +97,7 @@ struct AlnsCtl {
     int ls_c, ls_bz, ls_a, ls_ia, ls_b, ls_jb;
     int ls_moves, ls_new_best;
     long long ls_travel, ls_bt, ls_bflat;
+    int imports;                      // best-of-all solutions this replica took at checkpoints
 };
 
 struct AlnsTeam {
@@ -109,6 +110,9 @@ struct AlnsTeam {
     int stagnation_limit, tau, sigma1, sigma2, sigma3, q_min, q_max, iterations, repair_mask;
     int destroy_mask;        // bit 0 random, 1 worst, 2 Shaw, 3 cluster, 4 route, 5 critical path
     int ls_pickup, ls_relocate;  // local-search periods in iterations (0 = off)
+    int replica, nreplicas, sync_every;   // multi-instance: this team's index, team count, checkpoint period
+    unsigned* gbar;          // [2] grid barrier over all teams: count, generation
+    const AlnsTeam* sib;     // device array of all teams (siblings' best solutions at checkpoints)
     unsigned long long key;  // RNG stream key
     int mode;                // 0 = search, 1 = one-customer matrix dump
     int dump_c;
@@ -2284,6 +2288,79 @@ __device__ void phase_end(const AlnsTeam& t, const Smem& s, bool first) {
 }
 
 // ---------------------------------------------------------------------------
+// multi-instance checkpoints (Section 4.2.1): all teams of the launch meet
+// ---------------------------------------------------------------------------
+// Barrier over every CTA of the launch; bounded (about 2 s), sets ctl->err.
+__device__ bool grid_barrier(const AlnsTeam& t, unsigned& ggen) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &t.gbar[1];
+        const unsigned total = gridDim.x;
+        __threadfence();
+        const unsigned arrived = atomicAdd(&t.gbar[0], 1u) + 1u;
+        if (arrived == total) {
+            t.gbar[0] = 0u;
+            __threadfence();
+            atomicExch(&t.gbar[1], ggen + 1u);
+        } else {
+            const uint64_t t0 = global_ns();
+            while (*vgen == ggen) {
+                if (global_ns() - t0 > 2000000000ull) {
+                    atomicExch(&t.ctl->err, DEV_TIMEOUT_BARRIER);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    ggen += 1u;
+    __syncthreads();
+    return *reinterpret_cast<volatile int*>(&t.ctl->err) == 0;
+}
+
+// Rank 0 of each team, between two grid barriers: when the best of all teams
+// (lowest index among equal bests) beats this team's best, it becomes this
+// team's current and best solution.  Nothing writes a best solution between
+// the two barriers, so every team reads the same ones.
+__device__ __noinline__ void replica_import(const AlnsTeam& t, const Smem& s) {
+    AlnsCtl* ctl = t.ctl;
+    int* sh = s.misc;
+    if (threadIdx.x == 0) {
+        int g = 0, zg = *reinterpret_cast<volatile const int*>(&t.sib[0].ctl->z_best);
+        for (int r = 1; r < t.nreplicas; ++r) {
+            const int zr = *reinterpret_cast<volatile const int*>(&t.sib[r].ctl->z_best);
+            if (zr < zg) { zg = zr; g = r; }
+        }
+        sh[0] = ctl->z_best > zg ? g : -1;
+        sh[1] = zg;
+    }
+    __syncthreads();
+    const int g = sh[0];
+    if (g >= 0) {
+        const int* bo = t.sib[g].best_ops;
+        const int* bf = t.sib[g].best_off;
+        for (int k = threadIdx.x; k < 2 * t.n; k += blockDim.x) {
+            const int o = __ldcg(bo + k);
+            t.cur_ops[k] = o;
+            t.best_ops[k] = o;
+        }
+        for (int v = threadIdx.x; v <= t.m; v += blockDim.x) {
+            const int o = __ldcg(bf + v);
+            t.cur_off[v] = o;
+            t.best_off[v] = o;
+        }
+        if (threadIdx.x == 0) {
+            ctl->z_cur = sh[1];
+            ctl->z_best = sh[1];
+            ctl->stagnation = 0;
+            ctl->imports += 1;
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
 // periodic local search (Section 4.2.6), on the current solution
 // ---------------------------------------------------------------------------
 // Each candidate customer c runs one team step (prep, gaps, shortcut walks,
@@ -2553,7 +2630,7 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
     for (int c = threadIdx.x; c <= t.n; c += blockDim.x) s.sp[c] = t.p[c];
     if (t.coords)
         for (int i = threadIdx.x; i < 2 * (t.n + 1); i += blockDim.x) s.xy[i] = t.coords[i];
-    unsigned gen = 0;
+    unsigned gen = 0, ggen = 0;
     __syncthreads();
 
     if (t.mode == 1) {
@@ -2668,6 +2745,11 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
             if (!team_barrier(ctl, team_blocks, gen)) return;
             mark(6);
         }
+        if (t.nreplicas > 1 && t.sync_every > 0 && it % t.sync_every == 0) {
+            if (!grid_barrier(t, ggen)) return;
+            if (rank == 0) replica_import(t, s);
+            if (!grid_barrier(t, ggen)) return;
+        }
     }
 }
 
@@ -2770,7 +2852,8 @@ int alns_row_cap(int n, int m, int qmax, const vrprpd_alns_params* P) {
 }
 
 size_t alns_device_bytes(int n, int m, int qmax, const vrprpd_alns_params* P, int iterations) {
-    return team_bytes(n, m, alns_row_cap(n, m, qmax, P), iterations, false) + sizeof(AlnsTeam) + 8192;
+    const size_t R = static_cast<size_t>(std::max(1, P->replicas));
+    return R * (team_bytes(n, m, alns_row_cap(n, m, qmax, P), iterations, false) + sizeof(AlnsTeam)) + 8192;
 }
 
 bool alns_supported(const vrprpd_instance* I, std::string* why) {
@@ -2784,12 +2867,15 @@ bool alns_supported(const vrprpd_instance* I, std::string* why) {
     return true;
 }
 
-static int choose_team_blocks(const vrprpd_instance* I, int requested, size_t smem, int* out) {
+static int choose_team_blocks(const vrprpd_instance* I, int requested, size_t smem, int nteams, int* out) {
     int occ = 0;
     { int rc_ = ensure_smem_limit(reinterpret_cast<const void*>(&alns_kernel)); if (rc_) return rc_; }
     VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alns_kernel, ALNS_THREADS, smem));
     VRP_CHECK(occ > 0, VRPRPD_EINVAL, "ALNS block does not fit on an SM (n=%d)", I->n);
-    const int maxb = occ * I->num_sms;
+    // every CTA of every team is resident at once (a cooperative launch)
+    const int maxb = occ * I->num_sms / nteams;
+    VRP_CHECK(maxb >= 1, VRPRPD_EINVAL, "%d replicas exceed the %d resident ALNS blocks of this GPU", nteams,
+              occ * I->num_sms);
     int tb = requested;
     if (tb <= 0) {
         // about one tile of the first step's matrix per CTA, at least one CTA
@@ -2806,7 +2892,7 @@ static int launch_alns(const vrprpd_instance* I, AlnsTeam* d_teams, int nteams, 
                        cudaStream_t stream) {
     void* args[] = {&d_teams, &team_blocks};
     const int grid = nteams * team_blocks;
-    if (team_blocks > 1) {
+    if (grid > 1) {
         VRP_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(&alns_kernel), dim3(grid),
                                              dim3(ALNS_THREADS), args, smem, stream));
     } else {
@@ -2840,6 +2926,8 @@ extern "C" void vrprpd_alns_params_default(vrprpd_alns_params* P) {
     P->destroy_mask = 1;
     P->ls_pickup_every = 200;
     P->ls_relocate_every = 500;
+    P->replicas = 1;
+    P->sync_every = 1000;
 }
 
 // exact angular order around the depot: half plane, then cross product, then id
@@ -2911,11 +2999,22 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     const int iters = mode == 1 ? 0 : P->iterations;
     VRP_CHECK(iters >= 0 && iters <= (1 << 24), VRPRPD_EINVAL, "iterations out of range");
     VRP_CHECK(P->tau >= 1, VRPRPD_EINVAL, "tau must be >= 1");
+    VRP_CHECK(P->ls_pickup_every >= 0 && P->ls_relocate_every >= 0, VRPRPD_EINVAL,
+              "local-search periods must be >= 0 (0 = off)");
     const bool dump = mode == 1;
+    const int R = dump ? 1 : std::max(1, P->replicas);
+    VRP_CHECK(R <= 1024, VRPRPD_EINVAL, "replicas must lie in [0, 1024] (%d)", R);
+    VRP_CHECK(P->sync_every >= 0, VRPRPD_EINVAL, "sync_every must be >= 0 (0 = never)");
     const int qcap = dump ? 1 : alns_row_cap(n, m, qmax, P);
     DevBuf B;
-    B.cap = team_bytes(n, m, qcap, iters, dump) + 4096;
+    const size_t per_team = team_bytes(n, m, qcap, iters, dump);
+    B.cap = per_team * R + 4096;
     VRP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&B.base), B.cap, stream));
+    auto cleanup = [&]() { cudaFreeAsync(B.base, stream); };
+    unsigned* gbar = B.take<unsigned>(4);
+    AlnsTeam* d_team = nullptr;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d_team), sizeof(AlnsTeam) * R, stream);
+    if (e != cudaSuccess) { cleanup(); set_error("alns setup: %s", cudaGetErrorString(e)); return VRPRPD_ECUDA; }
     AlnsTeam t{};
     t.n = n;
     t.m = m;
@@ -2940,17 +3039,26 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     t.iterations = iters;
     t.repair_mask = P->repair_mask & 15;
     t.destroy_mask = P->destroy_mask & 63;
-    VRP_CHECK(P->ls_pickup_every >= 0 && P->ls_relocate_every >= 0, VRPRPD_EINVAL,
-              "local-search periods must be >= 0 (0 = off)");
     t.ls_pickup = dump ? 0 : P->ls_pickup_every;
     t.ls_relocate = dump ? 0 : P->ls_relocate_every;
-    VRP_CHECK(t.destroy_mask != 0, VRPRPD_EINVAL, "destroy_mask enables no destroy operator");
-    VRP_CHECK(t.repair_mask != 0, VRPRPD_EINVAL, "repair_mask enables no repair operator");
-    t.key = stream_key(seed, RNG_STREAM_ALNS);
+    auto fail_all = [&](int code) { cleanup(); cudaFreeAsync(d_team, stream); return code; };
+    if (t.destroy_mask == 0) { set_error("destroy_mask enables no destroy operator"); return fail_all(VRPRPD_EINVAL); }
+    if (t.repair_mask == 0) { set_error("repair_mask enables no repair operator"); return fail_all(VRPRPD_EINVAL); }
     t.mode = mode;
     t.dump_c = dump_c;
-    carve_team(t, B, n, m, qcap, iters, dump);
-    auto cleanup = [&]() { cudaFreeAsync(B.base, stream); };
+    t.nreplicas = R;
+    t.sync_every = P->sync_every;
+    t.gbar = gbar;
+    t.sib = d_team;
+    // replica r draws from its own stream: the single-run stream for r = 0,
+    // else a draw of it far past any iteration's counters
+    const uint64_t key0 = stream_key(seed, RNG_STREAM_ALNS);
+    std::vector<AlnsTeam> ts(R, t);
+    for (int r = 0; r < R; ++r) {
+        ts[r].replica = r;
+        ts[r].key = r == 0 ? key0 : draw(key0, (0xFFFFFFFFull << 32) + static_cast<uint64_t>(r));
+        carve_team(ts[r], B, n, m, qcap, iters, dump);
+    }
     AlnsCtl ctl{};
     for (int i = 0; i < 8; ++i) ctl.wd[i] = 1.0;
     ctl.wr[0] = ctl.wr[1] = ctl.wr[2] = ctl.wr[3] = 1.0;
@@ -2958,35 +3066,29 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
         ctl.nrem = 1;
         ctl.wsel = 0;
     }
-    cudaError_t e = cudaMemcpyAsync(t.ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, stream);
+    e = cudaMemsetAsync(gbar, 0, 16, stream);
+    for (int r = 0; r < R && e == cudaSuccess; ++r) e = cudaMemcpyAsync(ts[r].ctl, &ctl, sizeof(ctl), cudaMemcpyHostToDevice, stream);
     std::vector<int32_t> init_ops(2 * n), init_off(m + 1);
     if (!dump) {
         if (init) {
             std::memcpy(init_ops.data(), init->ops, 2 * n * 4);
             std::memcpy(init_off.data(), init->off, (m + 1) * 4);
         } else {
-            vrprpd_solution s{init_ops.data(), init_off.data(), 0, 0};
-            int rc = vrprpd_initial_solution(I, &s);
-            if (rc) { cleanup(); return rc; }
+            vrprpd_solution s0{init_ops.data(), init_off.data(), 0, 0};
+            int rc = vrprpd_initial_solution(I, &s0);
+            if (rc) return fail_all(rc);
         }
-        if (e == cudaSuccess) e = cudaMemcpyAsync(t.cur_ops, init_ops.data(), 2 * n * 4, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(t.cur_off, init_off.data(), (m + 1) * 4, cudaMemcpyHostToDevice, stream);
+        for (int r = 0; r < R && e == cudaSuccess; ++r) {
+            e = cudaMemcpyAsync(ts[r].cur_ops, init_ops.data(), 2 * n * 4, cudaMemcpyHostToDevice, stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(ts[r].cur_off, init_off.data(), (m + 1) * 4, cudaMemcpyHostToDevice, stream);
+        }
     } else {
         const int Nops = dump_off[m];
-        if (e == cudaSuccess) e = cudaMemcpyAsync(t.W_ops[0], dump_ops, std::max(Nops, 1) * 4, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(t.W_off[0], dump_off, (m + 1) * 4, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(t.rem, &dump_c, 4, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ts[0].W_ops[0], dump_ops, std::max(Nops, 1) * 4, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ts[0].W_off[0], dump_off, (m + 1) * 4, cudaMemcpyHostToDevice, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(ts[0].rem, &dump_c, 4, cudaMemcpyHostToDevice, stream);
         const size_t G = static_cast<size_t>(Nops) + m;
-        if (e == cudaSuccess) e = cudaMemsetAsync(t.dump_delta, 0xff, G * G * 4, stream);
-    }
-    AlnsTeam* d_team = nullptr;
-    if (e == cudaSuccess) e = cudaMallocAsync(reinterpret_cast<void**>(&d_team), sizeof(AlnsTeam), stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(d_team, &t, sizeof(AlnsTeam), cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) {
-        cleanup();
-        cudaFreeAsync(d_team, stream);
-        set_error("alns setup: %s", cudaGetErrorString(e));
-        return VRPRPD_ECUDA;
+        if (e == cudaSuccess) e = cudaMemsetAsync(ts[0].dump_delta, 0xff, G * G * 4, stream);
     }
     // recompute distances from staged coordinates only when that costs no resident CTAs
     size_t smem = alns_smem_words(n, m, false) * 4;
@@ -2997,84 +3099,101 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, alns_kernel, ALNS_THREADS, smem);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, alns_kernel, ALNS_THREADS, smem_c);
         if (occ1 >= occ0 && smem_c <= I->smem_optin) smem = smem_c;
-        else t.coords = nullptr;
-        cudaMemcpyAsync(d_team, &t, sizeof(AlnsTeam), cudaMemcpyHostToDevice, stream);
+        else for (auto& x : ts) x.coords = nullptr;
     }
-    VRP_CHECK(smem <= I->smem_optin, VRPRPD_EINVAL, "ALNS shared memory %zu exceeds the limit", smem);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_team, ts.data(), sizeof(AlnsTeam) * R, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) {
+        set_error("alns setup: %s", cudaGetErrorString(e));
+        return fail_all(VRPRPD_ECUDA);
+    }
+    if (smem > I->smem_optin) {
+        set_error("ALNS shared memory %zu exceeds the limit", smem);
+        return fail_all(VRPRPD_EINVAL);
+    }
     int tb = 1;
-    int rc = choose_team_blocks(I, P->team_blocks, smem, &tb);
-    if (rc) { cleanup(); cudaFreeAsync(d_team, stream); return rc; }
+    int rc = choose_team_blocks(I, P->team_blocks, smem, R, &tb);
+    if (rc) return fail_all(rc);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, stream);
-    rc = launch_alns(I, d_team, 1, tb, smem, stream);
+    rc = launch_alns(I, d_team, R, tb, smem, stream);
     cudaEventRecord(e1, stream);
-    if (rc) { cleanup(); cudaFreeAsync(d_team, stream); return rc; }
+    if (rc) return fail_all(rc);
     e = cudaStreamSynchronize(stream);
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    AlnsCtl out{};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&out, t.ctl, sizeof(out), cudaMemcpyDeviceToHost, stream);
+    std::vector<AlnsCtl> out(R);
+    for (int r = 0; r < R && e == cudaSuccess; ++r) e = cudaMemcpyAsync(&out[r], ts[r].ctl, sizeof(AlnsCtl), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) {
-        cleanup();
-        cudaFreeAsync(d_team, stream);
         set_error("alns run: %s", cudaGetErrorString(e));
-        return VRPRPD_ECUDA;
+        return fail_all(VRPRPD_ECUDA);
     }
-    if (out.err != 0) {
-        cleanup();
-        cudaFreeAsync(d_team, stream);
-        set_error("alns device error %d (%s)", out.err,
-                  out.err == DEV_TIMEOUT_BARRIER ? "team barrier timed out" : "inconsistent state");
-        return out.err == DEV_TIMEOUT_BARRIER ? VRPRPD_ETIMEOUT : VRPRPD_ECUDA;
+    for (int r = 0; r < R; ++r) {
+        if (out[r].err != 0) {
+            set_error("alns device error %d (%s)", out[r].err,
+                      out[r].err == DEV_TIMEOUT_BARRIER ? "team barrier timed out" : "inconsistent state");
+            return fail_all(out[r].err == DEV_TIMEOUT_BARRIER ? VRPRPD_ETIMEOUT : VRPRPD_ECUDA);
+        }
     }
+    // the best of all replicas, the lowest index on ties; replica 0 reports
+    // the current solution, the temperature and the weights
+    int g = 0;
+    for (int r = 1; r < R; ++r)
+        if (out[r].z_best < out[g].z_best) g = r;
     if (dump) {
         const size_t G = static_cast<size_t>(dump_off[m]) + m;
-        e = cudaMemcpyAsync(dump_delta, t.dump_delta, G * G * 4, cudaMemcpyDeviceToHost, stream);
-        if (e == cudaSuccess && dump_travel) e = cudaMemcpyAsync(dump_travel, t.dump_travel, G * G * 4, cudaMemcpyDeviceToHost, stream);
+        e = cudaMemcpyAsync(dump_delta, ts[0].dump_delta, G * G * 4, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess && dump_travel) e = cudaMemcpyAsync(dump_travel, ts[0].dump_travel, G * G * 4, cudaMemcpyDeviceToHost, stream);
     } else {
         if (best) {
-            e = cudaMemcpyAsync(best->ops, t.best_ops, 2 * n * 4, cudaMemcpyDeviceToHost, stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(best->off, t.best_off, (m + 1) * 4, cudaMemcpyDeviceToHost, stream);
-            best->makespan = out.z_best;
+            e = cudaMemcpyAsync(best->ops, ts[g].best_ops, 2 * n * 4, cudaMemcpyDeviceToHost, stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(best->off, ts[g].best_off, (m + 1) * 4, cudaMemcpyDeviceToHost, stream);
+            best->makespan = out[g].z_best;
             best->status = 0;
         }
         if (current && e == cudaSuccess) {
-            e = cudaMemcpyAsync(current->ops, t.cur_ops, 2 * n * 4, cudaMemcpyDeviceToHost, stream);
-            if (e == cudaSuccess) e = cudaMemcpyAsync(current->off, t.cur_off, (m + 1) * 4, cudaMemcpyDeviceToHost, stream);
-            current->makespan = out.z_cur;
+            e = cudaMemcpyAsync(current->ops, ts[0].cur_ops, 2 * n * 4, cudaMemcpyDeviceToHost, stream);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(current->off, ts[0].cur_off, (m + 1) * 4, cudaMemcpyDeviceToHost, stream);
+            current->makespan = out[0].z_cur;
             current->status = 0;
         }
-        if (trace && e == cudaSuccess && iters > 0) e = cudaMemcpyAsync(trace, t.trace, iters * 4, cudaMemcpyDeviceToHost, stream);
+        for (int r = 0; r < R && trace && e == cudaSuccess && iters > 0; ++r)
+            e = cudaMemcpyAsync(trace + static_cast<size_t>(r) * iters, ts[r].trace, iters * 4, cudaMemcpyDeviceToHost, stream);
     }
     if (stats) {
         std::memset(stats, 0, sizeof(*stats));
         stats->iterations = iters;
-        stats->accepted = out.accepted;
-        stats->improved = out.improved;
-        stats->new_best = out.new_best;
-        stats->reheats = out.reheats;
-        stats->rejected_infeasible = out.rejected;
-        stats->z_init = out.z_init;
-        stats->z_best = out.z_best;
-        stats->z_current = out.z_cur;
-        stats->T_final = out.T;
-        for (int i = 0; i < 8; ++i) stats->w_destroy[i] = i < ND_OPS ? out.wd[i] : 0.0;
-        for (int i = 0; i < 4; ++i) stats->w_repair[i] = out.wr[i];
+        for (int r = 0; r < R; ++r) {
+            const AlnsCtl& o = out[r];
+            stats->accepted += o.accepted;
+            stats->improved += o.improved;
+            stats->new_best += o.new_best;
+            stats->reheats += o.reheats;
+            stats->rejected_infeasible += o.rejected;
+            stats->matrix_entries += static_cast<int64_t>(o.entries);
+            stats->fallback_entries += static_cast<int64_t>(o.fallback_entries);
+            stats->incremental_steps += static_cast<int64_t>(o.steps_incr);
+            stats->full_steps += static_cast<int64_t>(o.steps_full);
+            stats->ls_moves += o.ls_moves;
+            stats->ls_new_best += o.ls_new_best;
+            stats->imports += o.imports;
+        }
+        stats->z_init = out[0].z_init;
+        stats->z_best = out[g].z_best;
+        stats->z_current = out[0].z_cur;
+        stats->T_final = out[0].T;
+        for (int i = 0; i < 8; ++i) stats->w_destroy[i] = i < ND_OPS ? out[0].wd[i] : 0.0;
+        for (int i = 0; i < 4; ++i) stats->w_repair[i] = out[0].wr[i];
         stats->device_ms = ms;
-        stats->matrix_entries = static_cast<int64_t>(out.entries);
-        stats->fallback_entries = static_cast<int64_t>(out.fallback_entries);
         stats->team_blocks = tb;
-        for (int i = 0; i < 6; ++i) stats->phase_ms[i] = static_cast<double>(out.phase_ns[i]) * 1e-6;
-        stats->incremental_steps = static_cast<int64_t>(out.steps_incr);
-        stats->full_steps = static_cast<int64_t>(out.steps_full);
-        stats->ls_moves = out.ls_moves;
-        stats->ls_new_best = out.ls_new_best;
-        stats->ls_ms = static_cast<double>(out.phase_ns[6]) * 1e-6;
+        for (int i = 0; i < 6; ++i) stats->phase_ms[i] = static_cast<double>(out[0].phase_ns[i]) * 1e-6;
+        stats->ls_ms = static_cast<double>(out[0].phase_ns[6]) * 1e-6;
+        stats->replicas = R;
+        stats->best_replica = g;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     cleanup();

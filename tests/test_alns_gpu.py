@@ -295,3 +295,40 @@ def test_alns_local_search_team_blocks_agree(vrp):
     assert np.array_equal(runs[0]["best_ops"], runs[1]["best_ops"])
     assert runs[0]["stats"].ls_moves == runs[1]["stats"].ls_moves
     assert oracle.evaluate(oi, runs[0]["best_ops"], runs[0]["best_off"]) == (runs[0]["z_best"], 0)
+
+
+def replicas_both(vrp, w, iters, seed, R, sync, q=(0, 0), mask=3, dmask=1, ls=(200, 500), team_blocks=0):
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    init = oracle.initial_solution(oi, w.coords)
+    g = vrp.alns_run(inst, vrp.alns_params(iters, q[0], q[1], mask, team_blocks, destroy_mask=dmask,
+                                           ls_pickup_every=ls[0], ls_relocate_every=ls[1], replicas=R,
+                                           sync_every=sync), seed=seed, init=init)
+    o = oracle.alns_run_replicas(oi, init[0], init[1],
+                                 oracle.alns_params(iters, q[0], q[1], mask, destroy_mask=dmask,
+                                                    ls_pickup_every=ls[0], ls_relocate_every=ls[1]),
+                                 seed, R, sync)
+    assert np.array_equal(g["traces"], o["traces"]), np.argwhere(g["traces"] != o["traces"])[:5]
+    gs = g["stats"]
+    assert gs.replicas == R and gs.imports == o["imports"] and gs.best_replica == o["best_replica"]
+    for f in ("accepted", "improved", "new_best", "reheats", "rejected_infeasible", "ls_moves"):
+        assert getattr(gs, f) == sum(getattr(st, f) for st in o["stats"]), f
+    assert np.array_equal(g["best_ops"], o["best_ops"]) and np.array_equal(g["best_off"], o["best_off"])
+    assert oracle.evaluate(oi, g["best_ops"], g["best_off"]) == (g["z_best"], 0)
+    return g, o
+
+
+@pytest.mark.parametrize("R,sync", [(3, 5), (4, 7)])
+def test_alns_replicas_small(vrp, R, sync):
+    # multi-instance ALNS (Section 4.2.1): replicas on their own streams, the
+    # best of all imported at every checkpoint
+    w = workloads.make_instance(24, 3, 6, 4, "5x", seed=7)
+    g, o = replicas_both(vrp, w, 30, 5, R, sync, q=(3, 6), mask=15, dmask=63, ls=(9, 13))
+    assert o["imports"] > 0
+
+
+def test_alns_replicas_medium(vrp):
+    # several CTAs per replica (the grid barrier spans teams of 8)
+    w = workloads.make_instance(60, 4, 10, 5, "2x", seed=3)
+    g, o = replicas_both(vrp, w, 8, 5, 4, 3, q=(4, 8))
+    assert g["stats"].team_blocks > 1
