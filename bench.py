@@ -188,6 +188,15 @@ def run_searches(vrp, args):
         "z_init": st.z_init, "z_best": st.z_best, "device_ms": st.device_ms,
         "phase_ms": dict(zip(["begin", "prep", "gaps", "matrix", "select", "end"], list(st.phase_ms))),
         "incremental_steps": st.incremental_steps, "full_steps": st.full_steps}
+    # the paper's multi-instance configuration: 32 replicas share the GPU
+    # (Section 4.2.1), each a team of 1/32 of the resident CTAs
+    rr = vrp.alns_run(i5, vrp.alns_params(args.alns_iters // 2, replicas=32, sync_every=5), seed=0)
+    sr = rr["stats"]
+    out["alns_n1000_x32"] = {
+        "value": 32 * (args.alns_iters // 2) / (sr.device_ms / 1000.0), "unit": "ALNS iters/s (all replicas)",
+        "config": "as alns_n1000 with 32 replicas (multi-instance, Section 4.2.1), best-of-all import every "
+                  "5 iterations", "iterations_per_replica": args.alns_iters // 2, "team_blocks": sr.team_blocks,
+        "imports": sr.imports, "z_best": sr.z_best, "device_ms": sr.device_ms}
     w2 = workloads.make_instance(100, 4, 10, 5, "2x", "uniform", seed=0)
     i2 = vrp.Instance.from_workload(w2)
     r2 = vrp.alns_run(i2, vrp.alns_params(args.alns_iters * 10, 10, 10), seed=0)
