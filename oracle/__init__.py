@@ -95,6 +95,7 @@ def lib():
             L.oracle_sp_closure.argtypes = [i32p, C.c_int32, i64p]
             L.oracle_coordination.argtypes = [C.POINTER(Inst), i32p, i32p, i32p, i32p]
             L.oracle_coordination.restype = C.c_uint32
+            L.oracle_initial_solution_paper.argtypes = [C.POINTER(Inst), i32p, C.c_int32, i32p, i32p]
             L.oracle_alns_run_replicas.argtypes = [C.POINTER(Inst), i32p, i32p, C.POINTER(AlnsParams), C.c_uint64,
                                                    C.c_int32, C.c_int32, i32p, i32p, i32p,
                                                    C.POINTER(AlnsStats), i32p, i32p]
@@ -356,6 +357,18 @@ def alns_run_replicas(I, init_ops, init_off, params, seed, replicas, sync_every=
         raise ValueError(f"oracle_alns_run_replicas failed rc={rc}")
     return dict(best_ops=bo, best_off=bf, best_replica=int(br[0]), stats=list(stats),
                 traces=traces[:, :params.iterations], imports=int(imp[0]))
+
+
+def initial_solution_paper(I, coords, refine_rounds=10):
+    """The paper's three-phase constructor and its refinement (Section 4.2.5)."""
+    ops = np.zeros(2 * I.n, np.int32)
+    off = np.zeros(I.m + 1, np.int32)
+    cc = np.ascontiguousarray(coords, dtype=np.int32) if coords is not None else None
+    rc = lib().oracle_initial_solution_paper(C.byref(I.c), _p(cc) if cc is not None else None, refine_rounds,
+                                             _p(ops), _p(off))
+    if rc != 0:
+        raise ValueError(f"oracle_initial_solution_paper failed rc={rc}")
+    return ops, off
 
 
 LS_PICKUP, LS_RELOCATE = 1, 2

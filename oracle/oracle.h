@@ -149,6 +149,12 @@ int oracle_decode_l(const oracle_inst* I, const float* keys, int32_t layout, int
 void oracle_encode(const oracle_inst* I, const int32_t* ops, const int32_t* off, float* keys);
 void oracle_encode_l(const oracle_inst* I, const int32_t* ops, const int32_t* off, int32_t layout, float* keys);
 
+/* The paper's three-phase initial solution (Section 4.2.5: sweep sectors,
+ * load balancing below 10% imbalance, nearest-neighbour routes) and up to
+ * refine_rounds rounds of its local-search refinement.  coords may be NULL. */
+int oracle_initial_solution_paper(const oracle_inst* I, const int32_t* coords, int32_t refine_rounds,
+                                  int32_t* ops, int32_t* off);
+
 /* Construction seed h (0 nearest neighbour, 1 load-balanced, 2 shortest
  * processing time) of the BRKGA warm start as a chromosome (Section 4.4.4). */
 void oracle_seed_chromosome(const oracle_inst* I, int32_t h, int32_t layout, float* keys);

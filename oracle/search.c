@@ -905,6 +905,117 @@ int oracle_alns_run_replicas(const oracle_inst* I, const int32_t* init_ops, cons
     return rc ? -2 : 0;
 }
 
+/* The paper's three-phase constructor (Section 4.2.5), then its refinement.
+ *   1. sweep: customers by exact angle around the depot (coordinates; without
+ *      coordinates, by id), cut into m' = min(m, R) sectors of equal count
+ *      (customer k of the order goes to sector floor(k m' / n));
+ *   2. load balancing on w_c = 2 d(0,c) + p_c: while 10 m' (W_max - W_min) >=
+ *      sum W (imbalance of 10% of the mean or more), the heaviest sector
+ *      (lowest index on ties) hands its boundary customer to its lighter
+ *      neighbour (lower index on ties), unless that would leave the
+ *      neighbour at least as heavy as the heaviest was; at most 4n moves;
+ *   3. nearest-neighbour routes: vehicle v serves its sector alone, starting
+ *      at the depot at time 0 with b = min(Q, floor(R / m')) resources; at
+ *      each step it takes the feasible op that completes first (a drop if a
+ *      resource is left: arrival; a pickup of a dropped customer: max(arrival,
+ *      T_drop + p)), ties by travel, then drop before pickup, then id.
+ *   Refinement: rounds of pickup repositioning then cross-agent relocation
+ *   (the periodic local search, three passes each) until a round moves
+ *   nothing, at most refine_rounds rounds.
+ * Feasible by construction: one vehicle per customer, at most b outstanding. */
+int oracle_initial_solution_paper(const oracle_inst* I, const int32_t* coords, int32_t refine_rounds,
+                                  int32_t* ops, int32_t* off) {
+    const int n = I->n, m = I->m;
+    if (I->R < 1 || I->Q < 1 || m < 1) return -1;
+    int* order = malloc(sizeof(int) * (n + 1));
+    for (int k = 0; k < n; k++) order[k] = k + 1;
+    if (coords) {
+        g_coords = coords;
+        qsort(order, (size_t)n, sizeof(int), angle_cmp);
+    }
+    const int mp = m < I->R ? m : I->R;
+    int b = I->R / mp;
+    if (b > I->Q) b = I->Q;
+    int* start = calloc((size_t)mp + 1, sizeof(int));
+    int64_t* Wl = calloc((size_t)mp, sizeof(int64_t));
+    for (int k = 0; k < n; k++) {
+        const int sct = (int)(((int64_t)k * mp) / n);
+        Wl[sct] += 2 * Dd(I, 0, order[k]) + I->p[order[k] - 1];
+    }
+    for (int sct = 0; sct <= mp; sct++) start[sct] = (int)(((int64_t)sct * n + mp - 1) / mp);
+    for (int mv = 0; mv < 4 * n && mp > 1; mv++) {
+        int h = 0, l = 0;
+        int64_t tot = 0;
+        for (int sct = 0; sct < mp; sct++) {
+            tot += Wl[sct];
+            if (Wl[sct] > Wl[h]) h = sct;
+            if (Wl[sct] < Wl[l]) l = sct;
+        }
+        if (10 * (int64_t)mp * (Wl[h] - Wl[l]) < tot) break;
+        int g = -1;
+        if (h > 0) g = h - 1;
+        if (h + 1 < mp && (g < 0 || Wl[h + 1] < Wl[g])) g = h + 1;
+        if (start[h + 1] == start[h]) break;
+        const int c = g < h ? order[start[h]] : order[start[h + 1] - 1];
+        const int64_t wc = 2 * Dd(I, 0, c) + I->p[c - 1];
+        if (Wl[g] + wc >= Wl[h]) break;
+        Wl[g] += wc;
+        Wl[h] -= wc;
+        if (g < h) start[h]++; else start[h + 1]--;
+    }
+    /* nearest-neighbour routes, one vehicle per sector */
+    char* state = calloc((size_t)n + 1, 1);      /* 0 waiting, 1 dropped, 2 picked */
+    int64_t* rdy = calloc((size_t)n + 1, sizeof(int64_t));
+    int w = 0;
+    off[0] = 0;
+    for (int v = 0; v < m; v++) {
+        if (v < mp) {
+            int64_t t = 0;
+            int loc = 0, out = 0;
+            const int cnt = start[v + 1] - start[v];
+            for (int step = 0; step < 2 * cnt; step++) {
+                int bo = -1;
+                int64_t bt = 0, bd = 0;
+                for (int k = start[v]; k < start[v + 1]; k++) {
+                    const int c = order[k];
+                    if (state[c] == 2 || (state[c] == 0 && out >= b)) continue;
+                    const int pick = state[c] == 1;
+                    const int64_t dl = Dd(I, loc, c);
+                    int64_t fin = t + dl;
+                    if (pick && rdy[c] > fin) fin = rdy[c];
+                    const int o = 2 * c + pick;
+                    int better = bo < 0;
+                    if (!better) {
+                        if (fin != bt) better = fin < bt;
+                        else if (dl != bd) better = dl < bd;
+                        else if ((o & 1) != (bo & 1)) better = (o & 1) < (bo & 1);
+                        else better = o < bo;
+                    }
+                    if (better) { bo = o; bt = fin; bd = dl; }
+                }
+                const int c = bo >> 1;
+                if (bo & 1) { state[c] = 2; out--; }
+                else { state[c] = 1; out++; rdy[c] = bt + I->p[c - 1]; }
+                t = bt;
+                loc = c;
+                ops[w++] = bo;
+            }
+        }
+        off[v + 1] = w;
+    }
+    free(state); free(rdy); free(order); free(start); free(Wl);
+    int32_t z;
+    uint32_t st;
+    oracle_evaluate(I, ops, off, 0, &z, &st, NULL);
+    if (st) return -3;
+    for (int r = 0; r < refine_rounds; r++) {
+        int moved = local_search(I, LS_PICKUP, ops, off, &z, 3);
+        moved += local_search(I, LS_RELOCATE, ops, off, &z, 3);
+        if (!moved) break;
+    }
+    return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* BRKGA decoder (Algorithm 2).  keys[0..2n) are op priorities (op index     */
 /* 2(c-1)+isPickup); then either m vehicle keys ordering the vehicles for    */
