@@ -266,6 +266,8 @@ typedef struct {
                                   index among equal bests) takes that solution as its current and best.
                                   The paper's replicas poll without meeting; meeting makes runs
                                   reproducible. */
+    int32_t init_mode;         /* start solution when init is NULL: 0 (default) vrprpd_initial_solution,
+                                  1 vrprpd_initial_solution_paper with 10 refinement rounds */
 } vrprpd_alns_params;
 
 typedef struct {
@@ -299,6 +301,28 @@ void vrprpd_alns_params_default(vrprpd_alns_params* params);
  * sector in blocks "D c1..cb, P c1..cb" with b = min(Q, R / min(m, R)).
  * out->ops / out->off are host buffers of 2n and m+1 int32; needs R, Q >= 1. */
 int vrprpd_initial_solution(const vrprpd_instance* inst, vrprpd_solution* out);
+
+/*
+ * The paper's three-phase initial solution (Section 4.2.5), built on the
+ * device, then refined:
+ *   1. customers by exact angle around the depot (by id for an instance made
+ *      from a distance matrix), cut into m' = min(m, R) sectors of equal count;
+ *   2. load balancing on w_c = 2 d(0,c) + p_c: while the spread of the sector
+ *      workloads is at least 10% of their mean, the heaviest sector (lowest
+ *      index on ties) hands its boundary customer to its lighter neighbour,
+ *      as long as that lowers the heavier of the two (at most 4n moves);
+ *   3. nearest-neighbour routes: vehicle v serves sector v alone, leaving the
+ *      depot with b = min(Q, floor(R/m')) resources, each step taking the
+ *      feasible op that completes first (ties: travel, drop before pickup,
+ *      op code).
+ * Refinement: up to refine_rounds rounds of the periodic local search
+ * (pickup repositioning, then cross-agent relocation, three passes each),
+ * stopping at the first round that moves nothing.
+ *   out  host buffers (2n ops, m+1 offsets); out->makespan is set.
+ * Needs what vrprpd_alns_run needs.  Blocking: returns when done.
+ */
+int vrprpd_initial_solution_paper(const vrprpd_instance* inst, int32_t refine_rounds, vrprpd_solution* out,
+                                  void* stream);
 
 /*
  * Run Algorithm 1 on the device: roulette selection of the enabled destroy

@@ -271,6 +271,14 @@ def initial_solution(inst):
     return ops, off
 
 
+def initial_solution_paper(inst, refine_rounds=10, stream=None):
+    """The paper's three-phase constructor and its refinement (Section 4.2.5),
+    on the device; returns (ops, off, makespan)."""
+    s, ops, off = _sol(inst)
+    _check(lib().vrprpd_initial_solution_paper(inst.handle, refine_rounds, C.byref(s), _stream_ptr(stream)))
+    return ops, off, s.makespan
+
+
 def alns_params(iterations=1000, q_min=0, q_max=0, repair_mask=3, team_blocks=0, **over):
     from ._search_sig import AlnsParams
     p = AlnsParams()

@@ -13,7 +13,7 @@ class AlnsParams(C.Structure):
                 ("q_min", C.c_int32), ("q_max", C.c_int32), ("iterations", C.c_int32),
                 ("repair_mask", C.c_int32), ("team_blocks", C.c_int32),
                 ("destroy_mask", C.c_int32), ("ls_pickup_every", C.c_int32), ("ls_relocate_every", C.c_int32),
-                ("replicas", C.c_int32), ("sync_every", C.c_int32)]
+                ("replicas", C.c_int32), ("sync_every", C.c_int32), ("init_mode", C.c_int32)]
 
 
 class AlnsStats(C.Structure):
@@ -58,6 +58,7 @@ def register(L):
     L.vrprpd_alns_params_default.argtypes = [C.POINTER(AlnsParams)]
     L.vrprpd_alns_params_default.restype = None
     L.vrprpd_initial_solution.argtypes = [vp, C.POINTER(Solution)]
+    L.vrprpd_initial_solution_paper.argtypes = [vp, C.c_int32, C.POINTER(Solution), vp]
     L.vrprpd_alns_run.argtypes = [vp, C.POINTER(Solution), C.POINTER(AlnsParams), C.c_uint64,
                                   C.POINTER(Solution), C.POINTER(Solution), C.POINTER(AlnsStats), vp, vp]
     L.vrprpd_insertion_matrix.argtypes = [vp, vp, vp, C.c_int32, vp, vp, vp]

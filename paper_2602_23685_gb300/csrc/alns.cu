@@ -114,7 +114,8 @@ struct AlnsTeam {
     unsigned* gbar;          // [2] grid barrier over all teams: count, generation
     const AlnsTeam* sib;     // device array of all teams (siblings' best solutions at checkpoints)
     unsigned long long key;  // RNG stream key
-    int mode;                // 0 = search, 1 = one-customer matrix dump
+    int mode;                // 0 = search, 1 = one-customer matrix dump, 2 = refine the start solution
+    int refine_rounds;       // mode 2: local-search rounds at most
     int dump_c;
     const int* coords;       // device (n+1) x 2 when distances can be recomputed exactly, else null
     // state and scratch (device)
@@ -2608,7 +2609,7 @@ __device__ __noinline__ void ls_finish(const AlnsTeam& t, const Smem& s, int it)
             ctl->stagnation = 0;
             ctl->ls_new_best += 1;
         }
-        if (t.trace) t.trace[it - 1] = ctl->z_cur;
+        if (t.trace && it > 0) t.trace[it - 1] = ctl->z_cur;
     }
     __syncthreads();
     if (flag[0]) {
@@ -2616,6 +2617,40 @@ __device__ __noinline__ void ls_finish(const AlnsTeam& t, const Smem& s, int it)
         for (int v = threadIdx.x; v <= t.m; v += blockDim.x) t.best_off[v] = t.cur_off[v];
     }
     __syncthreads();
+}
+
+// The local search of one iteration (it = 0: outside the iterations), every
+// CTA of the team: up to three passes of each mode in lsm, pickup
+// repositioning first.  False when a team barrier gave up.
+__device__ bool ls_block(const AlnsTeam& t, const Smem& s, int rank, int team_blocks, unsigned& gen, int lsm, int it) {
+    AlnsCtl* ctl = t.ctl;
+    for (int mode = LS_PICKUP; mode <= LS_RELOCATE; ++mode) {
+        if (!(lsm & mode)) continue;
+        for (int pass = 0; pass < 3; ++pass) {
+            if (rank == 0) ls_candidates(t, s, mode);
+            if (!team_barrier(ctl, team_blocks, gen)) return false;
+            const int ncand = *reinterpret_cast<volatile int*>(&ctl->ls_ncand);
+            for (int k = 0; k < ncand; ++k) {
+                if (rank == 0) ls_setup(t, s, mode, k);
+                if (!team_barrier(ctl, team_blocks, gen)) return false;
+                if (*reinterpret_cast<volatile int*>(&ctl->nrem) == 0) continue;
+                phase_prep(t, s, rank, team_blocks, false);
+                if (!team_barrier(ctl, team_blocks, gen)) return false;
+                phase_gaps(t, s, rank, team_blocks);
+                team_arrive(ctl, team_blocks, gen);
+                gap_walks(t, s, rank, team_blocks);
+                if (!team_wait(ctl, team_blocks, gen)) return false;
+                phase_matrix(t, s);
+                if (!team_barrier(ctl, team_blocks, gen)) return false;
+                if (rank == 0) ls_collect(t, s);
+            }
+            if (rank == 0) ls_apply(t, s);
+            if (!team_barrier(ctl, team_blocks, gen)) return false;
+            if (!*reinterpret_cast<volatile int*>(&ctl->ls_moved)) break;
+        }
+    }
+    if (rank == 0) ls_finish(t, s, it);
+    return team_barrier(ctl, team_blocks, gen);
 }
 
 __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, int team_blocks) {
@@ -2655,6 +2690,15 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
         phase_end(t, s, true);
     }
     if (!team_barrier(ctl, team_blocks, gen)) return;
+    if (t.mode == 2) {
+        // refinement of a start solution: local-search rounds until one moves nothing
+        for (int round = 0; round < t.refine_rounds; ++round) {
+            const int before = *reinterpret_cast<volatile int*>(&ctl->ls_moves);
+            if (!ls_block(t, s, rank, team_blocks, gen, LS_PICKUP | LS_RELOCATE, 0)) return;
+            if (*reinterpret_cast<volatile int*>(&ctl->ls_moves) == before) break;
+        }
+        return;
+    }
     // wall time per phase, read by rank 0 at each barrier exit
     uint64_t tmark = global_ns();
     auto mark = [&](int ph) {
@@ -2716,33 +2760,7 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
         const int lsm = (t.ls_pickup > 0 && it % t.ls_pickup == 0 ? LS_PICKUP : 0) |
                         (t.ls_relocate > 0 && it % t.ls_relocate == 0 ? LS_RELOCATE : 0);
         if (lsm) {
-            for (int mode = LS_PICKUP; mode <= LS_RELOCATE; ++mode) {
-                if (!(lsm & mode)) continue;
-                for (int pass = 0; pass < 3; ++pass) {
-                    if (rank == 0) ls_candidates(t, s, mode);
-                    if (!team_barrier(ctl, team_blocks, gen)) return;
-                    const int ncand = *reinterpret_cast<volatile int*>(&ctl->ls_ncand);
-                    for (int k = 0; k < ncand; ++k) {
-                        if (rank == 0) ls_setup(t, s, mode, k);
-                        if (!team_barrier(ctl, team_blocks, gen)) return;
-                        if (*reinterpret_cast<volatile int*>(&ctl->nrem) == 0) continue;
-                        phase_prep(t, s, rank, team_blocks, false);
-                        if (!team_barrier(ctl, team_blocks, gen)) return;
-                        phase_gaps(t, s, rank, team_blocks);
-                        team_arrive(ctl, team_blocks, gen);
-                        gap_walks(t, s, rank, team_blocks);
-                        if (!team_wait(ctl, team_blocks, gen)) return;
-                        phase_matrix(t, s);
-                        if (!team_barrier(ctl, team_blocks, gen)) return;
-                        if (rank == 0) ls_collect(t, s);
-                    }
-                    if (rank == 0) ls_apply(t, s);
-                    if (!team_barrier(ctl, team_blocks, gen)) return;
-                    if (!*reinterpret_cast<volatile int*>(&ctl->ls_moved)) break;
-                }
-            }
-            if (rank == 0) ls_finish(t, s, it);
-            if (!team_barrier(ctl, team_blocks, gen)) return;
+            if (!ls_block(t, s, rank, team_blocks, gen, lsm, it)) return;
             mark(6);
         }
         if (t.nreplicas > 1 && t.sync_every > 0 && it % t.sync_every == 0) {
@@ -2928,6 +2946,7 @@ extern "C" void vrprpd_alns_params_default(vrprpd_alns_params* P) {
     P->ls_relocate_every = 500;
     P->replicas = 1;
     P->sync_every = 1000;
+    P->init_mode = 0;
 }
 
 // exact angular order around the depot: half plane, then cross product, then id
@@ -2983,7 +3002,7 @@ extern "C" int vrprpd_initial_solution(const vrprpd_instance* I, vrprpd_solution
 static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const vrprpd_alns_params* P,
                     uint64_t seed, int mode, int dump_c, const int32_t* dump_ops, const int32_t* dump_off,
                     vrprpd_solution* best, vrprpd_solution* current, vrprpd_alns_stats* stats, int32_t* trace,
-                    int32_t* dump_delta, int32_t* dump_travel, cudaStream_t stream) {
+                    int32_t* dump_delta, int32_t* dump_travel, cudaStream_t stream, int refine_rounds = 0) {
     std::string why;
     VRP_CHECK(alns_supported(I, &why), VRPRPD_EINVAL, "%s", why.c_str());
     const int n = I->n, m = I->m;
@@ -2996,13 +3015,13 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     qmin = std::min(qmin, qmax);
     VRP_CHECK(qmin >= 1 && qmax <= 1024, VRPRPD_EINVAL, "removal size must lie in [1, 1024] (q_min=%d q_max=%d)",
               qmin, qmax);
-    const int iters = mode == 1 ? 0 : P->iterations;
+    const int iters = mode == 0 ? P->iterations : 0;
     VRP_CHECK(iters >= 0 && iters <= (1 << 24), VRPRPD_EINVAL, "iterations out of range");
     VRP_CHECK(P->tau >= 1, VRPRPD_EINVAL, "tau must be >= 1");
     VRP_CHECK(P->ls_pickup_every >= 0 && P->ls_relocate_every >= 0, VRPRPD_EINVAL,
               "local-search periods must be >= 0 (0 = off)");
     const bool dump = mode == 1;
-    const int R = dump ? 1 : std::max(1, P->replicas);
+    const int R = mode != 0 ? 1 : std::max(1, P->replicas);
     VRP_CHECK(R <= 1024, VRPRPD_EINVAL, "replicas must lie in [0, 1024] (%d)", R);
     VRP_CHECK(P->sync_every >= 0, VRPRPD_EINVAL, "sync_every must be >= 0 (0 = never)");
     const int qcap = dump ? 1 : alns_row_cap(n, m, qmax, P);
@@ -3045,6 +3064,7 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     if (t.destroy_mask == 0) { set_error("destroy_mask enables no destroy operator"); return fail_all(VRPRPD_EINVAL); }
     if (t.repair_mask == 0) { set_error("repair_mask enables no repair operator"); return fail_all(VRPRPD_EINVAL); }
     t.mode = mode;
+    t.refine_rounds = refine_rounds;
     t.dump_c = dump_c;
     t.nreplicas = R;
     t.sync_every = P->sync_every;
@@ -3075,7 +3095,8 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
             std::memcpy(init_off.data(), init->off, (m + 1) * 4);
         } else {
             vrprpd_solution s0{init_ops.data(), init_off.data(), 0, 0};
-            int rc = vrprpd_initial_solution(I, &s0);
+            const int rc = P->init_mode == 1 ? vrprpd_initial_solution_paper(I, 10, &s0, stream)
+                                             : vrprpd_initial_solution(I, &s0);
             if (rc) return fail_all(rc);
         }
         for (int r = 0; r < R && e == cudaSuccess; ++r) {
@@ -3203,6 +3224,39 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
         return VRPRPD_ECUDA;
     }
     return VRPRPD_OK;
+}
+
+extern "C" int vrprpd_initial_solution_paper(const vrprpd_instance* I, int32_t refine_rounds, vrprpd_solution* out,
+                                             void* stream_) {
+    VRP_CHECK(I && out && out->ops && out->off, VRPRPD_EINVAL, "NULL argument");
+    VRP_CHECK(refine_rounds >= 0, VRPRPD_EINVAL, "refine_rounds must be >= 0");
+    std::string why;
+    VRP_CHECK(alns_supported(I, &why), VRPRPD_EINVAL, "%s", why.c_str());
+    const cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+    const int n = I->n, m = I->m;
+    int32_t* dops = nullptr;
+    VRP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dops), (2 * n + m + 1) * 4, stream));
+    int32_t* doff = dops + 2 * n;
+    int rc = construct_paper_device(I, dops, doff, stream);
+    cudaError_t e = cudaSuccess;
+    if (!rc) {
+        e = cudaMemcpyAsync(out->ops, dops, 2 * n * 4, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out->off, doff, (m + 1) * 4, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    }
+    cudaFreeAsync(dops, stream);
+    if (rc) return rc;
+    if (e != cudaSuccess) {
+        set_error("initial solution: %s", cudaGetErrorString(e));
+        return VRPRPD_ECUDA;
+    }
+    // evaluation and refinement in the ALNS kernel (refine-only mode)
+    vrprpd_alns_params P;
+    vrprpd_alns_params_default(&P);
+    std::vector<int32_t> io(out->ops, out->ops + 2 * n), of(out->off, out->off + m + 1);
+    vrprpd_solution start{io.data(), of.data(), 0, 0};
+    return run_team(I, &start, &P, 0, 2, 0, nullptr, nullptr, nullptr, out, nullptr, nullptr, nullptr, nullptr,
+                    stream, refine_rounds);
 }
 
 extern "C" int vrprpd_alns_run(const vrprpd_instance* I, const vrprpd_solution* init, const vrprpd_alns_params* P,

@@ -18,6 +18,8 @@ void set_error(const char* fmt, ...);
 // so setting it per launch would race between host threads that launch the
 // same kernel with different sizes; the size a launch uses is its own.
 int ensure_smem_limit(const void* kernel);
+// The paper's three-phase initial solution into device buffers (construct.cu).
+int construct_paper_device(const vrprpd_instance* I, int32_t* ops, int32_t* off, cudaStream_t stream);
 
 #define VRP_CUDA(call)                                                                   \
     do {                                                                                 \

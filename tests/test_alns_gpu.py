@@ -332,3 +332,39 @@ def test_alns_replicas_medium(vrp):
     w = workloads.make_instance(60, 4, 10, 5, "2x", seed=3)
     g, o = replicas_both(vrp, w, 8, 5, 4, 3, q=(4, 8))
     assert g["stats"].team_blocks > 1
+
+
+@pytest.mark.parametrize("n,m,R,Q,v,lay", [(16, 2, 4, 4, "base", "uniform"), (40, 4, 10, 5, "2x", "uniform"),
+                                           (60, 5, 20, 4, "1R20", "clustered"), (7, 5, 3, 2, "base", "uniform"),
+                                           (1000, 20, 100, 10, "1R20", "mixed")])
+def test_initial_solution_paper_matches_oracle(vrp, n, m, R, Q, v, lay):
+    # the three-phase constructor alone (Section 4.2.5)
+    w = workloads.make_instance(n, m, R, Q, v, lay, seed=n)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    go, gf, gz = vrp.initial_solution_paper(inst, 0)
+    oo, of = oracle.initial_solution_paper(oi, w.coords, 0)
+    assert np.array_equal(go, oo) and np.array_equal(gf, of)
+    assert oracle.evaluate(oi, go, gf) == (gz, 0)
+
+
+@pytest.mark.parametrize("n,m,R,Q,v", [(24, 3, 8, 4, "5x"), (40, 5, 10, 5, "2x")])
+def test_initial_solution_paper_refined_matches_oracle(vrp, n, m, R, Q, v):
+    w = workloads.make_instance(n, m, R, Q, v, seed=n + 1)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    go, gf, gz = vrp.initial_solution_paper(inst, 10)
+    oo, of = oracle.initial_solution_paper(oi, w.coords, 10)
+    assert np.array_equal(go, oo) and np.array_equal(gf, of)
+    assert oracle.evaluate(oi, go, gf) == (gz, 0)
+
+
+def test_alns_from_the_paper_start(vrp):
+    w = workloads.make_instance(24, 3, 8, 4, "2x", seed=12)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    g = vrp.alns_run(inst, vrp.alns_params(30, init_mode=1), seed=4)
+    init = oracle.initial_solution_paper(oi, w.coords, 10)
+    o = oracle.alns_run(oi, init[0], init[1], oracle.alns_params(30), 4)
+    assert np.array_equal(g["trace"], o["trace"]) and g["stats"].z_init == o["stats"].z_init
+    assert np.array_equal(g["best_ops"], o["best_ops"])
