@@ -266,8 +266,9 @@ typedef struct {
                                   index among equal bests) takes that solution as its current and best.
                                   The paper's replicas poll without meeting; meeting makes runs
                                   reproducible. */
-    int32_t init_mode;         /* start solution when init is NULL: 0 (default) vrprpd_initial_solution,
-                                  1 vrprpd_initial_solution_paper with 10 refinement rounds */
+    int32_t init_mode;         /* start solution when init is NULL: 1 (default) the paper's
+                                  vrprpd_initial_solution_paper with 10 refinement rounds, 0 the plain
+                                  sweep of vrprpd_initial_solution */
 } vrprpd_alns_params;
 
 typedef struct {

@@ -2946,7 +2946,7 @@ extern "C" void vrprpd_alns_params_default(vrprpd_alns_params* P) {
     P->ls_relocate_every = 500;
     P->replicas = 1;
     P->sync_every = 1000;
-    P->init_mode = 0;
+    P->init_mode = 1;
 }
 
 // exact angular order around the depot: half plane, then cross product, then id
