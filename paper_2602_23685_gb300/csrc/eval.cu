@@ -2,20 +2,23 @@
 // 4.2.3 and the decoder's schedule simulation of Section 4.4.2, done exactly
 // on the semantics of Section 3.1, Eqs. 7-23).
 //
-// Batched form: a persistent launch; every warp owns a tile of k = 32/m
-// candidates (one lane per route).  Per tile:
-//   1. a TMA bulk copy stages the tile's op arrays in shared memory (plain
-//      loads fill the unaligned head and tail);
-//   2. a pre-pass over all ops, 32 at a time, validates op codes (range and
-//      duplicates) and replaces each op in place by a packed word
-//      (travel-in time << 12 | op code), the travel-in being d(previous stop,
-//      this stop);
-//   3. the route walk: each lane advances its route one op per step --
-//      a drop publishes its pickup-ready time T_drop + p_c to shared memory,
-//      a pickup waits until that time is published (cross-vehicle precedence,
-//      Eq. 9) and then leaves at max(arrival, ready) (Eqs. 8, 10).  A group
-//      that makes no progress in a step while unfinished is a precedence
-//      cycle.  Each lane also tracks its route's stock prefix (Eqs. 13-18);
+// Batched form: a persistent launch; the block stages the instance (distances
+// or coordinates, and p) in shared memory with TMA bulk copies, and every warp
+// owns a tile of k = 32/m candidates (one lane per route).  Per tile:
+//   1. offsets are checked and every customer's ready slot is set to
+//      -(p_c + 1): negative means "not dropped yet", and the drop recovers p_c
+//      from the value it reads anyway;
+//   2. the ops are read with coalesced loads, four per lane in flight, checked
+//      (code range, duplicates by a shared bitmap) and kept as 16-bit codes:
+//      half the footprint of the 32-bit stream, so 24 warps fit per SM where
+//      a staged 32-bit copy left room for 16;
+//   3. the route walk: each lane advances its route up to two ops per step,
+//      computing each travel time from the previous stop -- a drop publishes
+//      its pickup-ready time T_drop + p_c to shared memory, a pickup waits
+//      until that time is published (cross-vehicle precedence, Eq. 9) and then
+//      leaves at max(arrival, ready) (Eqs. 8, 10).  A group that makes no
+//      progress in a step while unfinished is a precedence cycle.  Each lane
+//      also tracks its route's stock prefix (Eqs. 13-18);
 //   4. per-candidate reductions: makespan = max return time (Eqs. 21-22),
 //      vehicle capacity, depot pool.
 // Plain form: one thread per candidate, Kahn order over routes, scratch in
@@ -62,24 +65,26 @@ __device__ __forceinline__ int dist(const EvalArgs& a, const int32_t* sh, int i,
     } else if constexpr (DM == VRPRPD_DIST_GLOBAL32) {
         return __ldg(a.d32 + i * a.N + j);
     } else {
-        return euc2d_small(sh[2 * i], sh[2 * i + 1], sh[2 * j], sh[2 * j + 1]);
+        const int2 pi = reinterpret_cast<const int2*>(sh)[i];
+        const int2 pj = reinterpret_cast<const int2*>(sh)[j];
+        return euc2d_small(pi.x, pi.y, pj.x, pj.y);
     }
 }
 
 // One tile of k candidates of one instance, processed by one warp.
 // W is the warp's shared-memory region (layout from a), sh/sp the block's
-// staged distances or coordinates and p.  Returns false if a bounded TMA
-// wait gave up (the caller must stop).
+// staged distances or coordinates and p.
 template <int DM>
 __device__ __forceinline__ bool eval_tile(const EvalArgs& a, const int32_t* sh, const int32_t* sp, int32_t* W,
                                           uint64_t* bar, unsigned& phase, long long t) {
+    (void)bar;
+    (void)phase;
     const int lane = threadIdx.x & 31;
     const int n = a.n, m = a.m, two_n = 2 * n, k = a.k;
-    int32_t* A = W;
-    int32_t* ready = A + a.a_words;
+    uint16_t* A = reinterpret_cast<uint16_t*>(W);            // op codes, 16 bits each
+    int32_t* ready = W + a.a_words;
     uint32_t* seen = reinterpret_cast<uint32_t*>(ready + a.ready_words);
-    uint32_t* starts = seen + a.seen_words;
-    int32_t* soff = reinterpret_cast<int32_t*>(starts + a.start_words);
+    int32_t* soff = reinterpret_cast<int32_t*>(seen + a.seen_words + a.start_words);
     int32_t* valid = soff + a.off_words;
     int32_t* red = valid + a.valid_words;      // 96 words
     const int grp = lane / m, v = lane - grp * m;
@@ -89,29 +94,13 @@ __device__ __forceinline__ bool eval_tile(const EvalArgs& a, const int32_t* sh, 
     const int elems = kt * two_n;
     const int32_t* src = a.ops + first * two_n;
 
-    // ---- 1. stage ops: aligned interior by TMA, head/tail by plain loads ----
-    const uintptr_t s0 = reinterpret_cast<uintptr_t>(src);
-    const uintptr_t s1 = s0 + static_cast<uintptr_t>(elems) * 4u;
-    const uintptr_t i0 = (s0 + 15u) & ~static_cast<uintptr_t>(15u);
-    const uintptr_t i1 = s1 & ~static_cast<uintptr_t>(15u);
-    const bool bulk = i1 > i0;
-    const int k0 = bulk ? static_cast<int>((i0 - s0) >> 2) : elems;
-    const int ke = bulk ? static_cast<int>((i1 - s0) >> 2) : elems;
-    const int shift = (4 - (k0 & 3)) & 3;
-    int32_t* Ab = A + shift;
-    fence_proxy_async_smem();
-    __syncwarp();
-    if (lane == 0 && bulk) {
-        mbar_arrive_expect_tx(bar, static_cast<unsigned>(i1 - i0));
-        tma_bulk_g2s(Ab + k0, reinterpret_cast<const void*>(i0), static_cast<unsigned>(i1 - i0), bar);
-    }
-    for (int e = lane; e < k0; e += 32) Ab[e] = __ldg(src + e);
-    for (int e = ke + lane; e < elems; e += 32) Ab[e] = __ldg(src + e);
+    // ---- 1. offsets, flags, duplicate bitmap, unresolved ready times ----
     for (int i = lane; i < kt * (m + 1); i += 32) soff[i] = __ldg(a.off + first * (m + 1) + i);
     for (int i = lane; i < kt; i += 32) valid[i] = 1;
     for (int i = lane; i < kt * a.sw; i += 32) seen[i] = 0u;
-    for (int i = lane; i < (elems + 31) / 32; i += 32) starts[i] = 0u;
-    for (int i = lane; i < kt * (n + 1); i += 32) ready[i] = UNRESOLVED;
+    // unresolved ready time of c: -(p_c + 1) (negative); the drop recovers p_c from it
+    for (int g = 0; g < kt; ++g)
+        for (int c = lane; c <= n; c += 32) ready[g * (n + 1) + c] = -1 - sp[c];
     __syncwarp();
     // offsets: off[0] = 0, off[m] = 2n, non-decreasing
     for (int i = lane; i < kt * (m + 1); i += 32) {
@@ -121,125 +110,90 @@ __device__ __forceinline__ bool eval_tile(const EvalArgs& a, const int32_t* sh, 
                    (vv < m && val > soff[i + 1]);
         if (bad) atomicAnd(&valid[g], 0);
     }
-    __syncwarp();
-    for (int i = lane; i < kt * m; i += 32) {
-        const int g = i / m, vv = i - g * m;
-        if (!valid[g]) continue;
-        const int o0 = soff[g * (m + 1) + vv], o1 = soff[g * (m + 1) + vv + 1];
-        if (o0 < o1) {
-            const int e = g * two_n + o0;
-            atomicOr(&starts[e >> 5], 1u << (e & 31));
-        }
-    }
-    if (bulk) {
-        if (!mbar_wait_bounded(bar, phase)) {
-            if (lane == 0) atomicExch(a.err, DEV_TIMEOUT_TMA);
-            mbar_wait_bounded(bar, phase);
-            return false;
-        }
-        phase ^= 1u;
-    }
-    __syncwarp();
 
-    // ---- 2. pre-pass: validate and pack (travel-in << 12 | op) in place ----
-    // Four chunks of 32 ops per round so their distance reads overlap.
-    // Candidate index of element e without a division: the candidate of the
-    // round's first element plus boundary steps (none when k == 1).
+    // ---- 2. ops: coalesced loads, four in flight per lane; code range and
+    // duplicates; kept as 16-bit codes (the walk computes the travel times) ----
     {
-        int carry = 0, gbase = 0;
+        int gbase = 0;
         for (int base = 0; base < elems; base += 128) {
-            int raw[4], prv[4], gg[4], dd[4];
-            bool in[4], ok[4];
+            int raw[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int e = base + 32 * u + lane;
-                in[u] = e < elems;
-                raw[u] = in[u] ? Ab[e] : 2;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                int pv = __shfl_up_sync(FULL_MASK, raw[u], 1);
-                if (lane == 0) pv = carry;
-                carry = __shfl_sync(FULL_MASK, raw[u], 31);
-                prv[u] = pv;
+                raw[u] = e < elems ? __ldg(src + e) : 2;
             }
             if (k > 1)
                 while ((gbase + 1) * two_n <= base) ++gbase;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int e = base + 32 * u + lane;
-                int g = gbase;
-                if (k > 1)
-                    while ((g + 1) * two_n <= e) ++g;
-                gg[u] = g;
-                ok[u] = raw[u] >= 2 && raw[u] <= two_n + 1;
-                const bool is_start = in[u] && ((starts[e >> 5] >> (e & 31)) & 1u);
-                const int pc = (is_start || prv[u] < 2 || prv[u] > two_n + 1) ? 0 : (prv[u] >> 1);
-                dd[u] = dist<DM>(a, sh, pc, ok[u] ? (raw[u] >> 1) : 0);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                bool bad = !ok[u];
-                if (in[u] && ok[u]) {
-                    const unsigned bit = 1u << (raw[u] & 31);
-                    bad = (atomicOr(&seen[gg[u] * a.sw + (raw[u] >> 5)], bit) & bit) != 0u;
+                if (e < elems) {
+                    int g = gbase;
+                    if (k > 1)
+                        while ((g + 1) * two_n <= e) ++g;
+                    const bool ok = raw[u] >= 2 && raw[u] <= two_n + 1;
+                    bool bad = !ok;
+                    if (ok) {
+                        const unsigned bit = 1u << (raw[u] & 31);
+                        bad = (atomicOr(&seen[g * a.sw + (raw[u] >> 5)], bit) & bit) != 0u;
+                    }
+                    if (bad) atomicAnd(&valid[g], 0);
+                    A[e] = static_cast<uint16_t>(ok ? raw[u] : 2);
                 }
-                if (in[u] && bad) atomicAnd(&valid[gg[u]], 0);
-            }
-            __syncwarp();
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int e = base + 32 * u + lane;
-                if (in[u]) Ab[e] = (dd[u] << PACK_SHIFT) | (ok[u] ? raw[u] : 2);
             }
         }
     }
     __syncwarp();
 
     // ---- 3. route walk (branch-free; up to two ops per lane per step) ----
-    // Ready times have a single writer (the dropping lane) and are read
-    // with volatile loads: a pickup sees either "unresolved" (and retries
-    // next step) or the final value.  The __syncwarp at the end of each
-    // step makes every write of step t visible in step t+1, so a group
-    // with no progress in a step can never progress again (a cycle).
+    // Each op's travel time is computed here from the previous stop.  Ready
+    // times have a single writer (the dropping lane) and are read with
+    // volatile loads: a pickup sees either "unresolved" (and retries next
+    // step) or the final value.  The __syncwarp at the end of each step makes
+    // every write of step t visible in step t+1, so a group with no progress
+    // in a step can never progress again (a cycle).
     const bool mine = grp < kt && valid[grp] != 0;
     int pos = 0, end = 0, start = 0;
     if (mine) {
         start = pos = soff[grp * (m + 1) + v];
         end = soff[grp * (m + 1) + v + 1];
     }
-    const int* wp = Ab + (grp < k ? grp : 0) * two_n;
+    const uint16_t* wp = A + (grp < k ? grp : 0) * two_n;
     volatile int* rdy = ready + (grp < k ? grp : 0) * (n + 1);
-    int dep = 0, s = 0, smin = 0, smax = 0;
+    int dep = 0, s = 0, smin = 0, smax = 0, loc = 0;
     bool walking = mine && pos < end, cyc = false;
     while (__any_sync(FULL_MASK, walking)) {
         // first op
-        const int w1 = walking ? wp[pos] : 0;
-        const int c1 = (w1 & PACK_MASK) >> 1;
-        const bool p1 = (w1 & 1) != 0;
+        const int o1 = walking ? wp[pos] : 0;
+        const int c1 = o1 >> 1;
+        const bool p1 = (o1 & 1) != 0;
+        const int t1 = walking ? dist<DM>(a, sh, loc, c1) : 0;
         const int r1 = rdy[c1];
         const bool go1 = walking && (!p1 || r1 >= 0);
-        const int a1 = dep + (w1 >> PACK_SHIFT);
-        if (go1 && !p1) rdy[c1] = a1 + sp[c1];
+        const int a1 = dep + t1;
+        if (go1 && !p1) rdy[c1] = a1 - 1 - r1;
         dep = go1 ? max(a1, p1 ? r1 : 0) : dep;
         s += go1 ? (p1 ? 1 : -1) : 0;
         smin = min(smin, s);
         smax = max(smax, s);
         pos += go1 ? 1 : 0;
+        loc = go1 ? c1 : loc;
         // second op, only behind a first one that went
         const bool try2 = go1 && pos < end;
-        const int w2 = try2 ? wp[pos] : 0;
-        const int c2 = (w2 & PACK_MASK) >> 1;
-        const bool p2 = (w2 & 1) != 0;
+        const int o2 = try2 ? wp[pos] : 0;
+        const int c2 = o2 >> 1;
+        const bool p2 = (o2 & 1) != 0;
+        const int t2 = try2 ? dist<DM>(a, sh, c1, c2) : 0;
         const int r2 = rdy[c2];
         const bool go2 = try2 && (!p2 || r2 >= 0);
-        const int a2 = dep + (w2 >> PACK_SHIFT);
-        if (go2 && !p2) rdy[c2] = a2 + sp[c2];
+        const int a2 = dep + t2;
+        if (go2 && !p2) rdy[c2] = a2 - 1 - r2;
         dep = go2 ? max(a2, p2 ? r2 : 0) : dep;
         s += go2 ? (p2 ? 1 : -1) : 0;
         smin = min(smin, s);
         smax = max(smax, s);
         pos += go2 ? 1 : 0;
+        loc = go2 ? c2 : loc;
         const unsigned prog = __ballot_sync(FULL_MASK, go1);
         const bool more = pos < end;
         cyc = cyc || (walking && more && (prog & gmask) == 0u);
@@ -248,15 +202,14 @@ __device__ __forceinline__ bool eval_tile(const EvalArgs& a, const int32_t* sh, 
     }
     if (cyc)                                   // finish the stock prefix of a blocked route
         for (; pos < end; ++pos) {
-            const int o = wp[pos] & PACK_MASK;
+            const int o = wp[pos];
             if (o & 1) { ++s; smax = max(smax, s); } else { --s; smin = min(smin, s); }
         }
-    const int last = (end > start) ? ((wp[end - 1] & PACK_MASK) >> 1) : 0;
 
     // ---- 4. per-candidate reduction ----
     int ret = 0, flags = 0, pool = 0;
     if (mine) {
-        if (!cyc && end > start) ret = dep + dist<DM>(a, sh, last, 0);
+        if (!cyc && end > start) ret = dep + dist<DM>(a, sh, loc, 0);
         if (a.load_full) {
             flags = (smin < -a.Q || smax > 0) ? VRPRPD_VEH_CAP : 0;
             pool = a.Q;
@@ -502,10 +455,10 @@ static bool make_plan(const vrprpd_instance* I, int dm, int warps, int blocks_pe
     a.dist_words = round4(dist_words);
     a.shared_words = a.dist_words + round4(N);
     a.sw = static_cast<int>((two_n + 2 + 31) / 32);
-    a.a_words = round4(a.k * two_n + 4);
+    a.a_words = round4((a.k * two_n + 1) / 2 + 2);
     a.ready_words = round4(static_cast<long long>(a.k) * N);
     a.seen_words = round4(static_cast<long long>(a.k) * a.sw);
-    a.start_words = round4((a.k * two_n + 31) / 32);
+    a.start_words = 0;
     a.off_words = round4(static_cast<long long>(a.k) * (I->m + 1));
     a.valid_words = round4(a.k);
     a.warp_words = a.a_words + a.ready_words + a.seen_words + a.start_words + a.off_words + a.valid_words + 96 + 4;
