@@ -511,7 +511,7 @@ static int choose_plan(const vrprpd_instance* I, long long num, Plan* P) {
                          VRPRPD_DIST_GLOBAL32};
     for (int dm : order) {
         if (!dist_mode_available(I, dm)) continue;
-        for (int warps : {16, 8}) {
+        for (int warps : {32, 24, 16, 8}) {
             if (dm != VRPRPD_DIST_GLOBAL32 && dm != VRPRPD_DIST_GLOBAL16 && warps < 8) continue;
             if (make_plan(I, dm, warps, 0, num, P)) return finalize_plan(I, 0, P);
         }
