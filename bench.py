@@ -30,6 +30,11 @@ import workloads  # noqa: E402
 
 N_CUST, M_VEH, R_POOL, Q_CAP = 1000, 20, 100, 10
 BASE_CANDS = 16384          # generated on the host, tiled on the device
+# DRAM bytes (read + write) per candidate of eval_tiles_kernel, from one ncu
+# capture of 16384 candidates of this workload; a full launch moves the same
+# bytes per candidate (the traffic grows in proportion)
+TRAFFIC_PER_EVAL = 8282
+TRAFFIC_SOURCE = "ncu dram__bytes_read+write of a 16384-candidate launch, scaled by candidates per launch"
 TILE = 32                   # batch = BASE_CANDS * TILE = 524288 candidates
 METRIC = "makespan evals/s and ALNS iters/s at n=1000; batched vs plain GPU, equal makespan"
 UNIT = "evals/s"
@@ -503,7 +508,8 @@ def main():
     peak = pk["hbm_gbs"] if pk else 6800.0
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured" if pk else "fallback",
-                "bytes_per_unit": bytes_per_eval, "units_per_launch": B, "traffic": None,
+                "bytes_per_unit": bytes_per_eval, "units_per_launch": B,
+                "traffic": TRAFFIC_PER_EVAL * B, "traffic_source": TRAFFIC_SOURCE,
                 "kernel": "eval_tiles_kernel", "kernel_ms": kernel_ms}
 
     if rank == 0:
