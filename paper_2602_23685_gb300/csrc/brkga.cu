@@ -43,7 +43,8 @@ struct DecArgs {
     int layout;          // VRPRPD_LAYOUT_VKEYS (2n+m keys) or VRPRPD_LAYOUT_HINTS (4n keys)
     const int32_t* d32;
     const int32_t* p;
-    int smem_dist;       // 1 = distance matrix staged in shared memory
+    int smem_dist;       // 1 = distance matrix staged in shared memory as int32, 2 = as uint16
+    const uint16_t* d16; // the 16-bit copy (max d < 65536) or null
     int32_t* ops;
     int32_t* off;
     int32_t* z;
@@ -77,10 +78,14 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = a.n, m = a.m, two_n = 2 * n, N1 = n + 1;
     int* sd = smem_dec;                                   // staged distances (optional)
-    int* sp = sd + (a.smem_dist ? ((N1 * N1 + 3) & ~3) : 0);
+    const int dist_words = a.smem_dist == 1 ? ((N1 * N1 + 3) & ~3) : a.smem_dist == 2 ? (((N1 * N1 + 1) / 2 + 3) & ~3) : 0;
+    int* sp = sd + dist_words;
+    uint16_t* sd16 = reinterpret_cast<uint16_t*>(sd);
     for (int i = threadIdx.x; i < N1; i += blockDim.x) sp[i] = a.p[i];
-    if (a.smem_dist)
+    if (a.smem_dist == 1)
         for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) sd[i] = a.d32[i];
+    if (a.smem_dist == 2)
+        for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) sd16[i] = a.d16[i];
     int* wbase = sp + ((N1 + 3) & ~3) + warp * static_cast<int>(dec_warp_words(n, a.P));
     unsigned long long* sb = reinterpret_cast<unsigned long long*>(wbase);
     int* tdrop = wbase + 2 * a.P;
@@ -90,7 +95,8 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
     const float* keys = a.keys;
     if (a.keys2 != nullptr && a.ctl->sel == 1) keys = a.keys2;
     auto dist = [&](int i, int j) -> int {
-        return a.smem_dist ? sd[i * N1 + j] : __ldg(a.d32 + i * N1 + j);
+        return a.smem_dist == 2 ? static_cast<int>(sd16[i * N1 + j])
+                                : a.smem_dist == 1 ? sd[i * N1 + j] : __ldg(a.d32 + i * N1 + j);
     };
     for (int ch = blockIdx.x * DEC_WARPS + warp; ch < a.num; ch += gridDim.x * DEC_WARPS) {
         const float* kk = keys + static_cast<long long>(ch) * a.L;
@@ -152,15 +158,13 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
                 }
                 const int arr = ok ? tv + dist(locv, c) : 0;
                 const int tie = hints ? (lane - hint_vehicle(kk[two_n + oi], m) + m) % m : rank;
-                unsigned long long key = ok ? ((static_cast<unsigned long long>(arr) << 10) |
-                                               (static_cast<unsigned>(tie) << 5) | static_cast<unsigned>(lane))
-                                            : ~0ull;
-                for (int off = 16; off > 0; off >>= 1) {
-                    const unsigned long long other = __shfl_xor_sync(FULL_MASK, key, off);
-                    key = other < key ? other : key;
-                }
-                if (key == ~0ull) continue;
-                const int win = static_cast<int>(key & 31u);
+                // SelectVehicle: least arrival, then tie rank, then lane -- two warp reductions
+                const unsigned ua = ok ? static_cast<unsigned>(arr) : 0xffffffffu;
+                const unsigned amin = __reduce_min_sync(FULL_MASK, ua);
+                if (amin == 0xffffffffu) continue;
+                const unsigned sub = (ok && ua == amin) ? ((static_cast<unsigned>(tie) << 5) | static_cast<unsigned>(lane))
+                                                        : 0xffffffffu;
+                const int win = static_cast<int>(__reduce_min_sync(FULL_MASK, sub) & 31u);
                 int dsum = 0;
                 if (lane == win) {
                     if (!pick) {
@@ -475,9 +479,20 @@ static int plan_decode(const vrprpd_instance* I, int num, DecPlan* D) {
     D->P = pow2_at_least(2 * n);
     const size_t warp_words = dec_warp_words(n, D->P);
     const size_t base_words = ((N1 + 3) & ~3) + DEC_WARPS * warp_words;
-    const size_t dist_words = (static_cast<size_t>(N1) * N1 + 3) & ~3;
-    D->smem_dist = (base_words + dist_words) * 4 + 64 <= I->smem_optin && N1 <= 240 ? 1 : 0;
-    D->smem = (base_words + (D->smem_dist ? dist_words : 0)) * 4;
+    // distances staged in shared memory: 16-bit when they fit in that (room for
+    // two blocks per SM at n = 200), else 32-bit for small n, else read from L2
+    const size_t dist_words32 = (static_cast<size_t>(N1) * N1 + 3) & ~3;
+    const size_t dist_words16 = ((static_cast<size_t>(N1) * N1 + 1) / 2 + 3) & ~3;
+    size_t dist_words = 0;
+    D->smem_dist = 0;
+    if (I->has_d16 && (base_words + dist_words16) * 4 + 64 <= I->smem_optin) {
+        D->smem_dist = 2;
+        dist_words = dist_words16;
+    } else if ((base_words + dist_words32) * 4 + 64 <= I->smem_optin && N1 <= 240) {
+        D->smem_dist = 1;
+        dist_words = dist_words32;
+    }
+    D->smem = (base_words + dist_words) * 4;
     VRP_CHECK(D->smem + 64 <= I->smem_optin, VRPRPD_EINVAL, "decode shared memory %zu too large", D->smem);
     { int rc_ = ensure_smem_limit(reinterpret_cast<const void*>(&decode_kernel)); if (rc_) return rc_; }
     int occ = 0;
@@ -501,6 +516,7 @@ static DecArgs dec_args(const vrprpd_instance* I, const DecPlan& D, int num, int
     a.d32 = I->d32;
     a.p = I->p;
     a.smem_dist = D.smem_dist;
+    a.d16 = I->d16;
     return a;
 }
 
