@@ -136,9 +136,10 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
         // ---- multi-pass decode (Algorithm 2), lane v = vehicle v ----
         int tv = 0, locv = 0, net = 0, nmin = 0, nmax = 0, load = 0, cnt = 0;
         int sum_load = 0, done = 0;
+        int len = two_n;                       // sb[0, len): ops not scheduled yet, priority order
         for (int pass = 0; pass < two_n && done < two_n; ++pass) {
             bool progress = false;
-            for (int k = 0; k < two_n; ++k) {
+            for (int k = 0; k < len; ++k) {
                 const int oi = static_cast<int>(sb[k] & 0xffffffffu);
                 const int o = oi + 2, c = o >> 1;
                 const bool pick = (o & 1) != 0;
@@ -190,6 +191,21 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
                 ++done;
             }
             if (!progress) break;
+            // the next pass scans only the ops still unscheduled, order kept (in
+            // place: a chunk is read into registers before any of it is written)
+            int w = 0;
+            for (int base = 0; base < len; base += 32) {
+                const int k = base + lane;
+                const unsigned long long e = k < len ? sb[k] : 0ull;
+                const int o = static_cast<int>(e & 0xffffffffu) + 2;
+                const bool keep = k < len && !((sched[o >> 5] >> (o & 31)) & 1u);
+                const unsigned bal = __ballot_sync(FULL_MASK, keep);
+                __syncwarp();
+                if (keep) sb[w + __popc(bal & ((1u << lane) - 1u))] = e;
+                w += __popc(bal);
+                __syncwarp();
+            }
+            len = w;
         }
         // ---- outputs: routes, makespan, penalty fitness ----
         int ret = (lane < m && cnt > 0) ? tv + dist(locv, 0) : 0;
