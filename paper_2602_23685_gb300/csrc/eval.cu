@@ -591,6 +591,39 @@ extern "C" int vrprpd_evaluate_host(const vrprpd_instance* I_, const vrprpd_batc
     const long long num = b->num;
     if (num == 0) return VRPRPD_OK;
     const size_t ops_b = static_cast<size_t>(num) * 2 * I->n * 4, off_b = static_cast<size_t>(num) * (I->m + 1) * 4;
+    // Pinned host buffers are read by the kernel in place over the host link
+    // (each op is read once, by coalesced loads): no staging copy.  Pageable
+    // buffers are copied to the device first.
+    const void* ops_dev = nullptr;
+    const void* off_dev = nullptr;
+    {
+        cudaPointerAttributes pa{}, pb{};
+        if (cudaPointerGetAttributes(&pa, b->ops) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            cudaPointerGetAttributes(&pb, b->off) == cudaSuccess && pb.type == cudaMemoryTypeHost) {
+            ops_dev = pa.devicePointer;
+            off_dev = pb.devicePointer;
+        }
+        cudaGetLastError();                    // a pageable pointer is not an error here
+    }
+    if (ops_dev && off_dev) {
+        const size_t need = 2 * ((num * 4 + 255) & ~255ull);
+        if (need > I->stage_bytes) {
+            if (I->stage) cudaFree(I->stage);
+            I->stage = nullptr;
+            I->stage_bytes = 0;
+            VRP_CUDA(cudaMalloc(&I->stage, need));
+            I->stage_bytes = need;
+        }
+        int32_t* d_z = reinterpret_cast<int32_t*>(I->stage);
+        uint32_t* d_st = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(d_z) + ((num * 4 + 255) & ~255ull));
+        rc = evaluate_device(I, static_cast<const int32_t*>(ops_dev), static_cast<const int32_t*>(off_dev), num, d_z,
+                             d_st, stream);
+        if (rc) return rc;
+        VRP_CUDA(cudaMemcpyAsync(z_host, d_z, num * 4, cudaMemcpyDeviceToHost, stream));
+        VRP_CUDA(cudaMemcpyAsync(st_host, d_st, num * 4, cudaMemcpyDeviceToHost, stream));
+        VRP_CUDA(cudaStreamSynchronize(stream));
+        return VRPRPD_OK;
+    }
     const size_t need = ((ops_b + 255) & ~255ull) + ((off_b + 255) & ~255ull) + 2 * ((num * 4 + 255) & ~255ull);
     if (need > I->stage_bytes) {
         if (I->stage) cudaFree(I->stage);

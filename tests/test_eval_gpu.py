@@ -119,6 +119,25 @@ def test_host_path_matches(vrp):
     assert np.array_equal(z1.cpu().numpy(), z2) and np.array_equal(s1.cpu().numpy().astype(np.uint32), s2)
 
 
+def test_pinned_host_path_reads_in_place(vrp):
+    # pinned buffers: the kernel reads the ops over the host link, no staging copy
+    import torch
+    for (n, m, seed) in ((100, 4, 2), (37, 5, 4), (1000, 20, 6)):
+        w = workloads.make_instance(n, m, 10, 5, "2x", seed=seed)
+        inst = vrp.Instance.from_workload(w)
+        oi = oracle.OracleInstance.from_workload(w)
+        ops, off = workloads.precedence_candidates(n, m, 700, seed=seed)
+        rops, roff = workloads.random_candidates(n, m, 300, seed=seed)
+        ops, off = np.concatenate([ops, rops]), np.concatenate([off, roff])
+        ops[5, 3] = ops[5, 4]                      # a repeated op
+        off[6, m] = 2 * n - 1                      # offsets that end short
+        tops = torch.from_numpy(ops).pin_memory()
+        toff = torch.from_numpy(off).pin_memory()
+        z, st = vrp.evaluate_host(inst, tops, toff)
+        zo, so = oracle.evaluate_batch(oi, ops, off, threads=8)
+        assert np.array_equal(z, zo) and np.array_equal(st, so)
+
+
 def test_autotune_keeps_results(vrp):
     w = workloads.make_instance(100, 4, 10, 5, "2x", seed=3)
     inst = vrp.Instance.from_workload(w)
