@@ -716,7 +716,7 @@ static int alns_init(alns_t* A, const oracle_inst* I, const int32_t* init_ops, c
      * regret-3, 3 regret-m (repair_mask bits) */
     for (int i = 0; i < ND_OPS; i++) { A->wd[i] = 1.0; A->en_d[i] = (P->destroy_mask >> i) & 1; }
     for (int i = 0; i < 4; i++) { A->wr[i] = 1.0; A->en_r[i] = (P->repair_mask >> i) & 1; }
-    A->T = P->T0 * (double)A->z;                   /* line 3 */
+    A->T = P->T0 * (double)A->z;                   /* initial temperature */
     A->T_init = A->T;
     A->stats = stats;
     A->z_trace = z_trace;
@@ -732,25 +732,25 @@ static void alns_iteration(alns_t* A, int it) {
     const int n = I->n, m = I->m, two_n = 2 * n, ND = ND_OPS, NR = 4;
     oracle_alns_stats* stats = A->stats;
     const uint64_t base = (uint64_t)it << 16, key = A->key;
-    int di = roulette(A->wd, A->en_d, ND, rng_unit(oracle_rng(key, base + 0)));   /* line 8 */
-    int rj = roulette(A->wr, A->en_r, NR, rng_unit(oracle_rng(key, base + 1)));   /* line 9 */
+    int di = roulette(A->wd, A->en_d, ND, rng_unit(oracle_rng(key, base + 0)));   /* destroy operator by roulette */
+    int rj = roulette(A->wr, A->en_r, NR, rng_unit(oracle_rng(key, base + 1)));   /* repair operator by roulette */
     A->ad[di]++;
-    A->ar[rj]++;                                                                 /* line 10 */
+    A->ar[rj]++;                                                                 /* attempt counts */
     int q = A->qmin + rng_below(oracle_rng(key, base + 2), A->qmax - A->qmin + 1);
-    oracle_destroy(I, di, A->S, A->So, q, A->qmin, key, base, A->rem);           /* line 11 */
+    oracle_destroy(I, di, A->S, A->So, q, A->qmin, key, base, A->rem);           /* destroy */
     remove_customers(m, A->S, A->So, A->rem, A->W, A->Wo);
     int cnt = 0;
     for (int c = 1; c <= n; c++)
         if (A->rem[c]) A->list[cnt++] = c;
     int32_t zn = INT32_MAX;
     uint32_t st = OR_MALFORMED;
-    if (repair(I, rj, A->W, A->Wo, A->list, cnt, A->tmp, A->tmpo) == 0)          /* line 11 */
-        oracle_evaluate(I, A->W, A->Wo, 0, &zn, &st, NULL);                      /* line 12 */
+    if (repair(I, rj, A->W, A->Wo, A->list, cnt, A->tmp, A->tmpo) == 0)          /* repair */
+        oracle_evaluate(I, A->W, A->Wo, 0, &zn, &st, NULL);                      /* makespan of the candidate */
     if (st) {
         /* repair found no feasible slot, or a route the destroy left over
          * capacity was never repaired: the candidate is rejected */
         stats->rejected_infeasible++;
-    } else if (zn < A->z) {                                                      /* lines 13-21 */
+    } else if (zn < A->z) {                                                      /* improving: accept, scores */
         memcpy(A->S, A->W, sizeof(int32_t) * two_n);
         memcpy(A->So, A->Wo, sizeof(int32_t) * (m + 1));
         A->z = zn;
@@ -770,7 +770,7 @@ static void alns_iteration(alns_t* A, int it) {
     } else {
         double x = -(double)((int64_t)zn - (int64_t)A->z) / A->T;
         double u = rng_unit(oracle_rng(key, base + 3));
-        if (u < oracle_exp(x)) {                                                 /* lines 22-25 */
+        if (u < oracle_exp(x)) {                                                 /* SA acceptance */
             memcpy(A->S, A->W, sizeof(int32_t) * two_n);
             memcpy(A->So, A->Wo, sizeof(int32_t) * (m + 1));
             A->z = zn;
@@ -779,14 +779,14 @@ static void alns_iteration(alns_t* A, int it) {
             stats->accepted++;
         }
     }
-    A->T = P->alpha * A->T;                                                      /* line 27 */
-    A->stagnation++;                                                             /* line 28 */
-    if (A->stagnation >= P->stagnation && A->T < 0.01 * A->T_init) {             /* lines 29-32 + text gate */
+    A->T = P->alpha * A->T;                                                      /* cooling */
+    A->stagnation++;                                                             /* stagnation count */
+    if (A->stagnation >= P->stagnation && A->T < 0.01 * A->T_init) {             /* reheat, with the text's temperature gate */
         A->T = (P->reheat * P->T0) * (double)A->zb;
         A->stagnation = 0;
         stats->reheats++;
     }
-    if (it % P->tau == 0) {                                                      /* lines 33-38 */
+    if (it % P->tau == 0) {                                                      /* weight update every tau */
         for (int i = 0; i < ND; i++) {
             double ratio = A->ad[i] ? (double)A->sd[i] / (double)A->ad[i] : 0.0;
             double w = (1.0 - P->r) * A->wd[i] + P->r * ratio;
@@ -1051,7 +1051,7 @@ int oracle_decode_l(const oracle_inst* I, const float* keys, int32_t layout, int
     int* rank = malloc(sizeof(int) * (m + 1));
     for (int k = 0; k < two_n; k++) order[k] = k;
     g_keys = keys;
-    qsort(order, (size_t)two_n, sizeof(int), key_cmp);                           /* line 1 */
+    qsort(order, (size_t)two_n, sizeof(int), key_cmp);                           /* ops by priority */
     for (int v = 0; v < m; v++) vorder[v] = v;
     if (layout == OR_LAYOUT_VKEYS) {
         g_keys = keys + two_n;
@@ -1070,13 +1070,13 @@ int oracle_decode_l(const oracle_inst* I, const float* keys, int32_t layout, int
     int64_t* tdrop = calloc((size_t)n + 1, sizeof(int64_t));
     int64_t sum_load = 0;
     int done = 0;
-    for (int pass = 1; pass <= two_n && done < two_n; pass++) {                  /* line 4 */
+    for (int pass = 1; pass <= two_n && done < two_n; pass++) {                  /* passes */
         int progress = 0;
-        for (int k = 0; k < two_n; k++) {                                       /* line 5 */
+        for (int k = 0; k < two_n; k++) {                                       /* ops in priority order */
             int oi = order[k];
             int o = oi + 2, c = o >> 1, pick = o & 1;
             if (sched[o]) continue;
-            if (pick && !sched[2 * c]) continue;                                /* line 11: drop first */
+            if (pick && !sched[2 * c]) continue;                                /* a pickup waits for its drop */
             int best = -1;
             int64_t best_arr = 0;
             for (int v = 0; v < m; v++) {
@@ -1150,7 +1150,7 @@ int oracle_decode_l(const oracle_inst* I, const float* keys, int32_t layout, int
     off[0] = 0;
     for (int v = 0; v < m; v++) {
         if (cnt[v] > 0) {
-            int64_t ret = t[v] + Dd(I, loc[v], 0);                              /* line 17 */
+            int64_t ret = t[v] + Dd(I, loc[v], 0);                              /* return to the depot */
             if (ret > z) z = ret;
         }
         for (int k = 0; k < cnt[v]; k++) ops[w++] = seq[(size_t)v * (two_n + 1) + k];
