@@ -269,8 +269,9 @@ typedef struct {
                                   The paper's replicas poll without meeting; meeting makes runs
                                   reproducible. */
     int32_t init_mode;         /* start solution when init is NULL: 1 (default) the paper's
-                                  vrprpd_initial_solution_paper with 10 refinement rounds, 0 the plain
-                                  sweep of vrprpd_initial_solution */
+                                  vrprpd_initial_solution_paper, 0 the plain sweep of
+                                  vrprpd_initial_solution */
+    int32_t init_refine_rounds;/* refinement rounds of that start (default 10; 0 = the constructor alone) */
 } vrprpd_alns_params;
 
 typedef struct {

@@ -438,12 +438,13 @@ class Server:
         self._h = h
         self._keep = {}
 
-    def submit(self, w, alns_iterations, brkga_pop=0, brkga_generations=0, seed=0, q_min=0, q_max=0):
+    def submit(self, w, alns_iterations, brkga_pop=0, brkga_generations=0, seed=0, q_min=0, q_max=0, **alns_over):
+        """alns_over: further vrprpd_alns_params fields (init_mode, init_refine_rounds, ...)."""
         from ._search_sig import Request
         coords = np.ascontiguousarray(w.coords, dtype=np.int32)
         p = np.ascontiguousarray(w.p, dtype=np.int32)
         req = Request(coords.ctypes.data, p.ctypes.data, w.n, w.m, w.R, w.Q, 0,
-                      alns_params(alns_iterations, q_min, q_max),
+                      alns_params(alns_iterations, q_min, q_max, **alns_over),
                       brkga_params(max(brkga_pop, 2), brkga_generations), C.c_uint64(seed))
         rid = C.c_int64()
         _check(lib().vrprpd_server_submit(self._h, C.byref(req), C.byref(rid)))

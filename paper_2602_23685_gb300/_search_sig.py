@@ -13,7 +13,8 @@ class AlnsParams(C.Structure):
                 ("q_min", C.c_int32), ("q_max", C.c_int32), ("iterations", C.c_int32),
                 ("repair_mask", C.c_int32), ("team_blocks", C.c_int32),
                 ("destroy_mask", C.c_int32), ("ls_pickup_every", C.c_int32), ("ls_relocate_every", C.c_int32),
-                ("replicas", C.c_int32), ("sync_every", C.c_int32), ("init_mode", C.c_int32)]
+                ("replicas", C.c_int32), ("sync_every", C.c_int32), ("init_mode", C.c_int32),
+                ("init_refine_rounds", C.c_int32)]
 
 
 class AlnsStats(C.Structure):

@@ -2947,6 +2947,7 @@ extern "C" void vrprpd_alns_params_default(vrprpd_alns_params* P) {
     P->replicas = 1;
     P->sync_every = 1000;
     P->init_mode = 1;
+    P->init_refine_rounds = 10;
 }
 
 // exact angular order around the depot: half plane, then cross product, then id
@@ -3095,8 +3096,9 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
             std::memcpy(init_off.data(), init->off, (m + 1) * 4);
         } else {
             vrprpd_solution s0{init_ops.data(), init_off.data(), 0, 0};
-            const int rc = P->init_mode == 1 ? vrprpd_initial_solution_paper(I, 10, &s0, stream)
-                                             : vrprpd_initial_solution(I, &s0);
+            const int rc = P->init_mode == 1
+                               ? initial_solution_paper_tb(I, P->init_refine_rounds, &s0, stream, P->team_blocks)
+                               : vrprpd_initial_solution(I, &s0);
             if (rc) return fail_all(rc);
         }
         for (int r = 0; r < R && e == cudaSuccess; ++r) {
@@ -3228,11 +3230,17 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
 
 extern "C" int vrprpd_initial_solution_paper(const vrprpd_instance* I, int32_t refine_rounds, vrprpd_solution* out,
                                              void* stream_) {
+    return initial_solution_paper_tb(I, refine_rounds, out, static_cast<cudaStream_t>(stream_), 0);
+}
+
+namespace vrp {
+
+int initial_solution_paper_tb(const vrprpd_instance* I, int32_t refine_rounds, vrprpd_solution* out,
+                              cudaStream_t stream, int team_blocks) {
     VRP_CHECK(I && out && out->ops && out->off, VRPRPD_EINVAL, "NULL argument");
     VRP_CHECK(refine_rounds >= 0, VRPRPD_EINVAL, "refine_rounds must be >= 0");
     std::string why;
     VRP_CHECK(alns_supported(I, &why), VRPRPD_EINVAL, "%s", why.c_str());
-    const cudaStream_t stream = static_cast<cudaStream_t>(stream_);
     const int n = I->n, m = I->m;
     int32_t* dops = nullptr;
     VRP_CUDA(cudaMallocAsync(reinterpret_cast<void**>(&dops), (2 * n + m + 1) * 4, stream));
@@ -3253,11 +3261,14 @@ extern "C" int vrprpd_initial_solution_paper(const vrprpd_instance* I, int32_t r
     // evaluation and refinement in the ALNS kernel (refine-only mode)
     vrprpd_alns_params P;
     vrprpd_alns_params_default(&P);
+    P.team_blocks = team_blocks;
     std::vector<int32_t> io(out->ops, out->ops + 2 * n), of(out->off, out->off + m + 1);
     vrprpd_solution start{io.data(), of.data(), 0, 0};
     return run_team(I, &start, &P, 0, 2, 0, nullptr, nullptr, nullptr, out, nullptr, nullptr, nullptr, nullptr,
                     stream, refine_rounds);
 }
+
+}  // namespace vrp
 
 extern "C" int vrprpd_alns_run(const vrprpd_instance* I, const vrprpd_solution* init, const vrprpd_alns_params* P,
                                uint64_t seed, vrprpd_solution* best, vrprpd_solution* current,

@@ -18,6 +18,10 @@ void set_error(const char* fmt, ...);
 // so setting it per launch would race between host threads that launch the
 // same kernel with different sizes; the size a launch uses is its own.
 int ensure_smem_limit(const void* kernel);
+// The three-phase start and its refinement by a team of team_blocks CTAs (0:
+// chosen from n); the server passes each request's share (alns.cu).
+int initial_solution_paper_tb(const vrprpd_instance* I, int32_t refine_rounds, vrprpd_solution* out,
+                              cudaStream_t stream, int team_blocks);
 // The paper's three-phase initial solution into device buffers (construct.cu).
 int construct_paper_device(const vrprpd_instance* I, int32_t* ops, int32_t* off, cudaStream_t stream);
 

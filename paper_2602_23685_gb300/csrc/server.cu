@@ -84,7 +84,11 @@ static void serve_one(vrprpd_server* S, vrprpd_server::Req& q, cudaStream_t stre
     cudaEventRecord(e0, stream);
     std::vector<int32_t> ops(2 * r.n), off(r.m + 1), bops(2 * r.n), boff(r.m + 1);
     vrprpd_solution init{ops.data(), off.data(), 0, 0};
-    if (rc == VRPRPD_OK) rc = vrprpd_initial_solution(I, &init);
+    // the start: the paper's three-phase constructor and its refinement on this
+    // request's share of the CTAs, or the plain sweep
+    if (rc == VRPRPD_OK)
+        rc = r.alns.init_mode == 1 ? initial_solution_paper_tb(I, r.alns.init_refine_rounds, &init, stream, q.ctas)
+                                   : vrprpd_initial_solution(I, &init);
     int32_t z_alns = 0;
     if (rc == VRPRPD_OK) {
         vrprpd_alns_params P = r.alns;
