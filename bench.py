@@ -35,6 +35,7 @@ BASE_CANDS = 16384          # generated on the host, tiled on the device
 # capture of 16384 candidates of this workload; a full launch moves the same
 # bytes per candidate (the traffic grows in proportion)
 TRAFFIC_PER_EVAL = 8282
+ALNS_OPS_PER_ENTRY = 8
 TRAFFIC_SOURCE = "ncu dram__bytes_read+write of a 16384-candidate launch, scaled by candidates per launch"
 TILE = 32                   # batch = BASE_CANDS * TILE = 524288 candidates
 METRIC = "makespan evals/s and ALNS iters/s at n=1000; batched vs plain GPU, equal makespan"
@@ -214,6 +215,16 @@ def run_searches(vrp, args):
         "z_init": st.z_init, "z_best": st.z_best, "device_ms": st.device_ms,
         "phase_ms": dict(zip(["begin", "prep", "gaps", "matrix", "select", "end"], list(st.phase_ms))),
         "incremental_steps": st.incremental_steps, "full_steps": st.full_steps}
+    # ALNS moves almost no DRAM bytes: its roofline is integer issue.  Eight
+    # integer ops per matrix entry (the max-plus formula: three adds and three
+    # maxima; the travel add; the compare into the running minimum) against
+    # 152 SMs x 128 int32 lanes x 2070 MHz
+    eps = st.matrix_entries / (st.device_ms / 1000.0)
+    alu_peak = 152 * 128 * 2.07e9 / 1e12
+    out["alns_n1000"]["roofline"] = {
+        "bound": "alu", "achieved": eps * ALNS_OPS_PER_ENTRY / 1e12, "peak": alu_peak, "unit": "Tops/s",
+        "frac": eps * ALNS_OPS_PER_ENTRY / 1e12 / alu_peak, "ops_per_entry": ALNS_OPS_PER_ENTRY,
+        "peak_source": "152 SMs x 128 int32 lanes x 2070 MHz (nominal)"}
     # the paper's multi-instance configuration: 32 replicas share the GPU
     # (Section 4.2.1), each a team of 1/32 of the resident CTAs
     rr = vrp.alns_run(i5, vrp.alns_params(args.alns_iters // 2, replicas=32, sync_every=5), seed=0)
