@@ -392,6 +392,22 @@ def run_profile_alns(args):
                       "matrix_entries": st.matrix_entries, "fallback_entries": st.fallback_entries}))
 
 
+def run_profile_brkga(args):
+    """The BRKGA leg's instance and warm start (n=200 clustered, 50 ALNS
+    iterations), then BRKGA with pop 1024 for 2 generations: two decode
+    launches after the initial one."""
+    import paper_2602_23685_gb300 as vrp
+    w = workloads.make_instance(200, 6, 20, 6, "5x", "clustered", seed=0)
+    inst = vrp.Instance.from_workload(w)
+    a = vrp.alns_run(inst, vrp.alns_params(50), seed=0)
+    warm = (a["best_ops"], a["best_off"])
+    t = time.perf_counter()
+    b = vrp.brkga_run(inst, vrp.brkga_params(1024, 3), seed=0, warm=warm)
+    dt = time.perf_counter() - t
+    print(json.dumps({"profile_case": "BRKGA n=200 m=6, pop 1024, 3 generations", "seconds": dt,
+                      "best_fitness": b["best_fitness"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -405,6 +421,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=24)
     ap.add_argument("--profile-alns", action="store_true",
                     help="small ALNS case for ncu: n=200, 10 iterations per launch, one warm-up launch")
+    ap.add_argument("--profile-brkga", action="store_true",
+                    help="small BRKGA case for ncu: n=200, pop 1024, 3 generations from the ALNS warm start")
     ap.add_argument("--profile-alns-n1000", action="store_true",
                     help="small ALNS case for ncu on the n=1000 workload: 2 iterations per launch")
     ap.add_argument("--profile", action="store_true",
@@ -418,6 +436,8 @@ def main():
         return run_profile(args)
     if args.profile_alns or args.profile_alns_n1000:
         return run_profile_alns(args)
+    if args.profile_brkga:
+        return run_profile_brkga(args)
 
     import torch
     import paper_2602_23685_gb300 as vrp
