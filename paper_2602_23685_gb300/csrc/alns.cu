@@ -2622,7 +2622,7 @@ __device__ __noinline__ void ls_finish(const AlnsTeam& t, const Smem& s, int it)
 // The local search of one iteration (it = 0: outside the iterations), every
 // CTA of the team: up to three passes of each mode in lsm, pickup
 // repositioning first.  False when a team barrier gave up.
-__device__ bool ls_block(const AlnsTeam& t, const Smem& s, int rank, int team_blocks, unsigned& gen, int lsm, int it) {
+__device__ __noinline__ bool ls_block(const AlnsTeam& t, const Smem& s, int rank, int team_blocks, unsigned& gen, int lsm, int it) {
     AlnsCtl* ctl = t.ctl;
     for (int mode = LS_PICKUP; mode <= LS_RELOCATE; ++mode) {
         if (!(lsm & mode)) continue;
