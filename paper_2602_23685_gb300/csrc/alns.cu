@@ -972,7 +972,7 @@ __device__ int walk_skip(const AlnsTeam& t, const Smem& s, int* rdy_, int cx) {
 // Worst removal's gains (Section 4.2.2): every CTA stages the current
 // solution, then one warp per customer c walks it without c; gains[c] =
 // z(cur) - z(cur - c).
-__device__ void phase_gains(const AlnsTeam& t, const Smem& s, int rank, int team_blocks) {
+__device__ __noinline__ void phase_gains(const AlnsTeam& t, const Smem& s, int rank, int team_blocks) {
     stage_ops(t, s, t.cur_ops, t.cur_off);
     const int warp = threadIdx.x >> 5;
     const int team_warps = team_blocks * ALNS_WARPS;
@@ -1864,7 +1864,7 @@ __device__ int roulette(const double* w, const int* en, int k, double u) {
 // weight update of the previous iteration.
 enum { D_RANDOM = 0, D_WORST = 1, D_SHAW = 2, D_CLUSTER = 3, D_ROUTE = 4, D_CRITICAL = 5, ND_OPS = 6 };
 
-__device__ void pick_operators(const AlnsTeam& t, int it) {
+__device__ __noinline__ void pick_operators(const AlnsTeam& t, int it) {
     AlnsCtl* ctl = t.ctl;
     const unsigned long long base = static_cast<unsigned long long>(it) << 16;
     int en_d[ND_OPS];
@@ -1898,7 +1898,7 @@ __device__ void block_sort(unsigned long long* a, int P) {
 // s.flags[c] and leaves the count in ctl->q.  Rankings sort (key << 12 | c),
 // so ties go to the smaller customer id.  Draws: the operator's pick at
 // counter base + 4, sequential draws k at base + 16 + k.
-__device__ void select_structured(const AlnsTeam& t, const Smem& s) {
+__device__ __noinline__ void select_structured(const AlnsTeam& t, const Smem& s) {
     AlnsCtl* ctl = t.ctl;
     const int n = t.n, m = t.m, di = ctl->di, q = ctl->q, qmin = t.q_min;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -2132,7 +2132,7 @@ __device__ void build_W_from_cur(const AlnsTeam& t, const Smem& s) {
     __syncthreads();
 }
 
-__device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
+__device__ __noinline__ void phase_begin(const AlnsTeam& t, const Smem& s) {
     AlnsCtl* ctl = t.ctl;
     const int n = t.n;
     int* perm = s.rdy;                         // [n], shared memory
@@ -2181,7 +2181,7 @@ __device__ void phase_begin(const AlnsTeam& t, const Smem& s) {
 
 // Rank 0: evaluate the repaired W and apply Algorithm 1's acceptance, cooling,
 // reheat and weight update.  With first = true only records the start.
-__device__ void phase_end(const AlnsTeam& t, const Smem& s, bool first) {
+__device__ __noinline__ void phase_end(const AlnsTeam& t, const Smem& s, bool first) {
     AlnsCtl* ctl = t.ctl;
     const int n = t.n, m = t.m;
     stage_W(t, s);
