@@ -326,19 +326,20 @@ def run_multi(vrp, args):
         "speedup_vs_plain": plain_ms / multi_ms, "equal_makespan": equal}}
 
 
-def run_serving(vrp, args, alns_over=None):
+def run_serving(vrp, args, alns_over=None, n_max=400, alns_iters=50, brkga_gens=20):
     """Continuous batching: a Poisson stream of solve requests (n uniform in
-    [50, 400], m = ceil(n/25), R = ceil(n/10), Q = 10, 1R20, mixed coords),
-    each running 50 ALNS iterations then 20 BRKGA generations of 256, admitted
-    by a device-memory budget onto 4 concurrent slots.  Capacity is measured
-    first with all requests queued at once; the stream then arrives at 0.8 of
-    that rate and p50/p99 submit-to-finish latency is reported."""
+    [50, n_max], m = min(20, ceil(n/25)), R = ceil(n/10), Q = 10, 1R20, mixed coords),
+    each running alns_iters ALNS iterations then brkga_gens BRKGA generations
+    of 256, admitted by a device-memory budget onto 4 concurrent slots.
+    Capacity is measured first with all requests queued at once; the stream
+    then arrives at 0.8 of that rate and p50/p99 submit-to-finish latency is
+    reported."""
     import numpy as np
     rng = np.random.default_rng(7)
     reqs = []
     for i in range(args.serve_requests):
-        n = int(rng.integers(50, 401))
-        reqs.append(workloads.make_instance(n, -(-n // 25), -(-n // 10), 10, "1R20", "mixed", seed=100 + i))
+        n = int(rng.integers(50, n_max + 1))
+        reqs.append(workloads.make_instance(n, min(20, -(-n // 25)), -(-n // 10), 10, "1R20", "mixed", seed=100 + i))
     budget = 16 << 30
 
     def run(rate):
@@ -350,8 +351,8 @@ def run_serving(vrp, args, alns_over=None):
                 time.sleep(float(rng.exponential(1.0 / rate)))
             # the paper's three-phase start, constructor alone (its refinement
             # rounds cost more than 50 iterations at this scale)
-            ids.append(srv.submit(w, alns_iterations=50, brkga_pop=256, brkga_generations=20, seed=i,
-                                  **(alns_over or {"init_mode": 1, "init_refine_rounds": 0})))
+            ids.append(srv.submit(w, alns_iterations=alns_iters, brkga_pop=256, brkga_generations=brkga_gens,
+                                  seed=i, **(alns_over or {"init_mode": 1, "init_refine_rounds": 0})))
         res = [srv.wait(r) for r in ids]
         wall = time.perf_counter() - t0
         st = srv.stats()
@@ -366,8 +367,9 @@ def run_serving(vrp, args, alns_over=None):
         "value": len(reqs) / wall, "unit": "requests/s", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
         "capacity_requests_per_s": capacity, "arrival_rate": 0.8 * capacity, "requests": len(reqs),
         "peak_active": st["peak_active"], "peak_bytes": st["peak_bytes"], "all_ok": ok,
-        "config": "Poisson arrivals at 0.8x measured capacity; n ~ U[50,400], m=ceil(n/25), R=ceil(n/10), "
-                  "Q=10, 1R20; three-phase start (constructor alone), 50 ALNS iterations + 20 BRKGA generations of 256 per request; 4 slots, 16 GiB"}}
+        "config": f"Poisson arrivals at 0.8x measured capacity; n ~ U[50,{n_max}], m=min(20,ceil(n/25)), "
+                  f"R=ceil(n/10), Q=10, 1R20; three-phase start (constructor alone), {alns_iters} ALNS iterations "
+                  f"+ {brkga_gens} BRKGA generations of 256 per request; 4 slots, 16 GiB"}}
 
 
 def run_profile_alns(args):
