@@ -1741,31 +1741,49 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
             const unsigned long long other = __shfl_xor_sync(FULL_MASK, bv, o);
             bv = other < bv ? other : bv;
         }
-        long long c1 = REGRET_INF, c2 = REGRET_INF;
-        for (int v = 0; v < m; ++v) {
-            const unsigned long long bvv = __shfl_sync(FULL_MASK, rk, v);
-            if (bvv == KEY_NONE) continue;
-            const long long cv = static_cast<long long>(static_cast<int>(static_cast<unsigned>(bvv >> 32) ^ 0x80000000u));
-            if (cv < c1) { c2 = c1; c1 = cv; } else if (cv < c2) { c2 = cv; }
-        }
         // regret-k over the per-vehicle options: the sum over the k best of
         // (c_i - c_1), options past the m there are counting as REGRET_INF;
-        // k = 2, 3 or m for repair operators 1, 2, 3
-        const int kreg = ctl->rj == 1 ? 2 : (ctl->rj == 2 ? 3 : m);
-        const long long cvl = (lane < m && rk != KEY_NONE)
-                                  ? static_cast<long long>(static_cast<int>(static_cast<unsigned>(rk >> 32) ^ 0x80000000u))
-                                  : REGRET_INF;
-        int rnk = 0;
-        for (int u = 0; u < m; ++u) {
-            const long long cu = __shfl_sync(FULL_MASK, cvl, u);
-            if (cu < cvl || (cu == cvl && u < lane)) ++rnk;
+        // k = 2, 3 or m for repair operators 1, 2, 3 (greedy needs none of it)
+        const int rj = ctl->rj;
+        long long reg = 0;
+        if (rj != 0) {
+            const long long cvl = (lane < m && rk != KEY_NONE)
+                                      ? static_cast<long long>(static_cast<int>(static_cast<unsigned>(rk >> 32) ^ 0x80000000u))
+                                      : REGRET_INF;
+            // the least option (with its lane) and the least of the others, by
+            // two warp min-reductions of (option + 2^31) << 6 | lane
+            const unsigned long long key1 = (static_cast<unsigned long long>(cvl + (1ll << 31)) << 6) |
+                                            static_cast<unsigned long long>(lane);
+            unsigned long long k1 = key1;
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(FULL_MASK, k1, o);
+                k1 = other < k1 ? other : k1;
+            }
+            unsigned long long k2 = (static_cast<int>(k1 & 63u) == lane) ? ~0ull : key1;
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long other = __shfl_xor_sync(FULL_MASK, k2, o);
+                k2 = other < k2 ? other : k2;
+            }
+            const long long c1 = static_cast<long long>(k1 >> 6) - (1ll << 31);
+            const long long c2 = static_cast<long long>(k2 >> 6) - (1ll << 31);
+            if (rj == 1) {
+                reg = c2 - c1;
+            } else {
+                const int kreg = rj == 2 ? 3 : m;
+                int rnk = 0;
+                for (int u = 0; u < m; ++u) {
+                    const long long cu = __shfl_sync(FULL_MASK, cvl, u);
+                    if (cu < cvl || (cu == cvl && u < lane)) ++rnk;
+                }
+                long long term = (lane < m && rnk < kreg) ? cvl - c1 : 0;
+                for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(FULL_MASK, term, o);
+                if (kreg > m) term += static_cast<long long>(kreg - m) * (REGRET_INF - c1);
+                reg = term;
+            }
         }
-        long long term = (lane < m && rnk < kreg) ? cvl - c1 : 0;
-        for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(FULL_MASK, term, o);
-        if (kreg > m) term += static_cast<long long>(kreg - m) * (REGRET_INF - c1);
         if (lane == 0) {
             bestv[ti] = bv;
-            regret[ti] = ctl->rj == 1 ? c2 - c1 : term;
+            regret[ti] = reg;
         }
     }
     __syncthreads();
