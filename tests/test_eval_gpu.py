@@ -110,6 +110,27 @@ def test_malformed_candidates(vrp):
     assert all(so[i] == oracle.MALFORMED for i in range(6))
 
 
+def test_duplicate_and_missing_ops(vrp):
+    # one op overwritten by a copy of another: a repeated code and a missing
+    # one, drops or pickups, on one route or across routes, in acyclic and
+    # cyclic candidates; plus two routes that start with the same drop (the
+    # duplicate reaches both lanes in the same step)
+    n, m = 30, 5
+    w = workloads.make_instance(n, m, 12, 4, "2x", seed=9)
+    rng = np.random.default_rng(9)
+    po, pf = workloads.precedence_candidates(n, m, 1500, seed=9)
+    ro, rf = workloads.random_candidates(n, m, 1500, seed=10)
+    ops, off = np.concatenate([po, ro]).copy(), np.concatenate([pf, rf])
+    for k in range(len(ops)):
+        i, j = rng.choice(2 * n, size=2, replace=False)
+        ops[k, i] = ops[k, j]
+    for k in range(0, 200):
+        if off[k, 1] > off[k, 0] and off[k, 2] > off[k, 1]:
+            ops[k, off[k, 1]] = ops[k, off[k, 0]]
+    inst, zo, so = check_against_oracle(vrp, w, ops, off)
+    assert (so == oracle.MALFORMED).all()
+
+
 def test_host_path_matches(vrp):
     w = workloads.make_instance(100, 4, 10, 5, "2x", seed=1)
     inst = vrp.Instance.from_workload(w)
