@@ -77,9 +77,9 @@ __device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, unsigne
 }
 
 // ---------------------------------------------------------------------------
-// EUC_2D: nint(sqrt(dx^2+dy^2)) exactly.  r0 approximates floor(sqrt(s));
-// one integer correction each way makes it exact, then round half up
-// (sqrt(s) is never an exact half-integer for integer s).
+// EUC_2D: nint(sqrt(dx^2+dy^2)) exactly.  sqrt(s) is never an exact
+// half-integer for integer s, and the nearest integer r >= 1 to sqrt(s) is the
+// one with (r - 1/2)^2 < s < (r + 1/2)^2, i.e. -r < s - r^2 <= r.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float sqrt_approx(float x) {
     float y;
@@ -87,14 +87,16 @@ __device__ __forceinline__ float sqrt_approx(float x) {
     return y;
 }
 
-// Small coordinates: s < 2^24 (checked on the host), fp32 path.
+// Small coordinates: s < 2^24 (checked on the host), fp32 path.  The nearest
+// integer to the approximate root is off by at most one; one step either way
+// by the test above makes it exact (s = 0 steps to -1 and is clamped).
 __device__ __forceinline__ int euc2d_small(int ax, int ay, int bx, int by) {
-    int dx = ax - bx, dy = ay - by;
-    int s = dx * dx + dy * dy;
-    int r = static_cast<int>(sqrt_approx(static_cast<float>(s)));
-    if (r * r > s) --r;
-    if ((r + 1) * (r + 1) <= s) ++r;
-    return r + ((s - r * r) > r ? 1 : 0);
+    const int dx = ax - bx, dy = ay - by;
+    const int s = dx * dx + dy * dy;
+    int r = __float2int_rn(sqrt_approx(static_cast<float>(s)));
+    const int e = s - r * r;
+    r += (e > r) ? 1 : ((e <= -r) ? -1 : 0);
+    return max(r, 0);
 }
 
 // General coordinates (|coord| <= 2^20): int64 square, fp64 estimate.

@@ -131,6 +131,62 @@ def test_duplicate_and_missing_ops(vrp):
     assert (so == oracle.MALFORMED).all()
 
 
+def _boundary_chain(n, seed):
+    """Depot at the centre of a 2895-wide box and n customers on a chain whose
+    consecutive legs have squared lengths on EUC_2D's rounding boundaries:
+    s = r^2 - r or r^2 + r (just below r -+ 1/2) and s = r^2 - r + 1 or
+    r^2 + r + 1 (just above), for 2 <= r <= 2040.  Every step moves toward the
+    centre, so the box (squared diagonal < 2^24) is never left."""
+    import math
+    rng = np.random.default_rng(seed)
+    pts = [(1448, 1448)]
+    while len(pts) <= n:
+        r = int(rng.integers(2, 2041))
+        s = r * r + int(rng.choice([-r, -r + 1, r, r + 1]))
+        reps = [(dx, math.isqrt(s - dx * dx)) for dx in range(0, math.isqrt(s) + 1)
+                if math.isqrt(s - dx * dx) ** 2 == s - dx * dx]
+        reps = [(dx, dy) for dx, dy in reps if dx <= 1447 and dy <= 1447]
+        if not reps:
+            continue
+        dx, dy = reps[int(rng.integers(0, len(reps)))]
+        x, y = pts[-1]
+        pts.append((x + (dx if x <= 1448 else -dx), y + (dy if y <= 1448 else -dy)))
+    coords = np.array(pts, dtype=np.int32)
+    leg = np.diff(coords.astype(np.int64), axis=0)
+    s = (leg ** 2).sum(axis=1)
+    r = np.array([math.isqrt(int(v)) for v in s])
+    gap = s - (r * r + r)
+    assert ((gap == 0) | (gap == 1)).all() and coords.min() >= 0 and coords.max() <= 2895
+    return coords
+
+
+def test_rounding_boundary_legs(vrp):
+    # makespans over chains of legs whose exact EUC_2D rounding is closest to
+    # a tie.  m = 32: one long route takes 1469 consecutive chain legs (it
+    # sets the makespan, so every one of its legs is in the result), the other
+    # 31 routes one customer each; its rotations move the cut.  m = 20: the
+    # chain cut into random routes.
+    n, m = 1500, 32
+    coords = _boundary_chain(n, seed=5)
+    p = np.random.default_rng(6).integers(0, 200, size=n).astype(np.int32)
+    chain = np.arange(1, n + 1)
+    ops1 = []
+    for k in range(0, n, 47):
+        order = np.roll(chain, -k)
+        ops1.append(np.stack([2 * order, 2 * order + 1], axis=1).reshape(-1))
+    ops1 = np.array(ops1, dtype=np.int32)
+    long = 2 * (n - (m - 1))
+    off1 = np.tile(np.concatenate([[0], np.arange(long, 2 * n + 1, 2)]).astype(np.int32), (len(ops1), 1))
+    assert off1.shape[1] == m + 1
+    inst, zo, so = check_against_oracle(vrp, workloads.Instance(coords, p, m, m, 2), ops1, off1)
+    assert (so == 0).all() and (zo > 1000 * n // 2).all()
+    m = 20
+    cuts = np.sort(np.random.default_rng(7).integers(0, n + 1, size=(64, m - 1)), axis=1)
+    off2 = np.concatenate([np.zeros((64, 1), np.int64), 2 * cuts, np.full((64, 1), 2 * n)], axis=1)
+    ops2 = np.tile(ops1[0], (64, 1))
+    check_against_oracle(vrp, workloads.Instance(coords, p, m, m, 2), ops2, off2.astype(np.int32))
+
+
 def test_host_path_matches(vrp):
     w = workloads.make_instance(100, 4, 10, 5, "2x", seed=1)
     inst = vrp.Instance.from_workload(w)
