@@ -529,6 +529,55 @@ def main():
     e2e_value = whole_job_rate(B * e2e_steps, world, e2e_s)
     assert torch.equal(z_h, z.cpu())
 
+    # the host link's own rate: a pinned host -> device copy of the step's
+    # candidate bytes, the ceiling of any end-to-end path that moves them
+    scratch = torch.empty_like(ops)
+    link_ms = []
+    for _ in range(3):
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(stream)
+        scratch.copy_(ops_pin, non_blocking=True)
+        l1.record(stream)
+        torch.cuda.synchronize()
+        link_ms.append(l0.elapsed_time(l1))
+    del scratch
+    link_gbs = ops.numel() * 4 / (min(link_ms[1:]) / 1000.0) / 1e9
+    e2e_bytes = int(ops.numel() * 4 + off.numel() * 4)
+    e2e_gbs = e2e_bytes * e2e_steps / e2e_s / 1e9          # per GPU, like its link
+
+    # the 16-bit form: the same candidates as 16-bit codes and offsets (half
+    # the bytes), on the device and end to end from pinned host memory
+    ops16, off16 = ops.to(torch.int16), off.to(torch.int16)
+    z16, st16 = torch.empty_like(z), torch.empty_like(st)
+    vrp.evaluate(inst, ops16, off16, z16, st16)
+    vrp.sync(inst)
+    assert torch.equal(z16, z) and torch.equal(st16, st)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for _ in range(e2e_steps):
+        vrp.evaluate(inst, ops16, off16, z16, st16)
+    s1.record(stream)
+    vrp.sync(inst)
+    w16_value = whole_job_rate(B * e2e_steps, world, max_over_ranks(dist, s0.elapsed_time(s1), "cuda") / 1000.0)
+    ops16_pin, off16_pin = ops16.cpu().pin_memory(), off16.cpu().pin_memory()
+    del ops16, off16
+    vrp.evaluate_host(inst, ops16_pin, off16_pin, z_h, st_h)
+    barrier()
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        vrp.evaluate_host(inst, ops16_pin, off16_pin, z_h, st_h)
+    barrier()
+    e2e16_s = max_over_ranks(dist, time.perf_counter() - t, "cuda")
+    assert torch.equal(z_h, z.cpu())
+    e2e16_bytes = int(ops16_pin.numel() * 2 + off16_pin.numel() * 2)
+    ops16_leg = {"ops16": {
+        "value": w16_value, "unit": UNIT,
+        "config": "the same batch as 16-bit op codes and offsets (vrprpd_evaluate16), results equal",
+        "e2e": {"value": whole_job_rate(B * e2e_steps, world, e2e16_s), "unit": UNIT,
+                "h2d_bytes_per_step": e2e16_bytes, "d2h_bytes_per_step": int(B * 8),
+                "link_frac": e2e16_bytes * e2e_steps / e2e16_s / 1e9 / link_gbs}}}
+    del ops16_pin, off16_pin
+
     # Section 5.2 coordination counts over the first quarter of the batch:
     # same candidate bytes read, a lock-step walk per candidate like the
     # evaluator's; every tiled copy must give the first copy's counts
@@ -573,14 +622,16 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "batch": B, "l2": "inputs larger than L2 (no flush)",
                        "eval_config": tuned},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(ops.numel() * 4 + off.numel() * 4),
-                    "d2h_bytes_per_step": int(B * 8)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_bytes,
+                    "d2h_bytes_per_step": int(B * 8), "link_gbs": link_gbs, "link_frac": e2e_gbs / link_gbs,
+                    "link_source": "pinned host -> device copy of the step's ops, CUDA events"},
             "gpu_launches": args.steps,
             "roofline": roofline,
             "clocks": clk.summary(),
             "plain_gpu": {"value": plain_value, "unit": UNIT, "equal_makespan": equal,
                           "speedup_batched_vs_plain": value / world / plain_value},
         }
+        line.update(ops16_leg)
         line.update(searches)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, ops_h, off_h)

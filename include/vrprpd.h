@@ -98,8 +98,10 @@ typedef struct {
  *   makespan  num int32: the makespan, or INT32_MAX for CYCLE/MALFORMED.
  *   status    num uint32: VRPRPD_* bits.
  * Asynchronous on stream.  Device pointers.  One persistent launch over the
- * whole batch: each warp stages a tile of candidates in shared memory with a
- * TMA bulk copy and walks all their routes in lock step.
+ * whole batch: each warp reads a tile of candidates with coalesced loads into
+ * shared memory (as 16-bit codes) and walks all their routes in lock step.
+ * Needs m <= 32, 2n+1 < 4096 and max d < 2^19 (VRPRPD_EINVAL otherwise; the
+ * plain form below has no such limit).
  */
 int vrprpd_evaluate(const vrprpd_instance* inst, const vrprpd_batch* batch, int32_t* makespan,
                     uint32_t* status, void* stream);
@@ -110,6 +112,29 @@ int vrprpd_evaluate(const vrprpd_instance* inst, const vrprpd_batch* batch, int3
  * to the device first.  Results are copied back. */
 int vrprpd_evaluate_host(const vrprpd_instance* inst, const vrprpd_batch* host_batch,
                          int32_t* makespan_host, uint32_t* status_host, void* stream);
+
+/* A batch with 16-bit op codes and offsets: the same values as vrprpd_batch
+ * in half the bytes (every op code of an instance the batched form accepts
+ * is below 4096, so nothing is lost).
+ *   ops  num x 2n uint16, candidate i at ops + i*2n (base 4-byte aligned).
+ *   off  num x (m+1) uint16, candidate i at off + i*(m+1) (2-byte aligned). */
+typedef struct {
+    int32_t num;
+    const uint16_t* ops;
+    const uint16_t* off;
+} vrprpd_batch16;
+
+/* vrprpd_evaluate on a 16-bit batch: same results (a code or offset out of
+ * range is MALFORMED as before), same arguments and stream semantics, device
+ * pointers.  Halves the candidate bytes each evaluation reads. */
+int vrprpd_evaluate16(const vrprpd_instance* inst, const vrprpd_batch16* batch, int32_t* makespan,
+                      uint32_t* status, void* stream);
+
+/* vrprpd_evaluate_host on a 16-bit batch (host pointers; pinned buffers are
+ * read in place, pageable ones copied first; returns when done).  Halves the
+ * bytes that cross the host link. */
+int vrprpd_evaluate16_host(const vrprpd_instance* inst, const vrprpd_batch16* host_batch,
+                           int32_t* makespan_host, uint32_t* status_host, void* stream);
 
 /* The plain GPU form kept as the comparison baseline: one thread per
  * candidate, distances read from global memory, no shared-memory staging,

@@ -56,7 +56,9 @@ def lib():
             L.vrprpd_instance_destroy.argtypes = [vp]
             L.vrprpd_instance_destroy.restype = None
             L.vrprpd_instance_get_dist.argtypes = [vp, vp]
-            for name in ("vrprpd_evaluate", "vrprpd_evaluate_host", "vrprpd_evaluate_plain", "vrprpd_coordination"):
+            # vrprpd_batch16 has vrprpd_batch's layout (int32, two pointers)
+            for name in ("vrprpd_evaluate", "vrprpd_evaluate_host", "vrprpd_evaluate_plain", "vrprpd_coordination",
+                         "vrprpd_evaluate16", "vrprpd_evaluate16_host"):
                 getattr(L, name).argtypes = [vp, C.POINTER(Batch), vp, vp, vp]
             L.vrprpd_sync.argtypes = [vp, vp]
             L.vrprpd_eval_set_config.argtypes = [vp, C.POINTER(EvalConfig)]
@@ -92,10 +94,19 @@ def _stream_ptr(stream):
     return C.c_void_p(s.cuda_stream)
 
 
-def _dev_i32(t, name, shape=None):
+def _is16(dtype):
+    """True for a 16-bit integer dtype (torch or numpy)."""
+    import torch
+    if isinstance(dtype, torch.dtype):
+        return dtype == torch.int16 or dtype == getattr(torch, "uint16", torch.int16)
+    return np.dtype(dtype) in (np.dtype(np.int16), np.dtype(np.uint16))
+
+
+def _dev_i32(t, name, shape=None, wide16=False):
     torch = _torch()
-    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or t.dtype != torch.int32:
-        raise TypeError(f"{name} must be a CUDA int32 tensor")
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda" or \
+            not (t.dtype == torch.int32 or (wide16 and _is16(t.dtype))):
+        raise TypeError(f"{name} must be a CUDA int32 tensor" + (" (or int16 for ops and off both)" if wide16 else ""))
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
     if shape is not None and tuple(t.shape) != tuple(shape):
@@ -160,22 +171,26 @@ class Instance:
             pass
 
 
-def _batch(inst, ops, off):
+def _batch(inst, ops, off, wide16=False):
     B = ops.shape[0]
-    _dev_i32(ops, "ops", (B, 2 * inst.n))
-    _dev_i32(off, "off", (B, inst.m + 1))
+    _dev_i32(ops, "ops", (B, 2 * inst.n), wide16)
+    _dev_i32(off, "off", (B, inst.m + 1), wide16)
+    if _is16(ops.dtype) != _is16(off.dtype):
+        raise TypeError("ops and off must both be 32-bit or both 16-bit")
     return Batch(B, ops.data_ptr(), off.data_ptr())
 
 
 def evaluate(inst, ops, off, z=None, st=None, stream=None):
-    """Batched evaluation on device tensors; returns (makespan int32, status int32 view)."""
+    """Batched evaluation on device tensors; returns (makespan int32, status int32 view).
+    ops and off are int32, or both int16 (the 16-bit form: the same codes in half the bytes)."""
     torch = _torch()
-    b = _batch(inst, ops, off)
+    b = _batch(inst, ops, off, wide16=True)
     if z is None:
         z = torch.empty(b.num, dtype=torch.int32, device=ops.device)
     if st is None:
         st = torch.empty(b.num, dtype=torch.int32, device=ops.device)
-    _check(lib().vrprpd_evaluate(inst.handle, C.byref(b), z.data_ptr(), st.data_ptr(), _stream_ptr(stream)))
+    fn = lib().vrprpd_evaluate16 if _is16(ops.dtype) else lib().vrprpd_evaluate
+    _check(fn(inst.handle, C.byref(b), z.data_ptr(), st.data_ptr(), _stream_ptr(stream)))
     return z, st
 
 
@@ -205,15 +220,24 @@ def coordination(inst, ops, off, stream=None):
 
 
 def evaluate_host(inst, ops, off, z=None, st=None, stream=None):
-    """Evaluation from host memory (numpy arrays or pinned CPU tensors): copies in,
-    evaluates, copies out, returns when done."""
-    def host_ptr(a, name):
+    """Evaluation from host memory (numpy arrays or CPU tensors; pinned tensors are
+    read in place, others copied in), returning when done.  ops and off are int32,
+    or both 16-bit (the same codes in half the bytes across the host link)."""
+    wide = _is16(ops.dtype)
+
+    def host_ptr(a, name, operand=True):
         if hasattr(a, "data_ptr"):
             if a.device.type != "cpu" or not a.is_contiguous():
                 raise TypeError(f"{name} must be a contiguous CPU tensor")
+            if operand and _is16(a.dtype) != wide:
+                raise TypeError("ops and off must both be 32-bit or both 16-bit")
+            if operand and not wide and a.dtype != _torch().int32:
+                raise TypeError(f"{name} must be int32 or 16-bit")
             return a.data_ptr()
-        if not (isinstance(a, np.ndarray) and a.flags.c_contiguous and a.dtype == np.int32):
-            raise TypeError(f"{name} must be a contiguous int32 array")
+        ok = isinstance(a, np.ndarray) and a.flags.c_contiguous and \
+            (not operand or (a.dtype in (np.int16, np.uint16)) == wide and (wide or a.dtype == np.int32))
+        if not ok:
+            raise TypeError(f"{name} must be a contiguous array: int32, or 16-bit for ops and off both")
         return a.ctypes.data
     B = ops.shape[0]
     if tuple(ops.shape) != (B, 2 * inst.n) or tuple(off.shape) != (B, inst.m + 1):
@@ -223,10 +247,9 @@ def evaluate_host(inst, ops, off, z=None, st=None, stream=None):
     if st is None:
         st = np.empty(B, np.uint32)
     b = Batch(B, host_ptr(ops, "ops"), host_ptr(off, "off"))
-    _check(lib().vrprpd_evaluate_host(inst.handle, C.byref(b), host_ptr(z, "z") if hasattr(z, "data_ptr")
-                                      else z.ctypes.data,
-                                      st.data_ptr() if hasattr(st, "data_ptr") else st.ctypes.data,
-                                      _stream_ptr(stream)))
+    fn = lib().vrprpd_evaluate16_host if wide else lib().vrprpd_evaluate_host
+    _check(fn(inst.handle, C.byref(b), host_ptr(z, "z", False) if hasattr(z, "data_ptr") else z.ctypes.data,
+              st.data_ptr() if hasattr(st, "data_ptr") else st.ctypes.data, _stream_ptr(stream)))
     return z, st
 
 

@@ -8,8 +8,9 @@
 //   1. offsets are checked and every customer's ready slot is set to
 //      -(p_c + 1): negative means "not dropped yet", and the drop recovers p_c
 //      from the value it reads anyway;
-//   2. the ops are read with coalesced loads, four per lane in flight, checked
-//      (code range, duplicates by a shared bitmap) and kept as 16-bit codes:
+//   2. the ops are read with coalesced loads, four per lane in flight (int32
+//      codes, or pairs of 16-bit codes in the 16-bit form), checked (code
+//      range, duplicates by a shared bitmap) and kept as 16-bit codes:
 //      half the footprint of the 32-bit stream, so 24 warps fit per SM where
 //      a staged 32-bit copy left room for 16;
 //   3. the route walk: each lane advances its route up to two ops per step,
@@ -34,6 +35,8 @@ namespace vrp {
 
 struct EvalArgs {
     const int32_t* ops;
+    const uint16_t* ops16;   // the 16-bit form (ops/off unused then)
+    const uint16_t* off16;
     const int32_t* off;
     int32_t* z;
     uint32_t* st;
@@ -74,7 +77,7 @@ __device__ __forceinline__ int dist(const EvalArgs& a, const int32_t* sh, int i,
 // One tile of k candidates of one instance, processed by one warp.
 // W is the warp's shared-memory region (layout from a), sh/sp the block's
 // staged distances or coordinates and p.
-template <int DM>
+template <int DM, bool W16>
 __device__ __forceinline__ bool eval_tile(const EvalArgs& a, const int32_t* sh, const int32_t* sp, int32_t* W,
                                           uint64_t* bar, unsigned& phase, long long t) {
     (void)bar;
@@ -92,10 +95,10 @@ __device__ __forceinline__ bool eval_tile(const EvalArgs& a, const int32_t* sh, 
     const long long first = t * k;
     const int kt = static_cast<int>(min(static_cast<long long>(k), a.num - first));
     const int elems = kt * two_n;
-    const int32_t* src = a.ops + first * two_n;
 
     // ---- 1. offsets, flags, duplicate bitmap, unresolved ready times ----
-    for (int i = lane; i < kt * (m + 1); i += 32) soff[i] = __ldg(a.off + first * (m + 1) + i);
+    for (int i = lane; i < kt * (m + 1); i += 32)
+        soff[i] = W16 ? static_cast<int32_t>(__ldg(a.off16 + first * (m + 1) + i)) : __ldg(a.off + first * (m + 1) + i);
     for (int i = lane; i < kt; i += 32) valid[i] = 1;
     for (int i = lane; i < kt * a.sw; i += 32) seen[i] = 0u;
     // unresolved ready time of c: -(p_c + 1) (negative); the drop recovers p_c from it
@@ -113,7 +116,47 @@ __device__ __forceinline__ bool eval_tile(const EvalArgs& a, const int32_t* sh, 
 
     // ---- 2. ops: coalesced loads, four in flight per lane; code range and
     // duplicates; kept as 16-bit codes (the walk computes the travel times) ----
-    {
+    if constexpr (W16) {
+        // code pairs as 32-bit words: 2n is even, so a pair never straddles
+        // two candidates (n pairs each), and candidate i starts 4n i bytes in
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(a.ops16 + first * two_n);
+        uint32_t* A2 = reinterpret_cast<uint32_t*>(A);
+        const int pairs = elems >> 1;
+        int gbase = 0;
+        for (int base = 0; base < pairs; base += 128) {
+            uint32_t raw[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = base + 32 * u + lane;
+                raw[u] = e < pairs ? __ldg(src + e) : 0x00020002u;
+            }
+            if (k > 1)
+                while ((gbase + 1) * n <= base) ++gbase;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = base + 32 * u + lane;
+                if (e < pairs) {
+                    int g = gbase;
+                    if (k > 1)
+                        while ((g + 1) * n <= e) ++g;
+                    const int lo = static_cast<int>(raw[u] & 0xffffu), hi = static_cast<int>(raw[u] >> 16);
+                    const bool okl = lo >= 2 && lo <= two_n + 1, okh = hi >= 2 && hi <= two_n + 1;
+                    bool bad = !(okl && okh);
+                    if (okl) {
+                        const unsigned bit = 1u << (lo & 31);
+                        bad |= (atomicOr(&seen[g * a.sw + (lo >> 5)], bit) & bit) != 0u;
+                    }
+                    if (okh) {
+                        const unsigned bit = 1u << (hi & 31);
+                        bad |= (atomicOr(&seen[g * a.sw + (hi >> 5)], bit) & bit) != 0u;
+                    }
+                    if (bad) atomicAnd(&valid[g], 0);
+                    A2[e] = static_cast<uint32_t>(okl ? lo : 2) | (static_cast<uint32_t>(okh ? hi : 2) << 16);
+                }
+            }
+        }
+    } else {
+        const int32_t* src = a.ops + first * two_n;
         int gbase = 0;
         for (int base = 0; base < elems; base += 128) {
             int raw[4];
@@ -241,7 +284,7 @@ __device__ __forceinline__ bool eval_tile(const EvalArgs& a, const int32_t* sh, 
     return true;
 }
 
-template <int DM>
+template <int DM, bool W16>
 __global__ void __launch_bounds__(1024) eval_tiles_kernel(EvalArgs a) {
     extern __shared__ __align__(16) int32_t smem[];
     __shared__ __align__(8) uint64_t block_bar;
@@ -278,7 +321,7 @@ __global__ void __launch_bounds__(1024) eval_tiles_kernel(EvalArgs a) {
     const long long nw = static_cast<long long>(gridDim.x) * nwarps;
     unsigned phase = 0;
     for (long long t = gw; t < ntiles; t += nw)
-        if (!eval_tile<DM>(a, sh, sp, W, bar, phase, t)) return;
+        if (!eval_tile<DM, W16>(a, sh, sp, W, bar, phase, t)) return;
 }
 
 // Many instances of uneven size in one persistent launch: tile t of the
@@ -306,7 +349,7 @@ __global__ void __launch_bounds__(1024) eval_multi_kernel(const EvalArgs* __rest
             if (__ldg(tile_prefix + mid) <= t) lo = mid; else hi = mid;
         }
         const EvalArgs a = insts[lo];
-        if (!eval_tile<DM>(a, nullptr, a.p, W, bar, phase, t - __ldg(tile_prefix + lo))) return;
+        if (!eval_tile<DM, false>(a, nullptr, a.p, W, bar, phase, t - __ldg(tile_prefix + lo))) return;
     }
 }
 
@@ -396,6 +439,7 @@ static int round4(long long w) { return static_cast<int>((w + 3) & ~3ll); }
 
 struct Plan {
     int dm = 0, warps = 0, blocks = 0;
+    bool w16 = false;    // 16-bit op codes and offsets
     size_t smem = 0;
     EvalArgs args{};
 };
@@ -470,21 +514,19 @@ static bool make_plan(const vrprpd_instance* I, int dm, int warps, int blocks_pe
     return true;
 }
 
-template <int DM>
-static const void* kernel_ptr() { return reinterpret_cast<const void*>(&eval_tiles_kernel<DM>); }
-
+template <bool W16>
 static const void* kernel_for(int dm) {
     switch (dm) {
-        case VRPRPD_DIST_SMEM32: return kernel_ptr<VRPRPD_DIST_SMEM32>();
-        case VRPRPD_DIST_SMEM16: return kernel_ptr<VRPRPD_DIST_SMEM16>();
-        case VRPRPD_DIST_GLOBAL16: return kernel_ptr<VRPRPD_DIST_GLOBAL16>();
-        case VRPRPD_DIST_GLOBAL32: return kernel_ptr<VRPRPD_DIST_GLOBAL32>();
-        default: return kernel_ptr<VRPRPD_DIST_COORDS>();
+        case VRPRPD_DIST_SMEM32: return reinterpret_cast<const void*>(&eval_tiles_kernel<VRPRPD_DIST_SMEM32, W16>);
+        case VRPRPD_DIST_SMEM16: return reinterpret_cast<const void*>(&eval_tiles_kernel<VRPRPD_DIST_SMEM16, W16>);
+        case VRPRPD_DIST_GLOBAL16: return reinterpret_cast<const void*>(&eval_tiles_kernel<VRPRPD_DIST_GLOBAL16, W16>);
+        case VRPRPD_DIST_GLOBAL32: return reinterpret_cast<const void*>(&eval_tiles_kernel<VRPRPD_DIST_GLOBAL32, W16>);
+        default: return reinterpret_cast<const void*>(&eval_tiles_kernel<VRPRPD_DIST_COORDS, W16>);
     }
 }
 
 static int finalize_plan(const vrprpd_instance* I, int blocks_per_sm, Plan* P) {
-    const void* fn = kernel_for(P->dm);
+    const void* fn = P->w16 ? kernel_for<true>(P->dm) : kernel_for<false>(P->dm);
     { int rc_ = ensure_smem_limit(fn); if (rc_) return rc_; }
     int occ = 0;
     VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, P->warps * 32, P->smem));
@@ -522,25 +564,30 @@ static int choose_plan(const vrprpd_instance* I, long long num, Plan* P) {
     return VRPRPD_EINVAL;
 }
 
-static int launch_plan(const Plan& P, cudaStream_t stream) {
-    EvalArgs a = P.args;
+template <bool W16>
+static void launch_tiles(const Plan& P, const EvalArgs& a, cudaStream_t stream) {
     switch (P.dm) {
         case VRPRPD_DIST_SMEM32:
-            eval_tiles_kernel<VRPRPD_DIST_SMEM32><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
+            eval_tiles_kernel<VRPRPD_DIST_SMEM32, W16><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
             break;
         case VRPRPD_DIST_SMEM16:
-            eval_tiles_kernel<VRPRPD_DIST_SMEM16><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
+            eval_tiles_kernel<VRPRPD_DIST_SMEM16, W16><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
             break;
         case VRPRPD_DIST_GLOBAL16:
-            eval_tiles_kernel<VRPRPD_DIST_GLOBAL16><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
+            eval_tiles_kernel<VRPRPD_DIST_GLOBAL16, W16><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
             break;
         case VRPRPD_DIST_GLOBAL32:
-            eval_tiles_kernel<VRPRPD_DIST_GLOBAL32><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
+            eval_tiles_kernel<VRPRPD_DIST_GLOBAL32, W16><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
             break;
         default:
-            eval_tiles_kernel<VRPRPD_DIST_COORDS><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
+            eval_tiles_kernel<VRPRPD_DIST_COORDS, W16><<<P.blocks, P.warps * 32, P.smem, stream>>>(a);
             break;
     }
+}
+
+static int launch_plan(const Plan& P, cudaStream_t stream) {
+    if (P.w16) launch_tiles<true>(P, P.args, stream);
+    else launch_tiles<false>(P, P.args, stream);
     VRP_CUDA(cudaGetLastError());
     return VRPRPD_OK;
 }
@@ -571,6 +618,92 @@ int evaluate_device(const vrprpd_instance* I, const int32_t* ops, const int32_t*
     return launch_plan(P, stream);
 }
 
+// The same evaluation from 16-bit op codes and offsets.
+static int evaluate_device16(const vrprpd_instance* I, const uint16_t* ops, const uint16_t* off, long long num,
+                             int32_t* z, uint32_t* st, cudaStream_t stream) {
+    if (num == 0) return VRPRPD_OK;
+    if (!batched_supported(I)) {
+        set_error("batched evaluation needs m <= 32, 2n+1 < 4096 and max d < 2^19 (use the plain form)");
+        return VRPRPD_EINVAL;
+    }
+    Plan P;
+    P.w16 = true;
+    int rc = choose_plan(I, num, &P);
+    if (rc) return rc;
+    P.args.ops16 = ops;
+    P.args.off16 = off;
+    P.args.z = z;
+    P.args.st = st;
+    return launch_plan(P, stream);
+}
+
+static int check_batch16(const vrprpd_instance* I, const vrprpd_batch16* b, const void* z, const void* st) {
+    VRP_CHECK(I && b && z && st, VRPRPD_EINVAL, "NULL argument");
+    VRP_CHECK(b->num >= 0, VRPRPD_EINVAL, "negative batch size");
+    VRP_CHECK(b->num == 0 || (b->ops && b->off), VRPRPD_EINVAL, "NULL ops/off");
+    VRP_CHECK((reinterpret_cast<uintptr_t>(b->ops) & 3u) == 0 && (reinterpret_cast<uintptr_t>(b->off) & 1u) == 0,
+              VRPRPD_EINVAL, "ops must be 4-byte and off 2-byte aligned");
+    return VRPRPD_OK;
+}
+
+// Host buffers (ops/off of esz bytes per value): pinned ones are read by the
+// kernel in place over the host link (each op is read once, by coalesced
+// loads), pageable ones are copied to the device first; the results come back
+// to z_host/st_host before the call returns.
+static int evaluate_host_impl(vrprpd_instance* I, const void* ops, const void* off, int esz, long long num,
+                              int32_t* z_host, uint32_t* st_host, cudaStream_t stream) {
+    if (num == 0) return VRPRPD_OK;
+    auto run = [&](const void* o, const void* f, int32_t* dz, uint32_t* dst) {
+        return esz == 2 ? evaluate_device16(I, static_cast<const uint16_t*>(o), static_cast<const uint16_t*>(f), num,
+                                            dz, dst, stream)
+                        : evaluate_device(I, static_cast<const int32_t*>(o), static_cast<const int32_t*>(f), num, dz,
+                                          dst, stream);
+    };
+    auto grow = [&](size_t need) -> int {
+        if (need > I->stage_bytes) {
+            if (I->stage) cudaFree(I->stage);
+            I->stage = nullptr;
+            I->stage_bytes = 0;
+            VRP_CUDA(cudaMalloc(&I->stage, need));
+            I->stage_bytes = need;
+        }
+        return VRPRPD_OK;
+    };
+    const size_t ops_b = static_cast<size_t>(num) * 2 * I->n * esz, off_b = static_cast<size_t>(num) * (I->m + 1) * esz;
+    const size_t res_b = (static_cast<size_t>(num) * 4 + 255) & ~static_cast<size_t>(255);
+    const void* ops_dev = nullptr;
+    const void* off_dev = nullptr;
+    {
+        cudaPointerAttributes pa{}, pb{};
+        if (cudaPointerGetAttributes(&pa, ops) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+            cudaPointerGetAttributes(&pb, off) == cudaSuccess && pb.type == cudaMemoryTypeHost) {
+            ops_dev = pa.devicePointer;
+            off_dev = pb.devicePointer;
+        }
+        cudaGetLastError();                    // a pageable pointer is not an error here
+    }
+    int32_t* d_z;
+    int rc;
+    if (ops_dev && off_dev) {
+        if ((rc = grow(2 * res_b))) return rc;
+        d_z = reinterpret_cast<int32_t*>(I->stage);
+        rc = run(ops_dev, off_dev, d_z, reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(d_z) + res_b));
+    } else {
+        const size_t ops_r = (ops_b + 255) & ~static_cast<size_t>(255), off_r = (off_b + 255) & ~static_cast<size_t>(255);
+        if ((rc = grow(ops_r + off_r + 2 * res_b))) return rc;
+        char* base = reinterpret_cast<char*>(I->stage);
+        VRP_CUDA(cudaMemcpyAsync(base, ops, ops_b, cudaMemcpyHostToDevice, stream));
+        VRP_CUDA(cudaMemcpyAsync(base + ops_r, off, off_b, cudaMemcpyHostToDevice, stream));
+        d_z = reinterpret_cast<int32_t*>(base + ops_r + off_r);
+        rc = run(base, base + ops_r, d_z, reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(d_z) + res_b));
+    }
+    if (rc) return rc;
+    VRP_CUDA(cudaMemcpyAsync(z_host, d_z, num * 4, cudaMemcpyDeviceToHost, stream));
+    VRP_CUDA(cudaMemcpyAsync(st_host, reinterpret_cast<char*>(d_z) + res_b, num * 4, cudaMemcpyDeviceToHost, stream));
+    VRP_CUDA(cudaStreamSynchronize(stream));
+    return VRPRPD_OK;
+}
+
 }  // namespace vrp
 
 using namespace vrp;
@@ -583,68 +716,26 @@ extern "C" int vrprpd_evaluate(const vrprpd_instance* I, const vrprpd_batch* b, 
 }
 
 extern "C" int vrprpd_evaluate_host(const vrprpd_instance* I_, const vrprpd_batch* b, int32_t* z_host,
-                                    uint32_t* st_host, void* stream_) {
+                                    uint32_t* st_host, void* stream) {
     vrprpd_instance* I = const_cast<vrprpd_instance*>(I_);
     int rc = check_batch(I, b, z_host, st_host);
     if (rc) return rc;
-    cudaStream_t stream = static_cast<cudaStream_t>(stream_);
-    const long long num = b->num;
-    if (num == 0) return VRPRPD_OK;
-    const size_t ops_b = static_cast<size_t>(num) * 2 * I->n * 4, off_b = static_cast<size_t>(num) * (I->m + 1) * 4;
-    // Pinned host buffers are read by the kernel in place over the host link
-    // (each op is read once, by coalesced loads): no staging copy.  Pageable
-    // buffers are copied to the device first.
-    const void* ops_dev = nullptr;
-    const void* off_dev = nullptr;
-    {
-        cudaPointerAttributes pa{}, pb{};
-        if (cudaPointerGetAttributes(&pa, b->ops) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-            cudaPointerGetAttributes(&pb, b->off) == cudaSuccess && pb.type == cudaMemoryTypeHost) {
-            ops_dev = pa.devicePointer;
-            off_dev = pb.devicePointer;
-        }
-        cudaGetLastError();                    // a pageable pointer is not an error here
-    }
-    if (ops_dev && off_dev) {
-        const size_t need = 2 * ((num * 4 + 255) & ~255ull);
-        if (need > I->stage_bytes) {
-            if (I->stage) cudaFree(I->stage);
-            I->stage = nullptr;
-            I->stage_bytes = 0;
-            VRP_CUDA(cudaMalloc(&I->stage, need));
-            I->stage_bytes = need;
-        }
-        int32_t* d_z = reinterpret_cast<int32_t*>(I->stage);
-        uint32_t* d_st = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(d_z) + ((num * 4 + 255) & ~255ull));
-        rc = evaluate_device(I, static_cast<const int32_t*>(ops_dev), static_cast<const int32_t*>(off_dev), num, d_z,
-                             d_st, stream);
-        if (rc) return rc;
-        VRP_CUDA(cudaMemcpyAsync(z_host, d_z, num * 4, cudaMemcpyDeviceToHost, stream));
-        VRP_CUDA(cudaMemcpyAsync(st_host, d_st, num * 4, cudaMemcpyDeviceToHost, stream));
-        VRP_CUDA(cudaStreamSynchronize(stream));
-        return VRPRPD_OK;
-    }
-    const size_t need = ((ops_b + 255) & ~255ull) + ((off_b + 255) & ~255ull) + 2 * ((num * 4 + 255) & ~255ull);
-    if (need > I->stage_bytes) {
-        if (I->stage) cudaFree(I->stage);
-        I->stage = nullptr;
-        I->stage_bytes = 0;
-        VRP_CUDA(cudaMalloc(&I->stage, need));
-        I->stage_bytes = need;
-    }
-    char* base = reinterpret_cast<char*>(I->stage);
-    int32_t* d_ops = reinterpret_cast<int32_t*>(base);
-    int32_t* d_off = reinterpret_cast<int32_t*>(base + ((ops_b + 255) & ~255ull));
-    int32_t* d_z = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(d_off) + ((off_b + 255) & ~255ull));
-    uint32_t* d_st = reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(d_z) + ((num * 4 + 255) & ~255ull));
-    VRP_CUDA(cudaMemcpyAsync(d_ops, b->ops, ops_b, cudaMemcpyHostToDevice, stream));
-    VRP_CUDA(cudaMemcpyAsync(d_off, b->off, off_b, cudaMemcpyHostToDevice, stream));
-    rc = evaluate_device(I, d_ops, d_off, num, d_z, d_st, stream);
+    return evaluate_host_impl(I, b->ops, b->off, 4, b->num, z_host, st_host, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int vrprpd_evaluate16(const vrprpd_instance* I, const vrprpd_batch16* b, int32_t* z, uint32_t* st,
+                                 void* stream) {
+    int rc = check_batch16(I, b, z, st);
     if (rc) return rc;
-    VRP_CUDA(cudaMemcpyAsync(z_host, d_z, num * 4, cudaMemcpyDeviceToHost, stream));
-    VRP_CUDA(cudaMemcpyAsync(st_host, d_st, num * 4, cudaMemcpyDeviceToHost, stream));
-    VRP_CUDA(cudaStreamSynchronize(stream));
-    return VRPRPD_OK;
+    return evaluate_device16(I, b->ops, b->off, b->num, z, st, static_cast<cudaStream_t>(stream));
+}
+
+extern "C" int vrprpd_evaluate16_host(const vrprpd_instance* I_, const vrprpd_batch16* b, int32_t* z_host,
+                                      uint32_t* st_host, void* stream) {
+    vrprpd_instance* I = const_cast<vrprpd_instance*>(I_);
+    int rc = check_batch16(I, b, z_host, st_host);
+    if (rc) return rc;
+    return evaluate_host_impl(I, b->ops, b->off, 2, b->num, z_host, st_host, static_cast<cudaStream_t>(stream));
 }
 
 extern "C" int vrprpd_evaluate_plain(const vrprpd_instance* I_, const vrprpd_batch* b, int32_t* z, uint32_t* st,

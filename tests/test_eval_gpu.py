@@ -215,6 +215,57 @@ def test_pinned_host_path_reads_in_place(vrp):
         assert np.array_equal(z, zo) and np.array_equal(st, so)
 
 
+def _as16(a):
+    assert a.min() >= 0 and a.max() < 65536
+    return a.astype(np.uint16).view(np.int16)
+
+
+@pytest.mark.parametrize("n,m,count,seed", [(17, 2, 333, 1), (100, 4, 1000, 2), (37, 1, 70, 3),
+                                            (61, 32, 45, 4), (1000, 20, 300, 5)])
+def test_sixteen_bit_form(vrp, n, m, count, seed):
+    # the same codes and offsets as 16-bit values: device, pageable host and
+    # pinned host paths all equal the oracle on the 32-bit values, in every
+    # distance mode, malformed candidates included (codes 0, 1, 2n+2 and 65535,
+    # a repeated code, offsets past 2n or decreasing)
+    import torch
+    w = workloads.make_instance(n, m, max(m, 10), 5, "2x", seed=seed)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    po, pf = workloads.precedence_candidates(n, m, count, seed=seed)
+    ro, rf = workloads.random_candidates(n, m, count, seed=seed + 50)
+    ops, off = np.concatenate([po, ro]).copy(), np.concatenate([pf, rf]).copy()
+    ops[0, 0], ops[1, 1], ops[2, 2], ops[3, 2 * n - 1] = 0, 1, 2 * n + 2, 65535
+    ops[4, 3] = ops[4, 4]
+    off[5, m] = 2 * n + 1
+    if m > 1:
+        off[6, 1] = off[6, 2] + 1
+    zo, so = oracle.evaluate_batch(oi, ops, off, threads=8)
+    assert (so[:6] == oracle.MALFORMED).all()
+    o16, f16 = _as16(ops), _as16(off)
+    res = run_modes(vrp, inst, o16, f16)
+    assert res
+    for mode, (z, st) in res.items():
+        assert np.array_equal(z, zo) and np.array_equal(st, so), mode
+    z, st = vrp.evaluate_host(inst, o16, f16)
+    assert np.array_equal(z, zo) and np.array_equal(st, so)
+    z, st = vrp.evaluate_host(inst, torch.from_numpy(o16).pin_memory(), torch.from_numpy(f16).pin_memory())
+    assert np.array_equal(z, zo) and np.array_equal(st, so)
+
+
+def test_sixteen_bit_form_rejects_mixed_widths(vrp):
+    import torch
+    w = workloads.make_instance(20, 2, 4, 4, seed=1)
+    inst = vrp.Instance.from_workload(w)
+    ops, off = workloads.precedence_candidates(20, 2, 8, seed=1)
+    with pytest.raises(TypeError):
+        vrp.evaluate(inst, dev(_as16(ops)), dev(off))
+    with pytest.raises(TypeError):
+        vrp.evaluate_host(inst, ops, _as16(off))
+    with pytest.raises(TypeError):
+        vrp.evaluate_plain(inst, dev(_as16(ops)), dev(_as16(off)))
+    assert torch.cuda.is_available()
+
+
 def test_autotune_keeps_results(vrp):
     w = workloads.make_instance(100, 4, 10, 5, "2x", seed=3)
     inst = vrp.Instance.from_workload(w)
