@@ -210,7 +210,21 @@ __device__ __forceinline__ bool eval_tile(const EvalArgs& a, const int32_t* sh, 
         const int o1 = walking ? wp[pos] : 0;
         const int c1 = o1 >> 1;
         const bool p1 = (o1 & 1) != 0;
-        const int t1 = walking ? dist<DM>(a, sh, loc, c1) : 0;
+        // Travel times from shared memory are computed branch-free on every
+        // lane (an idle lane reads code 0, the depot; its result is unused);
+        // with coordinates, c1's point is kept for the second op's leg.  Only
+        // the L2 gathers are skipped on idle lanes.
+        int2 pc1 = make_int2(0, 0);
+        int t1;
+        if constexpr (DM == VRPRPD_DIST_COORDS) {
+            const int2 pl = reinterpret_cast<const int2*>(sh)[loc];
+            pc1 = reinterpret_cast<const int2*>(sh)[c1];
+            t1 = euc2d_small(pl.x, pl.y, pc1.x, pc1.y);
+        } else if constexpr (DM == VRPRPD_DIST_SMEM32 || DM == VRPRPD_DIST_SMEM16) {
+            t1 = dist<DM>(a, sh, loc, c1);
+        } else {
+            t1 = walking ? dist<DM>(a, sh, loc, c1) : 0;
+        }
         const int r1 = rdy[c1];
         const bool go1 = walking && (!p1 || r1 >= 0);
         const int a1 = dep + t1;
@@ -226,7 +240,15 @@ __device__ __forceinline__ bool eval_tile(const EvalArgs& a, const int32_t* sh, 
         const int o2 = try2 ? wp[pos] : 0;
         const int c2 = o2 >> 1;
         const bool p2 = (o2 & 1) != 0;
-        const int t2 = try2 ? dist<DM>(a, sh, c1, c2) : 0;
+        int t2;
+        if constexpr (DM == VRPRPD_DIST_COORDS) {
+            const int2 pc2 = reinterpret_cast<const int2*>(sh)[c2];
+            t2 = euc2d_small(pc1.x, pc1.y, pc2.x, pc2.y);
+        } else if constexpr (DM == VRPRPD_DIST_SMEM32 || DM == VRPRPD_DIST_SMEM16) {
+            t2 = dist<DM>(a, sh, c1, c2);
+        } else {
+            t2 = try2 ? dist<DM>(a, sh, c1, c2) : 0;
+        }
         const int r2 = rdy[c2];
         const bool go2 = try2 && (!p2 || r2 >= 0);
         const int a2 = dep + t2;
