@@ -34,7 +34,7 @@ BASE_CANDS = 16384          # generated on the host, tiled on the device
 # DRAM bytes (read + write) per candidate of eval_tiles_kernel, from one ncu
 # capture of 16384 candidates of this workload; a full launch moves the same
 # bytes per candidate (the traffic grows in proportion)
-TRAFFIC_PER_EVAL = 8283
+TRAFFIC_PER_EVAL = 8307
 ALNS_OPS_PER_ENTRY = 8
 TRAFFIC_SOURCE = "ncu dram__bytes_read+write of a 16384-candidate launch, scaled by candidates per launch"
 TILE = 32                   # batch = BASE_CANDS * TILE = 524288 candidates
