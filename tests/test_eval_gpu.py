@@ -253,7 +253,6 @@ def test_sixteen_bit_form(vrp, n, m, count, seed):
 
 
 def test_sixteen_bit_form_rejects_mixed_widths(vrp):
-    import torch
     w = workloads.make_instance(20, 2, 4, 4, seed=1)
     inst = vrp.Instance.from_workload(w)
     ops, off = workloads.precedence_candidates(20, 2, 8, seed=1)
@@ -263,7 +262,6 @@ def test_sixteen_bit_form_rejects_mixed_widths(vrp):
         vrp.evaluate_host(inst, ops, _as16(off))
     with pytest.raises(TypeError):
         vrp.evaluate_plain(inst, dev(_as16(ops)), dev(_as16(off)))
-    assert torch.cuda.is_available()
 
 
 def test_autotune_keeps_results(vrp):
