@@ -326,6 +326,64 @@ def run_multi(vrp, args):
         "speedup_vs_plain": plain_ms / multi_ms, "equal_makespan": equal}}
 
 
+def run_sweep(vrp, args):
+    """Batched evaluation across the configurations' instance shapes (17 to 501
+    nodes; base, 2x, 5x and 1R10 processing times): per shape 4096
+    precedence-consistent candidates tiled on the device to more than L2, the
+    autotuned batched launch timed with CUDA events against the plain form on
+    the same batch (equal results asserted), and the HBM fraction of the
+    candidate bytes."""
+    import torch
+    shapes = [(16, 2, 4, 4, "base", "uniform"), (100, 4, 10, 5, "2x", "uniform"),
+              (200, 6, 20, 6, "5x", "clustered"), (500, 20, 50, 8, "1R10", "uniform")]
+    pk = peaks()
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    stream = torch.cuda.current_stream()
+    out = []
+    for (n, m, R, Q, variant, layout) in shapes:
+        w = workloads.make_instance(n, m, R, Q, variant, layout, seed=7)
+        o, f = workloads.precedence_candidates(n, m, 4096, seed=7)
+        bpc = 4 * (2 * n + m + 1) + 8
+        tiles = -(-(512 << 20) // (4096 * bpc))            # more than L2 per launch
+        ops = torch.from_numpy(o).cuda().repeat(tiles, 1).contiguous()
+        off = torch.from_numpy(f).cuda().repeat(tiles, 1).contiguous()
+        B = ops.shape[0]
+        inst = vrp.Instance.from_workload(w)
+        # the tuning slice holds four tiles per warp of a full GPU (32 warps per SM)
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        tune = min(B, sms * 32 * 4 * max(1, 32 // m))
+        cfg = vrp.autotune(inst, ops[:tune], off[:tune])
+        z = torch.empty(B, dtype=torch.int32, device="cuda")
+        st = torch.empty(B, dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            vrp.evaluate(inst, ops, off, z, st)
+        vrp.sync(inst)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 10
+        e0.record(stream)
+        for _ in range(reps):
+            vrp.evaluate(inst, ops, off, z, st)
+        e1.record(stream)
+        vrp.sync(inst)
+        ms = e0.elapsed_time(e1) / reps
+        zp, sp = vrp.evaluate_plain(inst, ops, off)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        vrp.evaluate_plain(inst, ops, off, zp, sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = e0.elapsed_time(e1)
+        gbs = B * bpc / (ms / 1000.0) / 1e9
+        out.append({"workload": f"n={n} m={m} R={R} Q={Q} {variant} {layout}", "batch": B,
+                    "value": B / (ms / 1000.0), "unit": UNIT, "achieved_gbs": gbs, "frac": gbs / peak,
+                    "plain_evals_per_s": B / (plain_ms / 1000.0), "speedup_vs_plain": plain_ms / ms,
+                    "equal_makespan": bool(torch.equal(zp, z)) and bool(torch.equal(sp, st)),
+                    "eval_config": cfg})
+        del ops, off, z, st, zp, sp, inst
+    return {"eval_sweep": {"peak_gbs": peak, "peak_source": "measured" if pk else "fallback",
+                           "shapes": out}}
+
+
 def run_serving(vrp, args, alns_over=None, n_max=400, alns_iters=50, brkga_gens=20):
     """Continuous batching: a Poisson stream of solve requests (n uniform in
     [50, n_max], m = min(20, ceil(n/25)), R = ceil(n/10), Q = 10, 1R20, mixed coords),
@@ -602,6 +660,7 @@ def main():
     searches = {} if args.no_search else run_searches(vrp, args)
     searches.update(coordination)
     if not args.no_search:
+        searches.update(run_sweep(vrp, args))
         searches.update(run_multi(vrp, args))
         searches.update(run_serving(vrp, args))
 

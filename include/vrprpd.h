@@ -203,7 +203,10 @@ typedef struct {
 
 int vrprpd_eval_set_config(vrprpd_instance* inst, const vrprpd_eval_config* cfg);
 int vrprpd_eval_get_config(const vrprpd_instance* inst, vrprpd_eval_config* cfg);
-/* Time each feasible configuration on `batch` (device) and keep the fastest. */
+/* Time each feasible configuration on `batch` (device) and keep the fastest.
+ * The choice holds for batches like the one timed: give it at least a few
+ * tiles (floor(32/m) candidates each) per warp of a full GPU, or it favours
+ * shapes that only suit a batch too small to fill the SMs. */
 int vrprpd_autotune(vrprpd_instance* inst, const vrprpd_batch* batch, void* stream,
                     vrprpd_eval_config* chosen);
 
