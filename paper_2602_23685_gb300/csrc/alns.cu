@@ -2876,8 +2876,6 @@ static void carve_team(AlnsTeam& t, DevBuf& B, int n, int m, int qmax, int itera
     t.dump_travel = dump ? B.take<int>(G * G) : nullptr;
 }
 
-bool coords_exact_small(const vrprpd_instance* I);
-
 // Rows of the per-customer buffers: a route removal takes a whole route, so
 // with that operator on, up to n customers wait for reinsertion at once; the
 // relocation local search runs up to m - 1 slots for one customer.

@@ -25,6 +25,10 @@ int initial_solution_paper_tb(const vrprpd_instance* I, int32_t refine_rounds, v
 // The paper's three-phase initial solution into device buffers (construct.cu).
 int construct_paper_device(const vrprpd_instance* I, int32_t* ops, int32_t* off, cudaStream_t stream);
 
+// Coordinates present and small enough (squared extent < 2^24) for the exact
+// fp32 EUC_2D path of the kernels.
+bool coords_exact_small(const vrprpd_instance* I);
+
 #define VRP_CUDA(call)                                                                   \
     do {                                                                                 \
         cudaError_t e_ = (call);                                                         \

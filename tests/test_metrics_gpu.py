@@ -48,6 +48,22 @@ def test_random_candidates_with_cycles(vrp, n, m):
     assert (il == -1).any() and (cr >= 0).all()
 
 
+def test_distance_paths_agree(vrp):
+    # legs recomputed from small coordinates, gathered from the matrix of an
+    # instance built from d, and gathered for coordinates too spread for the
+    # fp32 path: the same counts as the oracle
+    n, m = 50, 4
+    w = workloads.make_instance(n, m, n, 8, "2x", seed=11)
+    ops, off = workloads.precedence_candidates(n, m, 200, seed=11)
+    rops, roff = workloads.random_candidates(n, m, 100, seed=12)
+    ops, off = np.concatenate([ops, rops]), np.concatenate([off, roff])
+    cr, il = both(vrp, w, ops, off)
+    inst_d = vrp.Instance(m, n, 8, w.p, d=oracle.euc2d(w.coords))
+    c2, i2 = vrp.coordination(inst_d, dev(ops), dev(off))
+    assert np.array_equal(c2.cpu().numpy(), cr) and np.array_equal(i2.cpu().numpy(), il)
+    both(vrp, workloads.Instance(w.coords * 40, w.p, m, n, 8), ops, off)
+
+
 def test_malformed(vrp):
     n, m = 10, 3
     w = workloads.make_instance(n, m, n, 8, "base", seed=1)
