@@ -49,7 +49,7 @@ def matrix_case(vrp, w, seed, n_remove, load_full=False, start="initial"):
 
 @pytest.mark.parametrize("seed", range(4))
 def test_matrix_c1(vrp, seed):
-    cfg = workloads.CONFIGS["C1"]
+    cfg = workloads.CONFIGS["tiny_n16"]
     w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], seed=seed)
     matrix_case(vrp, w, seed, 4)
 
@@ -130,9 +130,9 @@ def assert_same_run(oi, g, o):
     assert oracle.evaluate(oi, g["cur_ops"], g["cur_off"]) == (g["z_current"], 0)
 
 
-def test_alns_c1_trajectory(vrp):
-    # configuration 1: n=16, m=2, R=4, Q=4, base p; 200 iterations from seed 0
-    cfg = workloads.CONFIGS["C1"]
+def test_alns_n16_trajectory(vrp):
+    # the tiny workload: n=16, m=2, R=4, Q=4, base p; 200 iterations from seed 0
+    cfg = workloads.CONFIGS["tiny_n16"]
     w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], seed=0)
     _, oi, g, o = run_both(vrp, w, 200, seed=0)
     assert_same_run(oi, g, o)
@@ -147,7 +147,7 @@ def test_alns_single_repair_operator(vrp, mask):
 
 
 def test_alns_medium_trajectory(vrp):
-    # configuration 2 shape (m=4, R=10, Q=5, 2x, q = 10% of n) at n=40 so the
+    # the n=100 ALNS workload's shape (m=4, R=10, Q=5, 2x, q = 10% of n) at n=40 so the
     # oracle's full re-simulation stays quick
     w = workloads.make_instance(40, 4, 10, 5, "2x", seed=2)
     _, oi, g, o = run_both(vrp, w, 6, seed=1, q=(4, 4))
@@ -167,7 +167,7 @@ def test_alns_team_blocks_agree(vrp):
 
 
 def test_alns_n1000_reevaluated(vrp):
-    cfg = workloads.CONFIGS["C5"]
+    cfg = workloads.CONFIGS["serving_n1000"]
     w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=0)
     inst = vrp.Instance.from_workload(w)
     oi = oracle.OracleInstance.from_workload(w)
@@ -178,7 +178,7 @@ def test_alns_n1000_reevaluated(vrp):
 
 
 def test_matrix_n1000_sampled(vrp):
-    cfg = workloads.CONFIGS["C5"]
+    cfg = workloads.CONFIGS["serving_n1000"]
     w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=1)
     inst = vrp.Instance.from_workload(w)
     oi = oracle.OracleInstance.from_workload(w)

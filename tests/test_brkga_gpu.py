@@ -78,9 +78,9 @@ def test_brkga_small_random_start(vrp):
     run_pair(vrp, w, 50, 10, seed=9, warm=False, elite=0.15, mutant=0.15)
 
 
-def test_brkga_c3_shape_few_generations(vrp):
-    # configuration 3 shape: n=200 clustered, m=6, R=20, Q=6, 5x; pop 1024, 0.2/0.1/0.7
-    cfg = workloads.CONFIGS["C3"]
+def test_brkga_n200_shape_few_generations(vrp):
+    # the BRKGA workload's shape: n=200 clustered, m=6, R=20, Q=6, 5x; pop 1024, 0.2/0.1/0.7
+    cfg = workloads.CONFIGS["brkga_n200"]
     w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=0)
     run_pair(vrp, w, 1024, 3, seed=0)
 
@@ -116,8 +116,8 @@ def test_brkga_hint_layout_warm(vrp):
     run_pair(vrp, w, 64, 25, seed=3, layout=1)
 
 
-def test_brkga_hint_layout_c3_shape_few_generations(vrp):
-    cfg = workloads.CONFIGS["C3"]
+def test_brkga_hint_layout_n200_shape_few_generations(vrp):
+    cfg = workloads.CONFIGS["brkga_n200"]
     w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=0)
     run_pair(vrp, w, 1024, 3, seed=0, layout=1)
 

@@ -47,8 +47,8 @@ def check_against_oracle(vrp, w, ops, off, modes=MODES, load_full=False, threads
     return inst, zo, so
 
 
-def test_c1_random_and_precedence(vrp):
-    cfg = workloads.CONFIGS["C1"]
+def test_n16_random_and_precedence(vrp):
+    cfg = workloads.CONFIGS["tiny_n16"]
     w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], seed=0)
     ops, off = workloads.random_candidates(w.n, w.m, 4096, seed=0)
     _, zo, so = check_against_oracle(vrp, w, ops, off)
@@ -58,8 +58,8 @@ def test_c1_random_and_precedence(vrp):
     assert not (so & oracle.CYCLE).any()
 
 
-def test_c2_full_batch(vrp):
-    cfg = workloads.CONFIGS["C2"]
+def test_n100_full_batch(vrp):
+    cfg = workloads.CONFIGS["alns_n100"]
     w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], seed=0)
     ops, off = workloads.precedence_candidates(w.n, w.m, 65536, seed=2)
     check_against_oracle(vrp, w, ops, off, modes=["smem32", "coords"])
@@ -280,7 +280,7 @@ def test_autotune_keeps_results(vrp):
 def test_n1000_full_size_sampled(vrp, seed):
     # the headline workload: n = 1000, m = 20, R = 100, Q = 10, 1R20 processing times;
     # a 4096-candidate batch on the device, the oracle checks every 8th candidate
-    cfg = workloads.CONFIGS["C5"]
+    cfg = workloads.CONFIGS["serving_n1000"]
     w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=seed)
     inst = vrp.Instance.from_workload(w)
     oi = oracle.OracleInstance.from_workload(w)

@@ -1,5 +1,5 @@
-"""Many instances of uneven size in one persistent launch (configuration-4
-shape): every candidate bit-exact against the oracle and against the
+"""Many instances of uneven size in one persistent launch (the uneven-instance
+workload's shape: n log-uniform in [17, 500]): every candidate bit-exact against the oracle and against the
 one-launch-per-instance plain form; graph replay gives the same results."""
 import numpy as np
 import pytest

@@ -202,17 +202,17 @@ def loguniform_sizes(count, lo, hi, seed):
     return np.floor(np.exp(np.log(lo) + u * (np.log(hi + 1) - np.log(lo)))).astype(np.int64).clip(lo, hi)
 
 
-# The five workload configurations (sizes as stated for the synthetic suite).
+# The five synthetic workloads, named by what they exercise and their size.
 CONFIGS = {
-    "C1": dict(n=16, m=2, R=4, Q=4, variant="base", layout="uniform", eval_batch=4096,
-               alns_iters=200),
-    "C2": dict(n=100, m=4, R=10, Q=5, variant="2x", layout="uniform", eval_batch=65536,
-               alns_iters=5000, q=10),
-    "C3": dict(n=200, m=6, R=20, Q=6, variant="5x", layout="clustered", pop=1024,
-               elite=0.2, mutant=0.1, rho=0.7, generations=1000),
-    "C4": dict(instances=256, n_lo=17, n_hi=500, Q=8, variant="1R10", layout="uniform",
-               per_instance=4096),
-    "C5": dict(n=1000, m=20, R=100, Q=10, variant="1R20", layout="mixed"),
+    "tiny_n16": dict(n=16, m=2, R=4, Q=4, variant="base", layout="uniform", eval_batch=4096,
+                     alns_iters=200),
+    "alns_n100": dict(n=100, m=4, R=10, Q=5, variant="2x", layout="uniform", eval_batch=65536,
+                      alns_iters=5000, q=10),
+    "brkga_n200": dict(n=200, m=6, R=20, Q=6, variant="5x", layout="clustered", pop=1024,
+                       elite=0.2, mutant=0.1, rho=0.7, generations=1000),
+    "uneven_256": dict(instances=256, n_lo=17, n_hi=500, Q=8, variant="1R10", layout="uniform",
+                       per_instance=4096),
+    "serving_n1000": dict(n=1000, m=20, R=100, Q=10, variant="1R20", layout="mixed"),
 }
 
 
