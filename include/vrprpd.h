@@ -124,8 +124,9 @@ typedef struct {
     const uint16_t* off;
 } vrprpd_batch16;
 
-/* vrprpd_evaluate on a 16-bit batch: same results (a code or offset out of
- * range is MALFORMED as before), same arguments and stream semantics, device
+/* vrprpd_evaluate on a 16-bit batch (the same evaluation of Section 3.1,
+ * Eqs. 7-23): same results (a code or offset out of range is MALFORMED as
+ * before), same arguments, limits, errors and stream semantics, device
  * pointers.  Halves the candidate bytes each evaluation reads. */
 int vrprpd_evaluate16(const vrprpd_instance* inst, const vrprpd_batch16* batch, int32_t* makespan,
                       uint32_t* status, void* stream);
