@@ -2671,6 +2671,52 @@ __device__ __noinline__ bool ls_block(const AlnsTeam& t, const Smem& s, int rank
     return team_barrier(ctl, team_blocks, gen);
 }
 
+// The team barrier after the matrix phase, with the selection folded in: the
+// CTA that arrives last (every tile and shortcut item of the step is then
+// done and visible) selects and applies the insertion before it releases the
+// others, so a greedy step crosses one barrier here instead of two.  Bounded
+// like team_barrier; false when a wait gave up.
+__device__ bool team_barrier_select(const AlnsTeam& t, const Smem& s, int team_blocks, unsigned& gen) {
+    AlnsCtl* ctl = t.ctl;
+    __shared__ int last;
+    __syncthreads();
+    if (team_blocks == 1) {
+        phase_select(t, s);
+        __syncthreads();
+        return *reinterpret_cast<volatile int*>(&ctl->err) == 0;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned arrived = atomicAdd(&ctl->bar_count, 1u) + 1u;
+        last = arrived == static_cast<unsigned>(team_blocks) ? 1 : 0;
+        if (last) __threadfence();
+    }
+    __syncthreads();
+    if (last) {
+        phase_select(t, s);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ctl->bar_count = 0u;
+            __threadfence();
+            atomicExch(&ctl->bar_gen, gen + 1u);
+        }
+    } else if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &ctl->bar_gen;
+        const uint64_t t0 = global_ns();
+        while (*vgen == gen) {
+            if (global_ns() - t0 > 2000000000ull) {
+                atomicExch(&ctl->err, DEV_TIMEOUT_BARRIER);
+                break;
+            }
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    gen += 1u;
+    __syncthreads();
+    return *reinterpret_cast<volatile int*>(&ctl->err) == 0;
+}
+
 __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, int team_blocks) {
     extern __shared__ __align__(16) int smem_alns[];
     __shared__ AlnsTeam team_s;
@@ -2766,10 +2812,8 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
             if (!team_wait(ctl, team_blocks, gen)) return;
             mark(2);
             phase_matrix(t, s);
-            if (!team_barrier(ctl, team_blocks, gen)) return;
+            if (!team_barrier_select(t, s, team_blocks, gen)) return;   // select runs inside
             mark(3);
-            if (rank == 0) phase_select(t, s);
-            if (!team_barrier(ctl, team_blocks, gen)) return;
             mark(4);
         }
         if (rank == 0) phase_end(t, s, false);
