@@ -93,6 +93,29 @@ def test_euc2d_exact_integer():
     assert small[0, 1] + small[1, 2] < small[0, 2]
 
 
+def test_euc2d_rounding_boundaries():
+    # legs whose squared length sits right at a rounding tie of EUC_2D:
+    # s = r^2 + r (sqrt just below r + 1/2: rounds to r) and s = r^2 + r + 1
+    # (just above: rounds to r + 1), for r up to about 4000, against integer
+    # arithmetic alone
+    g = np.arange(0, 2900, dtype=np.int64)
+    dx, dy = np.meshgrid(g, g, indexing="ij")
+    sq = (dx * dx + dy * dy).ravel()
+    r = np.floor(np.sqrt(sq.astype(np.float64))).astype(np.int64)
+    r -= (r * r > sq)
+    r += ((r + 1) * (r + 1) <= sq)
+    tie = (sq - r * r == r) | (sq - r * r == r + 1)
+    idx = np.nonzero(tie & (r >= 2))[0]
+    pick = np.random.default_rng(5).choice(idx, size=3000, replace=False)
+    pts = np.stack([dx.ravel()[pick], dy.ravel()[pick]], axis=1)
+    coords = np.concatenate([[[0, 0]], pts]).astype(np.int32)
+    d = oracle.euc2d(coords)
+    s0, r0 = sq[pick], r[pick]
+    want = r0 + (s0 - r0 * r0 > r0)
+    assert np.array_equal(d[0, 1:], want) and np.array_equal(d[1:, 0], want)
+    assert (want == r0).sum() > 1000 and (want == r0 + 1).sum() > 1000     # both sides of the tie
+
+
 def stock_feasible_existential(route_ops, Q):
     """Vehicle feasible iff SOME start load L in [0,Q] keeps stock in [0,Q] after every
     op (drop needs a resource, pickup needs room).  Returns the least such L or None."""
