@@ -154,16 +154,30 @@ int vrprpd_evaluate_plain(const vrprpd_instance* inst, const vrprpd_batch* batch
  *   Scratch: a fixed 16 MiB array inside the library image (4 Mi int32 words),
  *   present on every GPU that loads the library until the process exits.  A
  *   call needs (n+1) + 3m + ceil((2n+2)/32) words per thread and fails with
- *   VRPRPD_EINVAL when that leaves room for fewer than 32 threads.
+ *   VRPRPD_EINVAL when that leaves room for fewer than 32 threads (n above
+ *   about 123 000 at small m).  The launch never has more threads than the
+ *   scratch holds: blocks of up to 128 threads (a multiple of 32, fewer when
+ *   fewer fit), and no more blocks than fit (vrprpd_evaluate_plain_noalloc_shape
+ *   below gives the shape).
  *   The first call on each device looks up the array's device address (a
- *   runtime query, not an allocation); make that first call before any stream
- *   capture.  Every call shares the one array: calls whose kernels overlap on
- *   the GPU (different streams, or host threads without ordering) race on it.
- *   The kernel initialises every scratch word it reads, so leftover contents
- *   from a previous call are harmless.
+ *   runtime query, not an allocation) and keeps it for the life of the
+ *   process; make that first call before any stream capture, and do not use
+ *   this entry point after cudaDeviceReset on that device.  Every call shares
+ *   the one array: calls whose kernels overlap on the GPU (different streams,
+ *   or host threads without ordering) race on it.  The kernel initialises
+ *   every scratch word it reads, so leftover contents from a previous call
+ *   are harmless.
  */
 int vrprpd_evaluate_plain_noalloc(const vrprpd_instance* inst, const vrprpd_batch* batch,
                                   int32_t* makespan, uint32_t* status, void* stream);
+
+/* The launch shape vrprpd_evaluate_plain_noalloc uses for num candidates of an
+ * instance with n customers and m vehicles: *blocks blocks of *threads
+ * threads, with blocks x threads never above what the fixed scratch holds.
+ * Host only (no CUDA call); VRPRPD_EINVAL when fewer than 32 threads fit or
+ * an argument is out of range (n >= 1, m >= 1, num >= 0). */
+int vrprpd_evaluate_plain_noalloc_shape(int32_t n, int32_t m, int64_t num, int32_t* blocks,
+                                        int32_t* threads);
 
 /*
  * Coordination counts of Section 5.2 ("Key Metrics"; the paper reports them
@@ -412,7 +426,8 @@ int vrprpd_insertion_matrix(const vrprpd_instance* inst, const int32_t* ops_host
 
 typedef struct {
     int32_t pop, generations;
-    int32_t warm_slots;        /* slots seeded from the warm start (0 without one) */
+    int32_t warm_slots;        /* slots seeded from the warm start (0 without one);
+                                  negative: ceil(0.15 pop), Section 4.4.4 */
     int32_t warm_variants;     /* distinct warm variants cycled over those slots (20) */
     float elite_frac, mutant_frac, rho;  /* Table 3: 0.15, 0.15, 0.7 */
     float eps;                 /* warm perturbation half-width (0.03, Section 4.4.4) */
@@ -420,7 +435,7 @@ typedef struct {
 } vrprpd_brkga_params;
 
 /* Table 3 values: pop 30000, 20000 generations, elite/mutant 0.15, rho 0.7,
- * warm slots ceil(0.15 pop), 20 variants, eps 0.03; layout VRPRPD_LAYOUT_VKEYS. */
+ * warm slots -1 (= ceil(0.15 pop)), 20 variants, eps 0.03; layout VRPRPD_LAYOUT_VKEYS. */
 void vrprpd_brkga_params_default(vrprpd_brkga_params* params);
 
 /*

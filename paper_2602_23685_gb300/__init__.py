@@ -356,11 +356,12 @@ def key_length(inst, layout=LAYOUT_VKEYS):
     return 4 * inst.n if layout == LAYOUT_HINTS else 2 * inst.n + inst.m
 
 
-def brkga_params(pop, generations, elite=0.2, mutant=0.1, rho=0.7, warm_frac=0.15, warm_variants=20,
+def brkga_params(pop, generations, elite=0.2, mutant=0.1, rho=0.7, warm_slots=-1, warm_variants=20,
                  eps=0.03, layout=LAYOUT_VKEYS):
-    import math
+    """BRKGA parameters; warm_slots=-1 lets the library seed ceil(0.15 pop)
+    slots from the warm start (Section 4.4.4)."""
     from ._search_sig import BrkgaParams
-    return BrkgaParams(pop, generations, int(math.ceil(warm_frac * pop - 1e-9)), warm_variants,
+    return BrkgaParams(pop, generations, warm_slots, warm_variants,
                        elite, mutant, rho, eps, layout)
 
 

@@ -544,7 +544,7 @@ extern "C" void vrprpd_brkga_params_default(vrprpd_brkga_params* P) {
     if (!P) return;
     P->pop = 30000;
     P->generations = 20000;
-    P->warm_slots = 4500;      // ceil(0.15 * 30000)
+    P->warm_slots = -1;        // ceil(0.15 * pop), worked out by vrprpd_brkga_run
     P->warm_variants = 20;
     P->elite_frac = 0.15f;
     P->mutant_frac = 0.15f;
@@ -592,7 +592,9 @@ extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_par
     if (Ne < 1) Ne = 1;
     if (Ne + Nm > pop) Nm = pop - Ne;
     const int Nc = pop - Ne - Nm;
-    const int warm_slots = warm ? std::min(P->warm_slots, pop) : 0;
+    // a negative count asks for Section 4.4.4's 15% of the population, rounded up
+    const int warm_req = P->warm_slots < 0 ? static_cast<int>((15ll * pop + 99) / 100) : P->warm_slots;
+    const int warm_slots = warm ? std::min(warm_req, pop) : 0;
     // work already queued on the caller's stream comes first
     VRP_CUDA(cudaStreamSynchronize(static_cast<cudaStream_t>(stream_)));
     cudaStream_t s;

@@ -1086,16 +1086,37 @@ static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 static std::mutex g_noalloc_mu;
 }  // namespace vrp
 
+extern "C" int vrprpd_evaluate_plain_noalloc_shape(int32_t n, int32_t m, int64_t num, int32_t* blocks,
+                                                   int32_t* threads) {
+    VRP_CHECK(n >= 1 && m >= 1 && num >= 0 && blocks && threads, VRPRPD_EINVAL, "bad arguments");
+    const long long words = (n + 1ll) + 3ll * m + (2ll * n + 2 + 31) / 32;
+    const long long max_threads = NOALLOC_SCRATCH_WORDS / words;
+    VRP_CHECK(max_threads >= 32, VRPRPD_EINVAL,
+              "instance needs %lld scratch words per thread; the fixed %lld-word scratch fits fewer than 32 "
+              "threads (use vrprpd_evaluate_plain)", words, NOALLOC_SCRATCH_WORDS);
+    // a block of up to 128 threads, a multiple of 32, and only as many
+    // blocks as the scratch holds: every launched thread owns its words
+    const long long tpb = std::min<long long>(128, max_threads / 32 * 32);
+    const long long want = std::max<long long>(1, (num + tpb - 1) / tpb);
+    const long long nb = std::max<long long>(1, std::min<long long>(want, max_threads / tpb));
+    if (nb * tpb > max_threads) {
+        set_error("internal: launch shape exceeds the fixed scratch");
+        return VRPRPD_EINVAL;
+    }
+    *blocks = static_cast<int32_t>(nb);
+    *threads = static_cast<int32_t>(tpb);
+    return VRPRPD_OK;
+}
+
 extern "C" int vrprpd_evaluate_plain_noalloc(const vrprpd_instance* I, const vrprpd_batch* b, int32_t* z,
                                              uint32_t* st, void* stream) {
     int rc = check_batch(I, b, z, st);
     if (rc) return rc;
     if (b->num == 0) return VRPRPD_OK;
+    int32_t blocks = 0, threads = 0;
+    rc = vrprpd_evaluate_plain_noalloc_shape(I->n, I->m, b->num, &blocks, &threads);
+    if (rc) return rc;
     const long long words = (I->n + 1) + 3ll * I->m + (2ll * I->n + 2 + 31) / 32;
-    const long long max_threads = NOALLOC_SCRATCH_WORDS / words;
-    VRP_CHECK(max_threads >= 32, VRPRPD_EINVAL,
-              "instance needs %lld scratch words per thread; the fixed %lld-word scratch fits fewer than 32 "
-              "threads (use vrprpd_evaluate_plain)", words, NOALLOC_SCRATCH_WORDS);
     int dev = 0;
     VRP_CUDA(cudaGetDevice(&dev));
     VRP_CHECK(dev >= 0 && dev < NOALLOC_MAX_DEVICES, VRPRPD_EINVAL, "device index %d too large", dev);
@@ -1111,9 +1132,6 @@ extern "C" int vrprpd_evaluate_plain_noalloc(const vrprpd_instance* I, const vrp
         }
         scratch = g_noalloc_ptr[dev];
     }
-    const int threads = 128;
-    const long long want = (b->num + threads - 1) / threads;
-    const int blocks = static_cast<int>(std::max<long long>(1, std::min<long long>(want, max_threads / threads)));
     eval_plain_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
         b->ops, b->off, b->num, I->n, I->m, I->R, I->Q, (I->flags & VRPRPD_LOAD_FULL) != 0, I->d32, I->p, z, st,
         static_cast<int32_t*>(scratch), static_cast<int>(words));
