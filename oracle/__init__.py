@@ -128,6 +128,11 @@ def lib():
             L.oracle_encode_l.argtypes = [C.POINTER(Inst), i32p, i32p, C.c_int32, f32p]
             L.oracle_brkga_run.argtypes = [C.POINTER(Inst), C.POINTER(BrkgaParams), i32p, i32p,
                                            C.c_uint64, f32p, i64p, i32p, i32p, i64p]
+            L.oracle_repair.argtypes = [C.POINTER(Inst), C.c_int32, i32p, i32p, i32p, C.c_int32, C.c_int32,
+                                        i32p, i32p]
+            f64p = C.POINTER(C.c_double)
+            L.oracle_alns_adapt_script.argtypes = [C.POINTER(AlnsParams), C.c_int32, C.c_int32, i32p, i32p,
+                                                   i32p, u32p, f64p, C.POINTER(AlnsStats), i32p]
             _lib = L
     return _lib
 
@@ -405,3 +410,42 @@ def destroy(I, op, ops, off, q, qmin, key, base):
     mask = np.frombuffer(rem.raw, dtype=np.uint8).astype(bool)
     assert int(mask.sum()) == cnt
     return mask
+
+
+REPAIR = {"greedy": 0, "regret2": 1, "regret3": 2, "regretm": 3}
+
+
+def repair(I, op, ops, off, removed, max_steps=-1):
+    """The repair operator op (Section 4.2.3) on a partial solution: reinsert
+    the customers `removed` (at most max_steps insertions); returns (ops, off)
+    or None when some customer has no feasible insertion."""
+    ops = np.ascontiguousarray(ops if len(ops) else np.zeros(1, np.int32), dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int32)
+    rem = np.ascontiguousarray(sorted(int(c) for c in removed), dtype=np.int32)
+    N = int(off[-1])
+    oo = np.zeros(N + 2 * len(rem) + 1, np.int32)
+    of = np.zeros(I.m + 1, np.int32)
+    rc = lib().oracle_repair(C.byref(I.c), REPAIR.get(op, op), _p(ops), _p(off),
+                             _p(rem if len(rem) else np.zeros(1, np.int32)), len(rem), max_steps, _p(oo), _p(of))
+    if rc != 0:
+        return None
+    return oo[:int(of[-1])].copy(), of
+
+
+def alns_adapt_script(params, z0, steps):
+    """Algorithm 1's acceptance and adaptation on scripted iterations: steps is
+    a list of (destroy op, repair op, candidate makespan, status, SA draw u).
+    Returns (stats, z_trace)."""
+    k = len(steps)
+    di = np.array([s[0] for s in steps] or [0], np.int32)
+    rj = np.array([s[1] for s in steps] or [0], np.int32)
+    zn = np.array([s[2] for s in steps] or [0], np.int32)
+    st = np.array([s[3] for s in steps] or [0], np.uint32)
+    u = np.array([s[4] for s in steps] or [0.0], np.float64)
+    stats = AlnsStats()
+    trace = np.zeros(max(1, k), np.int32)
+    rc = lib().oracle_alns_adapt_script(C.byref(params), int(z0), k, _p(di), _p(rj), _p(zn), _p(st, C.c_uint32),
+                                        _p(u, C.c_double), C.byref(stats), _p(trace))
+    if rc != 0:
+        raise ValueError("bad operator index in the script")
+    return stats, trace[:k]

@@ -113,6 +113,25 @@ int oracle_destroy(const oracle_inst* I, int32_t di, const int32_t* S, const int
 int oracle_local_search(const oracle_inst* I, int32_t mode, int32_t passes, int32_t* ops, int32_t* off,
                         int32_t* z);
 
+/* The repair operators alone (Section 4.2.3) on a partial solution (ops, off;
+ * off[m] ops): reinsert the customers removed[0..count) (ascending ids), op
+ * 0 greedy, 1 regret-2, 2 regret-3, 3 regret-m, one insertion per step, at
+ * most max_steps steps (negative: all).  out_ops needs off[m] + 2 count
+ * entries.  Returns 0, or -1 on bad arguments or when a customer has no
+ * feasible insertion. */
+int oracle_repair(const oracle_inst* I, int32_t op, const int32_t* ops, const int32_t* off, const int32_t* removed,
+                  int32_t count, int32_t max_steps, int32_t* out_ops, int32_t* out_off);
+
+/* Algorithm 1's acceptance and adaptation alone, on a scripted run: iteration
+ * k (1-based) used destroy operator di[k-1] and repair operator rj[k-1], its
+ * repaired candidate has makespan zn[k-1] and status st[k-1], and u[k-1] is
+ * its SA draw.  Starts from makespan z0 (current = best), unit weights and
+ * T = T0 z0, as oracle_alns_run does; fills stats (scores, weights, T,
+ * counts) and z_trace (current makespan after each iteration). */
+int oracle_alns_adapt_script(const oracle_alns_params* P, int32_t z0, int32_t iters, const int32_t* di,
+                             const int32_t* rj, const int32_t* zn, const uint32_t* st, const double* u,
+                             oracle_alns_stats* stats, int32_t* z_trace);
+
 int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t* init_off,
                     const oracle_alns_params* P, uint64_t seed,
                     int32_t* best_ops, int32_t* best_off, int32_t* cur_ops, int32_t* cur_off,

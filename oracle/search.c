@@ -321,15 +321,16 @@ static void apply_insert(const oracle_inst* I, int32_t* ops, int32_t* off, int c
 
 #define REGRET_INF ((int64_t)1 << 40)
 
-/* Greedy (repair 0) or regret-2 (repair 1) reinsertion of the customers in
- * rem[] (listed in ascending id order in list[]). */
-static int repair(const oracle_inst* I, int op, int32_t* ops, int32_t* off, int* list, int cnt,
-                  int32_t* tmp_ops, int32_t* tmp_off) {
+/* Greedy (repair 0) or regret-k (repair 1, 2, 3: k = 2, 3, m) reinsertion of
+ * the customers listed in ascending id order in list[]: one insertion per
+ * step, at most max_steps steps (negative: until none is left). */
+static int repair_steps(const oracle_inst* I, int op, int32_t* ops, int32_t* off, int* list, int cnt,
+                        int max_steps, int32_t* tmp_ops, int32_t* tmp_off) {
     const int m = I->m;
     best_t* pv = (best_t*)malloc(sizeof(best_t) * m);
     best_t* bests = (best_t*)malloc(sizeof(best_t) * (cnt + 1));
     int64_t* regret = (int64_t*)malloc(sizeof(int64_t) * (cnt + 1));
-    while (cnt > 0) {
+    for (int step = 0; cnt > 0 && step != max_steps; step++) {
         for (int t = 0; t < cnt; t++) {
             scan_matrix(I, ops, off, list[t], &bests[t], pv);
             if (!bests[t].ok) { free(pv); free(bests); free(regret); return -1; }
@@ -366,6 +367,31 @@ static int repair(const oracle_inst* I, int op, int32_t* ops, int32_t* off, int*
     free(bests);
     free(regret);
     return 0;
+}
+
+static int repair(const oracle_inst* I, int op, int32_t* ops, int32_t* off, int* list, int cnt,
+                  int32_t* tmp_ops, int32_t* tmp_off) {
+    return repair_steps(I, op, ops, off, list, cnt, -1, tmp_ops, tmp_off);
+}
+
+int oracle_repair(const oracle_inst* I, int32_t op, const int32_t* ops, const int32_t* off, const int32_t* removed,
+                  int32_t count, int32_t max_steps, int32_t* out_ops, int32_t* out_off) {
+    const int m = I->m, N = off[m];
+    if (op < 0 || op > 3 || count < 0 || N + 2 * count > 2 * I->n) return -1;
+    int* list = malloc(sizeof(int) * (size_t)(count + 1));
+    for (int t = 0; t < count; t++) {
+        if (removed[t] < 1 || removed[t] > I->n || (t > 0 && removed[t] <= removed[t - 1])) { free(list); return -1; }
+        list[t] = removed[t];
+    }
+    int32_t* tmp = malloc(sizeof(int32_t) * (size_t)(2 * I->n + 2));
+    int32_t* tmpo = malloc(sizeof(int32_t) * (size_t)(m + 1));
+    memcpy(out_ops, ops, sizeof(int32_t) * (size_t)N);
+    memcpy(out_off, off, sizeof(int32_t) * (size_t)(m + 1));
+    int rc = repair_steps(I, op, out_ops, out_off, list, count, max_steps, tmp, tmpo);
+    free(list);
+    free(tmp);
+    free(tmpo);
+    return rc;
 }
 
 static int roulette(const double* w, const int* enabled, int k, double u) {
@@ -725,58 +751,50 @@ static int alns_init(alns_t* A, const oracle_inst* I, const int32_t* init_ops, c
     return 0;
 }
 
-/* Iteration it of Algorithm 1, then the periodic local search. */
-static void alns_iteration(alns_t* A, int it) {
-    const oracle_inst* I = A->I;
+/* Algorithm 1's bookkeeping of iteration it once the repair is done: destroy
+ * operator di and repair operator rj gave a candidate of makespan zn and
+ * status st, and u is the iteration's SA draw.  A candidate with a status bit
+ * is rejected.  One below the current makespan is accepted and scores sigma2,
+ * or sigma1 if it is also below the best.  Any other is accepted when
+ * u < exp(-(zn - z)/T) and scores sigma3 (an equal makespan gives exp(0) = 1).
+ * Then cooling T <- alpha T, the stagnation count, the reheat (stagnation and
+ * T below 1% of its start: T <- reheat T0 z_best) and, every tau iterations,
+ * w <- max(w_min, (1 - r) w + r s/a) per operator (s/a = 0 without attempts).
+ * Returns 0 (rejected), 1 (current) or 2 (current and new best). */
+static int alns_accept_adapt(alns_t* A, int it, int di, int rj, int32_t zn, uint32_t st, double u) {
     const oracle_alns_params* P = A->P;
-    const int n = I->n, m = I->m, two_n = 2 * n, ND = ND_OPS, NR = 4;
     oracle_alns_stats* stats = A->stats;
-    const uint64_t base = (uint64_t)it << 16, key = A->key;
-    int di = roulette(A->wd, A->en_d, ND, rng_unit(oracle_rng(key, base + 0)));   /* destroy operator by roulette */
-    int rj = roulette(A->wr, A->en_r, NR, rng_unit(oracle_rng(key, base + 1)));   /* repair operator by roulette */
+    const int ND = ND_OPS, NR = 4;
+    int took = 0;
     A->ad[di]++;
     A->ar[rj]++;                                                                 /* attempt counts */
-    int q = A->qmin + rng_below(oracle_rng(key, base + 2), A->qmax - A->qmin + 1);
-    oracle_destroy(I, di, A->S, A->So, q, A->qmin, key, base, A->rem);           /* destroy */
-    remove_customers(m, A->S, A->So, A->rem, A->W, A->Wo);
-    int cnt = 0;
-    for (int c = 1; c <= n; c++)
-        if (A->rem[c]) A->list[cnt++] = c;
-    int32_t zn = INT32_MAX;
-    uint32_t st = OR_MALFORMED;
-    if (repair(I, rj, A->W, A->Wo, A->list, cnt, A->tmp, A->tmpo) == 0)          /* repair */
-        oracle_evaluate(I, A->W, A->Wo, 0, &zn, &st, NULL);                      /* makespan of the candidate */
     if (st) {
         /* repair found no feasible slot, or a route the destroy left over
          * capacity was never repaired: the candidate is rejected */
         stats->rejected_infeasible++;
     } else if (zn < A->z) {                                                      /* improving: accept, scores */
-        memcpy(A->S, A->W, sizeof(int32_t) * two_n);
-        memcpy(A->So, A->Wo, sizeof(int32_t) * (m + 1));
         A->z = zn;
         A->sd[di] += P->sigma2;
         A->sr[rj] += P->sigma2;
         stats->improved++;
         stats->accepted++;
+        took = 1;
         if (zn < A->zb) {
-            memcpy(A->Sb, A->W, sizeof(int32_t) * two_n);
-            memcpy(A->Sbo, A->Wo, sizeof(int32_t) * (m + 1));
             A->zb = zn;
             A->sd[di] += P->sigma1 - P->sigma2;
             A->sr[rj] += P->sigma1 - P->sigma2;
             A->stagnation = 0;
             stats->new_best++;
+            took = 2;
         }
     } else {
         double x = -(double)((int64_t)zn - (int64_t)A->z) / A->T;
-        double u = rng_unit(oracle_rng(key, base + 3));
         if (u < oracle_exp(x)) {                                                 /* SA acceptance */
-            memcpy(A->S, A->W, sizeof(int32_t) * two_n);
-            memcpy(A->So, A->Wo, sizeof(int32_t) * (m + 1));
             A->z = zn;
             A->sd[di] += P->sigma3;
             A->sr[rj] += P->sigma3;
             stats->accepted++;
+            took = 1;
         }
     }
     A->T = P->alpha * A->T;                                                      /* cooling */
@@ -801,6 +819,37 @@ static void alns_iteration(alns_t* A, int it) {
             A->sr[i] = 0;
             A->ar[i] = 0;
         }
+    }
+    return took;
+}
+
+/* Iteration it of Algorithm 1, then the periodic local search. */
+static void alns_iteration(alns_t* A, int it) {
+    const oracle_inst* I = A->I;
+    const oracle_alns_params* P = A->P;
+    const int n = I->n, m = I->m, two_n = 2 * n, ND = ND_OPS, NR = 4;
+    oracle_alns_stats* stats = A->stats;
+    const uint64_t base = (uint64_t)it << 16, key = A->key;
+    int di = roulette(A->wd, A->en_d, ND, rng_unit(oracle_rng(key, base + 0)));   /* destroy operator by roulette */
+    int rj = roulette(A->wr, A->en_r, NR, rng_unit(oracle_rng(key, base + 1)));   /* repair operator by roulette */
+    int q = A->qmin + rng_below(oracle_rng(key, base + 2), A->qmax - A->qmin + 1);
+    oracle_destroy(I, di, A->S, A->So, q, A->qmin, key, base, A->rem);           /* destroy */
+    remove_customers(m, A->S, A->So, A->rem, A->W, A->Wo);
+    int cnt = 0;
+    for (int c = 1; c <= n; c++)
+        if (A->rem[c]) A->list[cnt++] = c;
+    int32_t zn = INT32_MAX;
+    uint32_t st = OR_MALFORMED;
+    if (repair(I, rj, A->W, A->Wo, A->list, cnt, A->tmp, A->tmpo) == 0)          /* repair */
+        oracle_evaluate(I, A->W, A->Wo, 0, &zn, &st, NULL);                      /* makespan of the candidate */
+    const int took = alns_accept_adapt(A, it, di, rj, zn, st, rng_unit(oracle_rng(key, base + 3)));
+    if (took >= 1) {                                                             /* the candidate is current */
+        memcpy(A->S, A->W, sizeof(int32_t) * two_n);
+        memcpy(A->So, A->Wo, sizeof(int32_t) * (m + 1));
+    }
+    if (took == 2) {                                                             /* and the new best */
+        memcpy(A->Sb, A->W, sizeof(int32_t) * two_n);
+        memcpy(A->Sbo, A->Wo, sizeof(int32_t) * (m + 1));
     }
     /* periodic local search on the current solution (Section 4.2.6):
      * pickup repositioning first when both fall due */
@@ -849,6 +898,34 @@ int oracle_alns_run(const oracle_inst* I, const int32_t* init_ops, const int32_t
     memcpy(best_ops, A.Sb, sizeof(int32_t) * 2 * I->n);
     memcpy(best_off, A.Sbo, sizeof(int32_t) * (I->m + 1));
     alns_free(&A);
+    return 0;
+}
+
+int oracle_alns_adapt_script(const oracle_alns_params* P, int32_t z0, int32_t iters, const int32_t* di,
+                             const int32_t* rj, const int32_t* zn, const uint32_t* st, const double* u,
+                             oracle_alns_stats* stats, int32_t* z_trace) {
+    alns_t A;
+    memset(&A, 0, sizeof(A));
+    memset(stats, 0, sizeof(*stats));
+    A.P = P;
+    A.stats = stats;
+    A.z = A.zb = z0;
+    for (int i = 0; i < ND_OPS; i++) A.wd[i] = 1.0;
+    for (int i = 0; i < 4; i++) A.wr[i] = 1.0;
+    A.T = P->T0 * (double)z0;                      /* initial temperature, as alns_init */
+    A.T_init = A.T;
+    stats->z_init = z0;
+    for (int it = 1; it <= iters; it++) {
+        if (di[it - 1] < 0 || di[it - 1] >= ND_OPS || rj[it - 1] < 0 || rj[it - 1] >= 4) return -1;
+        alns_accept_adapt(&A, it, di[it - 1], rj[it - 1], zn[it - 1], st[it - 1], u[it - 1]);
+        if (z_trace) z_trace[it - 1] = A.z;
+        stats->iterations = it;
+    }
+    stats->z_best = A.zb;
+    stats->z_current = A.z;
+    stats->T_final = A.T;
+    for (int i = 0; i < ND_OPS; i++) stats->w_destroy[i] = A.wd[i];
+    for (int i = 0; i < 4; i++) stats->w_repair[i] = A.wr[i];
     return 0;
 }
 

@@ -64,3 +64,71 @@ def test_alns_without_acceptance_keeps_its_start():
     z0 = oracle.evaluate(I, *init)[0]
     assert o["stats"].z_best == z0 and o["stats"].improved == 0
     assert np.array_equal(o["best_ops"], init[0]) and (o["trace"] == z0).all()
+
+
+def _generation_pair(rho, layout=0, pop=48, seed=6):
+    w = workloads.make_instance(12, 3, 6, 4, "2x", seed=7)
+    I = oracle.OracleInstance.from_workload(w)
+    warm = oracle.initial_solution(I, w.coords)
+    P1 = oracle.brkga_params(pop, 1, 0.25, 0.125, rho=rho, layout=layout)
+    P2 = oracle.brkga_params(pop, 2, 0.25, 0.125, rho=rho, layout=layout)
+    g0 = oracle.brkga_run(I, P1, warm[0], warm[1], seed)["keys"]
+    g1 = oracle.brkga_run(I, P2, warm[0], warm[1], seed)["keys"]
+    fit = [oracle.decode(I, g0[s], layout)[4] for s in range(pop)]
+    order = sorted(range(pop), key=lambda s: (fit[s], s))
+    ne, nm = int(math.floor(0.25 * pop)), int(math.floor(0.125 * pop))
+    return g0, g1, order, ne, nm
+
+
+def _rows(a):
+    return [r.view(np.uint32).tobytes() for r in a]
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_crossover_rho_one_copies_the_elite_parent(layout):
+    """Section 4.4.3: each gene comes from the elite parent with probability
+    rho.  With rho = 1 every child is a copy of one of the previous N_e best
+    (a draw u in [0, 1) is always below 1), and the copies do not all come
+    from one parent."""
+    g0, g1, order, ne, nm = _generation_pair(1.0, layout)
+    pop = g0.shape[0]
+    elite = set(_rows(g0[order[:ne]]))
+    rest = set(_rows(g0[order[ne:]]))
+    kids = _rows(g1[ne:pop - nm])
+    assert all(k in elite for k in kids)
+    assert not any(k in rest for k in kids)
+    assert len(set(kids)) > 1
+
+
+@pytest.mark.parametrize("layout", [0, 1])
+def test_crossover_rho_zero_copies_the_other_parent(layout):
+    """With rho = 0 no gene comes from the elite parent: every child copies one
+    chromosome from outside the previous N_e best."""
+    g0, g1, order, ne, nm = _generation_pair(0.0, layout)
+    pop = g0.shape[0]
+    elite = set(_rows(g0[order[:ne]]))
+    rest = set(_rows(g0[order[ne:]]))
+    kids = _rows(g1[ne:pop - nm])
+    assert all(k in rest for k in kids)
+    assert not any(k in elite for k in kids)
+    assert len(set(kids)) > 1
+
+
+def test_crossover_bias_is_rho():
+    """rho = 0.7: each child is explained by one (elite, other) parent pair,
+    and where the two parents differ the child takes the elite gene about 70%
+    of the time (about 1000 such genes here: 0.7 +- 0.05 is beyond 3 sigma)."""
+    g0, g1, order, ne, nm = _generation_pair(0.7, pop=64, seed=8)
+    pop = g0.shape[0]
+    E, O = g0[order[:ne]], g0[order[ne:]]
+    took_e = total = 0
+    for child in g1[ne:pop - nm]:
+        pairs = [(e, o) for e in range(ne) for o in range(len(O))
+                 if np.all((child == E[e]) | (child == O[o]))]
+        assert pairs, "a child not made from an (elite, other) pair"
+        e, o = pairs[0]
+        diff = E[e] != O[o]
+        took_e += int(np.sum(child[diff] == E[e][diff]))
+        total += int(np.sum(diff))
+    assert total > 800
+    assert abs(took_e / total - 0.7) < 0.05, took_e / total
