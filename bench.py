@@ -150,6 +150,34 @@ def cpu_baseline(w, ops, off, budget_s=12.0):
                       f"workload, one C thread per core, {dt:.1f} s"}
 
 
+def summary_of(line):
+    """The headline numbers of every leg in one short object, printed last so
+    that a reader of only the line's end still sees them all."""
+    def g(*keys):
+        x = line
+        for k in keys:
+            if not isinstance(x, dict) or k not in x:
+                return None
+            x = x[k]
+        return round(x, 4) if isinstance(x, float) else x
+    return {
+        "evals_per_s_n1000": g("value"), "roofline_frac": g("roofline", "frac"),
+        "e2e_evals_per_s": g("e2e", "value"), "plain_gpu_evals_per_s": g("plain_gpu", "value"),
+        "ops16_evals_per_s": g("ops16", "value"), "ops16_e2e_evals_per_s": g("ops16", "e2e", "value"),
+        "alns_n1000_iters_per_s": g("alns_n1000", "value"), "alns_n1000_iterations": g("alns_n1000", "iterations"),
+        "alns_n1000_alu_frac": g("alns_n1000", "roofline", "frac"),
+        "alns_n1000_x32_iters_per_s": g("alns_n1000_x32", "value"),
+        "alns_n100_iters_per_s": g("alns_n100", "value"), "alns_n100_iterations": g("alns_n100", "iterations"),
+        "brkga_n200_gens_per_s": g("brkga_n200", "value"), "brkga_n200_generations": g("brkga_n200", "generations"),
+        "brkga_n200_hints_gens_per_s": g("brkga_n200_hints", "value"),
+        "multi_evals_per_s": g("batched_multi", "value"),
+        "serving_req_per_s": g("serving", "value"), "serving_p50_ms": g("serving", "p50_ms"),
+        "serving_p99_ms": g("serving", "p99_ms"),
+        "serving_c5_completed": g("serving_c5", "completed"), "serving_c5_p50_ms": g("serving_c5", "p50_ms"),
+        "serving_c5_p99_ms": g("serving_c5", "p99_ms"),
+        "cpu_oracle_evals_per_s": g("cpu_baseline", "value")}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -203,7 +231,7 @@ def run_searches(vrp, args):
     out = {}
     w5 = workloads.make_instance(N_CUST, M_VEH, R_POOL, Q_CAP, "1R20", "mixed", seed=0)
     i5 = vrp.Instance.from_workload(w5)
-    vrp.alns_run(i5, vrp.alns_params(1), seed=1)                       # warm-up
+    vrp.alns_run(i5, vrp.alns_params(2), seed=1)                       # warm-up
     r = vrp.alns_run(i5, vrp.alns_params(args.alns_iters), seed=0)
     st = r["stats"]
     out["alns_n1000"] = {
@@ -227,22 +255,23 @@ def run_searches(vrp, args):
         "peak_source": "152 SMs x 128 int32 lanes x 2070 MHz (nominal)"}
     # the paper's multi-instance configuration: 32 replicas share the GPU
     # (Section 4.2.1), each a team of 1/32 of the resident CTAs
-    rr = vrp.alns_run(i5, vrp.alns_params(args.alns_iters // 2, replicas=32, sync_every=5), seed=0)
+    rr = vrp.alns_run(i5, vrp.alns_params(args.replica_iters, replicas=32, sync_every=5), seed=0)
     sr = rr["stats"]
     out["alns_n1000_x32"] = {
-        "value": 32 * (args.alns_iters // 2) / (sr.device_ms / 1000.0), "unit": "ALNS iters/s (all replicas)",
+        "value": 32 * args.replica_iters / (sr.device_ms / 1000.0), "unit": "ALNS iters/s (all replicas)",
         "config": "as alns_n1000 with 32 replicas (multi-instance, Section 4.2.1), best-of-all import every "
-                  "5 iterations", "iterations_per_replica": args.alns_iters // 2, "team_blocks": sr.team_blocks,
+                  "5 iterations", "iterations_per_replica": args.replica_iters, "team_blocks": sr.team_blocks,
         "imports": sr.imports, "z_best": sr.z_best, "device_ms": sr.device_ms}
     w2 = workloads.make_instance(100, 4, 10, 5, "2x", "uniform", seed=0)
     i2 = vrp.Instance.from_workload(w2)
-    r2 = vrp.alns_run(i2, vrp.alns_params(args.alns_iters * 10, 10, 10), seed=0)
+    vrp.alns_run(i2, vrp.alns_params(20, 10, 10), seed=1)             # warm-up
+    r2 = vrp.alns_run(i2, vrp.alns_params(args.alns100_iters, 10, 10), seed=0)
     st2 = r2["stats"]
     out["alns_n100"] = {
-        "value": args.alns_iters * 10 / (st2.device_ms / 1000.0), "unit": "ALNS iters/s",
+        "value": args.alns100_iters / (st2.device_ms / 1000.0), "unit": "ALNS iters/s",
         "config": "n=100 m=4 R=10 Q=5 2x, q=10; periodic local search (Section 4.2.6) included: pickup "
                   "repositioning every 200 and cross-agent relocation every 500 iterations",
-        "iterations": args.alns_iters * 10,
+        "iterations": args.alns100_iters,
         "matrix_entries_per_s": st2.matrix_entries / (st2.device_ms / 1000.0),
         "team_blocks": st2.team_blocks, "z_init": st2.z_init, "z_best": st2.z_best,
         "ls_moves": st2.ls_moves, "ls_ms": st2.ls_ms}
@@ -430,6 +459,75 @@ def run_serving(vrp, args, alns_over=None, n_max=400, alns_iters=50, brkga_gens=
                   f"+ {brkga_gens} BRKGA generations of 256 per request; 4 slots, 16 GiB"}}
 
 
+def run_serving_c5(vrp, args):
+    """The full-size serving mix: a Poisson stream of solve requests with n
+    uniform in [50, 1000], m = min(20, ceil(n/25)), R = ceil(n/10), Q = 10,
+    1R20, mixed coordinates, each running 2000 ALNS iterations then 200 BRKGA
+    generations of 1024, admitted by a 32 GiB device-memory budget onto 4
+    slots.  The 500-request stream takes far longer than a bench run, so it
+    runs in bounded windows: first the capacity (the stream's first requests
+    all queued at once for cal_s seconds), then arrivals at 0.8x that rate for
+    window_s seconds; requests still waiting for admission at a window's end
+    are withdrawn, and those already running finish.  Latencies (submit to
+    finish) are over the requests that ran, so the longest requests are
+    under-represented when a window cuts the stream."""
+    import numpy as np
+    rng = np.random.default_rng(11)
+    n_req = 500
+    ns = rng.integers(50, 1001, size=n_req)
+    reqs = [workloads.make_instance(int(n), min(20, -(-int(n) // 25)), -(-int(n) // 10), 10, "1R20", "mixed",
+                                    seed=1000 + i) for i, n in enumerate(ns)]
+    budget = 32 << 30
+
+    def submit(srv, i):
+        return srv.submit(reqs[i], alns_iterations=2000, brkga_pop=1024, brkga_generations=200, seed=i)
+
+    # capacity: everything queued, completions counted over the window
+    srv = vrp.Server(budget, max_active=4)
+    t0 = time.perf_counter()
+    ids = [submit(srv, i) for i in range(min(n_req, 24))]
+    while time.perf_counter() - t0 < args.serve_c5_cal and srv.stats()["completed"] < len(ids):
+        time.sleep(0.25)
+    done_cal = srv.stats()["completed"]
+    cal_s = time.perf_counter() - t0
+    srv.cancel_pending()
+    srv.close()
+    capacity = max(done_cal, 1) / cal_s
+    rate = 0.8 * capacity
+    # the stream at 0.8x capacity, from where the calibration stopped
+    srv = vrp.Server(budget, max_active=4)
+    t0 = time.perf_counter()
+    next_t, i, ids, idx = 0.0, len(ids), [], []
+    while i < n_req:
+        now = time.perf_counter() - t0
+        if now >= args.serve_c5_window:
+            break
+        if now >= next_t:
+            ids.append(submit(srv, i))
+            idx.append(i)
+            i += 1
+            next_t += float(rng.exponential(1.0 / rate))
+        else:
+            time.sleep(min(0.05, next_t - now))
+    withdrawn = srv.cancel_pending()
+    res = [srv.wait(r) for r in ids]
+    wall = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    ran_n = [reqs[k].n for k, r in zip(idx, res) if r["status"] == 0]
+    return {"serving_c5": {
+        "unit": "requests/s", "value": len(ran_n) / wall, "submitted": len(ids), "completed": st["completed"],
+        "withdrawn": withdrawn, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+        "capacity_requests_per_s": capacity, "arrival_rate": rate, "window_s": args.serve_c5_window,
+        "wall_s": wall, "calibration_s": cal_s, "calibration_completed": done_cal,
+        "peak_active": st["peak_active"], "peak_bytes": st["peak_bytes"],
+        "mean_n_completed": float(np.mean(ran_n)) if ran_n else None,
+        "config": "Poisson arrivals at 0.8x measured capacity; n ~ U[50,1000], m=min(20,ceil(n/25)), "
+                  "R=ceil(n/10), Q=10, 1R20, mixed coords; 2000 ALNS iterations + 200 BRKGA generations of "
+                  "1024 per request; 4 slots, 32 GiB; bounded window (requests not admitted by its end "
+                  "withdrawn)"}}
+
+
 def run_profile_alns(args):
     """One warm-up ALNS launch and one measured one: n=200 clustered, m=6,
     R=20, Q=6, 5x, 10 iterations; or (--profile-alns-n1000) the n=1000
@@ -476,9 +574,15 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-search", action="store_true", help="skip the ALNS / BRKGA legs")
-    ap.add_argument("--alns-iters", type=int, default=20)
-    ap.add_argument("--brkga-gens", type=int, default=100)
+    ap.add_argument("--alns-iters", type=int, default=200, help="ALNS iterations at n=1000")
+    ap.add_argument("--alns100-iters", type=int, default=5000, help="ALNS iterations at n=100")
+    ap.add_argument("--replica-iters", type=int, default=20, help="iterations per replica, 32 replicas at n=1000")
+    ap.add_argument("--brkga-gens", type=int, default=1000)
     ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--serve-c5-window", type=float, default=90.0,
+                    help="seconds of Poisson arrivals in the full-size serving leg (0 = skip the leg)")
+    ap.add_argument("--serve-c5-cal", type=float, default=45.0,
+                    help="seconds of the full-size serving leg's capacity measurement")
     ap.add_argument("--profile-alns", action="store_true",
                     help="small ALNS case for ncu: n=200, 10 iterations per launch, one warm-up launch")
     ap.add_argument("--profile-brkga", action="store_true",
@@ -663,6 +767,8 @@ def main():
         searches.update(run_sweep(vrp, args))
         searches.update(run_multi(vrp, args))
         searches.update(run_serving(vrp, args))
+        if args.serve_c5_window > 0:
+            searches.update(run_serving_c5(vrp, args))
 
     pk = peaks()
     bytes_per_eval = 4 * (2 * N_CUST + M_VEH + 1) + 8
@@ -694,6 +800,7 @@ def main():
         line.update(searches)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w, ops_h, off_h)
+        line["summary"] = summary_of(line)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

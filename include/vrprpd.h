@@ -408,6 +408,30 @@ int vrprpd_insertion_matrix(const vrprpd_instance* inst, const int32_t* ops_host
                             const int32_t* off_host, int32_t c, int32_t* delta_host,
                             int32_t* travel_host, void* stream);
 
+/*
+ * The repair of Section 4.2.3 stopped part way, for checking its later
+ * steps: the partial solution (host ops[off[m]], off[m+1], holding every
+ * customer but the `count` ascending ids in `removed`) is repaired for
+ * `steps` insertions (0 <= steps < count) by repair operator repair_op (0
+ * greedy, 1 regret-2, 2 regret-3, 3 regret-m) exactly as an ALNS iteration
+ * does, on a team of team_blocks CTAs (0 = the whole GPU): after an insertion
+ * whose two gaps are no shortcuts the next step updates the longest-path
+ * table in place instead of re-walking the solution.  Then the insertion
+ * matrix of the first customer still to insert (the smallest remaining id) is
+ * written out as vrprpd_insertion_matrix writes it.
+ *   out_ops/out_off  host, off[m] + 2 steps ops and m + 1 offsets: the
+ *                    partial solution after the steps.
+ *   delta/travel     host, G x G with G = off[m] + 2 steps + m (travel may be NULL).
+ *   incremental_steps  host, may be NULL: steps (the dump's included) whose
+ *                    table was updated in place.
+ * VRPRPD_EINVAL if a customer has no feasible insertion on the way.  Blocking.
+ */
+int vrprpd_repair_then_matrix(const vrprpd_instance* inst, const int32_t* ops_host, const int32_t* off_host,
+                              const int32_t* removed_host, int32_t count, int32_t repair_op, int32_t steps,
+                              int32_t team_blocks, int32_t* out_ops_host, int32_t* out_off_host,
+                              int32_t* delta_host, int32_t* travel_host, int64_t* incremental_steps,
+                              void* stream);
+
 /* ======================================================================== */
 /* BRKGA (Section 4.4, Algorithm 2) on the device                            */
 /* ======================================================================== */
@@ -530,6 +554,11 @@ int vrprpd_server_poll(vrprpd_server* server, int64_t id, vrprpd_result* out, in
 /* Blocking form of poll. */
 int vrprpd_server_wait(vrprpd_server* server, int64_t id, vrprpd_result* out, int32_t* ops, int32_t* off);
 int vrprpd_server_get_stats(vrprpd_server* server, vrprpd_server_stats* out);
+/* Withdraw every request still waiting for admission (requests already
+ * running finish).  Each withdrawn request completes at once with status
+ * VRPRPD_EBUSY and the message "withdrawn before admission"; *withdrawn (may
+ * be NULL) receives their count.  Serves a bounded serving window. */
+int vrprpd_server_cancel_pending(vrprpd_server* server, int32_t* withdrawn);
 /* Finish everything queued, stop the workers, free the server. */
 void vrprpd_server_destroy(vrprpd_server* server);
 

@@ -159,6 +159,12 @@ class Instance:
         _check(lib().vrprpd_instance_get_dist(self.handle, d.ctypes.data))
         return d
 
+    def cancel_pending(self):
+        """Withdraw the requests not admitted yet; returns how many."""
+        k = np.zeros(1, np.int32)
+        _check(lib().vrprpd_server_cancel_pending(self._h, k.ctypes.data))
+        return int(k[0])
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             lib().vrprpd_instance_destroy(self._h)
@@ -345,6 +351,29 @@ def insertion_matrix(inst, ops, off, c, stream=None):
     return delta, travel
 
 
+def repair_then_matrix(inst, ops, off, removed, steps, repair_op=0, team_blocks=0, stream=None):
+    """`steps` repair insertions of the customers `removed` into the host
+    partial solution (ops, off), then the insertion-delta matrix of the
+    smallest customer still to insert.  Returns (ops, off, delta, travel,
+    incremental steps)."""
+    ops = np.ascontiguousarray(ops, dtype=np.int32)
+    off = np.ascontiguousarray(off, dtype=np.int32)
+    rem = np.ascontiguousarray(sorted(int(c) for c in removed), dtype=np.int32)
+    nout = int(off[-1]) + 2 * int(steps)
+    G = nout + inst.m
+    oo = np.zeros(max(nout, 1), np.int32)
+    of = np.zeros(inst.m + 1, np.int32)
+    delta = np.empty((G, G), np.int32)
+    travel = np.empty((G, G), np.int32)
+    inc = np.zeros(1, np.int64)
+    opsp = ops if ops.size else np.zeros(1, np.int32)
+    _check(lib().vrprpd_repair_then_matrix(inst.handle, opsp.ctypes.data, off.ctypes.data, rem.ctypes.data,
+                                           len(rem), int(repair_op), int(steps), int(team_blocks), oo.ctypes.data,
+                                           of.ctypes.data, delta.ctypes.data, travel.ctypes.data, inc.ctypes.data,
+                                           _stream_ptr(stream)))
+    return oo[:nout], of, delta, travel, int(inc[0])
+
+
 # ---------------------------------------------------------------------------
 # BRKGA (Section 4.4)
 # ---------------------------------------------------------------------------
@@ -435,6 +464,12 @@ class MultiBatch:
         _check(lib().vrprpd_multi_autotune(self._h, _stream_ptr(stream), C.byref(cfg)))
         return {"dist_mode": _DIST_NAMES[cfg.dist_mode], "warps_per_block": cfg.warps_per_block}
 
+    def cancel_pending(self):
+        """Withdraw the requests not admitted yet; returns how many."""
+        k = np.zeros(1, np.int32)
+        _check(lib().vrprpd_server_cancel_pending(self._h, k.ctypes.data))
+        return int(k[0])
+
     def close(self):
         if getattr(self, "_h", None) is not None:
             lib().vrprpd_multi_destroy(self._h)
@@ -501,6 +536,12 @@ class Server:
         st = ServerStats()
         _check(lib().vrprpd_server_get_stats(self._h, C.byref(st)))
         return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def cancel_pending(self):
+        """Withdraw the requests not admitted yet; returns how many."""
+        k = np.zeros(1, np.int32)
+        _check(lib().vrprpd_server_cancel_pending(self._h, k.ctypes.data))
+        return int(k[0])
 
     def close(self):
         if getattr(self, "_h", None) is not None:

@@ -63,6 +63,8 @@ def register(L):
     L.vrprpd_alns_run.argtypes = [vp, C.POINTER(Solution), C.POINTER(AlnsParams), C.c_uint64,
                                   C.POINTER(Solution), C.POINTER(Solution), C.POINTER(AlnsStats), vp, vp]
     L.vrprpd_insertion_matrix.argtypes = [vp, vp, vp, C.c_int32, vp, vp, vp]
+    L.vrprpd_repair_then_matrix.argtypes = [vp, vp, vp, vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, vp, vp,
+                                            vp, vp, vp, vp]
     L.vrprpd_multi_create.argtypes = [vp, vp, vp, vp, C.c_int32, C.POINTER(vp)]
     L.vrprpd_multi_evaluate.argtypes = [vp, vp]
     L.vrprpd_multi_autotune.argtypes = [vp, vp, vp]
@@ -78,6 +80,7 @@ def register(L):
     L.vrprpd_server_poll.argtypes = [vp, C.c_int64, C.POINTER(Result), vp, vp]
     L.vrprpd_server_wait.argtypes = [vp, C.c_int64, C.POINTER(Result), vp, vp]
     L.vrprpd_server_get_stats.argtypes = [vp, C.POINTER(ServerStats)]
+    L.vrprpd_server_cancel_pending.argtypes = [vp, vp]
     L.vrprpd_server_destroy.argtypes = [vp]
     L.vrprpd_server_destroy.restype = None
     return L

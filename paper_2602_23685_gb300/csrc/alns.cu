@@ -114,9 +114,11 @@ struct AlnsTeam {
     unsigned* gbar;          // [2] grid barrier over all teams: count, generation
     const AlnsTeam* sib;     // device array of all teams (siblings' best solutions at checkpoints)
     unsigned long long key;  // RNG stream key
-    int mode;                // 0 = search, 1 = one-customer matrix dump, 2 = refine the start solution
+    int mode;                // 0 = search, 1 = one-customer matrix dump, 2 = refine the start solution,
+                             // 3 = dump_steps repair steps, then mode 1 on the first customer left
     int refine_rounds;       // mode 2: local-search rounds at most
     int dump_c;
+    int dump_steps;          // mode 3
     const int* coords;       // device (n+1) x 2 when distances can be recomputed exactly, else null
     // state and scratch (device)
     AlnsCtl* ctl;
@@ -1359,10 +1361,11 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
     unsigned local_entries = 0;
     const unsigned ncols = static_cast<unsigned>(max(0, min(TC / 8, (G - c0 - cb + 7) / 8)));  // this thread's columns < G
     if (dump) {
-        // every entry written out (parity runs): shortcut entries are left to
-        // the shortcut items, excluded pairs read "infeasible"
-        for (int tb = 0; tb < nrem; tb += CB) {
-            const int nb = min(CB, nrem - tb);
+        // every entry of the first customer still to insert written out
+        // (parity runs): shortcut entries are left to the shortcut items,
+        // excluded pairs read "infeasible"
+        for (int tb = 0; tb < min(nrem, 1); tb += CB) {
+            const int nb = 1;
             __syncthreads();
             if (tb > 0) load_batch(tb, nb);
             __syncthreads();
@@ -1521,6 +1524,7 @@ __device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N,
     const int e = item >> 1, as_col = item & 1;
     const int packed = t.slist[e];
     const int ti = packed / G, g = packed - ti * G;
+    if (t.mode == 1 && ti != 0) return;        // a dump writes out the first customer only
     const int c = t.rem[ti];
     const int n = t.n, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int rw = ((n + 1) + 3) & ~3;
@@ -2745,6 +2749,47 @@ __global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, 
         team_barrier(ctl, team_blocks, gen);
         return;
     }
+    if (t.mode == 3) {
+        // repair steps on the partial solution already in W[0] (the search's
+        // own step: prep, incrementally after a non-shortcut insertion, gaps,
+        // shortcut walks, matrix, selection), then the matrix of the first
+        // customer still to insert written out as in mode 1
+        if (!team_barrier(ctl, team_blocks, gen)) return;
+        for (int step = 0; step <= t.dump_steps; ++step) {
+            if (*reinterpret_cast<volatile int*>(&ctl->repair_fail) || *reinterpret_cast<volatile int*>(&ctl->nrem) == 0)
+                return;
+            const bool incr = *reinterpret_cast<volatile int*>(&ctl->incr) != 0;
+            if (rank == 0 && threadIdx.x == 0) {
+                if (incr) ctl->steps_incr += 1; else ctl->steps_full += 1;
+            }
+            phase_prep(t, s, rank, team_blocks, incr);
+            if (incr) {
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int* q = team_s.H; team_s.H = team_s.H2; team_s.H2 = q;
+                    q = team_s.T; team_s.T = team_s.T2; team_s.T2 = q;
+                    q = team_s.Ms; team_s.Ms = team_s.Ms2; team_s.Ms2 = q;
+                }
+                __syncthreads();
+            }
+            if (!team_barrier(ctl, team_blocks, gen)) return;
+            phase_gaps(t, s, rank, team_blocks);
+            team_arrive(ctl, team_blocks, gen);
+            gap_walks(t, s, rank, team_blocks);
+            if (!team_wait(ctl, team_blocks, gen)) return;
+            if (step == t.dump_steps) {
+                __syncthreads();
+                if (threadIdx.x == 0) team_s.mode = 1;
+                __syncthreads();
+                phase_matrix(t, s);
+                team_barrier(ctl, team_blocks, gen);
+                return;
+            }
+            phase_matrix(t, s);
+            if (!team_barrier_select(t, s, team_blocks, gen)) return;
+        }
+        return;
+    }
     // start: W = cur, evaluate
     if (rank == 0) {
         for (int k = threadIdx.x; k < 2 * t.n; k += blockDim.x) t.W_ops[0][k] = t.cur_ops[k];
@@ -3060,10 +3105,20 @@ extern "C" int vrprpd_initial_solution(const vrprpd_instance* I, vrprpd_solution
     return VRPRPD_OK;
 }
 
+// Mode 3 (repair steps, then a matrix dump): the customers to insert, the
+// repair operator, the steps, and where the partial solution goes afterwards.
+struct RepairDump {
+    int steps, op, count;
+    const int32_t* removed;
+    int32_t* out_ops;
+    int32_t* out_off;
+};
+
 static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const vrprpd_alns_params* P,
                     uint64_t seed, int mode, int dump_c, const int32_t* dump_ops, const int32_t* dump_off,
                     vrprpd_solution* best, vrprpd_solution* current, vrprpd_alns_stats* stats, int32_t* trace,
-                    int32_t* dump_delta, int32_t* dump_travel, cudaStream_t stream, int refine_rounds = 0) {
+                    int32_t* dump_delta, int32_t* dump_travel, cudaStream_t stream, int refine_rounds = 0,
+                    const RepairDump* rd = nullptr) {
     std::string why;
     VRP_CHECK(alns_supported(I, &why), VRPRPD_EINVAL, "%s", why.c_str());
     const int n = I->n, m = I->m;
@@ -3081,11 +3136,11 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     VRP_CHECK(P->tau >= 1, VRPRPD_EINVAL, "tau must be >= 1");
     VRP_CHECK(P->ls_pickup_every >= 0 && P->ls_relocate_every >= 0, VRPRPD_EINVAL,
               "local-search periods must be >= 0 (0 = off)");
-    const bool dump = mode == 1;
+    const bool dump = mode == 1 || mode == 3;
     const int R = mode != 0 ? 1 : std::max(1, P->replicas);
     VRP_CHECK(R <= 1024, VRPRPD_EINVAL, "replicas must lie in [0, 1024] (%d)", R);
     VRP_CHECK(P->sync_every >= 0, VRPRPD_EINVAL, "sync_every must be >= 0 (0 = never)");
-    const int qcap = dump ? 1 : alns_row_cap(n, m, qmax, P);
+    const int qcap = mode == 3 ? std::max(1, rd->count) : dump ? 1 : alns_row_cap(n, m, qmax, P);
     DevBuf B;
     const size_t per_team = team_bytes(n, m, qcap, iters, dump);
     B.cap = per_team * R + 4096;
@@ -3127,6 +3182,7 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     t.mode = mode;
     t.refine_rounds = refine_rounds;
     t.dump_c = dump_c;
+    t.dump_steps = mode == 3 ? rd->steps : 0;
     t.nreplicas = R;
     t.sync_every = P->sync_every;
     t.gbar = gbar;
@@ -3144,7 +3200,8 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     for (int i = 0; i < 8; ++i) ctl.wd[i] = 1.0;
     ctl.wr[0] = ctl.wr[1] = ctl.wr[2] = ctl.wr[3] = 1.0;
     if (dump) {
-        ctl.nrem = 1;
+        ctl.nrem = mode == 3 ? rd->count : 1;
+        ctl.rj = mode == 3 ? rd->op : 0;
         ctl.wsel = 0;
     }
     e = cudaMemsetAsync(gbar, 0, 16, stream);
@@ -3169,8 +3226,10 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
         const int Nops = dump_off[m];
         if (e == cudaSuccess) e = cudaMemcpyAsync(ts[0].W_ops[0], dump_ops, std::max(Nops, 1) * 4, cudaMemcpyHostToDevice, stream);
         if (e == cudaSuccess) e = cudaMemcpyAsync(ts[0].W_off[0], dump_off, (m + 1) * 4, cudaMemcpyHostToDevice, stream);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(ts[0].rem, &dump_c, 4, cudaMemcpyHostToDevice, stream);
-        const size_t G = static_cast<size_t>(Nops) + m;
+        if (e == cudaSuccess)
+            e = mode == 3 ? cudaMemcpyAsync(ts[0].rem, rd->removed, rd->count * 4, cudaMemcpyHostToDevice, stream)
+                          : cudaMemcpyAsync(ts[0].rem, &dump_c, 4, cudaMemcpyHostToDevice, stream);
+        const size_t G = static_cast<size_t>(Nops) + (mode == 3 ? 2 * rd->steps : 0) + m;
         if (e == cudaSuccess) e = cudaMemsetAsync(ts[0].dump_delta, 0xff, G * G * 4, stream);
     }
     // recompute distances from staged coordinates only when that costs no resident CTAs
@@ -3227,9 +3286,20 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
     int g = 0;
     for (int r = 1; r < R; ++r)
         if (out[r].z_best < out[g].z_best) g = r;
+    if (mode == 3 && out[0].repair_fail) {
+        set_error("a customer has no feasible insertion during the repair steps");
+        return fail_all(VRPRPD_EINVAL);
+    }
     if (dump) {
-        const size_t G = static_cast<size_t>(dump_off[m]) + m;
+        const int Nout = dump_off[m] + (mode == 3 ? 2 * rd->steps : 0);
+        const size_t G = static_cast<size_t>(Nout) + m;
         e = cudaMemcpyAsync(dump_delta, ts[0].dump_delta, G * G * 4, cudaMemcpyDeviceToHost, stream);
+        if (e == cudaSuccess && mode == 3) {
+            const int w = out[0].wsel;
+            e = cudaMemcpyAsync(rd->out_ops, ts[0].W_ops[w], std::max(Nout, 1) * 4, cudaMemcpyDeviceToHost, stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(rd->out_off, ts[0].W_off[w], (m + 1) * 4, cudaMemcpyDeviceToHost, stream);
+        }
         if (e == cudaSuccess && dump_travel) e = cudaMemcpyAsync(dump_travel, ts[0].dump_travel, G * G * 4, cudaMemcpyDeviceToHost, stream);
     } else {
         if (best) {
@@ -3336,6 +3406,41 @@ extern "C" int vrprpd_alns_run(const vrprpd_instance* I, const vrprpd_solution* 
     VRP_CHECK(I && P && best && best->ops && best->off, VRPRPD_EINVAL, "NULL argument");
     int rc = run_team(I, init, P, seed, 0, 0, nullptr, nullptr, best, current, stats, z_trace, nullptr, nullptr,
                       static_cast<cudaStream_t>(stream));
+    return rc;
+}
+
+extern "C" int vrprpd_repair_then_matrix(const vrprpd_instance* I, const int32_t* ops, const int32_t* off,
+                                         const int32_t* removed, int32_t count, int32_t repair_op, int32_t steps,
+                                         int32_t team_blocks, int32_t* out_ops, int32_t* out_off, int32_t* delta,
+                                         int32_t* travel, int64_t* incremental_steps, void* stream) {
+    VRP_CHECK(I && ops && off && removed && out_ops && out_off && delta, VRPRPD_EINVAL, "NULL argument");
+    const int m = I->m, n = I->n;
+    VRP_CHECK(count >= 1 && count <= 1024, VRPRPD_EINVAL, "count must lie in [1, 1024]");
+    VRP_CHECK(steps >= 0 && steps < count, VRPRPD_EINVAL, "steps must lie in [0, count)");
+    VRP_CHECK(repair_op >= 0 && repair_op <= 3, VRPRPD_EINVAL, "repair_op must lie in [0, 3]");
+    VRP_CHECK(off[0] == 0 && off[m] == 2 * (n - count), VRPRPD_EINVAL, "the partial solution must hold 2(n - count) ops");
+    for (int v = 0; v < m; ++v) VRP_CHECK(off[v + 1] >= off[v], VRPRPD_EINVAL, "offsets decrease");
+    std::vector<char> seen(2 * n + 2, 0);
+    for (int k = 0; k < off[m]; ++k) {
+        const int o = ops[k];
+        VRP_CHECK(o >= 2 && o <= 2 * n + 1 && !seen[o], VRPRPD_EINVAL, "bad or repeated op %d", o);
+        seen[o] = 1;
+    }
+    for (int k = 0; k < count; ++k) {
+        const int c = removed[k];
+        VRP_CHECK(c >= 1 && c <= n && (k == 0 || c > removed[k - 1]), VRPRPD_EINVAL,
+                  "removed customers must be ascending ids in [1, n]");
+        VRP_CHECK(!seen[2 * c] && !seen[2 * c + 1], VRPRPD_EINVAL, "customer %d is in the partial solution", c);
+    }
+    for (int q = 1; q <= n; ++q) VRP_CHECK(seen[2 * q] == seen[2 * q + 1], VRPRPD_EINVAL, "customer %d half present", q);
+    vrprpd_alns_params P;
+    vrprpd_alns_params_default(&P);
+    P.team_blocks = team_blocks;
+    RepairDump rd{steps, repair_op, count, removed, out_ops, out_off};
+    vrprpd_alns_stats st;
+    const int rc = run_team(I, nullptr, &P, 0, 3, 0, ops, off, nullptr, nullptr, &st, nullptr, delta, travel,
+                            static_cast<cudaStream_t>(stream), 0, &rd);
+    if (rc == VRPRPD_OK && incremental_steps) *incremental_steps = st.incremental_steps;
     return rc;
 }
 

@@ -275,7 +275,7 @@ extern "C" int vrprpd_server_get_stats(vrprpd_server* S, vrprpd_server_stats* ou
     int done = 0;
     std::vector<double> lat;
     for (auto& kv : S->reqs)
-        if (kv.second.done) {
+        if (kv.second.done == 1) {
             ++done;
             lat.push_back(kv.second.t_end - kv.second.t_submit);
         }
@@ -294,6 +294,28 @@ extern "C" int vrprpd_server_get_stats(vrprpd_server* S, vrprpd_server_stats* ou
     out->peak_bytes = S->peak_use;
     out->p50_ms = pct(0.50);
     out->p99_ms = pct(0.99);
+    return VRPRPD_OK;
+}
+
+extern "C" int vrprpd_server_cancel_pending(vrprpd_server* S, int32_t* withdrawn) {
+    VRP_CHECK(S, VRPRPD_EINVAL, "NULL server");
+    int32_t k = 0;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        const double t = S->now_ms();
+        for (const int64_t id : S->pending) {
+            auto& q = S->reqs.at(id);
+            q.rc = VRPRPD_EBUSY;
+            q.message = "withdrawn before admission";
+            q.t_start = q.t_end = t;
+            q.done = 2;                        // finished without running: no latency sample
+            ++k;
+        }
+        S->pending.clear();
+    }
+    S->cv_work.notify_all();
+    S->cv_done.notify_all();
+    if (withdrawn) *withdrawn = k;
     return VRPRPD_OK;
 }
 

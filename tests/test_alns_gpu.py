@@ -368,3 +368,145 @@ def test_alns_from_the_paper_start(vrp):
     o = oracle.alns_run(oi, init[0], init[1], oracle.alns_params(30), 4)
     assert np.array_equal(g["trace"], o["trace"]) and g["stats"].z_init == o["stats"].z_init
     assert np.array_equal(g["best_ops"], o["best_ops"])
+
+
+def test_alns_c3_shape_many_ctas(vrp):
+    """The BRKGA workload's instance (n=200, 8 Gaussian clusters, m=6, R=20,
+    Q=6, 5x) searched by a team of 64 CTAs for two iterations, replayed by the
+    oracle: the incremental longest-path updates and the shortcut-gap entries
+    both run (Section 4.2.3)."""
+    cfg = workloads.CONFIGS["brkga_n200"]
+    w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=0)
+    # draw seed 3 removes customers with shortcut gaps in these two iterations
+    _, oi, g, o = run_both(vrp, w, 2, seed=3, q=(5, 5), team_blocks=64)
+    assert g["stats"].team_blocks == 64
+    assert_same_run(oi, g, o)
+    assert g["stats"].incremental_steps > 0 and g["stats"].full_steps > 0
+    assert g["stats"].fallback_entries > 0
+
+
+def _shortcut_gaps(d, ops, off, m, c):
+    """Gaps (x, y) of the partial solution where the rounded legs through c are
+    shorter than x -> y: there the tile formula does not hold and the entries
+    come from the shortcut simulations."""
+    n_sc = 0
+    for v in range(m):
+        r = [0] + [o >> 1 for o in ops[off[v]:off[v + 1]]] + [0]
+        for x, y in zip(r[:-1], r[1:]):
+            n_sc += int(d[x, c]) + int(d[c, y]) < int(d[x, y])
+    return n_sc
+
+
+def test_repair_steps_then_matrix_c3_shortcuts(vrp):
+    """n = 200 clustered (m=6, R=20, Q=6, 5x) on 64 CTAs: removed customers
+    chosen so that shortcut gaps occur; each of four repair steps equals the
+    oracle's and each next matrix equals its full re-simulation."""
+    cfg = workloads.CONFIGS["brkga_n200"]
+    w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=2)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    ops, off = oracle.initial_solution(oi, w.coords)
+    rng = np.random.default_rng(0)
+    for _ in range(500):
+        removed = sorted(rng.choice(np.arange(1, w.n + 1), size=5, replace=False).tolist())
+        po, pf = _partial(ops, off, w.m, removed)
+        if _shortcut_gaps(oi.d, po, pf, w.m, removed[0]) > 0:
+            break
+    else:
+        pytest.fail("no removal with a shortcut gap")
+    seen_sc = 0
+    incr_total = 0
+    for steps in range(4):
+        go, gf, dg, tg, incr = vrp.repair_then_matrix(inst, po, pf, removed, steps, team_blocks=64)
+        oo, of = oracle.repair(oi, 0, po, pf, removed, max_steps=steps)
+        assert np.array_equal(gf, of) and np.array_equal(go, oo), steps
+        left = [c for c in removed if 2 * c not in set(go.tolist())]
+        seen_sc += _shortcut_gaps(oi.d, go, gf, w.m, left[0])
+        md, mt, _ = oracle.insertion_matrix(oi, go, gf, left[0])
+        assert np.array_equal(dg, md), steps
+        ok = md != INT32_MAX
+        assert np.array_equal(tg[ok], mt[ok]), steps
+        incr_total += incr
+    assert seen_sc > 0 and incr_total > 0
+
+
+def _partial(ops, off, m, removed):
+    rem = set(int(c) for c in removed)
+    routes = [[o for o in ops[off[v]:off[v + 1]] if (o >> 1) not in rem] for v in range(m)]
+    po = np.array([o for r in routes for o in r], np.int32)
+    pf = np.zeros(m + 1, np.int32)
+    pf[1:] = np.cumsum([len(r) for r in routes])
+    return po, pf
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_repair_steps_then_matrix_small(vrp, op):
+    """Part of a repair on the device, then the next matrix: the steps equal
+    the oracle's repair steps, and the whole matrix (after incremental
+    longest-path updates) equals the oracle's full re-simulation."""
+    w = workloads.make_instance(40, 4, 10, 5, "2x", seed=8)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    ops, off = oracle.initial_solution(oi, w.coords)
+    removed = sorted(np.random.default_rng(3).choice(np.arange(1, 41), size=6, replace=False).tolist())
+    po, pf = _partial(ops, off, w.m, removed)
+    incr_total = 0
+    for steps in range(0, 6):
+        go, gf, dg, tg, incr = vrp.repair_then_matrix(inst, po, pf, removed, steps, repair_op=op, team_blocks=3)
+        oo, of = oracle.repair(oi, op, po, pf, removed, max_steps=steps)
+        assert np.array_equal(gf, of) and np.array_equal(go, oo), steps
+        left = [c for c in removed if 2 * c not in set(go.tolist())]
+        md, mt, _ = oracle.insertion_matrix(oi, go, gf, left[0])
+        assert np.array_equal(dg, md), steps
+        ok = md != INT32_MAX
+        assert np.array_equal(tg[ok], mt[ok]), steps
+        incr_total += incr
+    assert incr_total > 0
+
+
+def test_repair_steps_then_matrix_n1000(vrp):
+    """At n = 1000 (m=20, R=100, Q=10, 1R20) on the whole GPU: eight greedy
+    steps from the three-phase start with 30 customers removed, most of them
+    incremental, then 400 sampled entries of the next matrix against the
+    oracle's re-simulation of the partial solution the steps produced."""
+    cfg = workloads.CONFIGS["serving_n1000"]
+    w = workloads.make_instance(cfg["n"], cfg["m"], cfg["R"], cfg["Q"], cfg["variant"], cfg["layout"], seed=2)
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    ops, off, _ = vrp.initial_solution_paper(inst, refine_rounds=0)
+    rng = np.random.default_rng(5)
+    removed = sorted(rng.choice(np.arange(1, w.n + 1), size=30, replace=False).tolist())
+    po, pf = _partial(ops, off, w.m, removed)
+    steps = 8
+    go, gf, dg, tg, incr = vrp.repair_then_matrix(inst, po, pf, removed, steps)
+    assert incr >= 5, incr
+    # the steps inserted eight whole customers into the partial solution and moved nothing else
+    present = set(go.tolist())
+    inserted = [c for c in removed if 2 * c in present]
+    assert len(inserted) == steps and all(2 * c + 1 in present for c in inserted)
+    keep = set(inserted)
+    assert np.array_equal(_partial(go, gf, w.m, keep)[0], po)
+    assert oracle.evaluate(oi, go, gf, allow_partial=True)[1] & (oracle.CYCLE | oracle.MALFORMED) == 0
+    c = [x for x in removed if x not in keep][0]
+    z0, _ = oracle.evaluate(oi, go, gf, allow_partial=True)
+    G = dg.shape[0]
+    gaps = [(v, i) for v in range(w.m) for i in range(gf[v + 1] - gf[v] + 1)]
+    for flat in rng.choice(G * G, size=400, replace=False):
+        r, col = divmod(int(flat), G)
+        (a, i), (b, j) = gaps[r], gaps[col]
+        if a == b and j < i:
+            assert dg[r, col] == INT32_MAX
+            continue
+        routes = [list(go[gf[v]:gf[v + 1]]) for v in range(w.m)]
+        if a == b:
+            routes[a] = routes[a][:i] + [2 * c] + routes[a][i:j] + [2 * c + 1] + routes[a][j:]
+        else:
+            routes[a] = routes[a][:i] + [2 * c] + routes[a][i:]
+            routes[b] = routes[b][:j] + [2 * c + 1] + routes[b][j:]
+        so = np.array(sum(routes, []), np.int32)
+        sf = np.zeros(w.m + 1, np.int32)
+        sf[1:] = np.cumsum([len(x) for x in routes])
+        z, st = oracle.evaluate(oi, so, sf, allow_partial=True)
+        cap = any(_route_cap_bad(routes[v], w.Q) for v in {a, b})
+        expect = INT32_MAX if (st & (oracle.CYCLE | oracle.POOL)) or cap else z - z0
+        assert dg[r, col] == expect, (r, col, dg[r, col], expect)

@@ -60,3 +60,26 @@ def test_admission_by_memory(vrp):
     with pytest.raises(vrp.VrpError):
         srv.submit(big, alns_iterations=5)
     srv.close()
+
+
+def test_withdraw_pending(vrp):
+    """A bounded serving window withdraws the requests not admitted yet: they
+    complete at once with EBUSY (-5) and no latency sample, while the admitted
+    one finishes and is re-evaluated by the oracle."""
+    ws = requests()[:5]
+    srv = vrp.Server(mem_budget_bytes=8 << 30, max_active=1)
+    ids = [srv.submit(w, alns_iterations=200, seed=i) for i, w in enumerate(ws)]
+    time.sleep(0.05)
+    k = srv.cancel_pending()
+    res = [srv.wait(r) for r in ids]
+    st = srv.stats()
+    srv.close()
+    ran = [r for r in res if r["status"] == 0]
+    gone = [r for r in res if r["status"] != 0]
+    assert k == len(gone) and k >= 1 and len(ran) >= 1
+    assert all(r["status"] == -5 and "withdrawn" in r["message"] for r in gone)
+    assert st["completed"] == len(ran)
+    for w, r in zip(ws, res):
+        if r["status"] == 0:
+            oi = oracle.OracleInstance.from_workload(w)
+            assert oracle.evaluate(oi, r["ops"], r["off"]) == (r["z_best"], 0)
