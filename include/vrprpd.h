@@ -210,10 +210,26 @@ int vrprpd_sync(const vrprpd_instance* inst, void* stream);
 #define VRPRPD_DIST_GLOBAL16 3 /* uint16 matrix gathered from L2 */
 #define VRPRPD_DIST_GLOBAL32 4 /* int32 matrix gathered from L2 */
 #define VRPRPD_DIST_COORDS 5   /* recomputed exactly from coordinates in shared memory */
+/* How a warp walks its candidates:
+ *   VRPRPD_WALK_STAGED    each warp reads a tile of floor(32/m) candidates
+ *                         with coalesced loads, checks every code (range,
+ *                         duplicates) and keeps them as 16-bit codes in shared
+ *                         memory, then walks them there;
+ *   VRPRPD_WALK_STREAMED  each route's lane reads its own codes from global
+ *                         memory through a register queue while it walks and
+ *                         checks them on the way (a blocked walk gets the full
+ *                         check afterwards); a group of group_warps warps (1
+ *                         or 2) walks floor(32 group_warps / m) candidates, so
+ *                         for m = 20 two warps walk three candidates.  Shared
+ *                         memory holds only the ready times and offsets. */
+#define VRPRPD_WALK_STAGED 0
+#define VRPRPD_WALK_STREAMED 1
 typedef struct {
     int32_t dist_mode;
     int32_t warps_per_block;
     int32_t blocks_per_sm;     /* 0 = as many as fit */
+    int32_t walk;              /* VRPRPD_WALK_STAGED or VRPRPD_WALK_STREAMED */
+    int32_t group_warps;       /* streamed walk: warps per candidate group (1 or 2) */
 } vrprpd_eval_config;
 
 int vrprpd_eval_set_config(vrprpd_instance* inst, const vrprpd_eval_config* cfg);

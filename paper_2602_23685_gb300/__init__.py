@@ -40,7 +40,12 @@ class Batch(C.Structure):
 
 
 class EvalConfig(C.Structure):
-    _fields_ = [("dist_mode", C.c_int32), ("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32)]
+    _fields_ = [("dist_mode", C.c_int32), ("warps_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("walk", C.c_int32), ("group_warps", C.c_int32)]
+
+
+WALKS = {"staged": 0, "streamed": 1}
+_WALK_NAMES = {v: k for k, v in WALKS.items()}
 
 
 def lib():
@@ -159,12 +164,6 @@ class Instance:
         _check(lib().vrprpd_instance_get_dist(self.handle, d.ctypes.data))
         return d
 
-    def cancel_pending(self):
-        """Withdraw the requests not admitted yet; returns how many."""
-        k = np.zeros(1, np.int32)
-        _check(lib().vrprpd_server_cancel_pending(self._h, k.ctypes.data))
-        return int(k[0])
-
     def close(self):
         if getattr(self, "_h", None) is not None:
             lib().vrprpd_instance_destroy(self._h)
@@ -263,25 +262,30 @@ def sync(inst, stream=None):
     _check(lib().vrprpd_sync(inst.handle, _stream_ptr(stream)))
 
 
-def set_eval_config(inst, dist_mode="auto", warps_per_block=0, blocks_per_sm=0):
+def set_eval_config(inst, dist_mode="auto", warps_per_block=0, blocks_per_sm=0, walk="staged", group_warps=1):
     cfg = EvalConfig(DIST_MODES[dist_mode] if isinstance(dist_mode, str) else int(dist_mode),
-                     warps_per_block, blocks_per_sm)
+                     warps_per_block, blocks_per_sm, WALKS[walk] if isinstance(walk, str) else int(walk),
+                     group_warps)
     _check(lib().vrprpd_eval_set_config(inst.handle, C.byref(cfg)))
+
+
+def _cfg_dict(cfg):
+    return {"dist_mode": _DIST_NAMES[cfg.dist_mode], "warps_per_block": cfg.warps_per_block,
+            "blocks_per_sm": cfg.blocks_per_sm, "walk": _WALK_NAMES.get(cfg.walk, cfg.walk),
+            "group_warps": cfg.group_warps}
 
 
 def get_eval_config(inst):
     cfg = EvalConfig()
     _check(lib().vrprpd_eval_get_config(inst.handle, C.byref(cfg)))
-    return {"dist_mode": _DIST_NAMES[cfg.dist_mode], "warps_per_block": cfg.warps_per_block,
-            "blocks_per_sm": cfg.blocks_per_sm}
+    return _cfg_dict(cfg)
 
 
 def autotune(inst, ops, off, stream=None):
     b = _batch(inst, ops, off)
     cfg = EvalConfig()
     _check(lib().vrprpd_autotune(inst.handle, C.byref(b), _stream_ptr(stream), C.byref(cfg)))
-    return {"dist_mode": _DIST_NAMES[cfg.dist_mode], "warps_per_block": cfg.warps_per_block,
-            "blocks_per_sm": cfg.blocks_per_sm}
+    return _cfg_dict(cfg)
 
 
 # ---------------------------------------------------------------------------
@@ -463,12 +467,6 @@ class MultiBatch:
         cfg = EvalConfig()
         _check(lib().vrprpd_multi_autotune(self._h, _stream_ptr(stream), C.byref(cfg)))
         return {"dist_mode": _DIST_NAMES[cfg.dist_mode], "warps_per_block": cfg.warps_per_block}
-
-    def cancel_pending(self):
-        """Withdraw the requests not admitted yet; returns how many."""
-        k = np.zeros(1, np.int32)
-        _check(lib().vrprpd_server_cancel_pending(self._h, k.ctypes.data))
-        return int(k[0])
 
     def close(self):
         if getattr(self, "_h", None) is not None:

@@ -55,6 +55,10 @@ struct EvalArgs {
     int dist_words;
     int a_words, ready_words, seen_words, start_words, off_words, valid_words, warp_words;
     int sw;           // seen words per candidate
+    // streamed form: G warps per group, K candidates per group tile, and the
+    // group region's layout in 32-bit words
+    int G, K;
+    int g_ready, g_off, g_flag, g_prog, g_red, group_words;
 };
 
 template <int DM>
@@ -346,6 +350,319 @@ __global__ void __launch_bounds__(1024) eval_tiles_kernel(EvalArgs a) {
         if (!eval_tile<DM, W16>(a, sh, sp, W, bar, phase, t)) return;
 }
 
+// ---------------------------------------------------------------------------
+// Streamed form.  No staging pass: each lane reads its own route's op codes
+// from global memory through a four-deep register queue (two codes in use,
+// the next two loaded at the top of every step, so their latency overlaps
+// the step), and checks them as it walks.  A group of G warps walks
+// K = floor(32 G / m) candidates at once, lane L of the group taking route
+// L mod m of candidate L / m, so for m that does not divide 32 (m = 20: three
+// candidates per two warps) candidates straddle warps and far fewer lanes
+// idle.  The group meets at a named barrier once per step.  Shared memory
+// holds only the ready times, the offsets and a few words per candidate.
+//
+// Validation without a staging pass.  Offsets are checked first.  Each code
+// is range-checked as it is walked.  A drop must find its customer's ready
+// slot unresolved (a resolved or picked slot means a second drop: MALFORMED);
+// a pickup marks the slot picked (INT32_MIN), so a second pickup of the same
+// customer waits forever.  Slots are written by atomic exchange and the old
+// value must be the one read: two lanes holding the same op in one step
+// cannot both pass.  If every route is walked to its end with no such
+// fault, the candidate is a permutation: the n drops are of distinct
+// customers, each pickup follows its own customer's drop and no customer is
+// picked twice, so the 2n codes hold n drops and n pickups of n distinct
+// customers.  A candidate whose walk blocks (a cycle, or a repeated or
+// missing op) gets the full check (range and a duplicate bitmap) after the
+// walk, which tells MALFORMED from CYCLE.
+// ---------------------------------------------------------------------------
+constexpr int PICKED = static_cast<int>(0x80000000u);   // ready slot of a customer already picked up
+
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+// barrier of the group plus an OR over its threads' predicates
+__device__ __forceinline__ bool named_any(int id, int nthreads, bool pred) {
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"(static_cast<unsigned>(pred)), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+
+// shared-memory ready slots by 32-bit shared address: a volatile load, and an
+// exchange executed only when `on` (else the read value comes back)
+__device__ __forceinline__ int lds_volatile(unsigned addr) {
+    int v;
+    asm volatile("ld.volatile.shared.b32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ int atoms_exch_if(bool on, unsigned addr, int val, int otherwise) {
+    int old = otherwise;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %2, 0;\n\t"
+        "@p atom.shared.exch.b32 %0, [%1], %3;\n\t}"
+        : "+r"(old)
+        : "r"(addr), "r"(static_cast<unsigned>(on)), "r"(val)
+        : "memory");
+    return old;
+}
+
+template <int G>
+__device__ __forceinline__ void group_sync(int id) {
+    if constexpr (G == 1) __syncwarp();
+    else named_sync(id, 32 * G);
+}
+template <int G>
+__device__ __forceinline__ bool group_any(int id, bool pred) {
+    if constexpr (G == 1) {
+        __syncwarp();
+        return __any_sync(FULL_MASK, pred) != 0;
+    } else {
+        return named_any(id, 32 * G, pred);
+    }
+}
+
+template <int DM, bool W16, int G>
+__device__ __forceinline__ void eval_stream_tile(const EvalArgs& a, const int32_t* sh, const int32_t* sp, int32_t* W,
+                                                 int gl, int bar_id, long long t) {
+    constexpr int NT = 32 * G;
+    const int n = a.n, m = a.m, two_n = 2 * n, K = a.K, N1 = n + 1;
+    int32_t* ready = W + a.g_ready;     // K x (n+1): -(p+1) unresolved, T_drop + p, or PICKED
+    int32_t* soff = W + a.g_off;        // K x (m+1)
+    int32_t* flag = W + a.g_flag;       // K: 1 = malformed
+    int32_t* prog = W + a.g_prog;       // K: the last step in which the candidate progressed
+    int32_t* red = W + a.g_red;         // 3 x NT
+    const long long first = t * K;
+    const int kt = static_cast<int>(min(static_cast<long long>(K), a.num - first));
+    const int cand = gl / m, v = gl - cand * m;
+    const bool active = cand < kt;
+
+    // ---- 1. offsets, flags, unresolved ready times ----
+    for (int i = gl; i < kt * (m + 1); i += NT)
+        soff[i] = W16 ? static_cast<int32_t>(__ldg(a.off16 + first * (m + 1) + i)) : __ldg(a.off + first * (m + 1) + i);
+    for (int i = gl; i < kt; i += NT) {
+        flag[i] = 0;
+        prog[i] = -1;
+    }
+    for (int g = 0; g < kt; ++g)
+        for (int c = gl; c <= n; c += NT) ready[g * N1 + c] = -1 - sp[c];
+    group_sync<G>(bar_id);
+    // each lane checks the offsets around its route: off[0] = 0, off[m] = 2n, non-decreasing
+    int pos = 0, end = 0, start = 0;
+    if (active) {
+        const int lo = soff[cand * (m + 1) + v], hi = soff[cand * (m + 1) + v + 1];
+        if (lo < 0 || hi > two_n || lo > hi || (v == 0 && lo != 0) || (v == m - 1 && hi != two_n)) flag[cand] = 1;
+        start = pos = lo;
+        end = hi;
+    }
+    group_sync<G>(bar_id);
+    const bool ok_off = active && flag[cand] == 0;
+
+    // ---- 2. the walk (up to two ops per lane per step) ----
+    const long long cbase = (first + (active ? cand : 0)) * two_n;
+    auto code_at = [&](int q) -> int {
+        return W16 ? static_cast<int>(__ldg(a.ops16 + cbase + q)) : __ldg(a.ops + cbase + q);
+    };
+    // this lane's codes from its current position on, and its candidate's
+    // ready slots as a shared-memory address
+    const int32_t* rp32 = a.ops + cbase + pos;
+    const uint16_t* rp16 = a.ops16 + cbase + pos;
+    const unsigned rdy_addr = smem_u32(ready + (active ? cand : 0) * N1);
+    int dep = 0, s = 0, smin = 0, smax = 0, loc = 0;
+    bool walking = ok_off && pos < end, cyc = false, bad = false;
+    int q0 = walking ? code_at(pos) : 0;
+    int q1 = (walking && pos + 1 < end) ? code_at(pos + 1) : 0;
+    for (int step = 0;; ++step) {
+        int q2 = 0, q3 = 0;
+        if (walking && pos + 2 < end) q2 = W16 ? static_cast<int>(__ldg(rp16 + 2)) : __ldg(rp32 + 2);
+        if (walking && pos + 3 < end) q3 = W16 ? static_cast<int>(__ldg(rp16 + 3)) : __ldg(rp32 + 3);
+        // first op
+        const int o1 = walking ? q0 : 0;
+        const bool in1 = static_cast<unsigned>(o1 - 2) < static_cast<unsigned>(two_n);
+        const int c1 = in1 ? (o1 >> 1) : 0;
+        const bool p1 = (o1 & 1) != 0;
+        int2 pc1 = make_int2(0, 0);
+        int t1;
+        if constexpr (DM == VRPRPD_DIST_COORDS) {
+            const int2 pl = reinterpret_cast<const int2*>(sh)[loc];
+            pc1 = reinterpret_cast<const int2*>(sh)[c1];
+            t1 = euc2d_small(pl.x, pl.y, pc1.x, pc1.y);
+        } else if constexpr (DM == VRPRPD_DIST_SMEM32 || DM == VRPRPD_DIST_SMEM16) {
+            t1 = dist<DM>(a, sh, loc, c1);
+        } else {
+            t1 = walking ? dist<DM>(a, sh, loc, c1) : 0;
+        }
+        const unsigned ad1 = rdy_addr + 4u * static_cast<unsigned>(c1);
+        const int r1 = lds_volatile(ad1);
+        // a drop needs an unresolved slot, -(p+1) in [-2^31 + 1, -1]
+        const bool bad1 = walking && (!in1 || (!p1 && static_cast<unsigned>(r1) <= 0x80000000u));
+        const bool go1 = walking && !bad1 && (!p1 || r1 >= 0);
+        const int a1 = dep + t1;
+        // exchange, not store: two lanes that read the same slot in the same
+        // step (a repeated op) cannot both see it unchanged
+        const int old1 = atoms_exch_if(go1, ad1, p1 ? PICKED : a1 - 1 - r1, r1);
+        const bool race1 = old1 != r1;
+        dep = go1 ? max(a1, p1 ? r1 : 0) : dep;
+        s += go1 ? (p1 ? 1 : -1) : 0;
+        smin = min(smin, s);
+        smax = max(smax, s);
+        pos += go1 ? 1 : 0;
+        loc = go1 ? c1 : loc;
+        // second op, only behind a first one that went
+        const bool try2 = go1 && !race1 && pos < end;
+        const int o2 = try2 ? q1 : 0;
+        const bool in2 = static_cast<unsigned>(o2 - 2) < static_cast<unsigned>(two_n);
+        const int c2 = in2 ? (o2 >> 1) : 0;
+        const bool p2 = (o2 & 1) != 0;
+        int t2;
+        if constexpr (DM == VRPRPD_DIST_COORDS) {
+            const int2 pc2 = reinterpret_cast<const int2*>(sh)[c2];
+            t2 = euc2d_small(pc1.x, pc1.y, pc2.x, pc2.y);
+        } else if constexpr (DM == VRPRPD_DIST_SMEM32 || DM == VRPRPD_DIST_SMEM16) {
+            t2 = dist<DM>(a, sh, c1, c2);
+        } else {
+            t2 = try2 ? dist<DM>(a, sh, c1, c2) : 0;
+        }
+        const unsigned ad2 = rdy_addr + 4u * static_cast<unsigned>(c2);
+        const int r2 = lds_volatile(ad2);
+        const bool bad2 = try2 && (!in2 || (!p2 && static_cast<unsigned>(r2) <= 0x80000000u));
+        const bool go2 = try2 && !bad2 && (!p2 || r2 >= 0);
+        const int a2 = dep + t2;
+        const int old2 = atoms_exch_if(go2, ad2, p2 ? PICKED : a2 - 1 - r2, r2);
+        const bool race2 = old2 != r2;
+        dep = go2 ? max(a2, p2 ? r2 : 0) : dep;
+        s += go2 ? (p2 ? 1 : -1) : 0;
+        smin = min(smin, s);
+        smax = max(smax, s);
+        pos += go2 ? 1 : 0;
+        loc = go2 ? c2 : loc;
+        // the queue and the code pointer move by the ops taken
+        const int took = (go1 ? 1 : 0) + (go2 ? 1 : 0);
+        q0 = go2 ? q2 : (go1 ? q1 : q0);
+        q1 = go2 ? q3 : (go1 ? q2 : q1);
+        rp32 += took;
+        rp16 += took;
+        const bool fault = bad1 || bad2 || race1 || race2;
+        bad = bad || fault;
+        if (go1) prog[cand] = step;
+        const bool cont = walking && !fault && pos < end;
+        // the group's barrier: every ready time and stamp of this step is
+        // visible after it, so a candidate with no progress in a step while
+        // unfinished can never progress again (a cycle, or a repeated or
+        // missing op that the full check below tells apart)
+        const bool any = group_any<G>(bar_id, cont);
+        cyc = cyc || (cont && prog[cand] != step);
+        walking = cont && !cyc;
+        if (!any) break;
+    }
+    if (bad) flag[cand] = 1;
+    if (cyc)                                   // finish the stock prefix of a blocked route
+        for (; pos < end; ++pos) {
+            const int o = code_at(pos);
+            if (o & 1) { ++s; smax = max(smax, s); } else { --s; smin = min(smin, s); }
+        }
+    red[gl] = cyc ? 1 : 0;
+    group_sync<G>(bar_id);
+
+    // ---- 3. full check of the candidates whose walk blocked ----
+    for (int g = 0; g < kt; ++g) {
+        bool blocked = false;
+        for (int j = 0; j < m; ++j) blocked = blocked || red[g * m + j] != 0;
+        if (!blocked || flag[g]) continue;     // uniform over the group
+        uint32_t* seen = reinterpret_cast<uint32_t*>(ready + g * N1);   // the ready times are no longer needed
+        const int sw = (two_n + 2 + 31) / 32;
+        for (int i = gl; i < sw; i += NT) seen[i] = 0u;
+        group_sync<G>(bar_id);
+        const long long gb = (first + g) * two_n;
+        for (int e = gl; e < two_n; e += NT) {
+            const int o = W16 ? static_cast<int>(__ldg(a.ops16 + gb + e)) : __ldg(a.ops + gb + e);
+            bool dup = static_cast<unsigned>(o - 2) >= static_cast<unsigned>(two_n);
+            if (!dup) {
+                const unsigned bit = 1u << (o & 31);
+                dup = (atomicOr(&seen[o >> 5], bit) & bit) != 0u;
+            }
+            if (dup) flag[g] = 1;
+        }
+        group_sync<G>(bar_id);
+    }
+
+    // ---- 4. per-candidate reduction ----
+    int ret = 0, f = 0, pool = 0;
+    if (ok_off) {
+        if (!cyc && end > start) ret = dep + dist<DM>(a, sh, loc, 0);
+        if (a.load_full) {
+            f = (smin < -a.Q || smax > 0) ? VRPRPD_VEH_CAP : 0;
+            pool = a.Q;
+        } else {
+            f = (-smin + smax > a.Q) ? VRPRPD_VEH_CAP : 0;
+            pool = -smin;
+        }
+        if (cyc) f |= VRPRPD_CYCLE;
+    }
+    group_sync<G>(bar_id);                     // the blocked marks above are read
+    red[gl] = ret;
+    red[NT + gl] = f;
+    red[2 * NT + gl] = pool;
+    group_sync<G>(bar_id);
+    if (active && v == 0) {
+        int z = 0, fl = 0;
+        long long pl = 0;
+        for (int j = 0; j < m; ++j) {
+            z = max(z, red[cand * m + j]);
+            fl |= red[NT + cand * m + j];
+            pl += red[2 * NT + cand * m + j];
+        }
+        if (pl > a.R) fl |= VRPRPD_POOL;
+        if (fl & VRPRPD_CYCLE) z = 0x7fffffff;
+        if (flag[cand]) { z = 0x7fffffff; fl = VRPRPD_MALFORMED; }
+        a.z[first + cand] = z;
+        a.st[first + cand] = static_cast<uint32_t>(fl);
+    }
+    group_sync<G>(bar_id);                     // the region is reused by the next tile
+}
+
+template <int DM, bool W16, int G>
+__global__ void __launch_bounds__(1024) eval_stream_kernel(EvalArgs a) {
+    extern __shared__ __align__(16) int32_t smem[];
+    __shared__ __align__(8) uint64_t block_bar;
+    // ---- block-wide staging of the instance (TMA bulk copies) ----
+    int32_t* sh = smem;
+    int32_t* sp = smem + a.dist_words;
+    if (threadIdx.x == 0) {
+        mbar_init(&block_bar, 1);
+        unsigned dist_bytes = 0;
+        if constexpr (DM == VRPRPD_DIST_SMEM32) dist_bytes = ((a.N * a.N * 4) + 15) & ~15;
+        if constexpr (DM == VRPRPD_DIST_SMEM16) dist_bytes = ((a.N * a.N * 2) + 15) & ~15;
+        if constexpr (DM == VRPRPD_DIST_COORDS) dist_bytes = ((a.N * 8) + 15) & ~15;
+        unsigned p_bytes = ((a.N * 4) + 15) & ~15;
+        mbar_arrive_expect_tx(&block_bar, dist_bytes + p_bytes);
+        if constexpr (DM == VRPRPD_DIST_SMEM32) tma_bulk_g2s(sh, a.d32, dist_bytes, &block_bar);
+        if constexpr (DM == VRPRPD_DIST_SMEM16) tma_bulk_g2s(sh, a.d16, dist_bytes, &block_bar);
+        if constexpr (DM == VRPRPD_DIST_COORDS) tma_bulk_g2s(sh, a.coords, dist_bytes, &block_bar);
+        tma_bulk_g2s(sp, a.p, p_bytes, &block_bar);
+    }
+    __syncthreads();
+    if (!mbar_wait_bounded(&block_bar, 0)) {
+        if (threadIdx.x == 0) atomicExch(a.err, DEV_TIMEOUT_TMA);
+        mbar_wait_bounded(&block_bar, 0);
+        return;
+    }
+    const int warp = threadIdx.x >> 5, group = warp / G, gl = threadIdx.x - group * 32 * G;
+    const int ngroups = (blockDim.x >> 5) / G;
+    if (group >= ngroups) return;
+    int32_t* W = smem + a.shared_words + static_cast<long long>(group) * a.group_words;
+    const long long ntiles = (a.num + a.K - 1) / a.K;
+    const long long g0 = static_cast<long long>(blockIdx.x) * ngroups + group;
+    const long long ng = static_cast<long long>(gridDim.x) * ngroups;
+    for (long long t = g0; t < ntiles; t += ng) eval_stream_tile<DM, W16, G>(a, sh, sp, W, gl, 1 + group, t);
+}
+
 // Many instances of uneven size in one persistent launch: tile t of the
 // whole job belongs to the instance whose tile prefix brackets it.  Distances
 // come from each instance's matrix in global memory (L2-resident); p is read
@@ -462,6 +779,8 @@ static int round4(long long w) { return static_cast<int>((w + 3) & ~3ll); }
 struct Plan {
     int dm = 0, warps = 0, blocks = 0;
     bool w16 = false;    // 16-bit op codes and offsets
+    int walk = VRPRPD_WALK_STAGED;
+    int G = 1;           // streamed form: warps per group
     size_t smem = 0;
     EvalArgs args{};
 };
@@ -494,6 +813,34 @@ static bool dist_mode_available(const vrprpd_instance* I, int dm) {
         case VRPRPD_DIST_COORDS: return coords_small(I);
     }
     return false;
+}
+
+static bool make_plan(const vrprpd_instance* I, int dm, int warps, int blocks_per_sm, long long num, Plan* P);
+
+// The streamed form's layout: groups of G warps (for G > 1 at most 15 per
+// block, one named barrier each), K = floor(32 G / m) candidates per group tile.
+static bool make_plan_stream(const vrprpd_instance* I, int dm, int warps, int G, long long num, Plan* P) {
+    if (G != 1 && G != 2) return false;
+    // groups of more than one warp meet at named barriers 1..15
+    if (warps % G != 0 || (G > 1 && warps / G > 15) || 32 * G < I->m) return false;
+    if (!make_plan(I, dm, G, 0, num, P)) return false;        // instance words and shared fields
+    EvalArgs& a = P->args;
+    const long long N1 = I->n + 1;
+    a.G = G;
+    a.K = (32 * G) / I->m;
+    a.g_ready = 0;
+    a.g_off = round4(static_cast<long long>(a.K) * N1);
+    a.g_flag = a.g_off + round4(static_cast<long long>(a.K) * (I->m + 1));
+    a.g_prog = a.g_flag + round4(a.K);
+    a.g_red = a.g_prog + round4(a.K);
+    a.group_words = a.g_red + 3 * 32 * G;
+    const size_t smem = static_cast<size_t>(a.shared_words + static_cast<long long>(warps / G) * a.group_words) * 4;
+    if (smem + 64 > I->smem_optin) return false;
+    P->walk = VRPRPD_WALK_STREAMED;
+    P->G = G;
+    P->warps = warps;
+    P->smem = smem;
+    return true;
 }
 
 // Fill the layout for (dist mode, warps per block); false if it does not fit.
@@ -532,8 +879,21 @@ static bool make_plan(const vrprpd_instance* I, int dm, int warps, int blocks_pe
     if (smem + 64 > I->smem_optin) return false;
     P->dm = dm;
     P->warps = warps;
+    P->walk = VRPRPD_WALK_STAGED;
+    P->G = 1;
     P->smem = smem;
     return true;
+}
+
+template <bool W16, int G>
+static const void* stream_kernel_for(int dm) {
+    switch (dm) {
+        case VRPRPD_DIST_SMEM32: return reinterpret_cast<const void*>(&eval_stream_kernel<VRPRPD_DIST_SMEM32, W16, G>);
+        case VRPRPD_DIST_SMEM16: return reinterpret_cast<const void*>(&eval_stream_kernel<VRPRPD_DIST_SMEM16, W16, G>);
+        case VRPRPD_DIST_GLOBAL16: return reinterpret_cast<const void*>(&eval_stream_kernel<VRPRPD_DIST_GLOBAL16, W16, G>);
+        case VRPRPD_DIST_GLOBAL32: return reinterpret_cast<const void*>(&eval_stream_kernel<VRPRPD_DIST_GLOBAL32, W16, G>);
+        default: return reinterpret_cast<const void*>(&eval_stream_kernel<VRPRPD_DIST_COORDS, W16, G>);
+    }
 }
 
 template <bool W16>
@@ -547,15 +907,26 @@ static const void* kernel_for(int dm) {
     }
 }
 
+static const void* plan_kernel(const Plan* P) {
+    if (P->walk == VRPRPD_WALK_STREAMED) {
+        if (P->G == 2) return P->w16 ? stream_kernel_for<true, 2>(P->dm) : stream_kernel_for<false, 2>(P->dm);
+        return P->w16 ? stream_kernel_for<true, 1>(P->dm) : stream_kernel_for<false, 1>(P->dm);
+    }
+    return P->w16 ? kernel_for<true>(P->dm) : kernel_for<false>(P->dm);
+}
+
 static int finalize_plan(const vrprpd_instance* I, int blocks_per_sm, Plan* P) {
-    const void* fn = P->w16 ? kernel_for<true>(P->dm) : kernel_for<false>(P->dm);
+    const void* fn = plan_kernel(P);
     { int rc_ = ensure_smem_limit(fn); if (rc_) return rc_; }
     int occ = 0;
     VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, P->warps * 32, P->smem));
     VRP_CHECK(occ > 0, VRPRPD_EINVAL, "evaluation layout does not fit on an SM");
     if (blocks_per_sm > 0) occ = std::min(occ, blocks_per_sm);
-    const long long ntiles = (P->args.num + P->args.k - 1) / P->args.k;
-    long long want = (ntiles + P->warps - 1) / P->warps;
+    const bool streamed = P->walk == VRPRPD_WALK_STREAMED;
+    const long long per_tile = streamed ? P->args.K : P->args.k;
+    const long long units = streamed ? P->warps / P->G : P->warps;     // tile workers per block
+    const long long ntiles = (P->args.num + per_tile - 1) / per_tile;
+    long long want = (ntiles + units - 1) / units;
     long long blocks = std::min<long long>(static_cast<long long>(occ) * I->num_sms, want);
     P->blocks = static_cast<int>(std::max<long long>(blocks, 1));
     return VRPRPD_OK;
@@ -567,6 +938,14 @@ static int choose_plan(const vrprpd_instance* I, long long num, Plan* P) {
     const EvalTuning& T = I->tune;
     if (T.dist_mode != VRPRPD_DIST_AUTO && T.warps_per_block > 0) {
         VRP_CHECK(dist_mode_available(I, T.dist_mode), VRPRPD_EINVAL, "configured distance mode unavailable");
+        if (T.walk == VRPRPD_WALK_STREAMED) {
+            const bool w16 = P->w16;
+            VRP_CHECK(make_plan_stream(I, T.dist_mode, T.warps_per_block, T.group_warps, num, P), VRPRPD_EINVAL,
+                      "configured streamed layout does not fit (warps %d, group %d)", T.warps_per_block,
+                      T.group_warps);
+            P->w16 = w16;
+            return finalize_plan(I, T.blocks_per_sm, P);
+        }
         VRP_CHECK(make_plan(I, T.dist_mode, T.warps_per_block, T.blocks_per_sm, num, P), VRPRPD_EINVAL,
                   "configured evaluation layout exceeds shared memory");
         return finalize_plan(I, T.blocks_per_sm, P);
@@ -607,9 +986,32 @@ static void launch_tiles(const Plan& P, const EvalArgs& a, cudaStream_t stream) 
     }
 }
 
+template <bool W16, int G>
+static void launch_stream(const Plan& P, const EvalArgs& a, cudaStream_t stream) {
+    const int th = P.warps * 32;
+    switch (P.dm) {
+        case VRPRPD_DIST_SMEM32: eval_stream_kernel<VRPRPD_DIST_SMEM32, W16, G><<<P.blocks, th, P.smem, stream>>>(a); break;
+        case VRPRPD_DIST_SMEM16: eval_stream_kernel<VRPRPD_DIST_SMEM16, W16, G><<<P.blocks, th, P.smem, stream>>>(a); break;
+        case VRPRPD_DIST_GLOBAL16: eval_stream_kernel<VRPRPD_DIST_GLOBAL16, W16, G><<<P.blocks, th, P.smem, stream>>>(a); break;
+        case VRPRPD_DIST_GLOBAL32: eval_stream_kernel<VRPRPD_DIST_GLOBAL32, W16, G><<<P.blocks, th, P.smem, stream>>>(a); break;
+        default: eval_stream_kernel<VRPRPD_DIST_COORDS, W16, G><<<P.blocks, th, P.smem, stream>>>(a); break;
+    }
+}
+
 static int launch_plan(const Plan& P, cudaStream_t stream) {
-    if (P.w16) launch_tiles<true>(P, P.args, stream);
-    else launch_tiles<false>(P, P.args, stream);
+    if (P.walk == VRPRPD_WALK_STREAMED) {
+        if (P.G == 2) {
+            if (P.w16) launch_stream<true, 2>(P, P.args, stream);
+            else launch_stream<false, 2>(P, P.args, stream);
+        } else {
+            if (P.w16) launch_stream<true, 1>(P, P.args, stream);
+            else launch_stream<false, 1>(P, P.args, stream);
+        }
+    } else if (P.w16) {
+        launch_tiles<true>(P, P.args, stream);
+    } else {
+        launch_tiles<false>(P, P.args, stream);
+    }
     VRP_CUDA(cudaGetLastError());
     return VRPRPD_OK;
 }
@@ -796,12 +1198,22 @@ extern "C" int vrprpd_eval_set_config(vrprpd_instance* I, const vrprpd_eval_conf
     VRP_CHECK(dist_mode_available(I, cfg->dist_mode), VRPRPD_EINVAL, "distance mode %d unavailable here",
               cfg->dist_mode);
     VRP_CHECK(cfg->warps_per_block >= 1 && cfg->warps_per_block <= 32, VRPRPD_EINVAL, "bad warps_per_block");
+    VRP_CHECK(cfg->walk == VRPRPD_WALK_STAGED || cfg->walk == VRPRPD_WALK_STREAMED, VRPRPD_EINVAL, "bad walk %d",
+              cfg->walk);
     Plan P;
-    VRP_CHECK(make_plan(I, cfg->dist_mode, cfg->warps_per_block, cfg->blocks_per_sm, 1, &P), VRPRPD_EINVAL,
-              "layout exceeds shared memory");
+    if (cfg->walk == VRPRPD_WALK_STREAMED) {
+        VRP_CHECK(make_plan_stream(I, cfg->dist_mode, cfg->warps_per_block, cfg->group_warps, 1, &P), VRPRPD_EINVAL,
+                  "streamed layout does not fit (group_warps must be 1 or 2, divide warps_per_block, leave at "
+                  "most 15 groups and cover m lanes)");
+    } else {
+        VRP_CHECK(make_plan(I, cfg->dist_mode, cfg->warps_per_block, cfg->blocks_per_sm, 1, &P), VRPRPD_EINVAL,
+                  "layout exceeds shared memory");
+    }
     I->tune.dist_mode = cfg->dist_mode;
     I->tune.warps_per_block = cfg->warps_per_block;
     I->tune.blocks_per_sm = cfg->blocks_per_sm;
+    I->tune.walk = cfg->walk;
+    I->tune.group_warps = cfg->walk == VRPRPD_WALK_STREAMED ? cfg->group_warps : 1;
     return VRPRPD_OK;
 }
 
@@ -813,6 +1225,8 @@ extern "C" int vrprpd_eval_get_config(const vrprpd_instance* I, vrprpd_eval_conf
     cfg->dist_mode = P.dm;
     cfg->warps_per_block = P.warps;
     cfg->blocks_per_sm = I->tune.blocks_per_sm;
+    cfg->walk = P.walk;
+    cfg->group_warps = P.G;
     return VRPRPD_OK;
 }
 
@@ -835,29 +1249,39 @@ extern "C" int vrprpd_autotune(vrprpd_instance* I, const vrprpd_batch* b, void* 
     const EvalTuning saved = I->tune;
     const int modes[] = {VRPRPD_DIST_SMEM32, VRPRPD_DIST_SMEM16, VRPRPD_DIST_COORDS, VRPRPD_DIST_GLOBAL16,
                          VRPRPD_DIST_GLOBAL32};
+    // the staged walk, then the streamed walk with one- and two-warp groups
+    struct Cand { int walk, dm, warps, bps, G; };
+    std::vector<Cand> cands;
     for (int dm : modes) {
         if (!dist_mode_available(I, dm)) continue;
-        for (int warps : {4, 8, 12, 16, 24, 32}) {
+        for (int warps : {4, 8, 12, 16, 24, 32})
             for (int bps : {0, 1, 2}) {
                 Plan P;
-                if (!make_plan(I, dm, warps, bps, b->num, &P)) continue;
-                I->tune = EvalTuning{dm, warps, bps};
-                float ms_min = 1e30f;
-                for (int rep = 0; rep < 4; ++rep) {
-                    cudaEventRecord(e0, stream);
-                    int rc = evaluate_device(I, b->ops, b->off, b->num, z, st, stream);
-                    cudaEventRecord(e1, stream);
-                    if (rc) break;
-                    cudaEventSynchronize(e1);
-                    float ms = 0;
-                    cudaEventElapsedTime(&ms, e0, e1);
-                    if (rep > 0) ms_min = std::min(ms_min, ms);
-                }
-                if (ms_min < best_ms) {
-                    best_ms = ms_min;
-                    best = I->tune;
-                }
+                if (make_plan(I, dm, warps, bps, b->num, &P)) cands.push_back({VRPRPD_WALK_STAGED, dm, warps, bps, 1});
             }
+        for (int G : {1, 2})
+            for (int warps : {4, 8, 12, 16, 20, 24, 28, 30, 32})
+                for (int bps : {0, 1, 2}) {
+                    Plan P;
+                    if (make_plan_stream(I, dm, warps, G, b->num, &P)) cands.push_back({VRPRPD_WALK_STREAMED, dm, warps, bps, G});
+                }
+    }
+    for (const Cand& cd : cands) {
+        I->tune = EvalTuning{cd.dm, cd.warps, cd.bps, cd.walk, cd.G};
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+            cudaEventRecord(e0, stream);
+            int rc = evaluate_device(I, b->ops, b->off, b->num, z, st, stream);
+            cudaEventRecord(e1, stream);
+            if (rc) break;
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) ms_min = std::min(ms_min, ms);
+        }
+        if (ms_min < best_ms) {
+            best_ms = ms_min;
+            best = I->tune;
         }
     }
     cudaEventDestroy(e0);
@@ -874,6 +1298,8 @@ extern "C" int vrprpd_autotune(vrprpd_instance* I, const vrprpd_batch* b, void* 
         chosen->dist_mode = best.dist_mode;
         chosen->warps_per_block = best.warps_per_block;
         chosen->blocks_per_sm = best.blocks_per_sm;
+        chosen->walk = best.walk;
+        chosen->group_warps = best.group_warps;
     }
     VRP_CUDA(cudaGetLastError());
     return VRPRPD_OK;

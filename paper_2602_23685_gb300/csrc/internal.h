@@ -54,6 +54,8 @@ struct EvalTuning {
     int dist_mode = VRPRPD_DIST_AUTO;
     int warps_per_block = 0;
     int blocks_per_sm = 0;
+    int walk = VRPRPD_WALK_STAGED;
+    int group_warps = 1;
 };
 
 }  // namespace vrp

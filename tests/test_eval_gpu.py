@@ -18,16 +18,22 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).cuda()
 
 
+# each distance mode runs with the staged walk and with the streamed walk in
+# groups of one and of two warps
+WALKS = [("staged", 1), ("streamed", 1), ("streamed", 2)]
+
+
 def run_modes(vrp, inst, ops, off, modes=MODES):
     results = {}
     for mode in modes:
-        try:
-            vrp.set_eval_config(inst, mode, 8)
-        except vrp.VrpError:
-            continue
-        z, st = vrp.evaluate(inst, dev(ops), dev(off))
-        vrp.sync(inst)
-        results[mode] = (z.cpu().numpy(), st.cpu().numpy().astype(np.uint32))
+        for walk, gw in WALKS:
+            try:
+                vrp.set_eval_config(inst, mode, 8, walk=walk, group_warps=gw)
+            except vrp.VrpError:
+                continue
+            z, st = vrp.evaluate(inst, dev(ops), dev(off))
+            vrp.sync(inst)
+            results[f"{mode}/{walk}{gw}"] = (z.cpu().numpy(), st.cpu().numpy().astype(np.uint32))
     vrp.set_eval_config(inst, "auto")
     return results
 
@@ -288,10 +294,19 @@ def test_n1000_full_size_sampled(vrp, seed):
     ops, off = workloads.precedence_candidates(w.n, w.m, 4096, seed=seed)
     idx = np.arange(0, 4096, 8)
     zo, so = oracle.evaluate_batch(oi, ops[idx], off[idx], threads=8)
-    for mode in ["coords", "global16", "global32", "auto"]:
-        vrp.set_eval_config(inst, mode, 4 if mode != "auto" else 0)
+    shapes = [("coords", 4, "staged", 1), ("global16", 4, "staged", 1), ("global32", 4, "staged", 1),
+              ("coords", 30, "streamed", 2), ("coords", 16, "streamed", 1), ("global16", 8, "streamed", 2),
+              ("auto", 0, "staged", 1)]
+    for mode, warps, walk, gw in shapes:
+        vrp.set_eval_config(inst, mode, warps, walk=walk, group_warps=gw)
         z, st = vrp.evaluate(inst, dev(ops), dev(off))
         vrp.sync(inst)
-        assert np.array_equal(z.cpu().numpy()[idx], zo), mode
-        assert np.array_equal(st.cpu().numpy().astype(np.uint32)[idx], so), mode
+        assert np.array_equal(z.cpu().numpy()[idx], zo), (mode, walk, gw)
+        assert np.array_equal(st.cpu().numpy().astype(np.uint32)[idx], so), (mode, walk, gw)
+    # the shape the autotuner picks (the one the benchmark times)
+    cfg = vrp.autotune(inst, dev(ops), dev(off))
+    z, st = vrp.evaluate(inst, dev(ops), dev(off))
+    vrp.sync(inst)
+    assert np.array_equal(z.cpu().numpy()[idx], zo), cfg
+    assert np.array_equal(st.cpu().numpy().astype(np.uint32)[idx], so), cfg
     vrp.set_eval_config(inst, "auto")
