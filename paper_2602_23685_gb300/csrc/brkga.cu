@@ -44,6 +44,7 @@ struct DecArgs {
     const int32_t* d32;
     const int32_t* p;
     int smem_dist;       // 1 = distance matrix staged in shared memory as int32, 2 = as uint16
+    int pack;            // every schedule time is below 2^22: SelectVehicle is one 32-bit reduction
     const uint16_t* d16; // the 16-bit copy (max d < 65536) or null
     int32_t* ops;
     int32_t* off;
@@ -59,9 +60,10 @@ __host__ __device__ inline int pow2_at_least(int x) {
 }
 
 __host__ __device__ inline size_t dec_warp_words(int n, int P) {
-    // sort buffer (u64) + tdrop + sched bitmap + per-op (vehicle<<16 | seq)
+    // sort buffer (u64) + tdrop + sched bitmap + per-op (vehicle<<16 | seq) +
+    // per-op hinted vehicle (bytes)
     return static_cast<size_t>(2 * P) + (((n + 1) + 3) & ~3) + ((((2 * n + 2 + 31) / 32) + 3) & ~3) +
-           (((2 * n) + 3) & ~3);
+           (((2 * n) + 3) & ~3) + ((((2 * n + 3) / 4) + 3) & ~3);
 }
 
 // The vehicle an assignment hint names: floor(m * alpha) in fp64 (exact for a
@@ -73,7 +75,7 @@ __host__ __device__ inline int hint_vehicle(float alpha, int m) {
     return h < 0 ? 0 : h;
 }
 
-__global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
+__global__ void __launch_bounds__(DEC_WARPS * 32, 1) decode_kernel(DecArgs a) {
     extern __shared__ __align__(16) int smem_dec[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = a.n, m = a.m, two_n = 2 * n, N1 = n + 1;
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
     int* tdrop = wbase + 2 * a.P;
     unsigned* sched = reinterpret_cast<unsigned*>(tdrop + (((n + 1) + 3) & ~3));
     int* vs = reinterpret_cast<int*>(sched + ((((two_n + 2 + 31) / 32) + 3) & ~3));
+    unsigned char* hv = reinterpret_cast<unsigned char*>(vs + ((two_n + 3) & ~3));
     __syncthreads();
     const float* keys = a.keys;
     if (a.keys2 != nullptr && a.ctl->sel == 1) keys = a.keys2;
@@ -112,6 +115,8 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
         for (int i = lane; i <= n; i += 32) tdrop[i] = 0;
         for (int i = lane; i < (two_n + 2 + 31) / 32; i += 32) sched[i] = 0u;
         for (int i = lane; i < two_n; i += 32) vs[i] = -1;
+        if (a.layout == VRPRPD_LAYOUT_HINTS)
+            for (int i = lane; i < two_n; i += 32) hv[i] = static_cast<unsigned char>(hint_vehicle(kk[two_n + i], m));
         __syncwarp();
         for (int size = 2; size <= a.P; size <<= 1) {
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
@@ -139,12 +144,20 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
         int len = two_n;                       // sb[0, len): ops not scheduled yet, priority order
         for (int pass = 0; pass < two_n && done < two_n; ++pass) {
             bool progress = false;
+            unsigned long long e_next = len > 0 ? sb[0] : 0ull;
             for (int k = 0; k < len; ++k) {
-                const int oi = static_cast<int>(sb[k] & 0xffffffffu);
+                // the next op's entry is read ahead: the order does not change
+                // within a pass, so its latency overlaps this op
+                const unsigned long long e_cur = e_next;
+                if (k + 1 < len) e_next = sb[k + 1];
+                const int oi = static_cast<int>(e_cur & 0xffffffffu);
                 const int o = oi + 2, c = o >> 1;
                 const bool pick = (o & 1) != 0;
-                if ((sched[o >> 5] >> (o & 31)) & 1u) continue;
+                const unsigned wo = sched[o >> 5];
+                if ((wo >> (o & 31)) & 1u) continue;
                 if (pick && !((sched[(2 * c) >> 5] >> ((2 * c) & 31)) & 1u)) continue;
+                // the time a pickup waits for, read before the selection
+                const int ready = pick ? tdrop[c] + sp[c] : 0;
                 bool ok = false;
                 if (lane < m) {
                     if (!pick) {
@@ -158,33 +171,51 @@ __global__ void __launch_bounds__(DEC_WARPS * 32) decode_kernel(DecArgs a) {
                     }
                 }
                 const int arr = ok ? tv + dist(locv, c) : 0;
-                const int tie = hints ? (lane - hint_vehicle(kk[two_n + oi], m) + m) % m : rank;
-                // SelectVehicle: least arrival, then tie rank, then lane -- two warp reductions
-                const unsigned ua = ok ? static_cast<unsigned>(arr) : 0xffffffffu;
-                const unsigned amin = __reduce_min_sync(FULL_MASK, ua);
-                if (amin == 0xffffffffu) continue;
-                const unsigned sub = (ok && ua == amin) ? ((static_cast<unsigned>(tie) << 5) | static_cast<unsigned>(lane))
-                                                        : 0xffffffffu;
-                const int win = static_cast<int>(__reduce_min_sync(FULL_MASK, sub) & 31u);
-                int dsum = 0;
-                if (lane == win) {
-                    if (!pick) {
-                        tv = arr;
-                        tdrop[c] = arr;
-                        --net;
-                        nmin = min(nmin, net);
-                        dsum = -nmin - load;
-                        load = -nmin;
-                    } else {
-                        tv = max(arr, tdrop[c] + sp[c]);
-                        ++net;
-                        nmax = max(nmax, net);
-                    }
+                int tie = rank;
+                if (hints) {                       // cyclic distance from the hinted vehicle
+                    tie = lane - static_cast<int>(hv[oi]);
+                    tie += tie < 0 ? m : 0;
+                }
+                // SelectVehicle: least arrival, then tie rank, then lane.  With
+                // every time below 2^22 the three fit one 32-bit key and one warp
+                // reduction; otherwise two reductions
+                int win;
+                if (a.pack) {
+                    const unsigned key = ok ? ((static_cast<unsigned>(arr) << 10) | (static_cast<unsigned>(tie) << 5) |
+                                               static_cast<unsigned>(lane))
+                                            : 0xffffffffu;
+                    const unsigned kmin = __reduce_min_sync(FULL_MASK, key);
+                    if (kmin == 0xffffffffu) continue;
+                    win = static_cast<int>(kmin & 31u);
+                } else {
+                    const unsigned ua = ok ? static_cast<unsigned>(arr) : 0xffffffffu;
+                    const unsigned amin = __reduce_min_sync(FULL_MASK, ua);
+                    if (amin == 0xffffffffu) continue;
+                    const unsigned sub = (ok && ua == amin)
+                                             ? ((static_cast<unsigned>(tie) << 5) | static_cast<unsigned>(lane))
+                                             : 0xffffffffu;
+                    win = static_cast<int>(__reduce_min_sync(FULL_MASK, sub) & 31u);
+                }
+                // the winner's update, by selects rather than a branch: a drop
+                // sets its arrival and lowers the net stock (the start load may
+                // grow), a pickup waits for its ready time and raises it
+                const bool me = lane == win;
+                const int nnet = net + (pick ? 1 : -1);
+                const int nnmin = min(nmin, nnet), nnmax = max(nmax, nnet);
+                const int nload = pick ? load : -nnmin;
+                const int dsum = (me && !pick) ? nload - load : 0;
+                if (me) {
+                    tv = pick ? max(arr, ready) : arr;
+                    net = nnet;
+                    nmin = nnmin;
+                    nmax = nnmax;
+                    load = nload;
                     locv = c;
                     vs[oi] = (lane << 16) | cnt;
-                    ++cnt;
-                    sched[o >> 5] |= 1u << (o & 31);
+                    sched[o >> 5] = wo | (1u << (o & 31));
+                    if (!pick) tdrop[c] = arr;
                 }
+                cnt += me ? 1 : 0;
                 sum_load += __shfl_sync(FULL_MASK, dsum, win);
                 __syncwarp();
                 progress = true;
@@ -533,6 +564,10 @@ static DecArgs dec_args(const vrprpd_instance* I, const DecPlan& D, int num, int
     a.p = I->p;
     a.smem_dist = D.smem_dist;
     a.d16 = I->d16;
+    // a decoded schedule is a precedence graph of the instance's ops, so no
+    // time exceeds (2n+1) max d + n max p
+    const long long bound = (2ll * I->n + 1) * I->maxd + static_cast<long long>(I->n) * I->maxp;
+    a.pack = bound < (1ll << 22) && I->m <= 32 ? 1 : 0;
     return a;
 }
 
