@@ -31,10 +31,10 @@ import workloads  # noqa: E402
 
 N_CUST, M_VEH, R_POOL, Q_CAP = 1000, 20, 100, 10
 BASE_CANDS = 16384          # generated on the host, tiled on the device
-# DRAM bytes (read + write) per candidate of eval_tiles_kernel, from one ncu
-# capture of 16384 candidates of this workload; a full launch moves the same
-# bytes per candidate (the traffic grows in proportion)
-TRAFFIC_PER_EVAL = 8307
+# DRAM bytes (read + write) per candidate of each batched kernel, from one ncu
+# capture of 16384 candidates of this workload per kernel; a full launch moves
+# the same bytes per candidate (the traffic grows in proportion)
+TRAFFIC_PER_EVAL = {"eval_tiles_kernel": 8307, "eval_stream_kernel": 8308}
 ALNS_OPS_PER_ENTRY = 8
 TRAFFIC_SOURCE = "ncu dram__bytes_read+write of a 16384-candidate launch, scaled by candidates per launch"
 TILE = 32                   # batch = BASE_CANDS * TILE = 524288 candidates
@@ -209,6 +209,9 @@ def run_profile(args):
     import paper_2602_23685_gb300 as vrp
     w, ops_h, off_h = make_inputs(seed=0)
     inst = vrp.Instance.from_workload(w)
+    if args.profile_walk == "streamed":
+        # the shape the autotuner picks for the full batch: two-warp groups of the streamed walk
+        vrp.set_eval_config(inst, "coords", 24, walk="streamed", group_warps=2)
     ops = torch.from_numpy(ops_h).cuda()
     off = torch.from_numpy(off_h).cuda()
     for _ in range(args.warmup):
@@ -590,7 +593,9 @@ def main():
     ap.add_argument("--profile-alns-n1000", action="store_true",
                     help="small ALNS case for ncu on the n=1000 workload: 2 iterations per launch")
     ap.add_argument("--profile", action="store_true",
-                    help="small case for ncu: 16384 candidates (132 MB), default kernel shape, no tuning")
+                    help="small case for ncu: 16384 candidates (132 MB), no tuning")
+    ap.add_argument("--profile-walk", default="staged", choices=["staged", "streamed"],
+                    help="--profile: the default staged shape, or the streamed two-warp-group shape")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -774,11 +779,12 @@ def main():
     bytes_per_eval = 4 * (2 * N_CUST + M_VEH + 1) + 8
     achieved = B * bytes_per_eval / (kernel_ms / 1000.0) / 1e9
     peak = pk["hbm_gbs"] if pk else 6800.0
+    kernel = "eval_stream_kernel" if tuned.get("walk") == "streamed" else "eval_tiles_kernel"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": "measured" if pk else "fallback",
                 "bytes_per_unit": bytes_per_eval, "units_per_launch": B,
-                "traffic": TRAFFIC_PER_EVAL * B, "traffic_source": TRAFFIC_SOURCE,
-                "kernel": "eval_tiles_kernel", "kernel_ms": kernel_ms}
+                "traffic": TRAFFIC_PER_EVAL[kernel] * B, "traffic_source": TRAFFIC_SOURCE,
+                "kernel": kernel, "kernel_ms": kernel_ms}
 
     if rank == 0:
         line = {

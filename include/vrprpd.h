@@ -108,8 +108,9 @@ int vrprpd_evaluate(const vrprpd_instance* inst, const vrprpd_batch* batch, int3
 
 /* Same result as vrprpd_evaluate from HOST buffers (ops/off/makespan/status
  * all host pointers), returning when done.  Pinned (page-locked) ops and off
- * are read by the kernel in place over the host link; pageable ones are copied
- * to the device first.  Results are copied back. */
+ * are read by the kernel in place over the host link, always by the staged
+ * walk (its coalesced reads; the best staged shape vrprpd_autotune saw);
+ * pageable ones are copied to the device first.  Results are copied back. */
 int vrprpd_evaluate_host(const vrprpd_instance* inst, const vrprpd_batch* host_batch,
                          int32_t* makespan_host, uint32_t* status_host, void* stream);
 

@@ -22,7 +22,7 @@
 namespace vrp {
 
 int evaluate_device(const vrprpd_instance* I, const int32_t* ops, const int32_t* off, long long num, int32_t* z,
-                    uint32_t* st, cudaStream_t stream);
+                    uint32_t* st, cudaStream_t stream, bool host_mapped = false);
 bool batched_supported(const vrprpd_instance* I);
 
 constexpr int DEC_WARPS = 4;

@@ -934,8 +934,12 @@ static int finalize_plan(const vrprpd_instance* I, int blocks_per_sm, Plan* P) {
 
 // Default shape: shared-memory distances when they leave room for 8 warps,
 // else recomputed coordinates, else L2 gathers.
-static int choose_plan(const vrprpd_instance* I, long long num, Plan* P) {
-    const EvalTuning& T = I->tune;
+// host_mapped: the candidates are read in place from pinned host memory over
+// the host link, where only the staged walk's coalesced reads are fast; the
+// best staged shape the autotuner saw is used then (else the default order).
+static int choose_plan(const vrprpd_instance* I, long long num, Plan* P, bool host_mapped = false) {
+    EvalTuning T = I->tune;
+    if (host_mapped && T.walk != VRPRPD_WALK_STAGED) T = I->tune_staged;
     if (T.dist_mode != VRPRPD_DIST_AUTO && T.warps_per_block > 0) {
         VRP_CHECK(dist_mode_available(I, T.dist_mode), VRPRPD_EINVAL, "configured distance mode unavailable");
         if (T.walk == VRPRPD_WALK_STREAMED) {
@@ -1026,14 +1030,14 @@ static int check_batch(const vrprpd_instance* I, const vrprpd_batch* b, const vo
 }
 
 int evaluate_device(const vrprpd_instance* I, const int32_t* ops, const int32_t* off, long long num,
-                    int32_t* z, uint32_t* st, cudaStream_t stream) {
+                    int32_t* z, uint32_t* st, cudaStream_t stream, bool host_mapped = false) {
     if (num == 0) return VRPRPD_OK;
     if (!batched_supported(I)) {
         set_error("batched evaluation needs m <= 32, 2n+1 < 4096 and max d < 2^19 (use the plain form)");
         return VRPRPD_EINVAL;
     }
     Plan P;
-    int rc = choose_plan(I, num, &P);
+    int rc = choose_plan(I, num, &P, host_mapped);
     if (rc) return rc;
     P.args.ops = ops;
     P.args.off = off;
@@ -1044,7 +1048,7 @@ int evaluate_device(const vrprpd_instance* I, const int32_t* ops, const int32_t*
 
 // The same evaluation from 16-bit op codes and offsets.
 static int evaluate_device16(const vrprpd_instance* I, const uint16_t* ops, const uint16_t* off, long long num,
-                             int32_t* z, uint32_t* st, cudaStream_t stream) {
+                             int32_t* z, uint32_t* st, cudaStream_t stream, bool host_mapped = false) {
     if (num == 0) return VRPRPD_OK;
     if (!batched_supported(I)) {
         set_error("batched evaluation needs m <= 32, 2n+1 < 4096 and max d < 2^19 (use the plain form)");
@@ -1052,7 +1056,7 @@ static int evaluate_device16(const vrprpd_instance* I, const uint16_t* ops, cons
     }
     Plan P;
     P.w16 = true;
-    int rc = choose_plan(I, num, &P);
+    int rc = choose_plan(I, num, &P, host_mapped);
     if (rc) return rc;
     P.args.ops16 = ops;
     P.args.off16 = off;
@@ -1077,11 +1081,11 @@ static int check_batch16(const vrprpd_instance* I, const vrprpd_batch16* b, cons
 static int evaluate_host_impl(vrprpd_instance* I, const void* ops, const void* off, int esz, long long num,
                               int32_t* z_host, uint32_t* st_host, cudaStream_t stream) {
     if (num == 0) return VRPRPD_OK;
-    auto run = [&](const void* o, const void* f, int32_t* dz, uint32_t* dst) {
+    auto run = [&](const void* o, const void* f, int32_t* dz, uint32_t* dst, bool mapped) {
         return esz == 2 ? evaluate_device16(I, static_cast<const uint16_t*>(o), static_cast<const uint16_t*>(f), num,
-                                            dz, dst, stream)
+                                            dz, dst, stream, mapped)
                         : evaluate_device(I, static_cast<const int32_t*>(o), static_cast<const int32_t*>(f), num, dz,
-                                          dst, stream);
+                                          dst, stream, mapped);
     };
     auto grow = [&](size_t need) -> int {
         if (need > I->stage_bytes) {
@@ -1111,7 +1115,7 @@ static int evaluate_host_impl(vrprpd_instance* I, const void* ops, const void* o
     if (ops_dev && off_dev) {
         if ((rc = grow(2 * res_b))) return rc;
         d_z = reinterpret_cast<int32_t*>(I->stage);
-        rc = run(ops_dev, off_dev, d_z, reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(d_z) + res_b));
+        rc = run(ops_dev, off_dev, d_z, reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(d_z) + res_b), true);
     } else {
         const size_t ops_r = (ops_b + 255) & ~static_cast<size_t>(255), off_r = (off_b + 255) & ~static_cast<size_t>(255);
         if ((rc = grow(ops_r + off_r + 2 * res_b))) return rc;
@@ -1119,7 +1123,7 @@ static int evaluate_host_impl(vrprpd_instance* I, const void* ops, const void* o
         VRP_CUDA(cudaMemcpyAsync(base, ops, ops_b, cudaMemcpyHostToDevice, stream));
         VRP_CUDA(cudaMemcpyAsync(base + ops_r, off, off_b, cudaMemcpyHostToDevice, stream));
         d_z = reinterpret_cast<int32_t*>(base + ops_r + off_r);
-        rc = run(base, base + ops_r, d_z, reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(d_z) + res_b));
+        rc = run(base, base + ops_r, d_z, reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(d_z) + res_b), false);
     }
     if (rc) return rc;
     VRP_CUDA(cudaMemcpyAsync(z_host, d_z, num * 4, cudaMemcpyDeviceToHost, stream));
@@ -1191,6 +1195,7 @@ extern "C" int vrprpd_eval_set_config(vrprpd_instance* I, const vrprpd_eval_conf
     VRP_CHECK(I && cfg, VRPRPD_EINVAL, "NULL argument");
     if (cfg->dist_mode == VRPRPD_DIST_AUTO) {
         I->tune = EvalTuning{};
+        I->tune_staged = EvalTuning{};
         return VRPRPD_OK;
     }
     VRP_CHECK(cfg->dist_mode >= VRPRPD_DIST_SMEM32 && cfg->dist_mode <= VRPRPD_DIST_COORDS, VRPRPD_EINVAL,
@@ -1244,8 +1249,8 @@ extern "C" int vrprpd_autotune(vrprpd_instance* I, const vrprpd_batch* b, void* 
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    float best_ms = 1e30f;
-    EvalTuning best{};
+    float best_ms = 1e30f, best_staged_ms = 1e30f;
+    EvalTuning best{}, best_staged{};
     const EvalTuning saved = I->tune;
     const int modes[] = {VRPRPD_DIST_SMEM32, VRPRPD_DIST_SMEM16, VRPRPD_DIST_COORDS, VRPRPD_DIST_GLOBAL16,
                          VRPRPD_DIST_GLOBAL32};
@@ -1283,6 +1288,10 @@ extern "C" int vrprpd_autotune(vrprpd_instance* I, const vrprpd_batch* b, void* 
             best_ms = ms_min;
             best = I->tune;
         }
+        if (cd.walk == VRPRPD_WALK_STAGED && ms_min < best_staged_ms) {
+            best_staged_ms = ms_min;
+            best_staged = I->tune;
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -1294,6 +1303,7 @@ extern "C" int vrprpd_autotune(vrprpd_instance* I, const vrprpd_batch* b, void* 
         return VRPRPD_EINVAL;
     }
     I->tune = best;
+    I->tune_staged = best_staged;
     if (chosen) {
         chosen->dist_mode = best.dist_mode;
         chosen->warps_per_block = best.warps_per_block;

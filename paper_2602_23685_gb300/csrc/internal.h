@@ -84,4 +84,5 @@ struct vrprpd_instance {
     int32_t* stage = nullptr;
     size_t stage_bytes = 0;
     vrp::EvalTuning tune;
+    vrp::EvalTuning tune_staged;   // the best staged-walk shape the autotuner saw (host-mapped candidates)
 };
