@@ -2974,6 +2974,19 @@ int alns_row_cap(int n, int m, int qmax, const vrprpd_alns_params* P) {
     return std::max(cap, 1);
 }
 
+// ALNS CTAs one SM holds for an instance of n customers and m vehicles (its
+// shared memory with staged coordinates, the larger layout); 0 if none fits.
+int alns_blocks_per_sm(int n, int m) {
+    if (ensure_smem_limit(reinterpret_cast<const void*>(&alns_kernel))) return 0;
+    int occ = 0;
+    const size_t smem = alns_smem_words(n, m, true) * 4;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, alns_kernel, ALNS_THREADS, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return occ;
+}
+
 size_t alns_device_bytes(int n, int m, int qmax, const vrprpd_alns_params* P, int iterations) {
     const size_t R = static_cast<size_t>(std::max(1, P->replicas));
     return R * (team_bytes(n, m, alns_row_cap(n, m, qmax, P), iterations, false) + sizeof(AlnsTeam)) + 8192;

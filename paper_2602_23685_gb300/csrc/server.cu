@@ -21,6 +21,7 @@
 
 namespace vrp {
 size_t alns_device_bytes(int n, int m, int qmax, const vrprpd_alns_params* P, int iterations);
+int alns_blocks_per_sm(int n, int m);
 }  // namespace vrp
 
 struct vrprpd_server {
@@ -30,6 +31,7 @@ struct vrprpd_server {
         std::vector<int32_t> coords, p;
         size_t need = 0;
         int ctas = 0;
+        double sm_share = 0;   // SMs' worth of resident ALNS CTAs this request holds: ctas / (CTAs per SM at its n)
         double t_submit = 0, t_start = 0, t_end = 0;
         int done = 0;
         int rc = VRPRPD_OK;
@@ -42,7 +44,8 @@ struct vrprpd_server {
     int device = 0;
     size_t budget = 0, in_use = 0, peak_use = 0;
     int max_active = 1, active = 0, peak_active = 0;
-    int cta_capacity = 0, ctas_in_use = 0;
+    int sms = 0;
+    double sm_in_use = 0;      // sum of the running requests' sm_share, at most sms
     int64_t next_id = 1;
     bool stopping = false;
     std::deque<int64_t> pending;
@@ -146,7 +149,7 @@ static void worker_main(vrprpd_server* S) {
                 if (S->stopping && S->pending.empty()) return true;
                 if (S->pending.empty()) return false;
                 const auto& q = S->reqs[S->pending.front()];
-                return S->in_use + q.need <= S->budget && S->ctas_in_use + q.ctas <= S->cta_capacity;
+                return S->in_use + q.need <= S->budget && S->sm_in_use + q.sm_share <= S->sms + 1e-9;
             });
             if (S->pending.empty()) break;
             id = S->pending.front();
@@ -154,7 +157,7 @@ static void worker_main(vrprpd_server* S) {
             qp = &S->reqs.at(id);
             auto& q = *qp;
             S->in_use += q.need;
-            S->ctas_in_use += q.ctas;
+            S->sm_in_use += q.sm_share;
             S->active += 1;
             S->peak_active = std::max(S->peak_active, S->active);
             S->peak_use = std::max(S->peak_use, S->in_use);
@@ -168,7 +171,7 @@ static void worker_main(vrprpd_server* S) {
             q.t_end = S->now_ms();
             q.done = 1;
             S->in_use -= q.need;
-            S->ctas_in_use -= q.ctas;
+            S->sm_in_use -= q.sm_share;
             S->active -= 1;
         }
         S->cv_work.notify_all();
@@ -187,7 +190,7 @@ extern "C" int vrprpd_server_create(size_t mem_budget, int32_t max_active, vrprp
     VRP_CUDA(cudaGetDevice(&S->device));
     int sms = 0;
     VRP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, S->device));
-    S->cta_capacity = sms;       // one ALNS CTA (256 threads, ~72 KB) per SM is always resident
+    S->sms = sms;
     S->budget = mem_budget;
     S->max_active = max_active;
     S->t0 = std::chrono::steady_clock::now();
@@ -209,11 +212,16 @@ extern "C" int vrprpd_server_submit(vrprpd_server* S, const vrprpd_request* r, i
     q.r.coords = nullptr;
     q.r.p = nullptr;
     q.need = request_bytes(*r);
-    // ALNS team size: what the instance would take alone, capped by a fair share
+    // ALNS team size: what the instance would take alone, capped by a fair
+    // share of the GPU's resident ALNS CTAs at this n (every CTA of a team is
+    // resident at once: a cooperative launch)
     const long long G = 2ll * r->n + r->m;
-    const long long tiles = ((G + 31) / 32) * ((G + 127) / 128);
-    int share = std::max(1, S->cta_capacity / S->max_active);
+    const long long tiles = ((G + 31) / 32) * ((G + 63) / 64);
+    const int occ = alns_blocks_per_sm(r->n, r->m);
+    VRP_CHECK(occ >= 1, VRPRPD_EINVAL, "an ALNS block of n=%d does not fit on an SM", r->n);
+    const int share = std::max(1, occ * S->sms / S->max_active);
     q.ctas = (G < 64) ? 1 : static_cast<int>(std::max<long long>(1, std::min<long long>(tiles, share)));
+    q.sm_share = static_cast<double>(q.ctas) / occ;
     {
         std::lock_guard<std::mutex> lock(S->mu);
         if (S->stopping) { set_error("server is shutting down"); return VRPRPD_EBUSY; }
