@@ -144,6 +144,13 @@ __global__ void __launch_bounds__(DEC_WARPS * 32, 1) decode_kernel(DecArgs a) {
         int len = two_n;                       // sb[0, len): ops not scheduled yet, priority order
         for (int pass = 0; pass < two_n && done < two_n; ++pass) {
             bool progress = false;
+            // Whether a drop (a pickup) fits some vehicle does not depend on the
+            // customer: it needs one unit of room, resp. stock, on a vehicle.  A
+            // drop never makes room for another drop (it lowers its vehicle's
+            // stock and raises the pool's load), nor a pickup for another pickup,
+            // so once no vehicle takes a drop, every drop fails until a pickup is
+            // scheduled, and the other way round.  Those visits are skipped.
+            bool drops_blocked = false, picks_blocked = false;
             unsigned long long e_next = len > 0 ? sb[0] : 0ull;
             for (int k = 0; k < len; ++k) {
                 // the next op's entry is read ahead: the order does not change
@@ -153,8 +160,9 @@ __global__ void __launch_bounds__(DEC_WARPS * 32, 1) decode_kernel(DecArgs a) {
                 const int oi = static_cast<int>(e_cur & 0xffffffffu);
                 const int o = oi + 2, c = o >> 1;
                 const bool pick = (o & 1) != 0;
-                const unsigned wo = sched[o >> 5];
-                if ((wo >> (o & 31)) & 1u) continue;
+                // the list holds only ops unscheduled at the pass's start, and only
+                // the op visited gets scheduled: o itself is still unscheduled
+                if (pick ? picks_blocked : drops_blocked) continue;
                 if (pick && !((sched[(2 * c) >> 5] >> ((2 * c) & 31)) & 1u)) continue;
                 // the time a pickup waits for, read before the selection
                 const int ready = pick ? tdrop[c] + sp[c] : 0;
@@ -185,12 +193,18 @@ __global__ void __launch_bounds__(DEC_WARPS * 32, 1) decode_kernel(DecArgs a) {
                                                static_cast<unsigned>(lane))
                                             : 0xffffffffu;
                     const unsigned kmin = __reduce_min_sync(FULL_MASK, key);
-                    if (kmin == 0xffffffffu) continue;
+                    if (kmin == 0xffffffffu) {
+                        if (pick) picks_blocked = true; else drops_blocked = true;
+                        continue;
+                    }
                     win = static_cast<int>(kmin & 31u);
                 } else {
                     const unsigned ua = ok ? static_cast<unsigned>(arr) : 0xffffffffu;
                     const unsigned amin = __reduce_min_sync(FULL_MASK, ua);
-                    if (amin == 0xffffffffu) continue;
+                    if (amin == 0xffffffffu) {
+                        if (pick) picks_blocked = true; else drops_blocked = true;
+                        continue;
+                    }
                     const unsigned sub = (ok && ua == amin)
                                              ? ((static_cast<unsigned>(tie) << 5) | static_cast<unsigned>(lane))
                                              : 0xffffffffu;
@@ -212,9 +226,11 @@ __global__ void __launch_bounds__(DEC_WARPS * 32, 1) decode_kernel(DecArgs a) {
                     load = nload;
                     locv = c;
                     vs[oi] = (lane << 16) | cnt;
-                    sched[o >> 5] = wo | (1u << (o & 31));
+                    sched[o >> 5] |= 1u << (o & 31);
                     if (!pick) tdrop[c] = arr;
                 }
+                // a pickup can make room for drops, a drop stock for pickups
+                if (pick) drops_blocked = false; else picks_blocked = false;
                 cnt += me ? 1 : 0;
                 sum_load += __shfl_sync(FULL_MASK, dsum, win);
                 __syncwarp();
