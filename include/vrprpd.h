@@ -260,8 +260,15 @@ int vrprpd_multi_create(const vrprpd_instance* const* insts, const vrprpd_batch*
  * CUDA graph and later calls replay it; inside a caller's capture (or on the
  * NULL stream) it launches directly.  Results as vrprpd_evaluate. */
 int vrprpd_multi_evaluate(vrprpd_multi* plan, void* stream);
-/* Time warps-per-block and distance modes on the plan's own batches; keep the fastest. */
+/* Time the walk (staged, or streamed with one-warp groups), warps per block
+ * and distance mode (GLOBAL16/GLOBAL32) on the plan's own batches; keep the
+ * fastest. */
 int vrprpd_multi_autotune(vrprpd_multi* plan, void* stream, vrprpd_eval_config* chosen);
+/* Set the plan's shape by hand: dist_mode GLOBAL16 (every instance with a
+ * 16-bit matrix) or GLOBAL32, warps_per_block 1..32, walk staged or streamed
+ * with group_warps 1 (Section 4.2.1's multi-instance parallelism, the same
+ * evaluation).  VRPRPD_EINVAL when the shape does not fit. */
+int vrprpd_multi_set_config(vrprpd_multi* plan, const vrprpd_eval_config* cfg);
 void vrprpd_multi_destroy(vrprpd_multi* plan);
 
 /* ======================================================================== */

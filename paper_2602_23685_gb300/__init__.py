@@ -466,7 +466,11 @@ class MultiBatch:
     def autotune(self, stream=None):
         cfg = EvalConfig()
         _check(lib().vrprpd_multi_autotune(self._h, _stream_ptr(stream), C.byref(cfg)))
-        return {"dist_mode": _DIST_NAMES[cfg.dist_mode], "warps_per_block": cfg.warps_per_block}
+        return _cfg_dict(cfg)
+
+    def set_config(self, dist_mode="global16", warps_per_block=8, walk="staged"):
+        cfg = EvalConfig(DIST_MODES[dist_mode], warps_per_block, 0, WALKS[walk], 1)
+        _check(lib().vrprpd_multi_set_config(self._h, C.byref(cfg)))
 
     def close(self):
         if getattr(self, "_h", None) is not None:

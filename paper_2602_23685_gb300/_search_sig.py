@@ -68,6 +68,7 @@ def register(L):
     L.vrprpd_multi_create.argtypes = [vp, vp, vp, vp, C.c_int32, C.POINTER(vp)]
     L.vrprpd_multi_evaluate.argtypes = [vp, vp]
     L.vrprpd_multi_autotune.argtypes = [vp, vp, vp]
+    L.vrprpd_multi_set_config.argtypes = [vp, vp]
     L.vrprpd_multi_destroy.argtypes = [vp]
     L.vrprpd_multi_destroy.restype = None
     L.vrprpd_brkga_params_default.argtypes = [C.POINTER(BrkgaParams)]

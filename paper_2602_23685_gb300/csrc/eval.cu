@@ -693,6 +693,30 @@ __global__ void __launch_bounds__(1024) eval_multi_kernel(const EvalArgs* __rest
 }
 
 
+// The same with the streamed walk, one-warp groups: tile t of the whole job is
+// ⌊32/m⌋ candidates of the instance whose tile prefix brackets it, walked by
+// one warp whose region is sized for the largest instance.
+template <int DM>
+__global__ void __launch_bounds__(1024) eval_multi_stream_kernel(const EvalArgs* __restrict__ insts,
+                                                                 const long long* __restrict__ tile_prefix,
+                                                                 int n_inst, int group_words) {
+    extern __shared__ __align__(16) int32_t smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int32_t* W = smem + warp * group_words;
+    const long long total = tile_prefix[n_inst];
+    const long long gw = static_cast<long long>(blockIdx.x) * nwarps + warp;
+    const long long nw = static_cast<long long>(gridDim.x) * nwarps;
+    for (long long t = gw; t < total; t += nw) {
+        int lo = 0, hi = n_inst;                // prefix[lo] <= t < prefix[lo+1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(tile_prefix + mid) <= t) lo = mid; else hi = mid;
+        }
+        const EvalArgs a = insts[lo];
+        eval_stream_tile<DM, false, 1>(a, nullptr, a.p, W, lane, 0, t - __ldg(tile_prefix + lo));
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Plain form: thread per candidate, global scratch, Kahn order.
 // scratch per thread: ready[n+1], pos[m], dep[m], loc[m], seen[(2n+2+31)/32]
@@ -1321,10 +1345,12 @@ extern "C" int vrprpd_autotune(vrprpd_instance* I, const vrprpd_batch* b, void* 
 struct vrprpd_multi {
     int n_inst = 0, device = 0, num_sms = 0;
     size_t smem_optin = 0;
-    std::vector<EvalArgs> args;
-    std::vector<long long> prefix;
-    EvalArgs* d_args = nullptr;
-    long long* d_prefix = nullptr;
+    // per walk (0 staged, 1 streamed): per-instance arguments and tile prefix
+    std::vector<EvalArgs> args[2];
+    std::vector<long long> prefix[2];
+    EvalArgs* d_args[2] = {nullptr, nullptr};
+    long long* d_prefix[2] = {nullptr, nullptr};
+    int walk = VRPRPD_WALK_STAGED;
     int dm = VRPRPD_DIST_GLOBAL16, warps = 8, blocks = 0, warp_words = 0;
     size_t smem = 0;
     cudaGraph_t graph = nullptr;
@@ -1334,20 +1360,29 @@ struct vrprpd_multi {
 
 namespace vrp {
 
-static int multi_layout(vrprpd_multi* M, int dm, int warps) {
+static const void* multi_kernel(int walk, int dm) {
+    if (walk == VRPRPD_WALK_STREAMED)
+        return dm == VRPRPD_DIST_GLOBAL16 ? reinterpret_cast<const void*>(&eval_multi_stream_kernel<VRPRPD_DIST_GLOBAL16>)
+                                          : reinterpret_cast<const void*>(&eval_multi_stream_kernel<VRPRPD_DIST_GLOBAL32>);
+    return dm == VRPRPD_DIST_GLOBAL16 ? reinterpret_cast<const void*>(&eval_multi_kernel<VRPRPD_DIST_GLOBAL16>)
+                                      : reinterpret_cast<const void*>(&eval_multi_kernel<VRPRPD_DIST_GLOBAL32>);
+}
+
+static int multi_layout(vrprpd_multi* M, int dm, int warps, int walk) {
+    const bool streamed = walk == VRPRPD_WALK_STREAMED;
     int ww = 0;
-    for (auto& a : M->args) ww = std::max(ww, a.warp_words);
+    for (auto& a : M->args[streamed]) ww = std::max(ww, streamed ? a.group_words : a.warp_words);
     const size_t smem = static_cast<size_t>(warps) * ww * 4;
     if (smem + 64 > M->smem_optin) return VRPRPD_EINVAL;
-    const void* fn = dm == VRPRPD_DIST_GLOBAL16 ? reinterpret_cast<const void*>(&eval_multi_kernel<VRPRPD_DIST_GLOBAL16>)
-                                                : reinterpret_cast<const void*>(&eval_multi_kernel<VRPRPD_DIST_GLOBAL32>);
+    const void* fn = multi_kernel(walk, dm);
     { int rc_ = ensure_smem_limit(fn); if (rc_) return rc_; }
     int occ = 0;
     VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, warps * 32, smem));
     if (occ <= 0) return VRPRPD_EINVAL;
-    const long long total = M->prefix.back();
+    const long long total = M->prefix[streamed].back();
     M->blocks = static_cast<int>(std::max<long long>(1, std::min<long long>(static_cast<long long>(occ) * M->num_sms,
                                                                          (total + warps - 1) / warps)));
+    M->walk = walk;
     M->dm = dm;
     M->warps = warps;
     M->warp_words = ww;
@@ -1358,12 +1393,20 @@ static int multi_layout(vrprpd_multi* M, int dm, int warps) {
 }
 
 static int multi_launch(vrprpd_multi* M, cudaStream_t s) {
-    if (M->dm == VRPRPD_DIST_GLOBAL16)
-        eval_multi_kernel<VRPRPD_DIST_GLOBAL16><<<M->blocks, M->warps * 32, M->smem, s>>>(M->d_args, M->d_prefix,
-                                                                                         M->n_inst, M->warp_words);
+    const int w = M->walk == VRPRPD_WALK_STREAMED ? 1 : 0;
+    const dim3 grid(M->blocks), block(M->warps * 32);
+    if (w && M->dm == VRPRPD_DIST_GLOBAL16)
+        eval_multi_stream_kernel<VRPRPD_DIST_GLOBAL16><<<grid, block, M->smem, s>>>(M->d_args[1], M->d_prefix[1],
+                                                                                   M->n_inst, M->warp_words);
+    else if (w)
+        eval_multi_stream_kernel<VRPRPD_DIST_GLOBAL32><<<grid, block, M->smem, s>>>(M->d_args[1], M->d_prefix[1],
+                                                                                   M->n_inst, M->warp_words);
+    else if (M->dm == VRPRPD_DIST_GLOBAL16)
+        eval_multi_kernel<VRPRPD_DIST_GLOBAL16><<<grid, block, M->smem, s>>>(M->d_args[0], M->d_prefix[0],
+                                                                            M->n_inst, M->warp_words);
     else
-        eval_multi_kernel<VRPRPD_DIST_GLOBAL32><<<M->blocks, M->warps * 32, M->smem, s>>>(M->d_args, M->d_prefix,
-                                                                                         M->n_inst, M->warp_words);
+        eval_multi_kernel<VRPRPD_DIST_GLOBAL32><<<grid, block, M->smem, s>>>(M->d_args[0], M->d_prefix[0],
+                                                                            M->n_inst, M->warp_words);
     VRP_CUDA(cudaGetLastError());
     return VRPRPD_OK;
 }
@@ -1377,7 +1420,8 @@ extern "C" int vrprpd_multi_create(const vrprpd_instance* const* insts, const vr
     *out = nullptr;
     vrprpd_multi* M = new vrprpd_multi();
     M->n_inst = n_inst;
-    M->prefix.assign(1, 0);
+    M->prefix[0].assign(1, 0);
+    M->prefix[1].assign(1, 0);
     bool all16 = true;
     for (int i = 0; i < n_inst; ++i) {
         const vrprpd_instance* I = insts[i];
@@ -1398,22 +1442,34 @@ extern "C" int vrprpd_multi_create(const vrprpd_instance* const* insts, const vr
             return VRPRPD_EINVAL;
         }
         all16 = all16 && I->has_d16;
-        Plan P;
-        make_plan(I, VRPRPD_DIST_GLOBAL32, 1, 0, batches[i].num, &P);
-        EvalArgs a = P.args;
-        a.shared_words = 0;
-        a.dist_words = 0;
-        a.ops = batches[i].ops;
-        a.off = batches[i].off;
-        a.z = makespan[i];
-        a.st = status[i];
-        M->args.push_back(a);
-        M->prefix.push_back(M->prefix.back() + (a.num + a.k - 1) / a.k);
+        // both walks' layouts: the staged one (per warp) and the streamed one
+        // (one-warp groups); no instance data is staged in shared memory
+        for (int w = 0; w < 2; ++w) {
+            Plan P;
+            if (w == 0) make_plan(I, VRPRPD_DIST_GLOBAL32, 1, 0, batches[i].num, &P);
+            else make_plan_stream(I, VRPRPD_DIST_GLOBAL32, 1, 1, batches[i].num, &P);
+            EvalArgs a = P.args;
+            a.shared_words = 0;
+            a.dist_words = 0;
+            a.ops = batches[i].ops;
+            a.off = batches[i].off;
+            a.z = makespan[i];
+            a.st = status[i];
+            const long long per_tile = w == 0 ? a.k : a.K;
+            M->args[w].push_back(a);
+            M->prefix[w].push_back(M->prefix[w].back() + (a.num + per_tile - 1) / per_tile);
+        }
     }
-    cudaError_t e = cudaMalloc(&M->d_args, sizeof(EvalArgs) * n_inst);
-    if (e == cudaSuccess) e = cudaMalloc(&M->d_prefix, sizeof(long long) * (n_inst + 1));
-    if (e == cudaSuccess) e = cudaMemcpy(M->d_args, M->args.data(), sizeof(EvalArgs) * n_inst, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(M->d_prefix, M->prefix.data(), sizeof(long long) * (n_inst + 1), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaSuccess;
+    for (int w = 0; w < 2 && e == cudaSuccess; ++w) {
+        e = cudaMalloc(&M->d_args[w], sizeof(EvalArgs) * n_inst);
+        if (e == cudaSuccess) e = cudaMalloc(&M->d_prefix[w], sizeof(long long) * (n_inst + 1));
+        if (e == cudaSuccess)
+            e = cudaMemcpy(M->d_args[w], M->args[w].data(), sizeof(EvalArgs) * n_inst, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(M->d_prefix[w], M->prefix[w].data(), sizeof(long long) * (n_inst + 1),
+                           cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) {
         set_error("multi_create: %s", cudaGetErrorString(e));
         vrprpd_multi_destroy(M);
@@ -1421,7 +1477,7 @@ extern "C" int vrprpd_multi_create(const vrprpd_instance* const* insts, const vr
     }
     int rc = VRPRPD_EINVAL;
     for (int warps : {8, 4, 2, 1}) {
-        rc = multi_layout(M, all16 ? VRPRPD_DIST_GLOBAL16 : VRPRPD_DIST_GLOBAL32, warps);
+        rc = multi_layout(M, all16 ? VRPRPD_DIST_GLOBAL16 : VRPRPD_DIST_GLOBAL32, warps, VRPRPD_WALK_STAGED);
         if (rc == VRPRPD_OK) break;
     }
     if (rc) {
@@ -1460,35 +1516,57 @@ extern "C" int vrprpd_multi_autotune(vrprpd_multi* M, void* stream_, vrprpd_eval
     VRP_CHECK(M, VRPRPD_EINVAL, "NULL plan");
     cudaStream_t s = static_cast<cudaStream_t>(stream_);
     bool all16 = true;
-    for (auto& a : M->args) all16 = all16 && a.d16 != nullptr;
+    for (auto& a : M->args[0]) all16 = all16 && a.d16 != nullptr;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int bdm = M->dm, bw = M->warps;
-    for (int dm : {VRPRPD_DIST_GLOBAL16, VRPRPD_DIST_GLOBAL32}) {
-        if (dm == VRPRPD_DIST_GLOBAL16 && !all16) continue;
-        for (int warps : {4, 8, 12, 16, 24, 32}) {
-            if (multi_layout(M, dm, warps) != VRPRPD_OK) continue;
-            float ms_min = 1e30f;
-            for (int rep = 0; rep < 3; ++rep) {
-                cudaEventRecord(e0, s);
-                multi_launch(M, s);
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) ms_min = std::min(ms_min, ms);
+    int bdm = M->dm, bw = M->warps, bwalk = M->walk;
+    for (int walk : {VRPRPD_WALK_STAGED, VRPRPD_WALK_STREAMED}) {
+        for (int dm : {VRPRPD_DIST_GLOBAL16, VRPRPD_DIST_GLOBAL32}) {
+            if (dm == VRPRPD_DIST_GLOBAL16 && !all16) continue;
+            for (int warps : {4, 8, 12, 16, 24, 32}) {
+                if (multi_layout(M, dm, warps, walk) != VRPRPD_OK) continue;
+                float ms_min = 1e30f;
+                for (int rep = 0; rep < 3; ++rep) {
+                    cudaEventRecord(e0, s);
+                    multi_launch(M, s);
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) ms_min = std::min(ms_min, ms);
+                }
+                if (ms_min < best) { best = ms_min; bdm = dm; bw = warps; bwalk = walk; }
             }
-            if (ms_min < best) { best = ms_min; bdm = dm; bw = warps; }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    int rc = multi_layout(M, bdm, bw);
+    int rc = multi_layout(M, bdm, bw, bwalk);
     if (rc) return rc;
-    if (chosen) { chosen->dist_mode = bdm; chosen->warps_per_block = bw; chosen->blocks_per_sm = 0; }
+    if (chosen) {
+        chosen->dist_mode = bdm;
+        chosen->warps_per_block = bw;
+        chosen->blocks_per_sm = 0;
+        chosen->walk = bwalk;
+        chosen->group_warps = 1;
+    }
     VRP_CUDA(cudaGetLastError());
+    return VRPRPD_OK;
+}
+
+extern "C" int vrprpd_multi_set_config(vrprpd_multi* M, const vrprpd_eval_config* cfg) {
+    VRP_CHECK(M && cfg, VRPRPD_EINVAL, "NULL argument");
+    VRP_CHECK(cfg->dist_mode == VRPRPD_DIST_GLOBAL16 || cfg->dist_mode == VRPRPD_DIST_GLOBAL32, VRPRPD_EINVAL,
+              "many-instance plans gather distances from L2: dist_mode must be GLOBAL16 or GLOBAL32");
+    VRP_CHECK(cfg->walk == VRPRPD_WALK_STAGED || (cfg->walk == VRPRPD_WALK_STREAMED && cfg->group_warps == 1),
+              VRPRPD_EINVAL, "walk must be staged, or streamed with one-warp groups");
+    if (cfg->dist_mode == VRPRPD_DIST_GLOBAL16)
+        for (auto& a : M->args[0]) VRP_CHECK(a.d16 != nullptr, VRPRPD_EINVAL, "an instance has no 16-bit matrix");
+    VRP_CHECK(cfg->warps_per_block >= 1 && cfg->warps_per_block <= 32, VRPRPD_EINVAL, "bad warps_per_block");
+    const int rc = multi_layout(M, cfg->dist_mode, cfg->warps_per_block, cfg->walk);
+    VRP_CHECK(rc == VRPRPD_OK, rc, "this layout does not fit shared memory");
     return VRPRPD_OK;
 }
 
@@ -1496,8 +1574,10 @@ extern "C" void vrprpd_multi_destroy(vrprpd_multi* M) {
     if (!M) return;
     if (M->exec) cudaGraphExecDestroy(M->exec);
     if (M->graph) cudaGraphDestroy(M->graph);
-    cudaFree(M->d_args);
-    cudaFree(M->d_prefix);
+    for (int w = 0; w < 2; ++w) {
+        cudaFree(M->d_args[w]);
+        cudaFree(M->d_prefix[w]);
+    }
     delete M;
 }
 

@@ -25,14 +25,25 @@ def test_uneven_instances_one_launch(vrp):
         items.append((inst, torch.from_numpy(ops).cuda(), torch.from_numpy(off).cuda()))
         host.append((w, ops, off))
     mb = vrp.MultiBatch(items)
+    expect = [oracle.evaluate_batch(oracle.OracleInstance.from_workload(w), ops, off, threads=8)
+              for w, ops, off in host]
     z, st = mb.evaluate()
     torch.cuda.synchronize()
-    for (w, ops, off), zi, si, (inst, dops, doff) in zip(host, z, st, items):
-        zo, so = oracle.evaluate_batch(oracle.OracleInstance.from_workload(w), ops, off, threads=8)
+    for (zo, so), zi, si, (inst, dops, doff) in zip(expect, z, st, items):
         assert np.array_equal(zi.cpu().numpy(), zo)
         assert np.array_equal(si.cpu().numpy().astype(np.uint32), so)
         zp, sp = vrp.evaluate_plain(inst, dops, doff)
         assert np.array_equal(zp.cpu().numpy(), zo)
+    # both walks by hand, both distance modes
+    for walk in ("staged", "streamed"):
+        for mode in ("global16", "global32"):
+            mb.set_config(mode, 8, walk)
+            zz, ss = mb.evaluate()
+            torch.cuda.synchronize()
+            for (zo, so), zi, si in zip(expect, zz, ss):
+                assert np.array_equal(zi.cpu().numpy(), zo), (walk, mode)
+                assert np.array_equal(si.cpu().numpy().astype(np.uint32), so), (walk, mode)
+            z = [t.clone() for t in zz]
     cfg = mb.autotune()
     assert cfg["warps_per_block"] > 0
     z2, st2 = mb.evaluate()                     # replayed graph after re-planning
