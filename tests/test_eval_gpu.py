@@ -310,3 +310,27 @@ def test_n1000_full_size_sampled(vrp, seed):
     assert np.array_equal(z.cpu().numpy()[idx], zo), cfg
     assert np.array_equal(st.cpu().numpy().astype(np.uint32)[idx], so), cfg
     vrp.set_eval_config(inst, "auto")
+
+
+def test_repeated_op_across_warps_same_step(vrp):
+    """The streamed walk with two-warp groups at m = 20 packs three candidates
+    onto 64 lanes: candidate 1 of a group has routes 0-11 on the first warp
+    and routes 12-19 on the second.  Two routes that start with the same drop
+    (or the same pickup right after the same drop) on different warps reach
+    it in the same step; the exchange on the ready slot must still catch the
+    repeat (MALFORMED, as the oracle says)."""
+    n, m = 60, 20
+    w = workloads.make_instance(n, m, 60, 6, "2x", seed=21)
+    ops, off = workloads.precedence_candidates(n, m, 300, seed=21)
+    ops, off = ops.copy(), off.copy()
+    changed = []
+    for k in range(len(ops)):
+        if k % 3 != 1:
+            continue
+        r0, r15 = (0, 15) if k % 2 else (3, 17)
+        if off[k, r0 + 1] > off[k, r0] and off[k, r15 + 1] > off[k, r15]:
+            ops[k, off[k, r15]] = ops[k, off[k, r0]]
+            changed.append(k)
+    assert len(changed) > 50
+    inst, zo, so = check_against_oracle(vrp, w, ops, off)
+    assert (so[changed] == oracle.MALFORMED).all()
