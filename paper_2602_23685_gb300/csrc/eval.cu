@@ -436,7 +436,11 @@ __device__ __forceinline__ void eval_stream_tile(const EvalArgs& a, const int32_
     int32_t* ready = W + a.g_ready;     // K x (n+1): -(p+1) unresolved, T_drop + p, or PICKED
     int32_t* soff = W + a.g_off;        // K x (m+1)
     int32_t* flag = W + a.g_flag;       // K: 1 = malformed
-    int32_t* prog = W + a.g_prog;       // K: the last step in which the candidate progressed
+    // [2][K]: the last step (of the slot's parity) in which the candidate
+    // progressed.  Two slots: a warp of the group that has left step t's
+    // barrier may stamp step t+1 before another warp of the group has read
+    // step t's stamp; it can never reach step t+2 before that read
+    int32_t* prog = W + a.g_prog;
     int32_t* red = W + a.g_red;         // 3 x NT
     const long long first = t * K;
     const int kt = static_cast<int>(min(static_cast<long long>(K), a.num - first));
@@ -449,6 +453,7 @@ __device__ __forceinline__ void eval_stream_tile(const EvalArgs& a, const int32_
     for (int i = gl; i < kt; i += NT) {
         flag[i] = 0;
         prog[i] = -1;
+        prog[K + i] = -1;
     }
     for (int g = 0; g < kt; ++g)
         for (int c = gl; c <= n; c += NT) ready[g * N1 + c] = -1 - sp[c];
@@ -515,7 +520,7 @@ __device__ __forceinline__ void eval_stream_tile(const EvalArgs& a, const int32_
         pos += go1 ? 1 : 0;
         loc = go1 ? c1 : loc;
         // second op, only behind a first one that went
-        const bool try2 = go1 && !race1 && pos < end;
+        const bool try2 = go1 && pos < end;
         const int o2 = try2 ? q1 : 0;
         const bool in2 = static_cast<unsigned>(o2 - 2) < static_cast<unsigned>(two_n);
         const int c2 = in2 ? (o2 >> 1) : 0;
@@ -548,16 +553,19 @@ __device__ __forceinline__ void eval_stream_tile(const EvalArgs& a, const int32_
         q1 = go2 ? q3 : (go1 ? q2 : q1);
         rp32 += took;
         rp16 += took;
-        const bool fault = bad1 || bad2 || race1 || race2;
-        bad = bad || fault;
-        if (go1) prog[cand] = step;
+        // a repeat caught by the exchange only marks the candidate: the walk
+        // goes on (its slots stay in range and it still ends), which keeps the
+        // exchange's round trip off the step's critical path
+        const bool fault = bad1 || bad2;
+        bad = bad || fault || race1 || race2;
+        if (go1) prog[(step & 1) * K + cand] = step;
         const bool cont = walking && !fault && pos < end;
         // the group's barrier: every ready time and stamp of this step is
         // visible after it, so a candidate with no progress in a step while
         // unfinished can never progress again (a cycle, or a repeated or
         // missing op that the full check below tells apart)
         const bool any = group_any<G>(bar_id, cont);
-        cyc = cyc || (cont && prog[cand] != step);
+        cyc = cyc || (cont && prog[(step & 1) * K + cand] != step);
         walking = cont && !cyc;
         if (!any) break;
     }
@@ -856,7 +864,7 @@ static bool make_plan_stream(const vrprpd_instance* I, int dm, int warps, int G,
     a.g_off = round4(static_cast<long long>(a.K) * N1);
     a.g_flag = a.g_off + round4(static_cast<long long>(a.K) * (I->m + 1));
     a.g_prog = a.g_flag + round4(a.K);
-    a.g_red = a.g_prog + round4(a.K);
+    a.g_red = a.g_prog + round4(2ll * a.K);
     a.group_words = a.g_red + 3 * 32 * G;
     const size_t smem = static_cast<size_t>(a.shared_words + static_cast<long long>(warps / G) * a.group_words) * 4;
     if (smem + 64 > I->smem_optin) return false;

@@ -334,3 +334,28 @@ def test_repeated_op_across_warps_same_step(vrp):
     assert len(changed) > 50
     inst, zo, so = check_against_oracle(vrp, w, ops, off)
     assert (so[changed] == oracle.MALFORMED).all()
+
+
+def test_streamed_groups_repeatable(vrp):
+    """Two-warp groups meet once per step; a warp that leaves the barrier first
+    may start the next step before its partner has read this step's progress.
+    Many launches of mostly cyclic and acyclic candidates at m = 20 (one
+    candidate of each group split across the two warps), in several block
+    shapes, must all equal the oracle."""
+    n, m = 80, 20
+    w = workloads.make_instance(n, m, 80, 6, "2x", seed=31)
+    po, pf = workloads.precedence_candidates(n, m, 1500, seed=31)
+    ro, rf = workloads.random_candidates(n, m, 1500, seed=32)
+    ops, off = np.concatenate([po, ro]), np.concatenate([pf, rf])
+    inst = vrp.Instance.from_workload(w)
+    oi = oracle.OracleInstance.from_workload(w)
+    zo, so = oracle.evaluate_batch(oi, ops, off, threads=8)
+    assert (so & oracle.CYCLE).any() and not (so[:1500] & oracle.CYCLE).any()
+    do, df = dev(ops), dev(off)
+    for warps in (2, 8, 24):
+        vrp.set_eval_config(inst, "coords", warps, walk="streamed", group_warps=2)
+        for _ in range(8):
+            z, st = vrp.evaluate(inst, do, df)
+            vrp.sync(inst)
+            assert np.array_equal(z.cpu().numpy(), zo) and np.array_equal(st.cpu().numpy().astype(np.uint32), so), warps
+    vrp.set_eval_config(inst, "auto")
