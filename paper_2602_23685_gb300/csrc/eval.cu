@@ -476,8 +476,10 @@ __device__ __forceinline__ void eval_stream_tile(const EvalArgs& a, const int32_
     };
     // this lane's codes from its current position on, and its candidate's
     // ready slots as a shared-memory address
-    const int32_t* rp32 = a.ops + cbase + pos;
-    const uint16_t* rp16 = a.ops16 + cbase + pos;
+    const int32_t* rp32 = nullptr;
+    const uint16_t* rp16 = nullptr;
+    if constexpr (W16) rp16 = a.ops16 + cbase + pos;
+    else rp32 = a.ops + cbase + pos;
     const unsigned rdy_addr = smem_u32(ready + (active ? cand : 0) * N1);
     int dep = 0, s = 0, smin = 0, smax = 0, loc = 0;
     bool walking = ok_off && pos < end, cyc = false, bad = false;
@@ -551,8 +553,8 @@ __device__ __forceinline__ void eval_stream_tile(const EvalArgs& a, const int32_
         const int took = (go1 ? 1 : 0) + (go2 ? 1 : 0);
         q0 = go2 ? q2 : (go1 ? q1 : q0);
         q1 = go2 ? q3 : (go1 ? q2 : q1);
-        rp32 += took;
-        rp16 += took;
+        if constexpr (W16) rp16 += took;
+        else rp32 += took;
         // a repeat caught by the exchange only marks the candidate: the walk
         // goes on (its slots stay in range and it still ends), which keeps the
         // exchange's round trip off the step's critical path
