@@ -2721,7 +2721,7 @@ __device__ bool team_barrier_select(const AlnsTeam& t, const Smem& s, int team_b
     return *reinterpret_cast<volatile int*>(&ctl->err) == 0;
 }
 
-__global__ void __launch_bounds__(ALNS_THREADS, 4) alns_kernel(AlnsTeam* teams, int team_blocks) {
+__global__ void __launch_bounds__(ALNS_THREADS, 3) alns_kernel(AlnsTeam* teams, int team_blocks) {
     extern __shared__ __align__(16) int smem_alns[];
     __shared__ AlnsTeam team_s;
     const int team = blockIdx.x / team_blocks, rank = blockIdx.x - team * team_blocks;
