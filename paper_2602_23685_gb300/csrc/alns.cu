@@ -1429,6 +1429,14 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
             if ((fm >> kk) & 1u) list[at++] = make_int2(lpv[kk], (r << 8) | (cb + 8 * kk));
     }
     for (int q = tid; q < CB * TR; q += blockDim.x) rowbest[q] = KEY_NONE;
+    // a tile with no surviving pair and no adjacent entry has nothing to
+    // compute (no batch need be loaded); its entries count as in the loop below
+    if (total == 0 && !__syncthreads_or(diag >= 0 && adj_ok ? 1 : 0)) {
+        if (row_ok) local_entries += static_cast<unsigned>(nrem) * ncols;
+        const unsigned warp_entries = __reduce_add_sync(FULL_MASK, local_entries);
+        if ((tid & 31) == 0 && warp_entries) atomicAdd(&ctl->entries, static_cast<unsigned long long>(warp_entries));
+        return;
+    }
     const int beg = static_cast<int>((static_cast<long long>(tid) * total) / blockDim.x);
     const int end = static_cast<int>((static_cast<long long>(tid + 1) * total) / blockDim.x);
     for (int tb = 0; tb < nrem; tb += CB) {
