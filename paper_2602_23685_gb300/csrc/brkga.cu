@@ -75,18 +75,23 @@ __host__ __device__ inline int hint_vehicle(float alpha, int m) {
     return h < 0 ? 0 : h;
 }
 
+// The decoder specialised on its per-visit choices, so the chain of one op's
+// visit holds no branch on them: SD where distances come from (0 L2 int32,
+// 1 shared int32, 2 shared uint16), HINTS the 4n layout's tie rule, FULL the
+// Eq. 13 start load, PACK the one-reduction SelectVehicle.
+template <int SD, bool HINTS, bool FULL, bool PACK>
 __global__ void __launch_bounds__(DEC_WARPS * 32, 1) decode_kernel(DecArgs a) {
     extern __shared__ __align__(16) int smem_dec[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = a.n, m = a.m, two_n = 2 * n, N1 = n + 1;
     int* sd = smem_dec;                                   // staged distances (optional)
-    const int dist_words = a.smem_dist == 1 ? ((N1 * N1 + 3) & ~3) : a.smem_dist == 2 ? (((N1 * N1 + 1) / 2 + 3) & ~3) : 0;
+    const int dist_words = SD == 1 ? ((N1 * N1 + 3) & ~3) : SD == 2 ? (((N1 * N1 + 1) / 2 + 3) & ~3) : 0;
     int* sp = sd + dist_words;
     uint16_t* sd16 = reinterpret_cast<uint16_t*>(sd);
     for (int i = threadIdx.x; i < N1; i += blockDim.x) sp[i] = a.p[i];
-    if (a.smem_dist == 1)
+    if (SD == 1)
         for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) sd[i] = a.d32[i];
-    if (a.smem_dist == 2)
+    if (SD == 2)
         for (int i = threadIdx.x; i < N1 * N1; i += blockDim.x) sd16[i] = a.d16[i];
     int* wbase = sp + ((N1 + 3) & ~3) + warp * static_cast<int>(dec_warp_words(n, a.P));
     unsigned long long* sb = reinterpret_cast<unsigned long long*>(wbase);
@@ -98,8 +103,9 @@ __global__ void __launch_bounds__(DEC_WARPS * 32, 1) decode_kernel(DecArgs a) {
     const float* keys = a.keys;
     if (a.keys2 != nullptr && a.ctl->sel == 1) keys = a.keys2;
     auto dist = [&](int i, int j) -> int {
-        return a.smem_dist == 2 ? static_cast<int>(sd16[i * N1 + j])
-                                : a.smem_dist == 1 ? sd[i * N1 + j] : __ldg(a.d32 + i * N1 + j);
+        if constexpr (SD == 2) return static_cast<int>(sd16[i * N1 + j]);
+        else if constexpr (SD == 1) return sd[i * N1 + j];
+        else return __ldg(a.d32 + i * N1 + j);
     };
     for (int ch = blockIdx.x * DEC_WARPS + warp; ch < a.num; ch += gridDim.x * DEC_WARPS) {
         const float* kk = keys + static_cast<long long>(ch) * a.L;
@@ -115,7 +121,7 @@ __global__ void __launch_bounds__(DEC_WARPS * 32, 1) decode_kernel(DecArgs a) {
         for (int i = lane; i <= n; i += 32) tdrop[i] = 0;
         for (int i = lane; i < (two_n + 2 + 31) / 32; i += 32) sched[i] = 0u;
         for (int i = lane; i < two_n; i += 32) vs[i] = -1;
-        if (a.layout == VRPRPD_LAYOUT_HINTS)
+        if (HINTS)
             for (int i = lane; i < two_n; i += 32) hv[i] = static_cast<unsigned char>(hint_vehicle(kk[two_n + i], m));
         __syncwarp();
         for (int size = 2; size <= a.P; size <<= 1) {
@@ -131,7 +137,7 @@ __global__ void __launch_bounds__(DEC_WARPS * 32, 1) decode_kernel(DecArgs a) {
         }
         // ---- tie-break order: vehicle ranks (stable argsort of the m vehicle
         // keys) or, per op, cyclic distance from the hinted vehicle ----
-        const bool hints = a.layout == VRPRPD_LAYOUT_HINTS;
+        constexpr bool hints = HINTS;
         const float kv = (!hints && lane < m) ? __fadd_rn(kk[two_n + lane], 0.0f) : 0.0f;
         int rank = 0;
         for (int u = 0; !hints && u < m; ++u) {
@@ -169,13 +175,13 @@ __global__ void __launch_bounds__(DEC_WARPS * 32, 1) decode_kernel(DecArgs a) {
                 bool ok = false;
                 if (lane < m) {
                     if (!pick) {
-                        if (a.load_full) ok = net > -a.Q;
+                        if (FULL) ok = net > -a.Q;
                         else {
                             const int nl = max(load, 1 - net);
                             ok = nl + nmax <= a.Q && sum_load - load + nl <= a.R;
                         }
                     } else {
-                        ok = a.load_full ? (net < 0) : (load + net + 1 <= a.Q);
+                        ok = FULL ? (net < 0) : (load + net + 1 <= a.Q);
                     }
                 }
                 const int arr = ok ? tv + dist(locv, c) : 0;
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(DEC_WARPS * 32, 1) decode_kernel(DecArgs a) {
                 // every time below 2^22 the three fit one 32-bit key and one warp
                 // reduction; otherwise two reductions
                 int win;
-                if (a.pack) {
+                if constexpr (PACK) {
                     const unsigned key = ok ? ((static_cast<unsigned>(arr) << 10) | (static_cast<unsigned>(tie) << 5) |
                                                static_cast<unsigned>(lane))
                                             : 0xffffffffu;
@@ -557,12 +563,43 @@ static int plan_decode(const vrprpd_instance* I, int num, DecPlan* D) {
     }
     D->smem = (base_words + dist_words) * 4;
     VRP_CHECK(D->smem + 64 <= I->smem_optin, VRPRPD_EINVAL, "decode shared memory %zu too large", D->smem);
-    { int rc_ = ensure_smem_limit(reinterpret_cast<const void*>(&decode_kernel)); if (rc_) return rc_; }
+    return VRPRPD_OK;
+}
+
+// The decoder instance for these arguments.
+template <int SD, bool HINTS, bool FULL>
+static const void* decode_fn3(bool pack) {
+    return pack ? reinterpret_cast<const void*>(&decode_kernel<SD, HINTS, FULL, true>)
+                : reinterpret_cast<const void*>(&decode_kernel<SD, HINTS, FULL, false>);
+}
+template <int SD>
+static const void* decode_fn2(bool hints, bool full, bool pack) {
+    if (hints) return full ? decode_fn3<SD, true, true>(pack) : decode_fn3<SD, true, false>(pack);
+    return full ? decode_fn3<SD, false, true>(pack) : decode_fn3<SD, false, false>(pack);
+}
+static const void* decode_fn(int sd, bool hints, bool full, bool pack) {
+    if (sd == 2) return decode_fn2<2>(hints, full, pack);
+    if (sd == 1) return decode_fn2<1>(hints, full, pack);
+    return decode_fn2<0>(hints, full, pack);
+}
+static const void* decode_fn(const DecArgs& a) {
+    return decode_fn(a.smem_dist, a.layout == VRPRPD_LAYOUT_HINTS, a.load_full != 0, a.pack != 0);
+}
+// The grid of the instance that decodes with arguments a: as many blocks as
+// the chromosomes need, at most what stays resident on all SMs.
+static int plan_decode_grid(const vrprpd_instance* I, int num, const DecArgs& a, DecPlan* D) {
+    const void* fn = decode_fn(a);
+    { int rc_ = ensure_smem_limit(fn); if (rc_) return rc_; }
     int occ = 0;
-    VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, decode_kernel, DEC_WARPS * 32, D->smem));
+    VRP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, DEC_WARPS * 32, D->smem));
     VRP_CHECK(occ > 0, VRPRPD_EINVAL, "decode block does not fit");
     D->blocks = std::max(1, std::min((num + DEC_WARPS - 1) / DEC_WARPS, occ * I->num_sms));
     return VRPRPD_OK;
+}
+static cudaError_t launch_decode(const DecArgs& a, int blocks, size_t smem, cudaStream_t s) {
+    DecArgs args = a;
+    void* params[] = {&args};
+    return cudaLaunchKernel(decode_fn(a), dim3(blocks), dim3(DEC_WARPS * 32), params, smem, s);
 }
 
 static DecArgs dec_args(const vrprpd_instance* I, const DecPlan& D, int num, int layout) {
@@ -616,14 +653,15 @@ extern "C" int vrprpd_brkga_decode(const vrprpd_instance* I, const float* keys, 
     int rc = plan_decode(I, num, &D);
     if (rc) return rc;
     DecArgs a = dec_args(I, D, num, layout);
+    rc = plan_decode_grid(I, num, a, &D);
+    if (rc) return rc;
     a.keys = keys;
     a.ops = ops;
     a.off = off;
     a.z = z;
     a.unsched = unsched;
     a.fitness = reinterpret_cast<long long*>(fitness);
-    decode_kernel<<<D.blocks, DEC_WARPS * 32, D.smem, static_cast<cudaStream_t>(stream)>>>(a);
-    VRP_CUDA(cudaGetLastError());
+    VRP_CUDA(launch_decode(a, D.blocks, D.smem, static_cast<cudaStream_t>(stream)));
     return VRPRPD_OK;
 }
 
@@ -711,6 +749,8 @@ extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_par
     int rc = plan_decode(I, pop, &D);
     if (rc) { cleanup(); return rc; }
     DecArgs da = dec_args(I, D, pop, P->layout);
+    rc = plan_decode_grid(I, pop, da, &D);
+    if (rc) { cleanup(); return rc; }
     da.keys = buf0;
     da.keys2 = buf1;
     da.ctl = ctl;
@@ -725,8 +765,7 @@ extern "C" int vrprpd_brkga_run(const vrprpd_instance* I, const vrprpd_brkga_par
     { int rc_ = ensure_smem_limit(reinterpret_cast<const void*>(&rank_kernel)); if (rc_) { cleanup(); return rc_; } }
     const int evo_blocks = static_cast<int>(std::min<long long>((static_cast<long long>(pop) * L + 255) / 256, 8192));
     auto enqueue_eval_rank = [&]() -> int {
-        decode_kernel<<<D.blocks, DEC_WARPS * 32, D.smem, s>>>(da);
-        VRP_CUDA(cudaGetLastError());
+        VRP_CUDA(launch_decode(da, D.blocks, D.smem, s));
         int r = evaluate_device(I, dops, doff, pop, zev, stev, s);
         if (r) return r;
         rank_kernel<<<1, 1024, rank_smem, s>>>(zdec, un, zev, stev, pop, Prank, ctl, rank, fit, dtrace);
