@@ -160,10 +160,10 @@ int vrprpd_evaluate_plain(const vrprpd_instance* inst, const vrprpd_batch* batch
  *   scratch holds: blocks of up to 128 threads (a multiple of 32, fewer when
  *   fewer fit), and no more blocks than fit (vrprpd_evaluate_plain_noalloc_shape
  *   below gives the shape).
- *   The first call on each device looks up the array's device address (a
- *   runtime query, not an allocation) and keeps it for the life of the
- *   process; make that first call before any stream capture, and do not use
- *   this entry point after cudaDeviceReset on that device.  Every call shares
+ *   Every call looks up the array's address on the current device (a runtime
+ *   query, not an allocation), so the entry point stays valid across
+ *   cudaDeviceReset.  The first call on a device may load the library's
+ *   device code there; make it before any stream capture.  Every call shares
  *   the one array: calls whose kernels overlap on the GPU (different streams,
  *   or host threads without ordering) race on it.  The kernel initialises
  *   every scratch word it reads, so leftover contents from a previous call

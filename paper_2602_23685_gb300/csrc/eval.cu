@@ -26,7 +26,6 @@
 // global memory, distances from global memory.
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 
 #include "device_common.cuh"
 #include "internal.h"
@@ -1607,9 +1606,6 @@ extern "C" void vrprpd_multi_destroy(vrprpd_multi* M) {
 namespace vrp {
 constexpr long long NOALLOC_SCRATCH_WORDS = 4ll << 20;   // 4 Mi int32 = 16 MiB
 static __device__ __align__(256) int32_t g_noalloc_scratch[NOALLOC_SCRATCH_WORDS];
-constexpr int NOALLOC_MAX_DEVICES = 64;
-static void* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
-static std::mutex g_noalloc_mu;
 }  // namespace vrp
 
 extern "C" int vrprpd_evaluate_plain_noalloc_shape(int32_t n, int32_t m, int64_t num, int32_t* blocks,
@@ -1643,21 +1639,11 @@ extern "C" int vrprpd_evaluate_plain_noalloc(const vrprpd_instance* I, const vrp
     rc = vrprpd_evaluate_plain_noalloc_shape(I->n, I->m, b->num, &blocks, &threads);
     if (rc) return rc;
     const long long words = (I->n + 1) + 3ll * I->m + (2ll * I->n + 2 + 31) / 32;
-    int dev = 0;
-    VRP_CUDA(cudaGetDevice(&dev));
-    VRP_CHECK(dev >= 0 && dev < NOALLOC_MAX_DEVICES, VRPRPD_EINVAL, "device index %d too large", dev);
+    // the array's address on the current device, looked up on every call (the
+    // lookup allocates nothing): a cached address would dangle after a
+    // device reset reloads the module
     void* scratch = nullptr;
-    {
-        // one-time set-up per device (the current one): the host needs the
-        // array's device address; the symbol's host-side name is not it
-        std::lock_guard<std::mutex> lock(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void* p = nullptr;
-            VRP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-            g_noalloc_ptr[dev] = p;
-        }
-        scratch = g_noalloc_ptr[dev];
-    }
+    VRP_CUDA(cudaGetSymbolAddress(&scratch, g_noalloc_scratch));
     eval_plain_kernel<<<blocks, threads, 0, static_cast<cudaStream_t>(stream)>>>(
         b->ops, b->off, b->num, I->n, I->m, I->R, I->Q, (I->flags & VRPRPD_LOAD_FULL) != 0, I->d32, I->p, z, st,
         static_cast<int32_t*>(scratch), static_cast<int>(words));
