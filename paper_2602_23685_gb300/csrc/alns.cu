@@ -1397,10 +1397,10 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
     }
     // Only part of the pairs survive (a sixth to a third at n = 1000), scattered
     // over the tile.  They are compacted into one row-major list for the whole
-    // CTA and every thread takes an equal contiguous share of it per customer,
-    // keeping a running minimum per row that it folds into the row's slot in
-    // shared memory when its row changes; once per batch the row minima go to
-    // the global keys.
+    // CTA; per batch the customers share the threads out and each thread takes
+    // an equal contiguous share of the list for its customer, keeping a running
+    // minimum per row that it folds into the row's slot in shared memory when
+    // its row changes; once per batch the row minima go to the global keys.
     unsigned long long* rowbest = reinterpret_cast<unsigned long long*>(avec + CB * TR);   // [CB][TR]
     int2* list = reinterpret_cast<int2*>(rowbest + CB * TR);                                // [TR * TC]
     unsigned fm = 0;
@@ -1437,58 +1437,51 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
         if ((tid & 31) == 0 && warp_entries) atomicAdd(&ctl->entries, static_cast<unsigned long long>(warp_entries));
         return;
     }
-    const int beg = static_cast<int>((static_cast<long long>(tid) * total) / blockDim.x);
-    const int end = static_cast<int>((static_cast<long long>(tid + 1) * total) / blockDim.x);
     for (int tb = 0; tb < nrem; tb += CB) {
         const int nb = min(CB, nrem - tb);
         __syncthreads();                       // the list and the row slots are ready; the previous batch is flushed
         if (tb > 0) load_batch(tb, nb);
         __syncthreads();
-        // IL customers per pass over the share: the list entry and the row
-        // change are shared, the minimum chains run side by side
-        constexpr int IL = 4;
+        // the batch's customers split the threads (L each, the rest idle); a
+        // thread walks a contiguous share of the list for its customer,
+        // keeping the running minimum of its current row, and folds it into
+        // the row's slot only when its row changes, so a row's slot sees a
+        // few atomics rather than one per pair and customer
         const unsigned long long lim = static_cast<unsigned long long>(SKIPV) << 32;
-        for (int k = 0; k < nb; k += IL) {
-            int kx[IL];
-#pragma unroll
-            for (int u = 0; u < IL; ++u) kx[u] = min(k + u, nb - 1);
+        const int L = ALNS_THREADS / nb;
+        const int k = tid / L, li = tid - k * L;
+        if (k < nb) {
+            const int qb = static_cast<int>((static_cast<long long>(li) * total) / L);
+            const int qe = static_cast<int>((static_cast<long long>(li + 1) * total) / L);
+            const int4* cv = cvec + k * TC;
+            const int4* rw = rvec + k * TR;
+            unsigned long long* rb = rowbest + k * TR;
             int cur = -1;
-            int4 rv[IL];
-            unsigned long long best[IL];
-#pragma unroll
-            for (int u = 0; u < IL; ++u) { rv[u] = make_int4(0, 0, 0, 0); best[u] = KEY_NONE; }
-            for (int q = beg; q < end; ++q) {
+            int4 rv = make_int4(0, 0, 0, 0);
+            unsigned long long best = KEY_NONE;
+            for (int q = qb; q < qe; ++q) {
                 const int2 le = list[q];
                 const int rr = le.y >> 8;
                 if (rr != cur) {
-#pragma unroll
-                    for (int u = 0; u < IL; ++u) {
-                        if (best[u] < lim && k + u < nb) atomicMin(&rowbest[kx[u] * TR + cur], best[u]);
-                        rv[u] = rvec[kx[u] * TR + rr];
-                        best[u] = KEY_NONE;
-                    }
+                    if (best < lim) atomicMin(&rb[cur], best);
+                    rv = rw[rr];
+                    best = KEY_NONE;
                     cur = rr;
                 }
-                const int cc = le.y & 0xFF;
-#pragma unroll
-                for (int u = 0; u < IL; ++u) {
-                    const int4 g = cvec[kx[u] * TC + cc];
-                    const int zz = max(max(rv[u].x, g.x), max(rv[u].y + g.y, rv[u].z + le.x + g.z));
-                    const unsigned lo = static_cast<unsigned>(rv[u].w) + static_cast<unsigned>(g.w);
-                    const unsigned long long key = (static_cast<unsigned long long>(static_cast<unsigned>(zz)) << 32) | lo;
-                    best[u] = key < best[u] ? key : best[u];
-                }
+                const int4 g = cv[le.y & 0xFF];
+                const int zz = max(max(rv.x, g.x), max(rv.y + g.y, rv.z + le.x + g.z));
+                const unsigned lo = static_cast<unsigned>(rv.w) + static_cast<unsigned>(g.w);
+                const unsigned long long key = (static_cast<unsigned long long>(static_cast<unsigned>(zz)) << 32) | lo;
+                best = key < best ? key : best;
             }
-#pragma unroll
-            for (int u = 0; u < IL; ++u)
-                if (best[u] < lim && k + u < nb) atomicMin(&rowbest[kx[u] * TR + cur], best[u]);
-            if (diag >= 0 && adj_ok) {
-                for (int u = 0; u < IL && k + u < nb; ++u) {
-                    const int2 a = avec[(k + u) * TR + r];
-                    const unsigned long long key =
-                        (static_cast<unsigned long long>(static_cast<unsigned>(a.x)) << 32) | static_cast<unsigned>(a.y);
-                    if (key < lim) atomicMin(&rowbest[(k + u) * TR + r], key);
-                }
+            if (best < lim) atomicMin(&rb[cur], best);
+        }
+        if (diag >= 0 && adj_ok) {
+            for (int u = 0; u < nb; ++u) {
+                const int2 a = avec[u * TR + r];
+                const unsigned long long key =
+                    (static_cast<unsigned long long>(static_cast<unsigned>(a.x)) << 32) | static_cast<unsigned>(a.y);
+                if (key < lim) atomicMin(&rowbest[u * TR + r], key);
             }
         }
         if (row_ok) local_entries += static_cast<unsigned>(nb) * ncols;
