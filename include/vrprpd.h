@@ -362,6 +362,12 @@ typedef struct {
                                   T_final, the weights and phase times are replica 0's */
     int32_t imports;           /* best-of-all solutions taken at checkpoints, over all replicas */
     int32_t best_replica;      /* the replica whose best solution is returned */
+    int64_t pruned_entries;    /* of matrix_entries, those never scored: a lower bound over their
+                                  tile showed that none of them can be the one the repair operator
+                                  picks (its per-vehicle bests, or the best, are already at or
+                                  below it); the result is the same as scoring them */
+    int64_t tiles;             /* insertion-matrix tiles (32 drop gaps x 64 pickup gaps) run */
+    int64_t tiles_pruned;      /* of those, tiles in which no customer was left to score */
 } vrprpd_alns_stats;
 
 void vrprpd_alns_params_default(vrprpd_alns_params* params);

@@ -26,7 +26,8 @@ class AlnsStats(C.Structure):
                 ("fallback_entries", C.c_int64), ("team_blocks", C.c_int32), ("phase_ms", C.c_double * 6),
                 ("incremental_steps", C.c_int64), ("full_steps", C.c_int64), ("ls_moves", C.c_int32),
                 ("ls_new_best", C.c_int32), ("ls_ms", C.c_double), ("replicas", C.c_int32),
-                ("imports", C.c_int32), ("best_replica", C.c_int32)]
+                ("imports", C.c_int32), ("best_replica", C.c_int32), ("pruned_entries", C.c_int64),
+                ("tiles", C.c_int64), ("tiles_pruned", C.c_int64)]
 
 
 class BrkgaParams(C.Structure):

@@ -88,6 +88,8 @@ struct AlnsCtl {
     int upd[16];
     unsigned long long steps_incr, steps_full;
     unsigned long long entries, fallback_entries;
+    unsigned long long pruned;        // tile entries skipped by the bound (counted in entries too)
+    unsigned long long tiles, tiles_pruned;  // matrix tiles run, and those with no customer left to score
     unsigned long long phase_ns[7];   // begin, prep, gaps, matrix, select, end, local search (rank 0 wall time)
     // periodic local search: its mode while a candidate's matrix runs (0
     // otherwise), the pass's candidates, the best move so far (customer,
@@ -137,6 +139,9 @@ struct AlnsTeam {
     int2 *vadj;              // [q_max][G]: per (customer, gap) adjacent-pair vector
     unsigned long long* keys;  // [q_max][G]: per drop gap, best (dz, dt, col)
     unsigned long long* rkeys; // [q_max][32]: per drop vehicle, best (dz, dt, row)
+    unsigned long long* gmin;  // [q_max][4]: per vehicle group (v mod 4), best (dz, dt) seen so far
+    int4* bands;               // [q_max][band_stride]: per 32 gaps, least row x, row w, col x, col w
+    int band_stride;
     unsigned char* sc;         // [q_max][G]
     int* slist;                // [q_max * G] entries t * G + g
     int* scix;                 // [q_max][G]: index in slist of a shortcut (customer, gap)
@@ -167,6 +172,11 @@ struct Smem {
 };
 constexpr int RV = 16, CV = 12;   // row / col vector widths (ints)
 constexpr int CB = 8;             // customers per matrix batch
+// A tile's batch vectors, row minima and pair list (words), then the list of
+// the customers the tile still has to score (up to ACT_CAP of them; with more
+// customers waiting, every tile scores every customer).
+constexpr int TILE_WORDS = CB * (4 * TC + 8 * TR) + 2 * TR * TC;
+constexpr int ACT_CAP = 256;
 
 // Walk buffers (one ready array per warp).  The same words hold a matrix
 // tile's batch vectors, row minima and pair list, a shortcut item's
@@ -180,7 +190,7 @@ __host__ __device__ inline size_t rdy_words(int n) {
     const size_t fb = 2 * rw + 2 * ((static_cast<size_t>(2 * n) + 3) & ~static_cast<size_t>(3));
     // tile: column and row vectors, adjacent-pair vectors and row minima per
     // customer of a batch, then the compacted pair list (int2 per pair)
-    const size_t batch = static_cast<size_t>(CB) * (4 * TC + 8 * TR) + 2 * static_cast<size_t>(TR) * TC;
+    const size_t batch = static_cast<size_t>(TILE_WORDS) + ACT_CAP;
     const size_t sel = 5 * static_cast<size_t>(n) + 8;
     size_t w = walks > batch ? walks : batch;
     w = w > fb ? w : fb;
@@ -1028,6 +1038,8 @@ __device__ void phase_prep(const AlnsTeam& t, const Smem& s, int rank, int team_
         const bool shortcut = Dx(t, s, x, c) + Dx(t, s, c, y) < w;
         t.keys[e] = KEY_NONE;
         if (g < 32) t.rkeys[ti * 32 + g] = KEY_NONE;
+        if (g == 0)
+            for (int k = 0; k < 4; ++k) t.gmin[ti * 4 + k] = KEY_NONE;
         t.sc[e] = shortcut ? 1 : 0;
         if (shortcut) {
             const int slot = atomicAdd(&ctl->n_short, 1);
@@ -1087,42 +1099,97 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
     //   row {max(z, beta) (SKIPV on a shortcut gap), A1 + p_c, E, (dtD + 2^19) << 12}
     //   adj {max(z, adjacent) (SKIPV on a shortcut gap), ((dtAdj + 2^19) << 12) + gap}
     //   col {gamma (SKIPV on a shortcut gap), B1, F, (dtP << 12) + gap}
+    // Each warp takes 32 consecutive gaps of one customer (G padded to a
+    // multiple of 32), so that it can also reduce, per band of 32 gaps, the
+    // least row and column terms (the tiles' lower bounds), and fold the
+    // adjacent entries (drop and pickup back to back in one gap, exact here)
+    // into the keys before any tile runs.
     {
         AlnsCtl* ctl = t.ctl;
         const int nrem = ctl->nrem, z = ctl->z_work, lsm = ctl->ls;
-        const long long total = static_cast<long long>(nrem) * G;
-        for (long long e = tid; e < total; e += nthr) {
-            const int ti = static_cast<int>(e / G), g = static_cast<int>(e - static_cast<long long>(ti) * G);
+        const int Gp = (G + 31) & ~31;
+        const long long total = static_cast<long long>(nrem) * Gp;
+        const int sumL = ctl->sum_load;
+        for (long long e0 = tid; e0 < total; e0 += nthr) {
+            const int ti = static_cast<int>(e0 / Gp), g = static_cast<int>(e0 - static_cast<long long>(ti) * Gp);
+            const long long e = static_cast<long long>(ti) * G + g;
+            const bool valid = g < G;
             const int c = t.rem[ti], pc = s.sp[c];
-            int lo = 0, hi = m;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (s.sWoff[mid] + mid <= g) lo = mid; else hi = mid;
+            int4 vr = make_int4(SKIPV, 0, 0, 0), vc = make_int4(SKIPV, 0, 0, 0);
+            unsigned long long akey = KEY_NONE;
+            int r = 0;
+            if (valid) {
+                int lo = 0, hi = m;
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s.sWoff[mid] + mid <= g) lo = mid; else hi = mid;
+                }
+                r = lo;
+                const int pos = g - (s.sWoff[r] + r), off = s.sWoff[r], L = s.sWoff[r + 1] - off;
+                const int xo = pos > 0 ? off + pos - 1 : -1, yo = pos < L ? off + pos : -1;
+                const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0;
+                const int y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
+                const int Hx = xo >= 0 ? t.H[xo] : 0, Ty = yo >= 0 ? t.T[yo] : 0;
+                const int w = (L == 0) ? 0 : Dx(t, s, x, y);
+                const int dxc = Dx(t, s, x, c), dcy = Dx(t, s, c, y), dcc = Dx(t, s, c, c);
+                const int delta = dxc + dcy;
+                const bool shortcut = delta < w;
+                // a local-search slot allows some drop gaps (rows) and pickup gaps
+                // (columns) only; the others read as excluded
+                bool rok = true, cok = true;
+                if (lsm) {
+                    const int4 mk = t.lsmask[ti];
+                    rok = ((static_cast<unsigned>(mk.x) >> r) & 1u) != 0 && (mk.z < 0 || mk.z == g);
+                    cok = ((static_cast<unsigned>(mk.y) >> r) & 1u) != 0;
+                }
+                vr = make_int4(shortcut || !rok ? SKIPV : max(z, Hx + delta + Ty), Hx + dxc + pc, Hx + delta,
+                               static_cast<int>(static_cast<unsigned>(delta - w + (1 << 19)) << 12));
+                const int2 va = make_int2(shortcut || !(rok && cok) ? SKIPV : max(z, Hx + dxc + max(dcc, pc) + dcy + Ty),
+                                          static_cast<int>((static_cast<unsigned>(dxc + dcc + dcy - w + (1 << 19)) << 12) |
+                                                           static_cast<unsigned>(g)));
+                vc = make_int4(shortcut || !cok ? SKIPV : Hx + Ty + delta, dcy + Ty, delta + Ty,
+                               static_cast<int>((static_cast<unsigned>(delta - w) << 12) + static_cast<unsigned>(g)));
+                t.vrow[e] = vr;
+                t.vadj[e] = va;
+                t.vcol[e] = vc;
+                // the adjacent entry of gap g: the stock check of the drop and
+                // pickup together at g (the tiles' row constant), then its key
+                // in the form the tiles' row minima take
+                const int sb = xo >= 0 ? t.S_[xo] : 0, pmn = xo >= 0 ? t.PMINp[xo] : 0, pmx = xo >= 0 ? t.PMAXp[xo] : 0;
+                const int smn = yo >= 0 ? t.SMINs[yo] : (1 << 28), smx = yo >= 0 ? t.SMAXs[yo] : -(1 << 28);
+                int ladj = 0;
+                const bool okAdj = cap_ok(t, min(min(pmn, sb - 1), smn), max(pmx, smx), ladj) &&
+                                   sumL + ladj - t.rload[r] <= t.R;
+                if (okAdj && va.x < SKIPV)
+                    akey = (static_cast<unsigned long long>(static_cast<unsigned>(va.x - z) ^ 0x80000000u) << 32) |
+                           static_cast<unsigned>(va.y);
+                t.keys[e] = akey;
             }
-            const int r = lo, pos = g - (s.sWoff[r] + r), off = s.sWoff[r], L = s.sWoff[r + 1] - off;
-            const int xo = pos > 0 ? off + pos - 1 : -1, yo = pos < L ? off + pos : -1;
-            const int x = xo >= 0 ? (s.sW[xo] & PACK_MASK) >> 1 : 0;
-            const int y = yo >= 0 ? (s.sW[yo] & PACK_MASK) >> 1 : 0;
-            const int Hx = xo >= 0 ? t.H[xo] : 0, Ty = yo >= 0 ? t.T[yo] : 0;
-            const int w = (L == 0) ? 0 : Dx(t, s, x, y);
-            const int dxc = Dx(t, s, x, c), dcy = Dx(t, s, c, y), dcc = Dx(t, s, c, c);
-            const int delta = dxc + dcy;
-            const bool shortcut = delta < w;
-            // a local-search slot allows some drop gaps (rows) and pickup gaps
-            // (columns) only; the others read as excluded
-            bool rok = true, cok = true;
-            if (lsm) {
-                const int4 mk = t.lsmask[ti];
-                rok = ((static_cast<unsigned>(mk.x) >> r) & 1u) != 0 && (mk.z < 0 || mk.z == g);
-                cok = ((static_cast<unsigned>(mk.y) >> r) & 1u) != 0;
+            // band minima (excluded rows / columns left out), one store per warp
+            const unsigned rx = __reduce_min_sync(FULL_MASK, vr.x < SKIPV ? static_cast<unsigned>(vr.x) : 0x7fffffffu);
+            const unsigned rw = __reduce_min_sync(FULL_MASK, vr.x < SKIPV ? static_cast<unsigned>(vr.w) : 0xffffffffu);
+            const unsigned cx = __reduce_min_sync(FULL_MASK, vc.x < SKIPV ? static_cast<unsigned>(vc.x) : 0x7fffffffu);
+            const unsigned cw = __reduce_min_sync(FULL_MASK, vc.x < SKIPV ? static_cast<unsigned>(vc.w) : 0xffffffffu);
+            const int lane = threadIdx.x & 31;
+            if (lane == 0)
+                t.bands[static_cast<long long>(ti) * t.band_stride + (g >> 5)] =
+                    make_int4(static_cast<int>(rx), static_cast<int>(rw), static_cast<int>(cx), static_cast<int>(cw));
+            // adjacent entries per drop vehicle: the gaps of one warp lie on
+            // consecutive routes, each reduced by the whole warp
+            const int rlo = static_cast<int>(__reduce_min_sync(FULL_MASK, valid ? static_cast<unsigned>(r) : 0xffffffffu));
+            const int rhi = static_cast<int>(__reduce_max_sync(FULL_MASK, valid ? static_cast<unsigned>(r) : 0u));
+            const unsigned long long rkey = akey == KEY_NONE ? KEY_NONE : ((akey >> 12) << 12) | static_cast<unsigned>(g);
+            for (int rr = rlo; rr <= rhi; ++rr) {
+                unsigned long long v = valid && r == rr ? rkey : KEY_NONE;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long other = __shfl_xor_sync(FULL_MASK, v, o);
+                    v = other < v ? other : v;
+                }
+                if (lane == 0 && v != KEY_NONE) {
+                    atomicMin(&t.rkeys[ti * 32 + rr], v);
+                    atomicMin(&t.gmin[ti * 4 + (rr & 3)], v >> 12);
+                }
             }
-            t.vrow[e] = make_int4(shortcut || !rok ? SKIPV : max(z, Hx + delta + Ty), Hx + dxc + pc, Hx + delta,
-                                  static_cast<int>(static_cast<unsigned>(delta - w + (1 << 19)) << 12));
-            t.vadj[e] = make_int2(shortcut || !(rok && cok) ? SKIPV : max(z, Hx + dxc + max(dcc, pc) + dcy + Ty),
-                                  static_cast<int>((static_cast<unsigned>(dxc + dcc + dcy - w + (1 << 19)) << 12) |
-                                                   static_cast<unsigned>(g)));
-            t.vcol[e] = make_int4(shortcut || !cok ? SKIPV : Hx + Ty + delta, dcy + Ty, delta + Ty,
-                                  static_cast<int>((static_cast<unsigned>(delta - w) << 12) + static_cast<unsigned>(g)));
         }
     }
     // sparse tables of the stock prefix over op positions.  Every range query
@@ -1264,6 +1331,50 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
     int* rowc = s.rowv;                        // [TR][RV] constants of the drop gaps
     int* colc = s.colv;                        // [TC][CV] constants of the pickup gaps
     const int sumL = ctl->sum_load;
+    const bool dump = t.mode == 1;
+    const int nrem = ctl->nrem;
+    const int z = ctl->z_work;
+    // Which customers can this tile change the repair operator's pick for?
+    // Every entry of customer c here is at least
+    //     (max(least row x, least col x), least row w + least col w)
+    // over the tile's rows and columns (the band minima).  The pick needs
+    // per customer the best entry (greedy and the local search) and, for
+    // regret-2 and regret-3, the makespans of the best two or three drop
+    // vehicles.  The best of each vehicle group so far bounds the best entry
+    // and those makespans from above; an entry whose drop vehicle already has
+    // an entry of no larger makespan cannot change that vehicle's makespan.
+    // A customer none of whose entries here can matter is not scored.
+    // Regret-m needs every vehicle's best and skips only tiles without an
+    // admissible entry.  The tiles' own scores tighten the bounds as they go.
+    const bool prune_on = !dump && nrem <= ACT_CAP;
+    int* act = s.rdy + TILE_WORDS;             // [ACT_CAP] customers to score
+    int* nact = s.misc + 12;
+    if (tid == 0) *nact = 0;
+    int4 bnd_r = make_int4(0, 0, 0, 0), bnd_c0 = bnd_r, bnd_c1 = make_int4(0, 0, 0x7fffffff, -1);
+    unsigned long long gm[4] = {KEY_NONE, KEY_NONE, KEY_NONE, KEY_NONE};
+    const bool mine = prune_on && tid < nrem;
+    const int kind = ctl->ls ? 0 : ctl->rj;
+    // drop vehicles of the tile's rows: the routes of gaps r0 and min(G, r0 + TR) - 1
+    auto route_of_gap = [&](int g) {
+        int lo = 0, hi = t.m;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s.sWoff[mid] + mid <= g) lo = mid; else hi = mid;
+        }
+        return lo;
+    };
+    const int va0 = route_of_gap(r0), va1 = route_of_gap(min(G, r0 + TR) - 1);
+    unsigned long long vbest = 0;              // largest best makespan among those vehicles (regret)
+    if (mine) {
+        const int4* bp = t.bands + static_cast<long long>(tid) * t.band_stride;
+        bnd_r = bp[rt];
+        bnd_c0 = bp[2 * ct];
+        if (2 * ct + 1 < ((G + 31) >> 5)) bnd_c1 = bp[2 * ct + 1];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) gm[k] = t.gmin[tid * 4 + k];
+        if (kind == 1 || kind == 2)
+            for (int v = va0; v <= va1; ++v) vbest = max(vbest, t.rkeys[tid * 32 + v] >> 32);
+    }
     __syncthreads();                           // the previous tile is done with rowc / colc and the vectors
     for (int e = tid; e < TR * (RV / 4) + TC * (CV / 4); e += blockDim.x) {
         if (e < TR * (RV / 4)) {
@@ -1281,7 +1392,36 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
             reinterpret_cast<int4*>(colc)[e2] = v;
         }
     }
+    if (mine) {
+        const int lzz = max(bnd_r.x, min(bnd_c0.z, bnd_c1.z));
+        const unsigned llo = static_cast<unsigned>(bnd_r.y) + min(static_cast<unsigned>(bnd_c0.w), static_cast<unsigned>(bnd_c1.w));
+        bool keep = lzz < SKIPV;
+        if (keep && kind <= 2) {
+            const unsigned long long ldz = static_cast<unsigned>(lzz - z) ^ 0x80000000u;
+            const unsigned long long u = min(min(gm[0], gm[1]), min(gm[2], gm[3]));
+            keep = ((ldz << 20) | (llo >> 12)) <= u;   // may be the best entry
+            if (!keep && kind > 0) {
+                // the second (regret-2) or third (regret-3) least group makespan
+                unsigned long long d[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) d[k] = gm[k] >> 20;
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3 - i; ++j) {
+                        const unsigned long long a = min(d[j], d[j + 1]), b = max(d[j], d[j + 1]);
+                        d[j] = a;
+                        d[j + 1] = b;
+                    }
+                // may lower a drop vehicle's best makespan that counts
+                keep = ldz <= d[kind] && ldz < vbest;
+            }
+        }
+        if (keep) act[atomicAdd(nact, 1)] = tid;
+    }
     __syncthreads();
+    const int na = prune_on ? *nact : nrem;
+    auto cust = [&](int i) { return prune_on ? act[i] : i; };
     // Per customer the vectors of the tile's gaps come from the per-step arrays, CB
     // customers per pair of block barriers, into the walk buffers (unused by tiles):
     //   cols [CB][TC] int4, rows [CB][TR] int4, adj [CB][TR] int2.
@@ -1291,7 +1431,7 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
     auto load_batch = [&](int tb, int nb) {
         for (int it = tid; it < nb * (TR + TC); it += blockDim.x) {
             const int k = it / (TR + TC), slot = it - k * (TR + TC);
-            const long long vb = static_cast<long long>(tb + k) * G;
+            const long long vb = static_cast<long long>(cust(tb + k)) * G;
             if (slot < TR) {
                 const int Rr = r0 + slot;
                 const bool in = Rr < G;
@@ -1303,18 +1443,35 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
             }
         }
     };
-    // the first batch's vectors load while the pair values below are read
-    load_batch(0, min(CB, ctl->nrem));
     // this thread's pairs
     const int r = tid >> 3, cb = tid & 7;
     const int* rk = rowc + r * RV;
     const int ra = rk[8];
     const bool row_ok = ra >= 0;               // all 8 lanes of a row agree; no early exit (shuffles below)
     const int R = r0 + r;
+    const unsigned ncols = static_cast<unsigned>(max(0, min(TC / 8, (G - c0 - cb + 7) / 8)));  // this thread's columns < G
+    // every entry of the tile counts, scored or not
+    const unsigned local_entries = row_ok ? static_cast<unsigned>(nrem) * ncols : 0u;
+    const unsigned local_pruned = row_ok ? static_cast<unsigned>(nrem - na) * ncols : 0u;
+    auto count_entries = [&]() {
+        const unsigned we = __reduce_add_sync(FULL_MASK, local_entries);
+        const unsigned wp = __reduce_add_sync(FULL_MASK, local_pruned);
+        if ((tid & 31) == 0 && we) atomicAdd(&ctl->entries, static_cast<unsigned long long>(we));
+        if ((tid & 31) == 0 && wp) atomicAdd(&ctl->pruned, static_cast<unsigned long long>(wp));
+    };
+    if (tid == 0) {
+        atomicAdd(&ctl->tiles, 1ull);
+        if (na == 0) atomicAdd(&ctl->tiles_pruned, 1ull);
+    }
+    if (na == 0) {                             // no customer left to score: no pair work either
+        count_entries();
+        return;
+    }
     int lpv[TC / 8];
     int diag = -1;                             // column slot of the coinciding gap, if in this thread's set
     // both table reads of every pair first, as predicated loads all in flight
-    // together: LP(y_a -> x_b) and the cycle test LP(y_b -> x_a) > NEG
+    // together: LP(y_a -> x_b) and the cycle test LP(y_b -> x_a) > NEG; the
+    // first batch's vectors load while they are in flight
     int lpl[TC / 8], rcl[TC / 8];
     {
         const int xa = rk[10], ya = rk[11];
@@ -1329,6 +1486,7 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
             rcl[kk] = okr ? t.Ms[static_cast<long long>(yb) * N + xa] : NEG;
         }
     }
+    load_batch(0, min(CB, na));
 #pragma unroll
     for (int kk = 0; kk < TC / 8; ++kk) {
         const int cc = cb + 8 * kk;
@@ -1355,11 +1513,6 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
         lpv[kk] = v;
     }
     const bool adj_ok = rk[3] != 0;
-    const bool dump = t.mode == 1;
-    const int nrem = ctl->nrem;
-    const int z = ctl->z_work;
-    unsigned local_entries = 0;
-    const unsigned ncols = static_cast<unsigned>(max(0, min(TC / 8, (G - c0 - cb + 7) / 8)));  // this thread's columns < G
     if (dump) {
         // every entry of the first customer still to insert written out
         // (parity runs): shortcut entries are left to the shortcut items,
@@ -1429,16 +1582,14 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
             if ((fm >> kk) & 1u) list[at++] = make_int2(lpv[kk], (r << 8) | (cb + 8 * kk));
     }
     for (int q = tid; q < CB * TR; q += blockDim.x) rowbest[q] = KEY_NONE;
-    // a tile with no surviving pair and no adjacent entry has nothing to
-    // compute (no batch need be loaded); its entries count as in the loop below
-    if (total == 0 && !__syncthreads_or(diag >= 0 && adj_ok ? 1 : 0)) {
-        if (row_ok) local_entries += static_cast<unsigned>(nrem) * ncols;
-        const unsigned warp_entries = __reduce_add_sync(FULL_MASK, local_entries);
-        if ((tid & 31) == 0 && warp_entries) atomicAdd(&ctl->entries, static_cast<unsigned long long>(warp_entries));
+    // a tile with no surviving pair has nothing to compute (the adjacent
+    // entries were scored with the gap vectors)
+    if (total == 0) {
+        count_entries();
         return;
     }
-    for (int tb = 0; tb < nrem; tb += CB) {
-        const int nb = min(CB, nrem - tb);
+    for (int tb = 0; tb < na; tb += CB) {
+        const int nb = min(CB, na - tb);
         __syncthreads();                       // the list and the row slots are ready; the previous batch is flushed
         if (tb > 0) load_batch(tb, nb);
         __syncthreads();
@@ -1476,33 +1627,24 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
             }
             if (best < lim) atomicMin(&rb[cur], best);
         }
-        if (diag >= 0 && adj_ok) {
-            for (int u = 0; u < nb; ++u) {
-                const int2 a = avec[u * TR + r];
-                const unsigned long long key =
-                    (static_cast<unsigned long long>(static_cast<unsigned>(a.x)) << 32) | static_cast<unsigned>(a.y);
-                if (key < lim) atomicMin(&rowbest[u * TR + r], key);
-            }
-        }
-        if (row_ok) local_entries += static_cast<unsigned>(nb) * ncols;
         __syncthreads();
         // row minima of the batch to the global keys, slots back to empty
         for (int q = tid; q < nb * TR; q += blockDim.x) {
             const unsigned long long b = rowbest[q];
             if (b != KEY_NONE) {
                 const int k = q / TR, rr = q - k * TR;
-                const int ti = tb + k, Rr = r0 + rr, rra = rowc[rr * RV + 8];
+                const int ti = cust(tb + k), Rr = r0 + rr, rra = rowc[rr * RV + 8];
                 const unsigned long long key =
                     (static_cast<unsigned long long>(static_cast<unsigned>(static_cast<int>(b >> 32) - z) ^ 0x80000000u) << 32) |
                     (b & 0xFFFFFFFFull);
                 atomicMin(&t.keys[static_cast<long long>(ti) * G + Rr], key);
                 atomicMin(&t.rkeys[ti * 32 + rra], ((key >> 12) << 12) | static_cast<unsigned long long>(Rr));
+                atomicMin(&t.gmin[ti * 4 + (rra & 3)], key >> 12);
                 rowbest[q] = KEY_NONE;
             }
         }
     }
-    const unsigned warp_entries = __reduce_add_sync(FULL_MASK, local_entries);
-    if ((tid & 31) == 0 && warp_entries) atomicAdd(&ctl->entries, static_cast<unsigned long long>(warp_entries));
+    count_entries();
 }
 
 // Shortcut item: every entry with one shortcut gap g for customer c (the
@@ -1663,6 +1805,26 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
         }
         return false;
     };
+    // Tiles go out by their distance d = |ct - rt/2| from the diagonal (the
+    // column tile that holds the row band's own gaps): the entries near it
+    // (drop and pickup on one route or on neighbouring ones) are where a
+    // customer's best insertion usually lies, so their scores tighten the
+    // bounds before the far tiles are reached.  Per d, the tiles left of the
+    // diagonal (ct = rt/2 - d, rt = 2d..RT-1), then those right of it
+    // (ct = rt/2 + d, rt = 0..2(CT-d)-1).
+    auto tile_of = [&](int item, int* prt, int* pct) {
+        if (item < RT) { *prt = item; *pct = item >> 1; return; }
+        item -= RT;
+        for (int d = 1; d < CT; ++d) {
+            const int nl = max(0, RT - 2 * d), nr = max(0, min(RT, 2 * (CT - d)));
+            if (item < nl) { *prt = 2 * d + item; *pct = (*prt >> 1) - d; return; }
+            item -= nl;
+            if (item < nr) { *prt = item; *pct = (item >> 1) + d; return; }
+            item -= nr;
+        }
+        *prt = -1;                             // not reached: the counts add up to RT * CT
+        *pct = -1;
+    };
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) slot[0] = atomicAdd(&ctl->work_counter, 1);
@@ -1670,8 +1832,9 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
         const int item = slot[0];
         if (item >= total) break;
         if (item < tiles) {
-            const int rt = item / CT, ct = item - rt * CT;
-            if (!ls_skip(rt, ct)) matrix_tile(t, s, rt, ct, N, G);
+            int rt = 0, ct = 0;
+            tile_of(item, &rt, &ct);
+            if (rt >= 0 && !ls_skip(rt, ct)) matrix_tile(t, s, rt, ct, N, G);
         } else {
             if (!walks_seen) {
                 // the shortcut simulations, still running in other CTAs, must be done (bounded wait)
@@ -2915,6 +3078,8 @@ static size_t team_bytes(int n, int m, int qmax, int iterations, bool dump) {
     add(static_cast<size_t>(qmax) * G, 8);
     add(static_cast<size_t>(qmax) * G, 8);
     add(static_cast<size_t>(qmax) * 32, 8);
+    add(static_cast<size_t>(qmax) * 4, 8);
+    add(static_cast<size_t>(qmax) * ((G + 31) / 32), 16);
     add(static_cast<size_t>(qmax) * G, 1);
     add(static_cast<size_t>(qmax) * G, 4);
     add(static_cast<size_t>(qmax) * G, 4);
@@ -2952,6 +3117,9 @@ static void carve_team(AlnsTeam& t, DevBuf& B, int n, int m, int qmax, int itera
     t.vadj = B.take<int2>(static_cast<size_t>(qmax) * G);
     t.keys = B.take<unsigned long long>(static_cast<size_t>(qmax) * G);
     t.rkeys = B.take<unsigned long long>(static_cast<size_t>(qmax) * 32);
+    t.gmin = B.take<unsigned long long>(static_cast<size_t>(qmax) * 4);
+    t.band_stride = static_cast<int>((G + 31) / 32);
+    t.bands = B.take<int4>(static_cast<size_t>(qmax) * t.band_stride);
     t.sc = B.take<unsigned char>(static_cast<size_t>(qmax) * G);
     t.slist = B.take<int>(static_cast<size_t>(qmax) * G);
     t.scix = B.take<int>(static_cast<size_t>(qmax) * G);
@@ -3343,6 +3511,9 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
             stats->rejected_infeasible += o.rejected;
             stats->matrix_entries += static_cast<int64_t>(o.entries);
             stats->fallback_entries += static_cast<int64_t>(o.fallback_entries);
+            stats->pruned_entries += static_cast<int64_t>(o.pruned);
+            stats->tiles += static_cast<int64_t>(o.tiles);
+            stats->tiles_pruned += static_cast<int64_t>(o.tiles_pruned);
             stats->incremental_steps += static_cast<int64_t>(o.steps_incr);
             stats->full_steps += static_cast<int64_t>(o.steps_full);
             stats->ls_moves += o.ls_moves;
