@@ -70,10 +70,7 @@ struct AlnsCtl {
     int z_cur, z_best, z_work;
     unsigned st_work;
     int stagnation, repair_fail, wsel, err;
-    int work_counter, n_short, sum_load;
-    int walks_done;                   // shortcut simulations finished in this greedy step
     int pick_t, pick_row, pick_col;
-    unsigned bar_count, bar_gen;
     double T, T_init;
     double wd[8], wr[4];
     int sd[8], sr[4], ad[8], ar[4];
@@ -87,9 +84,6 @@ struct AlnsCtl {
     int incr;
     int upd[16];
     unsigned long long steps_incr, steps_full;
-    unsigned long long entries, fallback_entries;
-    unsigned long long pruned;        // tile entries skipped by the bound (counted in entries too)
-    unsigned long long tiles, tiles_pruned;  // matrix tiles run, and those with no customer left to score
     unsigned long long phase_ns[7];   // begin, prep, gaps, matrix, select, end, local search (rank 0 wall time)
     // periodic local search: its mode while a candidate's matrix runs (0
     // otherwise), the pass's candidates, the best move so far (customer,
@@ -100,6 +94,19 @@ struct AlnsCtl {
     int ls_moves, ls_new_best;
     long long ls_travel, ls_bt, ls_bflat;
     int imports;                      // best-of-all solutions this replica took at checkpoints
+    // Words that the whole team hits with atomics or polls, each group on a
+    // cache line of its own: the CTA that selects an insertion while the
+    // others wait reads and writes the state above without meeting their
+    // traffic.
+    alignas(128) unsigned bar_count;
+    alignas(128) unsigned bar_gen;
+    alignas(128) int work_counter;
+    alignas(128) int walks_done;      // shortcut simulations finished in this greedy step
+    alignas(128) int n_short;
+    int sum_load;
+    alignas(128) unsigned long long entries, fallback_entries;
+    unsigned long long pruned;        // tile entries skipped by the bound (counted in entries too)
+    unsigned long long tiles, tiles_pruned;  // matrix tiles run, and those with no customer left to score
 };
 
 struct AlnsTeam {
@@ -1740,6 +1747,7 @@ __device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N,
             const unsigned long long key = pack_key(zn - z, dt, col);
             atomicMin(&t.keys[scrow + row], key);
             atomicMin(&t.rkeys[ti * 32 + a], ((key >> 12) << 12) | static_cast<unsigned long long>(row));
+            atomicMin(&t.gmin[ti * 4 + (a & 3)], key >> 12);
         }
     }
     // both gaps shortcuts, from the drop gap's item: full re-simulation, one warp each
@@ -1774,6 +1782,7 @@ __device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N,
                         const unsigned long long key = pack_key(zn - z, dt, col);
                         atomicMin(&t.keys[scrow + g], key);
                         atomicMin(&t.rkeys[ti * 32 + a], ((key >> 12) << 12) | static_cast<unsigned long long>(g));
+                        atomicMin(&t.gmin[ti * 4 + (a & 3)], key >> 12);
                     }
                 }
             }
@@ -1788,7 +1797,11 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
     const int N = s.sWoff[t.m], G = N + t.m;
     const int RT = (G + TR - 1) / TR, CT = (G + TC - 1) / TC;
     const int tiles = RT * CT;
-    const int nfb = 2 * ctl->n_short;          // shortcut items after the tiles: they wait for the walks
+    // The shortcut items go out first: each scores a whole row or column of
+    // G entries, far more work than a tile, so at the end of the phase they
+    // would leave most of the team waiting; their simulations are done by the
+    // time the phase starts (the team barrier before it waits for every walk).
+    const int nfb = 2 * ctl->n_short;
     const int total = tiles + nfb;
     const int nwalks = gap_walk_items(t);
     bool walks_seen = false;
@@ -1831,9 +1844,9 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
         __syncthreads();
         const int item = slot[0];
         if (item >= total) break;
-        if (item < tiles) {
+        if (item >= nfb) {
             int rt = 0, ct = 0;
-            tile_of(item, &rt, &ct);
+            tile_of(item - nfb, &rt, &ct);
             if (rt >= 0 && !ls_skip(rt, ct)) matrix_tile(t, s, rt, ct, N, G);
         } else {
             if (!walks_seen) {
@@ -1853,7 +1866,7 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
                 __syncthreads();
                 walks_seen = true;
             }
-            fallback_item(t, s, item - tiles, N, G);
+            fallback_item(t, s, item, N, G);
         }
     }
 }
@@ -1898,60 +1911,82 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
     long long* regret = reinterpret_cast<long long*>(s.rdy) + nrem;                // [nrem]
     // the column of a customer's best entry, read from its row key (needed on
     // ties of (dz, dt) between customers and for the one picked)
-    auto colof = [&](int ti) {
-        return static_cast<int>(t.keys[static_cast<long long>(ti) * G + (bestv[ti] & 0xFFF)] & 0xFFF);
-    };
-    for (int ti = warp; ti < nrem; ti += ALNS_WARPS) {
-        // best per drop vehicle (the regret-2 options) and overall, from the route keys
-        const unsigned long long rk = lane < m ? t.rkeys[ti * 32 + lane] : KEY_NONE;
-        unsigned long long bv = rk;
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long other = __shfl_xor_sync(FULL_MASK, bv, o);
-            bv = other < bv ? other : bv;
+    int* colv = reinterpret_cast<int*>(regret + nrem);                              // [nrem]
+    auto colof = [&](int ti) { return colv[ti]; };
+    // A warp takes customers warp, warp + 8, ... four at a time, with the
+    // route keys of all four loaded before any is reduced.
+    constexpr int SU = 4;
+    for (int t0 = warp; t0 < nrem; t0 += SU * ALNS_WARPS) {
+        unsigned long long rks[SU];
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const int ti = t0 + u * ALNS_WARPS;
+            rks[u] = (ti < nrem && lane < m) ? t.rkeys[ti * 32 + lane] : KEY_NONE;
         }
-        // regret-k over the per-vehicle options: the sum over the k best of
-        // (c_i - c_1), options past the m there are counting as REGRET_INF;
-        // k = 2, 3 or m for repair operators 1, 2, 3 (greedy needs none of it)
-        const int rj = ctl->rj;
-        long long reg = 0;
-        if (rj != 0) {
-            const long long cvl = (lane < m && rk != KEY_NONE)
-                                      ? static_cast<long long>(static_cast<int>(static_cast<unsigned>(rk >> 32) ^ 0x80000000u))
-                                      : REGRET_INF;
-            // the least option (with its lane) and the least of the others, by
-            // two warp min-reductions of (option + 2^31) << 6 | lane
-            const unsigned long long key1 = (static_cast<unsigned long long>(cvl + (1ll << 31)) << 6) |
-                                            static_cast<unsigned long long>(lane);
-            unsigned long long k1 = key1;
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const int ti = t0 + u * ALNS_WARPS;
+            if (ti >= nrem) break;
+            // best per drop vehicle (the regret-2 options) and overall, from the route keys
+            const unsigned long long rk = rks[u];
+            unsigned long long bv = rk;
             for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long other = __shfl_xor_sync(FULL_MASK, k1, o);
-                k1 = other < k1 ? other : k1;
+                const unsigned long long other = __shfl_xor_sync(FULL_MASK, bv, o);
+                bv = other < bv ? other : bv;
             }
-            unsigned long long k2 = (static_cast<int>(k1 & 63u) == lane) ? ~0ull : key1;
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long other = __shfl_xor_sync(FULL_MASK, k2, o);
-                k2 = other < k2 ? other : k2;
-            }
-            const long long c1 = static_cast<long long>(k1 >> 6) - (1ll << 31);
-            const long long c2 = static_cast<long long>(k2 >> 6) - (1ll << 31);
-            if (rj == 1) {
-                reg = c2 - c1;
-            } else {
-                const int kreg = rj == 2 ? 3 : m;
-                int rnk = 0;
-                for (int u = 0; u < m; ++u) {
-                    const long long cu = __shfl_sync(FULL_MASK, cvl, u);
-                    if (cu < cvl || (cu == cvl && u < lane)) ++rnk;
+            // regret-k over the per-vehicle options: the sum over the k best of
+            // (c_i - c_1), options past the m there are counting as REGRET_INF;
+            // k = 2, 3 or m for repair operators 1, 2, 3 (greedy needs none of it)
+            const int rj = ctl->rj;
+            long long reg = 0;
+            if (rj != 0) {
+                const long long cvl = (lane < m && rk != KEY_NONE)
+                                          ? static_cast<long long>(static_cast<int>(static_cast<unsigned>(rk >> 32) ^ 0x80000000u))
+                                          : REGRET_INF;
+                // the least option (with its lane) and the least of the others, by
+                // two warp min-reductions of (option + 2^31) << 6 | lane
+                const unsigned long long key1 = (static_cast<unsigned long long>(cvl + (1ll << 31)) << 6) |
+                                                static_cast<unsigned long long>(lane);
+                unsigned long long k1 = key1;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long other = __shfl_xor_sync(FULL_MASK, k1, o);
+                    k1 = other < k1 ? other : k1;
                 }
-                long long term = (lane < m && rnk < kreg) ? cvl - c1 : 0;
-                for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(FULL_MASK, term, o);
-                if (kreg > m) term += static_cast<long long>(kreg - m) * (REGRET_INF - c1);
-                reg = term;
+                unsigned long long k2 = (static_cast<int>(k1 & 63u) == lane) ? ~0ull : key1;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const unsigned long long other = __shfl_xor_sync(FULL_MASK, k2, o);
+                    k2 = other < k2 ? other : k2;
+                }
+                const long long c1 = static_cast<long long>(k1 >> 6) - (1ll << 31);
+                const long long c2 = static_cast<long long>(k2 >> 6) - (1ll << 31);
+                if (rj == 1) {
+                    reg = c2 - c1;
+                } else {
+                    const int kreg = rj == 2 ? 3 : m;
+                    int rnk = 0;
+                    for (int v = 0; v < m; ++v) {
+                        const long long cu = __shfl_sync(FULL_MASK, cvl, v);
+                        if (cu < cvl || (cu == cvl && v < lane)) ++rnk;
+                    }
+                    long long term = (lane < m && rnk < kreg) ? cvl - c1 : 0;
+                    for (int o = 16; o > 0; o >>= 1) term += __shfl_xor_sync(FULL_MASK, term, o);
+                    if (kreg > m) term += static_cast<long long>(kreg - m) * (REGRET_INF - c1);
+                    reg = term;
+                }
+            }
+            if (lane == 0) {
+                bestv[ti] = bv;
+                regret[ti] = reg;
             }
         }
-        if (lane == 0) {
-            bestv[ti] = bv;
-            regret[ti] = reg;
+        // the best entries' columns, the four loads in flight together
+        __syncwarp();
+        if (lane < SU) {
+            const int ti = t0 + lane * ALNS_WARPS;
+            if (ti < nrem) {
+                const unsigned long long bv = bestv[ti];
+                colv[ti] = bv == KEY_NONE ? 0 : static_cast<int>(t.keys[static_cast<long long>(ti) * G + (bv & 0xFFF)] & 0xFFF);
+            }
         }
     }
     __syncthreads();
@@ -1974,28 +2009,42 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
                 if (regret[ti] > regret[pick]) pick = ti;
             }
         }
+        int* sel = s.misc + 24;                // fail, customer slot, row, column
+        sel[0] = (fail || pick < 0) ? 1 : 0;
         if (fail || pick < 0) {
             ctl->repair_fail = 1;
         } else {
-            ctl->pick_t = pick;
-            ctl->pick_row = static_cast<int>(bestv[pick] & 0xFFF);
-            ctl->pick_col = colof(pick);
+            sel[1] = pick;
+            sel[2] = static_cast<int>(bestv[pick] & 0xFFF);
+            sel[3] = colof(pick);
+            ctl->pick_t = sel[1];
+            ctl->pick_row = sel[2];
+            ctl->pick_col = sel[3];
         }
     }
     __syncthreads();
-    if (ctl->repair_fail) return;
-    // apply to the other W buffer
-    const int pick = ctl->pick_t, row = ctl->pick_row, col = ctl->pick_col;
+    const int* sel = s.misc + 24;
+    if (sel[0]) return;
+    // apply to the other W buffer; every load the step needs is issued first
+    const int pick = sel[1], row = sel[2], col = sel[3];
     const int c = t.rem[pick];
     const int a = t.groute[row], ia = t.gpos[row], b = t.groute[col], jb = t.gpos[col];
+    const long long scb = static_cast<long long>(pick) * G;
+    int xa = 0, ya = 0, xb = 0, yb = 0;
+    bool shortcut = false;
+    if (threadIdx.x == 0) {
+        shortcut = t.sc[scb + row] != 0 || t.sc[scb + col] != 0;
+        xa = t.gx[row]; ya = t.gy[row]; xb = t.gx[col]; yb = t.gy[col];
+    }
+    // the customers still to insert without the inserted one, order kept (in
+    // registers for the first blockDim.x of them)
+    const int k0 = threadIdx.x;
+    const int remv = k0 + 1 < nrem ? t.rem[k0 + (k0 >= pick ? 1 : 0)] : 0;
     insert_staged(t, s, c, a, ia, b, jb, t.W_ops[ctl->wsel ^ 1], t.W_off[ctl->wsel ^ 1]);
     if (threadIdx.x == 0) {
         // the next step updates the longest-path table incrementally unless a
         // gap of this insertion was a shortcut for c
-        const long long scb = static_cast<long long>(pick) * G;
-        const bool shortcut = t.sc[scb + row] != 0 || t.sc[scb + col] != 0;
         int* up = ctl->upd;
-        const int xa = t.gx[row], ya = t.gy[row], xb = t.gx[col], yb = t.gy[col];
         auto loc = [&](int pos) { return pos >= 0 ? (s.sW[pos] & PACK_MASK) >> 1 : 0; };
         up[0] = 1;
         up[1] = c;
@@ -2014,12 +2063,16 @@ __device__ void phase_select(const AlnsTeam& t, const Smem& s) {
         ctl->sum_load = 0;                     // the route scans of the next step add it back up
         ctl->walks_done = 0;
     }
-    __syncthreads();
-    // drop the inserted customer from the ones still to insert, order kept
-    int* tmp = s.rdy;
-    for (int k = threadIdx.x; k + 1 < nrem; k += blockDim.x) tmp[k] = t.rem[k + (k >= pick ? 1 : 0)];
-    __syncthreads();
-    for (int k = threadIdx.x; k + 1 < nrem; k += blockDim.x) t.rem[k] = tmp[k];
+    __syncthreads();                           // every read of t.rem is done
+    if (k0 + 1 < nrem) t.rem[k0] = remv;
+    // more customers than threads (a route removal): the rest in chunks, the
+    // loads of a chunk ahead of its stores
+    for (int kb = blockDim.x; kb + 1 < nrem; kb += blockDim.x) {
+        const int k = kb + threadIdx.x;
+        const int v = k + 1 < nrem ? t.rem[k + (k >= pick ? 1 : 0)] : 0;
+        __syncthreads();
+        if (k + 1 < nrem) t.rem[k] = v;
+    }
     if (threadIdx.x == 0) {
         ctl->nrem = nrem - 1;
         ctl->wsel ^= 1;
