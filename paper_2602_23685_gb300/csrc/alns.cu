@@ -59,6 +59,10 @@ constexpr int SKIPV = 1 << 28;                 // excluded matrix entry; schedul
 // Per shortcut gap: departures and tails with the drop alone (H1, T1) and with
 // the pickup alone (H2, T2), N words each, then z1, h_v1, t_v1, z2, h_v2, t_v2.
 constexpr int SC_CAP = 64;
+// Each shortcut item is handed out as FB_SPLIT pieces, each taking every
+// FB_SPLIT-th block of the row or column: an item's entries are long chains of
+// dependent loads, and whole items outlasted the rest of the matrix phase.
+constexpr int FB_SPLIT = 8;
 constexpr int TR = 32, TC = 64;                // matrix tile rows, cols
 constexpr int ALNS_THREADS = 256;
 constexpr int ALNS_WARPS = ALNS_THREADS / 32;
@@ -324,16 +328,29 @@ __device__ void stage_ops(const AlnsTeam& t, const Smem& s, const int* W, const 
     for (int i = threadIdx.x; i <= m; i += blockDim.x) s.sWoff[i] = Wo[i];
     __syncthreads();
     const int N = s.sWoff[m];
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        // the op before k on its route: none if k starts a route
-        int lo = 0, hi = m;                    // find route r with off[r] <= k < off[r+1]
-        while (hi - lo > 1) {
-            int mid = (lo + hi) >> 1;
-            if (s.sWoff[mid] <= k) lo = mid; else hi = mid;
+    // every load of a thread in flight together: its ops and the ops before them
+    constexpr int SU = 8;
+    for (int k0 = 0; k0 < N; k0 += SU * ALNS_THREADS) {
+        int o[SU], pr[SU];
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const int k = k0 + u * ALNS_THREADS + static_cast<int>(threadIdx.x);
+            o[u] = k < N ? W[k] : 0;
+            pr[u] = (k < N && k > 0) ? W[k - 1] : 0;
         }
-        const int o = W[k];
-        const int prev = (k == s.sWoff[lo]) ? 0 : (W[k - 1] >> 1);
-        s.sW[k] = (Dx(t, s, prev, o >> 1) << PACK_SHIFT) | o;
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+            const int k = k0 + u * ALNS_THREADS + static_cast<int>(threadIdx.x);
+            if (k >= N) break;
+            // the op before k on its route: none if k starts a route
+            int lo = 0, hi = m;                // find route r with off[r] <= k < off[r+1]
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (s.sWoff[mid] <= k) lo = mid; else hi = mid;
+            }
+            const int prev = (k == s.sWoff[lo]) ? 0 : (pr[u] >> 1);
+            s.sW[k] = (Dx(t, s, prev, o[u] >> 1) << PACK_SHIFT) | o[u];
+        }
     }
     __syncthreads();
 }
@@ -1671,6 +1688,8 @@ __device__ void matrix_tile(const AlnsTeam& t, const Smem& s, int rt, int ct, in
 // them) are re-simulated in full, in the item of their drop gap.
 __device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N, int G) {
     AlnsCtl* ctl = t.ctl;
+    const int piece = item % FB_SPLIT;
+    item /= FB_SPLIT;
     const int e = item >> 1, as_col = item & 1;
     const int packed = t.slist[e];
     const int ti = packed / G, g = packed - ti * G;
@@ -1714,7 +1733,7 @@ __device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N,
         return ((static_cast<unsigned>(mk.x) >> t.groute[row]) & 1u) != 0 && (mk.z < 0 || mk.z == row) &&
                ((static_cast<unsigned>(mk.y) >> t.groute[col]) & 1u) != 0;
     };
-    for (int k = tid; k < G && z1 != 0x7fffffff; k += blockDim.x) {
+    for (int k = piece * blockDim.x + tid; k < G && z1 != 0x7fffffff; k += FB_SPLIT * blockDim.x) {
         if (k == g || t.sc[scrow + k]) continue;              // both gaps shortcuts: below / elsewhere
         const int row = as_col ? k : g, col = as_col ? g : k;
         if (lsm && !allowed(row, col)) continue;
@@ -1754,7 +1773,7 @@ __device__ void fallback_item(const AlnsTeam& t, const Smem& s, int item, int N,
     if (!as_col) {
         __syncthreads();                       // Hb / Tb done; walk buffers back to one per warp
         int* rdy = s.rdy + warp * rw;
-        for (int k0 = warp * 32; k0 < G; k0 += ALNS_WARPS * 32) {
+        for (int k0 = (piece * ALNS_WARPS + warp) * 32; k0 < G; k0 += FB_SPLIT * ALNS_WARPS * 32) {
             const int kl = k0 + lane;
             const bool both = kl < G && (kl == g || t.sc[scrow + kl]);
             unsigned todo = __ballot_sync(FULL_MASK, both);
@@ -1801,7 +1820,7 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
     // G entries, far more work than a tile, so at the end of the phase they
     // would leave most of the team waiting; their simulations are done by the
     // time the phase starts (the team barrier before it waits for every walk).
-    const int nfb = 2 * ctl->n_short;
+    const int nfb = 2 * ctl->n_short * FB_SPLIT;
     const int total = tiles + nfb;
     const int nwalks = gap_walk_items(t);
     bool walks_seen = false;
