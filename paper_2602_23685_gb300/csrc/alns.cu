@@ -1077,7 +1077,16 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
     const int m = t.m, N = s.sWoff[m], G = N + m;
     const long long tid = static_cast<long long>(rank) * blockDim.x + threadIdx.x;
     const long long nthr = static_cast<long long>(team_blocks) * blockDim.x;
-    for (long long gg = tid; gg < G; gg += nthr) {
+    // The phase has three independent parts: the per-gap constants, the
+    // per-(customer, gap) vectors and the sparse tables.  The vectors take the
+    // CTAs from rank 0 up; the constants and the tables take CTAs from the top
+    // of the team down, below the last four (which start the shortcut
+    // simulations right after this phase), so that no CTA does two parts.
+    const int npg = (G + ALNS_THREADS - 1) / ALNS_THREADS;
+    const int rank_pg = ((team_blocks - 5 - rank) % team_blocks + team_blocks) % team_blocks;
+    const int rank_sp = ((team_blocks - 5 - npg - rank) % team_blocks + team_blocks) % team_blocks;
+    const long long tid_pg = static_cast<long long>(rank_pg) * blockDim.x + threadIdx.x;
+    for (long long gg = tid_pg; gg < G; gg += nthr) {
         const int g = static_cast<int>(gg);
         int lo = 0, hi = m;
         while (hi - lo > 1) {
@@ -1228,7 +1237,7 @@ __device__ void phase_gaps(const AlnsTeam& t, const Smem& s, int rank, int team_
     const int nseg = (N + SPB - 1) / SPB;
     int* bufA = s.rdy;
     int* bufB = s.rdy + SPB + (1 << top);
-    for (int seg = rank; seg < nseg; seg += team_blocks) {
+    for (int seg = rank_sp; seg < nseg; seg += team_blocks) {
         const int k0 = seg * SPB;
         const int wn = min(SPB + (1 << top), N - k0);
         for (int pass = 0; pass < 2; ++pass) {
