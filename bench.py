@@ -553,7 +553,8 @@ def run_profile_alns(args):
                       "phase_ms": list(st.phase_ms), "incremental_steps": st.incremental_steps,
                       "full_steps": st.full_steps,
                       "iters_per_s": iters / (st.device_ms / 1000), "team_blocks": st.team_blocks,
-                      "matrix_entries": st.matrix_entries, "fallback_entries": st.fallback_entries}))
+                      "matrix_entries": st.matrix_entries, "fallback_entries": st.fallback_entries,
+                      "pruned_entries": st.pruned_entries, "tiles": st.tiles, "tiles_pruned": st.tiles_pruned}))
 
 
 def run_profile_brkga(args):

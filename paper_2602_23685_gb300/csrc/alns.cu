@@ -1042,10 +1042,12 @@ __device__ void phase_prep(const AlnsTeam& t, const Smem& s, int rank, int team_
         }
     }
     // shortcut gaps (the rounded legs x->c->y shorter than x->y) and key reset
-    // for every customer still to insert; W alone decides them
+    // for every customer still to insert; W alone decides them.  The CTAs
+    // from the top of the team down take this part: the update's tiles go
+    // from rank 0 up, and the first CTAs may hold one tile more than the rest.
     const int G = N + t.m, nrem = ctl->nrem;
     const long long total = static_cast<long long>(nrem) * G;
-    const long long tid = static_cast<long long>(rank) * blockDim.x + threadIdx.x;
+    const long long tid = static_cast<long long>(team_blocks - 1 - rank) * blockDim.x + threadIdx.x;
     const long long nthr = static_cast<long long>(team_blocks) * blockDim.x;
     for (long long e = tid; e < total; e += nthr) {
         const int ti = static_cast<int>(e / G), g = static_cast<int>(e - static_cast<long long>(ti) * G);
