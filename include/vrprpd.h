@@ -339,6 +339,9 @@ typedef struct {
                                   vrprpd_initial_solution_paper, 0 the plain sweep of
                                   vrprpd_initial_solution */
     int32_t init_refine_rounds;/* refinement rounds of that start (default 10; 0 = the constructor alone) */
+    int64_t wait_limit_ns;     /* limit of each device-side wait of the team (its barriers), in ns: a
+                                  wait that runs out ends the run with VRPRPD_ETIMEOUT instead of
+                                  hanging (default 2 s; 0 = the default) */
 } vrprpd_alns_params;
 
 typedef struct {

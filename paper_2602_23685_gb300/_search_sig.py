@@ -14,7 +14,7 @@ class AlnsParams(C.Structure):
                 ("repair_mask", C.c_int32), ("team_blocks", C.c_int32),
                 ("destroy_mask", C.c_int32), ("ls_pickup_every", C.c_int32), ("ls_relocate_every", C.c_int32),
                 ("replicas", C.c_int32), ("sync_every", C.c_int32), ("init_mode", C.c_int32),
-                ("init_refine_rounds", C.c_int32)]
+                ("init_refine_rounds", C.c_int32), ("wait_limit_ns", C.c_int64)]
 
 
 class AlnsStats(C.Structure):

@@ -75,6 +75,7 @@ struct AlnsCtl {
     unsigned st_work;
     int stagnation, repair_fail, wsel, err;
     int pick_t, pick_row, pick_col;
+    unsigned long long wait_ns;       // limit of each spin-wait; one that runs out sets err
     double T, T_init;
     double wd[8], wr[4];
     int sd[8], sr[4], ad[8], ar[4];
@@ -269,7 +270,7 @@ __device__ bool team_barrier(AlnsCtl* ctl, int team_blocks, unsigned& gen) {
             } else {
                 const uint64_t t0 = global_ns();
                 while (*vgen == gen) {
-                    if (global_ns() - t0 > 2000000000ull) {
+                    if (global_ns() - t0 > ctl->wait_ns) {
                         atomicExch(&ctl->err, DEV_TIMEOUT_BARRIER);
                         break;
                     }
@@ -306,7 +307,7 @@ __device__ bool team_wait(AlnsCtl* ctl, int team_blocks, unsigned& gen) {
             volatile unsigned* vgen = &ctl->bar_gen;
             const uint64_t t0 = global_ns();
             while (*vgen == gen) {
-                if (global_ns() - t0 > 2000000000ull) {
+                if (global_ns() - t0 > ctl->wait_ns) {
                     atomicExch(&ctl->err, DEV_TIMEOUT_BARRIER);
                     break;
                 }
@@ -1885,7 +1886,7 @@ __device__ void phase_matrix(const AlnsTeam& t, const Smem& s) {
                     volatile int* wd = &ctl->walks_done;
                     const uint64_t t0 = global_ns();
                     while (*wd < nwalks) {
-                        if (global_ns() - t0 > 2000000000ull) {
+                        if (global_ns() - t0 > ctl->wait_ns) {
                             atomicExch(&ctl->err, DEV_TIMEOUT_BARRIER);
                             break;
                         }
@@ -2575,7 +2576,7 @@ __device__ bool grid_barrier(const AlnsTeam& t, unsigned& ggen) {
         } else {
             const uint64_t t0 = global_ns();
             while (*vgen == ggen) {
-                if (global_ns() - t0 > 2000000000ull) {
+                if (global_ns() - t0 > t.ctl->wait_ns) {
                     atomicExch(&t.ctl->err, DEV_TIMEOUT_BARRIER);
                     break;
                 }
@@ -2955,7 +2956,7 @@ __device__ bool team_barrier_select(const AlnsTeam& t, const Smem& s, int team_b
         volatile unsigned* vgen = &ctl->bar_gen;
         const uint64_t t0 = global_ns();
         while (*vgen == gen) {
-            if (global_ns() - t0 > 2000000000ull) {
+            if (global_ns() - t0 > ctl->wait_ns) {
                 atomicExch(&ctl->err, DEV_TIMEOUT_BARRIER);
                 break;
             }
@@ -3318,6 +3319,7 @@ extern "C" void vrprpd_alns_params_default(vrprpd_alns_params* P) {
     P->sync_every = 1000;
     P->init_mode = 1;
     P->init_refine_rounds = 10;
+    P->wait_limit_ns = 2000000000ll;
 }
 
 // exact angular order around the depot: half plane, then cross product, then id
@@ -3462,6 +3464,7 @@ static int run_team(const vrprpd_instance* I, const vrprpd_solution* init, const
         carve_team(ts[r], B, n, m, qcap, iters, dump);
     }
     AlnsCtl ctl{};
+    ctl.wait_ns = P->wait_limit_ns > 0 ? static_cast<unsigned long long>(P->wait_limit_ns) : 2000000000ull;
     for (int i = 0; i < 8; ++i) ctl.wd[i] = 1.0;
     ctl.wr[0] = ctl.wr[1] = ctl.wr[2] = ctl.wr[3] = 1.0;
     if (dump) {
