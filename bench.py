@@ -166,6 +166,7 @@ def summary_of(line):
         "ops16_evals_per_s": g("ops16", "value"), "ops16_e2e_evals_per_s": g("ops16", "e2e", "value"),
         "alns_n1000_iters_per_s": g("alns_n1000", "value"), "alns_n1000_iterations": g("alns_n1000", "iterations"),
         "alns_n1000_alu_frac": g("alns_n1000", "roofline", "frac"),
+        "alns_n1000_pruned_frac": g("alns_n1000", "pruned_frac"),
         "alns_n1000_x32_iters_per_s": g("alns_n1000_x32", "value"),
         "alns_n100_iters_per_s": g("alns_n100", "value"), "alns_n100_iterations": g("alns_n100", "iterations"),
         "brkga_n200_gens_per_s": g("brkga_n200", "value"), "brkga_n200_generations": g("brkga_n200", "generations"),
