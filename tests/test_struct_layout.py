@@ -65,3 +65,27 @@ def test_ctypes_mirrors_match_the_header(tmp_path):
             if got[(cname, f[0])] != getattr(cls, f[0]).offset:
                 bad.append((cname, f[0], got[(cname, f[0])], getattr(cls, f[0]).offset))
     assert not bad, bad
+
+
+def header_defines():
+    import re
+    text = open(os.path.join(ROOT, "include", "vrprpd.h")).read()
+    out = {}
+    for m in re.finditer(r"^#define\s+(VRPRPD_\w+)\s+\(?(-?\d+)u?\)?", text, re.M):
+        out[m.group(1)] = int(m.group(2))
+    return out
+
+
+def test_binding_constants_match_the_header():
+    """The binding's names for the header's distance modes, walks and
+    chromosome layouts carry the header's values."""
+    import paper_2602_23685_gb300 as vrp
+    d = header_defines()
+    for name, v in vrp.DIST_MODES.items():
+        assert d["VRPRPD_DIST_" + name.upper()] == v, name
+    for name, v in vrp.WALKS.items():
+        assert d["VRPRPD_WALK_" + name.upper()] == v, name
+    assert d["VRPRPD_LAYOUT_VKEYS"] == vrp.LAYOUT_VKEYS and d["VRPRPD_LAYOUT_HINTS"] == vrp.LAYOUT_HINTS
+    # the error codes and status bits the tests name
+    assert d["VRPRPD_ETIMEOUT"] == -4 and d["VRPRPD_EINVAL"] == -1
+    assert (d["VRPRPD_CYCLE"], d["VRPRPD_VEH_CAP"], d["VRPRPD_POOL"], d["VRPRPD_MALFORMED"]) == (1, 2, 4, 8)
